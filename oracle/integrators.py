@@ -1,0 +1,282 @@
+"""FP64 NumPy oracle of the time integrators: Arnoldi (modified Gram-Schmidt),
+the ROK step, classical RK4, ESDIRK3 with Newton-GMRES, the finite-difference
+epsilon, the CFL time step and the L2 error metric.
+
+TEST INFRASTRUCTURE ONLY.  Each function follows the paper's equations in
+their printed order; library primitives (dot products, dense solves) serve as
+single steps.  Readings of silent points are stated where they are used.
+
+The integrators see the problem only through a ``System``: ``sys.f(y)`` and
+``sys.jvp(y, v, f0, eps)`` (``core.System`` wraps the C residual).
+"""
+import math
+
+import numpy as np
+
+from . import coefficients as C
+from . import core
+
+MACH_EPS = 2.0 ** -52
+
+
+def fd_eps(ynorm, vnorm=1.0):
+    """Finite-difference increment for Eq. matvecFD.
+
+    The paper asks for the optimum trade-off between truncation and
+    round-off (citing Knoll & Keyes) without a formula.  Reading:
+    eps = sqrt(u (1 + ||y||)) / ||v||, u = 2^-52, rounded to the nearest
+    power of two (log-scale rounding), which keeps it within sqrt(2) of the
+    Knoll-Keyes value and makes eps*v and the division by eps exact."""
+    x = math.sqrt(MACH_EPS * (1.0 + ynorm)) / vnorm
+    m, e = math.frexp(x)           # x = m 2^e, 0.5 <= m < 1
+    if m < math.sqrt(0.5):
+        e -= 1
+    return math.ldexp(1.0, e)
+
+
+def arnoldi(sys, y, F1, M, eps, breakdown_tol=1e-12):
+    """Modified-Gram-Schmidt Arnoldi (Sec. 2.3.3): V (M_eff x N, rows orthonormal)
+    and H = V^T J V (M_eff x M_eff, upper Hessenberg) of K_M(J, f(y_n)), with the
+    Jacobian applied by Eq. matvecFD.  Returns (V, H, M_eff).
+
+    Readings: beta = ||F1|| = 0 gives M_eff = 0; the basis is cut at column j
+    when h_{j+1,j} <= breakdown_tol * ||J v_j|| (a scale-consistent test);
+    h_{j+1,j} > 0 makes V unique."""
+    N = F1.size
+    V = np.zeros((M, N))
+    H = np.zeros((M, M))
+    beta = float(np.linalg.norm(F1.ravel()))
+    if M == 0 or beta == 0.0:
+        return V[:0], H[:0, :0], 0
+    V[0] = F1.ravel() / beta
+    y_flat = y.ravel()
+    shape = y.shape
+    f0 = F1
+    meff = M
+    for j in range(M):
+        w = np.asarray(sys.jvp(y_flat.reshape(shape), V[j].reshape(shape), f0, eps)).ravel()
+        wnorm0 = float(np.linalg.norm(w))
+        for i in range(j + 1):
+            H[i, j] = float(np.dot(V[i], w))
+            w = w - H[i, j] * V[i]
+        if j + 1 < M:
+            hn = float(np.linalg.norm(w))
+            if hn <= breakdown_tol * wnorm0:
+                meff = j + 1
+                break
+            H[j + 1, j] = hn
+            V[j + 1] = w / hn
+    return V[:meff], H[:meff, :meff], meff
+
+
+def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=None):
+    """One step of the Rosenbrock-Krylov method, Eq. ROK (Sec. 2.3.3):
+
+        F_i      = f(y_n + sum_{j<i} alpha_ij k_j)
+        phi_i    = V^T F_i
+        lambda_i = (I - h g H)^{-1} (h phi_i + h H sum_{j<i} gamma_ij lambda_j)
+        k_i      = V lambda_i + h (F_i - V phi_i)
+        y_{n+1}  = y_n + sum_i b_i k_i
+
+    with V, H from Arnoldi on K_M(J_n, f(y_n)); the M x M systems are solved
+    by a dense LU (numpy)."""
+    g = C.ROK4_GAMMA if gamma is None else gamma
+    al = np.array(C.ROK4_ALPHA if alpha is None else alpha)
+    gm = np.array(C.ROK4_GAMMA_OFFDIAG if gamma_off is None else gamma_off)
+    bb = np.array(C.ROK4_B if b is None else b)
+    s = len(bb)
+    shape = y.shape
+    yf = y.ravel()
+    F1 = np.asarray(sys.f(y))
+    eps = fd_eps(float(np.linalg.norm(yf)))
+    V, H, meff = arnoldi(sys, y, F1, M, eps)
+    L = np.eye(meff) - h * g * H
+    ks, lams = [], []
+    for i in range(s):
+        if i == 0:
+            F = F1.ravel()
+        else:
+            Y = yf.copy()
+            for j in range(i):
+                if al[i, j] != 0.0:
+                    Y = Y + al[i, j] * ks[j]
+            F = np.asarray(sys.f(Y.reshape(shape))).ravel()
+        phi = V @ F
+        acc = np.zeros(meff)
+        for j in range(i):
+            acc = acc + gm[i, j] * lams[j]
+        rhs = h * phi + h * (H @ acc)
+        lam = np.linalg.solve(L, rhs) if meff > 0 else np.zeros(0)
+        k = V.T @ lam + h * (F - V.T @ phi)
+        ks.append(k)
+        lams.append(lam)
+    ynew = yf.copy()
+    for i in range(s):
+        ynew = ynew + bb[i] * ks[i]
+    if info is not None:
+        info.update(m_eff=meff, eps=eps, H=H, V=V)
+    return ynew.reshape(shape)
+
+
+def rk_step(sys, y, h, A=None, b=None):
+    """Explicit Runge-Kutta step, Eq. RK (Sec. 2.1): k_i = f(y_n + h sum_j a_ij k_j),
+    y_{n+1} = y_n + h sum_j b_j k_j; classical RK4 by default."""
+    A = np.array(C.RK4_A if A is None else A)
+    b = np.array(C.RK4_B if b is None else b)
+    ks = []
+    for i in range(len(b)):
+        acc = np.zeros_like(y)
+        for j in range(i):
+            if A[i, j] != 0.0:
+                acc = acc + A[i, j] * ks[j]
+        ks.append(np.asarray(sys.f(y + h * acc)))
+    acc = np.zeros_like(y)
+    for j in range(len(b)):
+        acc = acc + b[j] * ks[j]
+    return y + h * acc
+
+
+def gmres(matvec, rhs, m=30, tol=1e-6, max_restarts=5):
+    """Restarted GMRES(m), no preconditioner, x0 = 0, modified Gram-Schmidt
+    Arnoldi, least-squares on the (j+2) x (j+1) Hessenberg each iteration.
+    Stops when ||rhs - A x|| <= tol ||rhs||.  Returns (x, iterations, converged)."""
+    n = rhs.size
+    x = np.zeros(n)
+    bnorm = float(np.linalg.norm(rhs))
+    if bnorm == 0.0:
+        return x, 0, True
+    its = 0
+    for _cycle in range(max_restarts + 1):
+        r = rhs - matvec(x) if its else rhs.copy()
+        beta = float(np.linalg.norm(r))
+        if beta <= tol * bnorm:
+            return x, its, True
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        V[0] = r / beta
+        yls = None
+        for j in range(m):
+            w = matvec(V[j])
+            for i in range(j + 1):
+                H[i, j] = float(np.dot(V[i], w))
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = float(np.linalg.norm(w))
+            its += 1
+            e1 = np.zeros(j + 2)
+            e1[0] = beta
+            yls = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+            res = float(np.linalg.norm(e1 - H[:j + 2, :j + 1] @ yls))
+            if res <= tol * bnorm or H[j + 1, j] == 0.0:
+                x = x + V[:j + 1].T @ yls
+                return x, its, True
+            V[j + 1] = w / H[j + 1, j]
+        x = x + V[:m].T @ yls
+    r = rhs - matvec(x)
+    return x, its, float(np.linalg.norm(r)) <= tol * bnorm
+
+
+def esdirk_step(sys, y, h, gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, newton_tol=1e-10,
+                newton_max=10, info=None):
+    """ESDIRK3 step (Sec. 2.1, Eqs. RK, Newton, SDIRK_Newton, Newton_Jac_Matrix):
+    k_1 = f(y_n); for i >= 2 solve k_i = f(xi_i + h g k_i), xi_i = y_n + h sum_{j<i} a_ij k_j,
+    by Newton with the matrix I - h g J_n (J_n at y_n, applied by Eq. matvecFD) and
+    GMRES for each Newton correction; y_{n+1} = y_n + h sum b_j k_j.
+
+    Readings: predictor k_i^0 = k_{i-1}; Newton stops when
+    h g ||dk|| <= newton_tol ||xi_i + h g k_i|| or after newton_max iterations."""
+    A = np.array(C.ESDIRK3_A)
+    b = np.array(C.ESDIRK3_B)
+    g = C.ESDIRK3_GAMMA
+    shape = y.shape
+    yf = y.ravel()
+    F0 = np.asarray(sys.f(y)).ravel()
+    eps = fd_eps(float(np.linalg.norm(yf)))
+
+    def jv(v):
+        return np.asarray(sys.jvp(y, v.reshape(shape), F0.reshape(shape), eps)).ravel()
+
+    def op(v):
+        return v - (h * g) * jv(v)
+
+    ks = [F0]
+    newton_its, gmres_its, ok = 0, 0, True
+    for i in range(1, len(b)):
+        xi = yf.copy()
+        for j in range(i):
+            if A[i, j] != 0.0:
+                xi = xi + (h * A[i, j]) * ks[j]
+        k = ks[-1].copy()
+        conv = False
+        for _it in range(newton_max):
+            Yst = xi + (h * g) * k
+            G = k - np.asarray(sys.f(Yst.reshape(shape))).ravel()
+            dk, its, _c = gmres(op, -G, gmres_m, gmres_tol, gmres_restarts)
+            gmres_its += its
+            newton_its += 1
+            k = k + dk
+            if (h * g) * float(np.linalg.norm(dk)) <= newton_tol * float(np.linalg.norm(xi + (h * g) * k)):
+                conv = True
+                break
+        ok = ok and conv
+        ks.append(k)
+    ynew = yf.copy()
+    acc = np.zeros_like(yf)
+    for j in range(len(b)):
+        acc = acc + b[j] * ks[j]
+    ynew = ynew + h * acc
+    if info is not None:
+        info.update(newton_iters=newton_its, gmres_iters=gmres_its, converged=ok, eps=eps)
+    return ynew.reshape(shape)
+
+
+def dt_from_cfl(prob, y, cfl):
+    """Time step from a CFL number (the paper does not define one).  Reading:
+    dt = CFL / max_cells [ (|u.S_i| + c|S_i|)/Vol + (|u.S_j| + c|S_j|)/Vol
+                           + 2 nu_eff (|S_i|^2 + |S_j|^2)/Vol^2 ],
+    S_i, S_j the mean face-area vectors of the cell's i and j faces,
+    nu_eff = max(4/3, gamma/Pr) mu / rho (zero for Euler)."""
+    if prob.kind == 2:
+        return cfl / (np.max(np.abs(y)) + 1.0)
+    g = prob.gamma
+    rho = y[0]
+    u = y[1] / rho
+    v = y[2] / rho
+    p = (g - 1.0) * (y[3] - 0.5 * rho * (u * u + v * v))
+    c = np.sqrt(g * p / rho)
+    if prob.xv is None:
+        dx, dy = prob.lx / prob.nx, prob.ly / prob.ny
+        six, siy = np.full(rho.shape, dy), np.zeros(rho.shape)
+        sjx, sjy = np.zeros(rho.shape), np.full(rho.shape, dx)
+        vol = np.full(rho.shape, dx * dy)
+    else:
+        xv, yv = prob.xv, prob.yv
+        # i-face area vectors (e_y, -e_x) at i and i+1, averaged
+        exi = xv[1:, :] - xv[:-1, :]
+        eyi = yv[1:, :] - yv[:-1, :]
+        six = 0.5 * (eyi[:, :-1] + eyi[:, 1:])
+        siy = 0.5 * (-exi[:, :-1] - exi[:, 1:])
+        exj = xv[:, 1:] - xv[:, :-1]
+        eyj = yv[:, 1:] - yv[:, :-1]
+        sjx = 0.5 * (-eyj[:-1, :] - eyj[1:, :])
+        sjy = 0.5 * (exj[:-1, :] + exj[1:, :])
+        vol = core.cell_volumes(prob)
+    si2 = six * six + siy * siy
+    sj2 = sjx * sjx + sjy * sjy
+    lam = (np.abs(u * six + v * siy) + c * np.sqrt(si2)) / vol + (np.abs(u * sjx + v * sjy) + c * np.sqrt(sj2)) / vol
+    if prob.kind == 1 and prob.mu > 0.0:
+        T = p / rho
+        if prob.sutherland_s > 0.0:
+            t = T / prob.t_ref
+            mu = prob.mu * t ** 1.5 * (1.0 + prob.sutherland_s) / (t + prob.sutherland_s)
+        else:
+            mu = prob.mu
+        nu = max(4.0 / 3.0, g / prob.prandtl) * mu / rho
+        lam = lam + 2.0 * nu * (si2 + sj2) / (vol * vol)
+    return float(cfl / np.max(lam))
+
+
+def l2_error(y, yref, relative=True):
+    """Error metric of Sec. 4.1: ||y_N - y_ref||_2 over the full state vector
+    (relative to ||y_ref||_2 when ``relative``)."""
+    e = float(np.linalg.norm((y - yref).ravel()))
+    return e / float(np.linalg.norm(yref.ravel())) if relative else e
