@@ -1,0 +1,292 @@
+"""Benchmark of the ROK4 hot path on GB300.
+
+Workload (one step = one ROK4 step, rows a1-a7 of the hot path): decaying 2-D
+Navier-Stokes Taylor-Green vortex, periodic 512 x 512 uniform grid, M = 0.1,
+Re = 1600, FP64 state, Krylov dimension M = 20, time step at CFL 8.  Synthetic
+data from the closed-form initial condition.  Metric: cells x JVPs per second
+of whole ROK4 steps (Mcell-JVP/s), with the roofline of the dominant kernel
+(the FP64 residual/JVP stencil) and the RK4 / ESDIRK3 comparators on the same
+state.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 evaluation of the same
+step) on this host's cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID, RE, MACH, KRYLOV, CFL = 512, 1600.0, 0.1, 20, 8.0
+METRIC = 'time-to-fixed-L2-error ROK4 vs RK4/ESDIRK; Mcell-JVP/s; % HBM peak'
+UNIT = 'Mcell-JVP/s'
+WORKLOAD = 'ns2d-taylor-green-512x512-Re1600-M0.1-rok4-M20-cfl8'
+
+# Algorithmic FP64 operations per cell of one stencil launch, Navier-Stokes on a
+# uniform grid (divisions and square roots counted as one operation each; each
+# face counted once).  Per face: MUSCL 44, Roe averages 42, Roe dissipation and
+# flux 75, viscous flux 34 -> 195; two faces per cell 390; primitives 10; face
+# balance 20; JVP state formation y + eps v 8 and quotient 8.
+FLOPS_RESIDUAL_NS = 390 + 10 + 20
+FLOPS_JVP_NS = FLOPS_RESIDUAL_NS + 8 + 8
+
+
+def _peaks():
+    path = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            return d, 'measured'
+        except Exception:
+            pass
+    return {'hbm_gbs': 6800.0, 'bf16_tflops': 1900.0}, 'fallback'
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+         'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.index), '--query-gpu=' + self.Q,
+                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(',')])
+
+    def stop(self):
+        if self.proc is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace('.', '').isdigit()]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == 'active':
+                        reasons.add(nm)
+        return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': max(mx) if mx else None,
+                'reasons': sorted(reasons), 'samples': len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group('nccl' if dist.is_nccl_available() else 'gloo')
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prob, y0 = W.taylor_green(N_GRID, mach=MACH, reynolds=RE)
+    cells = prob.ncells
+    stream = torch.cuda.current_stream()
+    ctx = rok.rok_init(prob, krylov_max=max(KRYLOV, 30), rounding=rok.ROK_ROUND_FAST, stream=stream)
+    y = rok.state_tensor(y0)
+    h = rok.rok_dt_from_cfl(ctx, y, CFL)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device='cuda')
+
+    fp64_peak = rok.rok_fp64_fma_peak(20) if rank == 0 else None
+
+    for _ in range(args.warmup):
+        rok.rok_step(ctx, y, h, KRYLOV)
+    info = rok.rok_step(ctx, y, h, KRYLOV, info=True)
+    assert info['m_eff'] == KRYLOV
+
+    rok.rok_get_counters(ctx, reset=True)
+    rok.rok_set_stencil_timing(ctx, True)
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))           # evict L2 between timed steps (outside the events)
+        ev[k][0].record(stream)
+        rok.rok_step(ctx, y, h, KRYLOV)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    cnt = rok.rok_get_counters(ctx, reset=True)
+    rok.rok_set_stencil_timing(ctx, False)
+    rok.rok_sync(ctx)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device='cuda')
+    if ws > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_per_step = ms / args.steps
+    jvps_per_step = KRYLOV
+    value = ws * cells * jvps_per_step * args.steps / (ms * 1e-3) / 1e6
+
+    # dominant kernel: the residual / JVP stencil (1 + M + 3 launches per step)
+    n_res, n_jvp = 4, KRYLOV
+    flops_step = cells * (n_res * FLOPS_RESIDUAL_NS + n_jvp * FLOPS_JVP_NS)
+    stencil_ms_per_launch = cnt['stencil_ms'] / max(cnt['stencil_timed'], 1)
+    achieved = flops_step / (n_res + n_jvp) / (stencil_ms_per_launch * 1e-3) / 1e12
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    yh = torch.from_numpy(y0.copy()).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rok.rok_step(ctx, yh, h, KRYLOV)   # host tensor: H2D, step, D2H
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = ws * cells * KRYLOV * e2e_steps / e2e_s / 1e6
+
+    # comparators on the same state: classical RK4 and ESDIRK3 Newton-GMRES(30)
+    yc = rok.state_tensor(y0)
+    h_rk = rok.rok_dt_from_cfl(ctx, yc, 1.0)
+    rok.rk_step(ctx, yc, h_rk)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        rok.rk_step(ctx, yc, h_rk)
+    e1.record(stream)
+    barrier()
+    rk_ms = e0.elapsed_time(e1) / 5
+    yc = rok.state_tensor(y0)
+    barrier()
+    t0 = time.perf_counter()
+    esd = rok.esdirk_step(ctx, yc, h, info=True)
+    barrier()
+    esd_ms = (time.perf_counter() - t0) * 1e3
+
+    if rank != 0:
+        return None
+    peaks, src = _peaks()
+    out = {
+        'metric': METRIC, 'value': round(value, 3), 'unit': UNIT, 'n_gpus': ws, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': round(ms_per_step, 4), 'higher_is_better': True,
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+        'config': {'workload': WORKLOAD, 'cells': cells, 'krylov_m': KRYLOV, 'cfl': CFL, 'dt': h,
+                   'rounding': 'fast (FMA contraction)', 'l2': 'flushed between timed steps (256 MB write)',
+                   'parallelism': 'replicas' if ws > 1 else 'single-gpu'},
+        'roofline': {'bound': 'alu', 'kernel': 'residual/JVP stencil (cart_kernel<NS>)',
+                     'achieved': round(achieved, 4), 'peak': round(fp64_peak, 4), 'unit': 'TFLOP/s',
+                     'frac': round(achieved / fp64_peak, 4), 'traffic': None,
+                     'peak_source': 'measured FP64 FMA microbenchmark (rok_fp64_fma_peak) on this GPU',
+                     'flops_per_cell': {'residual': FLOPS_RESIDUAL_NS, 'jvp': FLOPS_JVP_NS},
+                     'stencil_ms_per_launch': round(stencil_ms_per_launch, 5),
+                     'hbm_frac_of_' + src: round(cells * 96 / (stencil_ms_per_launch * 1e-3) / 1e9 / peaks['hbm_gbs'], 5)},
+        'clocks': clocks,
+        'e2e': {'value': round(e2e_value, 3), 'unit': UNIT, 'h2d_bytes_per_step': int(y0.nbytes),
+                'd2h_bytes_per_step': int(y0.nbytes)},
+        'gpu_launches': int(cnt['launches']),
+        'comparators': {'rk4_ms_per_step_cfl1': round(rk_ms, 4), 'rk4_dt': h_rk,
+                        'esdirk3_ms_per_step_cfl8': round(esd_ms, 2), 'esdirk3_info': esd},
+        'wall_s_timed': round(wall, 3),
+    }
+    if ws == 1:
+        out['cpu_baseline'] = cpu_baseline(prob, y0, h)
+    return out
+
+
+def cpu_baseline(prob, y0, h, steps=1):
+    """The CPU oracle, as it stands, on a bounded sample: `steps` ROK4 steps of the
+    same workload, single-threaded."""
+    from oracle import core
+    from oracle import integrators as I
+    sys_ = core.System(prob)
+    t0 = time.perf_counter()
+    y = y0
+    for _ in range(steps):
+        y = I.rok_step(sys_, y, h, KRYLOV)
+    dt = time.perf_counter() - t0
+    return {'value': round(prob.ncells * KRYLOV * steps / dt / 1e6, 5), 'unit': UNIT, 'cores': 1,
+            'kind': 'oracle', 'sample': '%d ROK4 step(s) of the 512x512 Taylor-Green workload (M=20), %.1f s'
+                                        % (steps, dt)}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return None
+    from paper_1607_06834_gb300 import workloads as W
+    from oracle import core
+    from oracle import integrators as I
+    prob, y0 = W.taylor_green(N_GRID, mach=MACH, reynolds=RE)
+    h = I.dt_from_cfl(prob, y0, CFL)
+    sys_ = core.System(prob)
+    y = y0
+    for _ in range(args.warmup):
+        y = I.rok_step(sys_, y, h, KRYLOV)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y = I.rok_step(sys_, y, h, KRYLOV)
+    dt = time.perf_counter() - t0
+    value = prob.ncells * KRYLOV * args.steps / dt / 1e6
+    return {'impl': 'reference', 'metric': METRIC, 'value': round(value, 5), 'unit': UNIT, 'n_gpus': ws,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': round(dt / args.steps * 1e3, 2),
+            'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': WORKLOAD, 'cells': prob.ncells, 'krylov_m': KRYLOV, 'cfl': CFL},
+            'cpu_baseline': {'value': round(value, 5), 'unit': UNIT, 'cores': 1, 'kind': 'oracle',
+                             'sample': '%d timed ROK4 steps of the same workload' % args.steps},
+            'e2e': {'value': round(value, 5), 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    out = run_reference(args) if args.impl == 'reference' else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == '__main__':
+    main()

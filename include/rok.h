@@ -1,0 +1,177 @@
+/*
+ * rok.h -- C ABI of librok.so: matrix-free Rosenbrock-Krylov (ROK) time
+ * stepping of semi-discrete compressible flow on one GB300 GPU (sm_103a).
+ *
+ * The library integrates the autonomous IVP y' = f(y), y in R^N (Sec. 2,
+ * Eq. ode), where f is the cell-centred finite-volume residual of the 2-D
+ * compressible Euler / Navier-Stokes equations (Sec. 3.2, Eq. Nav_Stokes)
+ * or the Lorenz-96 system (appendix).
+ *
+ * Conventions shared by every entry point
+ *   - State vectors are contiguous float64 arrays of N entries in DEVICE
+ *     memory, structure of arrays y[var][j][i] with var = (rho, rho u,
+ *     rho v, E), i fastest; N = 4 nx ny (Lorenz-96: N = nx).  The caller
+ *     owns every pointer it passes; the library owns all workspace, which
+ *     it allocates in rok_init (sized for desc.krylov_max) and frees in
+ *     rok_destroy -- no step allocates.
+ *   - All work is enqueued on the stream given to rok_init (or
+ *     rok_set_stream) and is asynchronous unless stated otherwise.
+ *   - Calls never abort or trap.  Argument errors are returned at once.
+ *     Errors found on the device (non-finite residuals, a singular stage
+ *     matrix, Newton non-convergence) are latched in the context; they are
+ *     returned by the step call itself when its `info` is non-NULL (that
+ *     call then synchronises the stream), otherwise by the next rok_sync.
+ *     A step that latches an error leaves y unmodified.
+ */
+#ifndef ROK_H
+#define ROK_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rok_ctx rok_ctx; /* opaque, library-owned */
+
+typedef enum {
+    ROK_OK = 0,
+    ROK_ERR_INVALID_ARG = 1,   /* bad pointer, size, enum or option        */
+    ROK_ERR_CUDA = 2,          /* a CUDA runtime call failed               */
+    ROK_ERR_NONFINITE = 3,     /* NaN/Inf in a residual or stage solve     */
+    ROK_ERR_NOT_CONVERGED = 4, /* ESDIRK Newton iteration did not converge */
+    ROK_ERR_TIMEOUT = 5,       /* a bounded device wait expired            */
+    ROK_ERR_UNSUPPORTED = 6,   /* valid request this build does not do     */
+    ROK_ERR_NOMEM = 7          /* workspace allocation failed              */
+} rok_status;
+
+enum { ROK_EULER2D = 0, ROK_NS2D = 1, ROK_LORENZ96 = 2 };
+enum { ROK_BC_PERIODIC = 0, ROK_BC_WALL = 1, ROK_BC_FARFIELD = 2 };
+enum { ROK_JVP_FD = 0, ROK_JVP_EXACT = 1 };
+/* ROK_ROUND_STRICT compiles the stencil without multiply-add contraction, so
+ * f(y) is the IEEE result of the written-out formulas (bitwise reproducible
+ * against a plain CPU evaluation in the same order); ROK_ROUND_FAST lets the
+ * compiler contract into FMA (fewer FP64 instructions, last-bit differences). */
+enum { ROK_ROUND_FAST = 0, ROK_ROUND_STRICT = 1 };
+
+/* Problem description, copied by rok_init (pointers are not retained). */
+typedef struct {
+    int kind;            /* ROK_EULER2D | ROK_NS2D | ROK_LORENZ96                     */
+    int nx, ny;          /* cells (i fastest); Lorenz-96: nx = N, ny = 1              */
+    const double *xv;    /* HOST vertex x, (ny+1)*(nx+1), index j*(nx+1)+i, or NULL    */
+    const double *yv;    /* HOST vertex y; NULL together with xv = uniform box         */
+    double lx, ly;       /* box size when xv == NULL                                  */
+    int bc[4];           /* i-low, i-high, j-low, j-high: ROK_BC_*                    */
+    double gamma;        /* ratio of specific heats                                   */
+    double prandtl;      /* Prandtl number (Navier-Stokes)                            */
+    double mu;           /* viscosity at t_ref (constant when sutherland_s <= 0)      */
+    double t_ref;        /* Sutherland reference temperature (T = p/rho, R = 1)        */
+    double sutherland_s; /* Sutherland S / t_ref; <= 0: constant viscosity            */
+    double q_inf[4];     /* free stream (conservative), far-field ghost state         */
+    double muscl_kappa;  /* kappa of the unlimited MUSCL reconstruction               */
+    double entropy_fix;  /* Harten coefficient: delta = c (|q_n| + a) on acoustic waves */
+    double lorenz_f;     /* Lorenz-96 forcing F                                       */
+    int krylov_max;      /* largest Krylov dimension M / GMRES restart length used    */
+    int rounding;        /* ROK_ROUND_FAST | ROK_ROUND_STRICT                         */
+} rok_problem_desc;
+
+typedef struct {
+    int status;          /* rok_status of the step                                     */
+    int m_eff;           /* Krylov dimension actually built (Arnoldi breakdown lowers it) */
+    int residual_evals;  /* f evaluations, JVPs included                               */
+    int jvps;            /* Jacobian-vector products                                   */
+    int newton_iters;    /* ESDIRK: Newton iterations, all stages                      */
+    int gmres_iters;     /* ESDIRK: GMRES iterations, all Newton steps                 */
+    double eps;          /* finite-difference increment used (Eq. matvecFD)            */
+} rok_step_info;
+
+typedef struct {
+    int gmres_m;         /* restart length (<= krylov_max)                             */
+    double gmres_tol;    /* relative residual tolerance of each linear solve           */
+    int gmres_restarts;  /* restarts after the first cycle                             */
+    double newton_tol;   /* stop when h g ||dk|| <= newton_tol ||stage state||          */
+    int newton_max;      /* Newton iterations per stage                                */
+} esdirk_opts;
+
+/* Create a context for one problem on the current CUDA device.  `cuda_stream`
+ * is a cudaStream_t (NULL = legacy default stream).  Allocates the Krylov
+ * basis ((krylov_max+1) x N float64), stage vectors (8 N) and, for
+ * curvilinear grids, the face metrics.  Errors: INVALID_ARG for inconsistent
+ * descriptions (non-positive sizes, unknown kind/bc, krylov_max < 0 or > 64,
+ * vertex arrays with a uniform-only feature), NOMEM, CUDA. */
+rok_status rok_init(rok_ctx **ctx, const rok_problem_desc *desc, void *cuda_stream);
+
+/* Synchronise and free everything the context owns.  NULL is accepted. */
+rok_status rok_destroy(rok_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+rok_status rok_set_stream(rok_ctx *ctx, void *cuda_stream);
+
+/* f = f(y): the semi-discrete residual (Sec. 3.2, Eq. Nav_Stokes with the
+ * MUSCL/Roe/central-viscous finite-volume scheme; appendix for Lorenz-96).
+ * y, f: device, N float64, must not overlap. */
+rok_status rok_residual(rok_ctx *ctx, const double *y, double *f);
+
+/* jv = J(y) v by the one-sided finite difference of Eq. matvecFD,
+ * (f(y + eps v) - f(y)) / eps.  fy = f(y) if the caller has it, else NULL
+ * (it is then computed).  eps > 0 is used as given (a power of two keeps
+ * the quotient exact); eps <= 0 selects sqrt(2^-52 (1 + ||y||)) / ||v||
+ * rounded to the nearest power of two.  mode: ROK_JVP_FD (ROK_JVP_EXACT
+ * returns UNSUPPORTED in this build).  All arrays device, N float64. */
+rok_status rok_jvp(rok_ctx *ctx, const double *y, const double *fy, const double *v, double *jv,
+                   double eps, int mode);
+
+/* Arnoldi process of Sec. 2.3.3 alone (modified Gram-Schmidt, FD JVPs):
+ * builds V (rows v_1..v_Meff, each N float64, row-major M x N) and
+ * H = V^T J V (M x M, row-major, zero beyond Meff) of K_M(J(y), f(y)).
+ * V, H: device; m_eff: host (this call synchronises).  M <= krylov_max. */
+rok_status rok_arnoldi(rok_ctx *ctx, const double *y, int M, double *V, double *H, int *m_eff);
+
+/* One ROK4 step of size h with Krylov dimension M (Sec. 2.3.3, Eq. ROK),
+ * y in place (device, N float64).  0 <= M <= krylov_max; M = 0 is the
+ * explicit RK limit.  info may be NULL (no synchronisation). */
+rok_status rok_step(rok_ctx *ctx, double *y, double h, int M, rok_step_info *info);
+
+/* One classical RK4 step (Sec. 2.1, Eq. RK), y in place. */
+rok_status rk_step(rok_ctx *ctx, double *y, double h, rok_step_info *info);
+
+/* One ESDIRK3 step (Sec. 2.1, Eqs. Newton, SDIRK_Newton, Newton_Jac_Matrix)
+ * with matrix-free Newton-GMRES, y in place.  opts NULL = (30, 1e-6, 5,
+ * 1e-10, 10).  Host-driven: synchronises the stream every GMRES iteration. */
+rok_status esdirk_step(rok_ctx *ctx, double *y, double h, const esdirk_opts *opts, rok_step_info *info);
+
+/* Time step for a CFL number: dt = cfl / max over cells of
+ * (|u.S_i| + c|S_i|)/Vol + (|u.S_j| + c|S_j|)/Vol + 2 nu_eff (|S_i|^2 + |S_j|^2)/Vol^2
+ * (S_i, S_j mean face-area vectors, nu_eff = max(4/3, gamma/Pr) mu/rho).
+ * dt: host; synchronises. */
+rok_status rok_dt_from_cfl(rok_ctx *ctx, const double *y, double cfl, double *dt);
+
+/* Wait for the stream and return (and clear) the latched device status;
+ * info (nullable) receives the counters of the last step. */
+rok_status rok_sync(rok_ctx *ctx, rok_step_info *info);
+
+/* Capture rok_step in a CUDA graph per (y, M) and replay it (1) or launch
+ * kernel by kernel (0, default). */
+rok_status rok_set_graph(rok_ctx *ctx, int enable);
+
+/* Kernel launch counter (all kernels this context launched) and, when
+ * timing is on, the accumulated device time of the residual/JVP stencil
+ * launches measured with CUDA events on the context stream. */
+typedef struct {
+    long long launches;         /* kernels launched since the last reset        */
+    long long stencil_launches; /* residual / JVP stencil launches              */
+    double stencil_ms;          /* summed event time of timed stencil launches  */
+    long long stencil_timed;    /* number of stencil launches timed             */
+} rok_counters;
+rok_status rok_get_counters(rok_ctx *ctx, rok_counters *c, int reset);
+rok_status rok_set_stencil_timing(rok_ctx *ctx, int enable);
+
+const char *rok_status_string(rok_status s);
+
+/* Measurement utility (no counterpart in the paper): FP64 fused-multiply-add
+ * throughput of the current device in TFLOP/s (2 flops per FMA), from
+ * `repeats` timed launches of independent FMA chains.  Synchronises. */
+rok_status rok_fp64_fma_peak(double *tflops, int repeats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROK_H */

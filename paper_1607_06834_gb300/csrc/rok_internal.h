@@ -1,0 +1,79 @@
+// Internal declarations of librok: parameter blocks shared by the host
+// drivers and the kernels, launch helpers, status codes on the device.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "rok.h"
+
+namespace rok {
+
+constexpr int kMaxKrylov = 64;   // largest Krylov dimension / GMRES restart length
+constexpr int kMaxAdd = 3;       // vectors added to the base state in one stencil load
+
+// device status word bits (latched; read by rok_sync / info)
+enum : int {
+    kStatusNonfinite = 1,
+    kStatusSingular = 2,
+};
+
+// Constants of the finite-volume residual (Sec. 3.2).  Every derived constant is
+// computed on the host by the same expression the plain CPU evaluation uses, so the
+// strict-rounding stencil reproduces it bit for bit.
+struct StencilConsts {
+    int nx, ny;
+    int bc[4];
+    int viscous, sutherland;
+    double gm1, inv_gm1;       // gamma - 1, 1 / (gamma - 1)
+    double c_lo, c_hi;         // 0.25 (1 - kappa), 0.25 (1 + kappa)
+    double efix;               // Harten coefficient
+    double kfac, c23;          // gamma / ((gamma - 1) Pr), 2 / 3
+    double g_over_pr;          // gamma / Pr (viscous time-step bound)
+    double mu, inv_tref, suth_s;
+    double rdx, rdy, q_rdx, q_rdy;  // 1/dx, 1/dy, 0.25/dx, 0.25/dy (uniform grids)
+    double prim_inf[6];        // rho, u, v, p, T, mu of the free stream
+    double lorenz_f;
+};
+
+// Face metrics of a curvilinear grid (device arrays).
+struct CurvGeom {
+    // i-faces: (nx+1) * ny, index j*(nx+1)+i ; j-faces: nx * (ny+1), index j*nx+i
+    const double *in_x, *in_y, *il, *ic0, *ic1, *ic2, *ic3;
+    const double *jn_x, *jn_y, *jl, *jc0, *jc1, *jc2, *jc3;
+    const double *inv_vol;     // nx * ny
+};
+
+// Inputs and epilogue of one stencil launch:
+//   state = base + sum_t c_t add_t                (c_t from coef or *coef_dev)
+//   t     = (sub ? r - sub : r) * s1              (s1 times *s1_dev if given)
+//   out   = add_out ? add_out + s2 t : t          (s2 times *s2_dev if given)
+struct StencilIO {
+    const double *base;
+    const double *add[kMaxAdd];
+    double coef[kMaxAdd];
+    const double *coef_dev[kMaxAdd];
+    int nadd;
+    const double *sub;
+    double s1;
+    const double *s1_dev;
+    const double *add_out;
+    double s2;
+    const double *s2_dev;
+    double *out;
+    int *status;
+    const int *active;         // nullable device flag: 0 = skip the launch's work
+};
+
+// stencil launchers, one set per rounding mode (separate translation units)
+namespace fast {
+cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_t s);
+cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s);
+}
+namespace strict {
+cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_t s);
+cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s);
+}
+cudaError_t launch_lorenz(const StencilConsts &c, const StencilIO &io, int n, cudaStream_t s);
+
+}  // namespace rok

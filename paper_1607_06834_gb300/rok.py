@@ -1,0 +1,272 @@
+"""Thin ctypes binding of ``librok.so`` (C ABI in ``include/rok.h``).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name with raw device pointers and sizes; all arithmetic runs in the
+library's CUDA kernels.  State tensors are float64 CUDA tensors of shape
+``problem.shape`` (contiguous).  CPU tensors are accepted by the step calls
+for end-to-end use: they are copied to a device buffer, stepped and copied
+back (host<->device copies, nothing else, on the host side).
+
+Importing this module loads the library and raises if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import workloads as _W
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), '_lib', 'librok.so')
+if not os.path.exists(_LIB_PATH):
+    raise ImportError('librok.so is not built (%s); run __graft_entry__.build()' % _LIB_PATH)
+_lib = ctypes.CDLL(_LIB_PATH)
+
+ROK_OK, ROK_ERR_INVALID_ARG, ROK_ERR_CUDA, ROK_ERR_NONFINITE = 0, 1, 2, 3
+ROK_ERR_NOT_CONVERGED, ROK_ERR_TIMEOUT, ROK_ERR_UNSUPPORTED, ROK_ERR_NOMEM = 4, 5, 6, 7
+ROK_JVP_FD, ROK_JVP_EXACT = 0, 1
+ROK_ROUND_FAST, ROK_ROUND_STRICT = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [
+        ('kind', ctypes.c_int), ('nx', ctypes.c_int), ('ny', ctypes.c_int),
+        ('xv', _dp), ('yv', _dp), ('lx', ctypes.c_double), ('ly', ctypes.c_double),
+        ('bc', ctypes.c_int * 4),
+        ('gamma', ctypes.c_double), ('prandtl', ctypes.c_double), ('mu', ctypes.c_double),
+        ('t_ref', ctypes.c_double), ('sutherland_s', ctypes.c_double),
+        ('q_inf', ctypes.c_double * 4),
+        ('muscl_kappa', ctypes.c_double), ('entropy_fix', ctypes.c_double), ('lorenz_f', ctypes.c_double),
+        ('krylov_max', ctypes.c_int), ('rounding', ctypes.c_int),
+    ]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [('status', ctypes.c_int), ('m_eff', ctypes.c_int), ('residual_evals', ctypes.c_int),
+                ('jvps', ctypes.c_int), ('newton_iters', ctypes.c_int), ('gmres_iters', ctypes.c_int),
+                ('eps', ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EsdirkOpts(ctypes.Structure):
+    _fields_ = [('gmres_m', ctypes.c_int), ('gmres_tol', ctypes.c_double), ('gmres_restarts', ctypes.c_int),
+                ('newton_tol', ctypes.c_double), ('newton_max', ctypes.c_int)]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [('launches', ctypes.c_longlong), ('stencil_launches', ctypes.c_longlong),
+                ('stencil_ms', ctypes.c_double), ('stencil_timed', ctypes.c_longlong)]
+
+
+_vp = ctypes.c_void_p
+_sig = {
+    'rok_init': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ProblemDesc), _vp]),
+    'rok_destroy': (ctypes.c_int, [_vp]),
+    'rok_set_stream': (ctypes.c_int, [_vp, _vp]),
+    'rok_residual': (ctypes.c_int, [_vp, _vp, _vp]),
+    'rok_jvp': (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int]),
+    'rok_arnoldi': (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    'rok_step': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(StepInfo)]),
+    'rk_step': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(StepInfo)]),
+    'esdirk_step': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(EsdirkOpts), ctypes.POINTER(StepInfo)]),
+    'rok_dt_from_cfl': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    'rok_sync': (ctypes.c_int, [_vp, ctypes.POINTER(StepInfo)]),
+    'rok_set_graph': (ctypes.c_int, [_vp, ctypes.c_int]),
+    'rok_get_counters': (ctypes.c_int, [_vp, ctypes.POINTER(Counters), ctypes.c_int]),
+    'rok_set_stencil_timing': (ctypes.c_int, [_vp, ctypes.c_int]),
+    'rok_status_string': (ctypes.c_char_p, [ctypes.c_int]),
+    'rok_fp64_fma_peak': (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class RokError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__('%s: %s (status %d)' % (where, rok_status_string(status), status))
+
+
+def rok_status_string(status):
+    return _lib.rok_status_string(int(status)).decode()
+
+
+def _check(status, where):
+    if status != ROK_OK:
+        raise RokError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous() or t.dtype != torch.float64:
+        raise ValueError('expected a contiguous float64 tensor')
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns one ``rok_ctx``; created by :func:`rok_init`."""
+
+    def __init__(self, handle, problem, stream):
+        self.handle = handle
+        self.problem = problem
+        self.stream = stream
+        self._stage = None
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.rok_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def _dev_state(self, y):
+        """Device view of a state; CPU tensors are staged through a device buffer."""
+        if y.is_cuda:
+            return y, None
+        if self._stage is None or self._stage.shape != y.shape:
+            self._stage = torch.empty(y.shape, dtype=torch.float64, device='cuda')
+        self._stage.copy_(y, non_blocking=True)
+        return self._stage, y
+
+
+def _desc(problem, krylov_max, rounding):
+    d = ProblemDesc()
+    d.kind = int(problem.kind)
+    d.nx, d.ny = int(problem.nx), int(problem.ny)
+    keep = []
+    if problem.xv is not None:
+        xv = np.ascontiguousarray(problem.xv, dtype=np.float64)
+        yv = np.ascontiguousarray(problem.yv, dtype=np.float64)
+        keep = [xv, yv]
+        d.xv = xv.ctypes.data_as(_dp)
+        d.yv = yv.ctypes.data_as(_dp)
+    d.lx, d.ly = float(problem.lx), float(problem.ly)
+    for k in range(4):
+        d.bc[k] = int(problem.bc[k])
+        d.q_inf[k] = float(problem.q_inf[k])
+    d.gamma, d.prandtl, d.mu = float(problem.gamma), float(problem.prandtl), float(problem.mu)
+    d.t_ref, d.sutherland_s = float(problem.t_ref), float(problem.sutherland_s)
+    d.muscl_kappa, d.entropy_fix, d.lorenz_f = float(problem.muscl_kappa), float(problem.entropy_fix), float(problem.lorenz_f)
+    d.krylov_max = int(krylov_max)
+    d.rounding = int(rounding)
+    return d, keep
+
+
+def rok_init(problem, krylov_max=20, rounding=ROK_ROUND_FAST, stream=None):
+    """Create a context (``rok_init``) for a :class:`workloads.FlowProblem`."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    d, keep = _desc(problem, krylov_max, rounding)
+    h = ctypes.c_void_p()
+    _check(_lib.rok_init(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream)), 'rok_init')
+    del keep
+    return Context(h, problem, stream)
+
+
+def rok_destroy(ctx):
+    _check(_lib.rok_destroy(ctx.handle), 'rok_destroy')
+    ctx.handle = None
+
+
+def rok_set_stream(ctx, stream):
+    ctx.stream = stream
+    _check(_lib.rok_set_stream(ctx.handle, ctypes.c_void_p(stream.cuda_stream)), 'rok_set_stream')
+
+
+def rok_residual(ctx, y, f=None):
+    if f is None:
+        f = torch.empty_like(y)
+    _check(_lib.rok_residual(ctx.handle, _ptr(y), _ptr(f)), 'rok_residual')
+    return f
+
+
+def rok_jvp(ctx, y, v, fy=None, eps=0.0, mode=ROK_JVP_FD, out=None):
+    if out is None:
+        out = torch.empty_like(y)
+    _check(_lib.rok_jvp(ctx.handle, _ptr(y), _ptr(fy), _ptr(v), _ptr(out), float(eps), int(mode)), 'rok_jvp')
+    return out
+
+
+def rok_arnoldi(ctx, y, M):
+    """Returns (V[M_eff, N], H[M, M], M_eff)."""
+    N = y.numel()
+    V = torch.zeros((M, N), dtype=torch.float64, device=y.device)
+    H = torch.zeros((M, M), dtype=torch.float64, device=y.device)
+    me = ctypes.c_int(0)
+    _check(_lib.rok_arnoldi(ctx.handle, _ptr(y), int(M), _ptr(V), _ptr(H), ctypes.byref(me)), 'rok_arnoldi')
+    return V[:me.value], H, me.value
+
+
+def _step_call(ctx, y, where, call, info):
+    yd, host = ctx._dev_state(y)
+    si = StepInfo()
+    st = call(yd, ctypes.byref(si) if (info or host is not None) else None)
+    if host is not None:
+        host.copy_(yd, non_blocking=False)
+    _check(st, where)
+    return si.as_dict() if info else None
+
+
+def rok_step(ctx, y, h, M, info=False):
+    """One ROK4 step in place (``rok_step``); returns the step info dict when info=True."""
+    return _step_call(ctx, y, 'rok_step', lambda yd, ip: _lib.rok_step(ctx.handle, _ptr(yd), float(h), int(M), ip), info)
+
+
+def rk_step(ctx, y, h, info=False):
+    return _step_call(ctx, y, 'rk_step', lambda yd, ip: _lib.rk_step(ctx.handle, _ptr(yd), float(h), ip), info)
+
+
+def esdirk_step(ctx, y, h, gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, newton_tol=1e-10, newton_max=10, info=False):
+    o = EsdirkOpts(int(gmres_m), float(gmres_tol), int(gmres_restarts), float(newton_tol), int(newton_max))
+    return _step_call(ctx, y, 'esdirk_step',
+                      lambda yd, ip: _lib.esdirk_step(ctx.handle, _ptr(yd), float(h), ctypes.byref(o), ip), info)
+
+
+def rok_dt_from_cfl(ctx, y, cfl):
+    dt = ctypes.c_double(0.0)
+    _check(_lib.rok_dt_from_cfl(ctx.handle, _ptr(y), float(cfl), ctypes.byref(dt)), 'rok_dt_from_cfl')
+    return dt.value
+
+
+def rok_sync(ctx):
+    si = StepInfo()
+    _check(_lib.rok_sync(ctx.handle, ctypes.byref(si)), 'rok_sync')
+    return si.as_dict()
+
+
+def rok_set_graph(ctx, enable):
+    _check(_lib.rok_set_graph(ctx.handle, int(bool(enable))), 'rok_set_graph')
+
+
+def rok_get_counters(ctx, reset=False):
+    c = Counters()
+    _check(_lib.rok_get_counters(ctx.handle, ctypes.byref(c), int(bool(reset))), 'rok_get_counters')
+    return {k: getattr(c, k) for k, _ in c._fields_}
+
+
+def rok_set_stencil_timing(ctx, enable):
+    _check(_lib.rok_set_stencil_timing(ctx.handle, int(bool(enable))), 'rok_set_stencil_timing')
+
+
+def rok_fp64_fma_peak(repeats=20):
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double(0.0)
+    _check(_lib.rok_fp64_fma_peak(ctypes.byref(t), int(repeats)), 'rok_fp64_fma_peak')
+    return t.value
+
+
+def state_tensor(y, device='cuda'):
+    """float64 tensor of a NumPy state on the device (helper for callers)."""
+    return torch.from_numpy(np.ascontiguousarray(y, dtype=np.float64)).to(device)

@@ -1,0 +1,220 @@
+"""GPU parity of the Arnoldi process (Sec. 2.3.3), the ROK4 step (Eq. ROK), RK4
+(Eq. RK), ESDIRK3 Newton-GMRES and the CFL time step against the CPU oracle,
+through the C ABI.
+
+Tolerances: 10 ROK4 steps agree to 1e-9 relative L2 (plain FP64 path); the
+Arnoldi basis and Hessenberg matrix to 1e-9 (they see FD-JVP rounding only
+through the dot-product order); RK4 to 1e-13; ESDIRK3 to the Newton/GMRES
+tolerances it is solved to (1e-10 Newton, 1e-6 GMRES -> 1e-8 on y)."""
+import numpy as np
+import pytest
+
+from oracle import core
+from oracle import integrators as I
+from paper_1607_06834_gb300 import workloads as W
+from tests.gpu_common import dev, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module')
+def rok():
+    from paper_1607_06834_gb300 import rok as r
+    return r
+
+
+@pytest.mark.parametrize('mode', ['strict', 'fast'])
+def test_arnoldi_matches_oracle(rok, mode):
+    prob, y = W.isentropic_vortex(48)
+    ctx = rok.rok_init(prob, krylov_max=12, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+    V, H, me = rok.rok_arnoldi(ctx, dev(y), 12)
+    sys_ = core.System(prob)
+    Vo, Ho, meo = I.arnoldi(sys_, y, core.residual(prob, y), 12, I.fd_eps(np.linalg.norm(y)))
+    assert me == meo == 12
+    V, H = host(V), host(H)
+    assert np.abs(H - Ho).max() <= 1e-9 * np.abs(Ho).max()
+    assert np.abs(V - Vo).max() <= 1e-9
+    assert np.abs(V @ V.T - np.eye(12)).max() <= 1e-12 * 12
+
+
+def test_arnoldi_full_size_properties(rok):
+    # 512^2 Taylor-Green, M = 20: orthonormal basis, Hessenberg structure, first
+    # vector = f/||f||, and H_ij = v_i . (J v_j) on sampled columns
+    prob, y = W.taylor_green(512, reynolds=1600.0)
+    ctx = rok.rok_init(prob, krylov_max=20)
+    yd = dev(y)
+    V, H, me = rok.rok_arnoldi(ctx, yd, 20)
+    assert me == 20
+    G = (V @ V.T).cpu().numpy()
+    assert np.abs(G - np.eye(20)).max() <= 1e-12 * 20
+    Hh = host(H)
+    assert np.all(np.tril(Hh, -2) == 0.0) and np.all(np.diag(Hh, -1) > 0)
+    f = rok.rok_residual(ctx, yd)
+    assert float((V[0] - f.ravel() / f.norm()).abs().max()) <= 1e-14
+    eps = I.fd_eps(float(np.linalg.norm(y)))
+    for j in (0, 7, 19):
+        w = rok.rok_jvp(ctx, yd, V[j].reshape(y.shape).contiguous(), fy=f, eps=eps)
+        col = (V @ w.ravel()).cpu().numpy()
+        assert np.abs(col[:j + 2 if j + 2 <= 20 else 20] - Hh[:min(j + 2, 20), j]).max() <= 1e-9 * np.abs(Hh).max()
+
+
+@pytest.mark.parametrize('mode', ['strict', 'fast'])
+def test_rok_ten_steps_vortex(rok, mode):
+    prob, y0 = W.isentropic_vortex(64)
+    M = 12
+    ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+    h = I.dt_from_cfl(prob, y0, 5.0)
+    y = dev(y0)
+    yo = y0.copy()
+    sys_ = core.System(prob)
+    for _ in range(10):
+        info = rok.rok_step(ctx, y, h, M, info=True)
+        assert info['m_eff'] == M
+        yo = I.rok_step(sys_, yo, h, M)
+    assert rel_l2(host(y), yo) <= 1e-9
+
+
+def test_rok_ns_and_ogrid_steps(rok):
+    prob, y0 = W.taylor_green(64, reynolds=200.0)
+    ctx = rok.rok_init(prob, krylov_max=8)
+    h = I.dt_from_cfl(prob, y0, 8.0)
+    y, yo = dev(y0), y0.copy()
+    for _ in range(3):
+        rok.rok_step(ctx, y, h, 8)
+        yo = I.rok_step(core.System(prob), yo, h, 8)
+    assert rel_l2(host(y), yo) <= 1e-9
+    p4, y4, _ = W.cylinder_ogrid(32, 64)
+    ctx = rok.rok_init(p4, krylov_max=10, rounding=rok.ROK_ROUND_STRICT)
+    h = I.dt_from_cfl(p4, y4, 50.0)
+    y, yo = dev(y4), y4.copy()
+    for _ in range(2):
+        rok.rok_step(ctx, y, h, 10)
+        yo = I.rok_step(core.System(p4), yo, h, 10)
+    assert rel_l2(host(y), yo) <= 1e-9
+
+
+def test_rok_full_size_one_step(rok):
+    # the benchmark workload: 512^2 Navier-Stokes Taylor-Green, ROK4, M = 20, CFL 8
+    prob, y0 = W.taylor_green(512, reynolds=1600.0)
+    ctx = rok.rok_init(prob, krylov_max=20)
+    h = I.dt_from_cfl(prob, y0, 8.0)
+    y = dev(y0)
+    rok.rok_step(ctx, y, h, 20)
+    yo = I.rok_step(core.System(prob), y0, h, 20)
+    d = host(y) - yo
+    assert np.linalg.norm(d) <= 1e-9 * np.linalg.norm(yo - y0)   # relative to the update itself
+    assert rel_l2(host(y), yo) <= 1e-12
+
+
+def test_rok_M0_is_rk4_and_free_stream(rok):
+    prob, y0 = W.isentropic_vortex(32)
+    ctx = rok.rok_init(prob, krylov_max=4)
+    h = I.dt_from_cfl(prob, y0, 0.8)
+    y = dev(y0)
+    rok.rok_step(ctx, y, h, 0)
+    y2 = dev(y0)
+    rok.rk_step(ctx, y2, h)
+    assert rel_l2(host(y), host(y2)) <= 1e-14
+    assert rel_l2(host(y2), I.rk_step(core.System(prob), y0, h)) <= 1e-13
+    yfs = np.empty_like(y0)
+    for k in range(4):
+        yfs[k] = prob.q_inf[k]
+    yd = dev(yfs)
+    info = rok.rok_step(ctx, yd, h, 4, info=True)
+    assert info['m_eff'] == 0 and np.array_equal(host(yd), yfs)
+
+
+def test_rok_conservation_and_graph_replay(rok):
+    prob, y0 = W.isentropic_vortex(64)
+    ctx = rok.rok_init(prob, krylov_max=12)
+    h = I.dt_from_cfl(prob, y0, 5.0)
+    y = dev(y0)
+    for _ in range(3):
+        rok.rok_step(ctx, y, h, 12)
+    yh = host(y)
+    for k in range(4):
+        assert abs(yh[k].sum() - y0[k].sum()) <= 1e-12 * np.abs(y0[k]).sum()
+    ctx2 = rok.rok_init(prob, krylov_max=12)
+    rok.rok_set_graph(ctx2, True)
+    yg = dev(y0)
+    for _ in range(3):
+        rok.rok_step(ctx2, yg, h, 12)
+    assert np.array_equal(host(yg), yh)
+
+
+def test_rok_lorenz96_order(rok):
+    # Lorenz-96 appendix problem on the GPU: observed order ~4 with M = 6
+    from scipy.integrate import solve_ivp
+    prob, _ = W.lorenz96(40)
+    y0 = 8.0 * np.ones(40)
+    y0[19] += 0.01
+    y0 = solve_ivp(lambda t, u: core.lorenz96_rhs(prob, u), (0, 3), y0, rtol=1e-12, atol=1e-12,
+                   method='DOP853').y[:, -1]
+    T = 0.3
+    ref = solve_ivp(lambda t, u: core.lorenz96_rhs(prob, u), (0, T), y0, rtol=1e-13, atol=1e-13,
+                    method='DOP853').y[:, -1]
+    ctx = rok.rok_init(prob, krylov_max=6)
+    errs = []
+    for n in (16, 32, 64):
+        y = dev(y0)
+        for _ in range(n):
+            rok.rok_step(ctx, y, T / n, 6)
+        errs.append(np.linalg.norm(host(y) - ref))
+    slope = np.log2(errs[1] / errs[2])
+    assert 3.6 < slope < 4.4, errs
+
+
+def test_nan_leaves_state_unmodified(rok):
+    prob, y0 = W.isentropic_vortex(32)
+    y0 = y0.copy()
+    y0[3, 10, 10] = np.inf
+    ctx = rok.rok_init(prob, krylov_max=4)
+    yd = dev(y0)
+    with pytest.raises(rok.RokError) as e:
+        rok.rok_step(ctx, yd, 0.01, 4, info=True)
+    assert e.value.status == rok.ROK_ERR_NONFINITE
+    assert np.array_equal(host(yd), y0)
+
+
+def test_invalid_arguments(rok):
+    prob, y0 = W.isentropic_vortex(16)
+    ctx = rok.rok_init(prob, krylov_max=4)
+    with pytest.raises(rok.RokError) as e:
+        rok.rok_step(ctx, dev(y0), 0.01, 5)
+    assert e.value.status == rok.ROK_ERR_INVALID_ARG
+    with pytest.raises(rok.RokError):
+        rok.rok_step(ctx, dev(y0), -1.0, 2)
+    bad = W.FlowProblem(**{**prob.__dict__, 'nx': 0})
+    with pytest.raises(rok.RokError):
+        rok.rok_init(bad)
+
+
+def test_rk4_and_dt(rok):
+    prob, y0 = W.taylor_green(40, reynolds=300.0)
+    ctx = rok.rok_init(prob, krylov_max=4)
+    yd = dev(y0)
+    dt = rok.rok_dt_from_cfl(ctx, yd, 1.0)
+    assert abs(dt - I.dt_from_cfl(prob, y0, 1.0)) <= 1e-12 * dt
+    rok.rk_step(ctx, yd, dt)
+    assert rel_l2(host(yd), I.rk_step(core.System(prob), y0, dt)) <= 1e-13
+    p4, y4, _ = W.cylinder_ogrid(24, 48)
+    ctx = rok.rok_init(p4, krylov_max=4)
+    dt = rok.rok_dt_from_cfl(ctx, dev(y4), 1.0)
+    assert abs(dt - I.dt_from_cfl(p4, y4, 1.0)) <= 1e-12 * dt
+
+
+@pytest.mark.parametrize('case', ['vortex', 'tgv'])
+def test_esdirk_step(rok, case):
+    if case == 'vortex':
+        prob, y0 = W.isentropic_vortex(32)
+        h = I.dt_from_cfl(prob, y0, 4.0)
+    else:
+        prob, y0 = W.taylor_green(32, reynolds=200.0)
+        h = I.dt_from_cfl(prob, y0, 6.0)
+    ctx = rok.rok_init(prob, krylov_max=30)
+    y = dev(y0)
+    info = rok.esdirk_step(ctx, y, h, info=True)
+    oi = {}
+    yo = I.esdirk_step(core.System(prob), y0, h, info=oi)
+    assert oi['converged'] and info['newton_iters'] >= 3
+    assert rel_l2(host(y), yo) <= 1e-8
