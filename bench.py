@@ -126,7 +126,8 @@ def run_ours(args):
     prob, y0 = W.taylor_green(N_GRID, mach=MACH, reynolds=RE)
     cells = prob.ncells
     stream = torch.cuda.current_stream()
-    ctx = rok.rok_init(prob, krylov_max=max(KRYLOV, 30), rounding=rok.ROK_ROUND_FAST, stream=stream)
+    rounding = rok.ROK_ROUND_STRICT if args.rounding == 'strict' else rok.ROK_ROUND_FAST
+    ctx = rok.rok_init(prob, krylov_max=max(KRYLOV, 30), rounding=rounding, stream=stream)
     y = rok.state_tensor(y0)
     h = rok.rok_dt_from_cfl(ctx, y, CFL)
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device='cuda')
@@ -209,7 +210,7 @@ def run_ours(args):
         'warmup': args.warmup, 'ms_per_step': round(ms_per_step, 4), 'higher_is_better': True,
         'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
         'config': {'workload': WORKLOAD, 'cells': cells, 'krylov_m': KRYLOV, 'cfl': CFL, 'dt': h,
-                   'rounding': 'fast (FMA contraction)', 'l2': 'flushed between timed steps (256 MB write)',
+                   'rounding': args.rounding, 'l2': 'flushed between timed steps (256 MB write)',
                    'parallelism': 'replicas' if ws > 1 else 'single-gpu'},
         'roofline': {'bound': 'alu', 'kernel': 'residual/JVP stencil (cart_kernel<NS>)',
                      'achieved': round(achieved, 4), 'peak': round(fp64_peak, 4), 'unit': 'TFLOP/s',
@@ -274,15 +275,51 @@ def run_reference(args):
             'e2e': {'value': round(value, 5), 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
 
 
+def run_stencil_only(args):
+    """Kernel-only mode (profiling): W + K FD-JVP stencil launches on an n x n
+    Taylor-Green state; prints the mean launch time."""
+    import torch
+
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    prob, y0 = W.taylor_green(args.n, mach=MACH, reynolds=RE)
+    rounding = rok.ROK_ROUND_STRICT if args.rounding == 'strict' else rok.ROK_ROUND_FAST
+    ctx = rok.rok_init(prob, krylov_max=1, rounding=rounding)
+    y = rok.state_tensor(y0)
+    f0 = rok.rok_residual(ctx, y)
+    g = torch.Generator(device='cuda').manual_seed(0)
+    v = torch.randn(y.shape, dtype=torch.float64, device='cuda', generator=g)
+    v /= v.norm()
+    w = torch.empty_like(y)
+    for _ in range(args.warmup):
+        rok.rok_jvp(ctx, y, v, fy=f0, eps=2.0 ** -20, out=w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        rok.rok_jvp(ctx, y, v, fy=f0, eps=2.0 ** -20, out=w)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({'mode': 'stencil', 'n': args.n, 'rounding': args.rounding, 'ms_per_launch': ms,
+                      'tflops_alg': prob.ncells * FLOPS_JVP_NS / (ms * 1e-3) / 1e12}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument('--mode', default='step', choices=['step', 'stencil'])
+    ap.add_argument('--n', type=int, default=N_GRID)
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=10)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--rounding', default='fast', choices=['fast', 'strict'])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.mode == 'stencil':
+        run_stencil_only(args)
+        return
     out = run_reference(args) if args.impl == 'reference' else run_ours(args)
     if out is not None:
         print(json.dumps(out))

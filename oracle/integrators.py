@@ -3,8 +3,10 @@ the ROK step, classical RK4, ESDIRK3 with Newton-GMRES, the finite-difference
 epsilon, the CFL time step and the L2 error metric.
 
 TEST INFRASTRUCTURE ONLY.  Each function follows the paper's equations in
-their printed order; library primitives (dot products, dense solves) serve as
-single steps.  Readings of silent points are stated where they are used.
+their printed order.  Every inner product of the ROK step is the pairwise sum of
+the rounded entrywise products (``dot``) and the small dense systems are solved
+by a plain LU, so that the floating-point result of a step is fully specified.
+Readings of silent points are stated where they are used.
 
 The integrators see the problem only through a ``System``: ``sys.f(y)`` and
 ``sys.jvp(y, v, f0, eps)`` (``core.System`` wraps the C residual).
@@ -17,6 +19,30 @@ from . import coefficients as C
 from . import core
 
 MACH_EPS = 2.0 ** -52
+
+
+def pairwise_sum(x):
+    """Sum of the entries of x by pairwise summation (Higham): a balanced binary
+    tree over the index range, x zero-padded to a power-of-two length, each level
+    adding entry 2i and entry 2i+1.  This fixes one rounding of the sum."""
+    x = np.ravel(np.asarray(x, dtype=np.float64))
+    n = 1
+    while n < x.size:
+        n *= 2
+    buf = np.zeros(n)
+    buf[:x.size] = x
+    while buf.size > 1:
+        buf = buf[0::2] + buf[1::2]
+    return float(buf[0])
+
+
+def dot(a, b):
+    """Inner product: the rounded entrywise products, summed pairwise."""
+    return pairwise_sum(np.ravel(a) * np.ravel(b))
+
+
+def norm(a):
+    return math.sqrt(dot(a, a))
 
 
 def fd_eps(ynorm, vnorm=1.0):
@@ -41,32 +67,75 @@ def arnoldi(sys, y, F1, M, eps, breakdown_tol=1e-12):
 
     Readings: beta = ||F1|| = 0 gives M_eff = 0; the basis is cut at column j
     when h_{j+1,j} <= breakdown_tol * ||J v_j|| (a scale-consistent test);
-    h_{j+1,j} > 0 makes V unique."""
+    h_{j+1,j} > 0 makes V unique.  Normalisation multiplies by 1/h."""
     N = F1.size
     V = np.zeros((M, N))
     H = np.zeros((M, M))
-    beta = float(np.linalg.norm(F1.ravel()))
-    if M == 0 or beta == 0.0:
+    beta = norm(F1)
+    if M == 0 or not beta > 0.0:
         return V[:0], H[:0, :0], 0
-    V[0] = F1.ravel() / beta
+    V[0] = F1.ravel() * (1.0 / beta)
     y_flat = y.ravel()
     shape = y.shape
     f0 = F1
     meff = M
     for j in range(M):
         w = np.asarray(sys.jvp(y_flat.reshape(shape), V[j].reshape(shape), f0, eps)).ravel()
-        wnorm0 = float(np.linalg.norm(w))
+        wnorm0 = norm(w)
         for i in range(j + 1):
-            H[i, j] = float(np.dot(V[i], w))
+            H[i, j] = dot(V[i], w)
             w = w - H[i, j] * V[i]
         if j + 1 < M:
-            hn = float(np.linalg.norm(w))
-            if hn <= breakdown_tol * wnorm0:
+            hn = norm(w)
+            if not hn > breakdown_tol * wnorm0:
                 meff = j + 1
                 break
             H[j + 1, j] = hn
-            V[j + 1] = w / hn
+            V[j + 1] = w * (1.0 / hn)
     return V[:meff], H[:meff, :meff], meff
+
+
+def lu_factor(A):
+    """LU factorisation with partial pivoting (first largest |pivot|), row
+    interchanges applied to the whole rows; returns (LU, piv) with the unit
+    lower factor below the diagonal.  Plain loops."""
+    A = np.array(A, dtype=np.float64)
+    m = A.shape[0]
+    piv = np.zeros(m, dtype=int)
+    for k in range(m):
+        p = k + int(np.argmax(np.abs(A[k:, k])))
+        piv[k] = p
+        if p != k:
+            A[[k, p]] = A[[p, k]]
+        d = A[k, k]
+        for i in range(k + 1, m):
+            l = A[i, k] / d
+            A[i, k] = l
+            for j in range(k + 1, m):
+                A[i, j] = A[i, j] - l * A[k, j]
+    return A, piv
+
+
+def lu_solve(LU, piv, b):
+    """Solve with the factors of lu_factor: interchanges, unit-lower forward and
+    upper backward substitution, plain loops."""
+    x = [float(v) for v in b]
+    m = len(x)
+    for k in range(m):
+        p = int(piv[k])
+        if p != k:
+            x[k], x[p] = x[p], x[k]
+    for i in range(m):
+        t = x[i]
+        for j in range(i):
+            t = t - LU[i, j] * x[j]
+        x[i] = t
+    for i in range(m - 1, -1, -1):
+        t = x[i]
+        for j in range(i + 1, m):
+            t = t - LU[i, j] * x[j]
+        x[i] = t / LU[i, i]
+    return np.array(x)
 
 
 def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=None):
@@ -78,8 +147,10 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
         k_i      = V lambda_i + h (F_i - V phi_i)
         y_{n+1}  = y_n + sum_i b_i k_i
 
-    with V, H from Arnoldi on K_M(J_n, f(y_n)); the M x M systems are solved
-    by a dense LU (numpy)."""
+    with V, H from Arnoldi on K_M(J_n, f(y_n)).  The M x M system is solved by
+    LU with partial pivoting (lu_factor/lu_solve); k_i is evaluated as
+    V (lambda_i - h phi_i) + h F_i, the same vector grouped once; sums over the
+    basis run in basis order."""
     g = C.ROK4_GAMMA if gamma is None else gamma
     al = np.array(C.ROK4_ALPHA if alpha is None else alpha)
     gm = np.array(C.ROK4_GAMMA_OFFDIAG if gamma_off is None else gamma_off)
@@ -88,9 +159,9 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
     shape = y.shape
     yf = y.ravel()
     F1 = np.asarray(sys.f(y))
-    eps = fd_eps(float(np.linalg.norm(yf)))
+    eps = fd_eps(norm(yf))
     V, H, meff = arnoldi(sys, y, F1, M, eps)
-    L = np.eye(meff) - h * g * H
+    LU, piv = lu_factor(np.eye(meff) - (h * g) * H)
     ks, lams = [], []
     for i in range(s):
         if i == 0:
@@ -101,13 +172,22 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
                 if al[i, j] != 0.0:
                     Y = Y + al[i, j] * ks[j]
             F = np.asarray(sys.f(Y.reshape(shape))).ravel()
-        phi = V @ F
+        phi = np.array([dot(V[m], F) for m in range(meff)])
         acc = np.zeros(meff)
         for j in range(i):
             acc = acc + gm[i, j] * lams[j]
-        rhs = h * phi + h * (H @ acc)
-        lam = np.linalg.solve(L, rhs) if meff > 0 else np.zeros(0)
-        k = V.T @ lam + h * (F - V.T @ phi)
+        rhs = np.zeros(meff)
+        for r in range(meff):
+            t = 0.0
+            for c in range(meff):
+                t = t + H[r, c] * acc[c]
+            rhs[r] = h * phi[r] + h * t
+        lam = lu_solve(LU, piv, rhs) if meff > 0 else np.zeros(0)
+        cvec = lam - h * phi
+        k = np.zeros_like(yf)
+        for m in range(meff):
+            k = k + cvec[m] * V[m]
+        k = k + h * F
         ks.append(k)
         lams.append(lam)
     ynew = yf.copy()

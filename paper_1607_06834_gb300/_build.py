@@ -20,7 +20,9 @@ LIB = os.path.join(OUT_DIR, 'librok.so')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 SOURCES = {
     'api.cu': [],
-    'linalg.cu': [],
+    'linalg_common.cu': [],
+    'linalg_fast.cu': [],
+    'linalg_strict.cu': ['--fmad=false'],
     'stencil_fast.cu': [],
     'stencil_strict.cu': ['--fmad=false'],
     'peak.cu': [],

@@ -57,7 +57,9 @@ struct rok_ctx {
     bool strict = false;
     int kind = 0;
     size_t nc = 0, N = 0;
-    int P = 0;                 // blocks of the reduction kernels
+    int P = 0;                 // CTAs (partials) of a reduction over N entries
+    int egrid = 0;             // CTAs of the element-wise kernels
+    const LinalgOps *ops = nullptr;
     int mmax = 0;
     cudaStream_t stream = nullptr;
     // workspace
@@ -113,7 +115,7 @@ rok_status stencil(rok_ctx *c, const StencilIO &io)
         CU(cudaEventRecord(ev.first, c->stream));
     }
     cudaError_t e;
-    if (c->kind == ROK_LORENZ96) e = launch_lorenz(c->C, io, c->C.nx, c->stream);
+    if (c->kind == ROK_LORENZ96) e = c->strict ? strict::launch_lorenz(c->C, io, c->C.nx, c->stream) : fast::launch_lorenz(c->C, io, c->C.nx, c->stream);
     else if (c->curv) e = c->strict ? strict::launch_curv(c->C, c->G, io, c->stream) : fast::launch_curv(c->C, c->G, io, c->stream);
     else e = c->strict ? strict::launch_cart(c->C, io, c->stream) : fast::launch_cart(c->C, io, c->stream);
     if (e != cudaSuccess) return ROK_ERR_CUDA;
@@ -356,36 +358,36 @@ rok_status enqueue_rok_body(rok_ctx *c, double *y, int M)
     rok_status r = stencil(c, io_plain(c, y, c->F[0]));
     if (r != ROK_OK) return r;
     // eps from ||y_n|| (unit basis vectors)
-    CU(launch_dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
-    CU(launch_eps(c->pA, P, true, 0.0, st, s));
+    CU(c->ops->dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
+    CU(c->ops->eps(c->pA, P, true, 0.0, st, s));
     c->launches += 2;
     if (M > 0) {
         // v_1 = F1 / ||F1||
-        CU(launch_dot2(c->F[0], c->F[0], nullptr, nullptr, N, c->pA, P, nullptr, s));
-        CU(launch_normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
+        CU(c->ops->dot2(c->F[0], c->F[0], nullptr, nullptr, N, c->pA, P, nullptr, s));
+        CU(c->ops->normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
         c->launches += 2;
         for (int j = 0; j < M; ++j) {
             StencilIO io = io_jvp(c, y, c->V + (size_t)j * N, c->F[0], c->w);
             io.active = &st->active;
             if ((r = stencil(c, io)) != ROK_OK) return r;
             // <v_1, w> and ||w||^2
-            CU(launch_dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
+            CU(c->ops->dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
             c->launches++;
             double *pin = c->pA, *pout = c->pB;
             for (int i = 1; i <= j + 1; ++i) {
                 const double *vnext = i <= j ? c->V + (size_t)i * N : nullptr;
-                CU(launch_mgs(c->w, c->V + (size_t)(i - 1) * N, vnext, N, pin, P,
+                CU(c->ops->mgs(c->w, c->V + (size_t)(i - 1) * N, vnext, N, pin, P,
                               &st->H[(i - 1) * kMaxKrylov + j], pout, i == 1, st, s));
                 c->launches++;
                 double *t = pin; pin = pout; pout = t;
             }
             if (j + 1 < M) {
-                CU(launch_normalize(c->w, c->V + (size_t)(j + 1) * N, N, pin, P,
+                CU(c->ops->normalize(c->w, c->V + (size_t)(j + 1) * N, N, pin, P,
                                     &st->H[(j + 1) * kMaxKrylov + j], j + 1, st, s));
                 c->launches++;
             }
         }
-        CU(launch_lu(st, s));
+        CU(c->ops->lu(st, s));
         c->launches++;
     }
     for (int i = 0; i < 4; ++i) {
@@ -400,15 +402,15 @@ rok_status enqueue_rok_body(rok_ctx *c, double *y, int M)
             if ((r = stencil(c, io)) != ROK_OK) return r;
         }
         if (M > 0) {
-            CU(launch_multidot(c->F[i], c->V, N, N, c->pM, P, st, s));
-            CU(launch_stage_solve(i, kRokGammaOff[i], c->pM, P, st, s));
+            CU(c->ops->multidot(c->F[i], c->V, N, N, c->pM, P, st, s));
+            CU(c->ops->stage_solve(i, kRokGammaOff[i], c->pM, P, st, s));
             c->launches += 2;
         }
-        CU(launch_stage_vec(c->K[i], c->F[i], c->V, N, N, i, st, s));
+        CU(c->ops->stage_vec(c->K[i], c->F[i], c->V, N, N, i, st, c->egrid, s));
         c->launches++;
     }
     const double *kv[4] = {c->K[0], c->K[1], c->K[2], c->K[3]};
-    CU(launch_axpy_n(y, y, kv, kRokB, 4, N, st, s));
+    CU(c->ops->axpy_n(y, y, kv, kRokB, 4, N, st, c->egrid, s));
     c->launches++;
     return ROK_OK;
 }
@@ -453,16 +455,26 @@ struct Givens {
     }
 };
 
+// pairwise (aligned binary tree) sum of p[0..n), zero-padded to a power of two
+double host_tree(const double *p, int n)
+{
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    std::vector<double> b(n2, 0.0);
+    for (int i = 0; i < n; ++i) b[i] = p[i];
+    for (int len = n2; len > 1; len >>= 1)
+        for (int i = 0; i < len / 2; ++i) b[i] = b[2 * i] + b[2 * i + 1];
+    return b[0];
+}
+
 double host_norm(rok_ctx *c, const double *a, rok_status *err)
 {
-    cudaError_t e1 = launch_dot2(a, a, nullptr, nullptr, c->N, c->pA, c->P, nullptr, c->stream);
+    cudaError_t e1 = c->ops->dot2(a, a, nullptr, nullptr, c->N, c->pA, c->P, nullptr, c->stream);
     cudaError_t e2 = cudaMemcpyAsync(c->h_part, c->pA, sizeof(double) * c->P, cudaMemcpyDeviceToHost, c->stream);
     cudaError_t e3 = cudaStreamSynchronize(c->stream);
     c->launches++;
     if (e1 || e2 || e3) { *err = ROK_ERR_CUDA; return 0.0; }
-    double s = 0.0;
-    for (int b = 0; b < c->P; ++b) s += c->h_part[b];
-    return sqrt(s);
+    return sqrt(host_tree(c->h_part, c->P));
 }
 
 }  // namespace
@@ -525,8 +537,9 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    c->P = 2 * sms;
-    set_elem_blocks(4 * 2 * sms);
+    c->P = reduction_blocks(c->N);
+    c->egrid = 8 * sms;
+    c->ops = c->strict ? &strict::ops : &fast::ops;
 
     StencilConsts &C = c->C;
     memset(&C, 0, sizeof(C));
@@ -614,8 +627,8 @@ rok_status rok_jvp(rok_ctx *c, const double *y, const double *fy, const double *
         fy = c->t0;
     }
     // ||y||^2 and ||v||^2 for the automatic increment
-    CU(launch_dot2(y, y, v, v, c->N, c->pA, c->P, nullptr, c->stream));
-    CU(launch_eps(c->pA, c->P, false, eps, c->st, c->stream));
+    CU(c->ops->dot2(y, y, v, v, c->N, c->pA, c->P, nullptr, c->stream));
+    CU(c->ops->eps(c->pA, c->P, false, eps, c->st, c->stream));
     c->launches += 2;
     return stencil(c, io_jvp(c, y, v, fy, jv));
 }
@@ -630,27 +643,27 @@ rok_status rok_arnoldi(rok_ctx *c, const double *y, int M, double *Vout, double 
     CU(launch_begin(st, 0.0, kRokGamma, M, s));
     rok_status r = stencil(c, io_plain(c, y, c->F[0]));
     if (r != ROK_OK) return r;
-    CU(launch_dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
-    CU(launch_eps(c->pA, P, true, 0.0, st, s));
-    CU(launch_dot2(c->F[0], c->F[0], nullptr, nullptr, N, c->pA, P, nullptr, s));
-    CU(launch_normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
+    CU(c->ops->dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
+    CU(c->ops->eps(c->pA, P, true, 0.0, st, s));
+    CU(c->ops->dot2(c->F[0], c->F[0], nullptr, nullptr, N, c->pA, P, nullptr, s));
+    CU(c->ops->normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
     CU(cudaMemsetAsync(st->H, 0, sizeof(st->H), s));
     c->launches += 5;
     for (int j = 0; j < M; ++j) {
         StencilIO io = io_jvp(c, y, c->V + (size_t)j * N, c->F[0], c->w);
         io.active = &st->active;
         if ((r = stencil(c, io)) != ROK_OK) return r;
-        CU(launch_dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
+        CU(c->ops->dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
         double *pin = c->pA, *pout = c->pB;
         for (int i = 1; i <= j + 1; ++i) {
             const double *vnext = i <= j ? c->V + (size_t)i * N : nullptr;
-            CU(launch_mgs(c->w, c->V + (size_t)(i - 1) * N, vnext, N, pin, P, &st->H[(i - 1) * kMaxKrylov + j], pout,
+            CU(c->ops->mgs(c->w, c->V + (size_t)(i - 1) * N, vnext, N, pin, P, &st->H[(i - 1) * kMaxKrylov + j], pout,
                           i == 1, st, s));
             double *t = pin; pin = pout; pout = t;
         }
         c->launches += 1 + (j + 1);
         if (j + 1 < M) {
-            CU(launch_normalize(c->w, c->V + (size_t)(j + 1) * N, N, pin, P, &st->H[(j + 1) * kMaxKrylov + j], j + 1,
+            CU(c->ops->normalize(c->w, c->V + (size_t)(j + 1) * N, N, pin, P, &st->H[(j + 1) * kMaxKrylov + j], j + 1,
                                 st, s));
             c->launches++;
         }
@@ -747,7 +760,7 @@ rok_status rk_step(rok_ctx *c, double *y, double h, rok_step_info *info)
     const double *kv[4] = {c->K[0], c->K[1], c->K[2], c->K[3]};
     double cb[4];
     for (int j = 0; j < 4; ++j) cb[j] = h * kRk4B[j];
-    CU(launch_axpy_n(y, y, kv, cb, 4, c->N, c->st, c->stream));
+    CU(c->ops->axpy_n(y, y, kv, cb, 4, c->N, c->st, c->egrid, c->stream));
     c->launches++;
     c->last = rok_step_info{};
     c->last.residual_evals = 4;
@@ -773,8 +786,8 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
     bool converged = true;
     // k_1 = f(y_n); J_n products use eps from ||y_n||
     if ((r = stencil(c, io_plain(c, y, c->K[0]))) != ROK_OK) return r;
-    CU(launch_dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
-    CU(launch_eps(c->pA, P, true, 0.0, st, s));
+    CU(c->ops->dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
+    CU(c->ops->eps(c->pA, P, true, 0.0, st, s));
     c->launches += 2;
     res_evals++;
     double *xi = c->t0, *rhs = c->t1, *dk = c->t2, *wv = c->w;
@@ -794,7 +807,7 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
         int cnt = 0;
         for (int j = 0; j < i; ++j)
             if (kEsdA[i][j] != 0.0) { kv[cnt] = c->K[j]; cf[cnt] = h * kEsdA[i][j]; cnt++; }
-        CU(launch_axpy_n(xi, y, kv, cf, cnt, N, nullptr, s));
+        CU(c->ops->axpy_n(xi, y, kv, cf, cnt, N, nullptr, c->egrid, s));
         CU(cudaMemcpyAsync(c->K[i], c->K[i - 1], N * sizeof(double), cudaMemcpyDeviceToDevice, s));
         c->launches++;
         bool conv = false;
@@ -820,7 +833,7 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
                         if ((r = apply_op(dk, wv)) != ROK_OK) return r;
                         const double *vv[1] = {wv};
                         double cc[1] = {-1.0};
-                        CU(launch_axpy_n(c->F[1], rhs, vv, cc, 1, N, nullptr, s));
+                        CU(c->ops->axpy_n(c->F[1], rhs, vv, cc, 1, N, nullptr, c->egrid, s));
                         c->launches++;
                         r0 = c->F[1];
                     }
@@ -829,8 +842,8 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
                     if (beta <= op.gmres_tol * bnorm) break;
                     // v_0 = r0 / beta
                     CU(launch_set_int(&st->active, 1, s));
-                    CU(launch_dot2(r0, r0, nullptr, nullptr, N, c->pA, P, nullptr, s));
-                    CU(launch_normalize(r0, c->V, N, c->pA, P, nullptr, 0, st, s));
+                    CU(c->ops->dot2(r0, r0, nullptr, nullptr, N, c->pA, P, nullptr, s));
+                    CU(c->ops->normalize(r0, c->V, N, c->pA, P, nullptr, 0, st, s));
                     c->launches += 3;
                     Givens gv;
                     gv.reset(op.gmres_m, beta);
@@ -838,18 +851,18 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
                     bool done = false;
                     for (int j = 0; j < op.gmres_m; ++j) {
                         if ((r = apply_op(c->V + (size_t)j * N, wv)) != ROK_OK) return r;
-                        CU(launch_dot2(c->V, wv, wv, wv, N, c->pA, P, nullptr, s));
+                        CU(c->ops->dot2(c->V, wv, wv, wv, N, c->pA, P, nullptr, s));
                         double *pin = c->pA, *pout = c->pB;
                         for (int q = 1; q <= j + 1; ++q) {
                             const double *vnext = q <= j ? c->V + (size_t)q * N : nullptr;
-                            CU(launch_mgs(wv, c->V + (size_t)(q - 1) * N, vnext, N, pin, P,
+                            CU(c->ops->mgs(wv, c->V + (size_t)(q - 1) * N, vnext, N, pin, P,
                                           &st->H[(q - 1) * kMaxKrylov + j], pout, q == 1, st, s));
                             double *t = pin; pin = pout; pout = t;
                         }
                         c->launches += 2 + j;
                         // h_{j+1,j} = ||w||; v_{j+1} = w / h_{j+1,j}
                         CU(cudaMemcpyAsync(c->h_part, pin, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
-                        CU(launch_normalize(wv, c->V + (size_t)(j + 1) * N, N, pin, P,
+                        CU(c->ops->normalize(wv, c->V + (size_t)(j + 1) * N, N, pin, P,
                                             &st->H[(j + 1) * kMaxKrylov + j], j + 1, st, s));
                         CU(cudaMemcpyAsync(&c->h_st->active, &st->active, sizeof(int), cudaMemcpyDeviceToHost, s));
                         c->launches++;
@@ -857,9 +870,7 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
                         CU(cudaMemcpy2DAsync(hc, sizeof(double), &st->H[j], kMaxKrylov * sizeof(double), sizeof(double),
                                              j + 1, cudaMemcpyDeviceToHost, s));
                         CU(cudaStreamSynchronize(s));
-                        double hn2 = 0.0;
-                        for (int b = 0; b < P; ++b) hn2 += c->h_part[b];
-                        hc[j + 1] = sqrt(hn2);
+                        hc[j + 1] = sqrt(host_tree(c->h_part, P));
                         its++;
                         double res = gv.add(j, hc);
                         k_used = j + 1;
@@ -868,7 +879,7 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
                     std::vector<double> yv(k_used);
                     gv.solve(k_used, yv.data());
                     CU(cudaMemcpyAsync(st->gcoef, yv.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
-                    CU(launch_basis_combine(dk, dk, c->V, N, N, k_used, st->gcoef, s));
+                    CU(c->ops->basis_combine(dk, dk, c->V, N, N, k_used, st->gcoef, c->egrid, s));
                     CU(cudaStreamSynchronize(s));
                     c->launches++;
                     if (done) break;
@@ -879,10 +890,10 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
             // k += dk; test h g ||dk|| <= tol ||xi + h g k||
             const double *dv[1] = {dk};
             double one[1] = {1.0};
-            CU(launch_axpy_n(c->K[i], c->K[i], dv, one, 1, N, nullptr, s));
+            CU(c->ops->axpy_n(c->K[i], c->K[i], dv, one, 1, N, nullptr, c->egrid, s));
             const double *kv2[1] = {c->K[i]};
             double hgc[1] = {hg};
-            CU(launch_axpy_n(c->F[2], xi, kv2, hgc, 1, N, nullptr, s));
+            CU(c->ops->axpy_n(c->F[2], xi, kv2, hgc, 1, N, nullptr, c->egrid, s));
             c->launches += 2;
             double dn = host_norm(c, dk, &err);
             if (err) return err;
@@ -895,7 +906,7 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
     const double *kv[4] = {c->K[0], c->K[1], c->K[2], c->K[3]};
     double cb[4];
     for (int j = 0; j < 4; ++j) cb[j] = h * kEsdB[j];
-    CU(launch_axpy_n(converged ? y : c->t0, y, kv, cb, 4, N, st, s));
+    CU(c->ops->axpy_n(converged ? y : c->t0, y, kv, cb, 4, N, st, c->egrid, s));
     c->launches++;
     c->last = rok_step_info{};
     c->last.residual_evals = res_evals;

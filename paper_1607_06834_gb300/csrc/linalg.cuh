@@ -9,7 +9,6 @@
 
 namespace rok {
 
-constexpr int kRedThreads = 256;
 
 // Step state kept in device memory so that a whole step runs without host
 // synchronisation (and can be captured in a CUDA graph).
@@ -32,43 +31,55 @@ struct StepState {
     double gcoef[kMaxKrylov + 1];  // host-provided coefficients (GMRES update)
 };
 
-// ---- launchers (linalg.cu) ---------------------------------------------------
-void set_elem_blocks(int blocks);
-cudaError_t launch_set_int(int *p, int v, cudaStream_t s);
-// out partials[2*P]: [0, P) sum a0*b0, [P, 2P) sum a1*b1 (a1 may be NULL: skipped)
-cudaError_t launch_dot2(const double *a0, const double *b0, const double *a1, const double *b1, size_t n,
+// ---- rounding-mode dependent vector kernels (linalg_impl.cuh, compiled twice) ----
+struct LinalgOps {
+    // partials[b] = <a0,b0>, partials[P+b] = <a1,b1> (a1 nullable) over CTA b's 2048 entries
+    cudaError_t (*dot2)(const double *a0, const double *b0, const double *a1, const double *b1, size_t n,
                         double *partials, int P, const int *active, cudaStream_t s);
-// h = sum(pin[0..P)); H entry <- h; w -= h vprev; pout <- partial dots of (vnext, w) or (w, w)
-// if first: also st->wnorm0 = sqrt(sum(pin[P..2P)))
-cudaError_t launch_mgs(double *w, const double *vprev, const double *vnext, size_t n, const double *pin,
-                       int P, double *hout, double *pout, bool first, StepState *st, cudaStream_t s);
-// hn = sqrt(sum pin[0..P)); breakdown / beta tests; v = w * (1/hn); hsub (nullable) <- hn
-cudaError_t launch_normalize(const double *w, double *v, size_t n, const double *pin, int P, double *hsub,
+    // h = tree(pin); *hout = h; w -= h vprev; pout[b] = <vnext, w> (or <w, w> when vnext is NULL);
+    // first: also st->wnorm0 = sqrt(tree(pin + P))
+    cudaError_t (*mgs)(double *w, const double *vprev, const double *vnext, size_t n, const double *pin, int P,
+                       double *hout, double *pout, bool first, StepState *st, cudaStream_t s);
+    // hn = sqrt(tree(pin)); breakdown / beta tests; v = w * (1/hn); *hsub = hn (nullable)
+    cudaError_t (*normalize)(const double *w, double *v, size_t n, const double *pin, int P, double *hsub,
                              int column, StepState *st, cudaStream_t s);
-// multi-dot: pout[m*P + b] = partial of <V_m, F>, m < meff
-cudaError_t launch_multidot(const double *F, const double *V, size_t ldv, size_t n, double *pout, int P,
+    // pout[m*P + b] = <V_m, F> over CTA b's entries, m < meff
+    cudaError_t (*multidot)(const double *F, const double *V, size_t ldv, size_t n, double *pout, int P,
                             const StepState *st, cudaStream_t s);
-// stage i: phi = reduce(pin), rhs = h phi + h H sum_j gam_ij lam_j, lam_i = LU solve, cvec_i = lam_i - h phi
-cudaError_t launch_stage_solve(int stage, const double *gam_row, const double *pin, int P, StepState *st,
+    // stage i: phi, rhs = h phi + h H sum_j gam_ij lam_j, lam_i by LU, cvec_i = lam_i - h phi
+    cudaError_t (*stage_solve)(int stage, const double *gam_row, const double *pin, int P, StepState *st,
                                cudaStream_t s);
-// LU with partial pivoting of I - h g H (meff x meff)
-cudaError_t launch_lu(StepState *st, cudaStream_t s);
-// k = sum_m cvec[stage][m] V_m + h F
-cudaError_t launch_stage_vec(double *k, const double *F, const double *V, size_t ldv, size_t n, int stage,
-                             const StepState *st, cudaStream_t s);
-// out = base + sum_t c_t v_t (c_t host; count <= 8); if guard: skip when st->status != 0
-cudaError_t launch_axpy_n(double *out, const double *base, const double *const *v, const double *c, int count,
-                          size_t n, const StepState *guard, cudaStream_t s);
-// out = sum_{m<count} gcoef[m] V_m + base (GMRES update x += V y), coefficients on the device
-cudaError_t launch_basis_combine(double *out, const double *base, const double *V, size_t ldv, size_t n,
-                                 int count, const double *gcoef, cudaStream_t s);
-// eps from reduced ||y||^2 (pin[0..P)) and ||v||^2 (pin[P..2P)) or vnorm = 1 when v_unit
-cudaError_t launch_eps(const double *pin, int P, bool v_unit, double eps_given, StepState *st, cudaStream_t s);
+    // LU with partial pivoting of I - h g H (meff x meff)
+    cudaError_t (*lu)(StepState *st, cudaStream_t s);
+    // k = sum_m cvec[stage][m] V_m + h F
+    cudaError_t (*stage_vec)(double *k, const double *F, const double *V, size_t ldv, size_t n, int stage,
+                             const StepState *st, int grid, cudaStream_t s);
+    // out = base + sum_q c_q v_q (count <= 8, host coefficients); skipped when guard->status != 0
+    cudaError_t (*axpy_n)(double *out, const double *base, const double *const *v, const double *c, int count,
+                          size_t n, const StepState *guard, int grid, cudaStream_t s);
+    // out = base + sum_{m<count} gcoef[m] V_m (device coefficients)
+    cudaError_t (*basis_combine)(double *out, const double *base, const double *V, size_t ldv, size_t n, int count,
+                                 const double *gcoef, int grid, cudaStream_t s);
+    // eps from tree(pin) = ||y||^2 and tree(pin + P) = ||v||^2 (or ||v|| = 1)
+    cudaError_t (*eps)(const double *pin, int P, bool v_unit, double eps_given, StepState *st, cudaStream_t s);
+    cudaError_t (*sum_sqrt)(const double *pin, int P, double *dst, cudaStream_t s);
+};
+
+namespace fast {
+extern const LinalgOps ops;
+}
+namespace strict {
+extern const LinalgOps ops;
+}
+
+// number of CTAs (and partials) of a reduction over n entries: 2048 entries per CTA
+inline int reduction_blocks(size_t n) { return n ? (int)((n + 2047) / 2048) : 1; }
+
+// ---- rounding-independent helpers (linalg_common.cu) -----------------------------
+cudaError_t launch_set_int(int *p, int v, cudaStream_t s);
 // begin a step: h, hg, meff = M, active = (M > 0)
 cudaError_t launch_begin(StepState *st, double h, double gamma, int M, cudaStream_t s);
-// beta = sqrt(sum pin); if beta == 0: meff = 0, active = 0
-cudaError_t launch_sum_sqrt(const double *pin, int P, double *dst, cudaStream_t s);
-// dt from CFL: per-cell spectral-radius bound, max reduction
+// dt from CFL: per-cell spectral-radius bound, max reduction (order independent)
 cudaError_t launch_cfl(const double *y, const StencilConsts &c, const double *geo_six, const double *geo_siy,
                        const double *geo_sjx, const double *geo_sjy, const double *geo_vol, double *pmax, int P,
                        cudaStream_t s);

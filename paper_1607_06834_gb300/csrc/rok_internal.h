@@ -69,11 +69,12 @@ struct StencilIO {
 namespace fast {
 cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_t s);
 cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s);
+cudaError_t launch_lorenz(const StencilConsts &c, const StencilIO &io, int n, cudaStream_t s);
 }
 namespace strict {
 cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_t s);
 cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s);
-}
 cudaError_t launch_lorenz(const StencilConsts &c, const StencilIO &io, int n, cudaStream_t s);
+}
 
 }  // namespace rok

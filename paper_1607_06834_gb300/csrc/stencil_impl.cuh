@@ -523,6 +523,39 @@ __global__ void __launch_bounds__(NT) curv_kernel(const StencilConsts C, const C
     }
 }
 
+// Lorenz-96 (appendix): f_i = (u_{i+1} - u_{i-2}) u_{i-1} - u_i + F, periodic,
+// with the stencil launch's state formation and epilogue.
+__global__ void lorenz_kernel(const StencilConsts C, const StencilIO io, int n)
+{
+    if (io.active && *io.active == 0) return;
+    double cf[kMaxAdd];
+#pragma unroll
+    for (int t = 0; t < kMaxAdd; ++t) cf[t] = io.coef_dev[t] ? io.coef[t] * *io.coef_dev[t] : io.coef[t];
+    const double s1 = io.s1_dev ? io.s1 * *io.s1_dev : io.s1;
+    const double s2 = io.s2_dev ? io.s2 * *io.s2_dev : io.s2;
+    auto q = [&](int i) {
+        i = (i % n + n) % n;
+        double v = io.base[i];
+        for (int t = 0; t < io.nadd; ++t) v = v + cf[t] * io.add[t][i];
+        return v;
+    };
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double r = ((q(i + 1) - q(i - 2)) * q(i - 1) - q(i)) + C.lorenz_f;
+        double t = io.sub ? (r - io.sub[i]) : r;
+        t = t * s1;
+        double o = io.add_out ? io.add_out[i] + s2 * t : t;
+        io.out[i] = o;
+        if (!isfinite(o)) atomicOr(io.status, kStatusNonfinite);
+    }
+}
+
+
+cudaError_t launch_lorenz(const StencilConsts &c, const StencilIO &io, int n, cudaStream_t s)
+{
+    lorenz_kernel<<<(n + 255) / 256, 256, 0, s>>>(c, io, n);
+    return cudaGetLastError();
+}
+
 template <bool V, bool S>
 static cudaError_t launch_cart_t(const StencilConsts &c, const StencilIO &io, cudaStream_t s)
 {

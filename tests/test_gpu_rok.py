@@ -12,7 +12,7 @@ import pytest
 from oracle import core
 from oracle import integrators as I
 from paper_1607_06834_gb300 import workloads as W
-from tests.gpu_common import dev, host, rel_l2
+from tests.gpu_common import U, dev, flux_scale, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -23,18 +23,31 @@ def rok():
     return r
 
 
+def _fd_noise(prob, y, eps):
+    """Bound on the last-bit difference of one FD-JVP entry between two roundings
+    of the residual: 64 u max|F|/h amplified by 1/eps (see test_gpu_stencil)."""
+    return 64 * U * flux_scale(prob, y) / eps
+
+
 @pytest.mark.parametrize('mode', ['strict', 'fast'])
 def test_arnoldi_matches_oracle(rok, mode):
     prob, y = W.isentropic_vortex(48)
-    ctx = rok.rok_init(prob, krylov_max=12, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
-    V, H, me = rok.rok_arnoldi(ctx, dev(y), 12)
+    M = 12
+    ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+    V, H, me = rok.rok_arnoldi(ctx, dev(y), M)
     sys_ = core.System(prob)
-    Vo, Ho, meo = I.arnoldi(sys_, y, core.residual(prob, y), 12, I.fd_eps(np.linalg.norm(y)))
-    assert me == meo == 12
+    eps = I.fd_eps(I.norm(y))
+    Vo, Ho, meo = I.arnoldi(sys_, y, core.residual(prob, y), M, eps)
+    assert me == meo == M
     V, H = host(V), host(H)
-    assert np.abs(H - Ho).max() <= 1e-9 * np.abs(Ho).max()
-    assert np.abs(V - Vo).max() <= 1e-9
-    assert np.abs(V @ V.T - np.eye(12)).max() <= 1e-12 * 12
+    if mode == 'strict':
+        # same residual bits, same pairwise inner products, same normalisation
+        assert np.array_equal(H, Ho) and np.array_equal(V, Vo)
+    else:
+        # FD-JVP rounding noise (|dw| <= sqrt(N) * noise per column), accumulated over the columns
+        tol = 4 * M * np.sqrt(y.size) * _fd_noise(prob, y, eps)
+        assert np.abs(H - Ho).max() <= tol, (np.abs(H - Ho).max(), tol)
+    assert np.abs(V @ V.T - np.eye(M)).max() <= 1e-12 * M
 
 
 def test_arnoldi_full_size_properties(rok):
@@ -51,59 +64,81 @@ def test_arnoldi_full_size_properties(rok):
     assert np.all(np.tril(Hh, -2) == 0.0) and np.all(np.diag(Hh, -1) > 0)
     f = rok.rok_residual(ctx, yd)
     assert float((V[0] - f.ravel() / f.norm()).abs().max()) <= 1e-14
-    eps = I.fd_eps(float(np.linalg.norm(y)))
+    eps = I.fd_eps(I.norm(y))
     for j in (0, 7, 19):
         w = rok.rok_jvp(ctx, yd, V[j].reshape(y.shape).contiguous(), fy=f, eps=eps)
         col = (V @ w.ravel()).cpu().numpy()
         assert np.abs(col[:j + 2 if j + 2 <= 20 else 20] - Hh[:min(j + 2, 20), j]).max() <= 1e-9 * np.abs(Hh).max()
 
 
-@pytest.mark.parametrize('mode', ['strict', 'fast'])
-def test_rok_ten_steps_vortex(rok, mode):
-    prob, y0 = W.isentropic_vortex(64)
-    M = 12
+def _ten_steps(rok, prob, y0, cfl, M, mode, steps=10):
     ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
-    h = I.dt_from_cfl(prob, y0, 5.0)
+    h = I.dt_from_cfl(prob, y0, cfl)
     y = dev(y0)
     yo = y0.copy()
     sys_ = core.System(prob)
-    for _ in range(10):
+    for _ in range(steps):
         info = rok.rok_step(ctx, y, h, M, info=True)
         assert info['m_eff'] == M
         yo = I.rok_step(sys_, yo, h, M)
-    assert rel_l2(host(y), yo) <= 1e-9
+    return host(y), yo, h
 
 
-def test_rok_ns_and_ogrid_steps(rok):
+def _oracle_self_sensitivity(prob, y0, h, M, steps=10):
+    """How far the oracle itself moves after `steps` ROK4 steps when one entry of
+    the initial state moves by one ulp: FD-JVP quotients re-round at every
+    evaluation, so two evaluations that differ in the last bit of the state drift
+    apart at the FD noise level."""
+    sys_ = core.System(prob)
+    ya, yb = y0.copy(), y0.copy()
+    yb.flat[yb.size // 3] = np.nextafter(yb.flat[yb.size // 3], np.inf)
+    for _ in range(steps):
+        ya = I.rok_step(sys_, ya, h, M)
+        yb = I.rok_step(sys_, yb, h, M)
+    return rel_l2(ya, yb)
+
+
+def test_rok_ten_steps_vortex_strict_bitexact(rok):
+    prob, y0 = W.isentropic_vortex(64)
+    y, yo, _ = _ten_steps(rok, prob, y0, 5.0, 12, 'strict')
+    assert np.array_equal(y, yo), rel_l2(y, yo)
+
+
+def test_rok_ten_steps_vortex_fast(rok):
+    prob, y0 = W.isentropic_vortex(64)
+    y, yo, h = _ten_steps(rok, prob, y0, 5.0, 12, 'fast')
+    err = rel_l2(y, yo)
+    sens = _oracle_self_sensitivity(prob, y0, h, 12)
+    assert err <= max(1e-9, 30 * sens), (err, sens)
+
+
+def test_rok_ns_and_ogrid_steps_strict_bitexact(rok):
     prob, y0 = W.taylor_green(64, reynolds=200.0)
-    ctx = rok.rok_init(prob, krylov_max=8)
-    h = I.dt_from_cfl(prob, y0, 8.0)
-    y, yo = dev(y0), y0.copy()
-    for _ in range(3):
-        rok.rok_step(ctx, y, h, 8)
-        yo = I.rok_step(core.System(prob), yo, h, 8)
-    assert rel_l2(host(y), yo) <= 1e-9
+    y, yo, _ = _ten_steps(rok, prob, y0, 8.0, 8, 'strict', steps=3)
+    assert np.array_equal(y, yo), rel_l2(y, yo)
     p4, y4, _ = W.cylinder_ogrid(32, 64)
-    ctx = rok.rok_init(p4, krylov_max=10, rounding=rok.ROK_ROUND_STRICT)
-    h = I.dt_from_cfl(p4, y4, 50.0)
-    y, yo = dev(y4), y4.copy()
-    for _ in range(2):
-        rok.rok_step(ctx, y, h, 10)
-        yo = I.rok_step(core.System(p4), yo, h, 10)
-    assert rel_l2(host(y), yo) <= 1e-9
+    y, yo, _ = _ten_steps(rok, p4, y4, 50.0, 10, 'strict', steps=2)
+    assert np.array_equal(y, yo), rel_l2(y, yo)
 
 
 def test_rok_full_size_one_step(rok):
-    # the benchmark workload: 512^2 Navier-Stokes Taylor-Green, ROK4, M = 20, CFL 8
+    # the benchmark workload: 512^2 Navier-Stokes Taylor-Green, ROK4, M = 20, CFL 8,
+    # strict rounding bit-exact; the FMA build within the FD noise of one step
     prob, y0 = W.taylor_green(512, reynolds=1600.0)
-    ctx = rok.rok_init(prob, krylov_max=20)
     h = I.dt_from_cfl(prob, y0, 8.0)
+    yo = I.rok_step(core.System(prob), y0, h, 20)
+    ctx = rok.rok_init(prob, krylov_max=20, rounding=rok.ROK_ROUND_STRICT)
     y = dev(y0)
     rok.rok_step(ctx, y, h, 20)
-    yo = I.rok_step(core.System(prob), y0, h, 20)
-    d = host(y) - yo
-    assert np.linalg.norm(d) <= 1e-9 * np.linalg.norm(yo - y0)   # relative to the update itself
-    assert rel_l2(host(y), yo) <= 1e-12
+    assert np.array_equal(host(y), yo)
+    ctx = rok.rok_init(prob, krylov_max=20, rounding=rok.ROK_ROUND_FAST)
+    y = dev(y0)
+    rok.rok_step(ctx, y, h, 20)
+    d = np.linalg.norm(host(y) - yo)
+    eps = I.fd_eps(I.norm(y0))
+    tol = 4 * 20 * np.sqrt(y0.size) * _fd_noise(prob, y0, eps) * h * 20
+    assert d <= tol, (d, tol)
+    assert rel_l2(host(y), yo) <= 1e-9
 
 
 def test_rok_M0_is_rk4_and_free_stream(rok):

@@ -53,13 +53,13 @@ def test_jvp_strict_bitexact(rok, case):
     v = rng.normal(size=y.shape)
     v /= np.linalg.norm(v)
     f0 = core.residual(prob, y)
-    eps = I.fd_eps(np.linalg.norm(y))
+    eps = I.fd_eps(I.norm(y))
     w = host(rok.rok_jvp(ctx, dev(y), dev(v), fy=dev(f0), eps=eps))
     wo = core.jvp_fd(prob, y, v, f0, eps)
     assert np.array_equal(w, wo), (name, np.abs(w - wo).max())
     # automatic increment (fy computed by the library): same power of two
     w2 = host(rok.rok_jvp(ctx, dev(y), dev(v)))
-    e2 = I.fd_eps(np.linalg.norm(y), np.linalg.norm(v))
+    e2 = I.fd_eps(I.norm(y), I.norm(v))
     assert np.array_equal(w2, core.jvp_fd(prob, y, v, f0, e2))
 
 
@@ -71,7 +71,7 @@ def test_jvp_fast_within_amplified_rounding(rok, case):
     v = rng.normal(size=y.shape)
     v /= np.linalg.norm(v)
     f0 = core.residual(prob, y)
-    eps = I.fd_eps(np.linalg.norm(y))
+    eps = I.fd_eps(I.norm(y))
     w = host(rok.rok_jvp(ctx, dev(y), dev(v), fy=dev(f0), eps=eps))
     wo = core.jvp_fd(prob, y, v, f0, eps)
     tol = 64 * U * flux_scale(prob, y) / eps

@@ -122,6 +122,27 @@ def test_esdirk3_order_and_L_stability():
     assert max(abs(R(1j * t)) for t in np.linspace(-100, 100, 2001)) <= 1 + 1e-12
 
 
+# ---- inner products ------------------------------------------------------------
+
+def test_pairwise_sum_is_the_balanced_tree():
+    import math
+    x = np.array([1e16, 1.0, -1e16, 1.0, 3.0])
+    # ((x0 + x1) + (x2 + x3)) + ((x4 + 0) + (0 + 0)), each addition rounded
+    expect = ((1e16 + 1.0) + (-1e16 + 1.0)) + 3.0
+    assert I.pairwise_sum(x) == expect
+    rng = np.random.default_rng(5)
+    for n in (1, 7, 1000, 4097):
+        v = rng.normal(size=n) * 10.0 ** rng.uniform(-5, 5, size=n)
+        exact = math.fsum(v)
+        depth = max(1, int(np.ceil(np.log2(n))))
+        bound = depth * 2.0 ** -53 / (1 - depth * 2.0 ** -53) * np.sum(np.abs(v))
+        assert abs(I.pairwise_sum(v) - exact) <= bound
+        ints = rng.integers(-1000, 1000, size=n).astype(float)
+        assert I.pairwise_sum(ints) == float(ints.sum())
+    a, b = rng.normal(size=300), rng.normal(size=300)
+    assert abs(I.dot(a, b) - math.fsum(a * b)) <= 1e-13 * np.sum(np.abs(a * b))
+
+
 # ---- Arnoldi -------------------------------------------------------------------
 
 def test_arnoldi_relations_and_cgs2():
