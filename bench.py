@@ -305,8 +305,106 @@ def run_stencil_only(args):
                       'tflops_alg': prob.ncells * FLOPS_JVP_NS / (ms * 1e-3) / 1e12}))
 
 
+def _interp_time(points, target):
+    """log-log interpolation of (error, seconds) points to a target error: the
+    time a method needs to reach `target` (None if it never does in the range)."""
+    pts = sorted((e, t) for e, t in points if e > 0)
+    if not pts:
+        return None
+    if pts[0][0] > target:
+        return None
+    if pts[-1][0] <= target:
+        return min(t for e, t in pts if e <= target)
+    for (e0, t0), (e1, t1) in zip(pts, pts[1:]):
+        if e0 <= target <= e1:
+            a = (np.log(target) - np.log(e0)) / (np.log(e1) - np.log(e0))
+            return float(np.exp(np.log(t0) + a * (np.log(t1) - np.log(t0))))
+    return None
+
+
+def run_tte(args):
+    """Time to a fixed L2 error (the paper's work-precision measure, Sec. 4.3):
+    ROK4 vs RK4 vs ESDIRK3 Newton-GMRES on one problem, fixed step sizes,
+    error against an RK4 reference at a 16x finer step, GPU time of the whole
+    integration by CUDA events."""
+    import torch
+
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    if args.case == 'tgv':
+        prob, y0 = W.taylor_green(args.n, mach=MACH, reynolds=RE)
+        krylov, cfls, cfl_rk = KRYLOV, [8.0, 4.0, 2.0], [1.0, 0.5]
+        base_cfl = 8.0
+    else:
+        prob, y0, _ = W.cylinder_ogrid(256, 512)
+        krylov, cfls, cfl_rk = 30, [1000.0, 300.0, 100.0], [1.0]
+        base_cfl = 1.0
+    ctx = rok.rok_init(prob, krylov_max=max(krylov, 30), rounding=rok.ROK_ROUND_FAST)
+    yd = rok.state_tensor(y0)
+    dt_unit = rok.rok_dt_from_cfl(ctx, yd, 1.0)
+    T = args.horizon * dt_unit * base_cfl
+    out = {'study': 'time-to-fixed-L2-error', 'case': prob.name, 'T': T, 'dt_cfl1': dt_unit, 'methods': {}}
+
+    def integrate(step_fn, dt):
+        n = max(1, int(round(T / dt)))
+        h = T / n
+        y = rok.state_tensor(y0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        infos = []
+        for _ in range(n):
+            r = step_fn(y, h)
+            if r is not None:
+                infos.append(r)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return y, n, h, e0.elapsed_time(e1) / 1e3, wall, infos
+
+    ref_dt = min(min(cfls), min(cfl_rk)) * dt_unit / args.ref_factor
+    yref, nref, _, tref, _, _ = integrate(lambda y, h: rok.rk_step(ctx, y, h), ref_dt)
+    yref_h = yref.cpu().numpy()
+    out['reference'] = {'method': 'RK4', 'steps': nref, 'gpu_s': tref}
+    nrm = float(np.linalg.norm(yref_h))
+
+    def record(name, y, n, h, gs, ws, extra=None):
+        e = float(np.linalg.norm(y.cpu().numpy() - yref_h))
+        d = {'steps': n, 'h': h, 'gpu_s': gs, 'wall_s': ws, 'abs_err': e, 'rel_err': e / nrm}
+        if extra:
+            d.update(extra)
+        out['methods'].setdefault(name, []).append(d)
+
+    for c in cfls:
+        y, n, h, gs, ws, _ = integrate(lambda y, h: rok.rok_step(ctx, y, h, krylov), c * dt_unit)
+        record('ROK4', y, n, h, gs, ws, {'cfl': c, 'M': krylov})
+    for c in cfl_rk:
+        y, n, h, gs, ws, _ = integrate(lambda y, h: rok.rk_step(ctx, y, h), c * dt_unit)
+        record('RK4', y, n, h, gs, ws, {'cfl': c})
+    for c in cfls:
+        try:
+            y, n, h, gs, ws, infos = integrate(lambda y, h: rok.esdirk_step(ctx, y, h, info=True), c * dt_unit)
+            record('ESDIRK3', y, n, h, gs, ws, {'cfl': c, 'gmres_iters': sum(i['gmres_iters'] for i in infos),
+                                                'newton_iters': sum(i['newton_iters'] for i in infos)})
+        except rok.RokError as err:
+            out['methods'].setdefault('ESDIRK3', []).append({'cfl': c, 'failed': str(err)})
+    out['time_to_error'] = {}
+    for tgt in (1e-4, 1e-6, 1e-8, 1e-10):
+        row = {}
+        for m, pts in out['methods'].items():
+            row[m] = _interp_time([(p['rel_err'], p['gpu_s']) for p in pts if 'rel_err' in p], tgt)
+        out['time_to_error']['%g' % tgt] = row
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument('--study', default=None, choices=[None, 'tte'])
+    ap.add_argument('--case', default='tgv', choices=['tgv', 'cylinder'])
+    ap.add_argument('--horizon', type=float, default=50.0, help='T in units of the base-CFL step')
+    ap.add_argument('--ref-factor', type=float, default=16.0)
     ap.add_argument('--mode', default='step', choices=['step', 'stencil'])
     ap.add_argument('--n', type=int, default=N_GRID)
     ap.add_argument('--gpus', type=int, default=1)
@@ -319,6 +417,9 @@ def main():
         args.warmup = 3
     if args.mode == 'stencil':
         run_stencil_only(args)
+        return
+    if args.study == 'tte':
+        run_tte(args)
         return
     out = run_reference(args) if args.impl == 'reference' else run_ours(args)
     if out is not None:

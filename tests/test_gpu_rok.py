@@ -117,8 +117,25 @@ def test_rok_ns_and_ogrid_steps_strict_bitexact(rok):
     y, yo, _ = _ten_steps(rok, prob, y0, 8.0, 8, 'strict', steps=3)
     assert np.array_equal(y, yo), rel_l2(y, yo)
     p4, y4, _ = W.cylinder_ogrid(32, 64)
-    y, yo, _ = _ten_steps(rok, p4, y4, 50.0, 10, 'strict', steps=2)
+    # impulsive start against the no-slip wall: ROK4 stays finite to CFL ~10 here
+    # (the CPU oracle blows up at CFL 20 as well; see test_ogrid_unstable_cfl_reports_nonfinite)
+    y, yo, _ = _ten_steps(rok, p4, y4, 5.0, 10, 'strict', steps=2)
     assert np.array_equal(y, yo), rel_l2(y, yo)
+
+
+def test_ogrid_unstable_cfl_reports_nonfinite(rok):
+    # beyond the stability limit the step reports NONFINITE and leaves y untouched,
+    # exactly where the oracle's step produces NaN
+    p4, y4, _ = W.cylinder_ogrid(32, 64)
+    h = I.dt_from_cfl(p4, y4, 50.0)
+    yo = I.rok_step(core.System(p4), y4, h, 10)
+    assert not np.isfinite(yo).all()
+    ctx = rok.rok_init(p4, krylov_max=10, rounding=rok.ROK_ROUND_STRICT)
+    yd = dev(y4)
+    with pytest.raises(rok.RokError) as e:
+        rok.rok_step(ctx, yd, h, 10, info=True)
+    assert e.value.status == rok.ROK_ERR_NONFINITE
+    assert np.array_equal(host(yd), y4)
 
 
 def test_rok_full_size_one_step(rok):
