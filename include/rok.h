@@ -166,6 +166,39 @@ rok_status rok_set_stencil_timing(rok_ctx *ctx, int enable);
 
 const char *rok_status_string(rok_status s);
 
+/* Allocation-free variant of rok_jvp (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory: code that runs inside a
+ * host application which owns every device allocation (a plug-in whose host
+ * framework forbids or pools cudaMalloc), and loops that must not call
+ * cudaMalloc/cudaFree because those calls synchronise the device.  Such a
+ * caller cannot create a rok_ctx (rok_init allocates the Krylov basis and the
+ * workspace), so this call takes the problem description directly and keeps
+ * its scratch -- the reduction partials of ||y||^2 and ||v||^2, eps, 1/eps and
+ * the status word -- in one static device array of about 134 KB that every GPU
+ * loading the library holds until the process exits.
+ *
+ * Computes jv = (f(y + eps v) - fy) / eps exactly as rok_jvp with the same
+ * description and rounding mode (same kernels, same result bits).
+ *   desc   uniform periodic Euler / Navier-Stokes grids (xv == NULL) or
+ *          Lorenz-96; curvilinear grids return ROK_ERR_UNSUPPORTED (their
+ *          metrics would need device memory).
+ *   y, fy, v, jv  device, N float64 (N = 4 nx ny, Lorenz-96: nx); fy = f(y)
+ *          is required; jv must not overlap the inputs.
+ *   eps    > 0 used as given; <= 0 selects the power-of-two increment of rok_jvp.
+ *   status nullable DEVICE int: receives the latched error bits of this call
+ *          (0 = ok, nonzero = a non-finite value was produced).
+ * N beyond ROK_NOALLOC_MAX_N returns ROK_ERR_INVALID_ARG without launching.
+ * Calls no cudaMalloc, cudaFree or allocating routine.  The first call on a
+ * device resolves the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls whose execution overlaps on the GPU (different
+ * streams, or concurrent host threads) race on it and must be serialised by
+ * the caller.  Asynchronous on cuda_stream. */
+#define ROK_NOALLOC_MAX_N (4096 * 2048)
+rok_status rok_jvp_noalloc(const rok_problem_desc *desc, const double *y, const double *fy, const double *v,
+                           double *jv, double eps, int *status, void *cuda_stream);
+
 /* Measurement utility (no counterpart in the paper): FP64 fused-multiply-add
  * throughput of the current device in TFLOP/s (2 flops per FMA), from
  * `repeats` timed launches of independent FMA chains.  Synchronises. */

@@ -26,6 +26,7 @@ SOURCES = {
     'stencil_fast.cu': [],
     'stencil_strict.cu': ['--fmad=false'],
     'peak.cu': [],
+    'noalloc.cu': [],
 }
 
 

@@ -82,6 +82,7 @@ _sig = {
     'rok_set_stencil_timing': (ctypes.c_int, [_vp, ctypes.c_int]),
     'rok_status_string': (ctypes.c_char_p, [ctypes.c_int]),
     'rok_fp64_fma_peak': (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    'rok_jvp_noalloc': (ctypes.c_int, [ctypes.POINTER(ProblemDesc), _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -258,6 +259,23 @@ def rok_get_counters(ctx, reset=False):
 
 def rok_set_stencil_timing(ctx, enable):
     _check(_lib.rok_set_stencil_timing(ctx.handle, int(bool(enable))), 'rok_set_stencil_timing')
+
+
+ROK_NOALLOC_MAX_N = 4096 * 2048
+
+
+def rok_jvp_noalloc(problem, y, v, fy, out, eps=0.0, status=None, rounding=ROK_ROUND_FAST, stream=None):
+    """``rok_jvp_noalloc``: FD Jacobian-vector product without any device
+    allocation by the library (no context; scratch in a static device array).
+    ``out`` (and the optional int32 device tensor ``status``) are the caller's."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    d, keep = _desc(problem, 0, rounding)
+    st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    _check(_lib.rok_jvp_noalloc(ctypes.byref(d), _ptr(y), _ptr(fy), _ptr(v), _ptr(out), float(eps), st,
+                                ctypes.c_void_p(stream.cuda_stream)), 'rok_jvp_noalloc')
+    del keep
+    return out
 
 
 def rok_fp64_fma_peak(repeats=20):
