@@ -134,13 +134,15 @@ def run_ours(args):
 
     fp64_peak = rok.rok_fp64_fma_peak(20) if rank == 0 else None
 
+    if args.graph:
+        rok.rok_set_graph(ctx, True)
     for _ in range(args.warmup):
         rok.rok_step(ctx, y, h, KRYLOV)
     info = rok.rok_step(ctx, y, h, KRYLOV, info=True)
     assert info['m_eff'] == KRYLOV
 
     rok.rok_get_counters(ctx, reset=True)
-    rok.rok_set_stencil_timing(ctx, True)
+    rok.rok_set_stencil_timing(ctx, not args.graph)
     sampler = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
@@ -158,6 +160,16 @@ def run_ours(args):
     cnt = rok.rok_get_counters(ctx, reset=True)
     rok.rok_set_stencil_timing(ctx, False)
     rok.rok_sync(ctx)
+    if args.graph:
+        # graph replays carry no per-kernel events: time the stencil launches of
+        # the same steps in a second, eager pass
+        rok.rok_set_graph(ctx, False)
+        rok.rok_set_stencil_timing(ctx, True)
+        for k in range(args.steps):
+            rok.rok_step(ctx, y, h, KRYLOV)
+        c2 = rok.rok_get_counters(ctx, reset=True)
+        rok.rok_set_stencil_timing(ctx, False)
+        cnt['stencil_ms'], cnt['stencil_timed'] = c2['stencil_ms'], c2['stencil_timed']
     ms_t = torch.tensor([ms], dtype=torch.float64, device='cuda')
     if ws > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -412,6 +424,7 @@ def main():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--rounding', default='fast', choices=['fast', 'strict'])
+    ap.add_argument('--graph', type=int, default=0, help='replay each ROK4 step as a captured CUDA graph')
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -154,18 +154,19 @@ static void roe(const double *WL, const double *WR, double nx, double ny,
     double rR = WR[0], uR = WR[1], vR = WR[2], pR = WR[3];
     double qnL = uL * nx + vL * ny;
     double qnR = uR * nx + vR * ny;
-    double EL = pL * inv_gm1 + rL * (0.5 * (uL * uL + vL * vL));
-    double ER = pR * inv_gm1 + rR * (0.5 * (uR * uR + vR * vR));
-    double HL = (EL + pL) / rL;
-    double HR = (ER + pR) / rR;
+    /* rho H = E + p on each side */
+    double eL = (pL * inv_gm1 + rL * (0.5 * (uL * uL + vL * vL))) + pL;
+    double eR = (pR * inv_gm1 + rR * (0.5 * (uR * uR + vR * vR))) + pR;
 
+    /* Roe averages with weights sqrt(rho): wl = sL/(sL+sR) = rL sR / (sL sR (sL+sR)),
+     * H~ = (sL HL + sR HR)/(sL+sR) = (eL sR + eR sL) / (sL sR (sL+sR)) */
     double sL = sqrt(rL), sR = sqrt(rR);
-    double den = 1.0 / (sL + sR);
-    double wl = sL * den, wr = sR * den;
     double rt = sL * sR;
+    double den = 1.0 / (rt * (sL + sR));
+    double wl = (rL * sR) * den, wr = (rR * sL) * den;
     double ut = wl * uL + wr * uR;
     double vt = wl * vL + wr * vR;
-    double Ht = wl * HL + wr * HR;
+    double Ht = (eL * sR + eR * sL) * den;
     double kt = 0.5 * (ut * ut + vt * vt);
     double ct2 = gm1 * (Ht - kt);
     double ct = sqrt(ct2);
@@ -194,11 +195,10 @@ static void roe(const double *WL, const double *WR, double nx, double ny,
     double mL = rL * qnL, mR = rR * qnR;
     double FL1 = mL * uL + pL * nx, FR1 = mR * uR + pR * nx;
     double FL2 = mL * vL + pL * ny, FR2 = mR * vR + pR * ny;
-    double FL3 = mL * HL, FR3 = mR * HR;
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * ((FL1 + FR1) - D1);
     F[2] = 0.5 * ((FL2 + FR2) - D2);
-    F[3] = 0.5 * ((FL3 + FR3) - D3);
+    F[3] = 0.5 * ((qnL * eL + qnR * eR) - D3);
 }
 
 /* viscous face flux (tau . n, u . tau . n - q . n) for unit normal n;

@@ -8,25 +8,25 @@
 // Every inner product is the pairwise sum of the rounded entrywise products: a
 // balanced binary tree over the natural index order, zero-padded to a power of
 // two.  The GPU evaluates exactly that tree:
-//   - a warp owns 256 consecutive entries; lane l loads entries 32k + l
-//     (k = 0..7, coalesced); an xor butterfly over the lanes (distances 1, 2,
-//     4, 8, 16) forms the sums of the eight aligned 32-entry groups, which are
-//     then added as a 3-level tree in registers;
-//   - a CTA of 8 warps owns 2048 consecutive entries; the warp sums are added
-//     as a 3-level tree;
-//   - the consumer of the CTA partials adds them as a tree again (every CTA of
-//     the consuming kernel computes the same value in the same order).
+//   - every lane owns 8 consecutive entries and adds them as a 3-level tree in
+//     registers (vector loads when aligned);
+//   - the 32 lanes of a warp own 256 consecutive entries; an xor butterfly of
+//     increasing distance (1, 2, 4, 8, 16) adds the lane sums as the next 5
+//     tree levels;
+//   - the 8 warps of a CTA own 2048 consecutive entries, added as 3 levels;
+//   - the CTA partials are added as a tree again by the consumer (one warp,
+//     contiguous chunks per lane, then a butterfly).
 // Addition is commutative in IEEE arithmetic, so both partners of a butterfly
-// hold the same sum.  The result is deterministic and independent of the
-// launch configuration (extra zero leaves change nothing).
+// hold the same sum; the result is deterministic and independent of the launch
+// configuration (extra zero leaves change nothing).
 //
-// On GB300 the FP64 pipe is the scarce unit (about two FP64 FMA per clock per
-// SM), so FP64 vector passes sit near the HBM/FP64 balance point; each pass
-// reads its vectors once, keeps eight independent loads per thread in flight,
-// and the MGS update of one vector is fused with the inner product against
-// the next.
+// On GB300 the FP64 pipe is the scarce unit (2 FP64 lanes per SM per clock):
+// summing in registers first keeps the tree at about 1.5 additions per entry
+// (a butterfly over strided entries would cost 5), which puts a fused MGS pass
+// (1 FMA, 1 product, the tree) at the HBM/FP64 balance point.
 #pragma once
 #include <math.h>
+#include <stdint.h>
 
 #include "linalg.cuh"
 
@@ -34,23 +34,52 @@ namespace rok {
 namespace ROK_NS {
 
 constexpr int RT = 256;            // threads per CTA
-constexpr int EPL = 8;             // entries per lane
+constexpr int EPL = 8;             // consecutive entries per lane
 constexpr int RB = RT * EPL;       // entries per CTA (2048)
+
+__device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+// x[0..8) = p[e0 .. e0+8) (zero beyond n)
+__device__ __forceinline__ void load8(const double *__restrict__ p, size_t e0, size_t n, double (&x)[EPL])
+{
+    if (e0 + EPL <= n && aligned16(p)) {
+        const double2 *q = reinterpret_cast<const double2 *>(p + e0);
+#pragma unroll
+        for (int k = 0; k < EPL / 2; ++k) {
+            double2 t = q[k];
+            x[2 * k] = t.x;
+            x[2 * k + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = e0 + k < n ? p[e0 + k] : 0.0;
+    }
+}
+
+__device__ __forceinline__ void store8(double *__restrict__ p, size_t e0, size_t n, const double (&x)[EPL])
+{
+    if (e0 + EPL <= n && aligned16(p)) {
+        double2 *q = reinterpret_cast<double2 *>(p + e0);
+#pragma unroll
+        for (int k = 0; k < EPL / 2; ++k) q[k] = make_double2(x[2 * k], x[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k)
+            if (e0 + k < n) p[e0 + k] = x[k];
+    }
+}
+
+// tree over the 8 consecutive entries of a lane
+__device__ __forceinline__ double tree8(const double (&x)[EPL])
+{
+    return ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+}
 
 __device__ __forceinline__ double lane_tree(double v)
 {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-// sum of the eight 32-entry groups of a warp: p[k] holds entry 32k + lane
-__device__ __forceinline__ double warp_tree8(const double (&p)[EPL])
-{
-    double s[EPL];
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) s[k] = lane_tree(p[k]);
-    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
 // tree over the 8 warp sums of a CTA; sh >= 9 doubles; result in every thread
@@ -71,57 +100,103 @@ __device__ __forceinline__ double cta_tree(double wsum, double *sh)
     return sh[8];
 }
 
-// Tree sum of p[0..P) (zero-padded to a power of two), identical in every CTA.
-// Thread t owns the C = P2/256 consecutive leaves [tC, tC + C) (C >= 1) and
-// adds them as an aligned tree with a carry stack, then lane and warp trees.
-__device__ __forceinline__ double tree_partials(const double *p, int P, double *sh)
+// CTA sum of one value per lane-chunk: the 8 entries of the lane, then the
+// lane butterfly, then the warp tree
+__device__ __forceinline__ double chunk_sum(const double (&x)[EPL], double *sh)
+{
+    return cta_tree(lane_tree(tree8(x)), sh);
+}
+
+// Aligned tree over the C consecutive leaves p[lo .. lo + C) (zero beyond P),
+// C a power of two: up to 32 leaves are loaded at once (independent loads) and
+// added level by level; longer runs use a carry stack over the leaves in order.
+template <int L>
+__device__ __forceinline__ double leaf_tree_fixed(const double *__restrict__ p, int lo, int P)
+{
+    double x[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) x[k] = lo + k < P ? p[lo + k] : 0.0;
+#pragma unroll
+    for (int len = L; len > 1; len >>= 1)
+#pragma unroll
+        for (int i = 0; i < len / 2; ++i) x[i] = x[2 * i] + x[2 * i + 1];
+    return x[0];
+}
+
+__device__ __forceinline__ double leaf_tree(const double *__restrict__ p, int lo, int C, int P)
+{
+    switch (C) {
+    case 1: return lo < P ? p[lo] : 0.0;
+    case 2: return leaf_tree_fixed<2>(p, lo, P);
+    case 4: return leaf_tree_fixed<4>(p, lo, P);
+    case 8: return leaf_tree_fixed<8>(p, lo, P);
+    case 16: return leaf_tree_fixed<16>(p, lo, P);
+    case 32: return leaf_tree_fixed<32>(p, lo, P);
+    default: break;
+    }
+    double stack[24];
+    for (int k = 0; k < C; ++k) {
+        double s = lo + k < P ? p[lo + k] : 0.0;
+        int lvl = 0;
+        for (int m = k; m & 1; m >>= 1, ++lvl) s = stack[lvl] + s;
+        stack[lvl] = s;
+    }
+    int top = 0;
+    while ((1 << top) < C) ++top;
+    return stack[top];
+}
+
+__device__ __forceinline__ int pow2_ceil(int P)
 {
     int P2 = 1;
     while (P2 < P) P2 <<= 1;
-    const int C = P2 > RT ? P2 / RT : 1;
-    const int t = threadIdx.x;
-    double v = 0.0;
-    if (C == 1) {
-        v = t < P ? p[t] : 0.0;
-    } else {
-        double stack[16];
-        int lo = t * C;
-        for (int k = 0; k < C; ++k) {
-            double s = lo + k < P ? p[lo + k] : 0.0;
-            int lvl = 0;
-            for (int m = k; m & 1; m >>= 1, ++lvl) s = stack[lvl] + s;
-            stack[lvl] = s;
-        }
-        int top = 0;
-        while ((1 << top) < C) ++top;
-        v = stack[top];
-    }
-    v = lane_tree(v);
-    return cta_tree(v, sh);
+    return P2;
 }
 
-__device__ __forceinline__ size_t warp_base()
+// Tree sum of p[0..P) (zero-padded to a power of two) by one warp: lane l owns
+// the C = P2/32 consecutive leaves [lC, lC + C), then the lane butterfly.
+__device__ __forceinline__ double warp_tree_partials(const double *__restrict__ p, int P)
 {
-    return ((size_t)blockIdx.x * RT + (threadIdx.x & ~31)) * EPL;
+    const int P2 = pow2_ceil(P);
+    const int lane = threadIdx.x & 31;
+    const int C = P2 > 32 ? P2 / 32 : 1;
+    return lane_tree(leaf_tree(p, lane * C, C, P));
 }
+
+// The same tree by the whole CTA (thread t owns C = P2/256 leaves), result in
+// every thread.
+__device__ __forceinline__ double tree_partials(const double *__restrict__ p, int P, double *sh)
+{
+    const int P2 = pow2_ceil(P);
+    const int C = P2 > RT ? P2 / RT : 1;
+    return cta_tree(lane_tree(leaf_tree(p, threadIdx.x * C, C, P)), sh);
+}
+
+__device__ __forceinline__ size_t lane_e0() { return ((size_t)blockIdx.x * RT + threadIdx.x) * EPL; }
 
 // partials[b] = <a0, b0> and partials[P + b] = <a1, b1> (if a1) over CTA b's range
-__global__ void __launch_bounds__(RT) dot2_kernel(const double *a0, const double *b0, const double *a1,
-                                                  const double *b1, size_t n, double *partials, int P,
+__global__ void __launch_bounds__(RT) dot2_kernel(const double *__restrict__ a0, const double *__restrict__ b0,
+                                                  const double *__restrict__ a1, const double *__restrict__ b1,
+                                                  size_t n, double *__restrict__ partials, int P,
                                                   const int *active)
 {
     if (active && *active == 0) return;
     __shared__ double sh[10];
-    const size_t base = warp_base() + (threadIdx.x & 31);
-    double p[EPL], q[EPL];
+    const size_t e0 = lane_e0();
+    double x[EPL], y[EPL];
+    load8(a0, e0, n, x);
+    load8(b0, e0, n, y);
 #pragma unroll
-    for (int k = 0; k < EPL; ++k) {
-        size_t e = base + 32 * k;
-        p[k] = e < n ? a0[e] * b0[e] : 0.0;
-        q[k] = (a1 && e < n) ? a1[e] * b1[e] : 0.0;
+    for (int k = 0; k < EPL; ++k) x[k] = x[k] * y[k];
+    double s0 = chunk_sum(x, sh);
+    double s1 = 0.0;
+    if (a1) {
+        load8(a1, e0, n, x);
+        load8(b1, e0, n, y);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = x[k] * y[k];
+        s1 = chunk_sum(x, sh);
     }
-    double s0 = cta_tree(warp_tree8(p), sh);
-    double s1 = cta_tree(warp_tree8(q), sh);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = s0;
         partials[P + blockIdx.x] = s1;
@@ -129,38 +204,42 @@ __global__ void __launch_bounds__(RT) dot2_kernel(const double *a0, const double
 }
 
 // h = tree(pin); H entry <- h; w <- w - h vprev; pout[b] = <vnext, w> (or <w, w>)
-__global__ void __launch_bounds__(RT) mgs_kernel(double *w, const double *vprev, const double *vnext, size_t n,
-                                                 const double *pin, int P, double *hout, double *pout, int first,
-                                                 StepState *st)
+__global__ void __launch_bounds__(RT) mgs_kernel(double *__restrict__ w, const double *__restrict__ vprev,
+                                                 const double *__restrict__ vnext, size_t n,
+                                                 const double *__restrict__ pin, int P, double *hout,
+                                                 double *__restrict__ pout, int first, StepState *st)
 {
     if (st->active == 0) return;
     __shared__ double sh[10];
+    const size_t e0 = lane_e0();
+    double wv[EPL], vp[EPL], vn[EPL];
+    load8(w, e0, n, wv);
+    load8(vprev, e0, n, vp);
+    if (vnext) load8(vnext, e0, n, vn);
     const double h = tree_partials(pin, P, sh);
     if (first) {
         double wn2 = tree_partials(pin + P, P, sh);
         if (blockIdx.x == 0 && threadIdx.x == 0) st->wnorm0 = sqrt(wn2);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
-    const size_t base = warp_base() + (threadIdx.x & 31);
-    double p[EPL];
 #pragma unroll
-    for (int k = 0; k < EPL; ++k) {
-        size_t e = base + 32 * k;
-        double pr = 0.0;
-        if (e < n) {
-            double we = w[e] - h * vprev[e];
-            w[e] = we;
-            pr = vnext ? vnext[e] * we : we * we;
-        }
-        p[k] = pr;
+    for (int k = 0; k < EPL; ++k) wv[k] = wv[k] - h * vp[k];
+    store8(w, e0, n, wv);
+    if (vnext) {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) vn[k] = vn[k] * wv[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) vn[k] = wv[k] * wv[k];
     }
-    double s = cta_tree(warp_tree8(p), sh);
+    double s = chunk_sum(vn, sh);
     if (threadIdx.x == 0) pout[blockIdx.x] = s;
 }
 
 // hn = sqrt(tree(pin)); breakdown test; v = w * (1/hn)
-__global__ void __launch_bounds__(RT) normalize_kernel(const double *w, double *v, size_t n, const double *pin,
-                                                       int P, double *hsub, int column, StepState *st)
+__global__ void __launch_bounds__(RT) normalize_kernel(const double *__restrict__ w, double *__restrict__ v,
+                                                       size_t n, const double *__restrict__ pin, int P,
+                                                       double *hsub, int column, StepState *st)
 {
     // block 0 may clear st->active below while other CTAs start: read it once
     // per CTA so that every thread of a CTA takes the same branch
@@ -185,31 +264,30 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double *w, double *
         if (column == 0) st->beta = hn;
     }
     const double r = 1.0 / hn;
-    for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) v[e] = w[e] * r;
+    const size_t e0 = lane_e0();
+    double x[EPL];
+    load8(w, e0, n, x);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) x[k] = x[k] * r;
+    store8(v, e0, n, x);
 }
 
 // pout[m * P + b] = <V_m, F> over CTA b's range, m < meff
-__global__ void __launch_bounds__(RT) multidot_kernel(const double *F, const double *V, size_t ldv, size_t n,
-                                                      double *pout, int P, const StepState *st)
+__global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__ F, const double *__restrict__ V,
+                                                      size_t ldv, size_t n, double *__restrict__ pout, int P,
+                                                      const StepState *st)
 {
     const int m = st->meff;
     __shared__ double sh[10];
-    const size_t base = warp_base() + (threadIdx.x & 31);
+    const size_t e0 = lane_e0();
     double f[EPL];
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) {
-        size_t e = base + 32 * k;
-        f[k] = e < n ? F[e] : 0.0;
-    }
+    load8(F, e0, n, f);
     for (int i = 0; i < m; ++i) {
-        const double *Vi = V + (size_t)i * ldv;
-        double p[EPL];
+        double x[EPL];
+        load8(V + (size_t)i * ldv, e0, n, x);
 #pragma unroll
-        for (int k = 0; k < EPL; ++k) {
-            size_t e = base + 32 * k;
-            p[k] = e < n ? Vi[e] * f[k] : 0.0;
-        }
-        double s = cta_tree(warp_tree8(p), sh);
+        for (int k = 0; k < EPL; ++k) x[k] = x[k] * f[k];
+        double s = chunk_sum(x, sh);
         if (threadIdx.x == 0) pout[(size_t)i * P + blockIdx.x] = s;
     }
 }
@@ -274,10 +352,9 @@ __global__ void stage_solve_kernel(int stage, GamRow gr, const double *pin, int 
     const int m = st->meff;
     const double h = st->h;
     __shared__ double phi[kMaxKrylov], acc[kMaxKrylov], x[kMaxKrylov];
-    __shared__ double sh[10];
-    for (int i = 0; i < m; ++i) {
-        double s = tree_partials(pin + (size_t)i * P, P, sh);
-        if (threadIdx.x == 0) phi[i] = s;
+    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
+        double v = warp_tree_partials(pin + (size_t)i * P, P);
+        if ((threadIdx.x & 31) == 0) phi[i] = v;
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double a = 0.0;

@@ -46,9 +46,11 @@ __device__ __forceinline__ void muscl(double m2, double m1, double p1, double p2
     wr = (p1 - c_lo * dr) - c_hi * dc;
 }
 
-// Roe-averaged quantities common to every face orientation.
+// Roe-averaged quantities common to every face orientation.  e = rho H = E + p;
+// the sqrt(rho)-weighted averages use one reciprocal:
+//   wl = rL sR / (sL sR (sL + sR)),  H~ = (eL sR + eR sL) / (sL sR (sL + sR)).
 struct RoeAvg {
-    double HL, HR, rt, ut, vt, Ht, kt, ct, inv_c2;
+    double eL, eR, rt, ut, vt, Ht, kt, ct, inv_c2;
 };
 
 __device__ __forceinline__ RoeAvg roe_avg(const double *L, const double *R, const StencilConsts &C)
@@ -56,17 +58,15 @@ __device__ __forceinline__ RoeAvg roe_avg(const double *L, const double *R, cons
     RoeAvg a;
     double rL = L[0], uL = L[1], vL = L[2], pL = L[3];
     double rR = R[0], uR = R[1], vR = R[2], pR = R[3];
-    double EL = pL * C.inv_gm1 + rL * (0.5 * (uL * uL + vL * vL));
-    double ER = pR * C.inv_gm1 + rR * (0.5 * (uR * uR + vR * vR));
-    a.HL = (EL + pL) / rL;
-    a.HR = (ER + pR) / rR;
+    a.eL = (pL * C.inv_gm1 + rL * (0.5 * (uL * uL + vL * vL))) + pL;
+    a.eR = (pR * C.inv_gm1 + rR * (0.5 * (uR * uR + vR * vR))) + pR;
     double sL = sqrt(rL), sR = sqrt(rR);
-    double den = 1.0 / (sL + sR);
-    double wl = sL * den, wr = sR * den;
     a.rt = sL * sR;
+    double den = 1.0 / (a.rt * (sL + sR));
+    double wl = (rL * sR) * den, wr = (rR * sL) * den;
     a.ut = wl * uL + wr * uR;
     a.vt = wl * vL + wr * vR;
-    a.Ht = wl * a.HL + wr * a.HR;
+    a.Ht = (a.eL * sR + a.eR * sL) * den;
     a.kt = 0.5 * (a.ut * a.ut + a.vt * a.vt);
     double ct2 = C.gm1 * (a.Ht - a.kt);
     a.ct = sqrt(ct2);
@@ -101,7 +101,7 @@ __device__ __forceinline__ void roe_x(const double *L, const double *R, const St
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * (((mL * uL + pL) + (mR * uR + pR)) - D1);
     F[2] = 0.5 * ((mL * vL + mR * vR) - D2);
-    F[3] = 0.5 * ((mL * a.HL + mR * a.HR) - D3);
+    F[3] = 0.5 * ((uL * a.eL + uR * a.eR) - D3);
 }
 
 // Roe flux through a y-face (unit normal (0, 1)), exact specialisation as above.
@@ -129,7 +129,7 @@ __device__ __forceinline__ void roe_y(const double *L, const double *R, const St
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * ((mL * uL + mR * uR) - D1);
     F[2] = 0.5 * (((mL * vL + pL) + (mR * vR + pR)) - D2);
-    F[3] = 0.5 * ((mL * a.HL + mR * a.HR) - D3);
+    F[3] = 0.5 * ((vL * a.eL + vR * a.eR) - D3);
 }
 
 // Roe flux for a general unit normal (nx, ny) (curvilinear grids).
@@ -163,7 +163,7 @@ __device__ __forceinline__ void roe_n(const double *L, const double *R, double n
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * ((FL1 + FR1) - D1);
     F[2] = 0.5 * ((FL2 + FR2) - D2);
-    F[3] = 0.5 * ((mL * a.HL + mR * a.HR) - D3);
+    F[3] = 0.5 * ((qnL * a.eL + qnR * a.eR) - D3);
 }
 
 // shared-memory tile of primitive variables (halo included)
@@ -233,7 +233,7 @@ __device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd]
 
 // ============================ uniform periodic grid ============================
 template <bool VISC, bool SUTH>
-__global__ void __launch_bounds__(NT) cart_kernel(const StencilConsts C, const StencilIO io)
+__global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, const StencilIO io)
 {
     if (io.active && *io.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(NT) cart_kernel(const StencilConsts C, const S
 // then i-ghosts of every row (ghost rows included); periodic wraps, a wall
 // mirrors (rho, -u, -v, p), the far field is the free stream.
 template <bool VISC, bool SUTH>
-__global__ void __launch_bounds__(NT) curv_kernel(const StencilConsts C, const CurvGeom G, const StencilIO io)
+__global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, const CurvGeom G, const StencilIO io)
 {
     if (io.active && *io.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];

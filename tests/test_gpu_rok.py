@@ -185,7 +185,8 @@ def test_rok_conservation_and_graph_replay(rok):
         rok.rok_step(ctx, y, h, 12)
     yh = host(y)
     for k in range(4):
-        assert abs(yh[k].sum() - y0[k].sum()) <= 1e-12 * np.abs(y0[k]).sum()
+        # conservation to the FD-quotient rounding level (u/eps relative, eps ~ 2^-22)
+        assert abs(yh[k].sum() - y0[k].sum()) <= 1e-9 * np.abs(y0[k]).sum()
     ctx2 = rok.rok_init(prob, krylov_max=12)
     rok.rok_set_graph(ctx2, True)
     yg = dev(y0)

@@ -234,7 +234,10 @@ def test_rok_conserves_and_keeps_free_stream():
     h = I.dt_from_cfl(prob, y, 5.0)
     y1 = I.rok_step(sys, y, h, 8)
     for k in range(4):
-        assert abs(y1[k].sum() - y[k].sum()) <= 1e-12 * np.abs(y[k]).sum()
+        # each f sums to zero over the cells up to rounding; the FD quotient divides
+        # that rounding by eps (~2^-22 here), so the basis vectors, and the step,
+        # conserve to about u/eps relative
+        assert abs(y1[k].sum() - y[k].sum()) <= 1e-9 * np.abs(y[k]).sum()
     yfs = np.empty_like(y)
     for k in range(4):
         yfs[k] = prob.q_inf[k]
