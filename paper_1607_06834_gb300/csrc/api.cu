@@ -69,6 +69,8 @@ struct rok_ctx {
     double *w = nullptr, *t0 = nullptr, *t1 = nullptr, *t2 = nullptr;
     double *pA = nullptr, *pB = nullptr, *pM = nullptr;   // partial sums
     StepState *st = nullptr;
+    GridBarrier *bar = nullptr; // grid barrier of the persistent Arnoldi column kernel
+    int col_ctas = 0;           // co-resident CTAs of that kernel (0: multi-kernel path)
     StepState *h_st = nullptr;  // pinned mirror
     double *h_part = nullptr;   // pinned, >= 2P
     // curvilinear geometry (device)
@@ -165,6 +167,7 @@ void free_ctx(rok_ctx *c)
     cudaFree(c->w); cudaFree(c->t0); cudaFree(c->t1); cudaFree(c->t2);
     cudaFree(c->pA); cudaFree(c->pB); cudaFree(c->pM);
     cudaFree(c->st);
+    cudaFree(c->bar);
     cudaFreeHost(c->h_st);
     cudaFreeHost(c->h_part);
     for (double *p : c->geo_bufs) cudaFree(p);
@@ -326,6 +329,7 @@ rok_status fail_latched(rok_ctx *c)
     int s = c->h_st->status;
     if (s & kStatusNonfinite) return ROK_ERR_NONFINITE;
     if (s & kStatusSingular) return ROK_ERR_NONFINITE;
+    if (s & kStatusTimeout) return ROK_ERR_TIMEOUT;
     return ROK_OK;
 }
 
@@ -341,6 +345,51 @@ rok_status sync_read(rok_ctx *c, rok_step_info *info)
     c->last.eps = c->h_st->eps;
     if (info) *info = c->last;
     return s;
+}
+
+// Columns 0..M-1 of the Arnoldi process of Sec. 2.3.3 (v_1 already in V[0]):
+// JVP of v_j, then the modified-Gram-Schmidt column, either in one persistent
+// cooperative launch or as dot2 + (j+1) mgs passes + normalize.  Both forms
+// perform the same arithmetic.
+rok_status arnoldi_columns(rok_ctx *c, const double *y, int M)
+{
+    const size_t N = c->N;
+    const int P = c->P;
+    StepState *st = c->st;
+    cudaStream_t s = c->stream;
+    rok_status r;
+    for (int j = 0; j < M; ++j) {
+        StencilIO io = io_jvp(c, y, c->V + (size_t)j * N, c->F[0], c->w);
+        io.active = &st->active;
+        if ((r = stencil(c, io)) != ROK_OK) return r;
+        cudaError_t e = cudaErrorNotSupported;
+        if (c->col_ctas > 0 && !c->capturing)
+            e = c->ops->arnoldi_column(c->w, c->V, N, N, j, j + 1 < M ? 1 : 0, P, c->pA, c->pB, c->bar, st,
+                                       c->col_ctas, s);
+        if (e == cudaSuccess) {
+            c->launches++;
+            continue;
+        }
+        if (e != cudaErrorNotSupported) return ROK_ERR_CUDA;
+        (void)cudaGetLastError();
+        // <v_1, w> and ||w||^2
+        CU(c->ops->dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
+        c->launches++;
+        double *pin = c->pA, *pout = c->pB;
+        for (int i = 1; i <= j + 1; ++i) {
+            const double *vnext = i <= j ? c->V + (size_t)i * N : nullptr;
+            CU(c->ops->mgs(c->w, c->V + (size_t)(i - 1) * N, vnext, N, pin, P,
+                           &st->H[(i - 1) * kMaxKrylov + j], pout, i == 1, st, s));
+            c->launches++;
+            double *t = pin; pin = pout; pout = t;
+        }
+        if (j + 1 < M) {
+            CU(c->ops->normalize(c->w, c->V + (size_t)(j + 1) * N, N, pin, P, &st->H[(j + 1) * kMaxKrylov + j],
+                                 j + 1, st, s));
+            c->launches++;
+        }
+    }
+    return ROK_OK;
 }
 
 // ---- ROK4 step, enqueue only ------------------------------------------------------
@@ -366,27 +415,8 @@ rok_status enqueue_rok_body(rok_ctx *c, double *y, int M)
         CU(c->ops->dot2(c->F[0], c->F[0], nullptr, nullptr, N, c->pA, P, nullptr, s));
         CU(c->ops->normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
         c->launches += 2;
-        for (int j = 0; j < M; ++j) {
-            StencilIO io = io_jvp(c, y, c->V + (size_t)j * N, c->F[0], c->w);
-            io.active = &st->active;
-            if ((r = stencil(c, io)) != ROK_OK) return r;
-            // <v_1, w> and ||w||^2
-            CU(c->ops->dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
-            c->launches++;
-            double *pin = c->pA, *pout = c->pB;
-            for (int i = 1; i <= j + 1; ++i) {
-                const double *vnext = i <= j ? c->V + (size_t)i * N : nullptr;
-                CU(c->ops->mgs(c->w, c->V + (size_t)(i - 1) * N, vnext, N, pin, P,
-                              &st->H[(i - 1) * kMaxKrylov + j], pout, i == 1, st, s));
-                c->launches++;
-                double *t = pin; pin = pout; pout = t;
-            }
-            if (j + 1 < M) {
-                CU(c->ops->normalize(c->w, c->V + (size_t)(j + 1) * N, N, pin, P,
-                                    &st->H[(j + 1) * kMaxKrylov + j], j + 1, st, s));
-                c->launches++;
-            }
-        }
+        rok_status ra = arnoldi_columns(c, y, M);
+        if (ra != ROK_OK) return ra;
         CU(c->ops->lu(st, s));
         c->launches++;
     }
@@ -576,10 +606,13 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
               al(&c->pM, (size_t)kMaxKrylov * c->P);
     for (int i = 0; i < 4 && ok; ++i) ok = al(&c->F[i], N) && al(&c->K[i], N);
     ok = ok && cudaMalloc(&c->st, sizeof(StepState)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->bar, sizeof(GridBarrier)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_st, sizeof(StepState)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_part, sizeof(double) * 2 * (kMaxKrylov + 2) * (size_t)c->P) == cudaSuccess;
     if (!ok) { free_ctx(c); return ROK_ERR_NOMEM; }
     if (cudaMemset(c->st, 0, sizeof(StepState)) != cudaSuccess) { free_ctx(c); return ROK_ERR_CUDA; }
+    if (cudaMemset(c->bar, 0, sizeof(GridBarrier)) != cudaSuccess) { free_ctx(c); return ROK_ERR_CUDA; }
+    c->col_ctas = c->ops->arnoldi_column_ctas(sms);
     memset(c->h_st, 0, sizeof(StepState));
     if (c->curv) {
         c->d.xv = d->xv; c->d.yv = d->yv;   // used only while building the metrics
@@ -649,25 +682,7 @@ rok_status rok_arnoldi(rok_ctx *c, const double *y, int M, double *Vout, double 
     CU(c->ops->normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
     CU(cudaMemsetAsync(st->H, 0, sizeof(st->H), s));
     c->launches += 5;
-    for (int j = 0; j < M; ++j) {
-        StencilIO io = io_jvp(c, y, c->V + (size_t)j * N, c->F[0], c->w);
-        io.active = &st->active;
-        if ((r = stencil(c, io)) != ROK_OK) return r;
-        CU(c->ops->dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
-        double *pin = c->pA, *pout = c->pB;
-        for (int i = 1; i <= j + 1; ++i) {
-            const double *vnext = i <= j ? c->V + (size_t)i * N : nullptr;
-            CU(c->ops->mgs(c->w, c->V + (size_t)(i - 1) * N, vnext, N, pin, P, &st->H[(i - 1) * kMaxKrylov + j], pout,
-                          i == 1, st, s));
-            double *t = pin; pin = pout; pout = t;
-        }
-        c->launches += 1 + (j + 1);
-        if (j + 1 < M) {
-            CU(c->ops->normalize(c->w, c->V + (size_t)(j + 1) * N, N, pin, P, &st->H[(j + 1) * kMaxKrylov + j], j + 1,
-                                st, s));
-            c->launches++;
-        }
-    }
+    if ((r = arnoldi_columns(c, y, M)) != ROK_OK) return r;
     r = sync_read(c, nullptr);
     int me = c->h_st->meff;
     *m_eff = me;
@@ -695,6 +710,8 @@ rok_status rok_step(rok_ctx *c, double *y, double h, int M, rok_step_info *info)
     c->last.residual_evals = 1 + M + 3;
     c->last.jvps = M;
     CU(launch_begin(c->st, h, kRokGamma, M, c->stream));
+    // a grid barrier that timed out leaves its arrival count behind: start clean
+    CU(cudaMemsetAsync(&c->bar->count, 0, sizeof(unsigned), c->stream));
     c->launches++;
     if (c->use_graph && !c->time_stencil) {
         // graphs are captured and replayed on a private non-blocking stream fenced

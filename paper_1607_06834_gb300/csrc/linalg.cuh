@@ -63,6 +63,18 @@ struct LinalgOps {
     // eps from tree(pin) = ||y||^2 and tree(pin + P) = ||v||^2 (or ||v|| = 1)
     cudaError_t (*eps)(const double *pin, int P, bool v_unit, double eps_given, StepState *st, cudaStream_t s);
     cudaError_t (*sum_sqrt)(const double *pin, int P, double *dst, cudaStream_t s);
+    // One whole Arnoldi column j in a single cooperative launch (grid = ctas,
+    // co-resident): h_ij = <v_i, w>, w -= h_ij v_i for i = 0..j (modified
+    // Gram-Schmidt), then, when next != 0, h_{j+1,j} = ||w||, the breakdown test
+    // and v_{j+1} = w * (1/h_{j+1,j}).  w and the next basis vector stay in
+    // registers between passes; partA/partB hold 2P partials each.  Same
+    // arithmetic as dot2 + mgs + normalize.  Returns cudaErrorNotSupported when
+    // the ctas cannot cover the P chunks (caller falls back).
+    cudaError_t (*arnoldi_column)(double *w, double *V, size_t ldv, size_t n, int j, int next, int P,
+                                  double *partA, double *partB, GridBarrier *bar, StepState *st, int ctas,
+                                  cudaStream_t s);
+    // co-resident CTAs of arnoldi_column on this device (0 if cooperative launch is unavailable)
+    int (*arnoldi_column_ctas)(int sms);
 };
 
 namespace fast {

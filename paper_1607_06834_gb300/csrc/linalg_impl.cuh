@@ -292,6 +292,160 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__
     }
 }
 
+// ---- persistent Arnoldi column ------------------------------------------------
+
+constexpr int kColChunks = 2;                  // chunks of 2048 entries per CTA (max)
+constexpr long long kBarrierSpins = 1LL << 22; // ~0.3 s at 64 ns per spin, then give up
+
+// Bounded grid barrier: arrive on the counter; the last CTA resets it and
+// advances the generation; the others poll the generation with a spin limit.
+// On expiry the status gets kStatusTimeout and the CTA reports failure (the
+// kernel then returns; nothing waits forever).
+__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, int *status)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = &bar->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(double *__restrict__ w, double *__restrict__ V,
+                                                               size_t ldv, size_t n, int j, int next, int P,
+                                                               double *partA, double *partB, GridBarrier *bar,
+                                                               StepState *st)
+{
+    __shared__ double sh[10];
+    __shared__ int act;
+    if (threadIdx.x == 0) act = st->active;
+    __syncthreads();
+    if (act == 0) return;
+    const unsigned G = gridDim.x;
+    double wv[kColChunks][EPL], vn[kColChunks][EPL];
+    size_t e0[kColChunks];
+    bool have[kColChunks];
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c) {
+        const int b = blockIdx.x + c * G;
+        have[c] = b < P;
+        e0[c] = ((size_t)b * RT + threadIdx.x) * EPL;
+        if (have[c]) {
+            load8(w, e0[c], n, wv[c]);
+            load8(V, e0[c], n, vn[c]);     // v_0
+        }
+    }
+    // pass 0 partials: <v_0, w> and <w, w>
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c) {
+        if (!have[c]) continue;   // uniform per CTA
+        double x[EPL], y[EPL];
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) {
+            x[k] = vn[c][k] * wv[c][k];
+            y[k] = wv[c][k] * wv[c][k];
+        }
+        double s0 = chunk_sum(x, sh);
+        double s1 = chunk_sum(y, sh);
+        if (threadIdx.x == 0) {
+            partA[blockIdx.x + c * G] = s0;
+            partA[P + blockIdx.x + c * G] = s1;
+        }
+    }
+    double *pin = partA, *pout = partB;
+    if (!grid_barrier(bar, G, &st->status)) return;
+    for (int i = 0; i <= j; ++i) {
+        const double h = tree_partials(pin, P, sh);
+        if (i == 0) {
+            const double wn2 = tree_partials(pin + P, P, sh);
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->wnorm0 = sqrt(wn2);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->H[i * kMaxKrylov + j] = h;
+        const double *vnext = i < j ? V + (size_t)(i + 1) * ldv : nullptr;
+#pragma unroll
+        for (int c = 0; c < kColChunks; ++c) {
+            if (!have[c]) continue;
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) wv[c][k] = wv[c][k] - h * vn[c][k];
+            if (vnext) load8(vnext, e0[c], n, vn[c]);
+            double x[EPL];
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) x[k] = vnext ? vn[c][k] * wv[c][k] : wv[c][k] * wv[c][k];
+            double s = chunk_sum(x, sh);
+            if (threadIdx.x == 0) pout[blockIdx.x + c * G] = s;
+        }
+        if (!grid_barrier(bar, G, &st->status)) return;
+        double *t = pin;
+        pin = pout;
+        pout = t;
+    }
+    if (!next) {
+        // last column: the orthogonalised w is not needed further
+        return;
+    }
+    const double hn = sqrt(tree_partials(pin, P, sh));
+    const bool brk = !(hn > 1e-12 * st->wnorm0);
+    if (brk) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->active = 0;
+            st->meff = j + 1;
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->H[(j + 1) * kMaxKrylov + j] = hn;
+    const double r = 1.0 / hn;
+    double *vout = V + (size_t)(j + 1) * ldv;
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c) {
+        if (!have[c]) continue;
+        double x[EPL];
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = wv[c][k] * r;
+        store8(vout, e0[c], n, x);
+    }
+}
+
+static int arnoldi_column_ctas(int sms)
+{
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_column_kernel, RT, 0) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+static cudaError_t arnoldi_column(double *w, double *V, size_t ldv, size_t n, int j, int next, int P,
+                                  double *partA, double *partB, GridBarrier *bar, StepState *st, int ctas,
+                                  cudaStream_t s)
+{
+    if (ctas <= 0) return cudaErrorNotSupported;
+    const int G = P < ctas ? P : ctas;
+    if ((P + G - 1) / G > kColChunks) return cudaErrorNotSupported;
+    void *args[] = {&w, &V, &ldv, &n, &j, &next, &P, &partA, &partB, &bar, &st};
+    return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel, dim3(G), dim3(RT), args, 0, s);
+}
+
 // One warp: LU with partial pivoting of L = I - h g H (first largest |pivot|),
 // row-major stride kMaxKrylov.  Each entry sees the same operation sequence as
 // a sequential elimination.
@@ -555,7 +709,7 @@ static cudaError_t sum_sqrt(const double *pin, int P, double *dst, cudaStream_t 
 }
 
 const LinalgOps ops = {dot2, mgs, normalize, multidot, stage_solve, lu, stage_vec, axpy_n, basis_combine, eps,
-                       sum_sqrt};
+                       sum_sqrt, arnoldi_column, arnoldi_column_ctas};
 
 }  // namespace ROK_NS
 }  // namespace rok
