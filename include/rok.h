@@ -51,6 +51,11 @@ enum { ROK_JVP_FD = 0, ROK_JVP_EXACT = 1 };
  * against a plain CPU evaluation in the same order); ROK_ROUND_FAST lets the
  * compiler contract into FMA (fewer FP64 instructions, last-bit differences). */
 enum { ROK_ROUND_FAST = 0, ROK_ROUND_STRICT = 1 };
+/* Krylov basis of the ROK step: binary64, or binary32 storage with binary32
+ * Gram-Schmidt (the mixed-precision form; the state, the finite-difference
+ * quotient and its eps, the flux accumulation, the Hessenberg / stage solves,
+ * the projections phi and the stage vectors stay binary64). */
+enum { ROK_BASIS_FP64 = 0, ROK_BASIS_FP32 = 1 };
 
 /* Problem description, copied by rok_init (pointers are not retained). */
 typedef struct {
@@ -71,6 +76,7 @@ typedef struct {
     double lorenz_f;     /* Lorenz-96 forcing F                                       */
     int krylov_max;      /* largest Krylov dimension M / GMRES restart length used    */
     int rounding;        /* ROK_ROUND_FAST | ROK_ROUND_STRICT                         */
+    int basis;           /* ROK_BASIS_FP64 | ROK_BASIS_FP32 (rok_step / rok_arnoldi)   */
 } rok_problem_desc;
 
 typedef struct {

@@ -21,28 +21,34 @@ from . import core
 MACH_EPS = 2.0 ** -52
 
 
-def pairwise_sum(x):
+def pairwise_sum(x, dtype=np.float64):
     """Sum of the entries of x by pairwise summation (Higham): a balanced binary
     tree over the index range, x zero-padded to a power-of-two length, each level
-    adding entry 2i and entry 2i+1.  This fixes one rounding of the sum."""
-    x = np.ravel(np.asarray(x, dtype=np.float64))
+    adding entry 2i and entry 2i+1, every addition rounded in `dtype`.  This fixes
+    one rounding of the sum."""
+    x = np.ravel(np.asarray(x, dtype=dtype))
     n = 1
     while n < x.size:
         n *= 2
-    buf = np.zeros(n)
+    buf = np.zeros(n, dtype=dtype)
     buf[:x.size] = x
     while buf.size > 1:
         buf = buf[0::2] + buf[1::2]
-    return float(buf[0])
+    return buf[0]
 
 
-def dot(a, b):
-    """Inner product: the rounded entrywise products, summed pairwise."""
-    return pairwise_sum(np.ravel(a) * np.ravel(b))
+def dot(a, b, dtype=np.float64):
+    """Inner product: the entrywise products rounded in `dtype`, summed pairwise."""
+    a = np.ravel(np.asarray(a, dtype=dtype))
+    b = np.ravel(np.asarray(b, dtype=dtype))
+    r = pairwise_sum(a * b, dtype)
+    return float(r) if dtype == np.float64 else r
 
 
-def norm(a):
-    return math.sqrt(dot(a, a))
+def norm(a, dtype=np.float64):
+    if dtype == np.float64:
+        return math.sqrt(dot(a, a))
+    return np.sqrt(dot(a, a, dtype))
 
 
 def fd_eps(ynorm, vnorm=1.0):
@@ -60,38 +66,50 @@ def fd_eps(ynorm, vnorm=1.0):
     return math.ldexp(1.0, e)
 
 
-def arnoldi(sys, y, F1, M, eps, breakdown_tol=1e-12):
+def arnoldi(sys, y, F1, M, eps, breakdown_tol=None, basis=np.float64):
     """Modified-Gram-Schmidt Arnoldi (Sec. 2.3.3): V (M_eff x N, rows orthonormal)
     and H = V^T J V (M_eff x M_eff, upper Hessenberg) of K_M(J, f(y_n)), with the
     Jacobian applied by Eq. matvecFD.  Returns (V, H, M_eff).
 
     Readings: beta = ||F1|| = 0 gives M_eff = 0; the basis is cut at column j
-    when h_{j+1,j} <= breakdown_tol * ||J v_j|| (a scale-consistent test);
-    h_{j+1,j} > 0 makes V unique.  Normalisation multiplies by 1/h."""
+    when h_{j+1,j} <= tol * ||J v_j|| (a scale-consistent test; tol 1e-12 in
+    binary64, 1e-5 in binary32); h_{j+1,j} > 0 makes V unique; normalisation
+    multiplies by 1/h.
+
+    basis = np.float32 is the mixed-precision form: the basis is stored and the
+    Gram-Schmidt arithmetic (inner products, updates, norms) is done in binary32;
+    each JVP result (a binary64 difference quotient at y + eps v) is rounded to
+    binary32 before orthogonalisation; H is kept in binary64."""
+    if breakdown_tol is None:
+        breakdown_tol = 1e-12 if basis == np.float64 else 1e-5
+    T = basis
     N = F1.size
-    V = np.zeros((M, N))
+    V = np.zeros((M, N), dtype=T)
     H = np.zeros((M, M))
-    beta = norm(F1)
+    w = np.asarray(F1, dtype=T).ravel()
+    beta = norm(w, T)
     if M == 0 or not beta > 0.0:
         return V[:0], H[:0, :0], 0
-    V[0] = F1.ravel() * (1.0 / beta)
+    V[0] = w * (T(1.0) / beta)
     y_flat = y.ravel()
     shape = y.shape
     f0 = F1
     meff = M
     for j in range(M):
-        w = np.asarray(sys.jvp(y_flat.reshape(shape), V[j].reshape(shape), f0, eps)).ravel()
-        wnorm0 = norm(w)
+        vj = V[j].astype(np.float64).reshape(shape)
+        w = np.asarray(sys.jvp(y_flat.reshape(shape), vj, f0, eps), dtype=T).ravel()
+        wnorm0 = norm(w, T)
         for i in range(j + 1):
-            H[i, j] = dot(V[i], w)
-            w = w - H[i, j] * V[i]
+            hij = dot(V[i], w, T)
+            H[i, j] = float(hij)
+            w = w - T(hij) * V[i]
         if j + 1 < M:
-            hn = norm(w)
-            if not hn > breakdown_tol * wnorm0:
+            hn = norm(w, T)
+            if not float(hn) > breakdown_tol * float(wnorm0):
                 meff = j + 1
                 break
-            H[j + 1, j] = hn
-            V[j + 1] = w * (1.0 / hn)
+            H[j + 1, j] = float(hn)
+            V[j + 1] = w * (T(1.0) / hn)
     return V[:meff], H[:meff, :meff], meff
 
 
@@ -138,7 +156,7 @@ def lu_solve(LU, piv, b):
     return np.array(x)
 
 
-def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=None):
+def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=None, basis=np.float64):
     """One step of the Rosenbrock-Krylov method, Eq. ROK (Sec. 2.3.3):
 
         F_i      = f(y_n + sum_{j<i} alpha_ij k_j)
@@ -150,7 +168,9 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
     with V, H from Arnoldi on K_M(J_n, f(y_n)).  The M x M system is solved by
     LU with partial pivoting (lu_factor/lu_solve); k_i is evaluated as
     V (lambda_i - h phi_i) + h F_i, the same vector grouped once; sums over the
-    basis run in basis order."""
+    basis run in basis order.  With basis = np.float32 only the basis storage and
+    Gram-Schmidt are binary32 (see arnoldi); phi, the stage solves and the stage
+    vectors read the basis exactly as binary64 and compute in binary64."""
     g = C.ROK4_GAMMA if gamma is None else gamma
     al = np.array(C.ROK4_ALPHA if alpha is None else alpha)
     gm = np.array(C.ROK4_GAMMA_OFFDIAG if gamma_off is None else gamma_off)
@@ -160,7 +180,8 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
     yf = y.ravel()
     F1 = np.asarray(sys.f(y))
     eps = fd_eps(norm(yf))
-    V, H, meff = arnoldi(sys, y, F1, M, eps)
+    V, H, meff = arnoldi(sys, y, F1, M, eps, basis=basis)
+    V = V.astype(np.float64)
     LU, piv = lu_factor(np.eye(meff) - (h * g) * H)
     ks, lams = [], []
     for i in range(s):

@@ -63,7 +63,9 @@ struct rok_ctx {
     int mmax = 0;
     cudaStream_t stream = nullptr;
     // workspace
-    double *V = nullptr;       // (mmax+1) x N basis
+    double *V = nullptr;       // (mmax+1) x N basis (binary64; also the GMRES basis)
+    float *Vf = nullptr;       // (mmax+1) x N binary32 basis of the mixed-precision ROK step
+    bool fp32 = false;
     double *F[4] = {};         // stage residuals
     double *K[4] = {};         // stage vectors
     double *w = nullptr, *t0 = nullptr, *t1 = nullptr, *t2 = nullptr;
@@ -163,6 +165,7 @@ void free_ctx(rok_ctx *c)
     for (auto &e : c->ev_used) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     for (auto &e : c->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     cudaFree(c->V);
+    cudaFree(c->Vf);
     for (int i = 0; i < 4; ++i) { cudaFree(c->F[i]); cudaFree(c->K[i]); }
     cudaFree(c->w); cudaFree(c->t0); cudaFree(c->t1); cudaFree(c->t2);
     cudaFree(c->pA); cudaFree(c->pB); cudaFree(c->pM);
@@ -358,19 +361,30 @@ rok_status arnoldi_columns(rok_ctx *c, const double *y, int M)
     StepState *st = c->st;
     cudaStream_t s = c->stream;
     rok_status r;
+    void *Vb = c->fp32 ? (void *)c->Vf : (void *)c->V;
     for (int j = 0; j < M; ++j) {
-        StencilIO io = io_jvp(c, y, c->V + (size_t)j * N, c->F[0], c->w);
+        StencilIO io;
+        if (c->fp32) {
+            io = io_plain(c, y, c->w);
+            io.addf = c->Vf + (size_t)j * N;
+            io.coef_f = 1.0;
+            io.coef_f_dev = &st->eps;
+            io.sub = c->F[0];
+            io.s1_dev = &st->inv_eps;
+        } else {
+            io = io_jvp(c, y, c->V + (size_t)j * N, c->F[0], c->w);
+        }
         io.active = &st->active;
         if ((r = stencil(c, io)) != ROK_OK) return r;
         cudaError_t e = cudaErrorNotSupported;
-        if (c->col_ctas > 0 && !c->capturing)
-            e = c->ops->arnoldi_column(c->w, c->V, N, N, j, j + 1 < M ? 1 : 0, P, c->pA, c->pB, c->bar, st,
-                                       c->col_ctas, s);
+        if (c->col_ctas > 0)
+            e = c->ops->arnoldi_column(c->w, Vb, c->fp32 ? 1 : 0, N, N, j, j + 1 < M ? 1 : 0, P, c->pA, c->pB,
+                                       c->bar, st, c->col_ctas, s);
         if (e == cudaSuccess) {
             c->launches++;
             continue;
         }
-        if (e != cudaErrorNotSupported) return ROK_ERR_CUDA;
+        if (e != cudaErrorNotSupported || c->fp32) return ROK_ERR_CUDA;
         (void)cudaGetLastError();
         // <v_1, w> and ||w||^2
         CU(c->ops->dot2(c->V, c->w, c->w, c->w, N, c->pA, P, &st->active, s));
@@ -410,10 +424,10 @@ rok_status enqueue_rok_body(rok_ctx *c, double *y, int M)
     CU(c->ops->dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
     CU(c->ops->eps(c->pA, P, true, 0.0, st, s));
     c->launches += 2;
+    void *Vb = c->fp32 ? (void *)c->Vf : (void *)c->V;
     if (M > 0) {
-        // v_1 = F1 / ||F1||
-        CU(c->ops->dot2(c->F[0], c->F[0], nullptr, nullptr, N, c->pA, P, nullptr, s));
-        CU(c->ops->normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
+        // v_1 = F1 / ||F1|| (in the basis precision)
+        CU(c->ops->first_vector(c->F[0], Vb, c->fp32 ? 1 : 0, N, c->pA, P, st, s));
         c->launches += 2;
         rok_status ra = arnoldi_columns(c, y, M);
         if (ra != ROK_OK) return ra;
@@ -432,11 +446,11 @@ rok_status enqueue_rok_body(rok_ctx *c, double *y, int M)
             if ((r = stencil(c, io)) != ROK_OK) return r;
         }
         if (M > 0) {
-            CU(c->ops->multidot(c->F[i], c->V, N, N, c->pM, P, st, s));
+            CU(c->ops->multidot(c->F[i], Vb, c->fp32 ? 1 : 0, N, N, c->pM, P, st, s));
             CU(c->ops->stage_solve(i, kRokGammaOff[i], c->pM, P, st, s));
             c->launches += 2;
         }
-        CU(c->ops->stage_vec(c->K[i], c->F[i], c->V, N, N, i, st, c->egrid, s));
+        CU(c->ops->stage_vec(c->K[i], c->F[i], Vb, c->fp32 ? 1 : 0, N, N, i, st, c->egrid, s));
         c->launches++;
     }
     const double *kv[4] = {c->K[0], c->K[1], c->K[2], c->K[3]};
@@ -534,6 +548,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     if (d->kind < ROK_EULER2D || d->kind > ROK_LORENZ96) return ROK_ERR_INVALID_ARG;
     if (d->krylov_max < 0 || d->krylov_max > kMaxKrylov) return ROK_ERR_INVALID_ARG;
     if (d->rounding != ROK_ROUND_FAST && d->rounding != ROK_ROUND_STRICT) return ROK_ERR_INVALID_ARG;
+    if (d->basis != ROK_BASIS_FP64 && d->basis != ROK_BASIS_FP32) return ROK_ERR_INVALID_ARG;
     if (d->kind == ROK_LORENZ96) {
         if (d->nx < 4) return ROK_ERR_INVALID_ARG;
     } else {
@@ -559,6 +574,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     c->kind = d->kind;
     c->strict = d->rounding == ROK_ROUND_STRICT;
     c->curv = d->kind != ROK_LORENZ96 && d->xv != nullptr;
+    c->fp32 = d->basis == ROK_BASIS_FP32;
     c->stream = (cudaStream_t)stream;
     c->mmax = d->krylov_max;
     c->nc = d->kind == ROK_LORENZ96 ? (size_t)d->nx : (size_t)d->nx * d->ny;
@@ -605,6 +621,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
               al(&c->t2, N) && al(&c->pA, 2 * (size_t)c->P) && al(&c->pB, 2 * (size_t)c->P) &&
               al(&c->pM, (size_t)kMaxKrylov * c->P);
     for (int i = 0; i < 4 && ok; ++i) ok = al(&c->F[i], N) && al(&c->K[i], N);
+    if (ok && c->fp32) ok = cudaMalloc(&c->Vf, (size_t)(c->mmax + 1) * N * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->st, sizeof(StepState)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->bar, sizeof(GridBarrier)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_st, sizeof(StepState)) == cudaSuccess;
@@ -613,6 +630,11 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     if (cudaMemset(c->st, 0, sizeof(StepState)) != cudaSuccess) { free_ctx(c); return ROK_ERR_CUDA; }
     if (cudaMemset(c->bar, 0, sizeof(GridBarrier)) != cudaSuccess) { free_ctx(c); return ROK_ERR_CUDA; }
     c->col_ctas = c->ops->arnoldi_column_ctas(sms);
+    if (c->fp32 && (c->col_ctas <= 0 || (c->P + c->col_ctas - 1) / c->col_ctas > 2)) {
+        // the binary32 basis runs on the persistent column kernel only
+        free_ctx(c);
+        return ROK_ERR_UNSUPPORTED;
+    }
     memset(c->h_st, 0, sizeof(StepState));
     if (c->curv) {
         c->d.xv = d->xv; c->d.yv = d->yv;   // used only while building the metrics
@@ -678,15 +700,15 @@ rok_status rok_arnoldi(rok_ctx *c, const double *y, int M, double *Vout, double 
     if (r != ROK_OK) return r;
     CU(c->ops->dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
     CU(c->ops->eps(c->pA, P, true, 0.0, st, s));
-    CU(c->ops->dot2(c->F[0], c->F[0], nullptr, nullptr, N, c->pA, P, nullptr, s));
-    CU(c->ops->normalize(c->F[0], c->V, N, c->pA, P, nullptr, 0, st, s));
+    CU(c->ops->first_vector(c->F[0], c->fp32 ? (void *)c->Vf : (void *)c->V, c->fp32 ? 1 : 0, N, c->pA, P, st, s));
     CU(cudaMemsetAsync(st->H, 0, sizeof(st->H), s));
     c->launches += 5;
     if ((r = arnoldi_columns(c, y, M)) != ROK_OK) return r;
     r = sync_read(c, nullptr);
     int me = c->h_st->meff;
     *m_eff = me;
-    CU(cudaMemcpyAsync(Vout, c->V, (size_t)me * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (c->fp32) CU(launch_f2d(c->Vf, Vout, (size_t)me * N, s));   // exact widening
+    else CU(cudaMemcpyAsync(Vout, c->V, (size_t)me * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CU(cudaMemcpy2DAsync(Hout, M * sizeof(double), st->H, kMaxKrylov * sizeof(double), M * sizeof(double), M,
                          cudaMemcpyDeviceToDevice, s));
     CU(cudaStreamSynchronize(s));

@@ -43,16 +43,16 @@ struct LinalgOps {
     // hn = sqrt(tree(pin)); breakdown / beta tests; v = w * (1/hn); *hsub = hn (nullable)
     cudaError_t (*normalize)(const double *w, double *v, size_t n, const double *pin, int P, double *hsub,
                              int column, StepState *st, cudaStream_t s);
-    // pout[m*P + b] = <V_m, F> over CTA b's entries, m < meff
-    cudaError_t (*multidot)(const double *F, const double *V, size_t ldv, size_t n, double *pout, int P,
+    // pout[m*P + b] = <V_m, F> over CTA b's entries, m < meff; V binary64 or (fp32) binary32
+    cudaError_t (*multidot)(const double *F, const void *V, int fp32, size_t ldv, size_t n, double *pout, int P,
                             const StepState *st, cudaStream_t s);
     // stage i: phi, rhs = h phi + h H sum_j gam_ij lam_j, lam_i by LU, cvec_i = lam_i - h phi
     cudaError_t (*stage_solve)(int stage, const double *gam_row, const double *pin, int P, StepState *st,
                                cudaStream_t s);
     // LU with partial pivoting of I - h g H (meff x meff)
     cudaError_t (*lu)(StepState *st, cudaStream_t s);
-    // k = sum_m cvec[stage][m] V_m + h F
-    cudaError_t (*stage_vec)(double *k, const double *F, const double *V, size_t ldv, size_t n, int stage,
+    // k = sum_m cvec[stage][m] V_m + h F (V binary64 or binary32, arithmetic binary64)
+    cudaError_t (*stage_vec)(double *k, const double *F, const void *V, int fp32, size_t ldv, size_t n, int stage,
                              const StepState *st, int grid, cudaStream_t s);
     // out = base + sum_q c_q v_q (count <= 8, host coefficients); skipped when guard->status != 0
     cudaError_t (*axpy_n)(double *out, const double *base, const double *const *v, const double *c, int count,
@@ -70,11 +70,15 @@ struct LinalgOps {
     // registers between passes; partA/partB hold 2P partials each.  Same
     // arithmetic as dot2 + mgs + normalize.  Returns cudaErrorNotSupported when
     // the ctas cannot cover the P chunks (caller falls back).
-    cudaError_t (*arnoldi_column)(double *w, double *V, size_t ldv, size_t n, int j, int next, int P,
+    // fp32: the basis V is binary32 and the Gram-Schmidt arithmetic binary32 (w rounded on load)
+    cudaError_t (*arnoldi_column)(const double *w, void *V, int fp32, size_t ldv, size_t n, int j, int next, int P,
                                   double *partA, double *partB, GridBarrier *bar, StepState *st, int ctas,
                                   cudaStream_t s);
     // co-resident CTAs of arnoldi_column on this device (0 if cooperative launch is unavailable)
     int (*arnoldi_column_ctas)(int sms);
+    // v_1 = (T)F1 / ||(T)F1|| (T = binary64 or binary32); beta = 0: empty basis
+    cudaError_t (*first_vector)(const double *F, void *V0, int fp32, size_t n, double *partials, int P,
+                                StepState *st, cudaStream_t s);
 };
 
 namespace fast {
@@ -89,6 +93,8 @@ inline int reduction_blocks(size_t n) { return n ? (int)((n + 2047) / 2048) : 1;
 
 // ---- rounding-independent helpers (linalg_common.cu) -----------------------------
 cudaError_t launch_set_int(int *p, int v, cudaStream_t s);
+// dst = (double) src, n entries (exact widening)
+cudaError_t launch_f2d(const float *src, double *dst, size_t n, cudaStream_t s);
 // begin a step: h, hg, meff = M, active = (M > 0)
 cudaError_t launch_begin(StepState *st, double h, double gamma, int M, cudaStream_t s);
 // dt from CFL: per-cell spectral-radius bound, max reduction (order independent)

@@ -23,6 +23,11 @@ __global__ void begin_kernel(StepState *st, double h, double gamma, int M)
 
 __global__ void set_int_kernel(int *p, int v) { *p = v; }
 
+__global__ void f2d_kernel(const float *src, double *dst, size_t n)
+{
+    for (size_t e = gtid(); e < n; e += gstride()) dst[e] = (double)src[e];
+}
+
 __global__ void cfl_kernel(const double *y, const StencilConsts C, const double *six, const double *siy,
                            const double *sjx, const double *sjy, const double *vol, double *pmax)
 {
@@ -67,6 +72,12 @@ __global__ void cfl_kernel(const double *y, const StencilConsts C, const double 
 cudaError_t launch_set_int(int *p, int v, cudaStream_t s)
 {
     set_int_kernel<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f2d(const float *src, double *dst, size_t n, cudaStream_t s)
+{
+    f2d_kernel<<<1024, 256, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ constexpr int RB = RT * EPL;       // entries per CTA (2048)
 
 __device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
-// x[0..8) = p[e0 .. e0+8) (zero beyond n)
+// x[0..8) = p[e0 .. e0+8) (zero beyond n); 16-byte vector loads when aligned
 __device__ __forceinline__ void load8(const double *__restrict__ p, size_t e0, size_t n, double (&x)[EPL])
 {
     if (e0 + EPL <= n && aligned16(p)) {
@@ -56,6 +56,24 @@ __device__ __forceinline__ void load8(const double *__restrict__ p, size_t e0, s
     }
 }
 
+__device__ __forceinline__ void load8(const float *__restrict__ p, size_t e0, size_t n, float (&x)[EPL])
+{
+    if (e0 + EPL <= n && aligned16(p + e0)) {
+        const float4 *q = reinterpret_cast<const float4 *>(p + e0);
+#pragma unroll
+        for (int k = 0; k < EPL / 4; ++k) {
+            float4 t = q[k];
+            x[4 * k] = t.x;
+            x[4 * k + 1] = t.y;
+            x[4 * k + 2] = t.z;
+            x[4 * k + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = e0 + k < n ? p[e0 + k] : 0.0f;
+    }
+}
+
 __device__ __forceinline__ void store8(double *__restrict__ p, size_t e0, size_t n, const double (&x)[EPL])
 {
     if (e0 + EPL <= n && aligned16(p)) {
@@ -69,28 +87,44 @@ __device__ __forceinline__ void store8(double *__restrict__ p, size_t e0, size_t
     }
 }
 
+__device__ __forceinline__ void store8(float *__restrict__ p, size_t e0, size_t n, const float (&x)[EPL])
+{
+    if (e0 + EPL <= n && aligned16(p + e0)) {
+        float4 *q = reinterpret_cast<float4 *>(p + e0);
+#pragma unroll
+        for (int k = 0; k < EPL / 4; ++k) q[k] = make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k)
+            if (e0 + k < n) p[e0 + k] = x[k];
+    }
+}
+
 // tree over the 8 consecutive entries of a lane
-__device__ __forceinline__ double tree8(const double (&x)[EPL])
+template <class T>
+__device__ __forceinline__ T tree8(const T (&x)[EPL])
 {
     return ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
 }
 
-__device__ __forceinline__ double lane_tree(double v)
+template <class T>
+__device__ __forceinline__ T lane_tree(T v)
 {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// tree over the 8 warp sums of a CTA; sh >= 9 doubles; result in every thread
-__device__ __forceinline__ double cta_tree(double wsum, double *sh)
+// tree over the 8 warp sums of a CTA; sh >= 9 values; result in every thread
+template <class T>
+__device__ __forceinline__ T cta_tree(T wsum, T *sh)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) sh[wid] = wsum;
     __syncthreads();
     if (wid == 0) {
-        double v = lane < 8 ? sh[lane] : 0.0;
+        T v = lane < 8 ? sh[lane] : T(0);
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
         v += __shfl_xor_sync(0xffffffffu, v, 4);
@@ -100,9 +134,10 @@ __device__ __forceinline__ double cta_tree(double wsum, double *sh)
     return sh[8];
 }
 
-// CTA sum of one value per lane-chunk: the 8 entries of the lane, then the
-// lane butterfly, then the warp tree
-__device__ __forceinline__ double chunk_sum(const double (&x)[EPL], double *sh)
+// CTA sum of one 8-entry chunk per lane: the lane's entries, the lane
+// butterfly, then the warp tree
+template <class T>
+__device__ __forceinline__ T chunk_sum(const T (&x)[EPL], T *sh)
 {
     return cta_tree(lane_tree(tree8(x)), sh);
 }
@@ -110,12 +145,12 @@ __device__ __forceinline__ double chunk_sum(const double (&x)[EPL], double *sh)
 // Aligned tree over the C consecutive leaves p[lo .. lo + C) (zero beyond P),
 // C a power of two: up to 32 leaves are loaded at once (independent loads) and
 // added level by level; longer runs use a carry stack over the leaves in order.
-template <int L>
-__device__ __forceinline__ double leaf_tree_fixed(const double *__restrict__ p, int lo, int P)
+template <int L, class T>
+__device__ __forceinline__ T leaf_tree_fixed(const T *__restrict__ p, int lo, int P)
 {
-    double x[L];
+    T x[L];
 #pragma unroll
-    for (int k = 0; k < L; ++k) x[k] = lo + k < P ? p[lo + k] : 0.0;
+    for (int k = 0; k < L; ++k) x[k] = lo + k < P ? p[lo + k] : T(0);
 #pragma unroll
     for (int len = L; len > 1; len >>= 1)
 #pragma unroll
@@ -123,10 +158,11 @@ __device__ __forceinline__ double leaf_tree_fixed(const double *__restrict__ p, 
     return x[0];
 }
 
-__device__ __forceinline__ double leaf_tree(const double *__restrict__ p, int lo, int C, int P)
+template <class T>
+__device__ __forceinline__ T leaf_tree(const T *__restrict__ p, int lo, int C, int P)
 {
     switch (C) {
-    case 1: return lo < P ? p[lo] : 0.0;
+    case 1: return lo < P ? p[lo] : T(0);
     case 2: return leaf_tree_fixed<2>(p, lo, P);
     case 4: return leaf_tree_fixed<4>(p, lo, P);
     case 8: return leaf_tree_fixed<8>(p, lo, P);
@@ -134,9 +170,9 @@ __device__ __forceinline__ double leaf_tree(const double *__restrict__ p, int lo
     case 32: return leaf_tree_fixed<32>(p, lo, P);
     default: break;
     }
-    double stack[24];
+    T stack[24];
     for (int k = 0; k < C; ++k) {
-        double s = lo + k < P ? p[lo + k] : 0.0;
+        T s = lo + k < P ? p[lo + k] : T(0);
         int lvl = 0;
         for (int m = k; m & 1; m >>= 1, ++lvl) s = stack[lvl] + s;
         stack[lvl] = s;
@@ -155,7 +191,8 @@ __device__ __forceinline__ int pow2_ceil(int P)
 
 // Tree sum of p[0..P) (zero-padded to a power of two) by one warp: lane l owns
 // the C = P2/32 consecutive leaves [lC, lC + C), then the lane butterfly.
-__device__ __forceinline__ double warp_tree_partials(const double *__restrict__ p, int P)
+template <class T>
+__device__ __forceinline__ T warp_tree_partials(const T *__restrict__ p, int P)
 {
     const int P2 = pow2_ceil(P);
     const int lane = threadIdx.x & 31;
@@ -165,7 +202,8 @@ __device__ __forceinline__ double warp_tree_partials(const double *__restrict__ 
 
 // The same tree by the whole CTA (thread t owns C = P2/256 leaves), result in
 // every thread.
-__device__ __forceinline__ double tree_partials(const double *__restrict__ p, int P, double *sh)
+template <class T>
+__device__ __forceinline__ T tree_partials(const T *__restrict__ p, int P, T *sh)
 {
     const int P2 = pow2_ceil(P);
     const int C = P2 > RT ? P2 / RT : 1;
@@ -272,8 +310,10 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double *__restrict_
     store8(v, e0, n, x);
 }
 
-// pout[m * P + b] = <V_m, F> over CTA b's range, m < meff
-__global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__ F, const double *__restrict__ V,
+// pout[m * P + b] = <V_m, F> over CTA b's range, m < meff (basis entries read
+// exactly as binary64; products and tree in binary64)
+template <class T>
+__global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__ F, const T *__restrict__ V,
                                                       size_t ldv, size_t n, double *__restrict__ pout, int P,
                                                       const StepState *st)
 {
@@ -283,10 +323,11 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__
     double f[EPL];
     load8(F, e0, n, f);
     for (int i = 0; i < m; ++i) {
+        T v[EPL];
+        load8(V + (size_t)i * ldv, e0, n, v);
         double x[EPL];
-        load8(V + (size_t)i * ldv, e0, n, x);
 #pragma unroll
-        for (int k = 0; k < EPL; ++k) x[k] = x[k] * f[k];
+        for (int k = 0; k < EPL; ++k) x[k] = (double)v[k] * f[k];
         double s = chunk_sum(x, sh);
         if (threadIdx.x == 0) pout[(size_t)i * P + blockIdx.x] = s;
     }
@@ -331,18 +372,22 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks,
     return ok != 0;
 }
 
-__global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(double *__restrict__ w, double *__restrict__ V,
+// One Arnoldi column in one cooperative launch.  T is the basis type: double
+// (plain path) or float (mixed path: basis storage and Gram-Schmidt in binary32;
+// the binary64 JVP result w is rounded to T on load; H is stored in binary64).
+template <class T>
+__global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__restrict__ w, T *__restrict__ V,
                                                                size_t ldv, size_t n, int j, int next, int P,
-                                                               double *partA, double *partB, GridBarrier *bar,
-                                                               StepState *st)
+                                                               T *partA, T *partB, GridBarrier *bar,
+                                                               StepState *st, double brk_tol)
 {
-    __shared__ double sh[10];
+    __shared__ T sh[10];
     __shared__ int act;
     if (threadIdx.x == 0) act = st->active;
     __syncthreads();
     if (act == 0) return;
     const unsigned G = gridDim.x;
-    double wv[kColChunks][EPL], vn[kColChunks][EPL];
+    T wv[kColChunks][EPL], vn[kColChunks][EPL];
     size_t e0[kColChunks];
     bool have[kColChunks];
 #pragma unroll
@@ -351,7 +396,10 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(double *__restric
         have[c] = b < P;
         e0[c] = ((size_t)b * RT + threadIdx.x) * EPL;
         if (have[c]) {
-            load8(w, e0[c], n, wv[c]);
+            double wd[EPL];
+            load8(w, e0[c], n, wd);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) wv[c][k] = (T)wd[k];
             load8(V, e0[c], n, vn[c]);     // v_0
         }
     }
@@ -359,52 +407,50 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(double *__restric
 #pragma unroll
     for (int c = 0; c < kColChunks; ++c) {
         if (!have[c]) continue;   // uniform per CTA
-        double x[EPL], y[EPL];
+        T x[EPL], y[EPL];
 #pragma unroll
         for (int k = 0; k < EPL; ++k) {
             x[k] = vn[c][k] * wv[c][k];
             y[k] = wv[c][k] * wv[c][k];
         }
-        double s0 = chunk_sum(x, sh);
-        double s1 = chunk_sum(y, sh);
+        T s0 = chunk_sum(x, sh);
+        T s1 = chunk_sum(y, sh);
         if (threadIdx.x == 0) {
             partA[blockIdx.x + c * G] = s0;
             partA[P + blockIdx.x + c * G] = s1;
         }
     }
-    double *pin = partA, *pout = partB;
+    T *pin = partA, *pout = partB;
     if (!grid_barrier(bar, G, &st->status)) return;
+    T wnorm0 = T(0);
     for (int i = 0; i <= j; ++i) {
-        const double h = tree_partials(pin, P, sh);
-        if (i == 0) {
-            const double wn2 = tree_partials(pin + P, P, sh);
-            if (blockIdx.x == 0 && threadIdx.x == 0) st->wnorm0 = sqrt(wn2);
+        const T h = tree_partials(pin, P, sh);
+        if (i == 0) wnorm0 = sqrt(tree_partials(pin + P, P, sh));
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->H[i * kMaxKrylov + j] = (double)h;
+            if (i == 0) st->wnorm0 = (double)wnorm0;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->H[i * kMaxKrylov + j] = h;
-        const double *vnext = i < j ? V + (size_t)(i + 1) * ldv : nullptr;
+        const T *vnext = i < j ? V + (size_t)(i + 1) * ldv : nullptr;
 #pragma unroll
         for (int c = 0; c < kColChunks; ++c) {
             if (!have[c]) continue;
 #pragma unroll
             for (int k = 0; k < EPL; ++k) wv[c][k] = wv[c][k] - h * vn[c][k];
             if (vnext) load8(vnext, e0[c], n, vn[c]);
-            double x[EPL];
+            T x[EPL];
 #pragma unroll
             for (int k = 0; k < EPL; ++k) x[k] = vnext ? vn[c][k] * wv[c][k] : wv[c][k] * wv[c][k];
-            double s = chunk_sum(x, sh);
+            T s = chunk_sum(x, sh);
             if (threadIdx.x == 0) pout[blockIdx.x + c * G] = s;
         }
         if (!grid_barrier(bar, G, &st->status)) return;
-        double *t = pin;
+        T *t = pin;
         pin = pout;
         pout = t;
     }
-    if (!next) {
-        // last column: the orthogonalised w is not needed further
-        return;
-    }
-    const double hn = sqrt(tree_partials(pin, P, sh));
-    const bool brk = !(hn > 1e-12 * st->wnorm0);
+    if (!next) return;   // last column: the orthogonalised w is not needed further
+    const T hn = sqrt(tree_partials(pin, P, sh));
+    const bool brk = !((double)hn > brk_tol * (double)wnorm0);
     if (brk) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->active = 0;
@@ -412,38 +458,110 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(double *__restric
         }
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->H[(j + 1) * kMaxKrylov + j] = hn;
-    const double r = 1.0 / hn;
-    double *vout = V + (size_t)(j + 1) * ldv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->H[(j + 1) * kMaxKrylov + j] = (double)hn;
+    const T r = T(1) / hn;
+    T *vout = V + (size_t)(j + 1) * ldv;
 #pragma unroll
     for (int c = 0; c < kColChunks; ++c) {
         if (!have[c]) continue;
-        double x[EPL];
+        T x[EPL];
 #pragma unroll
         for (int k = 0; k < EPL; ++k) x[k] = wv[c][k] * r;
         store8(vout, e0[c], n, x);
     }
 }
 
-static int arnoldi_column_ctas(int sms)
+// First basis vector: partials of ||(T)F1||^2 ...
+template <class T>
+__global__ void __launch_bounds__(RT) first_partials_kernel(const double *__restrict__ F, size_t n, T *partials)
 {
-    int dev = 0, coop = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_column_kernel, RT, 0) != cudaSuccess)
-        return 0;
-    return per_sm * sms;
+    __shared__ T sh[10];
+    const size_t e0 = lane_e0();
+    double fd[EPL];
+    load8(F, e0, n, fd);
+    T x[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+        T t = (T)fd[k];
+        x[k] = t * t;
+    }
+    T s = chunk_sum(x, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-static cudaError_t arnoldi_column(double *w, double *V, size_t ldv, size_t n, int j, int next, int P,
+// ... then beta = sqrt(tree), v_1 = (T)F1 * (1/beta); beta = 0 leaves an empty basis
+template <class T>
+__global__ void __launch_bounds__(RT) first_normalize_kernel(const double *__restrict__ F, T *__restrict__ V0,
+                                                             size_t n, const T *partials, int P, StepState *st)
+{
+    __shared__ T sh[10];
+    __shared__ int act;
+    if (threadIdx.x == 0) act = st->active;
+    __syncthreads();
+    if (act == 0) return;
+    const T beta = sqrt(tree_partials(partials, P, sh));
+    if (!(beta > T(0))) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->active = 0;
+            st->meff = 0;
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->beta = (double)beta;
+    const T r = T(1) / beta;
+    const size_t e0 = lane_e0();
+    double fd[EPL];
+    load8(F, e0, n, fd);
+    T x[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) x[k] = (T)fd[k] * r;
+    store8(V0, e0, n, x);
+}
+
+static int arnoldi_column_ctas(int sms)
+{
+    int dev = 0, coop = 0, p64 = 0, p32 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, arnoldi_column_kernel<double>, RT, 0) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, arnoldi_column_kernel<float>, RT, 0) != cudaSuccess)
+        return 0;
+    return (p64 < p32 ? p64 : p32) * sms;
+}
+
+static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv, size_t n, int j, int next, int P,
                                   double *partA, double *partB, GridBarrier *bar, StepState *st, int ctas,
                                   cudaStream_t s)
 {
     if (ctas <= 0) return cudaErrorNotSupported;
     const int G = P < ctas ? P : ctas;
     if ((P + G - 1) / G > kColChunks) return cudaErrorNotSupported;
-    void *args[] = {&w, &V, &ldv, &n, &j, &next, &P, &partA, &partB, &bar, &st};
-    return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel, dim3(G), dim3(RT), args, 0, s);
+    if (fp32) {
+        float *Vf = static_cast<float *>(V);
+        float *pa = reinterpret_cast<float *>(partA), *pb = reinterpret_cast<float *>(partB);
+        double tol = 1e-5;
+        void *args[] = {&w, &Vf, &ldv, &n, &j, &next, &P, &pa, &pb, &bar, &st, &tol};
+        return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<float>, dim3(G), dim3(RT), args, 0, s);
+    }
+    double *Vd = static_cast<double *>(V);
+    double tol = 1e-12;
+    void *args[] = {&w, &Vd, &ldv, &n, &j, &next, &P, &partA, &partB, &bar, &st, &tol};
+    return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<double>, dim3(G), dim3(RT), args, 0, s);
+}
+
+static cudaError_t first_vector(const double *F, void *V0, int fp32, size_t n, double *partials, int P,
+                                StepState *st, cudaStream_t s)
+{
+    if (fp32) {
+        float *pf = reinterpret_cast<float *>(partials);
+        first_partials_kernel<float><<<P, RT, 0, s>>>(F, n, pf);
+        first_normalize_kernel<float><<<P, RT, 0, s>>>(F, static_cast<float *>(V0), n, pf, P, st);
+    } else {
+        first_partials_kernel<double><<<P, RT, 0, s>>>(F, n, partials);
+        first_normalize_kernel<double><<<P, RT, 0, s>>>(F, static_cast<double *>(V0), n, partials, P, st);
+    }
+    return cudaGetLastError();
 }
 
 // One warp: LU with partial pivoting of L = I - h g H (first largest |pivot|),
@@ -548,9 +666,11 @@ __global__ void stage_solve_kernel(int stage, GamRow gr, const double *pin, int 
     }
 }
 
-// k = sum_{i<meff} cvec[stage][i] V_i + h F (basis order)
-__global__ void __launch_bounds__(RT) stage_vec_kernel(double *k, const double *F, const double *V, size_t ldv,
-                                                       size_t n, int stage, const StepState *st)
+// k = sum_{i<meff} cvec[stage][i] V_i + h F (basis order, binary64)
+template <class T>
+__global__ void __launch_bounds__(RT) stage_vec_kernel(double *__restrict__ k, const double *__restrict__ F,
+                                                       const T *__restrict__ V, size_t ldv, size_t n, int stage,
+                                                       const StepState *st)
 {
     __shared__ double c[kMaxKrylov];
     const int m = st->meff;
@@ -559,7 +679,7 @@ __global__ void __launch_bounds__(RT) stage_vec_kernel(double *k, const double *
     __syncthreads();
     for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
         double a = 0.0;
-        for (int i = 0; i < m; ++i) a = a + c[i] * V[(size_t)i * ldv + e];
+        for (int i = 0; i < m; ++i) a = a + c[i] * (double)V[(size_t)i * ldv + e];
         k[e] = a + h * F[e];
     }
 }
@@ -647,10 +767,11 @@ static cudaError_t normalize(const double *w, double *v, size_t n, const double 
     return cudaGetLastError();
 }
 
-static cudaError_t multidot(const double *F, const double *V, size_t ldv, size_t n, double *pout, int P,
+static cudaError_t multidot(const double *F, const void *V, int fp32, size_t ldv, size_t n, double *pout, int P,
                             const StepState *st, cudaStream_t s)
 {
-    multidot_kernel<<<P, RT, 0, s>>>(F, V, ldv, n, pout, P, st);
+    if (fp32) multidot_kernel<float><<<P, RT, 0, s>>>(F, static_cast<const float *>(V), ldv, n, pout, P, st);
+    else multidot_kernel<double><<<P, RT, 0, s>>>(F, static_cast<const double *>(V), ldv, n, pout, P, st);
     return cudaGetLastError();
 }
 
@@ -669,10 +790,11 @@ static cudaError_t lu(StepState *st, cudaStream_t s)
     return cudaGetLastError();
 }
 
-static cudaError_t stage_vec(double *k, const double *F, const double *V, size_t ldv, size_t n, int stage,
+static cudaError_t stage_vec(double *k, const double *F, const void *V, int fp32, size_t ldv, size_t n, int stage,
                              const StepState *st, int grid, cudaStream_t s)
 {
-    stage_vec_kernel<<<grid, RT, 0, s>>>(k, F, V, ldv, n, stage, st);
+    if (fp32) stage_vec_kernel<float><<<grid, RT, 0, s>>>(k, F, static_cast<const float *>(V), ldv, n, stage, st);
+    else stage_vec_kernel<double><<<grid, RT, 0, s>>>(k, F, static_cast<const double *>(V), ldv, n, stage, st);
     return cudaGetLastError();
 }
 
@@ -709,7 +831,7 @@ static cudaError_t sum_sqrt(const double *pin, int P, double *dst, cudaStream_t 
 }
 
 const LinalgOps ops = {dot2, mgs, normalize, multidot, stage_solve, lu, stage_vec, axpy_n, basis_combine, eps,
-                       sum_sqrt, arnoldi_column, arnoldi_column_ctas};
+                       sum_sqrt, arnoldi_column, arnoldi_column_ctas, first_vector};
 
 }  // namespace ROK_NS
 }  // namespace rok

@@ -53,7 +53,8 @@ struct CurvGeom {
 };
 
 // Inputs and epilogue of one stencil launch:
-//   state = base + sum_t c_t add_t                (c_t from coef or *coef_dev)
+//   state = base + sum_t c_t add_t [+ cf addf]     (c_t from coef or *coef_dev;
+//                                                  addf: a binary32 vector, read exactly)
 //   t     = (sub ? r - sub : r) * s1              (s1 times *s1_dev if given)
 //   out   = add_out ? add_out + s2 t : t          (s2 times *s2_dev if given)
 struct StencilIO {
@@ -62,6 +63,9 @@ struct StencilIO {
     double coef[kMaxAdd];
     const double *coef_dev[kMaxAdd];
     int nadd;
+    const float *addf;         // nullable binary32 term (mixed-precision Krylov basis)
+    double coef_f;
+    const double *coef_f_dev;
     const double *sub;
     double s1;
     const double *s1_dev;

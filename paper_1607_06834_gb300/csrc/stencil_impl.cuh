@@ -200,10 +200,11 @@ __device__ __forceinline__ void store_prim(Tile &t, int ly, int lx, double rho, 
     }
 }
 
-__device__ __forceinline__ double load_state(const StencilIO &io, const double (&cf)[kMaxAdd], size_t e)
+__device__ __forceinline__ double load_state(const StencilIO &io, const double (&cf)[kMaxAdd], double cff, size_t e)
 {
     double q = io.base[e];
     for (int t = 0; t < io.nadd; ++t) q = q + cf[t] * io.add[t][e];
+    if (io.addf) q = q + cff * (double)io.addf[e];
     return q;
 }
 
@@ -223,10 +224,11 @@ __device__ __forceinline__ void epilogue_store(const StencilIO &io, double s1, d
     if (!isfinite(o)) atomicOr(io.status, kStatusNonfinite);
 }
 
-__device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd], double &s1, double &s2)
+__device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd], double &cff, double &s1, double &s2)
 {
 #pragma unroll
     for (int t = 0; t < kMaxAdd; ++t) cf[t] = io.coef_dev[t] ? io.coef[t] * *io.coef_dev[t] : io.coef[t];
+    cff = io.coef_f_dev ? io.coef_f * *io.coef_f_dev : io.coef_f;
     s1 = io.s1_dev ? io.s1 * *io.s1_dev : io.s1;
     s2 = io.s2_dev ? io.s2 * *io.s2_dev : io.s2;
 }
@@ -244,17 +246,17 @@ __global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, cons
     const size_t nc = (size_t)nx * ny;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int tid = threadIdx.x;
-    double cf[kMaxAdd], s1, s2;
-    coefs(io, cf, s1, s2);
+    double cf[kMaxAdd], cff, s1, s2;
+    coefs(io, cf, cff, s1, s2);
 
     for (int idx = tid; idx < EW * EH; idx += NT) {
         int lx = idx % EW, ly = idx / EW;
         int gi = wrapi(i0 + lx - 2, nx), gj = wrapi(j0 + ly - 2, ny);
         size_t c = (size_t)gj * nx + gi;
-        double rho = load_state(io, cf, c);
-        double mx = load_state(io, cf, nc + c);
-        double my = load_state(io, cf, 2 * nc + c);
-        double E = load_state(io, cf, 3 * nc + c);
+        double rho = load_state(io, cf, cff, c);
+        double mx = load_state(io, cf, cff, nc + c);
+        double my = load_state(io, cf, cff, 2 * nc + c);
+        double E = load_state(io, cf, cff, 3 * nc + c);
         store_prim<SUTH>(tl, ly, lx, rho, mx, my, E, false, C);
     }
     __syncthreads();
@@ -350,8 +352,8 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
     const size_t nc = (size_t)nx * ny;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int tid = threadIdx.x;
-    double cf[kMaxAdd], s1, s2;
-    coefs(io, cf, s1, s2);
+    double cf[kMaxAdd], cff, s1, s2;
+    coefs(io, cf, cff, s1, s2);
 
     for (int idx = tid; idx < EW * EH; idx += NT) {
         int lx = idx % EW, ly = idx / EW;
@@ -382,10 +384,10 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
             if (SUTH) tl.mu[ly][lx] = C.prim_inf[5];
         } else {
             size_t c = (size_t)gj * nx + gi;
-            double rho = load_state(io, cf, c);
-            double mx = load_state(io, cf, nc + c);
-            double my = load_state(io, cf, 2 * nc + c);
-            double E = load_state(io, cf, 3 * nc + c);
+            double rho = load_state(io, cf, cff, c);
+            double mx = load_state(io, cf, cff, nc + c);
+            double my = load_state(io, cf, cff, 2 * nc + c);
+            double E = load_state(io, cf, cff, 3 * nc + c);
             store_prim<SUTH>(tl, ly, lx, rho, mx, my, E, mirror, C);
         }
     }
@@ -533,10 +535,12 @@ __global__ void lorenz_kernel(const StencilConsts C, const StencilIO io, int n)
     for (int t = 0; t < kMaxAdd; ++t) cf[t] = io.coef_dev[t] ? io.coef[t] * *io.coef_dev[t] : io.coef[t];
     const double s1 = io.s1_dev ? io.s1 * *io.s1_dev : io.s1;
     const double s2 = io.s2_dev ? io.s2 * *io.s2_dev : io.s2;
+    const double cff = io.coef_f_dev ? io.coef_f * *io.coef_f_dev : io.coef_f;
     auto q = [&](int i) {
         i = (i % n + n) % n;
         double v = io.base[i];
         for (int t = 0; t < io.nadd; ++t) v = v + cf[t] * io.add[t][i];
+        if (io.addf) v = v + cff * (double)io.addf[i];
         return v;
     };
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

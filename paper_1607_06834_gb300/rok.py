@@ -28,6 +28,7 @@ ROK_OK, ROK_ERR_INVALID_ARG, ROK_ERR_CUDA, ROK_ERR_NONFINITE = 0, 1, 2, 3
 ROK_ERR_NOT_CONVERGED, ROK_ERR_TIMEOUT, ROK_ERR_UNSUPPORTED, ROK_ERR_NOMEM = 4, 5, 6, 7
 ROK_JVP_FD, ROK_JVP_EXACT = 0, 1
 ROK_ROUND_FAST, ROK_ROUND_STRICT = 0, 1
+ROK_BASIS_FP64, ROK_BASIS_FP32 = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -41,7 +42,7 @@ class ProblemDesc(ctypes.Structure):
         ('t_ref', ctypes.c_double), ('sutherland_s', ctypes.c_double),
         ('q_inf', ctypes.c_double * 4),
         ('muscl_kappa', ctypes.c_double), ('entropy_fix', ctypes.c_double), ('lorenz_f', ctypes.c_double),
-        ('krylov_max', ctypes.c_int), ('rounding', ctypes.c_int),
+        ('krylov_max', ctypes.c_int), ('rounding', ctypes.c_int), ('basis', ctypes.c_int),
     ]
 
 
@@ -142,7 +143,7 @@ class Context:
         return self._stage, y
 
 
-def _desc(problem, krylov_max, rounding):
+def _desc(problem, krylov_max, rounding, basis=0):
     d = ProblemDesc()
     d.kind = int(problem.kind)
     d.nx, d.ny = int(problem.nx), int(problem.ny)
@@ -162,14 +163,15 @@ def _desc(problem, krylov_max, rounding):
     d.muscl_kappa, d.entropy_fix, d.lorenz_f = float(problem.muscl_kappa), float(problem.entropy_fix), float(problem.lorenz_f)
     d.krylov_max = int(krylov_max)
     d.rounding = int(rounding)
+    d.basis = int(basis)
     return d, keep
 
 
-def rok_init(problem, krylov_max=20, rounding=ROK_ROUND_FAST, stream=None):
+def rok_init(problem, krylov_max=20, rounding=ROK_ROUND_FAST, stream=None, basis=ROK_BASIS_FP64):
     """Create a context (``rok_init``) for a :class:`workloads.FlowProblem`."""
     if stream is None:
         stream = torch.cuda.current_stream()
-    d, keep = _desc(problem, krylov_max, rounding)
+    d, keep = _desc(problem, krylov_max, rounding, basis)
     h = ctypes.c_void_p()
     _check(_lib.rok_init(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream)), 'rok_init')
     del keep
