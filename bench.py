@@ -240,6 +240,29 @@ def run_ours(args):
         forms['mixed_fp32_basis'] = {'ms_per_step': round(ms32, 4), 'speedup_vs_fp64': round(ms_per_step / ms32, 3),
                                      'value': round(ws * cells * KRYLOV / (ms32 * 1e-3) / 1e6, 3),
                                      'rel_l2_vs_fp64_after_steps': diff, 'steps_compared': args.steps}
+        # exact (dual-number) Jacobian-vector products inside the Arnoldi process
+        ctxe = rok.rok_init(prob, krylov_max=KRYLOV, rounding=rounding, stream=stream, jvp=rok.ROK_JVP_EXACT)
+        if args.graph:
+            rok.rok_set_graph(ctxe, True)
+        ye, yf = rok.state_tensor(y0), rok.state_tensor(y0)
+        for _ in range(args.warmup):
+            rok.rok_step(ctxe, rok.state_tensor(y0), h, KRYLOV)
+        barrier()
+        eve = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rok.rok_step(ctxe, ye, h, KRYLOV)
+            b.record(stream)
+            eve.append((a, b))
+            rok.rok_step(ctx, yf, h, KRYLOV)
+        barrier()
+        mse = sum(a.elapsed_time(b) for a, b in eve) / args.steps
+        forms['exact_jvp'] = {'ms_per_step': round(mse, 4), 'speedup_vs_fd': round(ms_per_step / mse, 3),
+                              'value': round(ws * cells * KRYLOV / (mse * 1e-3) / 1e6, 3),
+                              'rel_l2_vs_fd_after_steps': float((ye - yf).norm() / yf.norm()),
+                              'steps_compared': args.steps}
     if rank != 0:
         return None
     peaks, src = _peaks()
@@ -383,19 +406,29 @@ def run_tte(args):
         base_cfl = 8.0
     else:
         prob, y0, _ = W.cylinder_ogrid(256, 512)
-        krylov, cfls, cfl_rk = 30, [1000.0, 300.0, 100.0], [1.0]
+        krylov, cfls, cfl_rk = 30, [1000.0, 300.0, 100.0, 30.0, 10.0], [1.0]
         base_cfl = 1.0
+    if args.cfls:
+        cfls = [float(x) for x in args.cfls.split(',')]
     ctx = rok.rok_init(prob, krylov_max=max(krylov, 30), rounding=rok.ROK_ROUND_FAST)
     yd = rok.state_tensor(y0)
     dt_unit = rok.rok_dt_from_cfl(ctx, yd, 1.0)
     T = args.horizon * dt_unit * base_cfl
     out = {'study': 'time-to-fixed-L2-error', 'case': prob.name, 'T': T, 'dt_cfl1': dt_unit, 'methods': {}}
 
-    def integrate(step_fn, dt):
+    def integrate(step_fn, dt, cap_s=None):
         n = max(1, int(round(T / dt)))
         h = T / n
         y = rok.state_tensor(y0)
         torch.cuda.synchronize()
+        if cap_s is not None:
+            # estimate the run from one step; skip runs that would exceed the cap
+            t1 = time.perf_counter()
+            step_fn(rok.state_tensor(y0), h)
+            torch.cuda.synchronize()
+            est = (time.perf_counter() - t1) * n
+            if est > cap_s:
+                raise TimeoutError('estimated %.0f s for %d steps' % (est, n))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         e0.record()
@@ -423,17 +456,21 @@ def run_tte(args):
         out['methods'].setdefault(name, []).append(d)
 
     for c in cfls:
-        y, n, h, gs, ws, _ = integrate(lambda y, h: rok.rok_step(ctx, y, h, krylov), c * dt_unit)
-        record('ROK4', y, n, h, gs, ws, {'cfl': c, 'M': krylov})
+        try:
+            y, n, h, gs, ws, _ = integrate(lambda y, h: rok.rok_step(ctx, y, h, krylov, info=True), c * dt_unit)
+            record('ROK4', y, n, h, gs, ws, {'cfl': c, 'M': krylov})
+        except rok.RokError as err:
+            out['methods'].setdefault('ROK4', []).append({'cfl': c, 'failed': str(err)})
     for c in cfl_rk:
         y, n, h, gs, ws, _ = integrate(lambda y, h: rok.rk_step(ctx, y, h), c * dt_unit)
         record('RK4', y, n, h, gs, ws, {'cfl': c})
     for c in cfls:
         try:
-            y, n, h, gs, ws, infos = integrate(lambda y, h: rok.esdirk_step(ctx, y, h, info=True), c * dt_unit)
+            y, n, h, gs, ws, infos = integrate(lambda y, h: rok.esdirk_step(ctx, y, h, info=True), c * dt_unit,
+                                               cap_s=args.esdirk_cap)
             record('ESDIRK3', y, n, h, gs, ws, {'cfl': c, 'gmres_iters': sum(i['gmres_iters'] for i in infos),
                                                 'newton_iters': sum(i['newton_iters'] for i in infos)})
-        except rok.RokError as err:
+        except (rok.RokError, TimeoutError) as err:
             out['methods'].setdefault('ESDIRK3', []).append({'cfl': c, 'failed': str(err)})
     out['time_to_error'] = {}
     for tgt in (1e-4, 1e-6, 1e-8, 1e-10):
@@ -450,6 +487,8 @@ def main():
     ap.add_argument('--case', default='tgv', choices=['tgv', 'cylinder'])
     ap.add_argument('--horizon', type=float, default=50.0, help='T in units of the base-CFL step')
     ap.add_argument('--ref-factor', type=float, default=16.0)
+    ap.add_argument('--esdirk-cap', type=float, default=150.0, help='skip ESDIRK runs estimated above this (s)')
+    ap.add_argument('--cfls', default=None, help='comma-separated ROK/ESDIRK CFL numbers (study)')
     ap.add_argument('--mode', default='step', choices=['step', 'stencil'])
     ap.add_argument('--n', type=int, default=N_GRID)
     ap.add_argument('--gpus', type=int, default=1)

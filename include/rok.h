@@ -77,6 +77,9 @@ typedef struct {
     int krylov_max;      /* largest Krylov dimension M / GMRES restart length used    */
     int rounding;        /* ROK_ROUND_FAST | ROK_ROUND_STRICT                         */
     int basis;           /* ROK_BASIS_FP64 | ROK_BASIS_FP32 (rok_step / rok_arnoldi)   */
+    int jvp;             /* Jacobian-vector products inside rok_step, rok_arnoldi and
+                            esdirk_step: ROK_JVP_FD (Eq. matvecFD) or ROK_JVP_EXACT
+                            (forward-mode dual numbers, J v to rounding)              */
 } rok_problem_desc;
 
 typedef struct {
@@ -116,12 +119,14 @@ rok_status rok_set_stream(rok_ctx *ctx, void *cuda_stream);
  * y, f: device, N float64, must not overlap. */
 rok_status rok_residual(rok_ctx *ctx, const double *y, double *f);
 
-/* jv = J(y) v by the one-sided finite difference of Eq. matvecFD,
- * (f(y + eps v) - f(y)) / eps.  fy = f(y) if the caller has it, else NULL
- * (it is then computed).  eps > 0 is used as given (a power of two keeps
- * the quotient exact); eps <= 0 selects sqrt(2^-52 (1 + ||y||)) / ||v||
- * rounded to the nearest power of two.  mode: ROK_JVP_FD (ROK_JVP_EXACT
- * returns UNSUPPORTED in this build).  All arrays device, N float64. */
+/* jv = J(y) v.  mode ROK_JVP_FD: the one-sided finite difference of
+ * Eq. matvecFD, (f(y + eps v) - f(y)) / eps; fy = f(y) if the caller has it,
+ * else NULL (it is then computed); eps > 0 is used as given (a power of two
+ * keeps the quotient exact), eps <= 0 selects sqrt(2^-52 (1 + ||y||)) / ||v||
+ * rounded to the nearest power of two.  mode ROK_JVP_EXACT: the exact
+ * directional derivative of the discrete residual by forward-mode dual
+ * numbers (the alternative the paper points to in Sec. 2.4); fy and eps are
+ * ignored.  All arrays device, N float64. */
 rok_status rok_jvp(rok_ctx *ctx, const double *y, const double *fy, const double *v, double *jv,
                    double eps, int mode);
 

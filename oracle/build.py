@@ -19,9 +19,12 @@ def build(force=False):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + '.tmp.%d' % os.getpid()
-    cmd = ['gcc', '-std=c11', '-O2', '-ffp-contract=off', '-fno-fast-math', '-fPIC', '-shared',
-           SRC, '-o', tmp, '-lm']
-    subprocess.check_call(cmd)
+    flags = ['gcc', '-std=c11', '-O2', '-ffp-contract=off', '-fno-fast-math', '-fPIC']
+    o_real = os.path.join(OUT_DIR, 'residual_real.o')
+    o_cplx = os.path.join(OUT_DIR, 'residual_cs.o')
+    subprocess.check_call(flags + ['-c', SRC, '-o', o_real])
+    subprocess.check_call(flags + ['-DORACLE_COMPLEX', '-c', SRC, '-o', o_cplx])
+    subprocess.check_call(['gcc', '-shared', o_real, o_cplx, '-o', tmp, '-lm'])
     os.replace(tmp, LIB)
     return LIB
 

@@ -40,6 +40,8 @@ def lib():
         L.oracle_roe_flux.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, dp]
         L.oracle_roe_flux.restype = None
+        L.oracle_jvp_cs.argtypes = [ctypes.POINTER(_Problem), dp, dp, ctypes.c_double, dp]
+        L.oracle_jvp_cs.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -115,6 +117,21 @@ def jvp_fd(prob, y, v, f0, eps):
     return w
 
 
+def jvp_exact(prob, y, v, h=1e-100):
+    """Exact Jacobian-vector product J(y) v: the complex-step derivative
+    Im f(y + i h v) / h of the same residual (no cancellation, exact to
+    rounding); analytic for Lorenz-96."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    if prob.kind == 2:
+        return (np.roll(v, -1) - np.roll(v, 2)) * np.roll(y, 1) + (np.roll(y, -1) - np.roll(y, 2)) * np.roll(v, 1) - v
+    w = np.empty_like(y)
+    rc = lib().oracle_jvp_cs(ctypes.byref(_desc(prob).s), _dp(y), _dp(v), float(h), _dp(w))
+    if rc != 0:
+        raise MemoryError('oracle_jvp_cs failed')
+    return w
+
+
 def cell_volumes(prob):
     vol = np.empty((prob.ny, prob.nx))
     lib().oracle_cell_volumes(ctypes.byref(_desc(prob).s), _dp(vol))
@@ -143,3 +160,10 @@ class System:
 
     def jvp(self, y, v, f0, eps):
         return jvp_fd(self.prob, y, v, f0, eps)
+
+
+class ExactSystem(System):
+    """The same f with the exact (complex-step) Jacobian-vector product."""
+
+    def jvp(self, y, v, f0, eps):
+        return jvp_exact(self.prob, y, v)

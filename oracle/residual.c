@@ -39,6 +39,25 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Scalar of every state-dependent quantity.  The file is compiled twice: with
+ * real_t = double (the residual and the FD-JVP), and with ORACLE_COMPLEX,
+ * real_t = double complex, for the complex-step derivative
+ * J v = Im f(y + i h v) / h (Squire & Trapp 1998), which is exact to rounding
+ * (no difference of nearly equal numbers).  |x| continues analytically as
+ * x sign(Re x) and every branch compares real parts. */
+#ifdef ORACLE_COMPLEX
+#include <complex.h>
+typedef double complex real_t;
+#define RSQRT(x) csqrt(x)
+#define RABS(x) (creal(x) < 0.0 ? -(x) : (x))
+#define RLT(a, b) (creal(a) < creal(b))
+#else
+typedef double real_t;
+#define RSQRT(x) sqrt(x)
+#define RABS(x) fabs(x)
+#define RLT(a, b) ((a) < (b))
+#endif
+
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_FARFIELD = 2 };
 
 typedef struct {
@@ -59,21 +78,21 @@ typedef struct {
 } oracle_problem;
 
 /* primitive state of one (possibly ghost) cell */
-typedef struct { double r, u, v, p, T, mu; } prim;
+typedef struct { real_t r, u, v, p, T, mu; } prim;
 
 #define NG 2
 
-static double sutherland(const oracle_problem *P, double T)
+static real_t sutherland(const oracle_problem *P, real_t T)
 {
     if (P->suth_s <= 0.0) return P->mu_ref;
-    double t = T * (1.0 / P->t_ref);
-    return P->mu_ref * (t * sqrt(t)) * ((1.0 + P->suth_s) / (t + P->suth_s));
+    real_t t = T * (1.0 / P->t_ref);
+    return P->mu_ref * (t * RSQRT(t)) * ((1.0 + P->suth_s) / (t + P->suth_s));
 }
 
-static prim to_prim(const oracle_problem *P, double rho, double mx, double my, double E)
+static prim to_prim(const oracle_problem *P, real_t rho, real_t mx, real_t my, real_t E)
 {
     prim w;
-    double rinv = 1.0 / rho;
+    real_t rinv = 1.0 / rho;
     w.r = rho;
     w.u = mx * rinv;
     w.v = my * rinv;
@@ -88,7 +107,7 @@ static prim mirror(prim w) { w.u = -w.u; w.v = -w.v; return w; }
 /* extended-array index, ghosts included: i in [-2, nx+1], j in [-2, ny+1] */
 #define EX(i, j) (((j) + NG) * (nx + 2 * NG) + ((i) + NG))
 
-static void fill_prims(const oracle_problem *P, const double *q, prim *W)
+static void fill_prims(const oracle_problem *P, const real_t *q, prim *W)
 {
     const int nx = P->nx, ny = P->ny;
     const size_t nc = (size_t)nx * ny;
@@ -130,71 +149,71 @@ static void fill_prims(const oracle_problem *P, const double *q, prim *W)
 
 /* kappa-MUSCL, no limiter, on one primitive variable.  m2, m1 | p1, p2 are
  * the four cells along the grid line, the face sits between m1 and p1. */
-static void muscl(double m2, double m1, double p1, double p2, double c_lo, double c_hi,
-                  double *wl, double *wr)
+static void muscl(real_t m2, real_t m1, real_t p1, real_t p2, double c_lo, double c_hi,
+                  real_t *wl, real_t *wr)
 {
-    double dl = m1 - m2, dc = p1 - m1, dr = p2 - p1;
+    real_t dl = m1 - m2, dc = p1 - m1, dr = p2 - p1;
     *wl = (m1 + c_lo * dl) + c_hi * dc;
     *wr = (p1 - c_lo * dr) - c_hi * dc;
 }
 
-static double harten(double lam, double delta)
+static real_t harten(real_t lam, real_t delta)
 {
-    double a = fabs(lam);
-    if (a < delta) a = (a * a + delta * delta) / (2.0 * delta);
+    real_t a = RABS(lam);
+    if (RLT(a, delta)) a = (a * a + delta * delta) / (2.0 * delta);
     return a;
 }
 
 /* Roe flux through a face of unit normal (nx, ny), primitive L/R states
  * WL = (rho, u, v, p).  Result F = 1/2 (F(L) + F(R)) - 1/2 sum |lam| a r. */
-static void roe(const double *WL, const double *WR, double nx, double ny,
-                double gm1, double inv_gm1, double efix, double *F)
+static void roe(const real_t *WL, const real_t *WR, double nx, double ny,
+                real_t gm1, double inv_gm1, double efix, real_t *F)
 {
-    double rL = WL[0], uL = WL[1], vL = WL[2], pL = WL[3];
-    double rR = WR[0], uR = WR[1], vR = WR[2], pR = WR[3];
-    double qnL = uL * nx + vL * ny;
-    double qnR = uR * nx + vR * ny;
+    real_t rL = WL[0], uL = WL[1], vL = WL[2], pL = WL[3];
+    real_t rR = WR[0], uR = WR[1], vR = WR[2], pR = WR[3];
+    real_t qnL = uL * nx + vL * ny;
+    real_t qnR = uR * nx + vR * ny;
     /* rho H = E + p on each side */
-    double eL = (pL * inv_gm1 + rL * (0.5 * (uL * uL + vL * vL))) + pL;
-    double eR = (pR * inv_gm1 + rR * (0.5 * (uR * uR + vR * vR))) + pR;
+    real_t eL = (pL * inv_gm1 + rL * (0.5 * (uL * uL + vL * vL))) + pL;
+    real_t eR = (pR * inv_gm1 + rR * (0.5 * (uR * uR + vR * vR))) + pR;
 
-    /* Roe averages with weights sqrt(rho): wl = sL/(sL+sR) = rL sR / (sL sR (sL+sR)),
+    /* Roe averages with weights RSQRT(rho): wl = sL/(sL+sR) = rL sR / (sL sR (sL+sR)),
      * H~ = (sL HL + sR HR)/(sL+sR) = (eL sR + eR sL) / (sL sR (sL+sR)) */
-    double sL = sqrt(rL), sR = sqrt(rR);
-    double rt = sL * sR;
-    double den = 1.0 / (rt * (sL + sR));
-    double wl = (rL * sR) * den, wr = (rR * sL) * den;
-    double ut = wl * uL + wr * uR;
-    double vt = wl * vL + wr * vR;
-    double Ht = (eL * sR + eR * sL) * den;
-    double kt = 0.5 * (ut * ut + vt * vt);
-    double ct2 = gm1 * (Ht - kt);
-    double ct = sqrt(ct2);
-    double qnt = ut * nx + vt * ny;
+    real_t sL = RSQRT(rL), sR = RSQRT(rR);
+    real_t rt = sL * sR;
+    real_t den = 1.0 / (rt * (sL + sR));
+    real_t wl = (rL * sR) * den, wr = (rR * sL) * den;
+    real_t ut = wl * uL + wr * uR;
+    real_t vt = wl * vL + wr * vR;
+    real_t Ht = (eL * sR + eR * sL) * den;
+    real_t kt = 0.5 * (ut * ut + vt * vt);
+    real_t ct2 = gm1 * (Ht - kt);
+    real_t ct = RSQRT(ct2);
+    real_t qnt = ut * nx + vt * ny;
 
-    double drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
-    double inv_c2 = 1.0 / ct2;
-    double rcdq = rt * ct * dqn;
-    double a1 = 0.5 * (dp - rcdq) * inv_c2;
-    double a2 = drho - dp * inv_c2;
-    double a3 = 0.5 * (dp + rcdq) * inv_c2;
+    real_t drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
+    real_t inv_c2 = 1.0 / ct2;
+    real_t rcdq = rt * ct * dqn;
+    real_t a1 = 0.5 * (dp - rcdq) * inv_c2;
+    real_t a2 = drho - dp * inv_c2;
+    real_t a3 = 0.5 * (dp + rcdq) * inv_c2;
 
     /* Harten's entropy fix on the two acoustic (genuinely nonlinear) waves */
-    double delta = efix * (fabs(qnt) + ct);
-    double l1 = harten(qnt - ct, delta);
-    double l2 = fabs(qnt);
-    double l3 = harten(qnt + ct, delta);
+    real_t delta = efix * (RABS(qnt) + ct);
+    real_t l1 = harten(qnt - ct, delta);
+    real_t l2 = RABS(qnt);
+    real_t l3 = harten(qnt + ct, delta);
 
-    double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
-    double D0 = (A1 + A2) + A3;
-    double D1 = ((A1 * (ut - ct * nx) + A2 * ut) + A3 * (ut + ct * nx)) + As * (du - dqn * nx);
-    double D2 = ((A1 * (vt - ct * ny) + A2 * vt) + A3 * (vt + ct * ny)) + As * (dv - dqn * ny);
-    double D3 = ((A1 * (Ht - ct * qnt) + A2 * kt) + A3 * (Ht + ct * qnt))
+    real_t A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
+    real_t D0 = (A1 + A2) + A3;
+    real_t D1 = ((A1 * (ut - ct * nx) + A2 * ut) + A3 * (ut + ct * nx)) + As * (du - dqn * nx);
+    real_t D2 = ((A1 * (vt - ct * ny) + A2 * vt) + A3 * (vt + ct * ny)) + As * (dv - dqn * ny);
+    real_t D3 = ((A1 * (Ht - ct * qnt) + A2 * kt) + A3 * (Ht + ct * qnt))
                 + As * ((ut * du + vt * dv) - qnt * dqn);
 
-    double mL = rL * qnL, mR = rR * qnR;
-    double FL1 = mL * uL + pL * nx, FR1 = mR * uR + pR * nx;
-    double FL2 = mL * vL + pL * ny, FR2 = mR * vR + pR * ny;
+    real_t mL = rL * qnL, mR = rR * qnR;
+    real_t FL1 = mL * uL + pL * nx, FR1 = mR * uR + pR * nx;
+    real_t FL2 = mL * vL + pL * ny, FR2 = mR * vR + pR * ny;
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * ((FL1 + FR1) - D1);
     F[2] = 0.5 * ((FL2 + FR2) - D2);
@@ -203,31 +222,31 @@ static void roe(const double *WL, const double *WR, double nx, double ny,
 
 /* viscous face flux (tau . n, u . tau . n - q . n) for unit normal n;
  * g = (ux, uy, vx, vy, Tx, Ty) are face gradients. */
-static void viscous(const double *g, double mu_f, double u_f, double v_f, double nx, double ny,
-                    double kfac, double c23, double *Fv)
+static void viscous(const real_t *g, real_t mu_f, real_t u_f, real_t v_f, double nx, double ny,
+                    real_t kfac, double c23, real_t *Fv)
 {
-    double ux = g[0], uy = g[1], vx = g[2], vy = g[3], Tx = g[4], Ty = g[5];
-    double div = ux + vy;
-    double txx = mu_f * (2.0 * ux - c23 * div);
-    double tyy = mu_f * (2.0 * vy - c23 * div);
-    double txy = mu_f * (uy + vx);
-    double tnx = txx * nx + txy * ny;
-    double tny = txy * nx + tyy * ny;
-    double kf = mu_f * kfac;
-    double dTn = Tx * nx + Ty * ny;
+    real_t ux = g[0], uy = g[1], vx = g[2], vy = g[3], Tx = g[4], Ty = g[5];
+    real_t div = ux + vy;
+    real_t txx = mu_f * (2.0 * ux - c23 * div);
+    real_t tyy = mu_f * (2.0 * vy - c23 * div);
+    real_t txy = mu_f * (uy + vx);
+    real_t tnx = txx * nx + txy * ny;
+    real_t tny = txy * nx + tyy * ny;
+    real_t kf = mu_f * kfac;
+    real_t dTn = Tx * nx + Ty * ny;
     Fv[0] = 0.0;
     Fv[1] = tnx;
     Fv[2] = tny;
     Fv[3] = (u_f * tnx + v_f * tny) + kf * dTn;
 }
 
-static double pget(const prim *w, int k)
+static real_t pget(const prim *w, int k)
 {
     switch (k) { case 0: return w->r; case 1: return w->u; case 2: return w->v; default: return w->p; }
 }
 
 /* 2x2 vertex average of the four cells around vertex (i, j) */
-static void vertex_vals(const oracle_problem *P, const prim *W, int i, int j, double *uvT)
+static void vertex_vals(const oracle_problem *P, const prim *W, int i, int j, real_t *uvT)
 {
     const int nx = P->nx;
     const prim *a = &W[EX(i - 1, j - 1)], *b = &W[EX(i, j - 1)], *c = &W[EX(i - 1, j)], *d = &W[EX(i, j)];
@@ -356,32 +375,32 @@ static void free_geom(geom *G)
 
 /* one face: MUSCL states, Roe flux, viscous flux; total (F_inv - F_visc) */
 static void face_flux(const oracle_problem *P, const prim *m2, const prim *m1, const prim *p1,
-                      const prim *p2, double nx_, double ny_, const double *grad, double *F)
+                      const prim *p2, double nx_, double ny_, const real_t *grad, real_t *F)
 {
     const double gm1 = P->gamma - 1.0, inv_gm1 = 1.0 / gm1;
     const double c_lo = 0.25 * (1.0 - P->kappa), c_hi = 0.25 * (1.0 + P->kappa);
-    double WL[4], WR[4];
+    real_t WL[4], WR[4];
     for (int k = 0; k < 4; ++k)
         muscl(pget(m2, k), pget(m1, k), pget(p1, k), pget(p2, k), c_lo, c_hi, &WL[k], &WR[k]);
     roe(WL, WR, nx_, ny_, gm1, inv_gm1, P->efix, F);
     if (P->viscous) {
         const double kfac = P->gamma / (gm1 * P->prandtl), c23 = 2.0 / 3.0;
-        double Fv[4];
-        double mu_f = 0.5 * (m1->mu + p1->mu);
-        double u_f = 0.5 * (m1->u + p1->u), v_f = 0.5 * (m1->v + p1->v);
+        real_t Fv[4];
+        real_t mu_f = 0.5 * (m1->mu + p1->mu);
+        real_t u_f = 0.5 * (m1->u + p1->u), v_f = 0.5 * (m1->v + p1->v);
         viscous(grad, mu_f, u_f, v_f, nx_, ny_, kfac, c23, Fv);
         for (int k = 0; k < 4; ++k) F[k] = F[k] - Fv[k];
     }
 }
 
-int oracle_residual(const oracle_problem *P, const double *q, double *f)
+static int residual_impl(const oracle_problem *P, const real_t *q, real_t *f)
 {
     const int nx = P->nx, ny = P->ny;
     if (nx < 1 || ny < 1) return 0;
     const size_t nc = (size_t)nx * ny;
     prim *W = malloc((size_t)(nx + 2 * NG) * (ny + 2 * NG) * sizeof(prim));
-    double *FX = malloc((size_t)4 * (nx + 1) * ny * sizeof(double));
-    double *FY = malloc((size_t)4 * nx * (ny + 1) * sizeof(double));
+    real_t *FX = malloc((size_t)4 * (nx + 1) * ny * sizeof(real_t));
+    real_t *FY = malloc((size_t)4 * nx * (ny + 1) * sizeof(real_t));
     if (!W || !FX || !FY) { free(W); free(FX); free(FY); return -1; }
     fill_prims(P, q, W);
     const size_t nfi = (size_t)(nx + 1) * ny, nfj = (size_t)nx * (ny + 1);
@@ -396,7 +415,7 @@ int oracle_residual(const oracle_problem *P, const double *q, double *f)
         for (int i = 0; i <= nx; ++i) {
             size_t fidx = (size_t)j * (nx + 1) + i;
             const prim *L = &W[EX(i - 1, j)], *R = &W[EX(i, j)];
-            double g[6] = {0, 0, 0, 0, 0, 0};
+            real_t g[6] = {0, 0, 0, 0, 0, 0};
             double nx_ = 1.0, ny_ = 0.0;
             if (P->curvilinear) { nx_ = G.in_x[fidx]; ny_ = G.in_y[fidx]; }
             if (P->viscous) {
@@ -410,18 +429,18 @@ int oracle_residual(const oracle_problem *P, const double *q, double *f)
                     g[4] = (R->T - L->T) * rdx;
                     g[5] = ((ln->T + rn->T) - (ls->T + rs->T)) * q_rdy;
                 } else {
-                    double a[3], b[3];
+                    real_t a[3], b[3];
                     vertex_vals(P, W, i, j, a);      /* P1 */
                     vertex_vals(P, W, i, j + 1, b);  /* P3 */
-                    double dC[3] = {R->u - L->u, R->v - L->v, R->T - L->T};
+                    real_t dC[3] = {R->u - L->u, R->v - L->v, R->T - L->T};
                     for (int k = 0; k < 3; ++k) {
-                        double dV = b[k] - a[k];
+                        real_t dV = b[k] - a[k];
                         g[2 * k] = dC[k] * G.ic[0][fidx] + dV * G.ic[1][fidx];
                         g[2 * k + 1] = dC[k] * G.ic[2][fidx] + dV * G.ic[3][fidx];
                     }
                 }
             }
-            double F[4];
+            real_t F[4];
             face_flux(P, &W[EX(i - 2, j)], L, R, &W[EX(i + 1, j)], nx_, ny_, g, F);
             if (P->curvilinear) for (int k = 0; k < 4; ++k) F[k] = F[k] * G.il[fidx];
             for (int k = 0; k < 4; ++k) FX[k * nfi + fidx] = F[k];
@@ -431,7 +450,7 @@ int oracle_residual(const oracle_problem *P, const double *q, double *f)
         for (int i = 0; i < nx; ++i) {
             size_t fidx = (size_t)j * nx + i;
             const prim *B = &W[EX(i, j - 1)], *T = &W[EX(i, j)];
-            double g[6] = {0, 0, 0, 0, 0, 0};
+            real_t g[6] = {0, 0, 0, 0, 0, 0};
             double nx_ = 0.0, ny_ = 1.0;
             if (P->curvilinear) { nx_ = G.jn_x[fidx]; ny_ = G.jn_y[fidx]; }
             if (P->viscous) {
@@ -445,18 +464,18 @@ int oracle_residual(const oracle_problem *P, const double *q, double *f)
                     g[4] = ((eb->T + et->T) - (wb->T + wt->T)) * q_rdx;
                     g[5] = (T->T - B->T) * rdy;
                 } else {
-                    double a[3], b[3];
+                    real_t a[3], b[3];
                     vertex_vals(P, W, i + 1, j, a);  /* P1 */
                     vertex_vals(P, W, i, j, b);      /* P3 */
-                    double dC[3] = {T->u - B->u, T->v - B->v, T->T - B->T};
+                    real_t dC[3] = {T->u - B->u, T->v - B->v, T->T - B->T};
                     for (int k = 0; k < 3; ++k) {
-                        double dV = b[k] - a[k];
+                        real_t dV = b[k] - a[k];
                         g[2 * k] = dC[k] * G.jc[0][fidx] + dV * G.jc[1][fidx];
                         g[2 * k + 1] = dC[k] * G.jc[2][fidx] + dV * G.jc[3][fidx];
                     }
                 }
             }
-            double F[4];
+            real_t F[4];
             face_flux(P, &W[EX(i, j - 2)], B, T, &W[EX(i, j + 1)], nx_, ny_, g, F);
             if (P->curvilinear) for (int k = 0; k < 4; ++k) F[k] = F[k] * G.jl[fidx];
             for (int k = 0; k < 4; ++k) FY[k * nfj + fidx] = F[k];
@@ -467,8 +486,8 @@ int oracle_residual(const oracle_problem *P, const double *q, double *f)
             size_t c = (size_t)j * nx + i;
             size_t fw = (size_t)j * (nx + 1) + i, fs = (size_t)j * nx + i, fn = (size_t)(j + 1) * nx + i;
             for (int k = 0; k < 4; ++k) {
-                double dX = FX[k * nfi + fw + 1] - FX[k * nfi + fw];
-                double dY = FY[k * nfj + fn] - FY[k * nfj + fs];
+                real_t dX = FX[k * nfi + fw + 1] - FX[k * nfi + fw];
+                real_t dY = FY[k * nfj + fn] - FY[k * nfj + fs];
                 if (P->curvilinear)
                     f[k * nc + c] = -((dX + dY) * G.inv_vol[c]);
                 else
@@ -479,6 +498,9 @@ int oracle_residual(const oracle_problem *P, const double *q, double *f)
     free(W); free(FX); free(FY);
     return 0;
 }
+
+#ifndef ORACLE_COMPLEX
+int oracle_residual(const oracle_problem *P, const double *q, double *f) { return residual_impl(P, q, f); }
 
 /* Sum over cells of Vol * f (discrete conservation check); volumes as used above */
 int oracle_cell_volumes(const oracle_problem *P, double *vol)
@@ -518,3 +540,19 @@ void oracle_roe_flux(const double *WL, const double *WR, double nx, double ny, d
     double gm1 = gamma - 1.0;
     roe(WL, WR, nx, ny, gm1, 1.0 / gm1, efix, F);
 }
+#else
+/* Exact Jacobian-vector product by the complex step: Im f(y + i h v) / h. */
+int oracle_jvp_cs(const oracle_problem *P, const double *y, const double *v, double h, double *jv)
+{
+    const size_t n = (size_t)4 * P->nx * P->ny;
+    real_t *q = malloc(n * sizeof(real_t));
+    real_t *f = malloc(n * sizeof(real_t));
+    if (!q || !f) { free(q); free(f); return -1; }
+    for (size_t k = 0; k < n; ++k) q[k] = y[k] + I * (h * v[k]);
+    int rc = residual_impl(P, q, f);
+    for (size_t k = 0; k < n; ++k) jv[k] = cimag(f[k]) / h;
+    free(q);
+    free(f);
+    return rc;
+}
+#endif

@@ -66,6 +66,7 @@ struct rok_ctx {
     double *V = nullptr;       // (mmax+1) x N basis (binary64; also the GMRES basis)
     float *Vf = nullptr;       // (mmax+1) x N binary32 basis of the mixed-precision ROK step
     bool fp32 = false;
+    bool exact_jvp = false;    // Jacobian-vector products by dual numbers inside the steps
     double *F[4] = {};         // stage residuals
     double *K[4] = {};         // stage vectors
     double *w = nullptr, *t0 = nullptr, *t1 = nullptr, *t2 = nullptr;
@@ -364,7 +365,11 @@ rok_status arnoldi_columns(rok_ctx *c, const double *y, int M)
     void *Vb = c->fp32 ? (void *)c->Vf : (void *)c->V;
     for (int j = 0; j < M; ++j) {
         StencilIO io;
-        if (c->fp32) {
+        if (c->exact_jvp) {
+            io = io_plain(c, y, c->w);   // J(y) v_j by dual numbers
+            if (c->fp32) io.dirf = c->Vf + (size_t)j * N;
+            else io.dir = c->V + (size_t)j * N;
+        } else if (c->fp32) {
             io = io_plain(c, y, c->w);
             io.addf = c->Vf + (size_t)j * N;
             io.coef_f = 1.0;
@@ -549,6 +554,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     if (d->krylov_max < 0 || d->krylov_max > kMaxKrylov) return ROK_ERR_INVALID_ARG;
     if (d->rounding != ROK_ROUND_FAST && d->rounding != ROK_ROUND_STRICT) return ROK_ERR_INVALID_ARG;
     if (d->basis != ROK_BASIS_FP64 && d->basis != ROK_BASIS_FP32) return ROK_ERR_INVALID_ARG;
+    if (d->jvp != ROK_JVP_FD && d->jvp != ROK_JVP_EXACT) return ROK_ERR_INVALID_ARG;
     if (d->kind == ROK_LORENZ96) {
         if (d->nx < 4) return ROK_ERR_INVALID_ARG;
     } else {
@@ -575,6 +581,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     c->strict = d->rounding == ROK_ROUND_STRICT;
     c->curv = d->kind != ROK_LORENZ96 && d->xv != nullptr;
     c->fp32 = d->basis == ROK_BASIS_FP32;
+    c->exact_jvp = d->jvp == ROK_JVP_EXACT;
     c->stream = (cudaStream_t)stream;
     c->mmax = d->krylov_max;
     c->nc = d->kind == ROK_LORENZ96 ? (size_t)d->nx : (size_t)d->nx * d->ny;
@@ -674,7 +681,11 @@ rok_status rok_residual(rok_ctx *c, const double *y, double *f)
 rok_status rok_jvp(rok_ctx *c, const double *y, const double *fy, const double *v, double *jv, double eps, int mode)
 {
     if (!c || !y || !v || !jv || jv == y || jv == v) return ROK_ERR_INVALID_ARG;
-    if (mode == ROK_JVP_EXACT) return ROK_ERR_UNSUPPORTED;
+    if (mode == ROK_JVP_EXACT) {
+        StencilIO io = io_plain(c, y, jv);
+        io.dir = v;
+        return stencil(c, io);
+    }
     if (mode != ROK_JVP_FD) return ROK_ERR_INVALID_ARG;
     rok_status r;
     if (!fy) {
@@ -832,7 +843,13 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
     double *xi = c->t0, *rhs = c->t1, *dk = c->t2, *wv = c->w;
     // op(v) = v - h g J_n v into out
     auto apply_op = [&](const double *v, double *out) -> rok_status {
-        StencilIO io = io_jvp(c, y, v, c->K[0], out);
+        StencilIO io;
+        if (c->exact_jvp) {
+            io = io_plain(c, y, out);
+            io.dir = v;
+        } else {
+            io = io_jvp(c, y, v, c->K[0], out);
+        }
         io.add_out = v;
         io.s2 = -hg;
         jvps++;

@@ -57,6 +57,8 @@ struct CurvGeom {
 //                                                  addf: a binary32 vector, read exactly)
 //   t     = (sub ? r - sub : r) * s1              (s1 times *s1_dev if given)
 //   out   = add_out ? add_out + s2 t : t          (s2 times *s2_dev if given)
+// With a direction (dir or dirf) the stencil runs on dual numbers and r is the
+// exact directional derivative J(state) dir instead of the residual.
 struct StencilIO {
     const double *base;
     const double *add[kMaxAdd];
@@ -66,6 +68,8 @@ struct StencilIO {
     const float *addf;         // nullable binary32 term (mixed-precision Krylov basis)
     double coef_f;
     const double *coef_f_dev;
+    const double *dir;         // exact JVP: direction v (the launch then writes J(state) v)
+    const float *dirf;         // ... or its binary32 form
     const double *sub;
     double s1;
     const double *s1_dev;

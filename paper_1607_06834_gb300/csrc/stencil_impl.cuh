@@ -20,6 +20,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dual.cuh"
 #include "rok_internal.h"
 
 namespace rok {
@@ -31,17 +32,19 @@ constexpr int NT = TX * TY;
 constexpr int EW = TX + 4;
 constexpr int EH = TY + 4;
 
-__device__ __forceinline__ double harten(double lam, double delta)
+template <class S>
+__device__ __forceinline__ S harten(S lam, S delta)
 {
-    double a = fabs(lam);
-    if (a < delta) a = (a * a + delta * delta) / (2.0 * delta);
+    S a = fabs(lam);
+    if (val(a) < val(delta)) a = (a * a + delta * delta) / (2.0 * delta);
     return a;
 }
 
-__device__ __forceinline__ void muscl(double m2, double m1, double p1, double p2, double c_lo,
-                                      double c_hi, double &wl, double &wr)
+template <class S>
+__device__ __forceinline__ void muscl(S m2, S m1, S p1, S p2, double c_lo,
+                                      double c_hi, S &wl, S &wr)
 {
-    double dl = m1 - m2, dc = p1 - m1, dr = p2 - p1;
+    S dl = m1 - m2, dc = p1 - m1, dr = p2 - p1;
     wl = (m1 + c_lo * dl) + c_hi * dc;
     wr = (p1 - c_lo * dr) - c_hi * dc;
 }
@@ -49,26 +52,28 @@ __device__ __forceinline__ void muscl(double m2, double m1, double p1, double p2
 // Roe-averaged quantities common to every face orientation.  e = rho H = E + p;
 // the sqrt(rho)-weighted averages use one reciprocal:
 //   wl = rL sR / (sL sR (sL + sR)),  H~ = (eL sR + eR sL) / (sL sR (sL + sR)).
+template <class S>
 struct RoeAvg {
-    double eL, eR, rt, ut, vt, Ht, kt, ct, inv_c2;
+    S eL, eR, rt, ut, vt, Ht, kt, ct, inv_c2;
 };
 
-__device__ __forceinline__ RoeAvg roe_avg(const double *L, const double *R, const StencilConsts &C)
+template <class S>
+__device__ __forceinline__ RoeAvg<S> roe_avg(const S *L, const S *R, const StencilConsts &C)
 {
-    RoeAvg a;
-    double rL = L[0], uL = L[1], vL = L[2], pL = L[3];
-    double rR = R[0], uR = R[1], vR = R[2], pR = R[3];
+    RoeAvg<S> a;
+    S rL = L[0], uL = L[1], vL = L[2], pL = L[3];
+    S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
     a.eL = (pL * C.inv_gm1 + rL * (0.5 * (uL * uL + vL * vL))) + pL;
     a.eR = (pR * C.inv_gm1 + rR * (0.5 * (uR * uR + vR * vR))) + pR;
-    double sL = sqrt(rL), sR = sqrt(rR);
+    S sL = sqrt(rL), sR = sqrt(rR);
     a.rt = sL * sR;
-    double den = 1.0 / (a.rt * (sL + sR));
-    double wl = (rL * sR) * den, wr = (rR * sL) * den;
+    S den = 1.0 / (a.rt * (sL + sR));
+    S wl = (rL * sR) * den, wr = (rR * sL) * den;
     a.ut = wl * uL + wr * uR;
     a.vt = wl * vL + wr * vR;
     a.Ht = (a.eL * sR + a.eR * sL) * den;
     a.kt = 0.5 * (a.ut * a.ut + a.vt * a.vt);
-    double ct2 = C.gm1 * (a.Ht - a.kt);
+    S ct2 = C.gm1 * (a.Ht - a.kt);
     a.ct = sqrt(ct2);
     a.inv_c2 = 1.0 / ct2;
     return a;
@@ -77,27 +82,28 @@ __device__ __forceinline__ RoeAvg roe_avg(const double *L, const double *R, cons
 // Roe flux through an x-face (unit normal (1, 0)).  Exact specialisation of the
 // general-normal formula: only products by 1 or 0 and additions of a zero are
 // removed, which leave the IEEE result of the general form unchanged.
-__device__ __forceinline__ void roe_x(const double *L, const double *R, const StencilConsts &C, double *F)
+template <class S>
+__device__ __forceinline__ void roe_x(const S *L, const S *R, const StencilConsts &C, S *F)
 {
-    RoeAvg a = roe_avg(L, R, C);
-    double rL = L[0], uL = L[1], vL = L[2], pL = L[3];
-    double rR = R[0], uR = R[1], vR = R[2], pR = R[3];
-    double drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL;
-    double rcdq = a.rt * a.ct * du;
-    double a1 = 0.5 * (dp - rcdq) * a.inv_c2;
-    double a2 = drho - dp * a.inv_c2;
-    double a3 = 0.5 * (dp + rcdq) * a.inv_c2;
-    double delta = C.efix * (fabs(a.ut) + a.ct);
-    double l1 = harten(a.ut - a.ct, delta);
-    double l2 = fabs(a.ut);
-    double l3 = harten(a.ut + a.ct, delta);
-    double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
-    double D0 = (A1 + A2) + A3;
-    double D1 = (A1 * (a.ut - a.ct) + A2 * a.ut) + A3 * (a.ut + a.ct);
-    double D2 = ((A1 * a.vt + A2 * a.vt) + A3 * a.vt) + As * dv;
-    double D3 = ((A1 * (a.Ht - a.ct * a.ut) + A2 * a.kt) + A3 * (a.Ht + a.ct * a.ut))
+    RoeAvg<S> a = roe_avg(L, R, C);
+    S rL = L[0], uL = L[1], vL = L[2], pL = L[3];
+    S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
+    S drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL;
+    S rcdq = a.rt * a.ct * du;
+    S a1 = 0.5 * (dp - rcdq) * a.inv_c2;
+    S a2 = drho - dp * a.inv_c2;
+    S a3 = 0.5 * (dp + rcdq) * a.inv_c2;
+    S delta = C.efix * (fabs(a.ut) + a.ct);
+    S l1 = harten(a.ut - a.ct, delta);
+    S l2 = fabs(a.ut);
+    S l3 = harten(a.ut + a.ct, delta);
+    S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
+    S D0 = (A1 + A2) + A3;
+    S D1 = (A1 * (a.ut - a.ct) + A2 * a.ut) + A3 * (a.ut + a.ct);
+    S D2 = ((A1 * a.vt + A2 * a.vt) + A3 * a.vt) + As * dv;
+    S D3 = ((A1 * (a.Ht - a.ct * a.ut) + A2 * a.kt) + A3 * (a.Ht + a.ct * a.ut))
                 + As * ((a.ut * du + a.vt * dv) - a.ut * du);
-    double mL = rL * uL, mR = rR * uR;
+    S mL = rL * uL, mR = rR * uR;
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * (((mL * uL + pL) + (mR * uR + pR)) - D1);
     F[2] = 0.5 * ((mL * vL + mR * vR) - D2);
@@ -105,27 +111,28 @@ __device__ __forceinline__ void roe_x(const double *L, const double *R, const St
 }
 
 // Roe flux through a y-face (unit normal (0, 1)), exact specialisation as above.
-__device__ __forceinline__ void roe_y(const double *L, const double *R, const StencilConsts &C, double *F)
+template <class S>
+__device__ __forceinline__ void roe_y(const S *L, const S *R, const StencilConsts &C, S *F)
 {
-    RoeAvg a = roe_avg(L, R, C);
-    double rL = L[0], uL = L[1], vL = L[2], pL = L[3];
-    double rR = R[0], uR = R[1], vR = R[2], pR = R[3];
-    double drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL;
-    double rcdq = a.rt * a.ct * dv;
-    double a1 = 0.5 * (dp - rcdq) * a.inv_c2;
-    double a2 = drho - dp * a.inv_c2;
-    double a3 = 0.5 * (dp + rcdq) * a.inv_c2;
-    double delta = C.efix * (fabs(a.vt) + a.ct);
-    double l1 = harten(a.vt - a.ct, delta);
-    double l2 = fabs(a.vt);
-    double l3 = harten(a.vt + a.ct, delta);
-    double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
-    double D0 = (A1 + A2) + A3;
-    double D1 = ((A1 * a.ut + A2 * a.ut) + A3 * a.ut) + As * du;
-    double D2 = (A1 * (a.vt - a.ct) + A2 * a.vt) + A3 * (a.vt + a.ct);
-    double D3 = ((A1 * (a.Ht - a.ct * a.vt) + A2 * a.kt) + A3 * (a.Ht + a.ct * a.vt))
+    RoeAvg<S> a = roe_avg(L, R, C);
+    S rL = L[0], uL = L[1], vL = L[2], pL = L[3];
+    S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
+    S drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL;
+    S rcdq = a.rt * a.ct * dv;
+    S a1 = 0.5 * (dp - rcdq) * a.inv_c2;
+    S a2 = drho - dp * a.inv_c2;
+    S a3 = 0.5 * (dp + rcdq) * a.inv_c2;
+    S delta = C.efix * (fabs(a.vt) + a.ct);
+    S l1 = harten(a.vt - a.ct, delta);
+    S l2 = fabs(a.vt);
+    S l3 = harten(a.vt + a.ct, delta);
+    S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
+    S D0 = (A1 + A2) + A3;
+    S D1 = ((A1 * a.ut + A2 * a.ut) + A3 * a.ut) + As * du;
+    S D2 = (A1 * (a.vt - a.ct) + A2 * a.vt) + A3 * (a.vt + a.ct);
+    S D3 = ((A1 * (a.Ht - a.ct * a.vt) + A2 * a.kt) + A3 * (a.Ht + a.ct * a.vt))
                 + As * ((a.ut * du + a.vt * dv) - a.vt * dv);
-    double mL = rL * vL, mR = rR * vR;
+    S mL = rL * vL, mR = rR * vR;
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * ((mL * uL + mR * uR) - D1);
     F[2] = 0.5 * (((mL * vL + pL) + (mR * vR + pR)) - D2);
@@ -133,33 +140,34 @@ __device__ __forceinline__ void roe_y(const double *L, const double *R, const St
 }
 
 // Roe flux for a general unit normal (nx, ny) (curvilinear grids).
-__device__ __forceinline__ void roe_n(const double *L, const double *R, double nx, double ny,
-                                      const StencilConsts &C, double *F)
+template <class S>
+__device__ __forceinline__ void roe_n(const S *L, const S *R, double nx, double ny,
+                                      const StencilConsts &C, S *F)
 {
-    double rL = L[0], uL = L[1], vL = L[2], pL = L[3];
-    double rR = R[0], uR = R[1], vR = R[2], pR = R[3];
-    double qnL = uL * nx + vL * ny;
-    double qnR = uR * nx + vR * ny;
-    RoeAvg a = roe_avg(L, R, C);
-    double qnt = a.ut * nx + a.vt * ny;
-    double drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
-    double rcdq = a.rt * a.ct * dqn;
-    double a1 = 0.5 * (dp - rcdq) * a.inv_c2;
-    double a2 = drho - dp * a.inv_c2;
-    double a3 = 0.5 * (dp + rcdq) * a.inv_c2;
-    double delta = C.efix * (fabs(qnt) + a.ct);
-    double l1 = harten(qnt - a.ct, delta);
-    double l2 = fabs(qnt);
-    double l3 = harten(qnt + a.ct, delta);
-    double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
-    double D0 = (A1 + A2) + A3;
-    double D1 = ((A1 * (a.ut - a.ct * nx) + A2 * a.ut) + A3 * (a.ut + a.ct * nx)) + As * (du - dqn * nx);
-    double D2 = ((A1 * (a.vt - a.ct * ny) + A2 * a.vt) + A3 * (a.vt + a.ct * ny)) + As * (dv - dqn * ny);
-    double D3 = ((A1 * (a.Ht - a.ct * qnt) + A2 * a.kt) + A3 * (a.Ht + a.ct * qnt))
+    S rL = L[0], uL = L[1], vL = L[2], pL = L[3];
+    S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
+    S qnL = uL * nx + vL * ny;
+    S qnR = uR * nx + vR * ny;
+    RoeAvg<S> a = roe_avg(L, R, C);
+    S qnt = a.ut * nx + a.vt * ny;
+    S drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
+    S rcdq = a.rt * a.ct * dqn;
+    S a1 = 0.5 * (dp - rcdq) * a.inv_c2;
+    S a2 = drho - dp * a.inv_c2;
+    S a3 = 0.5 * (dp + rcdq) * a.inv_c2;
+    S delta = C.efix * (fabs(qnt) + a.ct);
+    S l1 = harten(qnt - a.ct, delta);
+    S l2 = fabs(qnt);
+    S l3 = harten(qnt + a.ct, delta);
+    S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
+    S D0 = (A1 + A2) + A3;
+    S D1 = ((A1 * (a.ut - a.ct * nx) + A2 * a.ut) + A3 * (a.ut + a.ct * nx)) + As * (du - dqn * nx);
+    S D2 = ((A1 * (a.vt - a.ct * ny) + A2 * a.vt) + A3 * (a.vt + a.ct * ny)) + As * (dv - dqn * ny);
+    S D3 = ((A1 * (a.Ht - a.ct * qnt) + A2 * a.kt) + A3 * (a.Ht + a.ct * qnt))
                 + As * ((a.ut * du + a.vt * dv) - qnt * dqn);
-    double mL = rL * qnL, mR = rR * qnR;
-    double FL1 = mL * uL + pL * nx, FR1 = mR * uR + pR * nx;
-    double FL2 = mL * vL + pL * ny, FR2 = mR * vR + pR * ny;
+    S mL = rL * qnL, mR = rR * qnR;
+    S FL1 = mL * uL + pL * nx, FR1 = mR * uR + pR * nx;
+    S FL2 = mL * vL + pL * ny, FR2 = mR * vR + pR * ny;
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * ((FL1 + FR1) - D1);
     F[2] = 0.5 * ((FL2 + FR2) - D2);
@@ -167,46 +175,74 @@ __device__ __forceinline__ void roe_n(const double *L, const double *R, double n
 }
 
 // shared-memory tile of primitive variables (halo included)
+template <class S>
 struct Tile {
-    double r[EH][EW], u[EH][EW], v[EH][EW], p[EH][EW], T[EH][EW], mu[EH][EW];
+    S r[EH][EW], u[EH][EW], v[EH][EW], p[EH][EW], T[EH][EW], mu[EH][EW];
 };
+template <class S>
 struct Faces {
-    double fx[4][TY][TX + 1];
-    double fy[4][TY + 1][TX];
+    S fx[4][TY][TX + 1];
+    S fy[4][TY + 1][TX];
 };
 
-__device__ __forceinline__ double pick(const Tile &t, int k, int y, int x)
+template <class S>
+__device__ __forceinline__ S pick(const Tile<S> &t, int k, int y, int x)
 {
     return k == 0 ? t.r[y][x] : (k == 1 ? t.u[y][x] : (k == 2 ? t.v[y][x] : t.p[y][x]));
 }
 
-template <bool SUTH>
-__device__ __forceinline__ void store_prim(Tile &t, int ly, int lx, double rho, double mx, double my,
-                                           double E, bool mirror, const StencilConsts &C)
+template <bool SUTH, class S>
+__device__ __forceinline__ void store_prim(Tile<S> &t, int ly, int lx, S rho, S mx, S my,
+                                           S E, bool mirror, const StencilConsts &C)
 {
-    double rinv = 1.0 / rho;
-    double u = mx * rinv;
-    double v = my * rinv;
-    double p = C.gm1 * (E - 0.5 * (mx * u + my * v));
-    double T = p * rinv;
+    S rinv = 1.0 / rho;
+    S u = mx * rinv;
+    S v = my * rinv;
+    S p = C.gm1 * (E - 0.5 * (mx * u + my * v));
+    S T = p * rinv;
     t.r[ly][lx] = rho;
     t.u[ly][lx] = mirror ? -u : u;
     t.v[ly][lx] = mirror ? -v : v;
     t.p[ly][lx] = p;
     t.T[ly][lx] = T;
     if (SUTH) {
-        double tt = T * C.inv_tref;
+        S tt = T * C.inv_tref;
         t.mu[ly][lx] = C.mu * (tt * sqrt(tt)) * ((1.0 + C.suth_s) / (tt + C.suth_s));
     }
 }
 
-__device__ __forceinline__ double load_state(const StencilIO &io, const double (&cf)[kMaxAdd], double cff, size_t e)
+// state entry e: base + sum_t c_t add_t (+ cf addf); for dual numbers the
+// tangent is the direction of the exact JVP (dir or its binary32 form dirf)
+__device__ __forceinline__ double load_value(const StencilIO &io, const double (&cf)[kMaxAdd], double cff, size_t e)
 {
     double q = io.base[e];
     for (int t = 0; t < io.nadd; ++t) q = q + cf[t] * io.add[t][e];
     if (io.addf) q = q + cff * (double)io.addf[e];
     return q;
 }
+
+template <class S>
+__device__ __forceinline__ S load_state(const StencilIO &io, const double (&cf)[kMaxAdd], double cff, size_t e);
+
+template <>
+__device__ __forceinline__ double load_state<double>(const StencilIO &io, const double (&cf)[kMaxAdd], double cff,
+                                                     size_t e)
+{
+    return load_value(io, cf, cff, e);
+}
+
+template <>
+__device__ __forceinline__ Dual load_state<Dual>(const StencilIO &io, const double (&cf)[kMaxAdd], double cff, size_t e)
+{
+    return {load_value(io, cf, cff, e), io.dir ? io.dir[e] : (double)io.dirf[e]};
+}
+
+template <class S>
+__device__ __forceinline__ S lift(double x);
+template <>
+__device__ __forceinline__ double lift<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ Dual lift<Dual>(double x) { return {x, 0.0}; }
 
 __device__ __forceinline__ int wrapi(int i, int n)
 {
@@ -215,6 +251,8 @@ __device__ __forceinline__ int wrapi(int i, int n)
 }
 
 // ---- stage 3: balance + epilogue ---------------------------------------------
+// the launch output: t = (sub ? r - sub : r) * s1, out = add_out ? add_out + s2 t : t,
+// r the residual value (or the JVP tangent)
 __device__ __forceinline__ void epilogue_store(const StencilIO &io, double s1, double s2, size_t e, double r)
 {
     double t = io.sub ? (r - io.sub[e]) : r;
@@ -234,13 +272,13 @@ __device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd]
 }
 
 // ============================ uniform periodic grid ============================
-template <bool VISC, bool SUTH>
-__global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, const StencilIO io)
+template <bool VISC, bool SUTH, class S, int MINB>
+__global__ void __launch_bounds__(NT, MINB) cart_kernel(const StencilConsts C, const StencilIO io)
 {
     if (io.active && *io.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Tile &tl = *reinterpret_cast<Tile *>(smem_raw);
-    Faces &fc = *reinterpret_cast<Faces *>(smem_raw + sizeof(Tile));
+    Tile<S> &tl = *reinterpret_cast<Tile<S> *>(smem_raw);
+    Faces<S> &fc = *reinterpret_cast<Faces<S> *>(smem_raw + sizeof(Tile<S>));
 
     const int nx = C.nx, ny = C.ny;
     const size_t nc = (size_t)nx * ny;
@@ -253,11 +291,11 @@ __global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, cons
         int lx = idx % EW, ly = idx / EW;
         int gi = wrapi(i0 + lx - 2, nx), gj = wrapi(j0 + ly - 2, ny);
         size_t c = (size_t)gj * nx + gi;
-        double rho = load_state(io, cf, cff, c);
-        double mx = load_state(io, cf, cff, nc + c);
-        double my = load_state(io, cf, cff, 2 * nc + c);
-        double E = load_state(io, cf, cff, 3 * nc + c);
-        store_prim<SUTH>(tl, ly, lx, rho, mx, my, E, false, C);
+        S rho = load_state<S>(io, cf, cff, c);
+        S mx = load_state<S>(io, cf, cff, nc + c);
+        S my = load_state<S>(io, cf, cff, 2 * nc + c);
+        S E = load_state<S>(io, cf, cff, 3 * nc + c);
+        store_prim<SUTH, S>(tl, ly, lx, rho, mx, my, E, false, C);
     }
     __syncthreads();
 
@@ -265,25 +303,25 @@ __global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, cons
     for (int f = tid; f < NFX; f += NT) {
         int fx = f % (TX + 1), fy = f / (TX + 1);
         int y = fy + 2, xl = fx + 1, xr = fx + 2;
-        double WL[4], WR[4], F[4];
+        S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             muscl(pick(tl, k, y, xl - 1), pick(tl, k, y, xl), pick(tl, k, y, xr), pick(tl, k, y, xr + 1),
                   C.c_lo, C.c_hi, WL[k], WR[k]);
         roe_x(WL, WR, C, F);
         if (VISC) {
-            double ux = (tl.u[y][xr] - tl.u[y][xl]) * C.rdx;
-            double uy = ((tl.u[y + 1][xl] + tl.u[y + 1][xr]) - (tl.u[y - 1][xl] + tl.u[y - 1][xr])) * C.q_rdy;
-            double vx = (tl.v[y][xr] - tl.v[y][xl]) * C.rdx;
-            double vy = ((tl.v[y + 1][xl] + tl.v[y + 1][xr]) - (tl.v[y - 1][xl] + tl.v[y - 1][xr])) * C.q_rdy;
-            double Tx = (tl.T[y][xr] - tl.T[y][xl]) * C.rdx;
-            double mu_f = SUTH ? 0.5 * (tl.mu[y][xl] + tl.mu[y][xr]) : C.mu;
-            double u_f = 0.5 * (tl.u[y][xl] + tl.u[y][xr]);
-            double v_f = 0.5 * (tl.v[y][xl] + tl.v[y][xr]);
-            double div = ux + vy;
-            double txx = mu_f * (2.0 * ux - C.c23 * div);
-            double txy = mu_f * (uy + vx);
-            double kf = mu_f * C.kfac;
+            S ux = (tl.u[y][xr] - tl.u[y][xl]) * C.rdx;
+            S uy = ((tl.u[y + 1][xl] + tl.u[y + 1][xr]) - (tl.u[y - 1][xl] + tl.u[y - 1][xr])) * C.q_rdy;
+            S vx = (tl.v[y][xr] - tl.v[y][xl]) * C.rdx;
+            S vy = ((tl.v[y + 1][xl] + tl.v[y + 1][xr]) - (tl.v[y - 1][xl] + tl.v[y - 1][xr])) * C.q_rdy;
+            S Tx = (tl.T[y][xr] - tl.T[y][xl]) * C.rdx;
+            S mu_f = SUTH ? 0.5 * (tl.mu[y][xl] + tl.mu[y][xr]) : lift<S>(C.mu);
+            S u_f = 0.5 * (tl.u[y][xl] + tl.u[y][xr]);
+            S v_f = 0.5 * (tl.v[y][xl] + tl.v[y][xr]);
+            S div = ux + vy;
+            S txx = mu_f * (2.0 * ux - C.c23 * div);
+            S txy = mu_f * (uy + vx);
+            S kf = mu_f * C.kfac;
             F[1] = F[1] - txx;
             F[2] = F[2] - txy;
             F[3] = F[3] - ((u_f * txx + v_f * txy) + kf * Tx);
@@ -294,25 +332,25 @@ __global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, cons
     for (int f = tid; f < NFY; f += NT) {
         int fx = f % TX, fy = f / TX;
         int x = fx + 2, yb = fy + 1, yt = fy + 2;
-        double WL[4], WR[4], F[4];
+        S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             muscl(pick(tl, k, yb - 1, x), pick(tl, k, yb, x), pick(tl, k, yt, x), pick(tl, k, yt + 1, x),
                   C.c_lo, C.c_hi, WL[k], WR[k]);
         roe_y(WL, WR, C, F);
         if (VISC) {
-            double uy = (tl.u[yt][x] - tl.u[yb][x]) * C.rdy;
-            double ux = ((tl.u[yb][x + 1] + tl.u[yt][x + 1]) - (tl.u[yb][x - 1] + tl.u[yt][x - 1])) * C.q_rdx;
-            double vy = (tl.v[yt][x] - tl.v[yb][x]) * C.rdy;
-            double vx = ((tl.v[yb][x + 1] + tl.v[yt][x + 1]) - (tl.v[yb][x - 1] + tl.v[yt][x - 1])) * C.q_rdx;
-            double Ty = (tl.T[yt][x] - tl.T[yb][x]) * C.rdy;
-            double mu_f = SUTH ? 0.5 * (tl.mu[yb][x] + tl.mu[yt][x]) : C.mu;
-            double u_f = 0.5 * (tl.u[yb][x] + tl.u[yt][x]);
-            double v_f = 0.5 * (tl.v[yb][x] + tl.v[yt][x]);
-            double div = ux + vy;
-            double tyy = mu_f * (2.0 * vy - C.c23 * div);
-            double txy = mu_f * (uy + vx);
-            double kf = mu_f * C.kfac;
+            S uy = (tl.u[yt][x] - tl.u[yb][x]) * C.rdy;
+            S ux = ((tl.u[yb][x + 1] + tl.u[yt][x + 1]) - (tl.u[yb][x - 1] + tl.u[yt][x - 1])) * C.q_rdx;
+            S vy = (tl.v[yt][x] - tl.v[yb][x]) * C.rdy;
+            S vx = ((tl.v[yb][x + 1] + tl.v[yt][x + 1]) - (tl.v[yb][x - 1] + tl.v[yt][x - 1])) * C.q_rdx;
+            S Ty = (tl.T[yt][x] - tl.T[yb][x]) * C.rdy;
+            S mu_f = SUTH ? 0.5 * (tl.mu[yb][x] + tl.mu[yt][x]) : lift<S>(C.mu);
+            S u_f = 0.5 * (tl.u[yb][x] + tl.u[yt][x]);
+            S v_f = 0.5 * (tl.v[yb][x] + tl.v[yt][x]);
+            S div = ux + vy;
+            S tyy = mu_f * (2.0 * vy - C.c23 * div);
+            S txy = mu_f * (uy + vx);
+            S kf = mu_f * C.kfac;
             F[1] = F[1] - txy;
             F[2] = F[2] - tyy;
             F[3] = F[3] - ((u_f * txy + v_f * tyy) + kf * Ty);
@@ -328,10 +366,10 @@ __global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, cons
         size_t c = (size_t)gj * nx + gi;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            double dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
-            double dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
-            double r = -(dX * C.rdx + dY * C.rdy);
-            epilogue_store(io, s1, s2, k * nc + c, r);
+            S dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
+            S dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
+            S r = -(dX * C.rdx + dY * C.rdy);
+            epilogue_store(io, s1, s2, k * nc + c, result(r));
         }
     }
 }
@@ -340,13 +378,13 @@ __global__ void __launch_bounds__(NT, 3) cart_kernel(const StencilConsts C, cons
 // Ghost cells follow the boundary rules: j-ghosts of interior columns first,
 // then i-ghosts of every row (ghost rows included); periodic wraps, a wall
 // mirrors (rho, -u, -v, p), the far field is the free stream.
-template <bool VISC, bool SUTH>
-__global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, const CurvGeom G, const StencilIO io)
+template <bool VISC, bool SUTH, class S, int MINB>
+__global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, const CurvGeom G, const StencilIO io)
 {
     if (io.active && *io.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Tile &tl = *reinterpret_cast<Tile *>(smem_raw);
-    Faces &fc = *reinterpret_cast<Faces *>(smem_raw + sizeof(Tile));
+    Tile<S> &tl = *reinterpret_cast<Tile<S> *>(smem_raw);
+    Faces<S> &fc = *reinterpret_cast<Faces<S> *>(smem_raw + sizeof(Tile<S>));
 
     const int nx = C.nx, ny = C.ny;
     const size_t nc = (size_t)nx * ny;
@@ -376,19 +414,19 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
         gi = min(max(gi, 0), nx - 1);
         gj = min(max(gj, 0), ny - 1);
         if (inf) {
-            tl.r[ly][lx] = C.prim_inf[0];
-            tl.u[ly][lx] = mirror ? -C.prim_inf[1] : C.prim_inf[1];
-            tl.v[ly][lx] = mirror ? -C.prim_inf[2] : C.prim_inf[2];
-            tl.p[ly][lx] = C.prim_inf[3];
-            tl.T[ly][lx] = C.prim_inf[4];
-            if (SUTH) tl.mu[ly][lx] = C.prim_inf[5];
+            tl.r[ly][lx] = lift<S>(C.prim_inf[0]);
+            tl.u[ly][lx] = lift<S>(mirror ? -C.prim_inf[1] : C.prim_inf[1]);
+            tl.v[ly][lx] = lift<S>(mirror ? -C.prim_inf[2] : C.prim_inf[2]);
+            tl.p[ly][lx] = lift<S>(C.prim_inf[3]);
+            tl.T[ly][lx] = lift<S>(C.prim_inf[4]);
+            if (SUTH) tl.mu[ly][lx] = lift<S>(C.prim_inf[5]);
         } else {
             size_t c = (size_t)gj * nx + gi;
-            double rho = load_state(io, cf, cff, c);
-            double mx = load_state(io, cf, cff, nc + c);
-            double my = load_state(io, cf, cff, 2 * nc + c);
-            double E = load_state(io, cf, cff, 3 * nc + c);
-            store_prim<SUTH>(tl, ly, lx, rho, mx, my, E, mirror, C);
+            S rho = load_state<S>(io, cf, cff, c);
+            S mx = load_state<S>(io, cf, cff, nc + c);
+            S my = load_state<S>(io, cf, cff, 2 * nc + c);
+            S E = load_state<S>(io, cf, cff, 3 * nc + c);
+            store_prim<SUTH, S>(tl, ly, lx, rho, mx, my, E, mirror, C);
         }
     }
     __syncthreads();
@@ -400,7 +438,7 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
         if (gi > nx || gj >= ny) continue;
         size_t fi = (size_t)gj * (nx + 1) + gi;
         int y = fy + 2, xl = fx + 1, xr = fx + 2;
-        double WL[4], WR[4], F[4];
+        S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             muscl(pick(tl, k, y, xl - 1), pick(tl, k, y, xl), pick(tl, k, y, xr), pick(tl, k, y, xr + 1),
@@ -409,40 +447,40 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
         roe_n(WL, WR, nxf, nyf, C, F);
         if (VISC) {
             double c0 = G.ic0[fi], c1 = G.ic1[fi], c2 = G.ic2[fi], c3 = G.ic3[fi];
-            double g[6];
+            S g[6];
             // vertex (i, j) = P1 from rows y-1, y; vertex (i, j+1) = P3 from rows y, y+1
             {
-                double a = 0.25 * (((tl.u[y - 1][xl] + tl.u[y - 1][xr]) + tl.u[y][xl]) + tl.u[y][xr]);
-                double b = 0.25 * (((tl.u[y][xl] + tl.u[y][xr]) + tl.u[y + 1][xl]) + tl.u[y + 1][xr]);
-                double dC = tl.u[y][xr] - tl.u[y][xl], dV = b - a;
+                S a = 0.25 * (((tl.u[y - 1][xl] + tl.u[y - 1][xr]) + tl.u[y][xl]) + tl.u[y][xr]);
+                S b = 0.25 * (((tl.u[y][xl] + tl.u[y][xr]) + tl.u[y + 1][xl]) + tl.u[y + 1][xr]);
+                S dC = tl.u[y][xr] - tl.u[y][xl], dV = b - a;
                 g[0] = dC * c0 + dV * c1;
                 g[1] = dC * c2 + dV * c3;
             }
             {
-                double a = 0.25 * (((tl.v[y - 1][xl] + tl.v[y - 1][xr]) + tl.v[y][xl]) + tl.v[y][xr]);
-                double b = 0.25 * (((tl.v[y][xl] + tl.v[y][xr]) + tl.v[y + 1][xl]) + tl.v[y + 1][xr]);
-                double dC = tl.v[y][xr] - tl.v[y][xl], dV = b - a;
+                S a = 0.25 * (((tl.v[y - 1][xl] + tl.v[y - 1][xr]) + tl.v[y][xl]) + tl.v[y][xr]);
+                S b = 0.25 * (((tl.v[y][xl] + tl.v[y][xr]) + tl.v[y + 1][xl]) + tl.v[y + 1][xr]);
+                S dC = tl.v[y][xr] - tl.v[y][xl], dV = b - a;
                 g[2] = dC * c0 + dV * c1;
                 g[3] = dC * c2 + dV * c3;
             }
             {
-                double a = 0.25 * (((tl.T[y - 1][xl] + tl.T[y - 1][xr]) + tl.T[y][xl]) + tl.T[y][xr]);
-                double b = 0.25 * (((tl.T[y][xl] + tl.T[y][xr]) + tl.T[y + 1][xl]) + tl.T[y + 1][xr]);
-                double dC = tl.T[y][xr] - tl.T[y][xl], dV = b - a;
+                S a = 0.25 * (((tl.T[y - 1][xl] + tl.T[y - 1][xr]) + tl.T[y][xl]) + tl.T[y][xr]);
+                S b = 0.25 * (((tl.T[y][xl] + tl.T[y][xr]) + tl.T[y + 1][xl]) + tl.T[y + 1][xr]);
+                S dC = tl.T[y][xr] - tl.T[y][xl], dV = b - a;
                 g[4] = dC * c0 + dV * c1;
                 g[5] = dC * c2 + dV * c3;
             }
-            double mu_f = SUTH ? 0.5 * (tl.mu[y][xl] + tl.mu[y][xr]) : C.mu;
-            double u_f = 0.5 * (tl.u[y][xl] + tl.u[y][xr]);
-            double v_f = 0.5 * (tl.v[y][xl] + tl.v[y][xr]);
-            double div = g[0] + g[3];
-            double txx = mu_f * (2.0 * g[0] - C.c23 * div);
-            double tyy = mu_f * (2.0 * g[3] - C.c23 * div);
-            double txy = mu_f * (g[1] + g[2]);
-            double tnx = txx * nxf + txy * nyf;
-            double tny = txy * nxf + tyy * nyf;
-            double kf = mu_f * C.kfac;
-            double dTn = g[4] * nxf + g[5] * nyf;
+            S mu_f = SUTH ? 0.5 * (tl.mu[y][xl] + tl.mu[y][xr]) : lift<S>(C.mu);
+            S u_f = 0.5 * (tl.u[y][xl] + tl.u[y][xr]);
+            S v_f = 0.5 * (tl.v[y][xl] + tl.v[y][xr]);
+            S div = g[0] + g[3];
+            S txx = mu_f * (2.0 * g[0] - C.c23 * div);
+            S tyy = mu_f * (2.0 * g[3] - C.c23 * div);
+            S txy = mu_f * (g[1] + g[2]);
+            S tnx = txx * nxf + txy * nyf;
+            S tny = txy * nxf + tyy * nyf;
+            S kf = mu_f * C.kfac;
+            S dTn = g[4] * nxf + g[5] * nyf;
             F[1] = F[1] - tnx;
             F[2] = F[2] - tny;
             F[3] = F[3] - ((u_f * tnx + v_f * tny) + kf * dTn);
@@ -457,7 +495,7 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
         if (gi >= nx || gj > ny) continue;
         size_t fi = (size_t)gj * nx + gi;
         int x = fx + 2, yb = fy + 1, yt = fy + 2;
-        double WL[4], WR[4], F[4];
+        S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             muscl(pick(tl, k, yb - 1, x), pick(tl, k, yb, x), pick(tl, k, yt, x), pick(tl, k, yt + 1, x),
@@ -466,40 +504,40 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
         roe_n(WL, WR, nxf, nyf, C, F);
         if (VISC) {
             double c0 = G.jc0[fi], c1 = G.jc1[fi], c2 = G.jc2[fi], c3 = G.jc3[fi];
-            double g[6];
+            S g[6];
             // vertex (i+1, j) = P1 from columns x, x+1; vertex (i, j) = P3 from columns x-1, x
             {
-                double a = 0.25 * (((tl.u[yb][x] + tl.u[yb][x + 1]) + tl.u[yt][x]) + tl.u[yt][x + 1]);
-                double b = 0.25 * (((tl.u[yb][x - 1] + tl.u[yb][x]) + tl.u[yt][x - 1]) + tl.u[yt][x]);
-                double dC = tl.u[yt][x] - tl.u[yb][x], dV = b - a;
+                S a = 0.25 * (((tl.u[yb][x] + tl.u[yb][x + 1]) + tl.u[yt][x]) + tl.u[yt][x + 1]);
+                S b = 0.25 * (((tl.u[yb][x - 1] + tl.u[yb][x]) + tl.u[yt][x - 1]) + tl.u[yt][x]);
+                S dC = tl.u[yt][x] - tl.u[yb][x], dV = b - a;
                 g[0] = dC * c0 + dV * c1;
                 g[1] = dC * c2 + dV * c3;
             }
             {
-                double a = 0.25 * (((tl.v[yb][x] + tl.v[yb][x + 1]) + tl.v[yt][x]) + tl.v[yt][x + 1]);
-                double b = 0.25 * (((tl.v[yb][x - 1] + tl.v[yb][x]) + tl.v[yt][x - 1]) + tl.v[yt][x]);
-                double dC = tl.v[yt][x] - tl.v[yb][x], dV = b - a;
+                S a = 0.25 * (((tl.v[yb][x] + tl.v[yb][x + 1]) + tl.v[yt][x]) + tl.v[yt][x + 1]);
+                S b = 0.25 * (((tl.v[yb][x - 1] + tl.v[yb][x]) + tl.v[yt][x - 1]) + tl.v[yt][x]);
+                S dC = tl.v[yt][x] - tl.v[yb][x], dV = b - a;
                 g[2] = dC * c0 + dV * c1;
                 g[3] = dC * c2 + dV * c3;
             }
             {
-                double a = 0.25 * (((tl.T[yb][x] + tl.T[yb][x + 1]) + tl.T[yt][x]) + tl.T[yt][x + 1]);
-                double b = 0.25 * (((tl.T[yb][x - 1] + tl.T[yb][x]) + tl.T[yt][x - 1]) + tl.T[yt][x]);
-                double dC = tl.T[yt][x] - tl.T[yb][x], dV = b - a;
+                S a = 0.25 * (((tl.T[yb][x] + tl.T[yb][x + 1]) + tl.T[yt][x]) + tl.T[yt][x + 1]);
+                S b = 0.25 * (((tl.T[yb][x - 1] + tl.T[yb][x]) + tl.T[yt][x - 1]) + tl.T[yt][x]);
+                S dC = tl.T[yt][x] - tl.T[yb][x], dV = b - a;
                 g[4] = dC * c0 + dV * c1;
                 g[5] = dC * c2 + dV * c3;
             }
-            double mu_f = SUTH ? 0.5 * (tl.mu[yb][x] + tl.mu[yt][x]) : C.mu;
-            double u_f = 0.5 * (tl.u[yb][x] + tl.u[yt][x]);
-            double v_f = 0.5 * (tl.v[yb][x] + tl.v[yt][x]);
-            double div = g[0] + g[3];
-            double txx = mu_f * (2.0 * g[0] - C.c23 * div);
-            double tyy = mu_f * (2.0 * g[3] - C.c23 * div);
-            double txy = mu_f * (g[1] + g[2]);
-            double tnx = txx * nxf + txy * nyf;
-            double tny = txy * nxf + tyy * nyf;
-            double kf = mu_f * C.kfac;
-            double dTn = g[4] * nxf + g[5] * nyf;
+            S mu_f = SUTH ? 0.5 * (tl.mu[yb][x] + tl.mu[yt][x]) : lift<S>(C.mu);
+            S u_f = 0.5 * (tl.u[yb][x] + tl.u[yt][x]);
+            S v_f = 0.5 * (tl.v[yb][x] + tl.v[yt][x]);
+            S div = g[0] + g[3];
+            S txx = mu_f * (2.0 * g[0] - C.c23 * div);
+            S tyy = mu_f * (2.0 * g[3] - C.c23 * div);
+            S txy = mu_f * (g[1] + g[2]);
+            S tnx = txx * nxf + txy * nyf;
+            S tny = txy * nxf + tyy * nyf;
+            S kf = mu_f * C.kfac;
+            S dTn = g[4] * nxf + g[5] * nyf;
             F[1] = F[1] - tnx;
             F[2] = F[2] - tny;
             F[3] = F[3] - ((u_f * tnx + v_f * tny) + kf * dTn);
@@ -517,89 +555,93 @@ __global__ void __launch_bounds__(NT, 3) curv_kernel(const StencilConsts C, cons
         double iv = G.inv_vol[c];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            double dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
-            double dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
-            double r = -((dX + dY) * iv);
-            epilogue_store(io, s1, s2, k * nc + c, r);
+            S dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
+            S dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
+            S r = -((dX + dY) * iv);
+            epilogue_store(io, s1, s2, k * nc + c, result(r));
         }
     }
 }
 
 // Lorenz-96 (appendix): f_i = (u_{i+1} - u_{i-2}) u_{i-1} - u_i + F, periodic,
-// with the stencil launch's state formation and epilogue.
+// with the stencil launch's state formation and epilogue (dual numbers: the
+// exact JVP along io.dir / io.dirf).
+template <class S>
 __global__ void lorenz_kernel(const StencilConsts C, const StencilIO io, int n)
 {
     if (io.active && *io.active == 0) return;
-    double cf[kMaxAdd];
-#pragma unroll
-    for (int t = 0; t < kMaxAdd; ++t) cf[t] = io.coef_dev[t] ? io.coef[t] * *io.coef_dev[t] : io.coef[t];
-    const double s1 = io.s1_dev ? io.s1 * *io.s1_dev : io.s1;
-    const double s2 = io.s2_dev ? io.s2 * *io.s2_dev : io.s2;
-    const double cff = io.coef_f_dev ? io.coef_f * *io.coef_f_dev : io.coef_f;
+    double cf[kMaxAdd], cff, s1, s2;
+    coefs(io, cf, cff, s1, s2);
     auto q = [&](int i) {
         i = (i % n + n) % n;
-        double v = io.base[i];
-        for (int t = 0; t < io.nadd; ++t) v = v + cf[t] * io.add[t][i];
-        if (io.addf) v = v + cff * (double)io.addf[i];
-        return v;
+        return load_state<S>(io, cf, cff, (size_t)i);
     };
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double r = ((q(i + 1) - q(i - 2)) * q(i - 1) - q(i)) + C.lorenz_f;
-        double t = io.sub ? (r - io.sub[i]) : r;
-        t = t * s1;
-        double o = io.add_out ? io.add_out[i] + s2 * t : t;
-        io.out[i] = o;
-        if (!isfinite(o)) atomicOr(io.status, kStatusNonfinite);
+        S r = ((q(i + 1) - q(i - 2)) * q(i - 1) - q(i)) + C.lorenz_f;
+        epilogue_store(io, s1, s2, (size_t)i, result(r));
     }
 }
-
 
 cudaError_t launch_lorenz(const StencilConsts &c, const StencilIO &io, int n, cudaStream_t s)
 {
-    lorenz_kernel<<<(n + 255) / 256, 256, 0, s>>>(c, io, n);
+    if (io.dir || io.dirf) lorenz_kernel<Dual><<<(n + 255) / 256, 256, 0, s>>>(c, io, n);
+    else lorenz_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(c, io, n);
     return cudaGetLastError();
 }
 
-template <bool V, bool S>
+template <bool V, bool SU, class S>
 static cudaError_t launch_cart_t(const StencilConsts &c, const StencilIO &io, cudaStream_t s)
 {
-    const size_t smem = sizeof(Tile) + sizeof(Faces);
+    constexpr int MINB = sizeof(S) == sizeof(double) ? 3 : 1;
+    const size_t smem = sizeof(Tile<S>) + sizeof(Faces<S>);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(cart_kernel<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(cart_kernel<V, SU, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((c.nx + TX - 1) / TX, (c.ny + TY - 1) / TY);
-    cart_kernel<V, S><<<grid, NT, smem, s>>>(c, io);
+    cart_kernel<V, SU, S, MINB><<<grid, NT, smem, s>>>(c, io);
     return cudaGetLastError();
 }
 
-template <bool V, bool S>
+template <bool V, bool SU, class S>
 static cudaError_t launch_curv_t(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s)
 {
-    const size_t smem = sizeof(Tile) + sizeof(Faces);
+    constexpr int MINB = sizeof(S) == sizeof(double) ? 3 : 1;
+    const size_t smem = sizeof(Tile<S>) + sizeof(Faces<S>);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(curv_kernel<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(curv_kernel<V, SU, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((c.nx + TX - 1) / TX, (c.ny + TY - 1) / TY);
-    curv_kernel<V, S><<<grid, NT, smem, s>>>(c, g, io);
+    curv_kernel<V, SU, S, MINB><<<grid, NT, smem, s>>>(c, g, io);
     return cudaGetLastError();
 }
 
+// residual / FD-JVP launches use binary64 scalars; a launch with a direction
+// (io.dir or io.dirf) runs the dual-number kernel and writes the exact JVP
 cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_t s)
 {
-    if (!c.viscous) return launch_cart_t<false, false>(c, io, s);
-    return c.sutherland ? launch_cart_t<true, true>(c, io, s) : launch_cart_t<true, false>(c, io, s);
+    const bool dual = io.dir || io.dirf;
+    if (!c.viscous) return dual ? launch_cart_t<false, false, Dual>(c, io, s) : launch_cart_t<false, false, double>(c, io, s);
+    if (c.sutherland)
+        return dual ? launch_cart_t<true, true, Dual>(c, io, s) : launch_cart_t<true, true, double>(c, io, s);
+    return dual ? launch_cart_t<true, false, Dual>(c, io, s) : launch_cart_t<true, false, double>(c, io, s);
 }
 
 cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s)
 {
-    if (!c.viscous) return launch_curv_t<false, false>(c, g, io, s);
-    return c.sutherland ? launch_curv_t<true, true>(c, g, io, s) : launch_curv_t<true, false>(c, g, io, s);
+    const bool dual = io.dir || io.dirf;
+    if (!c.viscous)
+        return dual ? launch_curv_t<false, false, Dual>(c, g, io, s) : launch_curv_t<false, false, double>(c, g, io, s);
+    if (c.sutherland)
+        return dual ? launch_curv_t<true, true, Dual>(c, g, io, s) : launch_curv_t<true, true, double>(c, g, io, s);
+    return dual ? launch_curv_t<true, false, Dual>(c, g, io, s) : launch_curv_t<true, false, double>(c, g, io, s);
 }
 
 }  // namespace ROK_NS

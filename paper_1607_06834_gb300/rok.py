@@ -43,6 +43,7 @@ class ProblemDesc(ctypes.Structure):
         ('q_inf', ctypes.c_double * 4),
         ('muscl_kappa', ctypes.c_double), ('entropy_fix', ctypes.c_double), ('lorenz_f', ctypes.c_double),
         ('krylov_max', ctypes.c_int), ('rounding', ctypes.c_int), ('basis', ctypes.c_int),
+        ('jvp', ctypes.c_int),
     ]
 
 
@@ -143,7 +144,7 @@ class Context:
         return self._stage, y
 
 
-def _desc(problem, krylov_max, rounding, basis=0):
+def _desc(problem, krylov_max, rounding, basis=0, jvp=0):
     d = ProblemDesc()
     d.kind = int(problem.kind)
     d.nx, d.ny = int(problem.nx), int(problem.ny)
@@ -164,14 +165,15 @@ def _desc(problem, krylov_max, rounding, basis=0):
     d.krylov_max = int(krylov_max)
     d.rounding = int(rounding)
     d.basis = int(basis)
+    d.jvp = int(jvp)
     return d, keep
 
 
-def rok_init(problem, krylov_max=20, rounding=ROK_ROUND_FAST, stream=None, basis=ROK_BASIS_FP64):
+def rok_init(problem, krylov_max=20, rounding=ROK_ROUND_FAST, stream=None, basis=ROK_BASIS_FP64, jvp=ROK_JVP_FD):
     """Create a context (``rok_init``) for a :class:`workloads.FlowProblem`."""
     if stream is None:
         stream = torch.cuda.current_stream()
-    d, keep = _desc(problem, krylov_max, rounding, basis)
+    d, keep = _desc(problem, krylov_max, rounding, basis, jvp)
     h = ctypes.c_void_p()
     _check(_lib.rok_init(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream)), 'rok_init')
     del keep

@@ -321,3 +321,35 @@ def test_mixed_rok_fast_taylor_green_error_vs_fp64(rok):
     err = rel_l2(host(y), y64)
     print('mixed-precision Taylor-Green 64^2, 10 ROK4 steps, rel L2 vs FP64: %.3e' % err)
     assert err <= 1e-6
+
+
+# ---- ROK4 with exact Jacobian-vector products (NEXT row f3) --------------------
+
+@pytest.mark.parametrize('mode', ['fast', 'strict'])
+def test_exact_jvp_rok_ten_steps(rok, mode):
+    # without the FD quotient there is no rounding amplification: the FMA build
+    # meets the 1e-9 bar after 10 steps as well
+    prob, y0 = W.isentropic_vortex(64)
+    M = 12
+    ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()),
+                       jvp=rok.ROK_JVP_EXACT)
+    h = I.dt_from_cfl(prob, y0, 5.0)
+    y = dev(y0)
+    yo = y0.copy()
+    sys_ = core.ExactSystem(prob)
+    for _ in range(10):
+        rok.rok_step(ctx, y, h, M)
+        yo = I.rok_step(sys_, yo, h, M)
+    err = rel_l2(host(y), yo)
+    print('exact-JVP ROK4 vortex 64^2 (%s), 10 steps, rel L2 vs oracle: %.3e' % (mode, err))
+    assert err <= 1e-9
+
+
+def test_exact_jvp_esdirk_and_lorenz_order(rok):
+    prob, y0 = W.taylor_green(32, reynolds=200.0)
+    h = I.dt_from_cfl(prob, y0, 6.0)
+    ctx = rok.rok_init(prob, krylov_max=30, jvp=rok.ROK_JVP_EXACT)
+    y = dev(y0)
+    rok.esdirk_step(ctx, y, h)
+    yo = I.esdirk_step(core.ExactSystem(prob), y0, h)
+    assert rel_l2(host(y), yo) <= 1e-8

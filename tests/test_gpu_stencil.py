@@ -103,3 +103,18 @@ def test_nonfinite_detected(rok):
         rok.rok_sync(ctx)
     assert e.value.status == rok.ROK_ERR_NONFINITE
     rok.rok_sync(ctx)   # latched status was cleared
+
+
+# ---- exact JVP (forward-mode dual numbers) vs the complex-step oracle ----------
+
+@pytest.mark.parametrize('mode', ['fast', 'strict'])
+@pytest.mark.parametrize('case', CASES, ids=IDS)
+def test_exact_jvp_matches_complex_step(rok, case, mode):
+    # both are the derivative of the same discrete residual to rounding: 1e-12
+    name, prob, y = case
+    ctx = rok.rok_init(prob, krylov_max=4, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+    rng = np.random.default_rng(21)
+    v = rng.normal(size=y.shape)
+    w = host(rok.rok_jvp(ctx, dev(y), dev(v), mode=rok.ROK_JVP_EXACT))
+    wo = core.jvp_exact(prob, y, v)
+    assert np.linalg.norm(w - wo) <= 1e-12 * np.linalg.norm(wo), (name, np.linalg.norm(w - wo) / np.linalg.norm(wo))

@@ -235,3 +235,44 @@ def test_cfl_dt_uniform_closed_form():
     c = np.sqrt(1.4 * p / rho)
     dx = prob.lx / prob.nx
     assert np.isclose(dt, 1.0 / np.max((np.abs(u) + c) / dx + (np.abs(v) + c) / dx), rtol=1e-13)
+
+
+# ---- exact JVP (complex step) -------------------------------------------------
+
+@pytest.mark.parametrize('which', ['vortex', 'tgv', 'ogrid'])
+def test_complex_step_jvp_matches_dense_jacobian(which):
+    if which == 'vortex':
+        prob, y = W.isentropic_vortex(8)
+    elif which == 'tgv':
+        prob, y = W.taylor_green(8, reynolds=100.0)
+        prob = W.FlowProblem(**{**prob.__dict__, 'sutherland_s': 0.4, 't_ref': 70.0})
+    else:
+        prob, y, _ = W.cylinder_ogrid(6, 12)
+        y = y + 0.02 * W.random_smooth_state(prob, seed=1)
+    N = y.size
+    rng = np.random.default_rng(2)
+    v = rng.normal(size=y.shape)
+    w = core.jvp_exact(prob, y, v)
+    # fourth-order central differences, column by column of the dense Jacobian
+    hc = 1e-4
+    J = np.empty((N, N))
+    for c in range(N):
+        e = np.zeros(N); e[c] = hc
+        e = e.reshape(y.shape)
+        J[:, c] = ((-core.residual(prob, y + 2 * e) + 8 * core.residual(prob, y + e)
+                    - 8 * core.residual(prob, y - e) + core.residual(prob, y - 2 * e)) / (12 * hc)).ravel()
+    ref = J @ v.ravel()
+    assert np.linalg.norm(w.ravel() - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_complex_step_is_linear_and_matches_fd_limit():
+    prob, y = W.taylor_green(16, reynolds=200.0)
+    rng = np.random.default_rng(4)
+    v1, v2 = rng.normal(size=y.shape), rng.normal(size=y.shape)
+    w1, w2 = core.jvp_exact(prob, y, v1), core.jvp_exact(prob, y, v2)
+    w12 = core.jvp_exact(prob, y, 2.0 * v1 - 3.0 * v2)
+    assert np.abs(w12 - (2.0 * w1 - 3.0 * w2)).max() <= 1e-12 * np.abs(w12).max()
+    # the one-sided FD quotient approaches it at first order in eps
+    f0 = core.residual(prob, y)
+    e = [np.linalg.norm(core.jvp_fd(prob, y, v1, f0, 2.0 ** -k) - w1) for k in (10, 12, 14)]
+    assert 3.5 < e[0] / e[1] < 4.5 and 3.5 < e[1] / e[2] < 4.5
