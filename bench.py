@@ -106,6 +106,22 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_timing(ms_local, units_local, dist_ok):
+    """Whole-job timing of N replicas: the step time is the maximum over ranks,
+    the value the units all ranks processed divided by that time (weak scaling,
+    no data-path collective: only this scalar reduction and the barriers)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64)
+    if dist_ok:
+        mx = t[:1].clone()
+        tot = t[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        return float(mx.item()), float(tot.item())
+    return float(ms_local), float(units_local)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
