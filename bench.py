@@ -54,8 +54,9 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
-    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before the
+    warm-up; only the samples taken inside the timed window are summarised."""
+    Q = ('timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
          'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
          'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
 
@@ -63,11 +64,12 @@ class ClockSampler:
         self.index = index
         self.rows = []
         self.proc = None
+        self.window = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.index), '--query-gpu=' + self.Q,
-                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                          '--format=csv,noheader,nounits', '-lms', '50'],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -76,27 +78,34 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(',')])
+            self.rows.append((time.time(), [x.strip() for x in line.split(',')]))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
             return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace('.', '').isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace('.', '').isdigit()]
+        rows = [(t, r) for t, r in self.rows if len(r) >= 10]
+        inside = [(t, r) for t, r in rows if self.window and self.window[0] <= t <= self.window[1] + 0.06]
+        use = inside if inside else rows[-3:]
+        num = lambda x: float(x) if x.replace('.', '').isdigit() else None
+        sm = [num(r[2]) for _, r in use if num(r[2]) is not None]
+        mx = [num(r[3]) for _, r in use if num(r[3]) is not None]
         names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
         reasons = set()
-        for r in self.rows:
-            if len(r) >= 9:
-                for k, nm in enumerate(names):
-                    if r[5 + k].lower() == 'active':
-                        reasons.add(nm)
+        for _, r in use:
+            for k, nm in enumerate(names):
+                if r[6 + k].lower() == 'active':
+                    reasons.add(nm)
         return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': max(mx) if mx else None,
-                'reasons': sorted(reasons), 'samples': len(self.rows)}
+                'reasons': sorted(reasons), 'samples': len(use), 'samples_in_window': len(inside)}
 
 
 def _dist():
@@ -150,6 +159,8 @@ def run_ours(args):
 
     fp64_peak = rok.rok_fp64_fma_peak(20) if rank == 0 else None
 
+    sampler = ClockSampler(local)
+    sampler.start()
     if args.graph:
         rok.rok_set_graph(ctx, True)
     for _ in range(args.warmup):
@@ -159,11 +170,10 @@ def run_ours(args):
 
     rok.rok_get_counters(ctx, reset=True)
     rok.rok_set_stencil_timing(ctx, not args.graph)
-    sampler = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
-    sampler.start()
     t_wall0 = time.perf_counter()
+    t_epoch0 = time.time()
     for k in range(args.steps):
         flush.fill_(float(k))           # evict L2 between timed steps (outside the events)
         ev[k][0].record(stream)
@@ -171,6 +181,7 @@ def run_ours(args):
         ev[k][1].record(stream)
     barrier()
     wall = time.perf_counter() - t_wall0
+    sampler.mark(t_epoch0, time.time())
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     cnt = rok.rok_get_counters(ctx, reset=True)
@@ -508,7 +519,7 @@ def main():
     ap.add_argument('--mode', default='step', choices=['step', 'stencil'])
     ap.add_argument('--n', type=int, default=N_GRID)
     ap.add_argument('--gpus', type=int, default=1)
-    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--steps', type=int, default=30)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--rounding', default='fast', choices=['fast', 'strict'])

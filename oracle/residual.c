@@ -204,12 +204,15 @@ static void roe(const real_t *WL, const real_t *WR, double nx, double ny,
     real_t l2 = RABS(qnt);
     real_t l3 = harten(qnt + ct, delta);
 
+    /* sum_k |lam_k| a_k r_k with the eigenvectors r_1,3 = (1, u -+ c n, H -+ c q_n),
+     * r_2 = (1, u, k), shear r_s = (0, du - dq_n n, u.du - q_n dq_n), grouped by
+     * the wave sums sA = A1 + A3 and dA = A3 - A1 */
     real_t A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
-    real_t D0 = (A1 + A2) + A3;
-    real_t D1 = ((A1 * (ut - ct * nx) + A2 * ut) + A3 * (ut + ct * nx)) + As * (du - dqn * nx);
-    real_t D2 = ((A1 * (vt - ct * ny) + A2 * vt) + A3 * (vt + ct * ny)) + As * (dv - dqn * ny);
-    real_t D3 = ((A1 * (Ht - ct * qnt) + A2 * kt) + A3 * (Ht + ct * qnt))
-                + As * ((ut * du + vt * dv) - qnt * dqn);
+    real_t sA = A1 + A3, dA = A3 - A1;
+    real_t D0 = sA + A2;
+    real_t D1 = (ut * D0 + (ct * nx) * dA) + As * (du - dqn * nx);
+    real_t D2 = (vt * D0 + (ct * ny) * dA) + As * (dv - dqn * ny);
+    real_t D3 = ((Ht * sA + kt * A2) + (ct * qnt) * dA) + As * ((ut * du + vt * dv) - qnt * dqn);
 
     real_t mL = rL * qnL, mR = rR * qnR;
     real_t FL1 = mL * uL + pL * nx, FR1 = mR * uR + pR * nx;

@@ -81,7 +81,8 @@ __device__ __forceinline__ RoeAvg<S> roe_avg(const S *L, const S *R, const Stenc
 
 // Roe flux through an x-face (unit normal (1, 0)).  Exact specialisation of the
 // general-normal formula: only products by 1 or 0 and additions of a zero are
-// removed, which leave the IEEE result of the general form unchanged.
+// removed, which leave the IEEE result of the general form unchanged (e.g.
+// du - dqn nx = du - du = +0, so the shear term of D1 vanishes exactly).
 template <class S>
 __device__ __forceinline__ void roe_x(const S *L, const S *R, const StencilConsts &C, S *F)
 {
@@ -98,11 +99,11 @@ __device__ __forceinline__ void roe_x(const S *L, const S *R, const StencilConst
     S l2 = fabs(a.ut);
     S l3 = harten(a.ut + a.ct, delta);
     S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
-    S D0 = (A1 + A2) + A3;
-    S D1 = (A1 * (a.ut - a.ct) + A2 * a.ut) + A3 * (a.ut + a.ct);
-    S D2 = ((A1 * a.vt + A2 * a.vt) + A3 * a.vt) + As * dv;
-    S D3 = ((A1 * (a.Ht - a.ct * a.ut) + A2 * a.kt) + A3 * (a.Ht + a.ct * a.ut))
-                + As * ((a.ut * du + a.vt * dv) - a.ut * du);
+    S sA = A1 + A3, dA = A3 - A1;
+    S D0 = sA + A2;
+    S D1 = a.ut * D0 + a.ct * dA;
+    S D2 = a.vt * D0 + As * dv;
+    S D3 = ((a.Ht * sA + a.kt * A2) + (a.ct * a.ut) * dA) + As * ((a.ut * du + a.vt * dv) - a.ut * du);
     S mL = rL * uL, mR = rR * uR;
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * (((mL * uL + pL) + (mR * uR + pR)) - D1);
@@ -127,11 +128,11 @@ __device__ __forceinline__ void roe_y(const S *L, const S *R, const StencilConst
     S l2 = fabs(a.vt);
     S l3 = harten(a.vt + a.ct, delta);
     S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
-    S D0 = (A1 + A2) + A3;
-    S D1 = ((A1 * a.ut + A2 * a.ut) + A3 * a.ut) + As * du;
-    S D2 = (A1 * (a.vt - a.ct) + A2 * a.vt) + A3 * (a.vt + a.ct);
-    S D3 = ((A1 * (a.Ht - a.ct * a.vt) + A2 * a.kt) + A3 * (a.Ht + a.ct * a.vt))
-                + As * ((a.ut * du + a.vt * dv) - a.vt * dv);
+    S sA = A1 + A3, dA = A3 - A1;
+    S D0 = sA + A2;
+    S D1 = a.ut * D0 + As * du;
+    S D2 = a.vt * D0 + a.ct * dA;
+    S D3 = ((a.Ht * sA + a.kt * A2) + (a.ct * a.vt) * dA) + As * ((a.ut * du + a.vt * dv) - a.vt * dv);
     S mL = rL * vL, mR = rR * vR;
     F[0] = 0.5 * ((mL + mR) - D0);
     F[1] = 0.5 * ((mL * uL + mR * uR) - D1);
@@ -160,11 +161,11 @@ __device__ __forceinline__ void roe_n(const S *L, const S *R, double nx, double 
     S l2 = fabs(qnt);
     S l3 = harten(qnt + a.ct, delta);
     S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * a.rt;
-    S D0 = (A1 + A2) + A3;
-    S D1 = ((A1 * (a.ut - a.ct * nx) + A2 * a.ut) + A3 * (a.ut + a.ct * nx)) + As * (du - dqn * nx);
-    S D2 = ((A1 * (a.vt - a.ct * ny) + A2 * a.vt) + A3 * (a.vt + a.ct * ny)) + As * (dv - dqn * ny);
-    S D3 = ((A1 * (a.Ht - a.ct * qnt) + A2 * a.kt) + A3 * (a.Ht + a.ct * qnt))
-                + As * ((a.ut * du + a.vt * dv) - qnt * dqn);
+    S sA = A1 + A3, dA = A3 - A1;
+    S D0 = sA + A2;
+    S D1 = (a.ut * D0 + (a.ct * nx) * dA) + As * (du - dqn * nx);
+    S D2 = (a.vt * D0 + (a.ct * ny) * dA) + As * (dv - dqn * ny);
+    S D3 = ((a.Ht * sA + a.kt * A2) + (a.ct * qnt) * dA) + As * ((a.ut * du + a.vt * dv) - qnt * dqn);
     S mL = rL * qnL, mR = rR * qnR;
     S FL1 = mL * uL + pL * nx, FR1 = mR * uR + pR * nx;
     S FL2 = mL * vL + pL * ny, FR2 = mR * vR + pR * ny;
