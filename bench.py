@@ -290,6 +290,7 @@ def run_ours(args):
                               'value': round(ws * cells * KRYLOV / (mse * 1e-3) / 1e6, 3),
                               'rel_l2_vs_fd_after_steps': float((ye - yf).norm() / yf.norm()),
                               'steps_compared': args.steps}
+        forms['batched'] = batch_form(10)
     if rank != 0:
         return None
     peaks, src = _peaks()
@@ -327,7 +328,83 @@ def run_ours(args):
     return out
 
 
-def cpu_baseline(prob, y0, h, steps=1):
+def batch_form(steps, one_at_a_time=True):
+    """The batched form: 64 independent Euler-vortex / Navier-Stokes Taylor-Green
+    instances on periodic grids of sides 32..384 (per-instance seeds), ROK4
+    M = 16, each at its own CFL-derived step; `steps` steps of all instances in
+    one graph launch with autotuned launch shapes, against the same instances
+    stepped one at a time through the single-problem entry point (graph replay
+    per step).  Inputs are larger than L2 (flat vectors of ~110 MB, basis ~1.9 GB)."""
+    import torch
+
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    M = 16
+    inst = W.batched_instances()
+    probs = [i.problem for i in inst]
+    cells = sum(p.ncells for p in probs)
+    stream = torch.cuda.current_stream()
+    b = rok.rok_batch_init(probs, krylov_max=M, stream=stream)
+    y0 = b.pack([i.y0 for i in inst])
+    hs = []
+    for i in inst:
+        ctx = rok.rok_init(i.problem, krylov_max=1, stream=stream)
+        hs.append(rok.rok_dt_from_cfl(ctx, rok.state_tensor(i.y0), i.cfl))
+        del ctx
+    tuning = rok.rok_batch_tune(b, y0)
+    rok.rok_batch_set_graph(b, True)
+    y = y0.clone()
+    rok.rok_batch_step(b, y, hs, M, nsteps=steps)          # capture + first replay (warm-up)
+    y = y0.clone()
+    rok.rok_batch_get_launches(b, reset=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rok.rok_batch_step(b, y, hs, M, nsteps=steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = rok.rok_batch_get_launches(b)
+    info = rok.rok_batch_step(b, y0.clone(), hs, M, nsteps=1, info=True)
+    out = {'workload': 'batch-64-vortex-tgv-32..384-rok4-M16', 'instances': len(inst), 'cells': cells,
+           'steps': steps, 'ms': round(ms, 3), 'ms_per_step': round(ms / steps, 4),
+           'value': round(cells * M * steps / (ms * 1e-3) / 1e6, 3), 'unit': UNIT,
+           'gpu_launches_per_graph': launches, 'tuning': tuning,
+           'statuses_ok': all(i['status'] == 0 for i in info)}
+    del b
+    if one_at_a_time:
+        total = 0.0
+        for k, i in enumerate(inst):
+            ctx = rok.rok_init(i.problem, krylov_max=M, stream=stream)
+            rok.rok_set_graph(ctx, True)
+            ys = rok.state_tensor(i.y0)
+            rok.rok_step(ctx, ys, hs[k], M)
+            ys = rok.state_tensor(i.y0)
+            torch.cuda.synchronize()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                rok.rok_step(ctx, ys, hs[k], M)
+            c.record(stream)
+            torch.cuda.synchronize()
+            total += a.elapsed_time(c)
+            del ctx
+        out['one_at_a_time_ms'] = round(total, 3)
+        out['one_at_a_time_value'] = round(cells * M * steps / (total * 1e-3) / 1e6, 3)
+        out['speedup_vs_one_at_a_time'] = round(total / ms, 3)
+    return out
+
+
+def run_batch(args):
+    """--mode batch: the batched form alone, as one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    out = batch_form(args.steps)
+    out.update({'metric': METRIC, 'mode': 'batch', 'dtype': 'f64', 'data': 'synthetic'})
+    print(json.dumps(out))
+
+
+def cpu_baseline(prob, y0, h, steps=8):
     """The CPU oracle, as it stands, on a bounded sample: `steps` ROK4 steps of the
     same workload, single-threaded."""
     from oracle import core
@@ -516,7 +593,7 @@ def main():
     ap.add_argument('--ref-factor', type=float, default=16.0)
     ap.add_argument('--esdirk-cap', type=float, default=150.0, help='skip ESDIRK runs estimated above this (s)')
     ap.add_argument('--cfls', default=None, help='comma-separated ROK/ESDIRK CFL numbers (study)')
-    ap.add_argument('--mode', default='step', choices=['step', 'stencil'])
+    ap.add_argument('--mode', default='step', choices=['step', 'stencil', 'batch'])
     ap.add_argument('--n', type=int, default=N_GRID)
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=30)
@@ -530,6 +607,9 @@ def main():
         args.warmup = 3
     if args.mode == 'stencil':
         run_stencil_only(args)
+        return
+    if args.mode == 'batch':
+        run_batch(args)
         return
     if args.study == 'tte':
         run_tte(args)

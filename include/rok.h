@@ -177,6 +177,79 @@ rok_status rok_set_stencil_timing(rok_ctx *ctx, int enable);
 
 const char *rok_status_string(rok_status s);
 
+/* ---- Batches: many independent instances stepped together ---------------
+ *
+ * The paper integrates one problem at a time; a batch steps `count`
+ * independent problems with the same ROK4 step (Sec. 2.3.3, Eq. ROK), every
+ * kernel launch covering all of them, so that small grids fill the GPU.
+ *
+ * Instances: uniform periodic grids (xv == NULL, every bc ROK_BC_PERIODIC) of
+ * kind ROK_EULER2D or ROK_NS2D.  They fall into three physics groups: Euler,
+ * Navier-Stokes with constant viscosity, Navier-Stokes with Sutherland's law.
+ * nx, ny, lx, ly and mu are per instance; within a group gamma, muscl_kappa,
+ * entropy_fix (and prandtl, resp. t_ref and sutherland_s, where they apply)
+ * must agree, and rounding and krylov_max across the whole batch
+ * (ROK_ERR_INVALID_ARG otherwise); basis must be ROK_BASIS_FP64 and jvp
+ * ROK_JVP_FD (ROK_ERR_UNSUPPORTED otherwise).
+ *
+ * Layout: the states of all instances form ONE flat device float64 array of
+ * `total` entries (rok_batch_layout).  Instance k's 4 nx_k ny_k entries, in the
+ * single-problem order y[var][j][i], start at element offsets[k], a multiple
+ * of 2048; the entries between instances are padding that the library never
+ * reads or writes.  Each instance's result equals that of rok_step on the same
+ * description, state and h: bit for bit under ROK_ROUND_STRICT (the same
+ * reduction trees), to rounding under ROK_ROUND_FAST.
+ *
+ * Launch shapes: the residual stencil runs with one of three tile shapes per
+ * physics group and the vector passes with a chosen number of 2048-entry
+ * chunks per CTA.  rok_batch_tune times the candidates on the batch's own data
+ * and keeps the fastest; every candidate yields the same result bits. */
+typedef struct rok_batch rok_batch; /* opaque, library-owned */
+
+enum { ROK_TILE_32x8 = 0, ROK_TILE_16x16 = 1, ROK_TILE_64x4 = 2 };
+typedef struct {
+    int tile[3];          /* stencil tile per group: Euler, NS, NS with Sutherland (ROK_TILE_*) */
+    int chunks_per_cta;   /* reduction / MGS passes: 1, 2, 4 or 8                            */
+    int vec_chunks_per_cta; /* stage vectors, first basis vector, update: 1, 2, 4 or 8       */
+    float stencil_ms[3][3]; /* rok_batch_tune: residual launch time per group and tile (-1: none) */
+    float mgs_ms[4];      /* rok_batch_tune: one MGS pass per chunks_per_cta in (1, 2, 4, 8)   */
+    float vec_ms[4];      /* rok_batch_tune: one stage-vector pass per vec_chunks_per_cta       */
+} rok_batch_tuning;
+
+/* Create a batch of `count` >= 1 instances on the current device; workspace as
+ * for rok_init, sized for the flat length.  Errors as rok_init, plus those above. */
+rok_status rok_batch_init(rok_batch **batch, const rok_problem_desc *descs, int count, void *cuda_stream);
+rok_status rok_batch_destroy(rok_batch *batch);
+
+/* total: flat length; offsets (nullable, host, `count` entries): first entry of
+ * each instance. */
+rok_status rok_batch_layout(const rok_batch *batch, size_t *total, size_t *offsets);
+
+/* f = f(y) for every instance (flat device arrays, must not overlap). */
+rok_status rok_batch_residual(rok_batch *batch, const double *y, double *f);
+
+/* `nsteps` >= 1 ROK4 steps of every instance with Krylov dimension M
+ * (0 <= M <= krylov_max), instance k with step size h[k] (HOST array of
+ * `count` positive finite values, read during the call).  y in place.  An
+ * instance whose step latches an error (non-finite residual or stage solve)
+ * keeps its last good state for the remaining steps; its error is reported in
+ * info[k].status.  info: nullable HOST array of `count` entries; when given,
+ * the call synchronises and returns the first non-OK instance status (or OK),
+ * and clears the latched statuses.  With graphs enabled the nsteps steps are
+ * captured once per (y, M, nsteps) into one CUDA graph and replayed. */
+rok_status rok_batch_step(rok_batch *batch, double *y, const double *h, int M, int nsteps, rok_step_info *info);
+
+/* Time the launch-shape candidates on state y (flat device array, unchanged)
+ * and keep the fastest; out (nullable) receives the choice and the times.
+ * Synchronises. */
+rok_status rok_batch_tune(rok_batch *batch, const double *y, rok_batch_tuning *out);
+/* Set the launch shapes explicitly (the time fields are ignored). */
+rok_status rok_batch_set_tuning(rok_batch *batch, const rok_batch_tuning *t);
+rok_status rok_batch_get_tuning(const rok_batch *batch, rok_batch_tuning *t);
+rok_status rok_batch_set_graph(rok_batch *batch, int enable);
+/* kernels launched since the last reset (graph replays count their nodes) */
+rok_status rok_batch_get_launches(rok_batch *batch, long long *launches, int reset);
+
 /* Allocation-free variant of rok_jvp (no counterpart in the paper).
  *
  * For callers that cannot allocate device memory: code that runs inside a

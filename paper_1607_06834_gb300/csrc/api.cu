@@ -14,41 +14,11 @@
 #include <utility>
 #include <vector>
 
+#include "coefficients.h"
 #include "linalg.cuh"
 #include "rok_internal.h"
 
 using namespace rok;
-
-namespace {
-
-// ---- method coefficients (binary64) --------------------------------------------
-// ROK4: alpha and b are the classical RK4 tableau; gamma is the L-stable root
-// 0.5728160624821349 of g^4 - 4g^3 + 3g^2 - 2g/3 + 1/24 = 0; the off-diagonal
-// gamma_ij solve the ROK order-4 conditions for Krylov dimension M >= 4 (the
-// classical Rosenbrock conditions with the [[tau,tau]] condition split into its
-// alpha part, 1/12, and its gamma part, -g/3), with gamma_41 = 3/5.
-const double kRokGamma = 0.5728160624821349;
-const double kRokAlpha[4][4] = {{0.0, 0.0, 0.0, 0.0}, {0.5, 0.0, 0.0, 0.0}, {0.0, 0.5, 0.0, 0.0}, {0.0, 0.0, 1.0, 0.0}};
-const double kRokGammaOff[4][4] = {{0.0, 0.0, 0.0, 0.0},
-                                   {0.025068629909359066, 0.0, 0.0, 0.0},
-                                   {0.2477474325727758, -1.405913872491725, 0.0, 0.0},
-                                   {0.6, -0.020369905583413464, -1.7503308492902152, 0.0}};
-const double kRokB[4] = {0.16666666666666666, 0.3333333333333333, 0.3333333333333333, 0.16666666666666666};
-
-// classical RK4
-const double kRk4A[4][4] = {{0.0, 0.0, 0.0, 0.0}, {0.5, 0.0, 0.0, 0.0}, {0.0, 0.5, 0.0, 0.0}, {0.0, 0.0, 1.0, 0.0}};
-const double kRk4B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-
-// ESDIRK3: explicit first stage, stage order 2, stiffly accurate, L-stable
-// (gamma the root in (0.4, 0.5) of 6g^3 - 18g^2 + 9g - 1 = 0, c = (0, 2g, 3/5, 1)).
-const double kEsdGamma = 0.435866521508459;
-const double kEsdA[4][4] = {{0.0, 0.0, 0.0, 0.0},
-                            {0.435866521508459, 0.435866521508459, 0.0, 0.0},
-                            {0.2576482460664272, -0.09351476757488625, 0.435866521508459, 0.0},
-                            {0.18764102434672383, -0.595297473576955, 0.9717899277217721, 0.435866521508459}};
-const double kEsdB[4] = {0.18764102434672383, -0.595297473576955, 0.9717899277217721, 0.435866521508459};
-
-}  // namespace
 
 struct rok_ctx {
     rok_problem_desc d;

@@ -81,11 +81,49 @@ struct LinalgOps {
                                 StepState *st, cudaStream_t s);
 };
 
+// Segment table of a batch (device arrays): chunk c of a flat vector belongs to
+// instance chunk_inst[c]; st is the per-instance step state array.
+struct BSeg {
+    const int *chunk_inst;
+    const BatchInst *inst;
+    StepState *st;
+    int nchunks;
+};
+
+// ---- batched forms of the ROK step kernels (same arithmetic per instance) ----
+// cpc = 2048-entry chunks per CTA (grid = ceil(nchunks / cpc)); part/pin/pout hold
+// one partial per chunk (two sets for dot2 and the first MGS pass).
+struct BatchOps {
+    cudaError_t (*dot2)(const double *a0, const double *b0, const double *a1, const double *b1, double *part,
+                        const BSeg &sg, int use_active, int cpc, cudaStream_t s);
+    // eps of every instance from ||y||^2 partials (unit direction)
+    cudaError_t (*eps)(const double *part, const BSeg &sg, int ninst, cudaStream_t s);
+    cudaError_t (*first_normalize)(const double *F, double *V0, const double *part, const BSeg &sg, int cpc,
+                                   cudaStream_t s);
+    // MGS pass i (1 <= i <= j + 1) of column j
+    cudaError_t (*mgs)(double *w, const double *V, size_t ldv, int i, int j, const double *pin, double *pout,
+                       const BSeg &sg, int cpc, cudaStream_t s);
+    cudaError_t (*normalize)(const double *w, double *V, size_t ldv, int column, const double *pin, const BSeg &sg,
+                             int cpc, cudaStream_t s);
+    cudaError_t (*multidot)(const double *F, const double *V, size_t ldv, double *pout, const BSeg &sg, int cpc,
+                            cudaStream_t s);
+    cudaError_t (*stage_solve)(int stage, const double *gam_row, const double *pin, const BSeg &sg, int ninst,
+                               cudaStream_t s);
+    cudaError_t (*lu)(StepState *st, int ninst, cudaStream_t s);
+    cudaError_t (*stage_vec)(double *k, const double *F, const double *V, size_t ldv, int stage, const BSeg &sg,
+                             int cpc, cudaStream_t s);
+    // y += sum_q b_q k_q (4 stage vectors), skipped for instances with a latched status
+    cudaError_t (*update)(double *y, const double *const *kv, const double *b, const BSeg &sg, int cpc,
+                          cudaStream_t s);
+};
+
 namespace fast {
 extern const LinalgOps ops;
+extern const BatchOps bops;
 }
 namespace strict {
 extern const LinalgOps ops;
+extern const BatchOps bops;
 }
 
 // number of CTAs (and partials) of a reduction over n entries: 2048 entries per CTA
@@ -97,6 +135,10 @@ cudaError_t launch_set_int(int *p, int v, cudaStream_t s);
 cudaError_t launch_f2d(const float *src, double *dst, size_t n, cudaStream_t s);
 // begin a step: h, hg, meff = M, active = (M > 0)
 cudaError_t launch_begin(StepState *st, double h, double gamma, int M, cudaStream_t s);
+// the same for n instances, h[k] from a device array (latched status kept)
+cudaError_t launch_begin_batch(StepState *st, const double *h, double gamma, int M, int n, cudaStream_t s);
+// clear the latched status of n instances
+cudaError_t launch_clear_status(StepState *st, int n, cudaStream_t s);
 // dt from CFL: per-cell spectral-radius bound, max reduction (order independent)
 cudaError_t launch_cfl(const double *y, const StencilConsts &c, const double *geo_six, const double *geo_siy,
                        const double *geo_sjx, const double *geo_sjy, const double *geo_vol, double *pmax, int P,

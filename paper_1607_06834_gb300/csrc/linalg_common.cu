@@ -21,6 +21,26 @@ __global__ void begin_kernel(StepState *st, double h, double gamma, int M)
     st->wnorm0 = 0.0;
 }
 
+__global__ void begin_batch_kernel(StepState *st, const double *h, double gamma, int M, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    StepState *s = st + k;
+    const double hk = h[k];
+    s->h = hk;
+    s->hg = hk * gamma;
+    s->meff = M;
+    s->active = M > 0 ? 1 : 0;
+    s->beta = 0.0;
+    s->wnorm0 = 0.0;
+}
+
+__global__ void clear_status_kernel(StepState *st, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) st[k].status = 0;
+}
+
 __global__ void set_int_kernel(int *p, int v) { *p = v; }
 
 __global__ void f2d_kernel(const float *src, double *dst, size_t n)
@@ -84,6 +104,18 @@ cudaError_t launch_f2d(const float *src, double *dst, size_t n, cudaStream_t s)
 cudaError_t launch_begin(StepState *st, double h, double gamma, int M, cudaStream_t s)
 {
     begin_kernel<<<1, 1, 0, s>>>(st, h, gamma, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_begin_batch(StepState *st, const double *h, double gamma, int M, int n, cudaStream_t s)
+{
+    begin_batch_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, h, gamma, M, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_status(StepState *st, int n, cudaStream_t s)
+{
+    clear_status_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, n);
     return cudaGetLastError();
 }
 

@@ -567,7 +567,7 @@ static cudaError_t first_vector(const double *F, void *V0, int fp32, size_t n, d
 // One warp: LU with partial pivoting of L = I - h g H (first largest |pivot|),
 // row-major stride kMaxKrylov.  Each entry sees the same operation sequence as
 // a sequential elimination.
-__global__ void lu_kernel(StepState *st)
+__device__ __forceinline__ void lu_body(StepState *st)
 {
     const int m = st->meff;
     const double hg = st->hg;
@@ -613,19 +613,23 @@ __global__ void lu_kernel(StepState *st)
     }
 }
 
+__global__ void lu_kernel(StepState *st) { lu_body(st); }
+
 struct GamRow {
     double g[4];
 };
 
 // stage i: phi = V^T F_i (tree of the CTA partials), rhs = h phi + h H acc with
-// acc = sum_{j<i} gamma_ij lambda_j, lambda_i = LU solve, cvec_i = lambda_i - h phi
-__global__ void stage_solve_kernel(int stage, GamRow gr, const double *pin, int P, StepState *st)
+// acc = sum_{j<i} gamma_ij lambda_j, lambda_i = LU solve, cvec_i = lambda_i - h phi.
+// The partials of <V_i, F> are pin[i * istride + (0 .. P)].
+__device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, const double *pin, size_t istride,
+                                                 int P, StepState *st)
 {
     const int m = st->meff;
     const double h = st->h;
     __shared__ double phi[kMaxKrylov], acc[kMaxKrylov], x[kMaxKrylov];
     for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
-        double v = warp_tree_partials(pin + (size_t)i * P, P);
+        double v = warp_tree_partials(pin + (size_t)i * istride, P);
         if ((threadIdx.x & 31) == 0) phi[i] = v;
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -664,6 +668,11 @@ __global__ void stage_solve_kernel(int stage, GamRow gr, const double *pin, int 
         }
         if (!ok) st->status |= kStatusNonfinite;
     }
+}
+
+__global__ void stage_solve_kernel(int stage, GamRow gr, const double *pin, int P, StepState *st)
+{
+    stage_solve_body(stage, gr, pin, (size_t)P, P, st);
 }
 
 // k = sum_{i<meff} cvec[stage][i] V_i + h F (basis order, binary64)
@@ -741,6 +750,362 @@ __global__ void sum_sqrt_kernel(const double *pin, int P, double *dst)
     double s = tree_partials(pin, P, sh);
     if (threadIdx.x == 0) *dst = sqrt(s);
 }
+
+// ---- batches of independent instances --------------------------------------------
+// A flat batch vector is a sequence of 2048-entry chunks; chunk c belongs to
+// instance k = chunk_inst[c] and covers entries inst[k].off + (c - chunk0) 2048
+// + [0, 2048) of it, bounded by the instance length.  A CTA handles chunks
+// blockIdx.x, blockIdx.x + gridDim.x, ... (the chunks-per-CTA setting only
+// changes the grid); partials are stored per chunk, so instance k's partials
+// are part[chunk0 .. chunk0 + P_k) and its sums are the same trees as for a
+// single instance.  Instances whose Arnoldi flag is clear are skipped chunk by
+// chunk (the skip is uniform within the CTA).
+
+struct ChunkRef {
+    int k;            // instance
+    size_t off, n;    // instance's first entry and length
+    size_t e0;        // this lane's first entry within the instance
+    int chunk0, P;    // instance's first chunk and chunk count
+};
+
+__device__ __forceinline__ ChunkRef chunk_ref(const BSeg &sg, int c)
+{
+    ChunkRef r;
+    r.k = sg.chunk_inst[c];
+    const BatchInst &I = sg.inst[r.k];
+    r.off = I.off;
+    r.n = I.n;
+    r.chunk0 = I.chunk0;
+    r.P = I.nchunks;
+    r.e0 = ((size_t)(c - r.chunk0) * RT + threadIdx.x) * EPL;
+    return r;
+}
+
+// instance flag read once per CTA and chunk (uniform branch)
+__device__ __forceinline__ bool chunk_active(const StepState *st, int *sh_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *sh_flag = st->active;
+    __syncthreads();
+    return *sh_flag != 0;
+}
+
+// part[c] = <a0, b0>, part[nchunks + c] = <a1, b1> (a1 nullable) over chunk c
+__global__ void __launch_bounds__(RT) bdot2_kernel(const double *__restrict__ a0, const double *__restrict__ b0,
+                                                   const double *__restrict__ a1, const double *__restrict__ b1,
+                                                   double *__restrict__ part, const BSeg sg, int use_active)
+{
+    __shared__ double sh[10];
+    __shared__ int flag;
+    for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
+        const ChunkRef r = chunk_ref(sg, c);
+        if (use_active && !chunk_active(sg.st + r.k, &flag)) continue;
+        double x[EPL], y[EPL];
+        load8(a0 + r.off, r.e0, r.n, x);
+        load8(b0 + r.off, r.e0, r.n, y);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = x[k] * y[k];
+        double s0 = chunk_sum(x, sh);
+        double s1 = 0.0;
+        if (a1) {
+            load8(a1 + r.off, r.e0, r.n, x);
+            load8(b1 + r.off, r.e0, r.n, y);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) x[k] = x[k] * y[k];
+            s1 = chunk_sum(x, sh);
+        }
+        if (threadIdx.x == 0) {
+            part[c] = s0;
+            part[sg.nchunks + c] = s1;
+        }
+    }
+}
+
+// one CTA per instance: eps = sqrt(u (1 + ||y||)) rounded to a power of two (unit v)
+__global__ void beps_kernel(const double *part, const BSeg sg)
+{
+    __shared__ double sh[10];
+    const BatchInst &I = sg.inst[blockIdx.x];
+    StepState *st = sg.st + blockIdx.x;
+    const double yn = sqrt(tree_partials(part + I.chunk0, I.nchunks, sh));
+    if (threadIdx.x == 0) {
+        double x = sqrt(2.220446049250313e-16 * (1.0 + yn)) / 1.0;
+        int e2;
+        double mant = frexp(x, &e2);
+        if (mant < sqrt(0.5)) e2 -= 1;
+        const double eps = ldexp(1.0, e2);
+        st->eps = eps;
+        st->inv_eps = 1.0 / eps;
+        st->ynorm = yn;
+    }
+}
+
+// v_1 = F1 * (1/beta), beta = sqrt(tree(part)); beta = 0 leaves an empty basis
+__global__ void __launch_bounds__(RT) bfirst_normalize_kernel(const double *__restrict__ F, double *__restrict__ V0,
+                                                              const double *part, const BSeg sg)
+{
+    __shared__ double sh[10];
+    __shared__ int flag;
+    for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
+        const ChunkRef r = chunk_ref(sg, c);
+        StepState *st = sg.st + r.k;
+        if (!chunk_active(st, &flag)) continue;
+        const double beta = sqrt(tree_partials(part + r.chunk0, r.P, sh));
+        if (!(beta > 0.0)) {
+            if (c == r.chunk0 && threadIdx.x == 0) {
+                st->active = 0;
+                st->meff = 0;
+            }
+            continue;
+        }
+        if (c == r.chunk0 && threadIdx.x == 0) st->beta = beta;
+        const double rb = 1.0 / beta;
+        double x[EPL];
+        load8(F + r.off, r.e0, r.n, x);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = x[k] * rb;
+        store8(V0 + r.off, r.e0, r.n, x);
+    }
+}
+
+// MGS pass i of column j: h = tree(pin); H[i-1][j] = h; w -= h V_{i-1};
+// pout[c] = <V_i, w> (i <= j) or <w, w> (i = j + 1); first pass also
+// wnorm0 = sqrt(tree(pin + nchunks))
+__global__ void __launch_bounds__(RT) bmgs_kernel(double *__restrict__ w, const double *__restrict__ V, size_t ldv,
+                                                  int i, int j, const double *__restrict__ pin,
+                                                  double *__restrict__ pout, const BSeg sg)
+{
+    __shared__ double sh[10];
+    __shared__ int flag;
+    const double *vprev = V + (size_t)(i - 1) * ldv;
+    const double *vnext = i <= j ? V + (size_t)i * ldv : nullptr;
+    for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
+        const ChunkRef r = chunk_ref(sg, c);
+        StepState *st = sg.st + r.k;
+        if (!chunk_active(st, &flag)) continue;
+        double wv[EPL], vp[EPL], vn[EPL];
+        load8(w + r.off, r.e0, r.n, wv);
+        load8(vprev + r.off, r.e0, r.n, vp);
+        if (vnext) load8(vnext + r.off, r.e0, r.n, vn);
+        const double h = tree_partials(pin + r.chunk0, r.P, sh);
+        if (i == 1) {
+            const double wn2 = tree_partials(pin + sg.nchunks + r.chunk0, r.P, sh);
+            if (c == r.chunk0 && threadIdx.x == 0) st->wnorm0 = sqrt(wn2);
+        }
+        if (c == r.chunk0 && threadIdx.x == 0) st->H[(i - 1) * kMaxKrylov + j] = h;
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) wv[k] = wv[k] - h * vp[k];
+        store8(w + r.off, r.e0, r.n, wv);
+        if (vnext) {
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) vn[k] = vn[k] * wv[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) vn[k] = wv[k] * wv[k];
+        }
+        const double s = chunk_sum(vn, sh);
+        if (threadIdx.x == 0) pout[c] = s;
+    }
+}
+
+// column >= 1: hn = sqrt(tree(pin)); breakdown when hn <= 1e-12 ||J v_j||;
+// else H[column][column-1] = hn, V_column = w * (1/hn)
+__global__ void __launch_bounds__(RT) bnormalize_kernel(const double *__restrict__ w, double *__restrict__ V,
+                                                        size_t ldv, int column, const double *__restrict__ pin,
+                                                        const BSeg sg)
+{
+    __shared__ double sh[10];
+    __shared__ int flag;
+    double *v = V + (size_t)column * ldv;
+    for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
+        const ChunkRef r = chunk_ref(sg, c);
+        StepState *st = sg.st + r.k;
+        if (!chunk_active(st, &flag)) continue;
+        const double hn = sqrt(tree_partials(pin + r.chunk0, r.P, sh));
+        if (!(hn > 1e-12 * st->wnorm0)) {
+            if (c == r.chunk0 && threadIdx.x == 0) {
+                st->active = 0;
+                st->meff = column;
+            }
+            continue;
+        }
+        if (c == r.chunk0 && threadIdx.x == 0) st->H[column * kMaxKrylov + column - 1] = hn;
+        const double rh = 1.0 / hn;
+        double x[EPL];
+        load8(w + r.off, r.e0, r.n, x);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = x[k] * rh;
+        store8(v + r.off, r.e0, r.n, x);
+    }
+}
+
+// pout[m * nchunks + c] = <V_m, F> over chunk c, m < meff of its instance
+__global__ void __launch_bounds__(RT) bmultidot_kernel(const double *__restrict__ F, const double *__restrict__ V,
+                                                       size_t ldv, double *__restrict__ pout, const BSeg sg)
+{
+    __shared__ double sh[10];
+    for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
+        const ChunkRef r = chunk_ref(sg, c);
+        const int m = sg.st[r.k].meff;
+        double f[EPL];
+        load8(F + r.off, r.e0, r.n, f);
+        for (int i = 0; i < m; ++i) {
+            double v[EPL];
+            load8(V + (size_t)i * ldv + r.off, r.e0, r.n, v);
+            double x[EPL];
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) x[k] = v[k] * f[k];
+            const double s = chunk_sum(x, sh);
+            if (threadIdx.x == 0) pout[(size_t)i * sg.nchunks + c] = s;
+        }
+    }
+}
+
+// one CTA per instance: the projected stage solve
+__global__ void bstage_solve_kernel(int stage, GamRow gr, const double *pin, const BSeg sg)
+{
+    const BatchInst &I = sg.inst[blockIdx.x];
+    stage_solve_body(stage, gr, pin + I.chunk0, (size_t)sg.nchunks, I.nchunks, sg.st + blockIdx.x);
+}
+
+// one warp per instance: LU of I - h gamma H
+__global__ void blu_kernel(StepState *st) { lu_body(st + blockIdx.x); }
+
+// k = sum_{m<meff} cvec[stage][m] V_m + h F over each chunk (instance coefficients)
+__global__ void __launch_bounds__(RT) bstage_vec_kernel(double *__restrict__ kout, const double *__restrict__ F,
+                                                        const double *__restrict__ V, size_t ldv, int stage,
+                                                        const BSeg sg)
+{
+    __shared__ double cv[kMaxKrylov];
+    for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
+        const ChunkRef r = chunk_ref(sg, c);
+        const StepState *st = sg.st + r.k;
+        const int m = st->meff;
+        const double h = st->h;
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += RT) cv[i] = st->cvec[stage][i];
+        __syncthreads();
+        double a[EPL], f[EPL];
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) a[k] = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double v[EPL];
+            load8(V + (size_t)i * ldv + r.off, r.e0, r.n, v);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) a[k] = a[k] + cv[i] * v[k];
+        }
+        load8(F + r.off, r.e0, r.n, f);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) a[k] = a[k] + h * f[k];
+        store8(kout + r.off, r.e0, r.n, a);
+    }
+}
+
+// y = y + sum_q b_q k_q (q = 0..3, in order), skipped for instances with a latched status
+__global__ void __launch_bounds__(RT) bupdate_kernel(double *__restrict__ y, const double *__restrict__ k0,
+                                                     const double *__restrict__ k1, const double *__restrict__ k2,
+                                                     const double *__restrict__ k3, double b0, double b1, double b2,
+                                                     double b3, const BSeg sg)
+{
+    __shared__ int flag;
+    for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
+        const ChunkRef r = chunk_ref(sg, c);
+        __syncthreads();
+        if (threadIdx.x == 0) flag = sg.st[r.k].status;
+        __syncthreads();
+        if (flag != 0) continue;
+        double t[EPL], v[EPL];
+        load8(y + r.off, r.e0, r.n, t);
+        load8(k0 + r.off, r.e0, r.n, v);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) t[k] = t[k] + b0 * v[k];
+        load8(k1 + r.off, r.e0, r.n, v);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) t[k] = t[k] + b1 * v[k];
+        load8(k2 + r.off, r.e0, r.n, v);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) t[k] = t[k] + b2 * v[k];
+        load8(k3 + r.off, r.e0, r.n, v);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) t[k] = t[k] + b3 * v[k];
+        store8(y + r.off, r.e0, r.n, t);
+    }
+}
+
+static int bgrid(const BSeg &sg, int cpc) { return (sg.nchunks + cpc - 1) / cpc; }
+
+static cudaError_t b_dot2(const double *a0, const double *b0, const double *a1, const double *b1, double *part,
+                          const BSeg &sg, int use_active, int cpc, cudaStream_t s)
+{
+    bdot2_kernel<<<bgrid(sg, cpc), RT, 0, s>>>(a0, b0, a1, b1, part, sg, use_active);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_eps(const double *part, const BSeg &sg, int ninst, cudaStream_t s)
+{
+    beps_kernel<<<ninst, RT, 0, s>>>(part, sg);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_first_normalize(const double *F, double *V0, const double *part, const BSeg &sg, int cpc,
+                                     cudaStream_t s)
+{
+    bfirst_normalize_kernel<<<bgrid(sg, cpc), RT, 0, s>>>(F, V0, part, sg);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_mgs(double *w, const double *V, size_t ldv, int i, int j, const double *pin, double *pout,
+                         const BSeg &sg, int cpc, cudaStream_t s)
+{
+    bmgs_kernel<<<bgrid(sg, cpc), RT, 0, s>>>(w, V, ldv, i, j, pin, pout, sg);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_normalize(const double *w, double *V, size_t ldv, int column, const double *pin, const BSeg &sg,
+                               int cpc, cudaStream_t s)
+{
+    bnormalize_kernel<<<bgrid(sg, cpc), RT, 0, s>>>(w, V, ldv, column, pin, sg);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_multidot(const double *F, const double *V, size_t ldv, double *pout, const BSeg &sg, int cpc,
+                              cudaStream_t s)
+{
+    bmultidot_kernel<<<bgrid(sg, cpc), RT, 0, s>>>(F, V, ldv, pout, sg);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_stage_solve(int stage, const double *gam_row, const double *pin, const BSeg &sg, int ninst,
+                                 cudaStream_t s)
+{
+    GamRow gr;
+    for (int j = 0; j < 4; ++j) gr.g[j] = gam_row[j];
+    bstage_solve_kernel<<<ninst, RT, 0, s>>>(stage, gr, pin, sg);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_lu(StepState *st, int ninst, cudaStream_t s)
+{
+    blu_kernel<<<ninst, 32, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_stage_vec(double *k, const double *F, const double *V, size_t ldv, int stage, const BSeg &sg,
+                               int cpc, cudaStream_t s)
+{
+    bstage_vec_kernel<<<bgrid(sg, cpc), RT, 0, s>>>(k, F, V, ldv, stage, sg);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_update(double *y, const double *const *kv, const double *b, const BSeg &sg, int cpc,
+                            cudaStream_t s)
+{
+    bupdate_kernel<<<bgrid(sg, cpc), RT, 0, s>>>(y, kv[0], kv[1], kv[2], kv[3], b[0], b[1], b[2], b[3], sg);
+    return cudaGetLastError();
+}
+
+const BatchOps bops = {b_dot2, b_eps, b_first_normalize, b_mgs, b_normalize, b_multidot, b_stage_solve, b_lu,
+                       b_stage_vec, b_update};
 
 // ---- launchers ----------------------------------------------------------------
 

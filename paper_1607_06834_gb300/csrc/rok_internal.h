@@ -81,16 +81,46 @@ struct StencilIO {
     const int *active;         // nullable device flag: 0 = skip the launch's work
 };
 
+// ---- batches of independent uniform periodic grids ----------------------------
+// Per-instance constants of a batch (device array).  Flat vectors hold instance
+// k's N_k = 4 nx ny entries at [off, off + N_k); off is a multiple of 2048, the
+// entries of a reduction CTA, so that every CTA chunk belongs to one instance.
+struct BatchInst {
+    int nx, ny;
+    size_t off, n;             // element offset and length N_k
+    int chunk0, nchunks;       // first 2048-entry chunk and chunk count P_k
+    double rdx, rdy, q_rdx, q_rdy, mu;
+};
+
+// Tile table of one batched stencil launch (device arrays): CTA b computes tile
+// b - tile_first[k] of instance k = tile_inst[b]; per-instance scalars are
+// stride_bytes apart.
+struct BatchTiles {
+    const int *tile_inst;
+    const int *tile_first;
+    const BatchInst *inst;
+    size_t stride_bytes;
+};
+
+// tile shapes of the batched stencil (the autotuner picks one per physics group)
+enum { kShape32x8 = 0, kShape16x16 = 1, kShape64x4 = 2, kNumShapes = 3 };
+inline int shape_tx(int s) { return s == kShape16x16 ? 16 : (s == kShape64x4 ? 64 : 32); }
+inline int shape_ty(int s) { return s == kShape16x16 ? 16 : (s == kShape64x4 ? 4 : 8); }
+
 // stencil launchers, one set per rounding mode (separate translation units)
 namespace fast {
 cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_t s);
 cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s);
 cudaError_t launch_lorenz(const StencilConsts &c, const StencilIO &io, int n, cudaStream_t s);
+cudaError_t launch_cart_batch(const StencilConsts &c, const StencilIO &io, const BatchTiles &bt, int ntiles,
+                              int shape, cudaStream_t s);
 }
 namespace strict {
 cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_t s);
 cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s);
 cudaError_t launch_lorenz(const StencilConsts &c, const StencilIO &io, int n, cudaStream_t s);
+cudaError_t launch_cart_batch(const StencilConsts &c, const StencilIO &io, const BatchTiles &bt, int ntiles,
+                              int shape, cudaStream_t s);
 }
 
 }  // namespace rok

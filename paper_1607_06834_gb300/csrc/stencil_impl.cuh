@@ -26,11 +26,20 @@
 namespace rok {
 namespace ROK_NS {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
-constexpr int NT = TX * TY;
-constexpr int EW = TX + 4;
-constexpr int EH = TY + 4;
+// Tile shape: TXv x TYv cells per CTA, one thread per cell; the tile with its
+// 2-cell halo is EW x EH cells.
+template <int TXv, int TYv>
+struct Shape {
+    static constexpr int TX = TXv, TY = TYv, NT = TXv * TYv, EW = TXv + 4, EH = TYv + 4;
+};
+using Shape32x8 = Shape<32, 8>;
+
+// the single-grid kernels use 32 x 8 tiles
+constexpr int TX = Shape32x8::TX;
+constexpr int TY = Shape32x8::TY;
+constexpr int NT = Shape32x8::NT;
+constexpr int EW = Shape32x8::EW;
+constexpr int EH = Shape32x8::EH;
 
 template <class S>
 __device__ __forceinline__ S harten(S lam, S delta)
@@ -176,24 +185,25 @@ __device__ __forceinline__ void roe_n(const S *L, const S *R, double nx, double 
 }
 
 // shared-memory tile of primitive variables (halo included)
-template <class S>
+template <class S, class SH = Shape32x8>
 struct Tile {
-    S r[EH][EW], u[EH][EW], v[EH][EW], p[EH][EW], T[EH][EW], mu[EH][EW];
+    S r[SH::EH][SH::EW], u[SH::EH][SH::EW], v[SH::EH][SH::EW], p[SH::EH][SH::EW], T[SH::EH][SH::EW],
+        mu[SH::EH][SH::EW];
 };
-template <class S>
+template <class S, class SH = Shape32x8>
 struct Faces {
-    S fx[4][TY][TX + 1];
-    S fy[4][TY + 1][TX];
+    S fx[4][SH::TY][SH::TX + 1];
+    S fy[4][SH::TY + 1][SH::TX];
 };
 
-template <class S>
-__device__ __forceinline__ S pick(const Tile<S> &t, int k, int y, int x)
+template <class S, class SH>
+__device__ __forceinline__ S pick(const Tile<S, SH> &t, int k, int y, int x)
 {
     return k == 0 ? t.r[y][x] : (k == 1 ? t.u[y][x] : (k == 2 ? t.v[y][x] : t.p[y][x]));
 }
 
-template <bool SUTH, class S>
-__device__ __forceinline__ void store_prim(Tile<S> &t, int ly, int lx, S rho, S mx, S my,
+template <bool SUTH, class S, class SH>
+__device__ __forceinline__ void store_prim(Tile<S, SH> &t, int ly, int lx, S rho, S mx, S my,
                                            S E, bool mirror, const StencilConsts &C)
 {
     S rinv = 1.0 / rho;
@@ -217,7 +227,9 @@ __device__ __forceinline__ void store_prim(Tile<S> &t, int ly, int lx, S rho, S 
 __device__ __forceinline__ double load_value(const StencilIO &io, const double (&cf)[kMaxAdd], double cff, size_t e)
 {
     double q = io.base[e];
-    for (int t = 0; t < io.nadd; ++t) q = q + cf[t] * io.add[t][e];
+#pragma unroll
+    for (int t = 0; t < kMaxAdd; ++t)
+        if (t < io.nadd) q = q + cf[t] * io.add[t][e];
     if (io.addf) q = q + cff * (double)io.addf[e];
     return q;
 }
@@ -273,21 +285,21 @@ __device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd]
 }
 
 // ============================ uniform periodic grid ============================
-template <bool VISC, bool SUTH, class S, int MINB>
-__global__ void __launch_bounds__(NT, MINB) cart_kernel(const StencilConsts C, const StencilIO io)
+// One TX x TY tile with lower-left cell (i0, j0) of an nx x ny periodic grid.
+template <bool VISC, bool SUTH, class S, class SH>
+__device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilIO &io, int i0, int j0,
+                                          unsigned char *smem_raw)
 {
+    constexpr int TX = SH::TX, TY = SH::TY, NT = SH::NT, EW = SH::EW, EH = SH::EH;
     if (io.active && *io.active == 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Tile<S> &tl = *reinterpret_cast<Tile<S> *>(smem_raw);
-    Faces<S> &fc = *reinterpret_cast<Faces<S> *>(smem_raw + sizeof(Tile<S>));
+    Tile<S, SH> &tl = *reinterpret_cast<Tile<S, SH> *>(smem_raw);
+    Faces<S, SH> &fc = *reinterpret_cast<Faces<S, SH> *>(smem_raw + sizeof(Tile<S, SH>));
 
     const int nx = C.nx, ny = C.ny;
     const size_t nc = (size_t)nx * ny;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int tid = threadIdx.x;
     double cf[kMaxAdd], cff, s1, s2;
     coefs(io, cf, cff, s1, s2);
-
     for (int idx = tid; idx < EW * EH; idx += NT) {
         int lx = idx % EW, ly = idx / EW;
         int gi = wrapi(i0 + lx - 2, nx), gj = wrapi(j0 + ly - 2, ny);
@@ -296,7 +308,7 @@ __global__ void __launch_bounds__(NT, MINB) cart_kernel(const StencilConsts C, c
         S mx = load_state<S>(io, cf, cff, nc + c);
         S my = load_state<S>(io, cf, cff, 2 * nc + c);
         S E = load_state<S>(io, cf, cff, 3 * nc + c);
-        store_prim<SUTH, S>(tl, ly, lx, rho, mx, my, E, false, C);
+        store_prim<SUTH, S, SH>(tl, ly, lx, rho, mx, my, E, false, C);
     }
     __syncthreads();
 
@@ -373,6 +385,56 @@ __global__ void __launch_bounds__(NT, MINB) cart_kernel(const StencilConsts C, c
             epilogue_store(io, s1, s2, k * nc + c, result(r));
         }
     }
+}
+
+template <bool VISC, bool SUTH, class S, int MINB>
+__global__ void __launch_bounds__(NT, MINB) cart_kernel(const StencilConsts C, const StencilIO io)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cart_tile<VISC, SUTH, S, Shape32x8>(C, io, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
+}
+
+// Many independent uniform periodic grids of one physics group in one launch:
+// CTA b computes tile b - tile_first[k] of instance k = tile_inst[b].  The
+// instances share the gas model and scheme constants (C); grid size, spacing
+// and viscosity are per instance.  Vectors are flat: instance k's entries start
+// at element inst[k].off; the per-instance scalars (eps, 1/eps, status,
+// active flag) sit stride_bytes apart, starting at the pointers in io.
+template <bool VISC, bool SUTH, class SH, int MINB>
+__global__ void __launch_bounds__(SH::NT, MINB) cart_batch_kernel(const StencilConsts C, const StencilIO io,
+                                                                   const BatchTiles bt)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    const int k = bt.tile_inst[b];
+    const BatchInst I = bt.inst[k];
+    const size_t off = I.off;
+    const size_t sb = (size_t)k * bt.stride_bytes;
+    StencilIO q = io;
+    q.base = io.base + off;
+#pragma unroll
+    for (int t = 0; t < kMaxAdd; ++t) {
+        q.add[t] = io.add[t] ? io.add[t] + off : nullptr;
+        q.coef_dev[t] = io.coef_dev[t] ? reinterpret_cast<const double *>(reinterpret_cast<const char *>(io.coef_dev[t]) + sb) : nullptr;
+    }
+    q.sub = io.sub ? io.sub + off : nullptr;
+    q.add_out = io.add_out ? io.add_out + off : nullptr;
+    q.out = io.out + off;
+    q.s1_dev = io.s1_dev ? reinterpret_cast<const double *>(reinterpret_cast<const char *>(io.s1_dev) + sb) : nullptr;
+    q.s2_dev = io.s2_dev ? reinterpret_cast<const double *>(reinterpret_cast<const char *>(io.s2_dev) + sb) : nullptr;
+    q.status = reinterpret_cast<int *>(reinterpret_cast<char *>(io.status) + sb);
+    q.active = io.active ? reinterpret_cast<const int *>(reinterpret_cast<const char *>(io.active) + sb) : nullptr;
+    StencilConsts Ck = C;
+    Ck.nx = I.nx;
+    Ck.ny = I.ny;
+    Ck.rdx = I.rdx;
+    Ck.rdy = I.rdy;
+    Ck.q_rdx = I.q_rdx;
+    Ck.q_rdy = I.q_rdy;
+    Ck.mu = I.mu;
+    const int t = b - bt.tile_first[k];
+    const int ntx = (I.nx + SH::TX - 1) / SH::TX;
+    cart_tile<VISC, SUTH, double, SH>(Ck, q, (t % ntx) * SH::TX, (t / ntx) * SH::TY, smem_raw);
 }
 
 // ============================== curvilinear grid ===============================
@@ -633,6 +695,45 @@ cudaError_t launch_cart(const StencilConsts &c, const StencilIO &io, cudaStream_
     if (c.sutherland)
         return dual ? launch_cart_t<true, true, Dual>(c, io, s) : launch_cart_t<true, true, double>(c, io, s);
     return dual ? launch_cart_t<true, false, Dual>(c, io, s) : launch_cart_t<true, false, double>(c, io, s);
+}
+
+template <bool V, bool SU, class SH>
+static cudaError_t launch_cart_batch_t(const StencilConsts &c, const StencilIO &io, const BatchTiles &bt, int ntiles,
+                                       cudaStream_t s)
+{
+    const size_t smem = sizeof(Tile<double, SH>) + sizeof(Faces<double, SH>);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(cart_batch_kernel<V, SU, SH, 3>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cart_batch_kernel<V, SU, SH, 3><<<ntiles, SH::NT, smem, s>>>(c, io, bt);
+    return cudaGetLastError();
+}
+
+template <bool V, bool SU>
+static cudaError_t launch_cart_batch_v(const StencilConsts &c, const StencilIO &io, const BatchTiles &bt, int ntiles,
+                                       int shape, cudaStream_t s)
+{
+    switch (shape) {
+    case kShape32x8: return launch_cart_batch_t<V, SU, Shape<32, 8>>(c, io, bt, ntiles, s);
+    case kShape16x16: return launch_cart_batch_t<V, SU, Shape<16, 16>>(c, io, bt, ntiles, s);
+    case kShape64x4: return launch_cart_batch_t<V, SU, Shape<64, 4>>(c, io, bt, ntiles, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// batched residual / FD-JVP launch over the tiles of many grids (binary64 only)
+cudaError_t launch_cart_batch(const StencilConsts &c, const StencilIO &io, const BatchTiles &bt, int ntiles, int shape,
+                              cudaStream_t s)
+{
+    if (io.dir || io.dirf || io.addf) return cudaErrorInvalidValue;
+    if (ntiles <= 0) return cudaSuccess;
+    if (!c.viscous) return launch_cart_batch_v<false, false>(c, io, bt, ntiles, shape, s);
+    if (c.sutherland) return launch_cart_batch_v<true, true>(c, io, bt, ntiles, shape, s);
+    return launch_cart_batch_v<true, false>(c, io, bt, ntiles, shape, s);
 }
 
 cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s)

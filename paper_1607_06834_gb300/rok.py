@@ -66,6 +66,22 @@ class Counters(ctypes.Structure):
                 ('stencil_ms', ctypes.c_double), ('stencil_timed', ctypes.c_longlong)]
 
 
+ROK_TILE_32x8, ROK_TILE_16x16, ROK_TILE_64x4 = 0, 1, 2
+CHUNKS_PER_CTA = (1, 2, 4, 8)
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [('tile', ctypes.c_int * 3), ('chunks_per_cta', ctypes.c_int), ('vec_chunks_per_cta', ctypes.c_int),
+                ('stencil_ms', (ctypes.c_float * 3) * 3), ('mgs_ms', ctypes.c_float * 4),
+                ('vec_ms', ctypes.c_float * 4)]
+
+    def as_dict(self):
+        return {'tile': list(self.tile), 'chunks_per_cta': self.chunks_per_cta,
+                'vec_chunks_per_cta': self.vec_chunks_per_cta,
+                'stencil_ms': [list(r) for r in self.stencil_ms], 'mgs_ms': list(self.mgs_ms),
+                'vec_ms': list(self.vec_ms)}
+
+
 _vp = ctypes.c_void_p
 _sig = {
     'rok_init': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ProblemDesc), _vp]),
@@ -84,6 +100,16 @@ _sig = {
     'rok_set_stencil_timing': (ctypes.c_int, [_vp, ctypes.c_int]),
     'rok_status_string': (ctypes.c_char_p, [ctypes.c_int]),
     'rok_fp64_fma_peak': (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    'rok_batch_init': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ProblemDesc), ctypes.c_int, _vp]),
+    'rok_batch_destroy': (ctypes.c_int, [_vp]),
+    'rok_batch_layout': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    'rok_batch_residual': (ctypes.c_int, [_vp, _vp, _vp]),
+    'rok_batch_step': (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(StepInfo)]),
+    'rok_batch_tune': (ctypes.c_int, [_vp, _vp, ctypes.POINTER(BatchTuning)]),
+    'rok_batch_set_tuning': (ctypes.c_int, [_vp, ctypes.POINTER(BatchTuning)]),
+    'rok_batch_get_tuning': (ctypes.c_int, [_vp, ctypes.POINTER(BatchTuning)]),
+    'rok_batch_set_graph': (ctypes.c_int, [_vp, ctypes.c_int]),
+    'rok_batch_get_launches': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     'rok_jvp_noalloc': (ctypes.c_int, [ctypes.POINTER(ProblemDesc), _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -263,6 +289,130 @@ def rok_get_counters(ctx, reset=False):
 
 def rok_set_stencil_timing(ctx, enable):
     _check(_lib.rok_set_stencil_timing(ctx.handle, int(bool(enable))), 'rok_set_stencil_timing')
+
+
+class Batch:
+    """Owns one ``rok_batch`` (many independent problems stepped together);
+    created by :func:`rok_batch_init`.  ``offsets[k]`` is the first entry of
+    instance k in the flat state vector of ``total`` entries."""
+
+    def __init__(self, handle, problems, stream, total, offsets):
+        self.handle = handle
+        self.problems = list(problems)
+        self.stream = stream
+        self.total = total
+        self.offsets = offsets
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.rok_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def view(self, y, k):
+        """Instance k's state inside the flat vector y, shape problems[k].shape."""
+        p = self.problems[k]
+        n = 4 * p.nx * p.ny
+        return y[self.offsets[k]:self.offsets[k] + n].view(p.shape)
+
+    def pack(self, states, device='cuda'):
+        """Flat state vector from per-instance states (NumPy arrays or tensors)."""
+        y = torch.zeros(self.total, dtype=torch.float64, device=device)
+        for k, s in enumerate(states):
+            t = s if isinstance(s, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(s, dtype=np.float64))
+            self.view(y, k).copy_(t.reshape(self.problems[k].shape))
+        return y
+
+    def unpack(self, y):
+        """Per-instance NumPy states of a flat vector."""
+        yh = y.detach().cpu()
+        return [self.view(yh, k).numpy().copy() for k in range(len(self.problems))]
+
+
+def rok_batch_init(problems, krylov_max=16, rounding=ROK_ROUND_FAST, stream=None):
+    """Create a batch (``rok_batch_init``) of uniform periodic problems."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = len(problems)
+    arr = (ProblemDesc * n)()
+    for k, p in enumerate(problems):
+        d, _ = _desc(p, krylov_max, rounding)
+        arr[k] = d
+    h = ctypes.c_void_p()
+    _check(_lib.rok_batch_init(ctypes.byref(h), arr, n, ctypes.c_void_p(stream.cuda_stream)), 'rok_batch_init')
+    total = ctypes.c_size_t(0)
+    offs = (ctypes.c_size_t * n)()
+    _check(_lib.rok_batch_layout(h, ctypes.byref(total), offs), 'rok_batch_layout')
+    return Batch(h, problems, stream, total.value, [int(o) for o in offs])
+
+
+def rok_batch_layout(b):
+    """(total, offsets) of the flat state vector."""
+    total = ctypes.c_size_t(0)
+    offs = (ctypes.c_size_t * len(b.problems))()
+    _check(_lib.rok_batch_layout(b.handle, ctypes.byref(total), offs), 'rok_batch_layout')
+    return total.value, [int(o) for o in offs]
+
+
+def rok_batch_destroy(b):
+    _check(_lib.rok_batch_destroy(b.handle), 'rok_batch_destroy')
+    b.handle = None
+
+
+def rok_batch_residual(b, y, f=None):
+    if f is None:
+        f = torch.zeros_like(y)
+    _check(_lib.rok_batch_residual(b.handle, _ptr(y), _ptr(f)), 'rok_batch_residual')
+    return f
+
+
+def rok_batch_step(b, y, h, M, nsteps=1, info=False):
+    """``nsteps`` ROK4 steps of every instance in place; h: one step size per
+    instance (or one for all).  info=True synchronises and returns the
+    per-instance info dicts (a failed instance shows in its ``status``);
+    info=False raises only on argument or CUDA errors."""
+    hv = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (len(b.problems),)))
+    si = (StepInfo * len(b.problems))() if info else None
+    st = _lib.rok_batch_step(b.handle, _ptr(y), hv.ctypes.data_as(_dp), int(M), int(nsteps), si)
+    if not info:
+        _check(st, 'rok_batch_step')
+        return None
+    out = [s.as_dict() for s in si]
+    if st not in (ROK_OK, ROK_ERR_NONFINITE, ROK_ERR_TIMEOUT):
+        _check(st, 'rok_batch_step')
+    return out
+
+
+def rok_batch_tune(b, y):
+    t = BatchTuning()
+    _check(_lib.rok_batch_tune(b.handle, _ptr(y), ctypes.byref(t)), 'rok_batch_tune')
+    return t.as_dict()
+
+
+def rok_batch_set_tuning(b, tile=(0, 0, 0), chunks_per_cta=1, vec_chunks_per_cta=1):
+    t = BatchTuning()
+    for g in range(3):
+        t.tile[g] = int(tile[g])
+    t.chunks_per_cta, t.vec_chunks_per_cta = int(chunks_per_cta), int(vec_chunks_per_cta)
+    _check(_lib.rok_batch_set_tuning(b.handle, ctypes.byref(t)), 'rok_batch_set_tuning')
+
+
+def rok_batch_get_tuning(b):
+    t = BatchTuning()
+    _check(_lib.rok_batch_get_tuning(b.handle, ctypes.byref(t)), 'rok_batch_get_tuning')
+    return t.as_dict()
+
+
+def rok_batch_set_graph(b, enable):
+    _check(_lib.rok_batch_set_graph(b.handle, int(bool(enable))), 'rok_batch_set_graph')
+
+
+def rok_batch_get_launches(b, reset=False):
+    n = ctypes.c_longlong(0)
+    _check(_lib.rok_batch_get_launches(b.handle, ctypes.byref(n), int(bool(reset))), 'rok_batch_get_launches')
+    return n.value
 
 
 ROK_NOALLOC_MAX_N = 4096 * 2048

@@ -49,3 +49,21 @@ def test_init_without_gpu_reports_an_error_not_a_crash():
     lib.rok_init.restype = ctypes.c_int
     # a NULL description is rejected before any CUDA call
     assert lib.rok_init(None, None, None) == 1
+
+
+def test_batch_init_validates_descriptions_before_any_cuda_call():
+    from paper_1607_06834_gb300 import _build
+    _build.build()
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    a, _ = W.isentropic_vortex(32)
+    b, _ = W.taylor_green(40, reynolds=500.0)
+    descs = (rok.ProblemDesc * 2)()
+    descs[0], _ = rok._desc(a, 8, rok.ROK_ROUND_STRICT)
+    descs[1], _ = rok._desc(b, 8, rok.ROK_ROUND_FAST)     # rounding differs
+    h = ctypes.c_void_p()
+    assert rok._lib.rok_batch_init(ctypes.byref(h), descs, 2, None) == rok.ROK_ERR_INVALID_ARG
+    descs[1], _ = rok._desc(b, 8, rok.ROK_ROUND_STRICT, basis=rok.ROK_BASIS_FP32)
+    assert rok._lib.rok_batch_init(ctypes.byref(h), descs, 2, None) == rok.ROK_ERR_UNSUPPORTED
+    assert rok._lib.rok_batch_init(ctypes.byref(h), descs, 0, None) == rok.ROK_ERR_INVALID_ARG
+    assert rok._lib.rok_batch_init(None, descs, 2, None) == rok.ROK_ERR_INVALID_ARG
