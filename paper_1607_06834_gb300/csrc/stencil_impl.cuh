@@ -20,6 +20,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "dual.cuh"
 #include "rok_internal.h"
 
@@ -227,9 +229,7 @@ __device__ __forceinline__ void store_prim(Tile<S, SH> &t, int ly, int lx, S rho
 __device__ __forceinline__ double load_value(const StencilIO &io, const double (&cf)[kMaxAdd], double cff, size_t e)
 {
     double q = io.base[e];
-#pragma unroll
-    for (int t = 0; t < kMaxAdd; ++t)
-        if (t < io.nadd) q = q + cf[t] * io.add[t][e];
+    for (int t = 0; t < io.nadd; ++t) q = q + cf[t] * io.add[t][e];
     if (io.addf) q = q + cff * (double)io.addf[e];
     return q;
 }
@@ -263,35 +263,47 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return i < 0 ? i + n : i;
 }
 
+// a per-instance scalar `sb` bytes after the pointer (batches; 0 otherwise)
+template <class T>
+__device__ __forceinline__ T *at_bytes(T *p, size_t sb)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<typename std::conditional<std::is_const<T>::value, const char,
+                                                                             char>::type *>(p) + sb);
+}
+
 // ---- stage 3: balance + epilogue ---------------------------------------------
 // the launch output: t = (sub ? r - sub : r) * s1, out = add_out ? add_out + s2 t : t,
 // r the residual value (or the JVP tangent)
-__device__ __forceinline__ void epilogue_store(const StencilIO &io, double s1, double s2, size_t e, double r)
+__device__ __forceinline__ void epilogue_store(const StencilIO &io, double s1, double s2, size_t e, double r,
+                                               size_t sb = 0)
 {
     double t = io.sub ? (r - io.sub[e]) : r;
     t = t * s1;
     double o = io.add_out ? io.add_out[e] + s2 * t : t;
     io.out[e] = o;
-    if (!isfinite(o)) atomicOr(io.status, kStatusNonfinite);
+    if (!isfinite(o)) atomicOr(at_bytes(io.status, sb), kStatusNonfinite);
 }
 
-__device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd], double &cff, double &s1, double &s2)
+__device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd], double &cff, double &s1, double &s2,
+                                      size_t sb = 0)
 {
 #pragma unroll
-    for (int t = 0; t < kMaxAdd; ++t) cf[t] = io.coef_dev[t] ? io.coef[t] * *io.coef_dev[t] : io.coef[t];
-    cff = io.coef_f_dev ? io.coef_f * *io.coef_f_dev : io.coef_f;
-    s1 = io.s1_dev ? io.s1 * *io.s1_dev : io.s1;
-    s2 = io.s2_dev ? io.s2 * *io.s2_dev : io.s2;
+    for (int t = 0; t < kMaxAdd; ++t) cf[t] = io.coef_dev[t] ? io.coef[t] * *at_bytes(io.coef_dev[t], sb) : io.coef[t];
+    cff = io.coef_f_dev ? io.coef_f * *at_bytes(io.coef_f_dev, sb) : io.coef_f;
+    s1 = io.s1_dev ? io.s1 * *at_bytes(io.s1_dev, sb) : io.s1;
+    s2 = io.s2_dev ? io.s2 * *at_bytes(io.s2_dev, sb) : io.s2;
 }
 
 // ============================ uniform periodic grid ============================
 // One TX x TY tile with lower-left cell (i0, j0) of an nx x ny periodic grid.
+// Batches pass the instance's first entry `off` in the flat vectors and the
+// byte offset `sb` of its per-instance scalars (eps, 1/eps, status, flag).
 template <bool VISC, bool SUTH, class S, class SH>
 __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilIO &io, int i0, int j0,
-                                          unsigned char *smem_raw)
+                                          unsigned char *smem_raw, size_t off = 0, size_t sb = 0)
 {
     constexpr int TX = SH::TX, TY = SH::TY, NT = SH::NT, EW = SH::EW, EH = SH::EH;
-    if (io.active && *io.active == 0) return;
+    if (io.active && *at_bytes(io.active, sb) == 0) return;
     Tile<S, SH> &tl = *reinterpret_cast<Tile<S, SH> *>(smem_raw);
     Faces<S, SH> &fc = *reinterpret_cast<Faces<S, SH> *>(smem_raw + sizeof(Tile<S, SH>));
 
@@ -299,11 +311,11 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     const size_t nc = (size_t)nx * ny;
     const int tid = threadIdx.x;
     double cf[kMaxAdd], cff, s1, s2;
-    coefs(io, cf, cff, s1, s2);
+    coefs(io, cf, cff, s1, s2, sb);
     for (int idx = tid; idx < EW * EH; idx += NT) {
         int lx = idx % EW, ly = idx / EW;
         int gi = wrapi(i0 + lx - 2, nx), gj = wrapi(j0 + ly - 2, ny);
-        size_t c = (size_t)gj * nx + gi;
+        size_t c = off + (size_t)gj * nx + gi;
         S rho = load_state<S>(io, cf, cff, c);
         S mx = load_state<S>(io, cf, cff, nc + c);
         S my = load_state<S>(io, cf, cff, 2 * nc + c);
@@ -376,13 +388,13 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     const int tx = tid % TX, ty = tid / TX;
     const int gi = i0 + tx, gj = j0 + ty;
     if (gi < nx && gj < ny) {
-        size_t c = (size_t)gj * nx + gi;
+        size_t c = off + (size_t)gj * nx + gi;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             S dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
             S dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
             S r = -(dX * C.rdx + dY * C.rdy);
-            epilogue_store(io, s1, s2, k * nc + c, result(r));
+            epilogue_store(io, s1, s2, k * nc + c, result(r), sb);
         }
     }
 }
@@ -408,22 +420,6 @@ __global__ void __launch_bounds__(SH::NT, MINB) cart_batch_kernel(const StencilC
     const int b = blockIdx.x;
     const int k = bt.tile_inst[b];
     const BatchInst I = bt.inst[k];
-    const size_t off = I.off;
-    const size_t sb = (size_t)k * bt.stride_bytes;
-    StencilIO q = io;
-    q.base = io.base + off;
-#pragma unroll
-    for (int t = 0; t < kMaxAdd; ++t) {
-        q.add[t] = io.add[t] ? io.add[t] + off : nullptr;
-        q.coef_dev[t] = io.coef_dev[t] ? reinterpret_cast<const double *>(reinterpret_cast<const char *>(io.coef_dev[t]) + sb) : nullptr;
-    }
-    q.sub = io.sub ? io.sub + off : nullptr;
-    q.add_out = io.add_out ? io.add_out + off : nullptr;
-    q.out = io.out + off;
-    q.s1_dev = io.s1_dev ? reinterpret_cast<const double *>(reinterpret_cast<const char *>(io.s1_dev) + sb) : nullptr;
-    q.s2_dev = io.s2_dev ? reinterpret_cast<const double *>(reinterpret_cast<const char *>(io.s2_dev) + sb) : nullptr;
-    q.status = reinterpret_cast<int *>(reinterpret_cast<char *>(io.status) + sb);
-    q.active = io.active ? reinterpret_cast<const int *>(reinterpret_cast<const char *>(io.active) + sb) : nullptr;
     StencilConsts Ck = C;
     Ck.nx = I.nx;
     Ck.ny = I.ny;
@@ -434,7 +430,8 @@ __global__ void __launch_bounds__(SH::NT, MINB) cart_batch_kernel(const StencilC
     Ck.mu = I.mu;
     const int t = b - bt.tile_first[k];
     const int ntx = (I.nx + SH::TX - 1) / SH::TX;
-    cart_tile<VISC, SUTH, double, SH>(Ck, q, (t % ntx) * SH::TX, (t / ntx) * SH::TY, smem_raw);
+    cart_tile<VISC, SUTH, double, SH>(Ck, io, (t % ntx) * SH::TX, (t / ntx) * SH::TY, smem_raw, I.off,
+                                      (size_t)k * bt.stride_bytes);
 }
 
 // ============================== curvilinear grid ===============================
