@@ -42,6 +42,8 @@ def lib():
         L.oracle_roe_flux.restype = None
         L.oracle_jvp_cs.argtypes = [ctypes.POINTER(_Problem), dp, dp, ctypes.c_double, dp]
         L.oracle_jvp_cs.restype = ctypes.c_int
+        L.oracle_residual_cx.argtypes = [ctypes.POINTER(_Problem), dp, dp, dp, dp]
+        L.oracle_residual_cx.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -92,7 +94,11 @@ def lorenz96_rhs(prob, u):
 
 
 def residual(prob, y):
-    """f(y) for the problem; y has ``prob.shape``; returns a new float64 array."""
+    """f(y) for the problem; y has ``prob.shape``; returns a new float64 array
+    (complex128 for a complex y: the same residual continued analytically, for
+    complex-step derivatives of the integrators)."""
+    if np.iscomplexobj(y):
+        return _residual_complex(prob, y)
     y = np.ascontiguousarray(y, dtype=np.float64)
     if prob.kind == 2:
         return lorenz96_rhs(prob, y)
@@ -103,8 +109,22 @@ def residual(prob, y):
     return f
 
 
+def _residual_complex(prob, y):
+    y = np.ascontiguousarray(y, dtype=np.complex128)
+    if prob.kind == 2:
+        return lorenz96_rhs(prob, y)
+    q_re, q_im = np.ascontiguousarray(y.real), np.ascontiguousarray(y.imag)
+    f_re, f_im = np.empty_like(q_re), np.empty_like(q_re)
+    rc = lib().oracle_residual_cx(ctypes.byref(_desc(prob).s), _dp(q_re), _dp(q_im), _dp(f_re), _dp(f_im))
+    if rc != 0:
+        raise MemoryError('oracle_residual_cx failed')
+    return f_re + 1j * f_im
+
+
 def jvp_fd(prob, y, v, f0, eps):
     """Eq. matvecFD: (f(y + eps v) - f0) / eps."""
+    if np.iscomplexobj(y) or np.iscomplexobj(v) or np.iscomplexobj(f0):
+        return (_residual_complex(prob, np.asarray(y) + eps * np.asarray(v)) - f0) / eps
     y = np.ascontiguousarray(y, dtype=np.float64)
     v = np.ascontiguousarray(v, dtype=np.float64)
     f0 = np.ascontiguousarray(f0, dtype=np.float64)

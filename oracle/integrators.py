@@ -37,15 +37,29 @@ def pairwise_sum(x, dtype=np.float64):
     return buf[0]
 
 
+def _cx(*xs):
+    """True when any argument is complex: the integrators then run on the
+    analytic continuation (complex-step derivatives), every comparison and
+    every rounding-to-a-power-of-two on real parts; products are not
+    conjugated, so inner products and norms stay analytic."""
+    return any(np.iscomplexobj(x) for x in xs)
+
+
 def dot(a, b, dtype=np.float64):
     """Inner product: the entrywise products rounded in `dtype`, summed pairwise."""
+    if _cx(a, b):
+        dtype = np.complex128
     a = np.ravel(np.asarray(a, dtype=dtype))
     b = np.ravel(np.asarray(b, dtype=dtype))
     r = pairwise_sum(a * b, dtype)
+    if dtype == np.complex128:
+        return complex(r)
     return float(r) if dtype == np.float64 else r
 
 
 def norm(a, dtype=np.float64):
+    if _cx(a):
+        return complex(np.sqrt(dot(a, a)))
     if dtype == np.float64:
         return math.sqrt(dot(a, a))
     return np.sqrt(dot(a, a, dtype))
@@ -82,13 +96,13 @@ def arnoldi(sys, y, F1, M, eps, breakdown_tol=None, basis=np.float64):
     binary32 before orthogonalisation; H is kept in binary64."""
     if breakdown_tol is None:
         breakdown_tol = 1e-12 if basis == np.float64 else 1e-5
-    T = basis
+    T = np.complex128 if _cx(y, F1) else basis
     N = F1.size
     V = np.zeros((M, N), dtype=T)
-    H = np.zeros((M, M))
+    H = np.zeros((M, M), dtype=np.complex128 if T == np.complex128 else np.float64)
     w = np.asarray(F1, dtype=T).ravel()
     beta = norm(w, T)
-    if M == 0 or not beta > 0.0:
+    if M == 0 or not np.real(beta) > 0.0:
         return V[:0], H[:0, :0], 0
     V[0] = w * (T(1.0) / beta)
     y_flat = y.ravel()
@@ -96,19 +110,19 @@ def arnoldi(sys, y, F1, M, eps, breakdown_tol=None, basis=np.float64):
     f0 = F1
     meff = M
     for j in range(M):
-        vj = V[j].astype(np.float64).reshape(shape)
+        vj = V[j].astype(np.complex128 if T == np.complex128 else np.float64).reshape(shape)
         w = np.asarray(sys.jvp(y_flat.reshape(shape), vj, f0, eps), dtype=T).ravel()
         wnorm0 = norm(w, T)
         for i in range(j + 1):
             hij = dot(V[i], w, T)
-            H[i, j] = float(hij)
+            H[i, j] = hij if T == np.complex128 else float(hij)
             w = w - T(hij) * V[i]
         if j + 1 < M:
             hn = norm(w, T)
-            if not float(hn) > breakdown_tol * float(wnorm0):
+            if not np.real(hn) > breakdown_tol * np.real(wnorm0):
                 meff = j + 1
                 break
-            H[j + 1, j] = float(hn)
+            H[j + 1, j] = hn if T == np.complex128 else float(hn)
             V[j + 1] = w * (T(1.0) / hn)
     return V[:meff], H[:meff, :meff], meff
 
@@ -117,11 +131,11 @@ def lu_factor(A):
     """LU factorisation with partial pivoting (first largest |pivot|), row
     interchanges applied to the whole rows; returns (LU, piv) with the unit
     lower factor below the diagonal.  Plain loops."""
-    A = np.array(A, dtype=np.float64)
+    A = np.array(A, dtype=np.complex128 if _cx(A) else np.float64)
     m = A.shape[0]
     piv = np.zeros(m, dtype=int)
     for k in range(m):
-        p = k + int(np.argmax(np.abs(A[k:, k])))
+        p = k + int(np.argmax(np.abs(np.real(A[k:, k]))))
         piv[k] = p
         if p != k:
             A[[k, p]] = A[[p, k]]
@@ -137,7 +151,7 @@ def lu_factor(A):
 def lu_solve(LU, piv, b):
     """Solve with the factors of lu_factor: interchanges, unit-lower forward and
     upper backward substitution, plain loops."""
-    x = [float(v) for v in b]
+    x = [complex(v) if _cx(LU, b) else float(v) for v in b]
     m = len(x)
     for k in range(m):
         p = int(piv[k])
@@ -179,9 +193,10 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
     shape = y.shape
     yf = y.ravel()
     F1 = np.asarray(sys.f(y))
-    eps = fd_eps(norm(yf))
+    eps = fd_eps(float(np.real(norm(yf))))   # a constant of the step (real part)
     V, H, meff = arnoldi(sys, y, F1, M, eps, basis=basis)
-    V = V.astype(np.float64)
+    cx = _cx(y, F1)
+    V = V.astype(np.complex128 if cx else np.float64)
     LU, piv = lu_factor(np.eye(meff) - (h * g) * H)
     ks, lams = [], []
     for i in range(s):
@@ -194,16 +209,16 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
                     Y = Y + al[i, j] * ks[j]
             F = np.asarray(sys.f(Y.reshape(shape))).ravel()
         phi = np.array([dot(V[m], F) for m in range(meff)])
-        acc = np.zeros(meff)
+        acc = np.zeros(meff, dtype=V.dtype)
         for j in range(i):
             acc = acc + gm[i, j] * lams[j]
-        rhs = np.zeros(meff)
+        rhs = np.zeros(meff, dtype=V.dtype)
         for r in range(meff):
             t = 0.0
             for c in range(meff):
                 t = t + H[r, c] * acc[c]
             rhs[r] = h * phi[r] + h * t
-        lam = lu_solve(LU, piv, rhs) if meff > 0 else np.zeros(0)
+        lam = lu_solve(LU, piv, rhs) if meff > 0 else np.zeros(0, dtype=V.dtype)
         cvec = lam - h * phi
         k = np.zeros_like(yf)
         for m in range(meff):

@@ -558,4 +558,23 @@ int oracle_jvp_cs(const oracle_problem *P, const double *y, const double *v, dou
     free(f);
     return rc;
 }
+
+/* f at a complex state, real and imaginary parts in separate arrays (the
+ * complex-step derivative of integrators built on f). */
+int oracle_residual_cx(const oracle_problem *P, const double *q_re, const double *q_im, double *f_re, double *f_im)
+{
+    const size_t n = (size_t)4 * P->nx * P->ny;
+    real_t *q = malloc(n * sizeof(real_t));
+    real_t *f = malloc(n * sizeof(real_t));
+    if (!q || !f) { free(q); free(f); return -1; }
+    for (size_t k = 0; k < n; ++k) q[k] = q_re[k] + I * q_im[k];
+    int rc = residual_impl(P, q, f);
+    for (size_t k = 0; k < n; ++k) {
+        f_re[k] = creal(f[k]);
+        f_im[k] = cimag(f[k]);
+    }
+    free(q);
+    free(f);
+    return rc;
+}
 #endif
