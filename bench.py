@@ -404,6 +404,95 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+def run_grad(args):
+    """--mode grad: gradient of the final kinetic energy of the 256^2 Taylor-Green
+    vortex (Re = 1000) after 100 ROK4 steps (M = 20, CFL 8) with respect to the
+    initial state and the viscosity, through the reverse step with a checkpoint
+    every 10 steps.  Reports forward and backward times, the derivatives along
+    64 seeded random unit directions, the gradient over the first 2 steps against
+    the oracle's complex-step derivative (one direction and mu), and central
+    differences (h = 1e-6) of the GPU forward map along two directions."""
+    import torch
+
+    from oracle import adjoint as OA
+    from oracle import core
+    from oracle import integrators as OI
+    from paper_1607_06834_gb300 import autograd as G
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    n, M, K, every = 256, 20, (args.steps if args.steps != 30 else 100), 10
+    prob, y0 = W.taylor_green(n, mach=MACH, reynolds=1000.0)
+    ctx = rok.rok_init(prob, krylov_max=M)
+    yd0 = rok.state_tensor(y0)
+    h = rok.rok_dt_from_cfl(ctx, yd0, CFL)
+    stream = torch.cuda.current_stream()
+
+    def grad(nsteps):
+        y = yd0.clone().requires_grad_(True)
+        mu = torch.tensor(prob.mu, dtype=torch.float64, requires_grad=True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        J = G.kinetic_energy(G.integrate(ctx, y, mu, h, M, nsteps, checkpoint_every=every))
+        e[1].record(stream)
+        J.backward()
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        return y.grad.detach(), float(mu.grad), float(J), e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    grad(2)                                   # warm-up (allocations)
+    g, gmu, J, ms_f, ms_b = grad(K)
+    rng = np.random.default_rng(0)
+    dirs = rng.standard_normal((64, y0.size))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    dd = dirs @ g.cpu().numpy().ravel()
+    out = {'mode': 'grad', 'metric': METRIC, 'workload': 'ns2d-taylor-green-256x256-Re1000-rok4-M20-100steps',
+           'steps': K, 'krylov_m': M, 'checkpoint_every': every, 'dt': h, 'J_final_ke': J,
+           'forward_ms': round(ms_f, 2), 'backward_ms': round(ms_b, 2),
+           'backward_ms_per_step': round(ms_b / K, 3), 'dJ_dmu': gmu,
+           'grad_norm': float(g.norm()), 'directional_derivatives_64': {
+               'min': float(dd.min()), 'max': float(dd.max()), 'rms': float(np.sqrt(np.mean(dd ** 2)))},
+           'dtype': 'f64', 'data': 'synthetic'}
+    # check over the first 2 steps: GPU gradient against the oracle's complex step
+    g2, gmu2, _, _, _ = grad(2)
+    d = dirs[0].reshape(y0.shape)
+    sys_ = core.System(prob)
+    yc = y0 + 1e-30j * d
+    for _ in range(2):
+        yc = OI.rok_step(sys_, yc, h, M)
+    ke = lambda yy: 0.5 * np.sum((yy[1] ** 2 + yy[2] ** 2) / yy[0])
+    cs = float(np.imag(ke(yc)) / 1e-30)
+    gd = float(np.sum(g2.cpu().numpy() * d))
+
+    class MuStep(core.System):
+        def f(self, yy):
+            return core.residual(prob, yy) + 1e-30j * OA.residual_dmu(prob, yy)
+
+        def jvp(self, yy, v, f0, eps):
+            return (self.f(np.asarray(yy) + eps * np.asarray(v)) - f0) / eps
+    yc = y0.astype(complex)
+    for _ in range(2):
+        yc = OI.rok_step(MuStep(prob), yc, h, M)
+    csm = float(np.imag(ke(yc)) / 1e-30)
+    out['check_2_steps_vs_oracle_complex_step'] = {
+        'direction0': {'gpu': gd, 'oracle_cs': cs, 'rel_err': abs(gd - cs) / abs(cs)},
+        'mu': {'gpu': gmu2, 'oracle_cs': csm, 'rel_err': abs(gmu2 - csm) / abs(csm)}}
+    # central differences of the GPU forward map (h = 1e-6) along two directions
+    fd = []
+    for k in range(2):
+        dk = torch.from_numpy(dirs[k].reshape(y0.shape)).cuda()
+        vals = []
+        for sgn in (1.0, -1.0):
+            y = yd0 + sgn * 1e-6 * dk
+            for _ in range(K):
+                rok.rok_step(ctx, y, h, M)
+            vals.append(float(G.kinetic_energy(y)))
+        fdv = (vals[0] - vals[1]) / 2e-6
+        fd.append({'adjoint': float(dd[k]), 'central_fd': fdv, 'rel_diff': abs(fdv - dd[k]) / abs(dd[k])})
+    out['central_fd_h1e-6'] = fd
+    print(json.dumps(out))
+
+
 def cpu_baseline(prob, y0, h, steps=8):
     """The CPU oracle, as it stands, on a bounded sample: `steps` ROK4 steps of the
     same workload, single-threaded."""
@@ -593,7 +682,7 @@ def main():
     ap.add_argument('--ref-factor', type=float, default=16.0)
     ap.add_argument('--esdirk-cap', type=float, default=150.0, help='skip ESDIRK runs estimated above this (s)')
     ap.add_argument('--cfls', default=None, help='comma-separated ROK/ESDIRK CFL numbers (study)')
-    ap.add_argument('--mode', default='step', choices=['step', 'stencil', 'batch'])
+    ap.add_argument('--mode', default='step', choices=['step', 'stencil', 'batch', 'grad'])
     ap.add_argument('--n', type=int, default=N_GRID)
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=30)
@@ -610,6 +699,9 @@ def main():
         return
     if args.mode == 'batch':
         run_batch(args)
+        return
+    if args.mode == 'grad':
+        run_grad(args)
         return
     if args.study == 'tte':
         run_tte(args)

@@ -177,6 +177,32 @@ rok_status rok_set_stencil_timing(rok_ctx *ctx, int enable);
 
 const char *rok_status_string(rok_status s);
 
+/* ---- Reverse mode: gradients of a final-time functional ------------------
+ *
+ * For a scalar functional of the state after K steps, the gradient with
+ * respect to the initial state and the viscosity is accumulated backward step
+ * by step: ybar_n = (d y_{n+1} / d y_n)^T ybar_{n+1}, plus each step's
+ * viscosity part.  The derivative is that of the discrete step map (the
+ * discrete adjoint), with the finite-difference increment eps of
+ * Eq. matvecFD held constant.  Supported: uniform periodic grids (Euler, or
+ * Navier-Stokes with constant viscosity), binary64 basis, finite-difference
+ * JVPs; ROK_ERR_UNSUPPORTED otherwise. */
+
+/* ybar = J(y)^T ubar (the transposed Jacobian of the residual of
+ * rok_residual) and, if mubar is non-NULL (HOST), mubar = ubar . df/dmu(y)
+ * (0 for Euler; this call then synchronises).  y, ubar, ybar: device, N
+ * float64; ybar must not overlap the inputs.  Deterministic (no atomics). */
+rok_status rok_vjp(rok_ctx *ctx, const double *y, const double *ubar, double *ybar, double *mubar);
+
+/* Reverse of one rok_step(ctx, y, h, M): given ybar_in = dJ/dy_{n+1}, writes
+ * ybar_out = (dy_{n+1}/dy_n)^T ybar_in and, if mubar is non-NULL (HOST), the
+ * viscosity part dJ/dmu contributed by this step.  The step is recomputed from
+ * y (= y_n, unchanged).  y, ybar_in, ybar_out: device, N float64; ybar_out may
+ * equal ybar_in but not y.  Synchronises.  Workspace: about M + 20 state
+ * vectors, allocated on the first call. */
+rok_status rok_step_vjp(rok_ctx *ctx, const double *y, double h, int M, const double *ybar_in, double *ybar_out,
+                        double *mubar);
+
 /* ---- Batches: many independent instances stepped together ---------------
  *
  * The paper integrates one problem at a time; a batch steps `count`

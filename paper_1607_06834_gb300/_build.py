@@ -28,6 +28,7 @@ SOURCES = {
     'peak.cu': [],
     'noalloc.cu': [],
     'batch.cu': [],
+    'adjoint.cu': [],
 }
 
 

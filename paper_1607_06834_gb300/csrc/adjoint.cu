@@ -1,0 +1,722 @@
+// Reverse mode (vector-Jacobian products) of the residual and of one ROK4 step
+// with finite-difference Jacobian-vector products (Sec. 2.3.3, Eq. ROK;
+// Sec. 2.4, Eq. matvecFD), for gradients of a final-time functional with
+// respect to the state and the (constant) viscosity.
+//
+// Residual VJP, uniform periodic grids: f_c = -(F_{c+1/2} - F_{c-1/2}) / dx
+// - (G_{c+1/2} - G_{c-1/2}) / dy, so a face flux's adjoint is
+// Fbar = (ubar_R - ubar_L) / dx.  Pass 1 (one thread per face) takes Fbar back
+// through the face flux: the 4 x 8 Jacobian of the Roe flux with respect to the
+// reconstructed left/right primitive states comes from eight forward-mode
+// (dual-number) evaluations of the same flux function the residual uses; the
+// central viscous flux is reversed by hand.  Each face stores the adjoints of
+// its MUSCL states and of its viscous inputs.  Pass 2 (one thread per cell)
+// gathers, in a fixed order, the contributions of the faces whose stencils
+// contain the cell (MUSCL reaches two cells along the normal, the viscous
+// gradients one cell across) and maps primitive adjoints to conserved ones.
+// No atomics: the result is deterministic.
+//
+// ROK step reverse: the step is recomputed from y_n (its stage vectors, basis,
+// Hessenberg matrix and stage solutions stay in the context), then every
+// statement is reversed in the opposite order; eps is a constant of the step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "coefficients.h"
+#include "context.h"
+
+#define ROK_NS adj
+#define ROK_STENCIL_DEVICE_ONLY
+#define ROK_LINALG_DEVICE_ONLY
+#include "linalg_impl.cuh"
+#include "stencil_impl.cuh"
+
+using namespace rok;
+using namespace rok::adj;
+
+namespace rok_host {
+rok_status enqueue_step_body(rok_ctx *c, double *y, int M);
+rok_status launch_stencil(rok_ctx *c, const StencilIO &io);
+StencilIO plain_io(rok_ctx *c, const double *y, double *out);
+}  // namespace rok_host
+
+// ---- device state of the reverse step ------------------------------------------
+struct AdjState {
+    double Hb[(kMaxKrylov + 1) * kMaxKrylov];   // adjoint of H (row-major, stride kMaxKrylov)
+    double lamb[4][kMaxKrylov];                 // adjoint of lambda_i
+    double phib[4][kMaxKrylov];                 // adjoint of phi_i
+    double mub;                                 // adjoint of the viscosity
+    double scratch[2 * kMaxKrylov];
+};
+
+struct AdjWork {
+    size_t N = 0;
+    int M = 0, P = 0;
+    double *Vb = nullptr;      // M x N adjoint of the basis
+    double *kb[4] = {};        // adjoints of the stage vectors
+    double *yb = nullptr, *Fb = nullptr, *F1b = nullptr, *F1acc = nullptr;
+    double *wb = nullptr, *wcur = nullptr, *wlast = nullptr, *Yt = nullptr, *y1 = nullptr;
+    double *pA = nullptr, *pB = nullptr, *pM = nullptr;
+    double *faces = nullptr;   // 15 x (nx ny) per direction
+    double *mupart = nullptr;  // CTA partials of the viscosity adjoint
+    int nmu = 0;
+    AdjState *as = nullptr;
+    StepState *h_st = nullptr;
+    double *h_mub = nullptr;
+};
+
+namespace {
+
+#define CU(x)                                      \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return ROK_ERR_CUDA; \
+    } while (0)
+
+constexpr int AT = 256;
+constexpr int kFaceVals = 15;   // MUSCL left/right adjoints (8) + viscous input adjoints (7)
+
+__device__ __forceinline__ void prim_at(const StencilConsts &C, const double *__restrict__ y, size_t nc, size_t c,
+                                        double *P, double &T)
+{
+    const double rho = y[c], mx = y[nc + c], my = y[2 * nc + c], E = y[3 * nc + c];
+    const double rinv = 1.0 / rho;
+    const double u = mx * rinv, v = my * rinv;
+    const double p = C.gm1 * (E - 0.5 * (mx * u + my * v));
+    P[0] = rho;
+    P[1] = u;
+    P[2] = v;
+    P[3] = p;
+    T = p * rinv;
+}
+
+// Pass 1: face D (0: x-faces, face i of row j between cells (i-1, j) and (i, j);
+// 1: y-faces, face j of column i between (i, j-1) and (i, j)).  Stores
+// fa[q * nc + face] for q < 15 and one partial of ubar . df/dmu per CTA.
+template <bool VISC, int D>
+__global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, const double *__restrict__ y,
+                                                      const double *__restrict__ ub, double *__restrict__ fa,
+                                                      double *__restrict__ mupart)
+{
+    __shared__ double sh[10];
+    const int nx = C.nx, ny = C.ny;
+    const size_t nc = (size_t)nx * ny;
+    const size_t t = (size_t)blockIdx.x * AT + threadIdx.x;
+    double mu_c = 0.0;
+    if (t < nc) {
+        const int i = (int)(t % nx), j = (int)(t / nx);
+        auto cell = [&](int s) -> size_t {   // s-th cell along the normal, s = 0 is the face's upper cell
+            return D == 0 ? (size_t)j * nx + wrapi(i + s, nx) : (size_t)wrapi(j + s, ny) * nx + i;
+        };
+        const size_t cm2 = cell(-2), cm1 = cell(-1), cp1 = cell(0), cp2 = cell(1);
+        double Pm2[4], Pm1[4], Pp1[4], Pp2[4], Tm2, Tm1, Tp1, Tp2;
+        prim_at(C, y, nc, cm2, Pm2, Tm2);
+        prim_at(C, y, nc, cm1, Pm1, Tm1);
+        prim_at(C, y, nc, cp1, Pp1, Tp1);
+        prim_at(C, y, nc, cp2, Pp2, Tp2);
+        double WL[4], WR[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) muscl(Pm2[k], Pm1[k], Pp1[k], Pp2[k], C.c_lo, C.c_hi, WL[k], WR[k]);
+        const double rd = D == 0 ? C.rdx : C.rdy;
+        double Fb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Fb[k] = rd * (ub[k * nc + cp1] - ub[k * nc + cm1]);
+        // Roe flux: column q of its Jacobian by one dual-number evaluation
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            Dual L[4], R[4], F[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                L[k] = {WL[k], q == k ? 1.0 : 0.0};
+                R[k] = {WR[k], q == k + 4 ? 1.0 : 0.0};
+            }
+            if (D == 0) roe_x(L, R, C, F);
+            else roe_y(L, R, C, F);
+            fa[q * nc + t] = ((F[0].d * Fb[0] + F[1].d * Fb[1]) + F[2].d * Fb[2]) + F[3].d * Fb[3];
+        }
+        if (VISC) {
+            // normal cells a = cm1, b = cp1; tangential neighbours across the face
+            auto cross = [&](size_t c0, int s) -> size_t {
+                const int ci = (int)(c0 % nx), cj = (int)(c0 / nx);
+                return D == 0 ? (size_t)wrapi(cj + s, ny) * nx + ci : (size_t)cj * nx + wrapi(ci + s, nx);
+            };
+            auto uv = [&](size_t c0, int comp) -> double { return y[(1 + comp) * nc + c0] / y[c0]; };
+            const double q_rt = D == 0 ? C.q_rdy : C.q_rdx;
+            // normal and tangential derivatives of u and v, normal derivative of T
+            const double un = (Pp1[1] - Pm1[1]) * rd, vn = (Pp1[2] - Pm1[2]) * rd, Tn = (Tp1 - Tm1) * rd;
+            const double ut = ((uv(cross(cm1, 1), 0) + uv(cross(cp1, 1), 0)) -
+                               (uv(cross(cm1, -1), 0) + uv(cross(cp1, -1), 0))) * q_rt;
+            const double vt = ((uv(cross(cm1, 1), 1) + uv(cross(cp1, 1), 1)) -
+                               (uv(cross(cm1, -1), 1) + uv(cross(cp1, -1), 1))) * q_rt;
+            const double uf = 0.5 * (Pm1[1] + Pp1[1]), vf = 0.5 * (Pm1[2] + Pp1[2]);
+            const double mu = C.mu, kf = mu * C.kfac;
+            // x-face: ux = un, uy = ut, vx = vn, vy = vt; y-face: uy = un, ux = ut, vy = vn, vx = vt
+            const double ux = D == 0 ? un : ut, uy = D == 0 ? ut : un, vx = D == 0 ? vn : vt, vy = D == 0 ? vt : vn;
+            const double div = ux + vy;
+            const double txx1 = 2.0 * ux - C.c23 * div, tyy1 = 2.0 * vy - C.c23 * div, txy1 = uy + vx;
+            // flux terms removed by the viscous flux: x-face (txx, txy), y-face (txy, tyy)
+            const double s1 = D == 0 ? txx1 : txy1, s2 = D == 0 ? txy1 : tyy1;
+            // reverse of F1 -= mu s1, F2 -= mu s2, F3 -= (uf mu s1 + vf mu s2 + kf Tn)
+            const double s1b = -mu * (Fb[1] + uf * Fb[3]);     // adjoint of mu s1 ... times mu
+            const double s2b = -mu * (Fb[2] + vf * Fb[3]);
+            const double ufb = -mu * s1 * Fb[3], vfb = -mu * s2 * Fb[3], Tnb = -kf * Fb[3];
+            double uxb = 0.0, uyb = 0.0, vxb = 0.0, vyb = 0.0;
+            if (D == 0) {   // s1 = 2 ux - c23 (ux + vy), s2 = uy + vx
+                uxb = (2.0 - C.c23) * s1b;
+                vyb = -C.c23 * s1b;
+                uyb = s2b;
+                vxb = s2b;
+            } else {        // s1 = uy + vx, s2 = 2 vy - c23 (ux + vy)
+                uyb = s1b;
+                vxb = s1b;
+                vyb = (2.0 - C.c23) * s2b;
+                uxb = -C.c23 * s2b;
+            }
+            fa[8 * nc + t] = D == 0 ? uxb : uyb;    // normal derivative of u
+            fa[9 * nc + t] = D == 0 ? uyb : uxb;    // tangential derivative of u
+            fa[10 * nc + t] = D == 0 ? vxb : vyb;   // normal derivative of v
+            fa[11 * nc + t] = D == 0 ? vyb : vxb;   // tangential derivative of v
+            fa[12 * nc + t] = Tnb;
+            fa[13 * nc + t] = ufb;
+            fa[14 * nc + t] = vfb;
+            mu_c = -((Fb[1] * s1 + Fb[2] * s2) + Fb[3] * ((uf * s1 + vf * s2) + C.kfac * Tn));
+        }
+    }
+    const double s = cta_tree(lane_tree(mu_c), sh);
+    if (threadIdx.x == 0) mupart[blockIdx.x] = s;
+}
+
+struct VjpOut {
+    double *out1;            // out1 += s1 (* s1dev) g   (nullable)
+    double s1;
+    const double *s1dev;
+    double *out2;            // out2 += s2 (* s2dev) g   (nullable)
+    double s2;
+    const double *s2dev;
+};
+
+// Pass 2: g = J^T ubar at each cell from the face adjoints
+template <bool VISC>
+__global__ void __launch_bounds__(AT) vjp_cell_kernel(const StencilConsts C, const double *__restrict__ y,
+                                                      const double *__restrict__ fx, const double *__restrict__ fy,
+                                                      const VjpOut o)
+{
+    const int nx = C.nx, ny = C.ny;
+    const size_t nc = (size_t)nx * ny;
+    const size_t t = (size_t)blockIdx.x * AT + threadIdx.x;
+    if (t >= nc) return;
+    const int i = (int)(t % nx), j = (int)(t / nx);
+    auto xf = [&](int fi, int fj) -> size_t { return (size_t)wrapi(fj, ny) * nx + wrapi(fi, nx); };
+    const double a1 = (1.0 + C.c_lo) - C.c_hi;
+    double Pb[4] = {0.0, 0.0, 0.0, 0.0}, Tb = 0.0;
+    // MUSCL: the cell is m2 of face +2, m1 of face +1, p1 of face 0, p2 of face -1
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double *xl = fx + (size_t)k * nc, *xr = fx + (size_t)(k + 4) * nc;
+        const double *yl = fy + (size_t)k * nc, *yr = fy + (size_t)(k + 4) * nc;
+        double s = -C.c_lo * xl[xf(i + 2, j)];
+        s = s + (a1 * xl[xf(i + 1, j)] + C.c_hi * xr[xf(i + 1, j)]);
+        s = s + (C.c_hi * xl[xf(i, j)] + a1 * xr[xf(i, j)]);
+        s = s - C.c_lo * xr[xf(i - 1, j)];
+        s = s - C.c_lo * yl[xf(i, j + 2)];
+        s = s + (a1 * yl[xf(i, j + 1)] + C.c_hi * yr[xf(i, j + 1)]);
+        s = s + (C.c_hi * yl[xf(i, j)] + a1 * yr[xf(i, j)]);
+        s = s - C.c_lo * yr[xf(i, j - 1)];
+        Pb[k] = s;
+    }
+    if (VISC) {
+        auto F = [&](const double *f, int q, size_t idx) { return f[(size_t)q * nc + idx]; };
+        // x-faces: upper cell of face i, lower cell of face i + 1 (row j)
+        {
+            const size_t up = xf(i, j), lo = xf(i + 1, j);
+            Pb[1] += (F(fx, 8, up) - F(fx, 8, lo)) * C.rdx + 0.5 * (F(fx, 13, up) + F(fx, 13, lo));
+            Pb[2] += (F(fx, 10, up) - F(fx, 10, lo)) * C.rdx + 0.5 * (F(fx, 14, up) + F(fx, 14, lo));
+            Tb += (F(fx, 12, up) - F(fx, 12, lo)) * C.rdx;
+            // tangential: faces i, i+1 of row j-1 (+) and of row j+1 (-)
+            const size_t a = xf(i, j - 1), b = xf(i + 1, j - 1), c2 = xf(i, j + 1), d = xf(i + 1, j + 1);
+            Pb[1] += ((F(fx, 9, a) + F(fx, 9, b)) - (F(fx, 9, c2) + F(fx, 9, d))) * C.q_rdy;
+            Pb[2] += ((F(fx, 11, a) + F(fx, 11, b)) - (F(fx, 11, c2) + F(fx, 11, d))) * C.q_rdy;
+        }
+        // y-faces: upper cell of face j, lower cell of face j + 1 (column i)
+        {
+            const size_t up = xf(i, j), lo = xf(i, j + 1);
+            Pb[1] += (F(fy, 8, up) - F(fy, 8, lo)) * C.rdy + 0.5 * (F(fy, 13, up) + F(fy, 13, lo));
+            Pb[2] += (F(fy, 10, up) - F(fy, 10, lo)) * C.rdy + 0.5 * (F(fy, 14, up) + F(fy, 14, lo));
+            Tb += (F(fy, 12, up) - F(fy, 12, lo)) * C.rdy;
+            const size_t a = xf(i - 1, j), b = xf(i - 1, j + 1), c2 = xf(i + 1, j), d = xf(i + 1, j + 1);
+            Pb[1] += ((F(fy, 9, a) + F(fy, 9, b)) - (F(fy, 9, c2) + F(fy, 9, d))) * C.q_rdx;
+            Pb[2] += ((F(fy, 11, a) + F(fy, 11, b)) - (F(fy, 11, c2) + F(fy, 11, d))) * C.q_rdx;
+        }
+    }
+    double P[4], T;
+    prim_at(C, y, nc, t, P, T);
+    const double rho = P[0], u = P[1], v = P[2];
+    const double rinv = 1.0 / rho;
+    // T = p / rho
+    Pb[3] += Tb * rinv;
+    Pb[0] -= Tb * T * rinv;
+    // rho = q0, u = q1 / rho, v = q2 / rho, p = (gamma - 1) (q3 - (q1^2 + q2^2) / (2 q0))
+    double qb[4];
+    qb[0] = (Pb[0] - (u * Pb[1] + v * Pb[2]) * rinv) + C.gm1 * 0.5 * (u * u + v * v) * Pb[3];
+    qb[1] = Pb[1] * rinv - C.gm1 * u * Pb[3];
+    qb[2] = Pb[2] * rinv - C.gm1 * v * Pb[3];
+    qb[3] = C.gm1 * Pb[3];
+    const double s1 = o.s1dev ? o.s1 * *o.s1dev : o.s1;
+    const double s2 = o.s2dev ? o.s2 * *o.s2dev : o.s2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const size_t e = (size_t)k * nc + t;
+        if (o.out1) o.out1[e] = o.out1[e] + s1 * qb[k];
+        if (o.out2) o.out2[e] = o.out2[e] + s2 * qb[k];
+    }
+}
+
+// dst += factor (* fdev) tree(part[0..n)), one CTA
+__global__ void tree_add_kernel(const double *part, int n, double factor, const double *fdev, double *dst)
+{
+    __shared__ double sh[10];
+    const double s = tree_partials(part, n, sh);
+    if (threadIdx.x == 0) *dst = *dst + (fdev ? factor * *fdev : factor) * s;
+}
+
+// out = c0 x0 + (c1 * c1dev) x1   (x0 nullable)
+__global__ void __launch_bounds__(AT) lin2_kernel(double *out, const double *x0, double c0, const double *x1,
+                                                  double c1, const double *c1dev, size_t n)
+{
+    const double a = c1dev ? c1 * *c1dev : c1;
+    for (size_t e = (size_t)blockIdx.x * AT + threadIdx.x; e < n; e += (size_t)gridDim.x * AT)
+        out[e] = (x0 ? c0 * x0[e] : 0.0) + a * x1[e];
+}
+
+// Fbar = h kbar + sum_m phib[m] V_m
+__global__ void __launch_bounds__(AT) fbar_kernel(double *out, const double *kb, double h, const double *V, size_t ldv,
+                                                  size_t n, const double *phib, const StepState *st)
+{
+    __shared__ double c[kMaxKrylov];
+    const int m = st->meff;
+    for (int q = threadIdx.x; q < m; q += AT) c[q] = phib[q];
+    __syncthreads();
+    for (size_t e = (size_t)blockIdx.x * AT + threadIdx.x; e < n; e += (size_t)gridDim.x * AT) {
+        double a = h * kb[e];
+        for (int q = 0; q < m; ++q) a = a + c[q] * V[(size_t)q * ldv + e];
+        out[e] = a;
+    }
+}
+
+// Vbar_m = sum_i (cvec_i[m] kbar_i + phib_i[m] F_i), m < meff
+__global__ void __launch_bounds__(AT) assemble_vb_kernel(double *Vb, size_t ldv, size_t n, const double *k0,
+                                                         const double *k1, const double *k2, const double *k3,
+                                                         const double *F0, const double *F1, const double *F2,
+                                                         const double *F3, const StepState *st, const AdjState *as)
+{
+    const int m = st->meff;
+    for (size_t e = (size_t)blockIdx.x * AT + threadIdx.x; e < n; e += (size_t)gridDim.x * AT) {
+        const double kk[4] = {k0[e], k1[e], k2[e], k3[e]};
+        const double ff[4] = {F0[e], F1[e], F2[e], F3[e]};
+        for (int q = 0; q < m; ++q) {
+            double a = 0.0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a = a + (st->cvec[i][q] * kk[i] + as->phib[i][q] * ff[i]);
+            Vb[(size_t)q * ldv + e] = a;
+        }
+    }
+}
+
+struct GamRowA {
+    double g[4];
+};
+
+// Reverse of stage i's small system (one CTA):
+//   cbar = V^T kbar_i (tree of the CTA partials pc[m * P + b]);
+//   lambda_i = L^{-1} rhs_i, L = I - h g H (LU with row interchanges from the step);
+//   rhs_i = h phi_i + h H acc_i, acc_i = sum_{j<i} gamma_ij lambda_j.
+__global__ void stage_rev_kernel(int stage, GamRowA gr, const double *pc, int P, const StepState *st, AdjState *as)
+{
+    const int m = st->meff;
+    const double h = st->h, hg = st->hg;
+    __shared__ double cb[kMaxKrylov], z[kMaxKrylov], acc[kMaxKrylov];
+    for (int q = threadIdx.x >> 5; q < m; q += blockDim.x >> 5) {
+        const double v = warp_tree_partials(pc + (size_t)q * P, P);
+        if ((threadIdx.x & 31) == 0) cb[q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double *lamb = as->lamb[stage];
+    double *phib = as->phib[stage];
+    for (int q = 0; q < m; ++q) {
+        lamb[q] += cb[q];
+        phib[q] = -h * cb[q];
+    }
+    // z = L^{-T} lamb: U^T s = lamb, L^T t = s, then the interchanges in reverse order
+    const double *A = st->LU;
+    for (int r = 0; r < m; ++r) {
+        double s = lamb[r];
+        for (int k = 0; k < r; ++k) s = s - A[k * kMaxKrylov + r] * z[k];
+        z[r] = s / A[r * kMaxKrylov + r];
+    }
+    for (int r = m - 1; r >= 0; --r) {
+        double s = z[r];
+        for (int k = r + 1; k < m; ++k) s = s - A[k * kMaxKrylov + r] * z[k];
+        z[r] = s;
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        const int p = st->piv[k];
+        if (p != k) { double tmp = z[k]; z[k] = z[p]; z[p] = tmp; }
+    }
+    for (int q = 0; q < m; ++q) {
+        double a = 0.0;
+        for (int jj = 0; jj < stage; ++jj) a = a + gr.g[jj] * st->lam[jj][q];
+        acc[q] = a;
+    }
+    // H_bar += h g z lambda_i^T + h z acc_i^T ; phi_bar += h z ; acc_bar = h H^T z
+    for (int r = 0; r < m; ++r)
+        for (int q = 0; q < m; ++q)
+            as->Hb[r * kMaxKrylov + q] += hg * z[r] * st->lam[stage][q] + h * z[r] * acc[q];
+    for (int q = 0; q < m; ++q) phib[q] += h * z[q];
+    for (int q = 0; q < m; ++q) {
+        double a = 0.0;
+        for (int r = 0; r < m; ++r) a = a + st->H[r * kMaxKrylov + q] * z[r];
+        const double accb = h * a;
+        for (int jj = 0; jj < stage; ++jj) as->lamb[jj][q] += gr.g[jj] * accb;
+    }
+}
+
+// Reverse of v = w / hn, hn = ||w|| (or of v_1 = F1 / beta):
+//   out = (base ? base : 0) + vb / hn + (extra - <v, vb> / hn) v, <v, vb> = tree(pin)
+__global__ void __launch_bounds__(AT) normrev_kernel(double *out, const double *base, const double *vb,
+                                                     const double *v, size_t n, const double *pin, int P,
+                                                     const double *hn_ptr, const double *extra_ptr)
+{
+    __shared__ double sh[10];
+    const double d = tree_partials(pin, P, sh);
+    const double hn = *hn_ptr;
+    const double cv = (extra_ptr ? *extra_ptr : 0.0) - d / hn;
+    for (size_t e = (size_t)blockIdx.x * AT + threadIdx.x; e < n; e += (size_t)gridDim.x * AT)
+        out[e] = (base ? base[e] : 0.0) + vb[e] / hn + cv * v[e];
+}
+
+// Reverse of one modified-Gram-Schmidt pass of column j: w_{i+1} = w_i - h_ij v_i,
+// h_ij = <v_i, w_i>, given wbar = adjoint of w_{i+1} and wcur = w_{i+1}:
+//   hb = Hbar_ij - <v_i, wbar>;  w_i = wcur + h_ij v_i;
+//   Vbar_i += -h_ij wbar + hb w_i;  wbar += hb v_i;  wcur = w_i;
+// then the partials of <v_{i-1}, wbar> for the next pass (CTA chunks of 2048).
+__global__ void __launch_bounds__(RT) mgsrev_kernel(double *__restrict__ wb, double *__restrict__ wcur,
+                                                    double *__restrict__ Vbi, const double *__restrict__ vi,
+                                                    const double *__restrict__ vprev, size_t n,
+                                                    const double *__restrict__ pin, int P, const double *hij_ptr,
+                                                    const double *hbij_ptr, double *__restrict__ pout)
+{
+    __shared__ double sh[10];
+    const size_t e0 = lane_e0();
+    double w[EPL], c[EPL], v[EPL], g[EPL], x[EPL];
+    load8(wb, e0, n, w);
+    load8(wcur, e0, n, c);
+    load8(vi, e0, n, v);
+    load8(Vbi, e0, n, g);
+    const double d = tree_partials(pin, P, sh);
+    const double hij = *hij_ptr;
+    const double hb = *hbij_ptr - d;
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+        const double wi = c[k] + hij * v[k];
+        g[k] = (g[k] - hij * w[k]) + hb * wi;
+        w[k] = w[k] + hb * v[k];
+        c[k] = wi;
+    }
+    store8(wb, e0, n, w);
+    store8(wcur, e0, n, c);
+    store8(Vbi, e0, n, g);
+    if (vprev) {
+        load8(vprev, e0, n, x);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = x[k] * w[k];
+        const double s = chunk_sum(x, sh);
+        if (threadIdx.x == 0) pout[blockIdx.x] = s;
+    }
+}
+
+// residual VJP launches: out1 += s1 g, out2 += s2 g with g = J(ystate)^T ubar;
+// dst_mu += mu_factor (* mu_dev) ubar . df/dmu(ystate)
+rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, const VjpOut &o, double *dst_mu,
+               double mu_factor, const double *mu_dev)
+{
+    const StencilConsts &C = c->C;
+    const size_t nc = (size_t)C.nx * C.ny;
+    const int nb = (int)((nc + AT - 1) / AT);
+    double *fxa = A->faces, *fya = A->faces + kFaceVals * nc;
+    cudaStream_t s = c->stream;
+    if (C.viscous) {
+        vjp_face_kernel<true, 0><<<nb, AT, 0, s>>>(C, ystate, ub, fxa, A->mupart);
+        vjp_face_kernel<true, 1><<<nb, AT, 0, s>>>(C, ystate, ub, fya, A->mupart + nb);
+        vjp_cell_kernel<true><<<nb, AT, 0, s>>>(C, ystate, fxa, fya, o);
+    } else {
+        vjp_face_kernel<false, 0><<<nb, AT, 0, s>>>(C, ystate, ub, fxa, A->mupart);
+        vjp_face_kernel<false, 1><<<nb, AT, 0, s>>>(C, ystate, ub, fya, A->mupart + nb);
+        vjp_cell_kernel<false><<<nb, AT, 0, s>>>(C, ystate, fxa, fya, o);
+    }
+    c->launches += 3;
+    if (dst_mu && C.viscous) {
+        tree_add_kernel<<<1, AT, 0, s>>>(A->mupart, 2 * nb, mu_factor, mu_dev, dst_mu);
+        c->launches++;
+    }
+    CU(cudaGetLastError());
+    return ROK_OK;
+}
+
+rok_status vjp_supported(const rok_ctx *c)
+{
+    if (c->kind == ROK_LORENZ96 || c->curv) return ROK_ERR_UNSUPPORTED;
+    if (c->C.sutherland) return ROK_ERR_UNSUPPORTED;
+    return ROK_OK;
+}
+
+void free_work(AdjWork *A)
+{
+    if (!A) return;
+    cudaFree(A->Vb);
+    for (int i = 0; i < 4; ++i) cudaFree(A->kb[i]);
+    cudaFree(A->yb); cudaFree(A->Fb); cudaFree(A->F1b); cudaFree(A->F1acc);
+    cudaFree(A->wb); cudaFree(A->wcur); cudaFree(A->wlast); cudaFree(A->Yt); cudaFree(A->y1);
+    cudaFree(A->pA); cudaFree(A->pB); cudaFree(A->pM);
+    cudaFree(A->faces); cudaFree(A->mupart); cudaFree(A->as);
+    cudaFreeHost(A->h_st); cudaFreeHost(A->h_mub);
+    delete A;
+}
+
+rok_status ensure_work(rok_ctx *c, bool full)
+{
+    if (c->adj && (!full || c->adj->Vb)) return ROK_OK;
+    AdjWork *A = c->adj ? c->adj : new AdjWork();
+    c->adj = A;
+    const size_t N = c->N, nc = c->nc;
+    A->N = N;
+    A->P = c->P;
+    A->M = c->mmax;
+    auto al = [&](double **p, size_t n) { return cudaMalloc(p, n * sizeof(double)) == cudaSuccess; };
+    bool ok = true;
+    if (!A->faces) {
+        A->nmu = 2 * (int)((nc + AT - 1) / AT);
+        ok = al(&A->faces, 2 * kFaceVals * nc) && al(&A->mupart, A->nmu) &&
+             cudaMalloc(&A->as, sizeof(AdjState)) == cudaSuccess &&
+             cudaMallocHost(&A->h_mub, sizeof(double)) == cudaSuccess;
+    }
+    if (ok && full) {
+        ok = al(&A->Vb, (size_t)(c->mmax > 0 ? c->mmax : 1) * N) && al(&A->yb, N) && al(&A->Fb, N) &&
+             al(&A->F1b, N) && al(&A->F1acc, N) && al(&A->wb, N) && al(&A->wcur, N) && al(&A->wlast, N) &&
+             al(&A->Yt, N) && al(&A->y1, N) && al(&A->pA, 2 * (size_t)c->P) && al(&A->pB, 2 * (size_t)c->P) &&
+             al(&A->pM, (size_t)(c->mmax > 0 ? c->mmax : 1) * c->P) &&
+             cudaMallocHost(&A->h_st, sizeof(StepState)) == cudaSuccess;
+        for (int i = 0; i < 4 && ok; ++i) ok = al(&A->kb[i], N);
+    }
+    if (!ok) {
+        free_work(A);
+        c->adj = nullptr;
+        return ROK_ERR_NOMEM;
+    }
+    return ROK_OK;
+}
+
+inline int egrid(const rok_ctx *c) { return c->egrid; }
+
+}  // namespace
+
+void rok_free_adjoint(rok_ctx *c)
+{
+    if (c && c->adj) {
+        free_work(c->adj);
+        c->adj = nullptr;
+    }
+}
+
+extern "C" {
+
+rok_status rok_vjp(rok_ctx *c, const double *y, const double *ubar, double *ybar, double *mubar)
+{
+    if (!c || !y || !ubar || !ybar || ybar == y || ybar == ubar) return ROK_ERR_INVALID_ARG;
+    rok_status r = vjp_supported(c);
+    if (r != ROK_OK) return r;
+    if ((r = ensure_work(c, false)) != ROK_OK) return r;
+    AdjWork *A = c->adj;
+    CU(cudaMemsetAsync(ybar, 0, c->N * sizeof(double), c->stream));
+    if (mubar) CU(cudaMemsetAsync(&A->as->mub, 0, sizeof(double), c->stream));
+    VjpOut o{ybar, 1.0, nullptr, nullptr, 0.0, nullptr};
+    if ((r = vjp(c, A, y, ubar, o, mubar ? &A->as->mub : nullptr, 1.0, nullptr)) != ROK_OK) return r;
+    if (mubar) {
+        if (!c->C.viscous) {
+            *mubar = 0.0;
+            return ROK_OK;
+        }
+        CU(cudaMemcpyAsync(A->h_mub, &A->as->mub, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        *mubar = *A->h_mub;
+    }
+    return ROK_OK;
+}
+
+rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const double *ybar_in, double *ybar_out,
+                        double *mubar)
+{
+    if (!c || !y || !ybar_in || !ybar_out || M < 0 || M > c->mmax || !(h > 0.0) || !isfinite(h))
+        return ROK_ERR_INVALID_ARG;
+    if (ybar_out == y) return ROK_ERR_INVALID_ARG;
+    rok_status r = vjp_supported(c);
+    if (r != ROK_OK) return r;
+    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
+    if ((r = ensure_work(c, true)) != ROK_OK) return r;
+    AdjWork *A = c->adj;
+    const size_t N = c->N;
+    const int P = c->P;
+    StepState *st = c->st;
+    AdjState *as = A->as;
+    cudaStream_t s = c->stream;
+    const LinalgOps &ops = *c->ops;
+    const int eg = egrid(c);
+
+    // 1. the step again from y_n, keeping its internals (V, H, LU, lambda_i,
+    //    phi_i, F_i, k_i stay in the context)
+    CU(cudaMemcpyAsync(A->y1, y, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(launch_begin(st, h, kRokGamma, M, s));
+    CU(cudaMemsetAsync(&c->bar->count, 0, sizeof(unsigned), s));
+    if ((r = rok_host::enqueue_step_body(c, A->y1, M)) != ROK_OK) return r;
+    CU(cudaMemcpyAsync(A->h_st, st, offsetof(StepState, H), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (A->h_st->status) {
+        CU(launch_set_int(&st->status, 0, s));
+        return (A->h_st->status & kStatusTimeout) ? ROK_ERR_TIMEOUT : ROK_ERR_NONFINITE;
+    }
+    const int m = A->h_st->meff;
+    // the last column's orthogonalised w (not kept by the step): its JVP and MGS
+    // passes again, H entries to scratch
+    if (m > 0) {
+        StencilIO io = rok_host::plain_io(c, y, A->wlast);
+        io.add[0] = c->V + (size_t)(m - 1) * N;
+        io.coef[0] = 1.0;
+        io.coef_dev[0] = &st->eps;
+        io.nadd = 1;
+        io.sub = c->F[0];
+        io.s1_dev = &st->inv_eps;
+        if ((r = rok_host::launch_stencil(c, io)) != ROK_OK) return r;
+        CU(launch_set_int(&st->active, 1, s));
+        CU(ops.dot2(c->V, A->wlast, A->wlast, A->wlast, N, A->pA, P, nullptr, s));
+        double *pin = A->pA, *pout = A->pB;
+        for (int i = 1; i <= m; ++i) {
+            const double *vnext = i < m ? c->V + (size_t)i * N : nullptr;
+            CU(ops.mgs(A->wlast, c->V + (size_t)(i - 1) * N, vnext, N, pin, P, &as->scratch[0], pout, i == 1, st, s));
+            double *t = pin; pin = pout; pout = t;
+        }
+        c->launches += 2 + m;
+    }
+
+    // 2. stages in reverse: y_{n+1} = y_n + sum b_i k_i
+    CU(cudaMemsetAsync(as, 0, sizeof(AdjState), s));
+    CU(cudaMemcpyAsync(A->yb, ybar_in, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < 4; ++i) {
+        lin2_kernel<<<eg, AT, 0, s>>>(A->kb[i], nullptr, 0.0, ybar_in, kRokB[i], nullptr, N);
+        c->launches++;
+    }
+    for (int i = 3; i >= 0; --i) {
+        if (m > 0) {
+            CU(ops.multidot(A->kb[i], c->V, 0, N, N, A->pM, P, st, s));
+            GamRowA gr;
+            for (int j = 0; j < 4; ++j) gr.g[j] = kRokGammaOff[i][j];
+            stage_rev_kernel<<<1, AT, 0, s>>>(i, gr, A->pM, P, st, as);
+            fbar_kernel<<<eg, AT, 0, s>>>(A->Fb, A->kb[i], h, c->V, N, N, as->phib[i], st);
+            c->launches += 3;
+        } else {
+            lin2_kernel<<<eg, AT, 0, s>>>(A->Fb, nullptr, 0.0, A->kb[i], h, nullptr, N);
+            c->launches++;
+        }
+        if (i == 0) {
+            CU(cudaMemcpyAsync(A->F1b, A->Fb, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            continue;
+        }
+        // Y_i = y + sum_j alpha_ij k_j ; F_i = f(Y_i)
+        const double *kv[4];
+        double cf[4];
+        int cnt = 0;
+        for (int j = 0; j < i; ++j)
+            if (kRokAlpha[i][j] != 0.0) { kv[cnt] = c->K[j]; cf[cnt] = kRokAlpha[i][j]; cnt++; }
+        CU(ops.axpy_n(A->Yt, y, kv, cf, cnt, N, nullptr, eg, s));
+        c->launches++;
+        // g = J(Y_i)^T Fbar: ybar += g, kbar_j += alpha_ij g (one alpha per row here; others by a copy)
+        int jlast = -1;
+        for (int j = 0; j < i; ++j)
+            if (kRokAlpha[i][j] != 0.0) jlast = j;
+        VjpOut o{A->yb, 1.0, nullptr, jlast >= 0 ? A->kb[jlast] : nullptr, jlast >= 0 ? kRokAlpha[i][jlast] : 0.0,
+                 nullptr};
+        if (cnt > 1) {
+            // general tableau: keep g in wb, then add it to every k_j
+            CU(cudaMemsetAsync(A->wb, 0, N * sizeof(double), s));
+            VjpOut og{A->wb, 1.0, nullptr, nullptr, 0.0, nullptr};
+            if ((r = vjp(c, A, A->Yt, A->Fb, og, &as->mub, 1.0, nullptr)) != ROK_OK) return r;
+            lin2_kernel<<<eg, AT, 0, s>>>(A->yb, A->yb, 1.0, A->wb, 1.0, nullptr, N);
+            for (int j = 0; j < i; ++j)
+                if (kRokAlpha[i][j] != 0.0)
+                    lin2_kernel<<<eg, AT, 0, s>>>(A->kb[j], A->kb[j], 1.0, A->wb, kRokAlpha[i][j], nullptr, N);
+        } else if ((r = vjp(c, A, A->Yt, A->Fb, o, &as->mub, 1.0, nullptr)) != ROK_OK) {
+            return r;
+        }
+    }
+
+    // 3. Arnoldi in reverse
+    if (m > 0) {
+        assemble_vb_kernel<<<eg, AT, 0, s>>>(A->Vb, N, N, A->kb[0], A->kb[1], A->kb[2], A->kb[3], c->F[0], c->F[1],
+                                             c->F[2], c->F[3], st, as);
+        CU(cudaMemsetAsync(A->F1acc, 0, N * sizeof(double), s));
+        c->launches++;
+        for (int j = m - 1; j >= 0; --j) {
+            const double *vj = c->V + (size_t)j * N;
+            if (j + 1 < m) {
+                const double *v1 = c->V + (size_t)(j + 1) * N;
+                double *vb1 = A->Vb + (size_t)(j + 1) * N;
+                CU(ops.dot2(v1, vb1, nullptr, nullptr, N, A->pA, P, nullptr, s));
+                normrev_kernel<<<eg, AT, 0, s>>>(A->wb, nullptr, vb1, v1, N, A->pA, P,
+                                                 &st->H[(j + 1) * kMaxKrylov + j], &as->Hb[(j + 1) * kMaxKrylov + j]);
+                lin2_kernel<<<eg, AT, 0, s>>>(A->wcur, nullptr, 0.0, v1, 1.0, &st->H[(j + 1) * kMaxKrylov + j], N);
+                c->launches += 3;
+            } else {
+                CU(cudaMemsetAsync(A->wb, 0, N * sizeof(double), s));
+                CU(cudaMemcpyAsync(A->wcur, A->wlast, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            }
+            CU(ops.dot2(vj, A->wb, nullptr, nullptr, N, A->pA, P, nullptr, s));
+            c->launches++;
+            double *pin = A->pA, *pout = A->pB;
+            for (int i = j; i >= 0; --i) {
+                const double *vi = c->V + (size_t)i * N;
+                const double *vprev = i > 0 ? c->V + (size_t)(i - 1) * N : nullptr;
+                mgsrev_kernel<<<P, RT, 0, s>>>(A->wb, A->wcur, A->Vb + (size_t)i * N, vi, vprev, N, pin, P,
+                                               &st->H[i * kMaxKrylov + j], &as->Hb[i * kMaxKrylov + j], pout);
+                c->launches++;
+                double *t = pin; pin = pout; pout = t;
+            }
+            // w_0 = (f(y + eps v_j) - F1) / eps
+            lin2_kernel<<<eg, AT, 0, s>>>(A->Yt, y, 1.0, vj, 1.0, &st->eps, N);
+            c->launches++;
+            VjpOut o{A->Vb + (size_t)j * N, 1.0, nullptr, A->yb, 1.0, &st->inv_eps};
+            if ((r = vjp(c, A, A->Yt, A->wb, o, &as->mub, 1.0, &st->inv_eps)) != ROK_OK) return r;
+            lin2_kernel<<<eg, AT, 0, s>>>(A->F1acc, A->F1acc, 1.0, A->wb, 1.0, nullptr, N);
+            c->launches++;
+        }
+        // v_1 = F1 / beta
+        CU(ops.dot2(c->V, A->Vb, nullptr, nullptr, N, A->pA, P, nullptr, s));
+        normrev_kernel<<<eg, AT, 0, s>>>(A->F1b, A->F1b, A->Vb, c->V, N, A->pA, P, &st->beta, nullptr);
+        lin2_kernel<<<eg, AT, 0, s>>>(A->F1b, A->F1b, 1.0, A->F1acc, -1.0, &st->inv_eps, N);
+        c->launches += 3;
+    }
+    // 4. F1 = f(y_n)
+    VjpOut o{A->yb, 1.0, nullptr, nullptr, 0.0, nullptr};
+    if ((r = vjp(c, A, y, A->F1b, o, &as->mub, 1.0, nullptr)) != ROK_OK) return r;
+    CU(cudaMemcpyAsync(ybar_out, A->yb, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (mubar) {
+        CU(cudaMemcpyAsync(A->h_mub, &as->mub, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        *mubar = c->C.viscous ? *A->h_mub : 0.0;
+    }
+    CU(cudaGetLastError());
+    return ROK_OK;
+}
+
+}  // extern "C"

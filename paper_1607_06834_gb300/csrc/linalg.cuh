@@ -28,6 +28,7 @@ struct StepState {
     double lam[4][kMaxKrylov];
     double cvec[4][kMaxKrylov];
     double phi[kMaxKrylov];
+    double phis[4][kMaxKrylov];    // phi of every stage (kept for the reverse step)
     double gcoef[kMaxKrylov + 1];  // host-provided coefficients (GMRES update)
 };
 

@@ -212,6 +212,7 @@ __device__ __forceinline__ T tree_partials(const T *__restrict__ p, int P, T *sh
 
 __device__ __forceinline__ size_t lane_e0() { return ((size_t)blockIdx.x * RT + threadIdx.x) * EPL; }
 
+#ifndef ROK_LINALG_DEVICE_ONLY
 // partials[b] = <a0, b0> and partials[P + b] = <a1, b1> (if a1) over CTA b's range
 __global__ void __launch_bounds__(RT) dot2_kernel(const double *__restrict__ a0, const double *__restrict__ b0,
                                                   const double *__restrict__ a1, const double *__restrict__ b1,
@@ -664,6 +665,7 @@ __device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, co
             st->lam[stage][i] = x[i];
             st->cvec[stage][i] = x[i] - h * phi[i];
             st->phi[i] = phi[i];
+            st->phis[stage][i] = phi[i];
             ok = ok && isfinite(x[i]);
         }
         if (!ok) st->status |= kStatusNonfinite;
@@ -1197,6 +1199,8 @@ static cudaError_t sum_sqrt(const double *pin, int P, double *dst, cudaStream_t 
 
 const LinalgOps ops = {dot2, mgs, normalize, multidot, stage_solve, lu, stage_vec, axpy_n, basis_combine, eps,
                        sum_sqrt, arnoldi_column, arnoldi_column_ctas, first_vector};
+
+#endif  // ROK_LINALG_DEVICE_ONLY
 
 }  // namespace ROK_NS
 }  // namespace rok

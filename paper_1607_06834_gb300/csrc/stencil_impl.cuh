@@ -8,6 +8,9 @@
 // build therefore produces the IEEE result of that order, which is the order
 // of a plain CPU evaluation of the same formulas.
 //
+// With ROK_STENCIL_DEVICE_ONLY defined, only the device functions (MUSCL,
+// Roe flux, primitives) are compiled, for reuse by the adjoint kernels.
+//
 // Tile pipeline (the kernel is FP64-ALU bound on GB300, so the design
 // minimises FP64 work: primitives once per loaded cell, each face once):
 //   1. load the (TX+4) x (TY+4) cells of the tile and its 2-cell halo, form the
@@ -294,6 +297,7 @@ __device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd]
     s2 = io.s2_dev ? io.s2 * *at_bytes(io.s2_dev, sb) : io.s2;
 }
 
+#ifndef ROK_STENCIL_DEVICE_ONLY
 // ============================ uniform periodic grid ============================
 // One TX x TY tile with lower-left cell (i0, j0) of an nx x ny periodic grid.
 // Batches pass the instance's first entry `off` in the flat vectors and the
@@ -742,6 +746,8 @@ cudaError_t launch_curv(const StencilConsts &c, const CurvGeom &g, const Stencil
         return dual ? launch_curv_t<true, true, Dual>(c, g, io, s) : launch_curv_t<true, true, double>(c, g, io, s);
     return dual ? launch_curv_t<true, false, Dual>(c, g, io, s) : launch_curv_t<true, false, double>(c, g, io, s);
 }
+
+#endif  // ROK_STENCIL_DEVICE_ONLY
 
 }  // namespace ROK_NS
 }  // namespace rok

@@ -100,6 +100,8 @@ _sig = {
     'rok_set_stencil_timing': (ctypes.c_int, [_vp, ctypes.c_int]),
     'rok_status_string': (ctypes.c_char_p, [ctypes.c_int]),
     'rok_fp64_fma_peak': (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    'rok_vjp': (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+    'rok_step_vjp': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     'rok_batch_init': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ProblemDesc), ctypes.c_int, _vp]),
     'rok_batch_destroy': (ctypes.c_int, [_vp]),
     'rok_batch_layout': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
@@ -289,6 +291,27 @@ def rok_get_counters(ctx, reset=False):
 
 def rok_set_stencil_timing(ctx, enable):
     _check(_lib.rok_set_stencil_timing(ctx.handle, int(bool(enable))), 'rok_set_stencil_timing')
+
+
+def rok_vjp(ctx, y, ubar, out=None, mubar=False):
+    """``rok_vjp``: J(y)^T ubar (and, with mubar=True, also ubar . df/dmu;
+    returns (ybar, mubar) then)."""
+    if out is None:
+        out = torch.empty_like(y)
+    mb = ctypes.c_double(0.0)
+    _check(_lib.rok_vjp(ctx.handle, _ptr(y), _ptr(ubar), _ptr(out), ctypes.byref(mb) if mubar else None), 'rok_vjp')
+    return (out, mb.value) if mubar else out
+
+
+def rok_step_vjp(ctx, y, h, M, ybar, out=None):
+    """``rok_step_vjp``: reverse of one ROK4 step from y_n = y; returns
+    (ybar_n, mubar of the step)."""
+    if out is None:
+        out = torch.empty_like(y)
+    mb = ctypes.c_double(0.0)
+    _check(_lib.rok_step_vjp(ctx.handle, _ptr(y), float(h), int(M), _ptr(ybar), _ptr(out), ctypes.byref(mb)),
+           'rok_step_vjp')
+    return out, mb.value
 
 
 class Batch:

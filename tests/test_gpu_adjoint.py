@@ -1,0 +1,136 @@
+"""GPU reverse mode against the oracle's discrete adjoint and against the
+complex-step derivative of the oracle's step map, through the C ABI.
+
+Bars: the residual VJP equals the oracle's (exact transposed Jacobian) to 1e-12
+of its size and satisfies <u, J v> = <J^T u, v> against the exact (dual-number)
+JVP at 256^2; one reverse ROK4 step and a multi-step gradient with
+checkpointing agree with the oracle to 1e-5 relative (both are exact
+derivatives of the same discrete map; the finite-difference quotients inside
+make them differ at the u / eps level)."""
+import numpy as np
+import pytest
+
+from oracle import adjoint as A
+from oracle import core
+from oracle import integrators as I
+from paper_1607_06834_gb300 import workloads as W
+from tests.gpu_common import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module')
+def rok():
+    from paper_1607_06834_gb300 import rok as r
+    return r
+
+
+def _cases():
+    p, y = W.taylor_green(40, reynolds=300.0)
+    p = W.FlowProblem(**{**p.__dict__, 'ny': 36, 'ly': p.ly * 36 / 40})
+    y = np.ascontiguousarray(y[:, :36, :] + 0.01 * W.random_smooth_state(p, seed=3))
+    out = [('ns-40x36', p, y)]
+    p, y = W.isentropic_vortex(33)
+    out.append(('euler-33', p, y))
+    return out
+
+
+@pytest.mark.parametrize('name,prob,y', _cases(), ids=[c[0] for c in _cases()])
+def test_residual_vjp_matches_oracle(rok, name, prob, y):
+    u = np.random.default_rng(5).standard_normal(y.shape)
+    ctx = rok.rok_init(prob, krylov_max=4, rounding=rok.ROK_ROUND_STRICT)
+    got, mub = rok.rok_vjp(ctx, dev(y), dev(u), mubar=True)
+    ref = A.residual_vjp(prob, y, u)
+    assert np.abs(host(got) - ref).max() <= 1e-12 * np.abs(ref).max()
+    mref = float(np.sum(u * A.residual_dmu(prob, y)))
+    assert abs(mub - mref) <= 1e-12 * np.sum(np.abs(u * A.residual_dmu(prob, y))), (mub, mref)
+
+
+def test_residual_vjp_adjoint_identity_full_size(rok):
+    # 256^2 Taylor-Green at Re = 1000 (the gradient workload): <u, J v> with J v
+    # by the dual-number kernel equals <J^T u, v> by the reverse kernels
+    prob, y = W.taylor_green(256, reynolds=1000.0)
+    ctx = rok.rok_init(prob, krylov_max=4)
+    rng = np.random.default_rng(8)
+    u, v = dev(rng.standard_normal(y.shape)), dev(rng.standard_normal(y.shape))
+    yd = dev(y)
+    jv = rok.rok_jvp(ctx, yd, v, mode=rok.ROK_JVP_EXACT)
+    jtu = rok.rok_vjp(ctx, yd, u)
+    lhs, rhs = float((u * jv).sum()), float((jtu * v).sum())
+    scale = float((u.abs() * rok.rok_jvp(ctx, yd, v.abs(), mode=rok.ROK_JVP_EXACT).abs()).sum())
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+
+
+@pytest.mark.parametrize('M', [0, 4, 10])
+def test_step_vjp_matches_oracle_adjoint(rok, M):
+    prob, y = W.taylor_green(24, reynolds=400.0)
+    y = np.ascontiguousarray(y + 0.01 * W.random_smooth_state(prob, seed=5))
+    h = I.dt_from_cfl(prob, y, 5.0)
+    c = np.random.default_rng(M + 1).standard_normal(y.shape)
+    ctx = rok.rok_init(prob, krylov_max=max(M, 1), rounding=rok.ROK_ROUND_STRICT)
+    yb, mub = rok.rok_step_vjp(ctx, dev(y), h, M, dev(c))
+    ref, mref = A.rok_step_vjp(prob, y, h, M, c)
+    yb = host(yb)
+    assert np.linalg.norm(yb - ref) <= 1e-6 * np.linalg.norm(ref), np.linalg.norm(yb - ref) / np.linalg.norm(ref)
+    assert abs(mub - mref) <= 1e-6 * abs(mref), (mub, mref)
+
+
+def test_step_vjp_euler_vortex(rok):
+    prob, y = W.isentropic_vortex(32)
+    h = I.dt_from_cfl(prob, y, 5.0)
+    c = np.random.default_rng(3).standard_normal(y.shape)
+    ctx = rok.rok_init(prob, krylov_max=8)
+    yb, mub = rok.rok_step_vjp(ctx, dev(y), h, 8, dev(c))
+    ref, _ = A.rok_step_vjp(prob, y, h, 8, c)
+    assert np.linalg.norm(host(yb) - ref) <= 1e-6 * np.linalg.norm(ref)
+    assert mub == 0.0
+
+
+def test_gradient_with_checkpoints_matches_oracle_complex_step(rok):
+    # J = kinetic energy after 6 ROK4 steps (M = 6), checkpoint every 2 steps:
+    # dJ/dy0 . d and dJ/dmu against the complex-step derivative of the oracle's
+    # own 6-step integration
+    import torch
+
+    from paper_1607_06834_gb300 import autograd as G
+    prob, y0 = W.taylor_green(20, reynolds=200.0)
+    y0 = np.ascontiguousarray(y0 + 0.01 * W.random_smooth_state(prob, seed=9))
+    h = I.dt_from_cfl(prob, y0, 4.0)
+    M, K = 6, 6
+    ctx = rok.rok_init(prob, krylov_max=M)
+    y = dev(y0).requires_grad_(True)
+    mu = torch.tensor(prob.mu, dtype=torch.float64, requires_grad=True)
+    J = G.kinetic_energy(G.integrate(ctx, y, mu, h, M, K, checkpoint_every=2))
+    J.backward()
+    g, gmu = host(y.grad), float(mu.grad)
+    d = np.random.default_rng(11).standard_normal(y0.shape)
+
+    def ke(yy):
+        return 0.5 * np.sum((yy[1] ** 2 + yy[2] ** 2) / yy[0])
+
+    sys_ = core.System(prob)
+    yc = y0 + 1e-30j * d
+    for _ in range(K):
+        yc = I.rok_step(sys_, yc, h, M)
+    cs = float(np.imag(ke(yc)) / 1e-30)
+    assert abs(np.sum(g * d) - cs) <= 1e-5 * abs(cs), (np.sum(g * d), cs)
+
+    class MuStep(core.System):
+        def f(self, yy):
+            return core.residual(prob, yy) + 1e-30j * A.residual_dmu(prob, yy)
+
+        def jvp(self, yy, v, f0, eps):
+            return (self.f(np.asarray(yy) + eps * np.asarray(v)) - f0) / eps
+    yc = y0.astype(complex)
+    for _ in range(K):
+        yc = I.rok_step(MuStep(prob), yc, h, M)
+    csm = float(np.imag(ke(yc)) / 1e-30)
+    assert abs(gmu - csm) <= 1e-5 * abs(csm), (gmu, csm)
+
+
+def test_vjp_unsupported_cases(rok):
+    p4, y4, _ = W.cylinder_ogrid(16, 32)
+    ctx = rok.rok_init(p4, krylov_max=4)
+    with pytest.raises(rok.RokError) as e:
+        rok.rok_vjp(ctx, dev(y4), dev(y4))
+    assert e.value.status == rok.ROK_ERR_UNSUPPORTED
