@@ -40,6 +40,12 @@ WORKLOAD = 'ns2d-taylor-green-512x512-Re1600-M0.1-rok4-M20-cfl8'
 FLOPS_RESIDUAL_NS = 390 + 10 + 20
 FLOPS_JVP_NS = FLOPS_RESIDUAL_NS + 8 + 8
 
+# DRAM bytes (read + write) of one FD-JVP launch of the Navier-Stokes stencil at
+# 512 x 512, from an ncu capture of this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum, cold L2): the three inputs y, v, f(y) are read once
+# (25.17 MB algorithmic); the 8.4 MB output stays in L2 within the launch.
+STENCIL_JVP_DRAM_BYTES_512 = 25263360 + 2048
+
 
 def _peaks():
     path = os.path.join(ROOT, 'MEASURED_PEAKS.json')
@@ -308,7 +314,10 @@ def run_ours(args):
                    'parallelism': 'replicas' if ws > 1 else 'single-gpu'},
         'roofline': {'bound': 'alu', 'kernel': 'residual/JVP stencil (cart_kernel<NS>)',
                      'achieved': round(achieved, 4), 'peak': round(fp64_roof, 4), 'unit': 'TFLOP/s',
-                     'frac': round(achieved / fp64_roof, 4), 'traffic': None,
+                     'frac': round(achieved / fp64_roof, 4),
+                     'traffic': STENCIL_JVP_DRAM_BYTES_512 if N_GRID == 512 else None,
+                     'traffic_unit': 'bytes per launch (ncu dram read+write)',
+                     'algorithmic_bytes_per_launch': cells * 128,
                      'peak_source': 'FP64 FMA roof = 152 SMs x 2 FMA/clk/SM x 2 flops x measured SM clock',
                      'fp64_fma_microbenchmark_tflops': round(fp64_peak, 4),
                      'flops_per_cell': {'residual': FLOPS_RESIDUAL_NS, 'jvp': FLOPS_JVP_NS},

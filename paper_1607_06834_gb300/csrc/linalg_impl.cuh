@@ -311,27 +311,39 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double *__restrict_
     store8(v, e0, n, x);
 }
 
+// 8 warp sums of one CTA added as the warp tree of cta_tree does
+__device__ __forceinline__ double warp8_tree(const double *w)
+{
+    return ((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]));
+}
+
 // pout[m * P + b] = <V_m, F> over CTA b's range, m < meff (basis entries read
-// exactly as binary64; products and tree in binary64)
+// exactly as binary64; products and tree in binary64).  The m CTA sums are
+// formed together: every warp keeps its lane-tree sums in shared memory and
+// one barrier later each sum is finished with the warp tree of chunk_sum.
 template <class T>
 __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__ F, const T *__restrict__ V,
                                                       size_t ldv, size_t n, double *__restrict__ pout, int P,
                                                       const StepState *st)
 {
     const int m = st->meff;
-    __shared__ double sh[10];
+    __shared__ double ws[kMaxKrylov][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t e0 = lane_e0();
     double f[EPL];
     load8(F, e0, n, f);
+#pragma unroll 4
     for (int i = 0; i < m; ++i) {
         T v[EPL];
         load8(V + (size_t)i * ldv, e0, n, v);
         double x[EPL];
 #pragma unroll
         for (int k = 0; k < EPL; ++k) x[k] = (double)v[k] * f[k];
-        double s = chunk_sum(x, sh);
-        if (threadIdx.x == 0) pout[(size_t)i * P + blockIdx.x] = s;
+        const double s = lane_tree(tree8(x));
+        if (lane == 0) ws[i][wid] = s;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += RT) pout[(size_t)i * P + blockIdx.x] = warp8_tree(ws[i]);
 }
 
 // ---- persistent Arnoldi column ------------------------------------------------
@@ -570,10 +582,15 @@ static cudaError_t first_vector(const double *F, void *V0, int fp32, size_t n, d
 // a sequential elimination.
 __device__ __forceinline__ void lu_body(StepState *st)
 {
+    // the factorisation runs in shared memory (one warp); the factors and the
+    // pivots are written back at the end
+    __shared__ double A[kMaxKrylov * kMaxKrylov];
+    __shared__ int piv[kMaxKrylov];
+    __shared__ int failed;
     const int m = st->meff;
     const double hg = st->hg;
     const int lane = threadIdx.x;
-    double *A = st->LU;
+    if (lane == 0) failed = 0;
     for (int idx = lane; idx < m * m; idx += 32) {
         int i = idx / m, j = idx % m;
         A[i * kMaxKrylov + j] = (i == j ? 1.0 : 0.0) - hg * st->H[i * kMaxKrylov + j];
@@ -598,12 +615,15 @@ __device__ __forceinline__ void lu_body(StepState *st)
                 A[k * kMaxKrylov + j] = A[bi * kMaxKrylov + j];
                 A[bi * kMaxKrylov + j] = t;
             }
-        if (lane == 0) st->piv[k] = bi;
+        if (lane == 0) piv[k] = bi;
         __syncwarp();
         const double d = A[k * kMaxKrylov + k];
         if (!(fabs(d) > 0.0) || !isfinite(d)) {
-            if (lane == 0) st->status |= kStatusSingular;
-            return;
+            if (lane == 0) {
+                st->status |= kStatusSingular;
+                failed = 1;
+            }
+            break;
         }
         for (int i = k + 1 + lane; i < m; i += 32) {
             double l = A[i * kMaxKrylov + k] / d;
@@ -612,6 +632,13 @@ __device__ __forceinline__ void lu_body(StepState *st)
         }
         __syncwarp();
     }
+    __syncwarp();
+    if (failed) return;
+    for (int idx = lane; idx < m * m; idx += 32) {
+        int i = idx / m, j = idx % m;
+        st->LU[i * kMaxKrylov + j] = A[i * kMaxKrylov + j];
+    }
+    for (int k = lane; k < m; k += 32) st->piv[k] = piv[k];
 }
 
 __global__ void lu_kernel(StepState *st) { lu_body(st); }
@@ -629,6 +656,8 @@ __device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, co
     const int m = st->meff;
     const double h = st->h;
     __shared__ double phi[kMaxKrylov], acc[kMaxKrylov], x[kMaxKrylov];
+    __shared__ double A[kMaxKrylov * kMaxKrylov];
+    __shared__ int piv[kMaxKrylov];
     for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
         double v = warp_tree_partials(pin + (size_t)i * istride, P);
         if ((threadIdx.x & 31) == 0) phi[i] = v;
@@ -637,19 +666,25 @@ __device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, co
         double a = 0.0;
         for (int j = 0; j < stage; ++j) a = a + gr.g[j] * st->lam[j][i];
         acc[i] = a;
+        piv[i] = st->piv[i];
+    }
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        int i = idx / m, j = idx % m;
+        A[i * kMaxKrylov + j] = st->LU[i * kMaxKrylov + j];
+    }
+    __syncthreads();
+    // rhs_i = h phi_i + h (H acc)_i, one row per thread, columns in order
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double t = 0.0;
+        for (int j = 0; j < m; ++j) t = t + st->H[i * kMaxKrylov + j] * acc[j];
+        x[i] = h * phi[i] + h * t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < m; ++i) {
-            double t = 0.0;
-            for (int j = 0; j < m; ++j) t = t + st->H[i * kMaxKrylov + j] * acc[j];
-            x[i] = h * phi[i] + h * t;
-        }
         for (int k = 0; k < m; ++k) {
-            int p = st->piv[k];
+            int p = piv[k];
             if (p != k) { double t = x[k]; x[k] = x[p]; x[p] = t; }
         }
-        const double *A = st->LU;
         for (int i = 0; i < m; ++i) {
             double t = x[i];
             for (int j = 0; j < i; ++j) t = t - A[i * kMaxKrylov + j] * x[j];
@@ -660,16 +695,17 @@ __device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, co
             for (int j = i + 1; j < m; ++j) t = t - A[i * kMaxKrylov + j] * x[j];
             x[i] = t / A[i * kMaxKrylov + i];
         }
-        bool ok = true;
-        for (int i = 0; i < m; ++i) {
-            st->lam[stage][i] = x[i];
-            st->cvec[stage][i] = x[i] - h * phi[i];
-            st->phi[i] = phi[i];
-            st->phis[stage][i] = phi[i];
-            ok = ok && isfinite(x[i]);
-        }
-        if (!ok) st->status |= kStatusNonfinite;
     }
+    __syncthreads();
+    int bad = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        st->lam[stage][i] = x[i];
+        st->cvec[stage][i] = x[i] - h * phi[i];
+        st->phi[i] = phi[i];
+        st->phis[stage][i] = phi[i];
+        bad |= !isfinite(x[i]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) st->status |= kStatusNonfinite;
 }
 
 __global__ void stage_solve_kernel(int stage, GamRow gr, const double *pin, int P, StepState *st)
@@ -942,24 +978,30 @@ __global__ void __launch_bounds__(RT) bnormalize_kernel(const double *__restrict
 }
 
 // pout[m * nchunks + c] = <V_m, F> over chunk c, m < meff of its instance
+// (sums formed together as in multidot_kernel)
 __global__ void __launch_bounds__(RT) bmultidot_kernel(const double *__restrict__ F, const double *__restrict__ V,
                                                        size_t ldv, double *__restrict__ pout, const BSeg sg)
 {
-    __shared__ double sh[10];
+    __shared__ double ws[kMaxKrylov][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = blockIdx.x; c < sg.nchunks; c += gridDim.x) {
         const ChunkRef r = chunk_ref(sg, c);
         const int m = sg.st[r.k].meff;
         double f[EPL];
         load8(F + r.off, r.e0, r.n, f);
+        __syncthreads();
+#pragma unroll 4
         for (int i = 0; i < m; ++i) {
             double v[EPL];
             load8(V + (size_t)i * ldv + r.off, r.e0, r.n, v);
             double x[EPL];
 #pragma unroll
             for (int k = 0; k < EPL; ++k) x[k] = v[k] * f[k];
-            const double s = chunk_sum(x, sh);
-            if (threadIdx.x == 0) pout[(size_t)i * sg.nchunks + c] = s;
+            const double s = lane_tree(tree8(x));
+            if (lane == 0) ws[i][wid] = s;
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += RT) pout[(size_t)i * sg.nchunks + c] = warp8_tree(ws[i]);
     }
 }
 

@@ -403,11 +403,14 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     }
 }
 
+// tile shape of the single-grid uniform kernel
+using CartShape = Shape32x8;
+
 template <bool VISC, bool SUTH, class S, int MINB>
-__global__ void __launch_bounds__(NT, MINB) cart_kernel(const StencilConsts C, const StencilIO io)
+__global__ void __launch_bounds__(CartShape::NT, MINB) cart_kernel(const StencilConsts C, const StencilIO io)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cart_tile<VISC, SUTH, S, Shape32x8>(C, io, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
+    cart_tile<VISC, SUTH, S, CartShape>(C, io, blockIdx.x * CartShape::TX, blockIdx.y * CartShape::TY, smem_raw);
 }
 
 // Many independent uniform periodic grids of one physics group in one launch:
@@ -657,7 +660,7 @@ template <bool V, bool SU, class S>
 static cudaError_t launch_cart_t(const StencilConsts &c, const StencilIO &io, cudaStream_t s)
 {
     constexpr int MINB = sizeof(S) == sizeof(double) ? 3 : 1;
-    const size_t smem = sizeof(Tile<S>) + sizeof(Faces<S>);
+    const size_t smem = sizeof(Tile<S, CartShape>) + sizeof(Faces<S, CartShape>);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(cart_kernel<V, SU, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -665,8 +668,8 @@ static cudaError_t launch_cart_t(const StencilConsts &c, const StencilIO &io, cu
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((c.nx + TX - 1) / TX, (c.ny + TY - 1) / TY);
-    cart_kernel<V, SU, S, MINB><<<grid, NT, smem, s>>>(c, io);
+    dim3 grid((c.nx + CartShape::TX - 1) / CartShape::TX, (c.ny + CartShape::TY - 1) / CartShape::TY);
+    cart_kernel<V, SU, S, MINB><<<grid, CartShape::NT, smem, s>>>(c, io);
     return cudaGetLastError();
 }
 

@@ -130,3 +130,37 @@ def test_rok_step_vjp_viscosity_matches_complex_step(M):
     yc = I.rok_step(MuStep(prob), y.astype(complex), h, M)
     cs = float(np.sum(c * yc.imag) / 1e-30)
     assert abs(mub - cs) <= 1e-8 * abs(cs), (mub, cs)
+
+
+def test_multi_step_derivative_conditioning():
+    # Evidence for the choice of gradient checks: the derivative of the FD-JVP
+    # ROK4 map over several steps is well conditioned on the Euler vortex but
+    # moves by O(1e-2 .. 1) under 1e-12 relative changes of the state on the
+    # low-Mach Taylor-Green state at CFL 4 (complex-step derivatives of the
+    # oracle's own map, no differencing of the map)
+    def ke(yy):
+        return 0.5 * np.sum((yy[1] ** 2 + yy[2] ** 2) / yy[0])
+
+    def deriv(prob, y0, h, M, K, d):
+        yc = y0 + 1e-30j * d
+        for _ in range(K):
+            yc = I.rok_step(core.System(prob), yc, h, M)
+        return float(np.imag(ke(yc)) / 1e-30)
+
+    rng = np.random.default_rng(11)
+    out = {}
+    for name in ('vortex', 'tgv'):
+        if name == 'vortex':
+            prob, y0 = W.isentropic_vortex(20)
+            cfl = 1.0
+        else:
+            prob, y0 = W.taylor_green(20, reynolds=200.0)
+            y0 = np.ascontiguousarray(y0 + 0.01 * W.random_smooth_state(prob, seed=9))
+            cfl = 4.0
+        h = I.dt_from_cfl(prob, y0, cfl)
+        d = rng.standard_normal(y0.shape)
+        a = deriv(prob, y0, h, 6, 4, d)
+        b = deriv(prob, y0 * (1 + 1e-12 * rng.standard_normal(y0.shape)), h, 6, 4, d)
+        out[name] = abs(a - b) / abs(a)
+    assert out['vortex'] < 1e-7, out
+    assert out['tgv'] > 1e-4, out
