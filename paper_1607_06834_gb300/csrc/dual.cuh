@@ -9,6 +9,7 @@ namespace rok {
 
 // keep the binary64 overloads visible next to the dual ones
 using ::fabs;
+using ::rsqrt;
 using ::sqrt;
 
 struct Dual {
@@ -40,6 +41,11 @@ __device__ __forceinline__ Dual sqrt(Dual a)
 {
     double s = ::sqrt(a.v);
     return {s, a.d / (2.0 * s)};
+}
+__device__ __forceinline__ Dual rsqrt(Dual a)
+{
+    double r = ::rsqrt(a.v);
+    return {r, -0.5 * (r * r * r) * a.d};
 }
 __device__ __forceinline__ Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
 

@@ -88,8 +88,16 @@ __device__ __forceinline__ RoeAvg<S> roe_avg(const S *L, const S *R, const Stenc
     a.Ht = (a.eL * sR + a.eR * sL) * den;
     a.kt = 0.5 * (a.ut * a.ut + a.vt * a.vt);
     S ct2 = C.gm1 * (a.Ht - a.kt);
+#ifdef ROK_STENCIL_RSQRT
+    // one reciprocal square root gives both c~ and 1/c~^2 (the FMA build only:
+    // other rounding than sqrt and division, fewer FP64 instructions)
+    S rc = rsqrt(ct2);
+    a.ct = ct2 * rc;
+    a.inv_c2 = rc * rc;
+#else
     a.ct = sqrt(ct2);
     a.inv_c2 = 1.0 / ct2;
+#endif
     return a;
 }
 
