@@ -502,6 +502,115 @@ def run_grad(args):
     print(json.dumps(out))
 
 
+def run_configs(args):
+    """--mode configs: one line per workload of the method's five configurations
+    (vortex 64^2, Taylor-Green 512^2, cylinder O-grid with the binary32 basis,
+    64-instance batch; the gradient workload has --mode grad): GPU time per
+    step by CUDA events, the CPU oracle on the same steps where it finishes in
+    seconds, and the difference from the oracle / exact solution."""
+    import torch
+
+    from oracle import core
+    from oracle import integrators as OI
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out = {'mode': 'configs', 'metric': METRIC, 'dtype': 'f64', 'data': 'synthetic', 'configs': {}}
+
+    def timed(ctx, y, h, M, steps):
+        # warm-up step on the buffer that is timed (a graph is captured per buffer)
+        yw = y.clone()
+        rok.rok_step(ctx, yw, h, M)
+        yw.copy_(y)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            rok.rok_step(ctx, yw, h, M)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    # 1. Euler vortex 64^2, M = 12, 10 steps at CFL 5, exact advected solution
+    prob, y0 = W.isentropic_vortex(64)
+    ctx = rok.rok_init(prob, krylov_max=12)
+    yd = rok.state_tensor(y0)
+    h = rok.rok_dt_from_cfl(ctx, yd, 5.0)
+    rok.rok_set_graph(ctx, True)
+    ms = timed(ctx, yd, h, 12, 10)
+    for _ in range(10):
+        rok.rok_step(ctx, yd, h, 12)
+    t0 = time.perf_counter()
+    yo = y0
+    for _ in range(10):
+        yo = OI.rok_step(core.System(prob), yo, h, 12)
+    cpu_s = (time.perf_counter() - t0) / 10
+    ys = rok.state_tensor(y0)
+    ctxs = rok.rok_init(prob, krylov_max=12, rounding=rok.ROK_ROUND_STRICT)
+    for _ in range(10):
+        rok.rok_step(ctxs, ys, h, 12)
+    yg = yd.cpu().numpy()
+    ex = W.vortex_exact(prob, 10 * h)
+    out['configs']['1-vortex64-M12-cfl5-10steps'] = {
+        'gpu_ms_per_step': round(ms, 4), 'cpu_oracle_ms_per_step': round(cpu_s * 1e3, 2),
+        'rel_l2_fast_vs_oracle': float(np.linalg.norm(yg - yo) / np.linalg.norm(yo)),
+        'strict_bitexact_vs_oracle': bool(np.array_equal(ys.cpu().numpy(), yo)),
+        'rel_l2_vs_exact_solution': float(np.linalg.norm(yg - ex) / np.linalg.norm(ex))}
+    # 2. Taylor-Green 512^2, M = 20, CFL 8: one step against the oracle
+    prob, y0 = W.taylor_green(512, reynolds=1600.0)
+    ctx = rok.rok_init(prob, krylov_max=20)
+    yd = rok.state_tensor(y0)
+    h = rok.rok_dt_from_cfl(ctx, yd, 8.0)
+    rok.rok_set_graph(ctx, True)
+    ms = timed(ctx, yd, h, 20, 10)
+    y1 = yd.clone()
+    rok.rok_step(ctx, y1, h, 20)
+    t0 = time.perf_counter()
+    yo = OI.rok_step(core.System(prob), y0, h, 20)
+    cpu_s = time.perf_counter() - t0
+    out['configs']['2-tgv512-M20-cfl8'] = {
+        'gpu_ms_per_step': round(ms, 4), 'cpu_oracle_ms_per_step': round(cpu_s * 1e3, 1),
+        'rel_l2_fast_vs_oracle_1step': float(np.linalg.norm(y1.cpu().numpy() - yo) / np.linalg.norm(yo))}
+    # 3. cylinder O-grid 256 x 512, M = 30, binary32 basis vs binary64, CFL 10
+    prob, y0, _ = W.cylinder_ogrid(256, 512)
+    c64 = rok.rok_init(prob, krylov_max=30)
+    c32 = rok.rok_init(prob, krylov_max=30, basis=rok.ROK_BASIS_FP32)
+    yd = rok.state_tensor(y0)
+    h = rok.rok_dt_from_cfl(c64, yd, 10.0)
+    for c in (c64, c32):
+        rok.rok_set_graph(c, True)
+    ms64 = timed(c64, yd, h, 30, 5)
+    ms32 = timed(c32, yd, h, 30, 5)
+    ya, yb = yd.clone(), yd.clone()
+    for _ in range(5):
+        rok.rok_step(c64, ya, h, 30)
+        rok.rok_step(c32, yb, h, 30)
+    t0 = time.perf_counter()
+    yo = OI.rok_step(core.System(prob), y0, h, 30)
+    cpu_s = time.perf_counter() - t0
+    y1 = yd.clone()
+    rok.rok_step(c64, y1, h, 30)
+    big = {}
+    for cfl in (100.0, 1000.0):
+        yy = yd.clone()
+        try:
+            rok.rok_step(c64, yy, rok.rok_dt_from_cfl(c64, yd, cfl), 30, info=True)
+            big[str(cfl)] = 'ok'
+        except rok.RokError as e:
+            big[str(cfl)] = rok.rok_status_string(e.status)
+    out['configs']['3-cylinder256x512-M30-cfl10'] = {
+        'gpu_ms_per_step_fp64_basis': round(ms64, 3), 'gpu_ms_per_step_fp32_basis': round(ms32, 3),
+        'fp32_speedup': round(ms64 / ms32, 3),
+        'rel_l2_fp32_vs_fp64_after_5_steps': float((ya - yb).norm() / ya.norm()),
+        'cpu_oracle_ms_per_step': round(cpu_s * 1e3, 1),
+        'rel_l2_fast_vs_oracle_1step': float(np.linalg.norm(y1.cpu().numpy() - yo) / np.linalg.norm(yo)),
+        'first_step_at_cfl': big}
+    # 4. the batch
+    out['configs']['4-batch64'] = batch_form(10)
+    print(json.dumps(out))
+
+
 def cpu_baseline(prob, y0, h, steps=8):
     """The CPU oracle, as it stands, on a bounded sample: `steps` ROK4 steps of the
     same workload, single-threaded."""
@@ -691,7 +800,7 @@ def main():
     ap.add_argument('--ref-factor', type=float, default=16.0)
     ap.add_argument('--esdirk-cap', type=float, default=150.0, help='skip ESDIRK runs estimated above this (s)')
     ap.add_argument('--cfls', default=None, help='comma-separated ROK/ESDIRK CFL numbers (study)')
-    ap.add_argument('--mode', default='step', choices=['step', 'stencil', 'batch', 'grad'])
+    ap.add_argument('--mode', default='step', choices=['step', 'stencil', 'batch', 'grad', 'configs'])
     ap.add_argument('--n', type=int, default=N_GRID)
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=30)
@@ -711,6 +820,9 @@ def main():
         return
     if args.mode == 'grad':
         run_grad(args)
+        return
+    if args.mode == 'configs':
+        run_configs(args)
         return
     if args.study == 'tte':
         run_tte(args)

@@ -177,6 +177,41 @@ rok_status rok_set_stencil_timing(rok_ctx *ctx, int enable);
 
 const char *rok_status_string(rok_status s);
 
+/* ---- Adaptive time stepping ---------------------------------------------
+ *
+ * Integrate y' = f(y) from 0 to T with step sizes chosen by an embedded error
+ * estimate (the paper compares its methods with adaptive steps, Sec. 4.3).
+ * err = sqrt(sum_i (e_i / sc_i)^2 / N), sc_i = atol + rtol max(|y_i|, |ynew_i|);
+ * a step is accepted when err <= 1; the next step is
+ * h min(facmax, max(facmin, safety err^(-1/(q+1)))), q the embedded order,
+ * never larger than h right after a rejection; a non-finite err (or a step that
+ * latches a non-finite residual) is rejected with facmin; the last step ends
+ * at T.  y: device, N float64, in place.  Synchronises every step.  Returns
+ * ROK_ERR_NOT_CONVERGED when max_steps attempts do not reach T. */
+typedef struct {
+    double atol, rtol;   /* error weights                                         */
+    double h0;           /* first trial step (> 0)                                */
+    double safety;       /* 0.9 is usual                                          */
+    double facmin;       /* smallest step ratio (0.2)                             */
+    double facmax;       /* largest step ratio (5)                                */
+    int max_steps;       /* accepted + rejected attempts                          */
+} rok_adapt_opts;
+
+typedef struct {
+    int accepted, rejected;
+    double t;            /* time reached                                          */
+    double h_next;       /* step the controller proposes next                     */
+    long long residual_evals;
+} rok_adapt_info;
+
+/* ROK4 steps (Krylov dimension M) with the embedded order-2 estimate
+ * e = sum_i (b_i - bhat_i) k_i (q = 2). */
+rok_status rok_integrate(rok_ctx *ctx, double *y, double T, int M, const rok_adapt_opts *opts,
+                         rok_adapt_info *info);
+
+/* Dormand-Prince 5(4) steps (comparator; q = 4, first same as last). */
+rok_status dopri5_integrate(rok_ctx *ctx, double *y, double T, const rok_adapt_opts *opts, rok_adapt_info *info);
+
 /* ---- Reverse mode: gradients of a final-time functional ------------------
  *
  * For a scalar functional of the state after K steps, the gradient with

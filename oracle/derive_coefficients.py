@@ -46,6 +46,22 @@ stage 3 fixes a_32; b_2, b_3 from sum b c = 1/2 and sum b c^2 = 1/3 (order
 3 then follows from stage order 2); g is the root in (0.4, 0.5) of the
 condition R(inf) = 0, computed symbolically below.
 
+Embedded ROK4 weights (error estimate for adaptive steps)
+--------------------------------------------------------
+bhat reuses the four stages: sum bhat = 1, sum bhat_i a_i = 1/2 and
+sum bhat_i beta'_i = 1/2 - g (order 2 for every Krylov dimension: the first
+holds the explicit part at M = 0, the second adds the gamma part inside the
+Krylov space), and bhat_4 = 0.  The order-3 and R(inf) = 0 conditions cannot
+be added: the main weights b satisfy all of them, so with four stages they
+would force bhat = b.  y - yhat = sum (b_i - bhat_i) k_i is then an O(h^3)
+local error estimate.
+
+DOPRI5 (comparator with an embedded error estimate)
+---------------------------------------------------
+The Dormand-Prince 5(4) pair (Dormand & Prince, J. Comput. Appl. Math. 6,
+1980), 7 stages, first-same-as-last, written here as exact rationals; the
+order conditions it satisfies are checked in the oracle's tests.
+
 Run ``python oracle/derive_coefficients.py`` to regenerate the table file.
 """
 import os
@@ -88,7 +104,14 @@ def rok4():
     gm = {(2, 1): g21, (3, 1): g31, (3, 2): g32, (4, 1): g41, (4, 2): g42, (4, 3): g43}
     alpha = [[al.get((i, j), mp.mpf(0)) for j in range(1, 5)] for i in range(1, 5)]
     gamma = [[gm.get((i, j), mp.mpf(0)) for j in range(1, 5)] for i in range(1, 5)]
-    return dict(gamma=g, alpha=alpha, gamma_offdiag=gamma, b=[b[i] for i in range(1, 5)])
+    # embedded weights: sum bhat = 1, sum bhat a = 1/2, sum bhat beta' = 1/2 - g, bhat_4 = 0
+    a = [sum(alpha[i][j] for j in range(4)) for i in range(4)]
+    bp = [sum(alpha[i][j] + gamma[i][j] for j in range(4)) for i in range(4)]
+    Mx = mp.matrix([[1, 1, 1, 1], a, bp, [0, 0, 0, 1]])
+    rhs = mp.matrix([1, mp.mpf(1) / 2, mp.mpf(1) / 2 - g, 0])
+    bhat = mp.lu_solve(Mx, rhs)
+    return dict(gamma=g, alpha=alpha, gamma_offdiag=gamma, b=[b[i] for i in range(1, 5)],
+                bhat=[mp.chop(bhat[k], tol=mp.mpf(10) ** -30) for k in range(4)])
 
 
 def esdirk3():
@@ -114,6 +137,20 @@ def esdirk3():
     return dict(gamma=g, A=Ar, b=Ar[3], c=[sum(Ar[i]) for i in range(4)], rinf_poly=str(poly.as_expr()))
 
 
+def dopri5():
+    F = sp.Rational
+    A = [[0, 0, 0, 0, 0, 0, 0],
+         [F(1, 5), 0, 0, 0, 0, 0, 0],
+         [F(3, 40), F(9, 40), 0, 0, 0, 0, 0],
+         [F(44, 45), F(-56, 15), F(32, 9), 0, 0, 0, 0],
+         [F(19372, 6561), F(-25360, 2187), F(64448, 6561), F(-212, 729), 0, 0, 0],
+         [F(9017, 3168), F(-355, 33), F(46732, 5247), F(49, 176), F(-5103, 18656), 0, 0],
+         [F(35, 384), 0, F(500, 1113), F(125, 192), F(-2187, 6784), F(11, 84), 0]]
+    b = [F(35, 384), 0, F(500, 1113), F(125, 192), F(-2187, 6784), F(11, 84), 0]
+    bhat = [F(5179, 57600), 0, F(7571, 16695), F(393, 640), F(-92097, 339200), F(187, 2100), F(1, 40)]
+    return dict(A=A, b=b, bhat=bhat, c=[sum(r) for r in A])
+
+
 def fmt(v):
     return repr(float(v))
 
@@ -121,6 +158,7 @@ def fmt(v):
 def main():
     r = rok4()
     e = esdirk3()
+    d = dopri5()
     lines = [
         '"""Method coefficient tables of the oracle (binary64).',
         '',
@@ -134,6 +172,8 @@ def main():
         'ROK4_GAMMA_OFFDIAG = [' + ', '.join('[' + ', '.join(fmt(v) for v in row) + ']'
                                            for row in r['gamma_offdiag']) + ']',
         'ROK4_B = [' + ', '.join(fmt(v) for v in r['b']) + ']',
+        '# embedded weights (order 2, bhat_4 = 0): error estimate sum (b - bhat)_i k_i',
+        'ROK4_BHAT = [' + ', '.join(fmt(v) for v in r['bhat']) + ']',
         '',
         '# classical RK4 (Sec. 2.1, Eq. RK with a, b below)',
         'RK4_A = [[0.0, 0.0, 0.0, 0.0], [0.5, 0.0, 0.0, 0.0], [0.0, 0.5, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0]]',
@@ -145,6 +185,16 @@ def main():
         'ESDIRK3_A = [' + ', '.join('[' + ', '.join(fmt(v) for v in row) + ']' for row in e['A']) + ']',
         'ESDIRK3_B = [' + ', '.join(fmt(v) for v in e['b']) + ']',
         'ESDIRK3_C = [' + ', '.join(fmt(v) for v in e['c']) + ']',
+        '',
+        '# DOPRI5: Dormand-Prince 5(4), first same as last (row 7 of A = b)',
+        'DOPRI5_A = [' + ', '.join('[' + ', '.join(fmt(v) for v in row) + ']' for row in d['A']) + ']',
+        'DOPRI5_B = [' + ', '.join(fmt(v) for v in d['b']) + ']',
+        'DOPRI5_BHAT = [' + ', '.join(fmt(v) for v in d['bhat']) + ']',
+        'DOPRI5_C = [' + ', '.join(fmt(v) for v in d['c']) + ']',
+        '# exact rationals of the same table (order-condition checks)',
+        'DOPRI5_A_EXACT = ' + repr([[str(v) for v in row] for row in d['A']]),
+        'DOPRI5_B_EXACT = ' + repr([str(v) for v in d['b']]),
+        'DOPRI5_BHAT_EXACT = ' + repr([str(v) for v in d['bhat']]),
         '',
     ]
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'coefficients.py')

@@ -170,7 +170,8 @@ def lu_solve(LU, piv, b):
     return np.array(x)
 
 
-def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=None, basis=np.float64):
+def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=None, basis=np.float64,
+             stages=None):
     """One step of the Rosenbrock-Krylov method, Eq. ROK (Sec. 2.3.3):
 
         F_i      = f(y_n + sum_{j<i} alpha_ij k_j)
@@ -184,7 +185,8 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
     V (lambda_i - h phi_i) + h F_i, the same vector grouped once; sums over the
     basis run in basis order.  With basis = np.float32 only the basis storage and
     Gram-Schmidt are binary32 (see arnoldi); phi, the stage solves and the stage
-    vectors read the basis exactly as binary64 and compute in binary64."""
+    vectors read the basis exactly as binary64 and compute in binary64.
+    `stages` (a list, optional) receives the stage vectors k_i."""
     g = C.ROK4_GAMMA if gamma is None else gamma
     al = np.array(C.ROK4_ALPHA if alpha is None else alpha)
     gm = np.array(C.ROK4_GAMMA_OFFDIAG if gamma_off is None else gamma_off)
@@ -231,7 +233,113 @@ def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=
         ynew = ynew + bb[i] * ks[i]
     if info is not None:
         info.update(m_eff=meff, eps=eps, H=H, V=V)
+    if stages is not None:
+        stages.extend(ks)
     return ynew.reshape(shape)
+
+
+# ---- embedded error estimates and adaptive steps ----------------------------------
+
+def wrms(e, y, ynew, atol, rtol):
+    """Weighted RMS norm of an error estimate (Hairer, Norsett & Wanner, Solving
+    ODEs I, Sec. II.4): sqrt(sum_i (e_i / sc_i)^2 / N), sc_i = atol + rtol
+    max(|y_i|, |ynew_i|), the sum pairwise."""
+    e, y, ynew = np.ravel(e), np.ravel(y), np.ravel(ynew)
+    sc = atol + rtol * np.maximum(np.abs(y), np.abs(ynew))
+    r = e / sc
+    return math.sqrt(pairwise_sum(r * r) / r.size)
+
+
+def rok_step_embedded(sys, y, h, M):
+    """ROK4 step (Eq. ROK) and its error estimate y_{n+1} - yhat =
+    sum_i (b_i - bhat_i) k_i, bhat the embedded order-2 weights."""
+    ks = []
+    ynew = rok_step(sys, y, h, M, stages=ks)
+    d = [C.ROK4_B[i] - C.ROK4_BHAT[i] for i in range(4)]
+    e = np.zeros(y.size)
+    for q in range(4):
+        e = e + d[q] * ks[q]
+    return ynew, e.reshape(y.shape)
+
+
+def dopri5_step(sys, y, h, k1=None):
+    """One Dormand-Prince 5(4) step: k_i = f(y + sum_j (h a_ij) k_j), y_{n+1} = the
+    7th stage state y + sum_j (h b_j) k_j, error estimate sum_j (h (b_j - bhat_j)) k_j;
+    k_7 = f(y_{n+1}) is returned for the next step (first same as last)."""
+    A, b, bh = C.DOPRI5_A, C.DOPRI5_B, C.DOPRI5_BHAT
+    ks = [np.asarray(sys.f(y)) if k1 is None else k1]
+    Y = y
+    for i in range(1, 7):
+        Y = y.copy()
+        for j in range(i):
+            if A[i][j] != 0.0:
+                Y = Y + (h * A[i][j]) * ks[j]
+        ks.append(np.asarray(sys.f(Y)))
+    e = np.zeros_like(y)
+    for j in range(7):
+        d = b[j] - bh[j]
+        if d != 0.0:
+            e = e + (h * d) * ks[j]
+    return Y, e, ks[6]
+
+
+def integrate_adaptive(try_step, y0, T, h0, q, atol, rtol, safety=0.9, facmin=0.2, facmax=5.0,
+                       max_steps=100000):
+    """Adaptive step-size control (Hairer, Norsett & Wanner I, Sec. II.4).
+    try_step(y, h) -> (ynew, e); a step is accepted when err = wrms(e) <= 1;
+    the next step is h min(facmax, max(facmin, safety err^(-1/(q+1)))), q the
+    order of the embedded solution, never larger than h right after a
+    rejection; a non-finite err rejects with facmin.  The last step ends at T.
+    Returns (y, dict(accepted, rejected, t, h))."""
+    t, h, y = 0.0, h0, y0
+    acc = rej = 0
+    after_reject = False
+    while T - t > 1e-12 * T and acc + rej < max_steps:
+        if t + h > T:
+            h = T - t
+        ynew, e = try_step(y, h)
+        err = wrms(e, y, ynew, atol, rtol)
+        if not math.isfinite(err):
+            fac = facmin
+        elif err == 0.0:
+            fac = facmax
+        else:
+            fac = min(facmax, max(facmin, safety * err ** (-1.0 / (q + 1))))
+        if math.isfinite(err) and err <= 1.0:
+            t = t + h
+            y = ynew
+            acc += 1
+            if after_reject:
+                fac = min(fac, 1.0)
+            after_reject = False
+        else:
+            rej += 1
+            after_reject = True
+            fac = min(fac, 1.0)
+        h = h * fac
+    return y, dict(accepted=acc, rejected=rej, t=t, h=h)
+
+
+def rok_integrate(sys, y0, T, h0, M, atol, rtol, **kw):
+    """Adaptive ROK4 with the embedded order-2 estimate (exponent 1/3)."""
+    return integrate_adaptive(lambda y, h: rok_step_embedded(sys, y, h, M), y0, T, h0, 2, atol, rtol, **kw)
+
+
+def dopri5_integrate(sys, y0, T, h0, atol, rtol, **kw):
+    """Adaptive DOPRI5 (embedded order 4, exponent 1/5).  First same as last:
+    the k_7 of a step is f(y_{n+1}), reused as k_1 when y_{n+1} is accepted; after
+    a rejection the k_1 of the retried step is reused."""
+    known = []   # (state, f(state)) of the last attempt's start and result
+
+    def try_step(y, h):
+        k1 = next((k for a, k in known if a is y), None)
+        if k1 is None:
+            k1 = np.asarray(sys.f(y))
+        ynew, e, k7 = dopri5_step(sys, y, h, k1)
+        known[:] = [(y, k1), (ynew, k7)]
+        return ynew, e
+
+    return integrate_adaptive(try_step, y0, T, h0, 4, atol, rtol, **kw)
 
 
 def rk_step(sys, y, h, A=None, b=None):

@@ -29,6 +29,7 @@ SOURCES = {
     'noalloc.cu': [],
     'batch.cu': [],
     'adjoint.cu': [],
+    'adaptive.cu': [],
 }
 
 

@@ -31,4 +31,23 @@ inline constexpr double kEsdA[4][4] = {{0.0, 0.0, 0.0, 0.0},
                             {0.18764102434672383, -0.595297473576955, 0.9717899277217721, 0.435866521508459}};
 inline constexpr double kEsdB[4] = {0.18764102434672383, -0.595297473576955, 0.9717899277217721, 0.435866521508459};
 
+// embedded ROK4 weights (order 2 for every Krylov dimension, bhat_4 = 0): the error
+// estimate of an adaptive step is sum_i (b_i - bhat_i) k_i
+inline constexpr double kRokBhat[4] = {0.0, 0.4947033707526526, 0.5052966292473474, 0.0};
+
+// DOPRI5 comparator: the Dormand-Prince 5(4) pair (J. Comput. Appl. Math. 6, 1980),
+// 7 stages, first same as last (row 7 of A = b)
+inline constexpr double kDp5A[7][7] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0 / 5.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 40.0, 9.0 / 40.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0.0, 0.0, 0.0, 0.0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0.0, 0.0, 0.0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0.0, 0.0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0}};
+inline constexpr double kDp5B[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0,
+                                    0.0};
+inline constexpr double kDp5Bhat[7] = {5179.0 / 57600.0,    0.0,  7571.0 / 16695.0, 393.0 / 640.0,
+                                       -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
+
 }  // namespace rok

@@ -80,6 +80,10 @@ struct LinalgOps {
     // v_1 = (T)F1 / ||(T)F1|| (T = binary64 or binary32); beta = 0: empty basis
     cudaError_t (*first_vector)(const double *F, void *V0, int fp32, size_t n, double *partials, int P,
                                 StepState *st, cudaStream_t s);
+    // partials[b] = sum over CTA b of (e_i / sc_i)^2, e = sum_q d_q k_q (count <= 8, in order),
+    // sc_i = atol + rtol max(|y_i|, |ynew_i|): the weighted RMS norm of an error estimate
+    cudaError_t (*err_sum)(const double *y, const double *ynew, const double *const *kv, const double *d, int count,
+                           double atol, double rtol, size_t n, double *partials, int P, cudaStream_t s);
 };
 
 // Segment table of a batch (device arrays): chunk c of a flat vector belongs to

@@ -1151,6 +1151,37 @@ static cudaError_t b_update(double *y, const double *const *kv, const double *b,
 const BatchOps bops = {b_dot2, b_eps, b_first_normalize, b_mgs, b_normalize, b_multidot, b_stage_solve, b_lu,
                        b_stage_vec, b_update};
 
+// ---- embedded error estimates ------------------------------------------------------
+struct ErrArgs {
+    const double *k[8];
+    double d[8];
+};
+
+// partials[b] = sum over CTA b's entries of (e_i / sc_i)^2 with
+// e_i = sum_q d_q k_q[i] (in order) and sc_i = atol + rtol max(|y_i|, |ynew_i|)
+__global__ void __launch_bounds__(RT) err_kernel(const double *__restrict__ y, const double *__restrict__ ynew,
+                                                 ErrArgs a, int count, double atol, double rtol, size_t n,
+                                                 double *__restrict__ partials)
+{
+    __shared__ double sh[10];
+    const size_t e0 = lane_e0();
+    double x[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+        const size_t e = e0 + k;
+        x[k] = 0.0;
+        if (e < n) {
+            double ev = 0.0;
+            for (int q = 0; q < count; ++q) ev = ev + a.d[q] * a.k[q][e];
+            const double sc = atol + rtol * fmax(fabs(y[e]), fabs(ynew[e]));
+            const double r = ev / sc;
+            x[k] = r * r;
+        }
+    }
+    const double s = chunk_sum(x, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // ---- launchers ----------------------------------------------------------------
 
 inline int blocks_for(size_t n) { return (int)((n + RB - 1) / RB); }
@@ -1239,8 +1270,21 @@ static cudaError_t sum_sqrt(const double *pin, int P, double *dst, cudaStream_t 
     return cudaGetLastError();
 }
 
+static cudaError_t err_sum(const double *y, const double *ynew, const double *const *kv, const double *d, int count,
+                           double atol, double rtol, size_t n, double *partials, int P, cudaStream_t s)
+{
+    if (count > 8) return cudaErrorInvalidValue;
+    ErrArgs a;
+    for (int q = 0; q < 8; ++q) {
+        a.k[q] = q < count ? kv[q] : nullptr;
+        a.d[q] = q < count ? d[q] : 0.0;
+    }
+    err_kernel<<<P, RT, 0, s>>>(y, ynew, a, count, atol, rtol, n, partials);
+    return cudaGetLastError();
+}
+
 const LinalgOps ops = {dot2, mgs, normalize, multidot, stage_solve, lu, stage_vec, axpy_n, basis_combine, eps,
-                       sum_sqrt, arnoldi_column, arnoldi_column_ctas, first_vector};
+                       sum_sqrt, arnoldi_column, arnoldi_column_ctas, first_vector, err_sum};
 
 #endif  // ROK_LINALG_DEVICE_ONLY
 

@@ -66,6 +66,20 @@ class Counters(ctypes.Structure):
                 ('stencil_ms', ctypes.c_double), ('stencil_timed', ctypes.c_longlong)]
 
 
+class AdaptOpts(ctypes.Structure):
+    _fields_ = [('atol', ctypes.c_double), ('rtol', ctypes.c_double), ('h0', ctypes.c_double),
+                ('safety', ctypes.c_double), ('facmin', ctypes.c_double), ('facmax', ctypes.c_double),
+                ('max_steps', ctypes.c_int)]
+
+
+class AdaptInfo(ctypes.Structure):
+    _fields_ = [('accepted', ctypes.c_int), ('rejected', ctypes.c_int), ('t', ctypes.c_double),
+                ('h_next', ctypes.c_double), ('residual_evals', ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 ROK_TILE_32x8, ROK_TILE_16x16, ROK_TILE_64x4 = 0, 1, 2
 CHUNKS_PER_CTA = (1, 2, 4, 8)
 
@@ -100,6 +114,10 @@ _sig = {
     'rok_set_stencil_timing': (ctypes.c_int, [_vp, ctypes.c_int]),
     'rok_status_string': (ctypes.c_char_p, [ctypes.c_int]),
     'rok_fp64_fma_peak': (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    'rok_integrate': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(AdaptOpts),
+                                     ctypes.POINTER(AdaptInfo)]),
+    'dopri5_integrate': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(AdaptOpts),
+                                        ctypes.POINTER(AdaptInfo)]),
     'rok_vjp': (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     'rok_step_vjp': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     'rok_batch_init': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ProblemDesc), ctypes.c_int, _vp]),
@@ -291,6 +309,28 @@ def rok_get_counters(ctx, reset=False):
 
 def rok_set_stencil_timing(ctx, enable):
     _check(_lib.rok_set_stencil_timing(ctx.handle, int(bool(enable))), 'rok_set_stencil_timing')
+
+
+def _adapt(atol, rtol, h0, safety, facmin, facmax, max_steps):
+    return AdaptOpts(float(atol), float(rtol), float(h0), float(safety), float(facmin), float(facmax), int(max_steps))
+
+
+def rok_integrate(ctx, y, T, M, atol, rtol, h0, safety=0.9, facmin=0.2, facmax=5.0, max_steps=100000):
+    """``rok_integrate``: adaptive ROK4 from 0 to T in place; returns the info dict."""
+    o = _adapt(atol, rtol, h0, safety, facmin, facmax, max_steps)
+    info = AdaptInfo()
+    _check(_lib.rok_integrate(ctx.handle, _ptr(y), float(T), int(M), ctypes.byref(o), ctypes.byref(info)),
+           'rok_integrate')
+    return info.as_dict()
+
+
+def dopri5_integrate(ctx, y, T, atol, rtol, h0, safety=0.9, facmin=0.2, facmax=5.0, max_steps=100000):
+    """``dopri5_integrate``: adaptive Dormand-Prince 5(4) from 0 to T in place."""
+    o = _adapt(atol, rtol, h0, safety, facmin, facmax, max_steps)
+    info = AdaptInfo()
+    _check(_lib.dopri5_integrate(ctx.handle, _ptr(y), float(T), ctypes.byref(o), ctypes.byref(info)),
+           'dopri5_integrate')
+    return info.as_dict()
 
 
 def rok_vjp(ctx, y, ubar, out=None, mubar=False):

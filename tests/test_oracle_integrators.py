@@ -344,3 +344,138 @@ def test_esdirk_order3_lorenz96():
     sl, errs = _slopes(lambda y, h: I.esdirk_step(sys, y, h, gmres_tol=1e-12, newton_tol=1e-13),
                        y0, ref, 0.3, [32, 64, 128])
     assert abs(sl[-1] - 3.0) < 0.2, (sl, errs)
+
+
+# ---- embedded estimates and adaptive steps -------------------------------------
+
+def _trees(order):
+    """All rooted trees with `order` nodes, as sorted tuples of child trees."""
+    if order == 1:
+        return [()]
+    out = set()
+
+    def parts(n, maxpart):
+        if n == 0:
+            yield []
+            return
+        for k in range(min(n, maxpart), 0, -1):
+            for rest in parts(n - k, k):
+                yield [k] + rest
+    for p in parts(order - 1, order - 1):
+        def combos(sizes):
+            if not sizes:
+                yield ()
+                return
+            for t in _trees(sizes[0]):
+                for rest in combos(sizes[1:]):
+                    yield (t,) + rest
+        for ch in combos(p):
+            out.add(tuple(sorted(ch)))
+    return sorted(out)
+
+
+def _butcher_condition(A, b, tree):
+    """sum_i b_i Phi_i(tree) - 1/gamma(tree) in exact rationals."""
+    from fractions import Fraction
+    s = len(b)
+
+    def phi(t):
+        v = [Fraction(1)] * s
+        for ch in t:
+            pc = phi(ch)
+            for i in range(s):
+                v[i] *= sum(A[i][j] * pc[j] for j in range(s))
+        return v
+
+    def size(t):
+        return 1 + sum(size(c) for c in t)
+
+    def gam(t):
+        g = size(t)
+        for c in t:
+            g *= gam(c)
+        return g
+    ph = phi(tree)
+    return sum(b[i] * ph[i] for i in range(s)) - Fraction(1, gam(tree))
+
+
+def test_dopri5_order_conditions_exact():
+    # Butcher's conditions for every rooted tree: order 5 for b (17 trees), order 4
+    # for bhat (8 trees), and the order-5 conditions are NOT all met by bhat
+    from fractions import Fraction
+    A = [[Fraction(x) for x in row] for row in C.DOPRI5_A_EXACT]
+    b = [Fraction(x) for x in C.DOPRI5_B_EXACT]
+    bh = [Fraction(x) for x in C.DOPRI5_BHAT_EXACT]
+    counts = [len(_trees(p)) for p in range(1, 6)]
+    assert counts == [1, 1, 2, 4, 9]
+    for p in range(1, 6):
+        for t in _trees(p):
+            assert _butcher_condition(A, b, t) == 0, (p, t)
+            if p <= 4:
+                assert _butcher_condition(A, bh, t) == 0, (p, t)
+    assert any(_butcher_condition(A, bh, t) != 0 for t in _trees(5))
+    # the binary64 table is the rounding of the exact one; first same as last
+    assert all(float(A[i][j]) == C.DOPRI5_A[i][j] for i in range(7) for j in range(7))
+    assert [float(x) for x in b] == list(C.DOPRI5_A[6]) == list(C.DOPRI5_B)
+
+
+def test_rok_embedded_weights_conditions():
+    al = np.array(C.ROK4_ALPHA)
+    gm = np.array(C.ROK4_GAMMA_OFFDIAG)
+    bh = np.array(C.ROK4_BHAT)
+    a = al.sum(axis=1)
+    bp = (al + gm).sum(axis=1)
+    assert abs(bh.sum() - 1.0) <= 1e-15
+    assert abs(bh @ a - 0.5) <= 1e-15
+    assert abs(bh @ bp - (0.5 - C.ROK4_GAMMA)) <= 1e-15
+    assert bh[3] == 0.0 and np.abs(bh - np.array(C.ROK4_B)).max() > 0.1
+
+
+def test_rok_embedded_estimate_is_third_order():
+    # the estimate sum (b - bhat)_i k_i behaves like C h^3 (order-2 embedded
+    # solution) on Lorenz-96 with M = 8 >= 3
+    prob, y0 = W.lorenz96(40)
+    sys_ = core.System(prob)
+    hs = [0.02, 0.01, 0.005]
+    es = [np.linalg.norm(I.rok_step_embedded(sys_, y0, h, 8)[1]) for h in hs]
+    slopes = [np.log(es[k] / es[k + 1]) / np.log(2.0) for k in range(2)]
+    assert all(2.8 < s < 3.3 for s in slopes), slopes
+
+
+def test_dopri5_step_orders():
+    # one step on Lorenz-96 against a fine RK4 reference: the local error falls
+    # like h^6, the estimate like h^5
+    prob, y0 = W.lorenz96(40)
+    sys_ = core.System(prob)
+    ref = {}
+    for h in (0.02, 0.01):
+        yr = y0.copy()
+        for _ in range(64):
+            yr = I.rk_step(sys_, yr, h / 64)
+        ref[h] = yr
+    err = {h: np.linalg.norm(I.dopri5_step(sys_, y0, h)[0] - ref[h]) for h in (0.02, 0.01)}
+    est = {h: np.linalg.norm(I.dopri5_step(sys_, y0, h)[1]) for h in (0.02, 0.01)}
+    assert 5.5 < np.log2(err[0.02] / err[0.01]) < 6.5, err
+    assert 4.6 < np.log2(est[0.02] / est[0.01]) < 5.4, est
+
+
+@pytest.mark.parametrize('method', ['rok', 'dopri5'])
+def test_adaptive_integration_tolerance_proportionality(method):
+    # tighter tolerances give proportionally smaller global errors and more steps
+    prob, y0 = W.lorenz96(40)
+    sys_ = core.System(prob)
+    T = 0.5
+    yr = y0.copy()
+    for _ in range(2000):
+        yr = I.rk_step(sys_, yr, T / 2000)
+    errs, steps = [], []
+    for tol in (1e-5, 1e-7, 1e-9):
+        if method == 'rok':
+            y, st = I.rok_integrate(sys_, y0, T, 0.01, 8, tol, tol)
+        else:
+            y, st = I.dopri5_integrate(sys_, y0, T, 0.01, tol, tol)
+        assert abs(st['t'] - T) <= 1e-12 * T
+        errs.append(np.linalg.norm(y - yr) / np.linalg.norm(yr))
+        steps.append(st['accepted'])
+    assert errs[0] > 10 * errs[1] and errs[1] > 10 * errs[2] and errs[2] < 1e-6, errs
+    assert steps[0] < steps[1] < steps[2], steps
