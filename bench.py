@@ -701,6 +701,60 @@ def _interp_time(points, target):
     return None
 
 
+def run_wp(args):
+    """Work-precision with adaptive steps (the paper's comparison, Sec. 4.3):
+    ROK4 with its embedded estimate vs DOPRI5 vs fixed-step RK4 at CFL 1 over
+    the same horizon as the time-to-error study, tolerances 1e-4, 1e-6, 1e-8
+    (atol = rtol = tol); GPU time by CUDA events, error against an RK4
+    reference at a 16x finer step."""
+    import torch
+
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    if args.case == 'tgv':
+        prob, y0 = W.taylor_green(args.n, mach=MACH, reynolds=RE)
+        krylov, base_cfl = KRYLOV, 8.0
+    else:
+        prob, y0, _ = W.cylinder_ogrid(256, 512)
+        krylov, base_cfl = 30, 1.0
+    ctx = rok.rok_init(prob, krylov_max=krylov)
+    yd0 = rok.state_tensor(y0)
+    dt1 = rok.rok_dt_from_cfl(ctx, yd0, 1.0)
+    T = args.horizon * dt1 * base_cfl
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        y = yd0.clone()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info = fn(y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return y, a.elapsed_time(b) / 1e3, info
+
+    nref = int(round(T / (dt1 / 16)))
+    yref, tref, _ = timed(lambda y: [rok.rk_step(ctx, y, T / nref) for _ in range(nref)])
+    nrm = float(yref.norm())
+    out = {'study': 'work-precision-adaptive', 'case': prob.name, 'T': T, 'dt_cfl1': dt1, 'reference_rk4_steps': nref,
+           'methods': {}}
+    nrk = int(round(T / dt1))
+    y, s, _ = timed(lambda y: [rok.rk_step(ctx, y, T / nrk) for _ in range(nrk)])
+    out['methods']['RK4 fixed CFL 1'] = [{'steps': nrk, 'gpu_s': s, 'rel_err': float((y - yref).norm()) / nrm}]
+    for tol in (1e-4, 1e-6, 1e-8):
+        for name, fn in (('ROK4 adaptive', lambda y: rok.rok_integrate(ctx, y, T, krylov, tol, tol, base_cfl * dt1)),
+                         ('DOPRI5 adaptive', lambda y: rok.dopri5_integrate(ctx, y, T, tol, tol, dt1))):
+            try:
+                y, s, info = timed(fn)
+                out['methods'].setdefault(name, []).append(
+                    {'tol': tol, 'accepted': info['accepted'], 'rejected': info['rejected'], 'gpu_s': s,
+                     'rel_err': float((y - yref).norm()) / nrm})
+            except rok.RokError as err:
+                out['methods'].setdefault(name, []).append({'tol': tol, 'failed': str(err)})
+    print(json.dumps(out))
+
+
 def run_tte(args):
     """Time to a fixed L2 error (the paper's work-precision measure, Sec. 4.3):
     ROK4 vs RK4 vs ESDIRK3 Newton-GMRES on one problem, fixed step sizes,
@@ -794,7 +848,7 @@ def run_tte(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument('--study', default=None, choices=[None, 'tte'])
+    ap.add_argument('--study', default=None, choices=[None, 'tte', 'wp'])
     ap.add_argument('--case', default='tgv', choices=['tgv', 'cylinder'])
     ap.add_argument('--horizon', type=float, default=50.0, help='T in units of the base-CFL step')
     ap.add_argument('--ref-factor', type=float, default=16.0)
@@ -826,6 +880,9 @@ def main():
         return
     if args.study == 'tte':
         run_tte(args)
+        return
+    if args.study == 'wp':
+        run_wp(args)
         return
     out = run_reference(args) if args.impl == 'reference' else run_ours(args)
     if out is not None:
