@@ -31,11 +31,12 @@
 namespace rok {
 namespace ROK_NS {
 
-// Tile shape: TXv x TYv cells per CTA, one thread per cell; the tile with its
-// 2-cell halo is EW x EH cells.
-template <int TXv, int TYv>
+// Tile shape: TXv x TYv cells per CTA, NTv threads (one or more cells per
+// thread); the tile with its 2-cell halo is EW x EH cells.
+template <int TXv, int TYv, int NTv = TXv * TYv>
 struct Shape {
-    static constexpr int TX = TXv, TY = TYv, NT = TXv * TYv, EW = TXv + 4, EH = TYv + 4;
+    static constexpr int TX = TXv, TY = TYv, NT = NTv, EW = TXv + 4, EH = TYv + 4;
+    static_assert((TXv * TYv) % NTv == 0, "whole cells per thread");
 };
 using Shape32x8 = Shape<32, 8>;
 
@@ -397,16 +398,19 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     }
     __syncthreads();
 
-    const int tx = tid % TX, ty = tid / TX;
-    const int gi = i0 + tx, gj = j0 + ty;
-    if (gi < nx && gj < ny) {
-        size_t c = off + (size_t)gj * nx + gi;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            S dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
-            S dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
-            S r = -(dX * C.rdx + dY * C.rdy);
-            epilogue_store(io, s1, s2, k * nc + c, result(r), sb);
+    for (int cell = tid; cell < TX * TY; cell += NT) {
+        const int tx = cell % TX, ty = cell / TX;
+        const int gi = i0 + tx, gj = j0 + ty;
+        if (gi < nx && gj < ny) {
+            size_t c = off + (size_t)gj * nx + gi;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                S dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
+                S dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
+                S r = -(dX * C.rdx + dY * C.rdy);
+                epilogue_store(io, s1, s2, k * nc + c, result(r), sb);
+            }
         }
     }
 }
