@@ -80,7 +80,11 @@ __device__ __forceinline__ RoeAvg<S> roe_avg(const S *L, const S *R, const Stenc
     S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
     a.eL = (pL * C.inv_gm1 + rL * (0.5 * (uL * uL + vL * vL))) + pL;
     a.eR = (pR * C.inv_gm1 + rR * (0.5 * (uR * uR + vR * vR))) + pR;
+#ifdef ROK_STENCIL_RSQRT
+    S sL = rL * rsqrt(rL), sR = rR * rsqrt(rR);
+#else
     S sL = sqrt(rL), sR = sqrt(rR);
+#endif
     a.rt = sL * sR;
     S den = 1.0 / (a.rt * (sL + sR));
     S wl = (rL * sR) * den, wr = (rR * sL) * den;
