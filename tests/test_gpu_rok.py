@@ -353,3 +353,19 @@ def test_exact_jvp_esdirk_and_lorenz_order(rok):
     rok.esdirk_step(ctx, y, h)
     yo = I.esdirk_step(core.ExactSystem(prob), y0, h)
     assert rel_l2(host(y), yo) <= 1e-8
+
+
+def test_cylinder_full_size_one_step_strict_bitexact(rok):
+    # the stiff case at its full size: Navier-Stokes cylinder O-grid 256 x 512,
+    # Sutherland, far field and no-slip wall, ROK4 M = 30 at CFL 10, binary64
+    # and binary32 basis, strict rounding: both bit-exact against the oracle
+    prob, y0, _ = W.cylinder_ogrid(256, 512)
+    h = I.dt_from_cfl(prob, y0, 10.0)
+    sys_ = core.System(prob)
+    for basis, npb in ((rok.ROK_BASIS_FP64, np.float64), (rok.ROK_BASIS_FP32, np.float32)):
+        ctx = rok.rok_init(prob, krylov_max=30, rounding=rok.ROK_ROUND_STRICT, basis=basis)
+        y = dev(y0)
+        info = rok.rok_step(ctx, y, h, 30, info=True)
+        assert info['m_eff'] == 30
+        yo = I.rok_step(sys_, y0, h, 30, basis=npb)
+        assert np.array_equal(host(y), yo), (basis, rel_l2(host(y), yo))
