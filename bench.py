@@ -203,6 +203,7 @@ def run_ours(args):
         c2 = rok.rok_get_counters(ctx, reset=True)
         rok.rok_set_stencil_timing(ctx, False)
         cnt['stencil_ms'], cnt['stencil_timed'] = c2['stencil_ms'], c2['stencil_timed']
+        rok.rok_set_graph(ctx, True)
     ms_t = torch.tensor([ms], dtype=torch.float64, device='cuda')
     if ws > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -311,6 +312,7 @@ def run_ours(args):
         'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
         'config': {'workload': WORKLOAD, 'cells': cells, 'krylov_m': KRYLOV, 'cfl': CFL, 'dt': h,
                    'rounding': args.rounding, 'l2': 'flushed between timed steps (256 MB write)',
+                   'launch': 'CUDA-graph replay per step' if args.graph else 'kernel by kernel',
                    'parallelism': 'replicas' if ws > 1 else 'single-gpu'},
         'roofline': {'bound': 'alu', 'kernel': 'residual/JVP stencil (cart_kernel<NS>)',
                      'achieved': round(achieved, 4), 'peak': round(fp64_roof, 4), 'unit': 'TFLOP/s',
@@ -861,7 +863,7 @@ def main():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--rounding', default='fast', choices=['fast', 'strict'])
-    ap.add_argument('--graph', type=int, default=0, help='replay each ROK4 step as a captured CUDA graph')
+    ap.add_argument('--graph', type=int, default=1, help='replay each ROK4 step as a captured CUDA graph (0: launch kernel by kernel)')
     ap.add_argument('--forms', type=int, default=1, help='also time the mixed-precision form')
     args = ap.parse_args()
     if args.warmup < 3:

@@ -385,6 +385,36 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks,
     return ok != 0;
 }
 
+// The sums of two 2048-entry chunks at once, each the same tree as chunk_sum:
+// after the lane trees, even lanes finish the first chunk's butterfly and odd
+// lanes the second's (one exchange and five additions per lane instead of
+// ten); then the two 8-warp trees together.  Results in thread 0 (first) and
+// thread 8 (second).  sh needs 16 entries.
+template <class T>
+__device__ __forceinline__ void chunk_sum2(const T (&xa)[EPL], const T (&xb)[EPL], T *sh, T &sa, T &sb)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const T a = tree8(xa), b = tree8(xb);
+    const bool odd = lane & 1;
+    const T recv = __shfl_xor_sync(0xffffffffu, odd ? a : b, 1);
+    T v = odd ? recv + b : a + recv;   // a_l + a_{l+1} on even lanes, b_{l-1} + b_l on odd lanes
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    __syncthreads();
+    if (lane < 2) sh[lane * 8 + wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        T u = lane < 16 ? sh[lane] : T(0);
+        u += __shfl_xor_sync(0xffffffffu, u, 1);
+        u += __shfl_xor_sync(0xffffffffu, u, 2);
+        u += __shfl_xor_sync(0xffffffffu, u, 4);
+        if (lane == 0) sa = u;
+        if (lane == 8) sb = u;
+    }
+}
+
 // One Arnoldi column in one cooperative launch.  T is the basis type: double
 // (plain path) or float (mixed path: basis storage and Gram-Schmidt in binary32;
 // the binary64 JVP result w is rounded to T on load; H is stored in binary64).
@@ -394,7 +424,8 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
                                                                T *partA, T *partB, GridBarrier *bar,
                                                                StepState *st, double brk_tol)
 {
-    __shared__ T sh[10];
+    static_assert(kColChunks == 2, "the CTA sums are formed for two chunks at once");
+    __shared__ T sh[16];
     __shared__ int act;
     if (threadIdx.x == 0) act = st->active;
     __syncthreads();
@@ -416,21 +447,26 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
             load8(V, e0[c], n, vn[c]);     // v_0
         }
     }
-    // pass 0 partials: <v_0, w> and <w, w>
+    // pass 0 partials: <v_0, w> and <w, w> (a missing second chunk sums zeros)
+    {
+        T x[kColChunks][EPL], y[kColChunks][EPL];
 #pragma unroll
-    for (int c = 0; c < kColChunks; ++c) {
-        if (!have[c]) continue;   // uniform per CTA
-        T x[EPL], y[EPL];
+        for (int c = 0; c < kColChunks; ++c)
 #pragma unroll
-        for (int k = 0; k < EPL; ++k) {
-            x[k] = vn[c][k] * wv[c][k];
-            y[k] = wv[c][k] * wv[c][k];
-        }
-        T s0 = chunk_sum(x, sh);
-        T s1 = chunk_sum(y, sh);
+            for (int k = 0; k < EPL; ++k) {
+                x[c][k] = have[c] ? vn[c][k] * wv[c][k] : T(0);
+                y[c][k] = have[c] ? wv[c][k] * wv[c][k] : T(0);
+            }
+        T s0a, s0b, s1a, s1b;
+        chunk_sum2(x[0], x[1], sh, s0a, s0b);
+        chunk_sum2(y[0], y[1], sh, s1a, s1b);
         if (threadIdx.x == 0) {
-            partA[blockIdx.x + c * G] = s0;
-            partA[P + blockIdx.x + c * G] = s1;
+            partA[blockIdx.x] = s0a;
+            partA[P + blockIdx.x] = s1a;
+        }
+        if (threadIdx.x == 8 && have[1]) {
+            partA[blockIdx.x + G] = s0b;
+            partA[P + blockIdx.x + G] = s1b;
         }
     }
     T *pin = partA, *pout = partB;
@@ -444,18 +480,24 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
             if (i == 0) st->wnorm0 = (double)wnorm0;
         }
         const T *vnext = i < j ? V + (size_t)(i + 1) * ldv : nullptr;
+        T x[kColChunks][EPL];
 #pragma unroll
         for (int c = 0; c < kColChunks; ++c) {
-            if (!have[c]) continue;
+            if (!have[c]) {   // uniform per CTA
+#pragma unroll
+                for (int k = 0; k < EPL; ++k) x[c][k] = T(0);
+                continue;
+            }
 #pragma unroll
             for (int k = 0; k < EPL; ++k) wv[c][k] = wv[c][k] - h * vn[c][k];
             if (vnext) load8(vnext, e0[c], n, vn[c]);
-            T x[EPL];
 #pragma unroll
-            for (int k = 0; k < EPL; ++k) x[k] = vnext ? vn[c][k] * wv[c][k] : wv[c][k] * wv[c][k];
-            T s = chunk_sum(x, sh);
-            if (threadIdx.x == 0) pout[blockIdx.x + c * G] = s;
+            for (int k = 0; k < EPL; ++k) x[c][k] = vnext ? vn[c][k] * wv[c][k] : wv[c][k] * wv[c][k];
         }
+        T sa, sb;
+        chunk_sum2(x[0], x[1], sh, sa, sb);
+        if (threadIdx.x == 0) pout[blockIdx.x] = sa;
+        if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
         if (!grid_barrier(bar, G, &st->status)) return;
         T *t = pin;
         pin = pout;
