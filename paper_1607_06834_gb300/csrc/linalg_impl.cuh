@@ -311,6 +311,35 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double *__restrict_
     store8(v, e0, n, x);
 }
 
+// Lane trees of 16 values at once by recursive halving across the lanes: at
+// level l (exchange with lane ^ 2^l) each lane keeps half of its remaining
+// values and adds the partner's copy of them, so every value's sum over the 32
+// lanes is the same aligned pairwise tree as lane_tree, for 16 additions per
+// lane instead of 80.  Lane l (and l ^ 16) ends with the sum of value
+// 8 b0 + 4 b1 + 2 b2 + b3, b_k the bits of l.
+template <class T>
+__device__ __forceinline__ T lane_tree16(T (&t)[16], int lane)
+{
+#pragma unroll
+    for (int lev = 0; lev < 4; ++lev) {
+        const int half = 8 >> lev;
+        const bool upper = (lane >> lev) & 1;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const T recv = __shfl_xor_sync(0xffffffffu, upper ? t[k] : t[k + half], 1 << lev);
+            t[k] = upper ? recv + t[k + half] : t[k] + recv;
+        }
+    }
+    T v = t[0];
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    return v;
+}
+
+__device__ __forceinline__ int lane_tree16_value(int lane)
+{
+    return ((lane & 1) << 3) | ((lane & 2) << 1) | ((lane & 4) >> 1) | ((lane & 8) >> 3);
+}
+
 // 8 warp sums of one CTA added as the warp tree of cta_tree does
 __device__ __forceinline__ double warp8_tree(const double *w)
 {
@@ -332,15 +361,23 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__
     const size_t e0 = lane_e0();
     double f[EPL];
     load8(F, e0, n, f);
-#pragma unroll 4
-    for (int i = 0; i < m; ++i) {
-        T v[EPL];
-        load8(V + (size_t)i * ldv, e0, n, v);
-        double x[EPL];
+    for (int g = 0; g < m; g += 16) {
+        double t[16];
 #pragma unroll
-        for (int k = 0; k < EPL; ++k) x[k] = (double)v[k] * f[k];
-        const double s = lane_tree(tree8(x));
-        if (lane == 0) ws[i][wid] = s;
+        for (int q = 0; q < 16; ++q) {
+            t[q] = 0.0;
+            if (g + q < m) {
+                T v[EPL];
+                load8(V + (size_t)(g + q) * ldv, e0, n, v);
+                double x[EPL];
+#pragma unroll
+                for (int k = 0; k < EPL; ++k) x[k] = (double)v[k] * f[k];
+                t[q] = tree8(x);
+            }
+        }
+        const double s = lane_tree16(t, lane);
+        const int q = lane_tree16_value(lane);
+        if (lane < 16 && g + q < m) ws[g + q][wid] = s;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += RT) pout[(size_t)i * P + blockIdx.x] = warp8_tree(ws[i]);
@@ -1032,15 +1069,23 @@ __global__ void __launch_bounds__(RT) bmultidot_kernel(const double *__restrict_
         double f[EPL];
         load8(F + r.off, r.e0, r.n, f);
         __syncthreads();
-#pragma unroll 4
-        for (int i = 0; i < m; ++i) {
-            double v[EPL];
-            load8(V + (size_t)i * ldv + r.off, r.e0, r.n, v);
-            double x[EPL];
+        for (int g = 0; g < m; g += 16) {
+            double t[16];
 #pragma unroll
-            for (int k = 0; k < EPL; ++k) x[k] = v[k] * f[k];
-            const double s = lane_tree(tree8(x));
-            if (lane == 0) ws[i][wid] = s;
+            for (int q = 0; q < 16; ++q) {
+                t[q] = 0.0;
+                if (g + q < m) {
+                    double v[EPL];
+                    load8(V + (size_t)(g + q) * ldv + r.off, r.e0, r.n, v);
+                    double x[EPL];
+#pragma unroll
+                    for (int k = 0; k < EPL; ++k) x[k] = v[k] * f[k];
+                    t[q] = tree8(x);
+                }
+            }
+            const double s = lane_tree16(t, lane);
+            const int q = lane_tree16_value(lane);
+            if (lane < 16 && g + q < m) ws[g + q][wid] = s;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < m; i += RT) pout[(size_t)i * sg.nchunks + c] = warp8_tree(ws[i]);
