@@ -64,6 +64,15 @@ __device__ __forceinline__ void muscl(S m2, S m1, S p1, S p2, double c_lo,
     wr = (p1 - c_lo * dr) - c_hi * dc;
 }
 
+// the same reconstruction from the three cell differences dl = m1 - m2,
+// dc = p1 - m1, dr = p2 - p1 (computed once per cell and shared by the faces)
+template <class S>
+__device__ __forceinline__ void muscl_d(S m1, S p1, S dl, S dc, S dr, double c_lo, double c_hi, S &wl, S &wr)
+{
+    wl = (m1 + c_lo * dl) + c_hi * dc;
+    wr = (p1 - c_lo * dr) - c_hi * dc;
+}
+
 // Roe-averaged quantities common to every face orientation.  e = rho H = E + p;
 // the sqrt(rho)-weighted averages use one reciprocal:
 //   wl = rL sR / (sL sR (sL + sR)),  H~ = (eL sR + eR sL) / (sL sR (sL + sR)).
@@ -208,6 +217,13 @@ struct Tile {
     S r[SH::EH][SH::EW], u[SH::EH][SH::EW], v[SH::EH][SH::EW], p[SH::EH][SH::EW], T[SH::EH][SH::EW],
         mu[SH::EH][SH::EW];
 };
+// differences of the four reconstructed primitives between a cell and its
+// lower neighbour along x (dx) and y (dy)
+template <class S, class SH = Shape32x8>
+struct Diffs {
+    S dx[4][SH::EH][SH::EW], dy[4][SH::EH][SH::EW];
+};
+
 template <class S, class SH = Shape32x8>
 struct Faces {
     S fx[4][SH::TY][SH::TX + 1];
@@ -323,6 +339,7 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     if (io.active && *at_bytes(io.active, sb) == 0) return;
     Tile<S, SH> &tl = *reinterpret_cast<Tile<S, SH> *>(smem_raw);
     Faces<S, SH> &fc = *reinterpret_cast<Faces<S, SH> *>(smem_raw + sizeof(Tile<S, SH>));
+    Diffs<S, SH> &df = *reinterpret_cast<Diffs<S, SH> *>(smem_raw + sizeof(Tile<S, SH>) + sizeof(Faces<S, SH>));
 
     const int nx = C.nx, ny = C.ny;
     const size_t nc = (size_t)nx * ny;
@@ -340,6 +357,16 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         store_prim<SUTH, S, SH>(tl, ly, lx, rho, mx, my, E, false, C);
     }
     __syncthreads();
+    // cell differences along x (needed for lx >= 1) and y (ly >= 1)
+    for (int idx = tid; idx < EW * EH; idx += NT) {
+        int lx = idx % EW, ly = idx / EW;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (lx >= 1) df.dx[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
+            if (ly >= 1) df.dy[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
+        }
+    }
+    __syncthreads();
 
     constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
     for (int f = tid; f < NFX; f += NT) {
@@ -348,8 +375,8 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl(pick(tl, k, y, xl - 1), pick(tl, k, y, xl), pick(tl, k, y, xr), pick(tl, k, y, xr + 1),
-                  C.c_lo, C.c_hi, WL[k], WR[k]);
+            muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y][xl], df.dx[k][y][xr], df.dx[k][y][xr + 1],
+                    C.c_lo, C.c_hi, WL[k], WR[k]);
         roe_x(WL, WR, C, F);
         if (VISC) {
             S ux = (tl.u[y][xr] - tl.u[y][xl]) * C.rdx;
@@ -377,8 +404,8 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl(pick(tl, k, yb - 1, x), pick(tl, k, yb, x), pick(tl, k, yt, x), pick(tl, k, yt + 1, x),
-                  C.c_lo, C.c_hi, WL[k], WR[k]);
+            muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x], df.dy[k][yt][x], df.dy[k][yt + 1][x],
+                    C.c_lo, C.c_hi, WL[k], WR[k]);
         roe_y(WL, WR, C, F);
         if (VISC) {
             S uy = (tl.u[yt][x] - tl.u[yb][x]) * C.rdy;
@@ -676,7 +703,7 @@ template <bool V, bool SU, class S>
 static cudaError_t launch_cart_t(const StencilConsts &c, const StencilIO &io, cudaStream_t s)
 {
     constexpr int MINB = sizeof(S) == sizeof(double) ? 3 : 1;
-    const size_t smem = sizeof(Tile<S, CartShape>) + sizeof(Faces<S, CartShape>);
+    const size_t smem = sizeof(Tile<S, CartShape>) + sizeof(Faces<S, CartShape>) + sizeof(Diffs<S, CartShape>);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(cart_kernel<V, SU, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -721,7 +748,7 @@ template <bool V, bool SU, class SH>
 static cudaError_t launch_cart_batch_t(const StencilConsts &c, const StencilIO &io, const BatchTiles &bt, int ntiles,
                                        cudaStream_t s)
 {
-    const size_t smem = sizeof(Tile<double, SH>) + sizeof(Faces<double, SH>);
+    const size_t smem = sizeof(Tile<double, SH>) + sizeof(Faces<double, SH>) + sizeof(Diffs<double, SH>);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(cart_batch_kernel<V, SU, SH, 3>,
