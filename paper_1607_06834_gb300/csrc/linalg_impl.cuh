@@ -495,8 +495,13 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
                 y[c][k] = have[c] ? wv[c][k] * wv[c][k] : T(0);
             }
         T s0a, s0b, s1a, s1b;
-        chunk_sum2(x[0], x[1], sh, s0a, s0b);
-        chunk_sum2(y[0], y[1], sh, s1a, s1b);
+        if (have[1]) {   // uniform per CTA
+            chunk_sum2(x[0], x[1], sh, s0a, s0b);
+            chunk_sum2(y[0], y[1], sh, s1a, s1b);
+        } else {
+            s0a = chunk_sum(x[0], sh);
+            s1a = chunk_sum(y[0], sh);
+        }
         if (threadIdx.x == 0) {
             partA[blockIdx.x] = s0a;
             partA[P + blockIdx.x] = s1a;
@@ -532,7 +537,8 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
             for (int k = 0; k < EPL; ++k) x[c][k] = vnext ? vn[c][k] * wv[c][k] : wv[c][k] * wv[c][k];
         }
         T sa, sb;
-        chunk_sum2(x[0], x[1], sh, sa, sb);
+        if (have[1]) chunk_sum2(x[0], x[1], sh, sa, sb);
+        else sa = chunk_sum(x[0], sh);
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
         if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
         if (!grid_barrier(bar, G, &st->status)) return;
