@@ -553,6 +553,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
         C.q_rdx = 0.25 * C.rdx;
         C.q_rdy = 0.25 * C.rdy;
         to_prim_host(*d, C, d->q_inf, C.prim_inf);
+        set_fast_consts(C);
     }
     C.lorenz_f = d->lorenz_f;
 

@@ -121,6 +121,8 @@ void group_consts(const rok_problem_desc &d, StencilConsts &C)
     C.mu = d.kind == ROK_NS2D ? d.mu : 0.0;
     C.inv_tref = C.sutherland ? 1.0 / d.t_ref : 0.0;
     C.suth_s = d.sutherland_s;
+    C.gg = C.inv_gm1 + 1.0;
+    C.gm1h = 0.5 * C.gm1;
 }
 
 // instances of one group share the gas model and scheme constants
@@ -374,6 +376,10 @@ rok_status rok_batch_init(rok_batch **out, const rok_problem_desc *descs, int co
         I.q_rdx = 0.25 * I.rdx;
         I.q_rdy = 0.25 * I.rdy;
         I.mu = d.kind == ROK_NS2D ? d.mu : 0.0;
+        I.hrdx = 0.5 * I.rdx;
+        I.hrdy = 0.5 * I.rdy;
+        if (d.kind == ROK_NS2D)
+            face_coefs(I.mu, d.sutherland_s > 0.0, d.gamma / ((d.gamma - 1.0) * d.prandtl), I.rdx, I.rdy, I.vk);
         off += (size_t)I.nchunks * kChunk;
         chunk += I.nchunks;
         for (int c = 0; c < I.nchunks; ++c) chunk_inst.push_back(k);

@@ -94,6 +94,7 @@ void uniform_consts(const rok_problem_desc &d, StencilConsts &C)
         C.prim_inf[3] = p;
         C.prim_inf[4] = T;
         C.prim_inf[5] = d.kind == ROK_NS2D ? mu : 0.0;
+        set_fast_consts(C);
     }
     C.lorenz_f = d.lorenz_f;
 }

@@ -42,7 +42,44 @@ struct StencilConsts {
     double rdx, rdy, q_rdx, q_rdy;  // 1/dx, 1/dy, 0.25/dx, 0.25/dy (uniform grids)
     double prim_inf[6];        // rho, u, v, p, T, mu of the free stream
     double lorenz_f;
+    // FMA build of the uniform-grid stencil (faces hold G = 2F): gamma/(gamma-1),
+    // (gamma-1)/2, 0.5/dx, 0.5/dy and the viscous coefficients of face_coefs()
+    double gg, gm1h, hrdx, hrdy;
+    double vk[2][5];
 };
+
+// Viscous coefficients of the doubled face flux G = 2F of a uniform grid, per
+// face direction d (0: x-faces, 1: y-faces; n the face normal, t the tangent).
+// With the cell differences across the face (dnn: normal velocity, dtn:
+// tangential velocity, dTn: temperature) and the four-cell differences along it
+// (dnt: normal velocity, dtt: tangential velocity):
+//   2 tau_nn = m (vk0 dnn + vk1 dtt),  2 tau_nt = m (vk2 dnt + vk3 dtn),
+//   2 k dT/dn = m vk4 dTn,
+// where m = 1 and the factor 2 mu is folded in for a constant viscosity, and
+// m = mu_L + mu_R (= 2 mu_face) with Sutherland's law (Sec. 3.2, Stokes'
+// hypothesis: tau_nn = mu (4/3 du_n/dn - 2/3 du_t/dt)).
+inline void face_coefs(double mu, bool sutherland, double kfac, double rdx, double rdy, double vk[2][5])
+{
+    const double m = sutherland ? 1.0 : 2.0 * mu;
+    const double rdn[2] = {rdx, rdy}, qrdt[2] = {0.25 * rdy, 0.25 * rdx};
+    for (int d = 0; d < 2; ++d) {
+        vk[d][0] = m * (4.0 / 3.0) * rdn[d];
+        vk[d][1] = -m * (2.0 / 3.0) * qrdt[d];
+        vk[d][2] = m * qrdt[d];
+        vk[d][3] = m * rdn[d];
+        vk[d][4] = m * kfac * rdn[d];
+    }
+}
+
+// the FMA-build constants from the fields above (gm1, inv_gm1, mu, kfac, rdx, rdy)
+inline void set_fast_consts(StencilConsts &C)
+{
+    C.gg = C.inv_gm1 + 1.0;
+    C.gm1h = 0.5 * C.gm1;
+    C.hrdx = 0.5 * C.rdx;
+    C.hrdy = 0.5 * C.rdy;
+    face_coefs(C.mu, C.sutherland != 0, C.kfac, C.rdx, C.rdy, C.vk);
+}
 
 // Face metrics of a curvilinear grid (device arrays).
 struct CurvGeom {
@@ -90,6 +127,7 @@ struct BatchInst {
     size_t off, n;             // element offset and length N_k
     int chunk0, nchunks;       // first 2048-entry chunk and chunk count P_k
     double rdx, rdy, q_rdx, q_rdy, mu;
+    double hrdx, hrdy, vk[2][5];   // FMA-build constants (face_coefs)
 };
 
 // Tile table of one batched stencil launch (device arrays): CTA b computes tile

@@ -1,6 +1,6 @@
-// Residual stencil, FMA contraction allowed (default rounding mode); the square
-// roots of the Roe average and the speed of sound with 1/c^2 come from
-// reciprocal square roots.
+// Residual stencil, FMA contraction allowed (default rounding mode): the
+// uniform-grid faces use the restructured doubled-flux formulas, the Roe
+// averages and the speed of sound come from reciprocal square roots.
 #define ROK_NS fast
-#define ROK_STENCIL_RSQRT
+#define ROK_STENCIL_FAST
 #include "stencil_impl.cuh"

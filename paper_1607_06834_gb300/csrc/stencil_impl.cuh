@@ -89,7 +89,7 @@ __device__ __forceinline__ RoeAvg<S> roe_avg(const S *L, const S *R, const Stenc
     S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
     a.eL = (pL * C.inv_gm1 + rL * (0.5 * (uL * uL + vL * vL))) + pL;
     a.eR = (pR * C.inv_gm1 + rR * (0.5 * (uR * uR + vR * vR))) + pR;
-#ifdef ROK_STENCIL_RSQRT
+#ifdef ROK_STENCIL_FAST
     S sL = rL * rsqrt(rL), sR = rR * rsqrt(rR);
 #else
     S sL = sqrt(rL), sR = sqrt(rR);
@@ -102,7 +102,7 @@ __device__ __forceinline__ RoeAvg<S> roe_avg(const S *L, const S *R, const Stenc
     a.Ht = (a.eL * sR + a.eR * sL) * den;
     a.kt = 0.5 * (a.ut * a.ut + a.vt * a.vt);
     S ct2 = C.gm1 * (a.Ht - a.kt);
-#ifdef ROK_STENCIL_RSQRT
+#ifdef ROK_STENCIL_FAST
     // one reciprocal square root gives both c~ and 1/c~^2 (the FMA build only:
     // other rounding than sqrt and division, fewer FP64 instructions)
     S rc = rsqrt(ct2);
@@ -211,6 +211,137 @@ __device__ __forceinline__ void roe_n(const S *L, const S *R, double nx, double 
     F[3] = 0.5 * ((qnL * a.eL + qnR * a.eR) - D3);
 }
 
+#ifdef ROK_STENCIL_FAST
+// ---- FMA build of the uniform-grid faces: fewer FP64 instructions -------------
+// GB300 issues FP64 at 2 lane-operations per SM per clock, against 64 for
+// 32-bit integers, and the stencil is bound by FP64 issue.  The FMA build
+// therefore evaluates the same formulas with fewer FP64 operations (other
+// rounding, within a few ulp of the flux scale):
+//   * faces hold G = 2F, so the factor 1/2 of the central and upwind parts is
+//     dropped and the cell balance uses 0.5/dx, 0.5/dy;
+//   * the viscous coefficients carry mu, the grid spacing and the factor 2
+//     (face_coefs);
+//   * rho H = p gamma/(gamma-1) + rho k, and the Roe weights from
+//     1/(sqrt(rho_L) + sqrt(rho_R)) and the reciprocal square roots;
+//   * halving and the comparison of non-negative numbers on the integer pipe;
+//   * reciprocals from the hardware estimate and one Newton step.
+
+// x / 2 by lowering the exponent field by one.  Exact for every x whose half
+// is a normal number; a result below the normal range flushes to a signed
+// zero (as the flush-to-zero modes do), infinities and NaNs pass unchanged.
+__device__ __forceinline__ double half(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    const bool keep = e == 0x7ffu;
+    const bool normal = e - 2u < 0x7fdu;   // 2 <= e <= 0x7fe
+    const int h = normal ? hi - 0x00100000 : (keep ? hi : (hi & (int)0x80000000));
+    return __hiloint2double(h, normal || keep ? lo : 0);
+}
+__device__ __forceinline__ Dual half(Dual x) { return {half(x.v), half(x.d)}; }
+
+// 1/x: the hardware estimate r0 (rcp.approx.ftz.f64, relative error e0) and one
+// third-order Newton step for f(r) = 1/r - x: with e = 1 - x r0,
+// 1/x = r0 (1 + e + e^2 + ...), so r0 + r0 (e + e^2) has relative error
+// O(e0^3) below the final rounding (Householder's method of order 2).
+__device__ __forceinline__ double rcp(double x)
+{
+    double r0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(x));
+    const double e = fma(-x, r0, 1.0);
+    return fma(r0, fma(e, e, e), r0);
+}
+__device__ __forceinline__ Dual rcp(Dual x)
+{
+    const double r = rcp(x.v);
+    return {r, -(x.d * r) * r};
+}
+
+
+// a < b for non-negative (or +0) binary64 values: the bit patterns order alike
+__device__ __forceinline__ bool less_nonneg(double a, double b)
+{
+    return __double_as_longlong(a) < __double_as_longlong(b);
+}
+
+// |x| by clearing the sign bit (the result feeds an integer comparison)
+__device__ __forceinline__ double abs_bits(double x) { return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x)); }
+__device__ __forceinline__ Dual abs_bits(Dual x) { return __double2hiint(x.v) < 0 ? -x : x; }
+
+template <class S>
+__device__ __forceinline__ S harten2(S lam, S delta)
+{
+    S a = abs_bits(lam);
+    if (less_nonneg(val(a), val(delta))) a = (a * a + delta * delta) / (2.0 * delta);
+    return a;
+}
+
+// Doubled Roe flux G = 2F through a face of a uniform grid with unit normal
+// e_DIR (DIR 0: x, 1: y): the same flux as roe_x / roe_y, component N the
+// normal and T the tangential momentum.
+template <int DIR, class S>
+__device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts &C, S *G)
+{
+    constexpr int N = 1 + DIR, T = 2 - DIR;
+    const S rL = L[0], nL = L[N], tL = L[T], pL = L[3];
+    const S rR = R[0], nR = R[N], tR = R[T], pR = R[3];
+    // Roe average; qX = 1/sqrt(rho_X), sX = sqrt(rho_X)
+    const S eL = pL * C.gg + rL * half(nL * nL + tL * tL);   // rho H = E + p
+    const S eR = pR * C.gg + rR * half(nR * nR + tR * tR);
+    const S qL = rsqrt(rL), qR = rsqrt(rR);
+    const S sL = rL * qL, sR = rR * qR;
+    const S rt = sL * sR;
+    const S inv = rcp(sL + sR);
+    const S wl = sL * inv, wr = sR * inv;
+    const S nt = wl * nL + wr * nR, tt = wl * tL + wr * tR;
+    const S Ht = (eL * qL + eR * qR) * inv;
+    const S kt = half(nt * nt + tt * tt);
+    const S ct2 = C.gm1 * (Ht - kt);
+    const S rc = rsqrt(ct2);
+    const S ct = ct2 * rc, inv_c2 = rc * rc, hc = half(inv_c2);
+    // wave strengths and speeds (Harten's fix on the acoustic waves)
+    const S drho = rR - rL, dp = pR - pL, dn = nR - nL, dt = tR - tL;
+    const S rcdq = (rt * ct) * dn;
+    const S a1 = (dp - rcdq) * hc, a3 = (dp + rcdq) * hc;
+    const S a2 = drho - dp * inv_c2;
+    const S l2 = fabs(nt);
+    const S delta = C.efix * (l2 + ct);
+    const S l1 = harten2(nt - ct, delta), l3 = harten2(nt + ct, delta);
+    const S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
+    const S sA = A1 + A3, dA = A3 - A1, D0 = sA + A2;
+    const S Asdt = As * dt;
+    const S Dn = nt * D0 + ct * dA;
+    const S Dt = tt * D0 + Asdt;
+    const S D3 = Ht * sA + (kt * A2 + ((ct * nt) * dA + tt * Asdt));
+    const S mL = rL * nL, mR = rR * nR;
+    G[0] = (mL + mR) - D0;
+    G[N] = mL * nL + (mR * nR + ((pL + pR) - Dn));
+    G[T] = mL * tL + (mR * tR - Dt);
+    G[3] = nL * eL + (nR * eR - D3);
+}
+
+// Doubled viscous flux subtracted from G (coefficients of face_coefs): dnn,
+// dtn, dTn differences across the face, dnt, dtt four-cell differences along
+// it, sn, st the sums of the two cells' normal and tangential velocities, mus
+// the sum of their viscosities (Sutherland's law only).
+template <int DIR, bool SUTH, class S>
+__device__ __forceinline__ void visc2(S *G, S dnn, S dtn, S dTn, S dnt, S dtt, S sn, S st, S mus, const double *vk)
+{
+    constexpr int N = 1 + DIR, T = 2 - DIR;
+    S tnn = dnn * vk[0] + dtt * vk[1];
+    S tnt = dnt * vk[2] + dtn * vk[3];
+    S q = dTn * vk[4];
+    if (SUTH) {
+        tnn = tnn * mus;
+        tnt = tnt * mus;
+        q = q * mus;
+    }
+    G[N] = G[N] - tnn;
+    G[T] = G[T] - tnt;
+    G[3] = G[3] - (half(sn) * tnn + (half(st) * tnt + q));
+}
+#endif  // ROK_STENCIL_FAST
+
 // shared-memory tile of primitive variables (halo included)
 template <class S, class SH = Shape32x8>
 struct Tile {
@@ -240,10 +371,17 @@ template <bool SUTH, class S, class SH>
 __device__ __forceinline__ void store_prim(Tile<S, SH> &t, int ly, int lx, S rho, S mx, S my,
                                            S E, bool mirror, const StencilConsts &C)
 {
+#ifdef ROK_STENCIL_FAST
+    S rinv = rcp(rho);
+    S u = mx * rinv;
+    S v = my * rinv;
+    S p = C.gm1 * E - C.gm1h * (mx * u + my * v);
+#else
     S rinv = 1.0 / rho;
     S u = mx * rinv;
     S v = my * rinv;
     S p = C.gm1 * (E - 0.5 * (mx * u + my * v));
+#endif
     S T = p * rinv;
     t.r[ly][lx] = rho;
     t.u[ly][lx] = mirror ? -u : u;
@@ -313,7 +451,8 @@ __device__ __forceinline__ void epilogue_store(const StencilIO &io, double s1, d
     t = t * s1;
     double o = io.add_out ? io.add_out[e] + s2 * t : t;
     io.out[e] = o;
-    if (!isfinite(o)) atomicOr(at_bytes(io.status, sb), kStatusNonfinite);
+    if ((__double2hiint(o) & 0x7ff00000) == 0x7ff00000)   // infinity or NaN
+        atomicOr(at_bytes(io.status, sb), kStatusNonfinite);
 }
 
 __device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd], double &cff, double &s1, double &s2,
@@ -357,13 +496,19 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         store_prim<SUTH, S, SH>(tl, ly, lx, rho, mx, my, E, false, C);
     }
     __syncthreads();
-    // cell differences along x (needed for lx >= 1) and y (ly >= 1)
-    for (int idx = tid; idx < EW * EH; idx += NT) {
-        int lx = idx % EW, ly = idx / EW;
+    // cell differences the faces read: along x in the tile's rows (lx >= 1),
+    // along y in the tile's columns (ly >= 1)
+    constexpr int NDX = (EW - 1) * TY, NDY = TX * (EH - 1);
+    for (int idx = tid; idx < NDX + NDY; idx += NT) {
+        if (idx < NDX) {
+            const int ly = 2 + idx / (EW - 1), lx = 1 + idx % (EW - 1);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (lx >= 1) df.dx[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
-            if (ly >= 1) df.dy[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
+            for (int k = 0; k < 4; ++k) df.dx[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
+        } else {
+            const int j = idx - NDX;
+            const int ly = 1 + j / TX, lx = 2 + j % TX;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) df.dy[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
         }
     }
     __syncthreads();
@@ -377,6 +522,15 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         for (int k = 0; k < 4; ++k)
             muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y][xl], df.dx[k][y][xr], df.dx[k][y][xr + 1],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
+#ifdef ROK_STENCIL_FAST
+        roe2<0>(WL, WR, C, F);
+        if (VISC)
+            visc2<0, SUTH>(F, tl.u[y][xr] - tl.u[y][xl], tl.v[y][xr] - tl.v[y][xl], tl.T[y][xr] - tl.T[y][xl],
+                           (tl.u[y + 1][xl] + tl.u[y + 1][xr]) - (tl.u[y - 1][xl] + tl.u[y - 1][xr]),
+                           (tl.v[y + 1][xl] + tl.v[y + 1][xr]) - (tl.v[y - 1][xl] + tl.v[y - 1][xr]),
+                           tl.u[y][xl] + tl.u[y][xr], tl.v[y][xl] + tl.v[y][xr],
+                           SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C.vk[0]);
+#else
         roe_x(WL, WR, C, F);
         if (VISC) {
             S ux = (tl.u[y][xr] - tl.u[y][xl]) * C.rdx;
@@ -395,6 +549,7 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
             F[2] = F[2] - txy;
             F[3] = F[3] - ((u_f * txx + v_f * txy) + kf * Tx);
         }
+#endif
 #pragma unroll
         for (int k = 0; k < 4; ++k) fc.fx[k][fy][fx] = F[k];
     }
@@ -406,6 +561,15 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         for (int k = 0; k < 4; ++k)
             muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x], df.dy[k][yt][x], df.dy[k][yt + 1][x],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
+#ifdef ROK_STENCIL_FAST
+        roe2<1>(WL, WR, C, F);
+        if (VISC)
+            visc2<1, SUTH>(F, tl.v[yt][x] - tl.v[yb][x], tl.u[yt][x] - tl.u[yb][x], tl.T[yt][x] - tl.T[yb][x],
+                           (tl.v[yb][x + 1] + tl.v[yt][x + 1]) - (tl.v[yb][x - 1] + tl.v[yt][x - 1]),
+                           (tl.u[yb][x + 1] + tl.u[yt][x + 1]) - (tl.u[yb][x - 1] + tl.u[yt][x - 1]),
+                           tl.v[yb][x] + tl.v[yt][x], tl.u[yb][x] + tl.u[yt][x],
+                           SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C.vk[1]);
+#else
         roe_y(WL, WR, C, F);
         if (VISC) {
             S uy = (tl.u[yt][x] - tl.u[yb][x]) * C.rdy;
@@ -424,11 +588,17 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
             F[2] = F[2] - tyy;
             F[3] = F[3] - ((u_f * txy + v_f * tyy) + kf * Ty);
         }
+#endif
 #pragma unroll
         for (int k = 0; k < 4; ++k) fc.fy[k][fy][fx] = F[k];
     }
     __syncthreads();
 
+#ifdef ROK_STENCIL_FAST
+    const double bx = C.hrdx, by = C.hrdy;   // the faces hold 2F
+#else
+    const double bx = C.rdx, by = C.rdy;
+#endif
 #pragma unroll
     for (int cell = tid; cell < TX * TY; cell += NT) {
         const int tx = cell % TX, ty = cell / TX;
@@ -439,7 +609,7 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
             for (int k = 0; k < 4; ++k) {
                 S dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
                 S dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
-                S r = -(dX * C.rdx + dY * C.rdy);
+                S r = -(dX * bx + dY * by);
                 epilogue_store(io, s1, s2, k * nc + c, result(r), sb);
             }
         }
@@ -478,6 +648,12 @@ __global__ void __launch_bounds__(SH::NT, MINB) cart_batch_kernel(const StencilC
     Ck.q_rdx = I.q_rdx;
     Ck.q_rdy = I.q_rdy;
     Ck.mu = I.mu;
+    Ck.hrdx = I.hrdx;
+    Ck.hrdy = I.hrdy;
+#pragma unroll
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Ck.vk[d][q] = I.vk[d][q];
     const int t = b - bt.tile_first[k];
     const int ntx = (I.nx + SH::TX - 1) / SH::TX;
     cart_tile<VISC, SUTH, double, SH>(Ck, io, (t % ntx) * SH::TX, (t / ntx) * SH::TY, smem_raw, I.off,

@@ -77,14 +77,33 @@ def test_step_vjp_matches_oracle_adjoint(rok, M):
     assert abs(mub - mref) <= 1e-5 * abs(mref), (mub, mref)
 
 
-def test_step_vjp_euler_vortex(rok):
+def _adjoint_self_sensitivity(prob, y, h, M, c):
+    """How far the oracle's own reverse step moves when every state entry moves
+    by one ulp: the FD quotients of the recomputed forward step re-round, as they
+    do when the FMA build evaluates the residual with other rounding."""
+    rng = np.random.default_rng(21)
+    yp = y + rng.choice([-1.0, 1.0], size=y.shape) * np.spacing(y)
+    ra, _ = A.rok_step_vjp(prob, y, h, M, c)
+    rb, _ = A.rok_step_vjp(prob, yp, h, M, c)
+    return np.linalg.norm(ra - rb) / np.linalg.norm(ra)
+
+
+@pytest.mark.parametrize('mode', ['strict', 'fast'])
+def test_step_vjp_euler_vortex(rok, mode):
+    # strict: the forward recompute is the oracle's step bit for bit, the bar is
+    # the 1e-5 of the reverse arithmetic; FMA build: the recomputed step carries
+    # the FD noise of its own residual rounding (Eq. matvecFD divides it by
+    # eps), bounded by 4 x the oracle's own change under one-ulp changes of the
+    # state (3.3e-5 here: the old 1e-5 bar held for the FMA build by chance)
     prob, y = W.isentropic_vortex(32)
     h = I.dt_from_cfl(prob, y, 5.0)
     c = np.random.default_rng(3).standard_normal(y.shape)
-    ctx = rok.rok_init(prob, krylov_max=8)
+    ctx = rok.rok_init(prob, krylov_max=8, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
     yb, mub = rok.rok_step_vjp(ctx, dev(y), h, 8, dev(c))
     ref, _ = A.rok_step_vjp(prob, y, h, 8, c)
-    assert np.linalg.norm(host(yb) - ref) <= 1e-5 * np.linalg.norm(ref)
+    err = np.linalg.norm(host(yb) - ref) / np.linalg.norm(ref)
+    bar = 1e-5 if mode == 'strict' else max(1e-5, 4 * _adjoint_self_sensitivity(prob, y, h, 8, c))
+    assert err <= bar, (err, bar)
     assert mub == 0.0
 
 
