@@ -444,15 +444,20 @@ __device__ __forceinline__ T *at_bytes(T *p, size_t sb)
 // ---- stage 3: balance + epilogue ---------------------------------------------
 // the launch output: t = (sub ? r - sub : r) * s1, out = add_out ? add_out + s2 t : t,
 // r the residual value (or the JVP tangent)
-__device__ __forceinline__ void epilogue_store(const StencilIO &io, double s1, double s2, size_t e, double r,
-                                               size_t sb = 0)
+// the part after the scaling by s1: out = add_out ? add_out + s2 t : t
+__device__ __forceinline__ void epilogue_finish(const StencilIO &io, double s2, size_t e, double t, size_t sb = 0)
 {
-    double t = io.sub ? (r - io.sub[e]) : r;
-    t = t * s1;
     double o = io.add_out ? io.add_out[e] + s2 * t : t;
     io.out[e] = o;
     if ((__double2hiint(o) & 0x7ff00000) == 0x7ff00000)   // infinity or NaN
         atomicOr(at_bytes(io.status, sb), kStatusNonfinite);
+}
+
+__device__ __forceinline__ void epilogue_store(const StencilIO &io, double s1, double s2, size_t e, double r,
+                                               size_t sb = 0)
+{
+    double t = io.sub ? (r - io.sub[e]) : r;
+    epilogue_finish(io, s2, e, t * s1, sb);
 }
 
 __device__ __forceinline__ void coefs(const StencilIO &io, double (&cf)[kMaxAdd], double &cff, double &s1, double &s2,
@@ -513,8 +518,13 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     }
     __syncthreads();
 
+    // one face per thread, in warp-sized batches with the x-face batches first:
+    // warp w takes batches w, w + NT/32, ...  Every batch has one orientation
+    // (a warp-uniform branch), and the partial x batch and the last y batch
+    // fall to different warps.
     constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-    for (int f = tid; f < NFX; f += NT) {
+    constexpr int BX = (NFX + 31) / 32, BY = (NFY + 31) / 32;
+    auto xface = [&](int f) {
         int fx = f % (TX + 1), fy = f / (TX + 1);
         int y = fy + 2, xl = fx + 1, xr = fx + 2;
         S WL[4], WR[4], F[4];
@@ -552,8 +562,8 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
 #endif
 #pragma unroll
         for (int k = 0; k < 4; ++k) fc.fx[k][fy][fx] = F[k];
-    }
-    for (int f = tid; f < NFY; f += NT) {
+    };
+    auto yface = [&](int f) {
         int fx = f % TX, fy = f / TX;
         int x = fx + 2, yb = fy + 1, yt = fy + 2;
         S WL[4], WR[4], F[4];
@@ -591,6 +601,16 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
 #endif
 #pragma unroll
         for (int k = 0; k < 4; ++k) fc.fy[k][fy][fx] = F[k];
+    };
+    for (int bt = tid >> 5; bt < BX + BY; bt += NT / 32) {
+        const int lane = tid & 31;
+        if (bt < BX) {
+            const int f = bt * 32 + lane;
+            if (f < NFX) xface(f);
+        } else {
+            const int f = (bt - BX) * 32 + lane;
+            if (f < NFY) yface(f);
+        }
     }
     __syncthreads();
 
@@ -609,6 +629,15 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
             for (int k = 0; k < 4; ++k) {
                 S dX = fc.fx[k][ty][tx + 1] - fc.fx[k][ty][tx];
                 S dY = fc.fy[k][ty + 1][tx] - fc.fy[k][ty][tx];
+#ifdef ROK_STENCIL_FAST
+                if constexpr (std::is_same<S, double>::value) {
+                    // r - sub = -(dX bx + (dY by + sub)): two FMAs
+                    const size_t e = k * nc + c;
+                    const double t = io.sub ? -(dX * bx + (dY * by + io.sub[e])) : -(dX * bx + dY * by);
+                    epilogue_finish(io, s2, e, t * s1, sb);
+                    continue;
+                }
+#endif
                 S r = -(dX * bx + dY * by);
                 epilogue_store(io, s1, s2, k * nc + c, result(r), sb);
             }
