@@ -658,12 +658,16 @@ def run_reference(args):
 
 def run_stencil_only(args):
     """Kernel-only mode (profiling): W + K FD-JVP stencil launches on an n x n
-    Taylor-Green state; prints the mean launch time."""
+    Taylor-Green state (or, with --case cylinder, the 256 x 512 O-grid);
+    prints the mean launch time."""
     import torch
 
     from paper_1607_06834_gb300 import rok
     from paper_1607_06834_gb300 import workloads as W
-    prob, y0 = W.taylor_green(args.n, mach=MACH, reynolds=RE)
+    if args.case == 'cylinder':
+        prob, y0, _ = W.cylinder_ogrid(256, 512)
+    else:
+        prob, y0 = W.taylor_green(args.n, mach=MACH, reynolds=RE)
     rounding = rok.ROK_ROUND_STRICT if args.rounding == 'strict' else rok.ROK_ROUND_FAST
     ctx = rok.rok_init(prob, krylov_max=1, rounding=rounding)
     y = rok.state_tensor(y0)
@@ -682,7 +686,7 @@ def run_stencil_only(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({'mode': 'stencil', 'n': args.n, 'rounding': args.rounding, 'ms_per_launch': ms,
+    print(json.dumps({'mode': 'stencil', 'case': args.case, 'n': args.n, 'rounding': args.rounding, 'ms_per_launch': ms,
                       'tflops_alg': prob.ncells * FLOPS_JVP_NS / (ms * 1e-3) / 1e12}))
 
 

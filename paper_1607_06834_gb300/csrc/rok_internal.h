@@ -42,10 +42,12 @@ struct StencilConsts {
     double rdx, rdy, q_rdx, q_rdy;  // 1/dx, 1/dy, 0.25/dx, 0.25/dy (uniform grids)
     double prim_inf[6];        // rho, u, v, p, T, mu of the free stream
     double lorenz_f;
-    // FMA build of the uniform-grid stencil (faces hold G = 2F): gamma/(gamma-1),
-    // (gamma-1)/2, 0.5/dx, 0.5/dy and the viscous coefficients of face_coefs()
+    // FMA build of the stencil (faces hold G = 2F): gamma/(gamma-1), (gamma-1)/2,
+    // 0.5/dx, 0.5/dy, the uniform-grid viscous coefficients of face_coefs() and
+    // the curvilinear ones (m 4/3, -m 2/3, m, m k with m as in face_coefs)
     double gg, gm1h, hrdx, hrdy;
     double vk[2][5];
+    double vc[4];
 };
 
 // Viscous coefficients of the doubled face flux G = 2F of a uniform grid, per
@@ -79,6 +81,11 @@ inline void set_fast_consts(StencilConsts &C)
     C.hrdx = 0.5 * C.rdx;
     C.hrdy = 0.5 * C.rdy;
     face_coefs(C.mu, C.sutherland != 0, C.kfac, C.rdx, C.rdy, C.vk);
+    const double m = C.sutherland ? 1.0 : 2.0 * C.mu;
+    C.vc[0] = m * (4.0 / 3.0);
+    C.vc[1] = -m * (2.0 / 3.0);
+    C.vc[2] = m;
+    C.vc[3] = m * C.kfac;
 }
 
 // Face metrics of a curvilinear grid (device arrays).

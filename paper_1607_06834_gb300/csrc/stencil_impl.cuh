@@ -240,6 +240,17 @@ __device__ __forceinline__ double half(double x)
 }
 __device__ __forceinline__ Dual half(Dual x) { return {half(x.v), half(x.d)}; }
 
+// x / 4 in the same way (exponent field lowered by two)
+__device__ __forceinline__ double quarter(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    const bool keep = e == 0x7ffu;
+    const bool normal = e - 3u < 0x7fcu;   // 3 <= e <= 0x7fe
+    const int h = normal ? hi - 0x00200000 : (keep ? hi : (hi & (int)0x80000000));
+    return __hiloint2double(h, normal || keep ? lo : 0);
+}
+
 // 1/x: the hardware estimate r0 (rcp.approx.ftz.f64, relative error e0) and one
 // third-order Newton step for f(r) = 1/r - x: with e = 1 - x r0,
 // 1/x = r0 (1 + e + e^2 + ...), so r0 + r0 (e + e^2) has relative error
@@ -339,6 +350,76 @@ __device__ __forceinline__ void visc2(S *G, S dnn, S dtn, S dTn, S dnt, S dtt, S
     G[N] = G[N] - tnn;
     G[T] = G[T] - tnt;
     G[3] = G[3] - (half(sn) * tnn + (half(st) * tnt + q));
+}
+// Doubled Roe flux G = 2F through a face with unit normal (nx, ny) (curvilinear
+// grids): the flux of roe_n.
+template <class S>
+__device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double ny, const StencilConsts &C, S *G)
+{
+    const S rL = L[0], uL = L[1], vL = L[2], pL = L[3];
+    const S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
+    const S qnL = uL * nx + vL * ny, qnR = uR * nx + vR * ny;
+    const S eL = pL * C.gg + rL * half(uL * uL + vL * vL);
+    const S eR = pR * C.gg + rR * half(uR * uR + vR * vR);
+    const S qL = rsqrt(rL), qR = rsqrt(rR);
+    const S sL = rL * qL, sR = rR * qR;
+    const S rt = sL * sR;
+    const S inv = rcp(sL + sR);
+    const S wl = sL * inv, wr = sR * inv;
+    const S ut = wl * uL + wr * uR, vt = wl * vL + wr * vR;
+    const S Ht = (eL * qL + eR * qR) * inv;
+    const S kt = half(ut * ut + vt * vt);
+    const S ct2 = C.gm1 * (Ht - kt);
+    const S rc = rsqrt(ct2);
+    const S ct = ct2 * rc, inv_c2 = rc * rc, hc = half(inv_c2);
+    const S qnt = ut * nx + vt * ny;
+    const S drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
+    const S rcdq = (rt * ct) * dqn;
+    const S a1 = (dp - rcdq) * hc, a3 = (dp + rcdq) * hc;
+    const S a2 = drho - dp * inv_c2;
+    const S l2 = fabs(qnt);
+    const S delta = C.efix * (l2 + ct);
+    const S l1 = harten2(qnt - ct, delta), l3 = harten2(qnt + ct, delta);
+    const S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
+    const S sA = A1 + A3, dA = A3 - A1, D0 = sA + A2;
+    const S cdA = ct * dA;
+    const S D1 = ut * D0 + (cdA * nx + As * (du - dqn * nx));
+    const S D2 = vt * D0 + (cdA * ny + As * (dv - dqn * ny));
+    const S D3 = Ht * sA + (kt * A2 + (qnt * cdA + As * ((ut * du + vt * dv) - qnt * dqn)));
+    const S mL = rL * qnL, mR = rR * qnR, pLR = pL + pR;
+    G[0] = (mL + mR) - D0;
+    G[1] = mL * uL + (mR * uR + (pLR * nx - D1));
+    G[2] = mL * vL + (mR * vR + (pLR * ny - D2));
+    G[3] = qnL * eL + (qnR * eR - D3);
+}
+
+// Doubled viscous flux of a curvilinear face subtracted from G.  The gradients
+// come from the difference across the face (dC*) and four times the difference
+// of the two vertex averages along it (dV*: the middle pair of cells cancels),
+// with the metric terms c0, c1q = c1 / 4, c2, c3q = c3 / 4; su, sv the sums of
+// the two cells' velocities, mus of their viscosities (Sutherland's law only).
+template <bool SUTH, class S>
+__device__ __forceinline__ void visc_n2(S *G, double nx, double ny, double c0, double c1q, double c2, double c3q,
+                                        S dCu, S dCv, S dCT, S dVu, S dVv, S dVT, S su, S sv, S mus,
+                                        const StencilConsts &C)
+{
+    const S ux = dCu * c0 + dVu * c1q, uy = dCu * c2 + dVu * c3q;
+    const S vx = dCv * c0 + dVv * c1q, vy = dCv * c2 + dVv * c3q;
+    const S Tx = dCT * c0 + dVT * c1q, Ty = dCT * c2 + dVT * c3q;
+    S txx = ux * C.vc[0] + vy * C.vc[1];
+    S tyy = vy * C.vc[0] + ux * C.vc[1];
+    S txy = (uy + vx) * C.vc[2];
+    S q = (Tx * nx + Ty * ny) * C.vc[3];
+    if (SUTH) {
+        txx = txx * mus;
+        tyy = tyy * mus;
+        txy = txy * mus;
+        q = q * mus;
+    }
+    const S tnx = txx * nx + txy * ny, tny = txy * nx + tyy * ny;
+    G[1] = G[1] - tnx;
+    G[2] = G[2] - tny;
+    G[3] = G[3] - (half(su) * tnx + (half(sv) * tny + q));
 }
 #endif  // ROK_STENCIL_FAST
 
@@ -700,6 +781,7 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Tile<S> &tl = *reinterpret_cast<Tile<S> *>(smem_raw);
     Faces<S> &fc = *reinterpret_cast<Faces<S> *>(smem_raw + sizeof(Tile<S>));
+    Diffs<S> &df = *reinterpret_cast<Diffs<S> *>(smem_raw + sizeof(Tile<S>) + sizeof(Faces<S>));
 
     const int nx = C.nx, ny = C.ny;
     const size_t nc = (size_t)nx * ny;
@@ -745,20 +827,49 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
         }
     }
     __syncthreads();
+    // the cell differences the faces' MUSCL reconstruction reads (as in cart_tile)
+    constexpr int NDX = (EW - 1) * TY, NDY = TX * (EH - 1);
+    for (int idx = tid; idx < NDX + NDY; idx += NT) {
+        if (idx < NDX) {
+            const int ly = 2 + idx / (EW - 1), lx = 1 + idx % (EW - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) df.dx[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
+        } else {
+            const int j = idx - NDX;
+            const int ly = 1 + j / TX, lx = 2 + j % TX;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) df.dy[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
+        }
+    }
+    __syncthreads();
 
+    // faces in warp-sized batches spread over the warps (as in cart_tile)
     constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-    for (int f = tid; f < NFX; f += NT) {
+    constexpr int BX = (NFX + 31) / 32, BY = (NFY + 31) / 32;
+    auto xface = [&](int f) {
         int fx = f % (TX + 1), fy = f / (TX + 1);
         int gi = i0 + fx, gj = j0 + fy;
-        if (gi > nx || gj >= ny) continue;
+        if (gi > nx || gj >= ny) return;
         size_t fi = (size_t)gj * (nx + 1) + gi;
         int y = fy + 2, xl = fx + 1, xr = fx + 2;
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl(pick(tl, k, y, xl - 1), pick(tl, k, y, xl), pick(tl, k, y, xr), pick(tl, k, y, xr + 1),
-                  C.c_lo, C.c_hi, WL[k], WR[k]);
+            muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y][xl], df.dx[k][y][xr], df.dx[k][y][xr + 1],
+                    C.c_lo, C.c_hi, WL[k], WR[k]);
         double nxf = G.in_x[fi], nyf = G.in_y[fi];
+#ifdef ROK_STENCIL_FAST
+        roe_n2(WL, WR, nxf, nyf, C, F);
+        if (VISC)
+            visc_n2<SUTH>(F, nxf, nyf, G.ic0[fi], quarter(G.ic1[fi]), G.ic2[fi], quarter(G.ic3[fi]),
+                          tl.u[y][xr] - tl.u[y][xl], tl.v[y][xr] - tl.v[y][xl], tl.T[y][xr] - tl.T[y][xl],
+                          (tl.u[y + 1][xl] + tl.u[y + 1][xr]) - (tl.u[y - 1][xl] + tl.u[y - 1][xr]),
+                          (tl.v[y + 1][xl] + tl.v[y + 1][xr]) - (tl.v[y - 1][xl] + tl.v[y - 1][xr]),
+                          (tl.T[y + 1][xl] + tl.T[y + 1][xr]) - (tl.T[y - 1][xl] + tl.T[y - 1][xr]),
+                          tl.u[y][xl] + tl.u[y][xr], tl.v[y][xl] + tl.v[y][xr],
+                          SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C);
+        const double len = half(G.il[fi]);   // the face holds 2F
+#else
         roe_n(WL, WR, nxf, nyf, C, F);
         if (VISC) {
             double c0 = G.ic0[fi], c1 = G.ic1[fi], c2 = G.ic2[fi], c3 = G.ic3[fi];
@@ -800,22 +911,35 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
             F[2] = F[2] - tny;
             F[3] = F[3] - ((u_f * tnx + v_f * tny) + kf * dTn);
         }
-        double len = G.il[fi];
+        const double len = G.il[fi];
+#endif
 #pragma unroll
         for (int k = 0; k < 4; ++k) fc.fx[k][fy][fx] = F[k] * len;
-    }
-    for (int f = tid; f < NFY; f += NT) {
+    };
+    auto yface = [&](int f) {
         int fx = f % TX, fy = f / TX;
         int gi = i0 + fx, gj = j0 + fy;
-        if (gi >= nx || gj > ny) continue;
+        if (gi >= nx || gj > ny) return;
         size_t fi = (size_t)gj * nx + gi;
         int x = fx + 2, yb = fy + 1, yt = fy + 2;
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl(pick(tl, k, yb - 1, x), pick(tl, k, yb, x), pick(tl, k, yt, x), pick(tl, k, yt + 1, x),
-                  C.c_lo, C.c_hi, WL[k], WR[k]);
+            muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x], df.dy[k][yt][x], df.dy[k][yt + 1][x],
+                    C.c_lo, C.c_hi, WL[k], WR[k]);
         double nxf = G.jn_x[fi], nyf = G.jn_y[fi];
+#ifdef ROK_STENCIL_FAST
+        roe_n2(WL, WR, nxf, nyf, C, F);
+        if (VISC)
+            visc_n2<SUTH>(F, nxf, nyf, G.jc0[fi], quarter(G.jc1[fi]), G.jc2[fi], quarter(G.jc3[fi]),
+                          tl.u[yt][x] - tl.u[yb][x], tl.v[yt][x] - tl.v[yb][x], tl.T[yt][x] - tl.T[yb][x],
+                          (tl.u[yb][x - 1] + tl.u[yt][x - 1]) - (tl.u[yb][x + 1] + tl.u[yt][x + 1]),
+                          (tl.v[yb][x - 1] + tl.v[yt][x - 1]) - (tl.v[yb][x + 1] + tl.v[yt][x + 1]),
+                          (tl.T[yb][x - 1] + tl.T[yt][x - 1]) - (tl.T[yb][x + 1] + tl.T[yt][x + 1]),
+                          tl.u[yb][x] + tl.u[yt][x], tl.v[yb][x] + tl.v[yt][x],
+                          SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C);
+        const double len = half(G.jl[fi]);   // the face holds 2F
+#else
         roe_n(WL, WR, nxf, nyf, C, F);
         if (VISC) {
             double c0 = G.jc0[fi], c1 = G.jc1[fi], c2 = G.jc2[fi], c3 = G.jc3[fi];
@@ -857,9 +981,20 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
             F[2] = F[2] - tny;
             F[3] = F[3] - ((u_f * tnx + v_f * tny) + kf * dTn);
         }
-        double len = G.jl[fi];
+        const double len = G.jl[fi];
+#endif
 #pragma unroll
         for (int k = 0; k < 4; ++k) fc.fy[k][fy][fx] = F[k] * len;
+    };
+    for (int bt = tid >> 5; bt < BX + BY; bt += NT / 32) {
+        const int lane = tid & 31;
+        if (bt < BX) {
+            const int f = bt * 32 + lane;
+            if (f < NFX) xface(f);
+        } else {
+            const int f = (bt - BX) * 32 + lane;
+            if (f < NFY) yface(f);
+        }
     }
     __syncthreads();
 
@@ -925,7 +1060,7 @@ template <bool V, bool SU, class S>
 static cudaError_t launch_curv_t(const StencilConsts &c, const CurvGeom &g, const StencilIO &io, cudaStream_t s)
 {
     constexpr int MINB = sizeof(S) == sizeof(double) ? 3 : 1;
-    const size_t smem = sizeof(Tile<S>) + sizeof(Faces<S>);
+    const size_t smem = sizeof(Tile<S>) + sizeof(Faces<S>) + sizeof(Diffs<S>);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(curv_kernel<V, SU, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
