@@ -142,6 +142,34 @@ __device__ __forceinline__ T chunk_sum(const T (&x)[EPL], T *sh)
     return cta_tree(lane_tree(tree8(x)), sh);
 }
 
+// The lane's part of a dot product, sum_k a_k b_k over its 8 entries (in T).
+// Strict build: the 8 products, then the aligned tree (the order of a plain
+// pairwise evaluation).  FMA build (ROK_LINALG_FMA_DOT): one chain of fused
+// multiply-adds in entry order, 8 FP64 operations instead of 11 (deterministic,
+// other rounding).
+template <class T, class U>
+__device__ __forceinline__ T lane_dot(const U (&a)[EPL], const T (&b)[EPL])
+{
+#ifdef ROK_LINALG_FMA_DOT
+    T s = (T)a[0] * b[0];
+#pragma unroll
+    for (int k = 1; k < EPL; ++k) s = (T)a[k] * b[k] + s;
+    return s;
+#else
+    T x[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) x[k] = (T)a[k] * b[k];
+    return tree8(x);
+#endif
+}
+
+// CTA sum from the lanes' parts v (lane butterfly, then the warp tree)
+template <class T>
+__device__ __forceinline__ T chunk_sumv(T v, T *sh)
+{
+    return cta_tree(lane_tree(v), sh);
+}
+
 // Aligned tree over the C consecutive leaves p[lo .. lo + C) (zero beyond P),
 // C a power of two: up to 32 leaves are loaded at once (independent loads) and
 // added level by level; longer runs use a carry stack over the leaves in order.
@@ -264,14 +292,7 @@ __global__ void __launch_bounds__(RT) mgs_kernel(double *__restrict__ w, const d
 #pragma unroll
     for (int k = 0; k < EPL; ++k) wv[k] = wv[k] - h * vp[k];
     store8(w, e0, n, wv);
-    if (vnext) {
-#pragma unroll
-        for (int k = 0; k < EPL; ++k) vn[k] = vn[k] * wv[k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < EPL; ++k) vn[k] = wv[k] * wv[k];
-    }
-    double s = chunk_sum(vn, sh);
+    double s = chunk_sumv(vnext ? lane_dot(vn, wv) : lane_dot(wv, wv), sh);
     if (threadIdx.x == 0) pout[blockIdx.x] = s;
 }
 
@@ -369,10 +390,7 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__
             if (g + q < m) {
                 T v[EPL];
                 load8(V + (size_t)(g + q) * ldv, e0, n, v);
-                double x[EPL];
-#pragma unroll
-                for (int k = 0; k < EPL; ++k) x[k] = (double)v[k] * f[k];
-                t[q] = tree8(x);
+                t[q] = lane_dot(v, f);
             }
         }
         const double s = lane_tree16(t, lane);
@@ -422,16 +440,15 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks,
     return ok != 0;
 }
 
-// The sums of two 2048-entry chunks at once, each the same tree as chunk_sum:
-// after the lane trees, even lanes finish the first chunk's butterfly and odd
-// lanes the second's (one exchange and five additions per lane instead of
-// ten); then the two 8-warp trees together.  Results in thread 0 (first) and
-// thread 8 (second).  sh needs 16 entries.
+// The sums of two 2048-entry chunks at once from the lanes' parts a and b
+// (lane_dot), each the same tree as chunk_sumv: even lanes finish the first
+// chunk's butterfly and odd lanes the second's (one exchange and five
+// additions per lane instead of ten); then the two 8-warp trees together.
+// Results in thread 0 (first) and thread 8 (second).  sh needs 16 entries.
 template <class T>
-__device__ __forceinline__ void chunk_sum2(const T (&xa)[EPL], const T (&xb)[EPL], T *sh, T &sa, T &sb)
+__device__ __forceinline__ void chunk_sum2v(const T a, const T b, T *sh, T &sa, T &sb)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const T a = tree8(xa), b = tree8(xb);
     const bool odd = lane & 1;
     const T recv = __shfl_xor_sync(0xffffffffu, odd ? a : b, 1);
     T v = odd ? recv + b : a + recv;   // a_l + a_{l+1} on even lanes, b_{l-1} + b_l on odd lanes
@@ -486,21 +503,19 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
     }
     // pass 0 partials: <v_0, w> and <w, w> (a missing second chunk sums zeros)
     {
-        T x[kColChunks][EPL], y[kColChunks][EPL];
+        T x[kColChunks], y[kColChunks];
 #pragma unroll
-        for (int c = 0; c < kColChunks; ++c)
-#pragma unroll
-            for (int k = 0; k < EPL; ++k) {
-                x[c][k] = have[c] ? vn[c][k] * wv[c][k] : T(0);
-                y[c][k] = have[c] ? wv[c][k] * wv[c][k] : T(0);
-            }
+        for (int c = 0; c < kColChunks; ++c) {
+            x[c] = have[c] ? lane_dot(vn[c], wv[c]) : T(0);
+            y[c] = have[c] ? lane_dot(wv[c], wv[c]) : T(0);
+        }
         T s0a, s0b, s1a, s1b;
         if (have[1]) {   // uniform per CTA
-            chunk_sum2(x[0], x[1], sh, s0a, s0b);
-            chunk_sum2(y[0], y[1], sh, s1a, s1b);
+            chunk_sum2v(x[0], x[1], sh, s0a, s0b);
+            chunk_sum2v(y[0], y[1], sh, s1a, s1b);
         } else {
-            s0a = chunk_sum(x[0], sh);
-            s1a = chunk_sum(y[0], sh);
+            s0a = chunk_sumv(x[0], sh);
+            s1a = chunk_sumv(y[0], sh);
         }
         if (threadIdx.x == 0) {
             partA[blockIdx.x] = s0a;
@@ -522,23 +537,21 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
             if (i == 0) st->wnorm0 = (double)wnorm0;
         }
         const T *vnext = i < j ? V + (size_t)(i + 1) * ldv : nullptr;
-        T x[kColChunks][EPL];
+        T x[kColChunks];
 #pragma unroll
         for (int c = 0; c < kColChunks; ++c) {
             if (!have[c]) {   // uniform per CTA
-#pragma unroll
-                for (int k = 0; k < EPL; ++k) x[c][k] = T(0);
+                x[c] = T(0);
                 continue;
             }
 #pragma unroll
             for (int k = 0; k < EPL; ++k) wv[c][k] = wv[c][k] - h * vn[c][k];
             if (vnext) load8(vnext, e0[c], n, vn[c]);
-#pragma unroll
-            for (int k = 0; k < EPL; ++k) x[c][k] = vnext ? vn[c][k] * wv[c][k] : wv[c][k] * wv[c][k];
+            x[c] = vnext ? lane_dot(vn[c], wv[c]) : lane_dot(wv[c], wv[c]);
         }
         T sa, sb;
-        if (have[1]) chunk_sum2(x[0], x[1], sh, sa, sb);
-        else sa = chunk_sum(x[0], sh);
+        if (have[1]) chunk_sum2v(x[0], x[1], sh, sa, sb);
+        else sa = chunk_sumv(x[0], sh);
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
         if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
         if (!grid_barrier(bar, G, &st->status)) return;
@@ -1019,14 +1032,7 @@ __global__ void __launch_bounds__(RT) bmgs_kernel(double *__restrict__ w, const 
 #pragma unroll
         for (int k = 0; k < EPL; ++k) wv[k] = wv[k] - h * vp[k];
         store8(w + r.off, r.e0, r.n, wv);
-        if (vnext) {
-#pragma unroll
-            for (int k = 0; k < EPL; ++k) vn[k] = vn[k] * wv[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < EPL; ++k) vn[k] = wv[k] * wv[k];
-        }
-        const double s = chunk_sum(vn, sh);
+        const double s = chunk_sumv(vnext ? lane_dot(vn, wv) : lane_dot(wv, wv), sh);
         if (threadIdx.x == 0) pout[c] = s;
     }
 }
@@ -1083,10 +1089,7 @@ __global__ void __launch_bounds__(RT) bmultidot_kernel(const double *__restrict_
                 if (g + q < m) {
                     double v[EPL];
                     load8(V + (size_t)(g + q) * ldv + r.off, r.e0, r.n, v);
-                    double x[EPL];
-#pragma unroll
-                    for (int k = 0; k < EPL; ++k) x[k] = v[k] * f[k];
-                    t[q] = tree8(x);
+                    t[q] = lane_dot(v, f);
                 }
             }
             const double s = lane_tree16(t, lane);
