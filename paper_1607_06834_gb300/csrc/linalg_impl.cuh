@@ -144,13 +144,13 @@ __device__ __forceinline__ T chunk_sum(const T (&x)[EPL], T *sh)
 
 // The lane's part of a dot product, sum_k a_k b_k over its 8 entries (in T).
 // Strict build: the 8 products, then the aligned tree (the order of a plain
-// pairwise evaluation).  FMA build (ROK_LINALG_FMA_DOT): one chain of fused
+// pairwise evaluation).  FMA build (ROK_LINALG_FAST): one chain of fused
 // multiply-adds in entry order, 8 FP64 operations instead of 11 (deterministic,
 // other rounding).
 template <class T, class U>
 __device__ __forceinline__ T lane_dot(const U (&a)[EPL], const T (&b)[EPL])
 {
-#ifdef ROK_LINALG_FMA_DOT
+#ifdef ROK_LINALG_FAST
     T s = (T)a[0] * b[0];
 #pragma unroll
     for (int k = 1; k < EPL; ++k) s = (T)a[k] * b[k] + s;
@@ -469,6 +469,15 @@ __device__ __forceinline__ void chunk_sum2v(const T a, const T b, T *sh, T &sa, 
     }
 }
 
+// Hint: fetch the 128-byte line holding this thread's entries of p (from e0)
+// into L2; one thread per line issues it.
+template <class T>
+__device__ __forceinline__ void prefetch_l2(const T *p, size_t e0, size_t n)
+{
+    constexpr int kThreadsPerLine = 128 / (EPL * (int)sizeof(T));
+    if (e0 < n && threadIdx.x % kThreadsPerLine == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + e0));
+}
+
 // One Arnoldi column in one cooperative launch.  T is the basis type: double
 // (plain path) or float (mixed path: basis storage and Gram-Schmidt in binary32;
 // the binary64 JVP result w is rounded to T on load; H is stored in binary64).
@@ -499,6 +508,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
 #pragma unroll
             for (int k = 0; k < EPL; ++k) wv[c][k] = (T)wd[k];
             load8(V, e0[c], n, vn[c]);     // v_0
+            if (j >= 1) prefetch_l2(V + ldv, e0[c], n);   // v_1, read after the first barrier
         }
     }
     // pass 0 partials: <v_0, w> and <w, w> (a missing second chunk sums zeros)
@@ -547,6 +557,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
 #pragma unroll
             for (int k = 0; k < EPL; ++k) wv[c][k] = wv[c][k] - h * vn[c][k];
             if (vnext) load8(vnext, e0[c], n, vn[c]);
+            if (i + 2 <= j) prefetch_l2(V + (size_t)(i + 2) * ldv, e0[c], n);   // the next pass's vector
             x[c] = vnext ? lane_dot(vn[c], wv[c]) : lane_dot(wv[c], wv[c]);
         }
         T sa, sb;
@@ -675,71 +686,86 @@ static cudaError_t first_vector(const double *F, void *V0, int fp32, size_t n, d
     return cudaGetLastError();
 }
 
-// One warp: LU with partial pivoting of L = I - h g H (first largest |pivot|),
-// row-major stride kMaxKrylov.  Each entry sees the same operation sequence as
-// a sequential elimination.
+constexpr int kLuThreads = 128;      // threads of the LU launch
+constexpr int kSolveThreads = 1024;  // threads of the stage-solve launch (one warp per projection)
+
+// LU with partial pivoting of L = I - h g H (first largest |pivot|), row-major
+// stride kMaxKrylov, by the whole CTA: warp 0 searches the pivot, then the row
+// multipliers and the trailing update are spread over the threads.  Each entry
+// sees the same operation sequence as a sequential elimination (one multiplier
+// division per row, one update per step), so the factors are those of the
+// plain loops.
 __device__ __forceinline__ void lu_body(StepState *st)
 {
-    // the factorisation runs in shared memory (one warp); the factors and the
-    // pivots are written back at the end
+    // the factorisation runs in shared memory; the factors and the pivots are
+    // written back at the end
     __shared__ double A[kMaxKrylov * kMaxKrylov];
     __shared__ int piv[kMaxKrylov];
-    __shared__ int failed;
+    __shared__ int failed, pk;
     const int m = st->meff;
     const double hg = st->hg;
-    const int lane = threadIdx.x;
-    if (lane == 0) failed = 0;
-    for (int idx = lane; idx < m * m; idx += 32) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    if (tid == 0) failed = 0;
+    for (int idx = tid; idx < m * m; idx += nt) {
         int i = idx / m, j = idx % m;
         A[i * kMaxKrylov + j] = (i == j ? 1.0 : 0.0) - hg * st->H[i * kMaxKrylov + j];
     }
-    __syncwarp();
+    __syncthreads();
     for (int k = 0; k < m; ++k) {
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + lane; i < m; i += 32) {
-            double a = fabs(A[i * kMaxKrylov + k]);
-            if (a > best) { best = a; bi = i; }
-        }
+        if (tid < 32) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + lane; i < m; i += 32) {
+                double a = fabs(A[i * kMaxKrylov + k]);
+                if (a > best) { best = a; bi = i; }
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                piv[k] = bi;
+                pk = bi;
+            }
         }
+        __syncthreads();
+        const int bi = pk;
         if (bi != k)
-            for (int j = lane; j < m; j += 32) {
+            for (int j = tid; j < m; j += nt) {
                 double t = A[k * kMaxKrylov + j];
                 A[k * kMaxKrylov + j] = A[bi * kMaxKrylov + j];
                 A[bi * kMaxKrylov + j] = t;
             }
-        if (lane == 0) piv[k] = bi;
-        __syncwarp();
+        __syncthreads();
         const double d = A[k * kMaxKrylov + k];
-        if (!(fabs(d) > 0.0) || !isfinite(d)) {
-            if (lane == 0) {
+        if (!(fabs(d) > 0.0) || !isfinite(d)) {   // the same value in every thread
+            if (tid == 0) {
                 st->status |= kStatusSingular;
                 failed = 1;
             }
             break;
         }
-        for (int i = k + 1 + lane; i < m; i += 32) {
-            double l = A[i * kMaxKrylov + k] / d;
-            A[i * kMaxKrylov + k] = l;
-            for (int j = k + 1; j < m; ++j) A[i * kMaxKrylov + j] = A[i * kMaxKrylov + j] - l * A[k * kMaxKrylov + j];
+        for (int i = k + 1 + tid; i < m; i += nt) A[i * kMaxKrylov + k] = A[i * kMaxKrylov + k] / d;
+        __syncthreads();
+        const int w = m - k - 1;
+        for (int idx = tid; idx < w * w; idx += nt) {
+            const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+            A[i * kMaxKrylov + j] = A[i * kMaxKrylov + j] - A[i * kMaxKrylov + k] * A[k * kMaxKrylov + j];
         }
-        __syncwarp();
+        __syncthreads();
     }
-    __syncwarp();
+    __syncthreads();
     if (failed) return;
-    for (int idx = lane; idx < m * m; idx += 32) {
+    for (int idx = tid; idx < m * m; idx += nt) {
         int i = idx / m, j = idx % m;
         st->LU[i * kMaxKrylov + j] = A[i * kMaxKrylov + j];
     }
-    for (int k = lane; k < m; k += 32) st->piv[k] = piv[k];
+    for (int k = tid; k < m; k += nt) st->piv[k] = piv[k];
 }
 
-__global__ void lu_kernel(StepState *st) { lu_body(st); }
+__global__ void __launch_bounds__(kLuThreads) lu_kernel(StepState *st) { lu_body(st); }
 
 struct GamRow {
     double g[4];
@@ -778,6 +804,37 @@ __device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, co
         x[i] = h * phi[i] + h * t;
     }
     __syncthreads();
+#ifdef ROK_LINALG_FAST
+    // FMA build: warp 0 solves column by column, lane l holding rows l and l + 32
+    // (other summation order than the row loops below)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0)
+            for (int k = 0; k < m; ++k) {
+                int p = piv[k];
+                if (p != k) { double t = x[k]; x[k] = x[p]; x[p] = t; }
+            }
+        __syncwarp();
+        const int i0 = lane, i1 = lane + 32;
+        double r0 = i0 < m ? x[i0] : 0.0, r1 = i1 < m ? x[i1] : 0.0;
+        for (int j = 0; j + 1 < m; ++j) {   // unit lower factor
+            const double xj = __shfl_sync(0xffffffffu, j < 32 ? r0 : r1, j & 31);
+            if (i0 > j && i0 < m) r0 = r0 - A[i0 * kMaxKrylov + j] * xj;
+            if (i1 > j && i1 < m) r1 = r1 - A[i1 * kMaxKrylov + j] * xj;
+        }
+        const double d0 = i0 < m ? 1.0 / A[i0 * kMaxKrylov + i0] : 0.0;
+        const double d1 = i1 < m ? 1.0 / A[i1 * kMaxKrylov + i1] : 0.0;
+        for (int j = m - 1; j >= 0; --j) {   // upper factor
+            if (i0 == j) r0 = r0 * d0;
+            if (i1 == j) r1 = r1 * d1;
+            const double xj = __shfl_sync(0xffffffffu, j < 32 ? r0 : r1, j & 31);
+            if (i0 < j) r0 = r0 - A[i0 * kMaxKrylov + j] * xj;
+            if (i1 < j) r1 = r1 - A[i1 * kMaxKrylov + j] * xj;
+        }
+        if (i0 < m) x[i0] = r0;
+        if (i1 < m) x[i1] = r1;
+    }
+#else
     if (threadIdx.x == 0) {
         for (int k = 0; k < m; ++k) {
             int p = piv[k];
@@ -794,6 +851,7 @@ __device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, co
             x[i] = t / A[i * kMaxKrylov + i];
         }
     }
+#endif
     __syncthreads();
     int bad = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -806,7 +864,7 @@ __device__ __forceinline__ void stage_solve_body(int stage, const GamRow &gr, co
     if (__syncthreads_or(bad) && threadIdx.x == 0) st->status |= kStatusNonfinite;
 }
 
-__global__ void stage_solve_kernel(int stage, GamRow gr, const double *pin, int P, StepState *st)
+__global__ void __launch_bounds__(kSolveThreads) stage_solve_kernel(int stage, GamRow gr, const double *pin, int P, StepState *st)
 {
     stage_solve_body(stage, gr, pin, (size_t)P, P, st);
 }
@@ -1102,14 +1160,14 @@ __global__ void __launch_bounds__(RT) bmultidot_kernel(const double *__restrict_
 }
 
 // one CTA per instance: the projected stage solve
-__global__ void bstage_solve_kernel(int stage, GamRow gr, const double *pin, const BSeg sg)
+__global__ void __launch_bounds__(kSolveThreads) bstage_solve_kernel(int stage, GamRow gr, const double *pin, const BSeg sg)
 {
     const BatchInst &I = sg.inst[blockIdx.x];
     stage_solve_body(stage, gr, pin + I.chunk0, (size_t)sg.nchunks, I.nchunks, sg.st + blockIdx.x);
 }
 
 // one warp per instance: LU of I - h gamma H
-__global__ void blu_kernel(StepState *st) { lu_body(st + blockIdx.x); }
+__global__ void __launch_bounds__(kLuThreads) blu_kernel(StepState *st) { lu_body(st + blockIdx.x); }
 
 // k = sum_{m<meff} cvec[stage][m] V_m + h F over each chunk (instance coefficients)
 __global__ void __launch_bounds__(RT) bstage_vec_kernel(double *__restrict__ kout, const double *__restrict__ F,
@@ -1220,13 +1278,13 @@ static cudaError_t b_stage_solve(int stage, const double *gam_row, const double 
 {
     GamRow gr;
     for (int j = 0; j < 4; ++j) gr.g[j] = gam_row[j];
-    bstage_solve_kernel<<<ninst, RT, 0, s>>>(stage, gr, pin, sg);
+    bstage_solve_kernel<<<ninst, kSolveThreads, 0, s>>>(stage, gr, pin, sg);
     return cudaGetLastError();
 }
 
 static cudaError_t b_lu(StepState *st, int ninst, cudaStream_t s)
 {
-    blu_kernel<<<ninst, 32, 0, s>>>(st);
+    blu_kernel<<<ninst, kLuThreads, 0, s>>>(st);
     return cudaGetLastError();
 }
 
@@ -1316,13 +1374,13 @@ static cudaError_t stage_solve(int stage, const double *gam_row, const double *p
 {
     GamRow gr;
     for (int j = 0; j < 4; ++j) gr.g[j] = gam_row[j];
-    stage_solve_kernel<<<1, RT, 0, s>>>(stage, gr, pin, P, st);
+    stage_solve_kernel<<<1, kSolveThreads, 0, s>>>(stage, gr, pin, P, st);
     return cudaGetLastError();
 }
 
 static cudaError_t lu(StepState *st, cudaStream_t s)
 {
-    lu_kernel<<<1, 32, 0, s>>>(st);
+    lu_kernel<<<1, kLuThreads, 0, s>>>(st);
     return cudaGetLastError();
 }
 

@@ -222,7 +222,8 @@ __device__ __forceinline__ void roe_n(const S *L, const S *R, double nx, double 
 //   * the viscous coefficients carry mu, the grid spacing and the factor 2
 //     (face_coefs);
 //   * rho H = p gamma/(gamma-1) + rho k, and the Roe weights from
-//     1/(sqrt(rho_L) + sqrt(rho_R)) and the reciprocal square roots;
+//     1/(sqrt(rho_L) + sqrt(rho_R)) and the reciprocal square roots, the
+//     averaged velocity as q_R - w_L (q_R - q_L);
 //   * halving and the comparison of non-negative numbers on the integer pipe;
 //   * reciprocals from the hardware estimate and one Newton step.
 
@@ -303,15 +304,15 @@ __device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts
     const S sL = rL * qL, sR = rR * qR;
     const S rt = sL * sR;
     const S inv = rcp(sL + sR);
-    const S wl = sL * inv, wr = sR * inv;
-    const S nt = wl * nL + wr * nR, tt = wl * tL + wr * tR;
+    const S drho = rR - rL, dp = pR - pL, dn = nR - nL, dt = tR - tL;
+    const S wl = sL * inv;   // the right weight is 1 - wl
+    const S nt = nR - wl * dn, tt = tR - wl * dt;
     const S Ht = (eL * qL + eR * qR) * inv;
     const S kt = half(nt * nt + tt * tt);
     const S ct2 = C.gm1 * (Ht - kt);
     const S rc = rsqrt(ct2);
     const S ct = ct2 * rc, inv_c2 = rc * rc, hc = half(inv_c2);
     // wave strengths and speeds (Harten's fix on the acoustic waves)
-    const S drho = rR - rL, dp = pR - pL, dn = nR - nL, dt = tR - tL;
     const S rcdq = (rt * ct) * dn;
     const S a1 = (dp - rcdq) * hc, a3 = (dp + rcdq) * hc;
     const S a2 = drho - dp * inv_c2;
@@ -365,15 +366,15 @@ __device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double
     const S sL = rL * qL, sR = rR * qR;
     const S rt = sL * sR;
     const S inv = rcp(sL + sR);
-    const S wl = sL * inv, wr = sR * inv;
-    const S ut = wl * uL + wr * uR, vt = wl * vL + wr * vR;
+    const S drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
+    const S wl = sL * inv;   // the right weight is 1 - wl
+    const S ut = uR - wl * du, vt = vR - wl * dv;
     const S Ht = (eL * qL + eR * qR) * inv;
     const S kt = half(ut * ut + vt * vt);
     const S ct2 = C.gm1 * (Ht - kt);
     const S rc = rsqrt(ct2);
     const S ct = ct2 * rc, inv_c2 = rc * rc, hc = half(inv_c2);
     const S qnt = ut * nx + vt * ny;
-    const S drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
     const S rcdq = (rt * ct) * dqn;
     const S a1 = (dp - rcdq) * hc, a3 = (dp + rcdq) * hc;
     const S a2 = drho - dp * inv_c2;
