@@ -404,37 +404,57 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__
 // ---- persistent Arnoldi column ------------------------------------------------
 
 constexpr int kColChunks = 2;                  // chunks of 2048 entries per CTA (max)
-constexpr long long kBarrierSpins = 1LL << 22; // ~0.3 s at 64 ns per spin, then give up
+constexpr long long kBarrierSpins = 1LL << 22; // 4M polls (~0.3 s or more), then give up
 
-// Bounded grid barrier: arrive on the counter; the last CTA resets it and
-// advances the generation; the others poll the generation with a spin limit.
-// On expiry the status gets kStatusTimeout and the CTA reports failure (the
-// kernel then returns; nothing waits forever).
+// gpu-scope acquire / release accesses of the grid barrier's words
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned x)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(x) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned x)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned x)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+
+// Bounded grid barrier: after the CTA barrier, thread 0 arrives on the counter
+// (acquire-release: it publishes the CTA's writes); the last CTA resets the
+// counter and advances the generation (release); the others poll the
+// generation (acquire) with a spin limit.  On expiry the status gets
+// kStatusTimeout and the CTA reports failure (the kernel then returns; nothing
+// waits forever).
 __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, int *status)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned *vgen = &bar->gen;
-        const unsigned g = *vgen;
-        __threadfence();
-        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
+        const unsigned g = ld_acquire_gpu(&bar->gen);
+        if (atom_add_acq_rel_gpu(&bar->count, 1u) == nblocks - 1) {
+            st_relaxed_gpu(&bar->count, 0u);
+            red_add_release_gpu(&bar->gen, 1u);
         } else {
             long long spins = 0;
-            while (*vgen == g) {
+            while (ld_acquire_gpu(&bar->gen) == g) {
                 if (++spins > kBarrierSpins) {
                     atomicOr(status, kStatusTimeout);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
