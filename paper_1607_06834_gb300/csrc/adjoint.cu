@@ -93,6 +93,183 @@ __device__ __forceinline__ void prim_at(const StencilConsts &C, const double *__
     T = p * rinv;
 }
 
+// Reverse of the Roe flux of roe_x (DIR 0) / roe_y (DIR 1): Lb = (dF/dL)^T Fb,
+// Rb = (dF/dR)^T Fb for the left and right primitive states (rho, u, v, p),
+// one forward sweep that keeps the intermediates and one reverse sweep
+// (about three flux evaluations, against eight dual-number evaluations for
+// the Jacobian columns).  N is the normal and T the tangential velocity
+// component; |x| and Harten's switch differentiate as the dual numbers do
+// (sign +1 at 0, the branch taken by the value).
+template <int DIR>
+__device__ __forceinline__ void roe_vjp(const double *L, const double *R, const StencilConsts &C, const double *Fb,
+                                        double *Lb, double *Rb)
+{
+    constexpr int N = 1 + DIR, T = 2 - DIR;
+    const double rL = L[0], nL = L[N], tL = L[T], pL = L[3];
+    const double rR = R[0], nR = R[N], tR = R[T], pR = R[3];
+    // forward (the order of roe_avg and roe_x / roe_y)
+    const double kinL = 0.5 * (L[1] * L[1] + L[2] * L[2]), kinR = 0.5 * (R[1] * R[1] + R[2] * R[2]);
+    const double eL = (pL * C.inv_gm1 + rL * kinL) + pL, eR = (pR * C.inv_gm1 + rR * kinR) + pR;
+    const double sL = sqrt(rL), sR = sqrt(rR);
+    const double rt = sL * sR;
+    const double Y = rt * (sL + sR), den = 1.0 / Y;
+    const double rLsR = rL * sR, rRsL = rR * sL;
+    const double wl = rLsR * den, wr = rRsL * den;
+    const double nt = wl * nL + wr * nR, tt = wl * tL + wr * tR;
+    const double X = eL * sR + eR * sL, Ht = X * den;
+    const double kt = 0.5 * (nt * nt + tt * tt);
+    const double ct2 = C.gm1 * (Ht - kt);
+    const double ct = sqrt(ct2), inv_c2 = 1.0 / ct2;
+    const double drho = rR - rL, dp = pR - pL, dn = nR - nL, dt = tR - tL;
+    const double rtct = rt * ct, rcdq = rtct * dn;
+    const double q1 = 0.5 * (dp - rcdq), q3 = 0.5 * (dp + rcdq);
+    const double a1 = q1 * inv_c2, a2 = drho - dp * inv_c2, a3 = q3 * inv_c2;
+    const double snt = nt < 0.0 ? -1.0 : 1.0, l2 = snt * nt;
+    const double delta = C.efix * (l2 + ct);
+    const double lam1 = nt - ct, lam3 = nt + ct;
+    const double s1 = lam1 < 0.0 ? -1.0 : 1.0, s3 = lam3 < 0.0 ? -1.0 : 1.0;
+    const double m1 = s1 * lam1, m3 = s3 * lam3;   // |lambda|
+    const bool h1 = m1 < delta, h3 = m3 < delta;
+    const double l1 = h1 ? (m1 * m1 + delta * delta) / (2.0 * delta) : m1;
+    const double l3 = h3 ? (m3 * m3 + delta * delta) / (2.0 * delta) : m3;
+    const double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
+    const double sA = A1 + A3, dA = A3 - A1, D0 = sA + A2;
+    const double mL = rL * nL, mR = rR * nR;
+    // reverse
+    const double F0b = Fb[0], Fnb = Fb[N], Ftb = Fb[T], F3b = Fb[3];
+    double mLb = 0.5 * F0b, mRb = 0.5 * F0b, D0b = -0.5 * F0b;
+    mLb += 0.5 * Fnb * nL;
+    mRb += 0.5 * Fnb * nR;
+    double nLb = 0.5 * Fnb * mL, nRb = 0.5 * Fnb * mR, pLb = 0.5 * Fnb, pRb = 0.5 * Fnb;
+    const double Dnb = -0.5 * Fnb;
+    mLb += 0.5 * Ftb * tL;
+    mRb += 0.5 * Ftb * tR;
+    double tLb = 0.5 * Ftb * mL, tRb = 0.5 * Ftb * mR;
+    const double Dtb = -0.5 * Ftb;
+    nLb += 0.5 * F3b * eL;
+    nRb += 0.5 * F3b * eR;
+    double eLb = 0.5 * F3b * nL, eRb = 0.5 * F3b * nR;
+    const double D3b = -0.5 * F3b;
+    double rLb = mLb * nL, rRb = mRb * nR;
+    nLb += mLb * rL;
+    nRb += mRb * rR;
+    // D3 = Ht sA + kt A2 + ct nt dA + As tt dt
+    double Htb = D3b * sA, sAb = D3b * Ht, ktb = D3b * A2, A2b = D3b * kt;
+    double ctb = D3b * nt * dA, ntb = D3b * ct * dA, dAb = D3b * ct * nt;
+    double Asb = D3b * tt * dt, ttb = D3b * As * dt, dtb = D3b * As * tt;
+    // Dt = tt D0 + As dt;  Dn = nt D0 + ct dA
+    ttb += Dtb * D0;
+    D0b += Dtb * tt;
+    Asb += Dtb * dt;
+    dtb += Dtb * As;
+    ntb += Dnb * D0;
+    D0b += Dnb * nt;
+    ctb += Dnb * dA;
+    dAb += Dnb * ct;
+    // D0 = sA + A2;  sA = A1 + A3;  dA = A3 - A1
+    sAb += D0b;
+    A2b += D0b;
+    const double A1b = sAb - dAb, A3b = sAb + dAb;
+    // A1 = l1 a1, A2 = l2 a2, A3 = l3 a3, As = l2 rt
+    const double l1b = A1b * a1, l3b = A3b * a3;
+    const double a1b = A1b * l1, a2b = A2b * l2, a3b = A3b * l3;
+    double l2b = A2b * a2 + Asb * rt;
+    double rtb = Asb * l2;
+    // Harten's switch on the acoustic speeds
+    double deltab = 0.0, m1b, m3b;
+    if (h1) {
+        m1b = l1b * m1 / delta;
+        deltab += l1b * (delta * delta - m1 * m1) / (2.0 * delta * delta);
+    } else {
+        m1b = l1b;
+    }
+    if (h3) {
+        m3b = l3b * m3 / delta;
+        deltab += l3b * (delta * delta - m3 * m3) / (2.0 * delta * delta);
+    } else {
+        m3b = l3b;
+    }
+    const double lam1b = s1 * m1b, lam3b = s3 * m3b;
+    ntb += lam1b + lam3b;
+    ctb += lam3b - lam1b;
+    // delta = efix (l2 + ct), l2 = |nt|
+    l2b += C.efix * deltab;
+    ctb += C.efix * deltab;
+    ntb += snt * l2b;
+    // a1 = q1 / c^2, a3 = q3 / c^2, a2 = drho - dp / c^2
+    const double q1b = a1b * inv_c2, q3b = a3b * inv_c2;
+    double inv_c2b = a1b * q1 + a3b * q3 - a2b * dp;
+    const double drhob = a2b;
+    double dpb = 0.5 * q1b + 0.5 * q3b - a2b * inv_c2;
+    const double rcdqb = 0.5 * (q3b - q1b);
+    const double rtctb = rcdqb * dn;
+    double dnb = rcdqb * rtct;
+    rtb += rtctb * ct;
+    ctb += rtctb * rt;
+    // differences
+    rRb += drhob;
+    rLb -= drhob;
+    pRb += dpb;
+    pLb -= dpb;
+    nRb += dnb;
+    nLb -= dnb;
+    tRb += dtb;
+    tLb -= dtb;
+    // ct = sqrt(ct2), inv_c2 = 1 / ct2, ct2 = gm1 (Ht - kt)
+    const double ct2b = ctb * 0.5 / ct - inv_c2b * inv_c2 * inv_c2;
+    Htb += C.gm1 * ct2b;
+    ktb -= C.gm1 * ct2b;
+    // kt = (nt^2 + tt^2) / 2
+    ntb += ktb * nt;
+    ttb += ktb * tt;
+    // Ht = X den, X = eL sR + eR sL
+    const double Xb = Htb * den;
+    double denb = Htb * X;
+    eLb += Xb * sR;
+    eRb += Xb * sL;
+    double sRb = Xb * eL, sLb = Xb * eR;
+    // nt = wl nL + wr nR, tt = wl tL + wr tR
+    const double wlb = ntb * nL + ttb * tL, wrb = ntb * nR + ttb * tR;
+    nLb += ntb * wl;
+    nRb += ntb * wr;
+    tLb += ttb * wl;
+    tRb += ttb * wr;
+    // wl = (rL sR) den, wr = (rR sL) den
+    denb += wlb * rLsR + wrb * rRsL;
+    rLb += wlb * den * sR;
+    sRb += wlb * den * rL;
+    rRb += wrb * den * sL;
+    sLb += wrb * den * rR;
+    // den = 1 / Y, Y = rt (sL + sR)
+    const double Yb = -denb * den * den;
+    rtb += Yb * (sL + sR);
+    sLb += Yb * rt;
+    sRb += Yb * rt;
+    // rt = sL sR, s = sqrt(rho)
+    sLb += rtb * sR;
+    sRb += rtb * sL;
+    rLb += sLb * 0.5 / sL;
+    rRb += sRb * 0.5 / sR;
+    // e = p / (gamma - 1) + rho kin + p, kin = (u^2 + v^2) / 2
+    pLb += eLb * (C.inv_gm1 + 1.0);
+    pRb += eRb * (C.inv_gm1 + 1.0);
+    rLb += eLb * kinL;
+    rRb += eRb * kinR;
+    const double kinLb = eLb * rL, kinRb = eRb * rR;
+    nLb += kinLb * nL;
+    tLb += kinLb * tL;
+    nRb += kinRb * nR;
+    tRb += kinRb * tR;
+    Lb[0] = rLb;
+    Lb[N] = nLb;
+    Lb[T] = tLb;
+    Lb[3] = pLb;
+    Rb[0] = rRb;
+    Rb[N] = nRb;
+    Rb[T] = tRb;
+    Rb[3] = pRb;
+}
+
 // Pass 1: face D (0: x-faces, face i of row j between cells (i-1, j) and (i, j);
 // 1: y-faces, face j of column i between (i, j-1) and (i, j)).  Stores
 // fa[q * nc + face] for q < 15 and one partial of ubar . df/dmu per CTA.
@@ -124,18 +301,15 @@ __global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, con
         double Fb[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) Fb[k] = rd * (ub[k * nc + cp1] - ub[k * nc + cm1]);
-        // Roe flux: column q of its Jacobian by one dual-number evaluation
-#pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-            Dual L[4], R[4], F[4];
+        // Roe flux: (dF/dWL)^T Fb and (dF/dWR)^T Fb by one reverse sweep
+        {
+            double Lb[4], Rb[4];
+            roe_vjp<D>(WL, WR, C, Fb, Lb, Rb);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                L[k] = {WL[k], q == k ? 1.0 : 0.0};
-                R[k] = {WR[k], q == k + 4 ? 1.0 : 0.0};
+            for (int q = 0; q < 4; ++q) {
+                fa[q * nc + t] = Lb[q];
+                fa[(q + 4) * nc + t] = Rb[q];
             }
-            if (D == 0) roe_x(L, R, C, F);
-            else roe_y(L, R, C, F);
-            fa[q * nc + t] = ((F[0].d * Fb[0] + F[1].d * Fb[1]) + F[2].d * Fb[2]) + F[3].d * Fb[3];
         }
         if (VISC) {
             // normal cells a = cm1, b = cp1; tangential neighbours across the face
