@@ -61,8 +61,10 @@ struct AdjWork {
     double *wb = nullptr, *wcur = nullptr, *wlast = nullptr, *Yt = nullptr, *y1 = nullptr;
     double *pA = nullptr, *pB = nullptr, *pM = nullptr;
     double *faces = nullptr;   // 15 x (nx ny) per direction
+    double *prims = nullptr;   // rho, u, v, p, T of every cell (5 x nx ny)
     double *mupart = nullptr;  // CTA partials of the viscosity adjoint
     int nmu = 0;
+    int rev_ctas = -1;         // CTAs of the cooperative reverse-MGS launch (0: pass by pass)
     AdjState *as = nullptr;
     StepState *h_st = nullptr;
     double *h_mub = nullptr;
@@ -91,6 +93,28 @@ __device__ __forceinline__ void prim_at(const StencilConsts &C, const double *__
     P[2] = v;
     P[3] = p;
     T = p * rinv;
+}
+
+// Pass 0: the primitives of every cell, once (the face pass reads each cell's
+// from four faces and the viscous terms from four more)
+__global__ void __launch_bounds__(AT) prim_kernel(const StencilConsts C, const double *__restrict__ y,
+                                                  double *__restrict__ pr)
+{
+    const size_t nc = (size_t)C.nx * C.ny;
+    const size_t t = (size_t)blockIdx.x * AT + threadIdx.x;
+    if (t >= nc) return;
+    double P[4], T;
+    prim_at(C, y, nc, t, P, T);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pr[k * nc + t] = P[k];
+    pr[4 * nc + t] = T;
+}
+
+__device__ __forceinline__ void prim_load(const double *__restrict__ pr, size_t nc, size_t c, double *P, double &T)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) P[k] = pr[k * nc + c];
+    T = pr[4 * nc + c];
 }
 
 // Reverse of the Roe flux of roe_x (DIR 0) / roe_y (DIR 1): Lb = (dF/dL)^T Fb,
@@ -274,7 +298,7 @@ __device__ __forceinline__ void roe_vjp(const double *L, const double *R, const 
 // 1: y-faces, face j of column i between (i, j-1) and (i, j)).  Stores
 // fa[q * nc + face] for q < 15 and one partial of ubar . df/dmu per CTA.
 template <bool VISC, int D>
-__global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, const double *__restrict__ y,
+__global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, const double *__restrict__ pr,
                                                       const double *__restrict__ ub, double *__restrict__ fa,
                                                       double *__restrict__ mupart)
 {
@@ -290,10 +314,10 @@ __global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, con
         };
         const size_t cm2 = cell(-2), cm1 = cell(-1), cp1 = cell(0), cp2 = cell(1);
         double Pm2[4], Pm1[4], Pp1[4], Pp2[4], Tm2, Tm1, Tp1, Tp2;
-        prim_at(C, y, nc, cm2, Pm2, Tm2);
-        prim_at(C, y, nc, cm1, Pm1, Tm1);
-        prim_at(C, y, nc, cp1, Pp1, Tp1);
-        prim_at(C, y, nc, cp2, Pp2, Tp2);
+        prim_load(pr, nc, cm2, Pm2, Tm2);
+        prim_load(pr, nc, cm1, Pm1, Tm1);
+        prim_load(pr, nc, cp1, Pp1, Tp1);
+        prim_load(pr, nc, cp2, Pp2, Tp2);
         double WL[4], WR[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) muscl(Pm2[k], Pm1[k], Pp1[k], Pp2[k], C.c_lo, C.c_hi, WL[k], WR[k]);
@@ -317,7 +341,7 @@ __global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, con
                 const int ci = (int)(c0 % nx), cj = (int)(c0 / nx);
                 return D == 0 ? (size_t)wrapi(cj + s, ny) * nx + ci : (size_t)cj * nx + wrapi(ci + s, nx);
             };
-            auto uv = [&](size_t c0, int comp) -> double { return y[(1 + comp) * nc + c0] / y[c0]; };
+            auto uv = [&](size_t c0, int comp) -> double { return pr[(1 + comp) * nc + c0]; };
             const double q_rt = D == 0 ? C.q_rdy : C.q_rdx;
             // normal and tangential derivatives of u and v, normal derivative of T
             const double un = (Pp1[1] - Pm1[1]) * rd, vn = (Pp1[2] - Pm1[2]) * rd, Tn = (Tp1 - Tm1) * rd;
@@ -374,7 +398,7 @@ struct VjpOut {
 
 // Pass 2: g = J^T ubar at each cell from the face adjoints
 template <bool VISC>
-__global__ void __launch_bounds__(AT) vjp_cell_kernel(const StencilConsts C, const double *__restrict__ y,
+__global__ void __launch_bounds__(AT) vjp_cell_kernel(const StencilConsts C, const double *__restrict__ pr,
                                                       const double *__restrict__ fx, const double *__restrict__ fy,
                                                       const VjpOut o)
 {
@@ -426,7 +450,7 @@ __global__ void __launch_bounds__(AT) vjp_cell_kernel(const StencilConsts C, con
         }
     }
     double P[4], T;
-    prim_at(C, y, nc, t, P, T);
+    prim_load(pr, nc, t, P, T);
     const double rho = P[0], u = P[1], v = P[2];
     const double rinv = 1.0 / rho;
     // T = p / rho
@@ -612,6 +636,90 @@ __global__ void __launch_bounds__(RT) mgsrev_kernel(double *__restrict__ wb, dou
     }
 }
 
+// The j+1 reverse passes of mgsrev_kernel for Arnoldi column j in one
+// cooperative launch (the mirror of arnoldi_column_kernel: the adjoint wbar and
+// w stay in registers, v_i is carried from one pass to the next, a bounded grid
+// barrier between passes).  On entry wb holds the adjoint of w_{j+1} and wcur =
+// w_{j+1}; on exit wb holds the adjoint of w_0 = J v_j (wcur is not updated).
+// The same arithmetic as the pass-by-pass kernels.
+__global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict__ wb, const double *__restrict__ wcur,
+                                                              double *__restrict__ Vb, const double *__restrict__ V,
+                                                              size_t ldv, size_t n, int j, int P, double *partA,
+                                                              double *partB, GridBarrier *bar, StepState *st,
+                                                              const AdjState *as)
+{
+    __shared__ double sh[16];
+    const unsigned G = gridDim.x;
+    double b[kColChunks][EPL], w[kColChunks][EPL], v[kColChunks][EPL];
+    size_t e0[kColChunks];
+    bool have[kColChunks];
+    double x[kColChunks];
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c) {
+        const int blk = blockIdx.x + c * G;
+        have[c] = blk < P;
+        e0[c] = ((size_t)blk * RT + threadIdx.x) * EPL;
+        x[c] = 0.0;
+        if (have[c]) {
+            load8(wb, e0[c], n, b[c]);
+            load8(wcur, e0[c], n, w[c]);
+            load8(V + (size_t)j * ldv, e0[c], n, v[c]);
+            x[c] = lane_dot(v[c], b[c]);   // <v_j, wbar>
+        }
+    }
+    double sa, sb;
+    if (have[1]) {   // uniform per CTA
+        chunk_sum2v(x[0], x[1], sh, sa, sb);
+    } else {
+        sa = chunk_sumv(x[0], sh);
+    }
+    if (threadIdx.x == 0) partA[blockIdx.x] = sa;
+    if (threadIdx.x == 8 && have[1]) partA[blockIdx.x + G] = sb;
+    if (!grid_barrier(bar, G, &st->status)) return;
+    double *pin = partA, *pout = partB;
+    for (int i = j; i >= 0; --i) {
+        const double d = tree_partials(pin, P, sh);
+        const double hij = st->H[i * kMaxKrylov + j];
+        const double hb = as->Hb[i * kMaxKrylov + j] - d;
+        double *vbi = Vb + (size_t)i * ldv;
+#pragma unroll
+        for (int c = 0; c < kColChunks; ++c) {
+            x[c] = 0.0;
+            if (!have[c]) continue;
+            double g[EPL];
+            load8(vbi, e0[c], n, g);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) {
+                const double wi = w[c][k] + hij * v[c][k];
+                g[k] = (g[k] - hij * b[c][k]) + hb * wi;
+                b[c][k] = b[c][k] + hb * v[c][k];
+                w[c][k] = wi;
+            }
+            store8(vbi, e0[c], n, g);
+            if (i > 0) {
+                load8(V + (size_t)(i - 1) * ldv, e0[c], n, v[c]);
+                if (i >= 2) prefetch_l2(V + (size_t)(i - 2) * ldv, e0[c], n);
+                x[c] = lane_dot(v[c], b[c]);   // <v_{i-1}, wbar>
+            }
+        }
+        if (i == 0) break;
+        if (have[1]) {
+            chunk_sum2v(x[0], x[1], sh, sa, sb);
+        } else {
+            sa = chunk_sumv(x[0], sh);
+        }
+        if (threadIdx.x == 0) pout[blockIdx.x] = sa;
+        if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
+        if (!grid_barrier(bar, G, &st->status)) return;
+        double *t = pin;
+        pin = pout;
+        pout = t;
+    }
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c)
+        if (have[c]) store8(wb, e0[c], n, b[c]);
+}
+
 // residual VJP launches: out1 += s1 g, out2 += s2 g with g = J(ystate)^T ubar;
 // dst_mu += mu_factor (* mu_dev) ubar . df/dmu(ystate)
 rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, const VjpOut &o, double *dst_mu,
@@ -622,16 +730,17 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
     const int nb = (int)((nc + AT - 1) / AT);
     double *fxa = A->faces, *fya = A->faces + kFaceVals * nc;
     cudaStream_t s = c->stream;
+    prim_kernel<<<nb, AT, 0, s>>>(C, ystate, A->prims);
     if (C.viscous) {
-        vjp_face_kernel<true, 0><<<nb, AT, 0, s>>>(C, ystate, ub, fxa, A->mupart);
-        vjp_face_kernel<true, 1><<<nb, AT, 0, s>>>(C, ystate, ub, fya, A->mupart + nb);
-        vjp_cell_kernel<true><<<nb, AT, 0, s>>>(C, ystate, fxa, fya, o);
+        vjp_face_kernel<true, 0><<<nb, AT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
+        vjp_face_kernel<true, 1><<<nb, AT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nb);
+        vjp_cell_kernel<true><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
     } else {
-        vjp_face_kernel<false, 0><<<nb, AT, 0, s>>>(C, ystate, ub, fxa, A->mupart);
-        vjp_face_kernel<false, 1><<<nb, AT, 0, s>>>(C, ystate, ub, fya, A->mupart + nb);
-        vjp_cell_kernel<false><<<nb, AT, 0, s>>>(C, ystate, fxa, fya, o);
+        vjp_face_kernel<false, 0><<<nb, AT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
+        vjp_face_kernel<false, 1><<<nb, AT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nb);
+        vjp_cell_kernel<false><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
     }
-    c->launches += 3;
+    c->launches += 4;
     if (dst_mu && C.viscous) {
         tree_add_kernel<<<1, AT, 0, s>>>(A->mupart, 2 * nb, mu_factor, mu_dev, dst_mu);
         c->launches++;
@@ -655,7 +764,7 @@ void free_work(AdjWork *A)
     cudaFree(A->yb); cudaFree(A->Fb); cudaFree(A->F1b); cudaFree(A->F1acc);
     cudaFree(A->wb); cudaFree(A->wcur); cudaFree(A->wlast); cudaFree(A->Yt); cudaFree(A->y1);
     cudaFree(A->pA); cudaFree(A->pB); cudaFree(A->pM);
-    cudaFree(A->faces); cudaFree(A->mupart); cudaFree(A->as);
+    cudaFree(A->faces); cudaFree(A->prims); cudaFree(A->mupart); cudaFree(A->as);
     cudaFreeHost(A->h_st); cudaFreeHost(A->h_mub);
     delete A;
 }
@@ -673,7 +782,7 @@ rok_status ensure_work(rok_ctx *c, bool full)
     bool ok = true;
     if (!A->faces) {
         A->nmu = 2 * (int)((nc + AT - 1) / AT);
-        ok = al(&A->faces, 2 * kFaceVals * nc) && al(&A->mupart, A->nmu) &&
+        ok = al(&A->faces, 2 * kFaceVals * nc) && al(&A->prims, 5 * nc) && al(&A->mupart, A->nmu) &&
              cudaMalloc(&A->as, sizeof(AdjState)) == cudaSuccess &&
              cudaMallocHost(&A->h_mub, sizeof(double)) == cudaSuccess;
     }
@@ -694,6 +803,17 @@ rok_status ensure_work(rok_ctx *c, bool full)
 }
 
 inline int egrid(const rok_ctx *c) { return c->egrid; }
+
+// co-resident CTAs of mgsrev_column_kernel (0 without cooperative launch)
+int rev_column_ctas()
+{
+    int dev = 0, coop = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgsrev_column_kernel, RT, 0) != cudaSuccess) return 0;
+    return per * sms;
+}
 
 }  // namespace
 
@@ -855,16 +975,33 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
                 CU(cudaMemsetAsync(A->wb, 0, N * sizeof(double), s));
                 CU(cudaMemcpyAsync(A->wcur, A->wlast, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
             }
-            CU(ops.dot2(vj, A->wb, nullptr, nullptr, N, A->pA, P, nullptr, s));
-            c->launches++;
-            double *pin = A->pA, *pout = A->pB;
-            for (int i = j; i >= 0; --i) {
-                const double *vi = c->V + (size_t)i * N;
-                const double *vprev = i > 0 ? c->V + (size_t)(i - 1) * N : nullptr;
-                mgsrev_kernel<<<P, RT, 0, s>>>(A->wb, A->wcur, A->Vb + (size_t)i * N, vi, vprev, N, pin, P,
-                                               &st->H[i * kMaxKrylov + j], &as->Hb[i * kMaxKrylov + j], pout);
+            if (A->rev_ctas < 0) A->rev_ctas = rev_column_ctas();
+            const int G = P < A->rev_ctas ? P : A->rev_ctas;
+            if (G > 0 && (P + G - 1) / G <= kColChunks) {
+                // all j + 1 reverse passes in one cooperative launch
+                double *wbp = A->wb, *pa = A->pA, *pb = A->pB;
+                const double *wcp = A->wcur, *Vp = c->V;
+                double *Vbp = A->Vb;
+                size_t ldv = N, nn = N;
+                int jj = j, PP = P;
+                GridBarrier *barp = c->bar;
+                StepState *stp = st;
+                const AdjState *asp = as;
+                void *args[] = {&wbp, &wcp, &Vbp, &Vp, &ldv, &nn, &jj, &PP, &pa, &pb, &barp, &stp, &asp};
+                CU(cudaLaunchCooperativeKernel((const void *)mgsrev_column_kernel, dim3(G), dim3(RT), args, 0, s));
                 c->launches++;
-                double *t = pin; pin = pout; pout = t;
+            } else {
+                CU(ops.dot2(vj, A->wb, nullptr, nullptr, N, A->pA, P, nullptr, s));
+                c->launches++;
+                double *pin = A->pA, *pout = A->pB;
+                for (int i = j; i >= 0; --i) {
+                    const double *vi = c->V + (size_t)i * N;
+                    const double *vprev = i > 0 ? c->V + (size_t)(i - 1) * N : nullptr;
+                    mgsrev_kernel<<<P, RT, 0, s>>>(A->wb, A->wcur, A->Vb + (size_t)i * N, vi, vprev, N, pin, P,
+                                                   &st->H[i * kMaxKrylov + j], &as->Hb[i * kMaxKrylov + j], pout);
+                    c->launches++;
+                    double *t = pin; pin = pout; pout = t;
+                }
             }
             // w_0 = (f(y + eps v_j) - F1) / eps
             lin2_kernel<<<eg, AT, 0, s>>>(A->Yt, y, 1.0, vj, 1.0, &st->eps, N);

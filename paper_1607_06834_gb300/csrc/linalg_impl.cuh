@@ -240,6 +240,103 @@ __device__ __forceinline__ T tree_partials(const T *__restrict__ p, int P, T *sh
 
 __device__ __forceinline__ size_t lane_e0() { return ((size_t)blockIdx.x * RT + threadIdx.x) * EPL; }
 
+// ---- persistent kernels: grid barrier and paired chunk sums ---------------------
+
+constexpr int kColChunks = 2;                  // chunks of 2048 entries per CTA (max)
+constexpr long long kBarrierSpins = 1LL << 22; // 4M polls (~0.3 s or more), then give up
+
+// gpu-scope acquire / release accesses of the grid barrier's words
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned x)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(x) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned x)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned x)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+
+// Bounded grid barrier: after the CTA barrier, thread 0 arrives on the counter
+// (acquire-release: it publishes the CTA's writes); the last CTA resets the
+// counter and advances the generation (release); the others poll the
+// generation (acquire) with a spin limit.  On expiry the status gets
+// kStatusTimeout and the CTA reports failure (the kernel then returns; nothing
+// waits forever).
+__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, int *status)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned g = ld_acquire_gpu(&bar->gen);
+        if (atom_add_acq_rel_gpu(&bar->count, 1u) == nblocks - 1) {
+            st_relaxed_gpu(&bar->count, 0u);
+            red_add_release_gpu(&bar->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acquire_gpu(&bar->gen) == g) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// The sums of two 2048-entry chunks at once from the lanes' parts a and b
+// (lane_dot), each the same tree as chunk_sumv: even lanes finish the first
+// chunk's butterfly and odd lanes the second's (one exchange and five
+// additions per lane instead of ten); then the two 8-warp trees together.
+// Results in thread 0 (first) and thread 8 (second).  sh needs 16 entries.
+template <class T>
+__device__ __forceinline__ void chunk_sum2v(const T a, const T b, T *sh, T &sa, T &sb)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool odd = lane & 1;
+    const T recv = __shfl_xor_sync(0xffffffffu, odd ? a : b, 1);
+    T v = odd ? recv + b : a + recv;   // a_l + a_{l+1} on even lanes, b_{l-1} + b_l on odd lanes
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    __syncthreads();
+    if (lane < 2) sh[lane * 8 + wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        T u = lane < 16 ? sh[lane] : T(0);
+        u += __shfl_xor_sync(0xffffffffu, u, 1);
+        u += __shfl_xor_sync(0xffffffffu, u, 2);
+        u += __shfl_xor_sync(0xffffffffu, u, 4);
+        if (lane == 0) sa = u;
+        if (lane == 8) sb = u;
+    }
+}
+
+// Hint: fetch the 128-byte line holding this thread's entries of p (from e0)
+// into L2; one thread per line issues it.
+template <class T>
+__device__ __forceinline__ void prefetch_l2(const T *p, size_t e0, size_t n)
+{
+    constexpr int kThreadsPerLine = 128 / (EPL * (int)sizeof(T));
+    if (e0 < n && threadIdx.x % kThreadsPerLine == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + e0));
+}
+
 #ifndef ROK_LINALG_DEVICE_ONLY
 // partials[b] = <a0, b0> and partials[P + b] = <a1, b1> (if a1) over CTA b's range
 __global__ void __launch_bounds__(RT) dot2_kernel(const double *__restrict__ a0, const double *__restrict__ b0,
@@ -402,101 +499,6 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__
 }
 
 // ---- persistent Arnoldi column ------------------------------------------------
-
-constexpr int kColChunks = 2;                  // chunks of 2048 entries per CTA (max)
-constexpr long long kBarrierSpins = 1LL << 22; // 4M polls (~0.3 s or more), then give up
-
-// gpu-scope acquire / release accesses of the grid barrier's words
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned x)
-{
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(x) : "memory");
-    return old;
-}
-__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned x)
-{
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
-}
-__device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned x)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
-}
-
-// Bounded grid barrier: after the CTA barrier, thread 0 arrives on the counter
-// (acquire-release: it publishes the CTA's writes); the last CTA resets the
-// counter and advances the generation (release); the others poll the
-// generation (acquire) with a spin limit.  On expiry the status gets
-// kStatusTimeout and the CTA reports failure (the kernel then returns; nothing
-// waits forever).
-__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, int *status)
-{
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned g = ld_acquire_gpu(&bar->gen);
-        if (atom_add_acq_rel_gpu(&bar->count, 1u) == nblocks - 1) {
-            st_relaxed_gpu(&bar->count, 0u);
-            red_add_release_gpu(&bar->gen, 1u);
-        } else {
-            long long spins = 0;
-            while (ld_acquire_gpu(&bar->gen) == g) {
-                if (++spins > kBarrierSpins) {
-                    atomicOr(status, kStatusTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// The sums of two 2048-entry chunks at once from the lanes' parts a and b
-// (lane_dot), each the same tree as chunk_sumv: even lanes finish the first
-// chunk's butterfly and odd lanes the second's (one exchange and five
-// additions per lane instead of ten); then the two 8-warp trees together.
-// Results in thread 0 (first) and thread 8 (second).  sh needs 16 entries.
-template <class T>
-__device__ __forceinline__ void chunk_sum2v(const T a, const T b, T *sh, T &sa, T &sb)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const bool odd = lane & 1;
-    const T recv = __shfl_xor_sync(0xffffffffu, odd ? a : b, 1);
-    T v = odd ? recv + b : a + recv;   // a_l + a_{l+1} on even lanes, b_{l-1} + b_l on odd lanes
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    __syncthreads();
-    if (lane < 2) sh[lane * 8 + wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        T u = lane < 16 ? sh[lane] : T(0);
-        u += __shfl_xor_sync(0xffffffffu, u, 1);
-        u += __shfl_xor_sync(0xffffffffu, u, 2);
-        u += __shfl_xor_sync(0xffffffffu, u, 4);
-        if (lane == 0) sa = u;
-        if (lane == 8) sb = u;
-    }
-}
-
-// Hint: fetch the 128-byte line holding this thread's entries of p (from e0)
-// into L2; one thread per line issues it.
-template <class T>
-__device__ __forceinline__ void prefetch_l2(const T *p, size_t e0, size_t n)
-{
-    constexpr int kThreadsPerLine = 128 / (EPL * (int)sizeof(T));
-    if (e0 < n && threadIdx.x % kThreadsPerLine == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + e0));
-}
 
 // One Arnoldi column in one cooperative launch.  T is the basis type: double
 // (plain path) or float (mixed path: basis storage and Gram-Schmidt in binary32;
