@@ -5,11 +5,12 @@
 //
 // Residual VJP, uniform periodic grids: f_c = -(F_{c+1/2} - F_{c-1/2}) / dx
 // - (G_{c+1/2} - G_{c-1/2}) / dy, so a face flux's adjoint is
-// Fbar = (ubar_R - ubar_L) / dx.  Pass 1 (one thread per face) takes Fbar back
-// through the face flux: the 4 x 8 Jacobian of the Roe flux with respect to the
-// reconstructed left/right primitive states comes from eight forward-mode
-// (dual-number) evaluations of the same flux function the residual uses; the
-// central viscous flux is reversed by hand.  Each face stores the adjoints of
+// Fbar = (ubar_R - ubar_L) / dx.  Pass 0 computes every cell's primitives once.
+// Pass 1 (one thread per face) takes Fbar back through the face flux: one
+// evaluation of the Roe flux keeps its intermediates and a hand-written reverse
+// sweep gives (dF/dW_L)^T Fbar and (dF/dW_R)^T Fbar for the reconstructed
+// left/right primitive states; the central viscous flux is reversed by hand
+// too.  Each face stores the adjoints of
 // its MUSCL states and of its viscous inputs.  Pass 2 (one thread per cell)
 // gathers, in a fixed order, the contributions of the faces whose stencils
 // contain the cell (MUSCL reaches two cells along the normal, the viscous
@@ -19,6 +20,8 @@
 // ROK step reverse: the step is recomputed from y_n (its stage vectors, basis,
 // Hessenberg matrix and stage solutions stay in the context), then every
 // statement is reversed in the opposite order; eps is a constant of the step.
+// The reverse Gram-Schmidt passes of one Arnoldi column run as one cooperative
+// launch where the device allows it (pass by pass otherwise).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
