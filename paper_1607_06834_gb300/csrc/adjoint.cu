@@ -534,50 +534,72 @@ struct GamRowA {
 //   cbar = V^T kbar_i (tree of the CTA partials pc[m * P + b]);
 //   lambda_i = L^{-1} rhs_i, L = I - h g H (LU with row interchanges from the step);
 //   rhs_i = h phi_i + h H acc_i, acc_i = sum_{j<i} gamma_ij lambda_j.
-__global__ void stage_rev_kernel(int stage, GamRowA gr, const double *pc, int P, const StepState *st, AdjState *as)
+__global__ void __launch_bounds__(AT) stage_rev_kernel(int stage, GamRowA gr, const double *pc, int P,
+                                                       const StepState *st, AdjState *as)
 {
     const int m = st->meff;
     const double h = st->h, hg = st->hg;
-    __shared__ double cb[kMaxKrylov], z[kMaxKrylov], acc[kMaxKrylov];
-    for (int q = threadIdx.x >> 5; q < m; q += blockDim.x >> 5) {
+    const int tid = threadIdx.x;
+    __shared__ double cb[kMaxKrylov], z[kMaxKrylov], acc[kMaxKrylov], lam[kMaxKrylov];
+    __shared__ double A[kMaxKrylov * kMaxKrylov];
+    for (int q = tid >> 5; q < m; q += blockDim.x >> 5) {
         const double v = warp_tree_partials(pc + (size_t)q * P, P);
-        if ((threadIdx.x & 31) == 0) cb[q] = v;
+        if ((tid & 31) == 0) cb[q] = v;
     }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    double *lamb = as->lamb[stage];
-    double *phib = as->phib[stage];
-    for (int q = 0; q < m; ++q) {
-        lamb[q] += cb[q];
-        phib[q] = -h * cb[q];
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+        const int r = idx / m, q = idx % m;
+        A[r * kMaxKrylov + q] = st->LU[r * kMaxKrylov + q];
     }
-    // z = L^{-T} lamb: U^T s = lamb, L^T t = s, then the interchanges in reverse order
-    const double *A = st->LU;
-    for (int r = 0; r < m; ++r) {
-        double s = lamb[r];
-        for (int k = 0; k < r; ++k) s = s - A[k * kMaxKrylov + r] * z[k];
-        z[r] = s / A[r * kMaxKrylov + r];
-    }
-    for (int r = m - 1; r >= 0; --r) {
-        double s = z[r];
-        for (int k = r + 1; k < m; ++k) s = s - A[k * kMaxKrylov + r] * z[k];
-        z[r] = s;
-    }
-    for (int k = m - 1; k >= 0; --k) {
-        const int p = st->piv[k];
-        if (p != k) { double tmp = z[k]; z[k] = z[p]; z[p] = tmp; }
-    }
-    for (int q = 0; q < m; ++q) {
+    for (int q = tid; q < m; q += blockDim.x) {
         double a = 0.0;
         for (int jj = 0; jj < stage; ++jj) a = a + gr.g[jj] * st->lam[jj][q];
         acc[q] = a;
+        lam[q] = st->lam[stage][q];
     }
+    __syncthreads();
+    double *lamb = as->lamb[stage];
+    double *phib = as->phib[stage];
+    for (int q = tid; q < m; q += blockDim.x) {
+        const double l = lamb[q] + cb[q];
+        lamb[q] = l;
+        z[q] = l;
+        phib[q] = -h * cb[q];
+    }
+    __syncthreads();
+    // z = L^{-T} lamb: U^T s = lamb, L^T t = s, then the interchanges in reverse
+    // order; one warp, column by column (lane l holds rows l and l + 32)
+    if (tid < 32) {
+        const int r0 = tid, r1 = tid + 32;
+        double s0 = r0 < m ? z[r0] : 0.0, s1 = r1 < m ? z[r1] : 0.0;
+        for (int k = 0; k < m; ++k) {   // U^T: row r needs z_k for k < r, ascending k
+            if (r0 == k) s0 = s0 / A[k * kMaxKrylov + k];
+            if (r1 == k) s1 = s1 / A[k * kMaxKrylov + k];
+            const double zk = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
+            if (r0 > k && r0 < m) s0 = s0 - A[k * kMaxKrylov + r0] * zk;
+            if (r1 > k && r1 < m) s1 = s1 - A[k * kMaxKrylov + r1] * zk;
+        }
+        for (int k = m - 1; k > 0; --k) {   // L^T (unit): row r needs z_k for k > r
+            const double zk = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
+            if (r0 < k) s0 = s0 - A[k * kMaxKrylov + r0] * zk;
+            if (r1 < k) s1 = s1 - A[k * kMaxKrylov + r1] * zk;
+        }
+        if (r0 < m) z[r0] = s0;
+        if (r1 < m) z[r1] = s1;
+        __syncwarp();
+        if (tid == 0)
+            for (int k = m - 1; k >= 0; --k) {
+                const int p = st->piv[k];
+                if (p != k) { double tmp = z[k]; z[k] = z[p]; z[p] = tmp; }
+            }
+    }
+    __syncthreads();
     // H_bar += h g z lambda_i^T + h z acc_i^T ; phi_bar += h z ; acc_bar = h H^T z
-    for (int r = 0; r < m; ++r)
-        for (int q = 0; q < m; ++q)
-            as->Hb[r * kMaxKrylov + q] += hg * z[r] * st->lam[stage][q] + h * z[r] * acc[q];
-    for (int q = 0; q < m; ++q) phib[q] += h * z[q];
-    for (int q = 0; q < m; ++q) {
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+        const int r = idx / m, q = idx % m;
+        as->Hb[r * kMaxKrylov + q] += hg * z[r] * lam[q] + h * z[r] * acc[q];
+    }
+    for (int q = tid; q < m; q += blockDim.x) {
+        phib[q] += h * z[q];
         double a = 0.0;
         for (int r = 0; r < m; ++r) a = a + st->H[r * kMaxKrylov + q] * z[r];
         const double accb = h * a;
