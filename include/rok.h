@@ -163,6 +163,16 @@ rok_status rok_sync(rok_ctx *ctx, rok_step_info *info);
  * kernel by kernel (0, default). */
 rok_status rok_set_graph(rok_ctx *ctx, int enable);
 
+/* Modified Gram-Schmidt of the Arnoldi process (Sec. 2.3.3) and its reverse in
+ * rok_step_vjp: one persistent cooperative launch per Krylov column where the
+ * device holds the whole grid (1, default), or one launch per pass (0) -- the
+ * path that grids beyond the persistent kernels' reach (more than 2 x 2048
+ * entries per co-resident CTA) always take.  Both compute the same sums in
+ * the same order.  Synchronises the context stream and drops its captured
+ * step graphs.  ROK_ERR_UNSUPPORTED for 0 with the binary32 basis, which runs
+ * on the persistent kernel only. */
+rok_status rok_set_persistent(rok_ctx *ctx, int enable);
+
 /* Kernel launch counter (all kernels this context launched) and, when
  * timing is on, the accumulated device time of the residual/JVP stencil
  * launches measured with CUDA events on the context stream. */

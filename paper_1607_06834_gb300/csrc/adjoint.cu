@@ -654,9 +654,7 @@ __global__ void __launch_bounds__(RT) mgsrev_kernel(double *__restrict__ wb, dou
     store8(Vbi, e0, n, g);
     if (vprev) {
         load8(vprev, e0, n, x);
-#pragma unroll
-        for (int k = 0; k < EPL; ++k) x[k] = x[k] * w[k];
-        const double s = chunk_sum(x, sh);
+        const double s = chunk_sumv(lane_dot(x, w), sh);   // <v_{i-1}, wbar>
         if (threadIdx.x == 0) pout[blockIdx.x] = s;
     }
 }
@@ -664,9 +662,10 @@ __global__ void __launch_bounds__(RT) mgsrev_kernel(double *__restrict__ wb, dou
 // The j+1 reverse passes of mgsrev_kernel for Arnoldi column j in one
 // cooperative launch (the mirror of arnoldi_column_kernel: the adjoint wbar and
 // w stay in registers, v_i is carried from one pass to the next, a bounded grid
-// barrier between passes).  On entry wb holds the adjoint of w_{j+1} and wcur =
-// w_{j+1}; on exit wb holds the adjoint of w_0 = J v_j (wcur is not updated).
-// The same arithmetic as the pass-by-pass kernels.
+// barrier between passes).  On entry wb holds the adjoint of w_{j+1}, wcur =
+// w_{j+1} and partA the chunk partials of <v_j, wbar> (dot2, as on the
+// pass-by-pass path); on exit wb holds the adjoint of w_0 = J v_j (wcur is not
+// updated).  The same arithmetic as the pass-by-pass kernels.
 __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict__ wb, const double *__restrict__ wcur,
                                                               double *__restrict__ Vb, const double *__restrict__ V,
                                                               size_t ldv, size_t n, int j, int P, double *partA,
@@ -684,23 +683,13 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
         const int blk = blockIdx.x + c * G;
         have[c] = blk < P;
         e0[c] = ((size_t)blk * RT + threadIdx.x) * EPL;
-        x[c] = 0.0;
         if (have[c]) {
             load8(wb, e0[c], n, b[c]);
             load8(wcur, e0[c], n, w[c]);
             load8(V + (size_t)j * ldv, e0[c], n, v[c]);
-            x[c] = lane_dot(v[c], b[c]);   // <v_j, wbar>
         }
     }
     double sa, sb;
-    if (have[1]) {   // uniform per CTA
-        chunk_sum2v(x[0], x[1], sh, sa, sb);
-    } else {
-        sa = chunk_sumv(x[0], sh);
-    }
-    if (threadIdx.x == 0) partA[blockIdx.x] = sa;
-    if (threadIdx.x == 8 && have[1]) partA[blockIdx.x + G] = sb;
-    if (!grid_barrier(bar, G, &st->status)) return;
     double *pin = partA, *pout = partB;
     for (int i = j; i >= 0; --i) {
         const double d = tree_partials(pin, P, sh);
@@ -1002,7 +991,9 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
             }
             if (A->rev_ctas < 0) A->rev_ctas = rev_column_ctas();
             const int G = P < A->rev_ctas ? P : A->rev_ctas;
-            if (G > 0 && (P + G - 1) / G <= kColChunks) {
+            CU(ops.dot2(vj, A->wb, nullptr, nullptr, N, A->pA, P, nullptr, s));
+            c->launches++;
+            if (c->persistent && G > 0 && (P + G - 1) / G <= kColChunks) {
                 // all j + 1 reverse passes in one cooperative launch
                 double *wbp = A->wb, *pa = A->pA, *pb = A->pB;
                 const double *wcp = A->wcur, *Vp = c->V;
@@ -1016,8 +1007,6 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
                 CU(cudaLaunchCooperativeKernel((const void *)mgsrev_column_kernel, dim3(G), dim3(RT), args, 0, s));
                 c->launches++;
             } else {
-                CU(ops.dot2(vj, A->wb, nullptr, nullptr, N, A->pA, P, nullptr, s));
-                c->launches++;
                 double *pin = A->pA, *pout = A->pB;
                 for (int i = j; i >= 0; --i) {
                     const double *vi = c->V + (size_t)i * N;

@@ -309,7 +309,7 @@ rok_status arnoldi_columns(rok_ctx *c, const double *y, int M)
         io.active = &st->active;
         if ((r = stencil(c, io)) != ROK_OK) return r;
         cudaError_t e = cudaErrorNotSupported;
-        if (c->col_ctas > 0)
+        if (c->col_ctas > 0 && c->persistent)
             e = c->ops->arnoldi_column(c->w, Vb, c->fp32 ? 1 : 0, N, N, j, j + 1 < M ? 1 : 0, P, c->pA, c->pB,
                                        c->bar, st, c->col_ctas, s);
         if (e == cudaSuccess) {
@@ -593,6 +593,18 @@ rok_status rok_destroy(rok_ctx *c)
     if (!c) return ROK_OK;
     cudaStreamSynchronize(c->stream);
     free_ctx(c);
+    return ROK_OK;
+}
+
+rok_status rok_set_persistent(rok_ctx *c, int enable)
+{
+    if (!c) return ROK_ERR_INVALID_ARG;
+    if (c->fp32 && !enable) return ROK_ERR_UNSUPPORTED;   // the binary32 basis needs the column kernel
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ROK_ERR_CUDA;
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    c->graph_launches.clear();
+    c->persistent = enable != 0;
     return ROK_OK;
 }
 

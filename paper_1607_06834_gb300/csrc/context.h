@@ -39,6 +39,7 @@ struct rok_ctx {
     StepState *st = nullptr;
     GridBarrier *bar = nullptr; // grid barrier of the persistent Arnoldi column kernel
     int col_ctas = 0;           // co-resident CTAs of that kernel (0: multi-kernel path)
+    bool persistent = true;     // use the persistent column kernels where they fit
     StepState *h_st = nullptr;  // pinned mirror
     double *h_part = nullptr;   // pinned, >= 2P
     // curvilinear geometry (device)

@@ -350,16 +350,12 @@ __global__ void __launch_bounds__(RT) dot2_kernel(const double *__restrict__ a0,
     double x[EPL], y[EPL];
     load8(a0, e0, n, x);
     load8(b0, e0, n, y);
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) x[k] = x[k] * y[k];
-    double s0 = chunk_sum(x, sh);
+    double s0 = chunk_sumv(lane_dot(x, y), sh);
     double s1 = 0.0;
     if (a1) {
         load8(a1, e0, n, x);
         load8(b1, e0, n, y);
-#pragma unroll
-        for (int k = 0; k < EPL; ++k) x[k] = x[k] * y[k];
-        s1 = chunk_sum(x, sh);
+        s1 = chunk_sumv(lane_dot(x, y), sh);
     }
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = s0;

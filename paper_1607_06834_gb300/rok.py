@@ -110,6 +110,7 @@ _sig = {
     'rok_dt_from_cfl': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     'rok_sync': (ctypes.c_int, [_vp, ctypes.POINTER(StepInfo)]),
     'rok_set_graph': (ctypes.c_int, [_vp, ctypes.c_int]),
+    'rok_set_persistent': (ctypes.c_int, [_vp, ctypes.c_int]),
     'rok_get_counters': (ctypes.c_int, [_vp, ctypes.POINTER(Counters), ctypes.c_int]),
     'rok_set_stencil_timing': (ctypes.c_int, [_vp, ctypes.c_int]),
     'rok_status_string': (ctypes.c_char_p, [ctypes.c_int]),
@@ -299,6 +300,13 @@ def rok_sync(ctx):
 
 def rok_set_graph(ctx, enable):
     _check(_lib.rok_set_graph(ctx.handle, int(bool(enable))), 'rok_set_graph')
+
+
+def rok_set_persistent(ctx, enable):
+    """``rok_set_persistent``: one cooperative launch per Arnoldi column (and
+    per reverse column) where it fits (True, default) or one launch per
+    Gram-Schmidt pass (False)."""
+    _check(_lib.rok_set_persistent(ctx.handle, int(bool(enable))), 'rok_set_persistent')
 
 
 def rok_get_counters(ctx, reset=False):

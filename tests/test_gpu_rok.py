@@ -369,3 +369,39 @@ def test_cylinder_full_size_one_step_strict_bitexact(rok):
         assert info['m_eff'] == 30
         yo = I.rok_step(sys_, y0, h, 30, basis=npb)
         assert np.array_equal(host(y), yo), (basis, rel_l2(host(y), yo))
+
+
+@pytest.mark.parametrize('mode', ['strict', 'fast'])
+def test_persistent_and_pass_by_pass_gram_schmidt_agree(rok, mode):
+    # one ROK4 step and its reverse, with the Gram-Schmidt passes of each Krylov
+    # column in one cooperative launch and with one launch per pass (the path of
+    # grids beyond the cooperative kernels' reach): the same sums in the same
+    # order, so the same bits; strict rounding also equals the oracle's step
+    prob, y0 = W.taylor_green(48, reynolds=300.0)
+    y0 = np.ascontiguousarray(y0 + 0.01 * W.random_smooth_state(prob, seed=7))
+    h = I.dt_from_cfl(prob, y0, 4.0)
+    M = 10
+    c = np.random.default_rng(4).standard_normal(y0.shape)
+    res = []
+    for persistent in (True, False):
+        ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+        rok.rok_set_persistent(ctx, persistent)
+        y = dev(y0)
+        rok.rok_step(ctx, y, h, M)
+        yb, mub = rok.rok_step_vjp(ctx, dev(y0), h, M, dev(c))
+        res.append((host(y), host(yb), mub))
+    (ya, yba, ma), (yp, ybp, mp) = res
+    assert np.array_equal(ya, yp)
+    assert np.array_equal(yba, ybp)
+    assert ma == mp
+    if mode == 'strict':
+        assert np.array_equal(ya, I.rok_step(core.System(prob), y0, h, M))
+
+
+def test_persistent_switch_refused_for_binary32_basis(rok):
+    prob, y0 = W.isentropic_vortex(32)
+    ctx = rok.rok_init(prob, krylov_max=8, basis=rok.ROK_BASIS_FP32)
+    with pytest.raises(rok.RokError) as e:
+        rok.rok_set_persistent(ctx, False)
+    assert e.value.status == rok.ROK_ERR_UNSUPPORTED
+    rok.rok_set_persistent(ctx, True)
