@@ -247,6 +247,14 @@ def run_ours(args):
     esd = rok.esdirk_step(ctx, yc, h, info=True)
     barrier()
     esd_ms = (time.perf_counter() - t0) * 1e3
+    ros = {}
+    for name, meth in (('ros4', rok.ROK_ROS_ROS4), ('row', rok.ROK_ROS_ROW)):
+        yc = rok.state_tensor(y0)
+        barrier()
+        t0 = time.perf_counter()
+        inf = rok.ros_step(ctx, yc, h, method=meth, info=True)
+        barrier()
+        ros[name] = ((time.perf_counter() - t0) * 1e3, inf)
 
     # the mixed-precision form (binary32 basis and Gram-Schmidt) on the same steps:
     # time per step and its difference from the binary64 form after the same steps
@@ -330,7 +338,9 @@ def run_ours(args):
                 'd2h_bytes_per_step': int(y0.nbytes)},
         'gpu_launches': int(cnt['launches']),
         'comparators': {'rk4_ms_per_step_cfl1': round(rk_ms, 4), 'rk4_dt': h_rk,
-                        'esdirk3_ms_per_step_cfl8': round(esd_ms, 2), 'esdirk3_info': esd},
+                        'esdirk3_ms_per_step_cfl8': round(esd_ms, 2), 'esdirk3_info': esd,
+                        'ros4_ms_per_step_cfl8': round(ros['ros4'][0], 2), 'ros4_info': ros['ros4'][1],
+                        'row_ms_per_step_cfl8': round(ros['row'][0], 2), 'row_info': ros['row'][1]},
         'wall_s_timed': round(wall, 3),
         'forms': forms,
     }
@@ -843,6 +853,14 @@ def run_tte(args):
                                                 'newton_iters': sum(i['newton_iters'] for i in infos)})
         except (rok.RokError, TimeoutError) as err:
             out['methods'].setdefault('ESDIRK3', []).append({'cfl': c, 'failed': str(err)})
+    for name, meth in (('ROS4', rok.ROK_ROS_ROS4), ('ROW', rok.ROK_ROS_ROW)):
+        for c in cfls:
+            try:
+                y, n, h, gs, ws, infos = integrate(lambda y, h: rok.ros_step(ctx, y, h, method=meth, info=True),
+                                                   c * dt_unit, cap_s=args.esdirk_cap)
+                record(name, y, n, h, gs, ws, {'cfl': c, 'gmres_iters': sum(i['gmres_iters'] for i in infos)})
+            except (rok.RokError, TimeoutError) as err:
+                out['methods'].setdefault(name, []).append({'cfl': c, 'failed': str(err)})
     out['time_to_error'] = {}
     for tgt in (1e-4, 1e-6, 1e-8, 1e-10):
         row = {}

@@ -88,7 +88,7 @@ typedef struct {
     int residual_evals;  /* f evaluations, JVPs included                               */
     int jvps;            /* Jacobian-vector products                                   */
     int newton_iters;    /* ESDIRK: Newton iterations, all stages                      */
-    int gmres_iters;     /* ESDIRK: GMRES iterations, all Newton steps                 */
+    int gmres_iters;     /* ESDIRK, ROS4/ROW: GMRES iterations of the step             */
     double eps;          /* finite-difference increment used (Eq. matvecFD)            */
 } rok_step_info;
 
@@ -148,6 +148,24 @@ rok_status rk_step(rok_ctx *ctx, double *y, double h, rok_step_info *info);
  * with matrix-free Newton-GMRES, y in place.  opts NULL = (30, 1e-6, 5,
  * 1e-10, 10).  Host-driven: synchronises the stream every GMRES iteration. */
 rok_status esdirk_step(rok_ctx *ctx, double *y, double h, const esdirk_opts *opts, rok_step_info *info);
+
+/* One Rosenbrock step (Sec. 2.3, Eq. ROS), the paper's ROS4 and ROW
+ * comparators (table of methods, Sec. 3.1):
+ *   Y_i = y_n + h sum_{j<i} alpha_ij k_j,
+ *   (I - h g J_n) k_i = f(Y_i) + h J_n sum_{j<i} gamma_ij k_j   (Eq. ROS_stage_eq),
+ *   y_{n+1} = y_n + h sum_j b_j k_j,
+ * matrix-free: J_n at y_n by Eq. matvecFD (or exactly with ROK_JVP_EXACT),
+ * each stage system by GMRES(m) from 0 with the GMRES fields of opts
+ * (gmres_m <= krylov_max, gmres_tol, gmres_restarts; the Newton fields are
+ * ignored; NULL: m = 30, tol 1e-6, 5 restarts).  method: ROK_ROS_ROS4 (the
+ * L-stable order-4 method of Hairer & Wanner IV.7) or ROK_ROS_ROW
+ * (ROS34PW2 of Rang & Angermann, order 3 for any Jacobian approximation).
+ * Device y in/out, untouched unless every stage system converged
+ * (ROK_ERR_NOT_CONVERGED otherwise) and every value is finite.  info:
+ * GMRES iterations, Jacobian-vector products, residual evaluations.
+ * Synchronises (GMRES decisions on the host). */
+enum { ROK_ROS_ROS4 = 0, ROK_ROS_ROW = 1 };
+rok_status ros_step(rok_ctx *ctx, double *y, double h, int method, const esdirk_opts *opts, rok_step_info *info);
 
 /* Time step for a CFL number: dt = cfl / max over cells of
  * (|u.S_i| + c|S_i|)/Vol + (|u.S_j| + c|S_j|)/Vol + 2 nu_eff (|S_i|^2 + |S_j|^2)/Vol^2

@@ -62,6 +62,26 @@ The Dormand-Prince 5(4) pair (Dormand & Prince, J. Comput. Appl. Math. 6,
 1980), 7 stages, first-same-as-last, written here as exact rationals; the
 order conditions it satisfies are checked in the oracle's tests.
 
+ROS4 and ROW (Rosenbrock comparators, Sec. 2.3, Eq. ROS)
+---------------------------------------------------------
+The paper's ROS4 is a 4-stage, order-4, L-stable Rosenbrock method and its
+ROW a 4-stage, order-3, L-stable Rosenbrock-W method (table of methods,
+Sec. 3.1); it cites Hairer & Wanner IV.7 for the former and Rang &
+Angermann (BIT 45, 2005) for W-methods.  Tables used here:
+  * ROS4: the L-stable method of Hairer & Wanner (Solving ODEs II, Sec. IV.7,
+    g = 0.57282), whose coefficients are published for the implementation
+    form (1/(h g) I - J) u_i = f(y + sum a_ij u_j) + sum (c_ij / h) u_j,
+    y_1 = y_0 + sum m_j u_j.  Eq. ROS is recovered exactly (rational
+    arithmetic on the published decimals): Gamma = (diag(1/g) - C)^{-1},
+    alpha = A Gamma, b = m Gamma (the paper's stages are h-free: k = u / h
+    combinations, so alpha and gamma carry over unchanged).
+  * ROW: ROS34PW2 of Rang & Angermann, published in the form of Eq. ROS
+    (g = 0.435866521508459, the root of 6x^3 - 18x^2 + 9x - 1 in (0.4, 0.5)),
+    with its embedded order-2 weights.
+The oracle's tests check the order conditions (8 for ROS4, the classical
+order-3 set for ROW), L-stability, and the orders reached on Lorenz-96,
+for ROW also with a wrong Jacobian (the W-property).
+
 Run ``python oracle/derive_coefficients.py`` to regenerate the table file.
 """
 import os
@@ -151,6 +171,47 @@ def dopri5():
     return dict(A=A, b=b, bhat=bhat, c=[sum(r) for r in A])
 
 
+def ros4():
+    F = sp.Rational
+    g = F('0.57282')
+    A = sp.zeros(4, 4)
+    C = sp.zeros(4, 4)
+    A[1, 0] = F('2.000000000000000')
+    A[2, 0] = F('1.867943637803922')
+    A[2, 1] = F('0.2344449711399156')
+    A[3, 0], A[3, 1], A[3, 2] = A[2, 0], A[2, 1], 0
+    C[1, 0] = F('-7.137615036412310')
+    C[2, 0] = F('2.580708087951457')
+    C[2, 1] = F('0.6515950076447975')
+    C[3, 0] = F('-2.137148994382534')
+    C[3, 1] = F('-0.3214669691237626')
+    C[3, 2] = F('-0.6949742501781779')
+    m = sp.Matrix([[F('2.255570073418735'), F('0.2870493262186792'), F('0.4353179431840180'),
+                    F('1.093502252409163')]])
+    Gam = (sp.eye(4) / g - C).inv()
+    alpha = A * Gam
+    b = m * Gam
+    off = [[Gam[i, j] if j < i else 0 for j in range(4)] for i in range(4)]
+    return dict(gamma=g, alpha=[[alpha[i, j] for j in range(4)] for i in range(4)], gamma_offdiag=off,
+                b=[b[0, j] for j in range(4)])
+
+
+def row():
+    F = sp.Rational
+    g = F('0.43586652150845900')
+    al = [[0, 0, 0, 0],
+          [F('0.87173304301691801'), 0, 0, 0],
+          [F('0.84457060015369423'), F('-0.11299064236484185'), 0, 0],
+          [0, 0, 1, 0]]
+    ga = [[0, 0, 0, 0],
+          [F('-0.87173304301691801'), 0, 0, 0],
+          [F('-0.90338057013044082'), F('0.054180672388095326'), 0, 0],
+          [F('0.24212380706095346'), F('-1.2232505839045147'), F('0.54526025533510214'), 0]]
+    b = [F('0.24212380706095346'), F('-1.2232505839045147'), F('1.5452602553351020'), F('0.43586652150845900')]
+    bhat = [F('0.37810903145819369'), F('-0.096042292212423178'), F('0.5'), F('0.21793326075422950')]
+    return dict(gamma=g, alpha=al, gamma_offdiag=ga, b=b, bhat=bhat)
+
+
 def fmt(v):
     return repr(float(v))
 
@@ -159,6 +220,8 @@ def main():
     r = rok4()
     e = esdirk3()
     d = dopri5()
+    ro = ros4()
+    rw = row()
     lines = [
         '"""Method coefficient tables of the oracle (binary64).',
         '',
@@ -195,6 +258,21 @@ def main():
         'DOPRI5_A_EXACT = ' + repr([[str(v) for v in row] for row in d['A']]),
         'DOPRI5_B_EXACT = ' + repr([str(v) for v in d['b']]),
         'DOPRI5_BHAT_EXACT = ' + repr([str(v) for v in d['bhat']]),
+        '',
+        '# ROS4: L-stable Rosenbrock method of order 4 (Hairer & Wanner), Eq. ROS form',
+        'ROS4_GAMMA = ' + fmt(ro['gamma']),
+        'ROS4_ALPHA = [' + ', '.join('[' + ', '.join(fmt(v) for v in row) + ']' for row in ro['alpha']) + ']',
+        'ROS4_GAMMA_OFFDIAG = [' + ', '.join('[' + ', '.join(fmt(v) for v in row) + ']'
+                                           for row in ro['gamma_offdiag']) + ']',
+        'ROS4_B = [' + ', '.join(fmt(v) for v in ro['b']) + ']',
+        '',
+        '# ROW: ROS34PW2 (Rang & Angermann), Rosenbrock-W method of order 3, Eq. ROS form',
+        'ROW_GAMMA = ' + fmt(rw['gamma']),
+        'ROW_ALPHA = [' + ', '.join('[' + ', '.join(fmt(v) for v in row) + ']' for row in rw['alpha']) + ']',
+        'ROW_GAMMA_OFFDIAG = [' + ', '.join('[' + ', '.join(fmt(v) for v in row) + ']'
+                                          for row in rw['gamma_offdiag']) + ']',
+        'ROW_B = [' + ', '.join(fmt(v) for v in rw['b']) + ']',
+        'ROW_BHAT = [' + ', '.join(fmt(v) for v in rw['bhat']) + ']',
         '',
     ]
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'coefficients.py')

@@ -453,6 +453,66 @@ def esdirk_step(sys, y, h, gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, newton_
     return ynew.reshape(shape)
 
 
+def ros_step(sys, y, h, method='ros4', gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, info=None):
+    """Rosenbrock step, Sec. 2.3, Eq. ROS (method 'ros4') or Rosenbrock-W step
+    of the same form (method 'row'):
+        Y_i = y_n + h sum_{j<i} alpha_ij k_j,
+        (I - h g J_n) k_i = f(Y_i) + h J_n sum_{j<i} gamma_ij k_j   (Eq. ROS_stage_eq),
+        y_{n+1} = y_n + h sum_j b_j k_j,
+    J_n at y_n applied by Eq. matvecFD (eps from ||y_n||), every stage system
+    solved by GMRES(m) from x0 = 0 (the matrix-free setting of the paper's
+    experiments).  Reading: the J_n term of the right-hand side is one more
+    Jacobian-vector product per stage (skipped when all gamma_ij of the stage
+    vanish)."""
+    if method == 'ros4':
+        al, ga, b, g = np.array(C.ROS4_ALPHA), np.array(C.ROS4_GAMMA_OFFDIAG), np.array(C.ROS4_B), C.ROS4_GAMMA
+    elif method == 'row':
+        al, ga, b, g = np.array(C.ROW_ALPHA), np.array(C.ROW_GAMMA_OFFDIAG), np.array(C.ROW_B), C.ROW_GAMMA
+    else:
+        raise ValueError(method)
+    shape = y.shape
+    yf = y.ravel()
+    F0 = np.asarray(sys.f(y)).ravel()
+    eps = fd_eps(float(np.linalg.norm(yf)))
+
+    def jv(v):
+        return np.asarray(sys.jvp(y, v.reshape(shape), F0.reshape(shape), eps)).ravel()
+
+    def op(v):
+        return v - (h * g) * jv(v)
+
+    ks = []
+    gmres_its, ok = 0, True
+    for i in range(len(b)):
+        if i == 0:
+            rhs = F0.copy()
+        else:
+            Yi = yf.copy()
+            for j in range(i):
+                if al[i, j] != 0.0:
+                    Yi = Yi + (h * al[i, j]) * ks[j]
+            rhs = np.asarray(sys.f(Yi.reshape(shape))).ravel()
+            u = np.zeros_like(yf)
+            any_g = False
+            for j in range(i):
+                if ga[i, j] != 0.0:
+                    u = u + ga[i, j] * ks[j]
+                    any_g = True
+            if any_g:
+                rhs = rhs + h * jv(u)
+        k, its, conv = gmres(op, rhs, gmres_m, gmres_tol, gmres_restarts)
+        gmres_its += its
+        ok = ok and conv
+        ks.append(k)
+    acc = np.zeros_like(yf)
+    for j in range(len(b)):
+        acc = acc + b[j] * ks[j]
+    ynew = yf + h * acc
+    if info is not None:
+        info.update(gmres_iters=gmres_its, converged=ok, eps=eps)
+    return ynew.reshape(shape)
+
+
 def dt_from_cfl(prob, y, cfl):
     """Time step from a CFL number (the paper does not define one).  Reading:
     dt = CFL / max_cells [ (|u.S_i| + c|S_i|)/Vol + (|u.S_j| + c|S_j|)/Vol

@@ -765,14 +765,120 @@ rok_status rk_step(rok_ctx *c, double *y, double h, rok_step_info *info)
     return ROK_OK;
 }
 
+// x = (I - hg J_n)^{-1} rhs by restarted GMRES(m) from x0 = 0 (modified
+// Gram-Schmidt Arnoldi on the device, Givens rotations of the small
+// Hessenberg system on the host, stop at ||rhs - op(x)|| <= tol ||rhs||);
+// J_n at y applied by the FD product with base F0 = f(y) (or exactly).  Uses
+// c->V, c->H, c->w and c->F[1] as workspace; rhs and x must be other buffers.
+static rok_status gmres_solve(rok_ctx *c, const double *y, const double *F0, double hg, const double *rhs,
+                              double *x, const esdirk_opts &op, int *its_out, bool *conv_out, int *jvps,
+                              int *res_evals)
+{
+    const size_t N = c->N;
+    const int P = c->P;
+    StepState *st = c->st;
+    cudaStream_t s = c->stream;
+    double *wv = c->w;
+    rok_status r, err = ROK_OK;
+    // op(v) = v - h g J_n v into out
+    auto apply_op = [&](const double *v, double *out) -> rok_status {
+        StencilIO io;
+        if (c->exact_jvp) {
+            io = io_plain(c, y, out);
+            io.dir = v;
+        } else {
+            io = io_jvp(c, y, v, F0, out);
+        }
+        io.add_out = v;
+        io.s2 = -hg;
+        (*jvps)++;
+        (*res_evals)++;
+        return stencil(c, io);
+    };
+    CU(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    double bnorm = host_norm(c, rhs, &err);
+    if (err) return err;
+    int its = 0;
+    bool conv = bnorm == 0.0;
+    if (bnorm > 0.0) {
+        for (int cycle = 0; cycle <= op.gmres_restarts; ++cycle) {
+            // r0 = rhs - op(x)
+            const double *r0 = rhs;
+            if (its > 0) {
+                if ((r = apply_op(x, wv)) != ROK_OK) return r;
+                const double *vv[1] = {wv};
+                double cc[1] = {-1.0};
+                CU(c->ops->axpy_n(c->F[1], rhs, vv, cc, 1, N, nullptr, c->egrid, s));
+                c->launches++;
+                r0 = c->F[1];
+            }
+            double beta = host_norm(c, r0, &err);
+            if (err) return err;
+            if (beta <= op.gmres_tol * bnorm) { conv = true; break; }
+            // v_0 = r0 / beta
+            CU(launch_set_int(&st->active, 1, s));
+            CU(c->ops->dot2(r0, r0, nullptr, nullptr, N, c->pA, P, nullptr, s));
+            CU(c->ops->normalize(r0, c->V, N, c->pA, P, nullptr, 0, st, s));
+            c->launches += 3;
+            Givens gv;
+            gv.reset(op.gmres_m, beta);
+            int k_used = 0;
+            bool done = false;
+            for (int j = 0; j < op.gmres_m; ++j) {
+                if ((r = apply_op(c->V + (size_t)j * N, wv)) != ROK_OK) return r;
+                CU(c->ops->dot2(c->V, wv, wv, wv, N, c->pA, P, nullptr, s));
+                double *pin = c->pA, *pout = c->pB;
+                for (int q = 1; q <= j + 1; ++q) {
+                    const double *vnext = q <= j ? c->V + (size_t)q * N : nullptr;
+                    CU(c->ops->mgs(wv, c->V + (size_t)(q - 1) * N, vnext, N, pin, P,
+                                  &st->H[(q - 1) * kMaxKrylov + j], pout, q == 1, st, s));
+                    double *t = pin; pin = pout; pout = t;
+                }
+                c->launches += 2 + j;
+                // h_{j+1,j} = ||w||; v_{j+1} = w / h_{j+1,j}
+                CU(cudaMemcpyAsync(c->h_part, pin, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+                CU(c->ops->normalize(wv, c->V + (size_t)(j + 1) * N, N, pin, P,
+                                    &st->H[(j + 1) * kMaxKrylov + j], j + 1, st, s));
+                CU(cudaMemcpyAsync(&c->h_st->active, &st->active, sizeof(int), cudaMemcpyDeviceToHost, s));
+                c->launches++;
+                double hc[kMaxKrylov + 1];
+                CU(cudaMemcpy2DAsync(hc, sizeof(double), &st->H[j], kMaxKrylov * sizeof(double), sizeof(double),
+                                     j + 1, cudaMemcpyDeviceToHost, s));
+                CU(cudaStreamSynchronize(s));
+                hc[j + 1] = sqrt(host_tree(c->h_part, P));
+                its++;
+                double res = gv.add(j, hc);
+                k_used = j + 1;
+                if (res <= op.gmres_tol * bnorm || c->h_st->active == 0) { done = true; break; }
+            }
+            std::vector<double> yv(k_used);
+            gv.solve(k_used, yv.data());
+            CU(cudaMemcpyAsync(st->gcoef, yv.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
+            CU(c->ops->basis_combine(x, x, c->V, N, N, k_used, st->gcoef, c->egrid, s));
+            CU(cudaStreamSynchronize(s));
+            c->launches++;
+            if (done) { conv = true; break; }
+        }
+    }
+    *its_out = its;
+    *conv_out = conv;
+    return ROK_OK;
+}
+
+static rok_status check_gmres_opts(const rok_ctx *c, const esdirk_opts &op)
+{
+    if (op.gmres_m < 1 || op.gmres_m > c->mmax || op.gmres_m > kMaxKrylov || op.gmres_restarts < 0 ||
+        op.newton_max < 1 || !(op.gmres_tol > 0.0) || !(op.newton_tol > 0.0))
+        return ROK_ERR_INVALID_ARG;
+    return ROK_OK;
+}
+
 rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, rok_step_info *info)
 {
     if (!c || !y || !(h > 0.0) || !isfinite(h)) return ROK_ERR_INVALID_ARG;
     esdirk_opts op = {30, 1e-6, 5, 1e-10, 10};
     if (o) op = *o;
-    if (op.gmres_m < 1 || op.gmres_m > c->mmax || op.gmres_m > kMaxKrylov || op.gmres_restarts < 0 ||
-        op.newton_max < 1 || !(op.gmres_tol > 0.0) || !(op.newton_tol > 0.0))
-        return ROK_ERR_INVALID_ARG;
+    if (check_gmres_opts(c, op) != ROK_OK) return ROK_ERR_INVALID_ARG;
     const size_t N = c->N;
     const int P = c->P;
     StepState *st = c->st;
@@ -787,22 +893,7 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
     CU(c->ops->eps(c->pA, P, true, 0.0, st, s));
     c->launches += 2;
     res_evals++;
-    double *xi = c->t0, *rhs = c->t1, *dk = c->t2, *wv = c->w;
-    // op(v) = v - h g J_n v into out
-    auto apply_op = [&](const double *v, double *out) -> rok_status {
-        StencilIO io;
-        if (c->exact_jvp) {
-            io = io_plain(c, y, out);
-            io.dir = v;
-        } else {
-            io = io_jvp(c, y, v, c->K[0], out);
-        }
-        io.add_out = v;
-        io.s2 = -hg;
-        jvps++;
-        res_evals++;
-        return stencil(c, io);
-    };
+    double *xi = c->t0, *rhs = c->t1, *dk = c->t2;
     for (int i = 1; i < 4; ++i) {
         // xi_i = y_n + h sum_{j<i} a_ij k_j
         const double *kv[4];
@@ -824,70 +915,10 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
             if ((r = stencil(c, io)) != ROK_OK) return r;
             res_evals++;
             // GMRES(m) for (I - h g J_n) dk = rhs, x0 = 0
-            CU(cudaMemsetAsync(dk, 0, N * sizeof(double), s));
-            double bnorm = host_norm(c, rhs, &err);
-            if (err) return err;
             int its = 0;
-            if (bnorm > 0.0) {
-                for (int cycle = 0; cycle <= op.gmres_restarts; ++cycle) {
-                    // r0 = rhs - op(dk)
-                    const double *r0 = rhs;
-                    if (its > 0) {
-                        if ((r = apply_op(dk, wv)) != ROK_OK) return r;
-                        const double *vv[1] = {wv};
-                        double cc[1] = {-1.0};
-                        CU(c->ops->axpy_n(c->F[1], rhs, vv, cc, 1, N, nullptr, c->egrid, s));
-                        c->launches++;
-                        r0 = c->F[1];
-                    }
-                    double beta = host_norm(c, r0, &err);
-                    if (err) return err;
-                    if (beta <= op.gmres_tol * bnorm) break;
-                    // v_0 = r0 / beta
-                    CU(launch_set_int(&st->active, 1, s));
-                    CU(c->ops->dot2(r0, r0, nullptr, nullptr, N, c->pA, P, nullptr, s));
-                    CU(c->ops->normalize(r0, c->V, N, c->pA, P, nullptr, 0, st, s));
-                    c->launches += 3;
-                    Givens gv;
-                    gv.reset(op.gmres_m, beta);
-                    int k_used = 0;
-                    bool done = false;
-                    for (int j = 0; j < op.gmres_m; ++j) {
-                        if ((r = apply_op(c->V + (size_t)j * N, wv)) != ROK_OK) return r;
-                        CU(c->ops->dot2(c->V, wv, wv, wv, N, c->pA, P, nullptr, s));
-                        double *pin = c->pA, *pout = c->pB;
-                        for (int q = 1; q <= j + 1; ++q) {
-                            const double *vnext = q <= j ? c->V + (size_t)q * N : nullptr;
-                            CU(c->ops->mgs(wv, c->V + (size_t)(q - 1) * N, vnext, N, pin, P,
-                                          &st->H[(q - 1) * kMaxKrylov + j], pout, q == 1, st, s));
-                            double *t = pin; pin = pout; pout = t;
-                        }
-                        c->launches += 2 + j;
-                        // h_{j+1,j} = ||w||; v_{j+1} = w / h_{j+1,j}
-                        CU(cudaMemcpyAsync(c->h_part, pin, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
-                        CU(c->ops->normalize(wv, c->V + (size_t)(j + 1) * N, N, pin, P,
-                                            &st->H[(j + 1) * kMaxKrylov + j], j + 1, st, s));
-                        CU(cudaMemcpyAsync(&c->h_st->active, &st->active, sizeof(int), cudaMemcpyDeviceToHost, s));
-                        c->launches++;
-                        double hc[kMaxKrylov + 1];
-                        CU(cudaMemcpy2DAsync(hc, sizeof(double), &st->H[j], kMaxKrylov * sizeof(double), sizeof(double),
-                                             j + 1, cudaMemcpyDeviceToHost, s));
-                        CU(cudaStreamSynchronize(s));
-                        hc[j + 1] = sqrt(host_tree(c->h_part, P));
-                        its++;
-                        double res = gv.add(j, hc);
-                        k_used = j + 1;
-                        if (res <= op.gmres_tol * bnorm || c->h_st->active == 0) { done = true; break; }
-                    }
-                    std::vector<double> yv(k_used);
-                    gv.solve(k_used, yv.data());
-                    CU(cudaMemcpyAsync(st->gcoef, yv.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
-                    CU(c->ops->basis_combine(dk, dk, c->V, N, N, k_used, st->gcoef, c->egrid, s));
-                    CU(cudaStreamSynchronize(s));
-                    c->launches++;
-                    if (done) break;
-                }
-            }
+            bool gconv = false;
+            if ((r = gmres_solve(c, y, c->K[0], hg, rhs, dk, op, &its, &gconv, &jvps, &res_evals)) != ROK_OK)
+                return r;
             gmres_total += its;
             newton_total++;
             // k += dk; test h g ||dk|| <= tol ||xi + h g k||
@@ -918,6 +949,128 @@ rok_status esdirk_step(rok_ctx *c, double *y, double h, const esdirk_opts *o, ro
     c->last.gmres_iters = gmres_total;
     rok_status rs = sync_read(c, nullptr);
     c->last.newton_iters = newton_total;
+    c->last.gmres_iters = gmres_total;
+    c->last.residual_evals = res_evals;
+    c->last.jvps = jvps;
+    if (rs == ROK_OK && !converged) rs = ROK_ERR_NOT_CONVERGED;
+    c->last.status = rs;
+    if (info) *info = c->last;
+    return rs;
+}
+
+// Coefficients of Eq. ROS for a Rosenbrock method: ROS4 is published for the
+// transformed stages u_i = h sum_j gamma_ij k_j, so Gamma = (diag(1/g) - C)^{-1}
+// (lower triangular, by substitution), alpha = A Gamma, b = m Gamma; ROW is
+// published in the form of Eq. ROS.
+static void ros_tableau(int method, double al[4][4], double ga[4][4], double b[4], double *g)
+{
+    if (method == ROK_ROS_ROW) {
+        *g = kRowGamma;
+        for (int i = 0; i < 4; ++i) {
+            b[i] = kRowB[i];
+            for (int j = 0; j < 4; ++j) {
+                al[i][j] = kRowAlpha[i][j];
+                ga[i][j] = kRowGammaOff[i][j];
+            }
+        }
+        return;
+    }
+    const double gg = kRos4Gamma;
+    double Gam[4][4] = {};
+    // columns of the inverse of L = diag(1/g) - C (lower triangular)
+    for (int col = 0; col < 4; ++col)
+        for (int i = col; i < 4; ++i) {
+            double t = i == col ? 1.0 : 0.0;
+            for (int k = col; k < i; ++k) t += kRos4C[i][k] * Gam[k][col];
+            Gam[i][col] = t * gg;
+        }
+    *g = gg;
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < 4; ++k) t += kRos4A[i][k] * Gam[k][j];
+            al[i][j] = t;
+            ga[i][j] = j < i ? Gam[i][j] : 0.0;
+        }
+        double t = 0.0;
+        for (int k = 0; k < 4; ++k) t += kRos4M[k] * Gam[k][i];
+        b[i] = t;
+    }
+}
+
+rok_status ros_step(rok_ctx *c, double *y, double h, int method, const esdirk_opts *o, rok_step_info *info)
+{
+    if (!c || !y || !(h > 0.0) || !isfinite(h)) return ROK_ERR_INVALID_ARG;
+    if (method != ROK_ROS_ROS4 && method != ROK_ROS_ROW) return ROK_ERR_INVALID_ARG;
+    esdirk_opts op = {30, 1e-6, 5, 1e-10, 10};
+    if (o) op = *o;
+    if (check_gmres_opts(c, op) != ROK_OK) return ROK_ERR_INVALID_ARG;
+    const size_t N = c->N;
+    const int P = c->P;
+    StepState *st = c->st;
+    cudaStream_t s = c->stream;
+    double al[4][4], ga[4][4], bw[4], g;
+    ros_tableau(method, al, ga, bw, &g);
+    const double hg = h * g;
+    rok_status r;
+    int gmres_total = 0, res_evals = 0, jvps = 0;
+    bool converged = true;
+    // F0 = f(y_n) (first right-hand side and base of the FD products); eps from ||y_n||
+    double *F0 = c->F[0], *xi = c->t0, *rhs = c->t1, *u = c->F[2];
+    if ((r = stencil(c, io_plain(c, y, F0))) != ROK_OK) return r;
+    CU(c->ops->dot2(y, y, nullptr, nullptr, N, c->pA, P, nullptr, s));
+    CU(c->ops->eps(c->pA, P, true, 0.0, st, s));
+    c->launches += 2;
+    res_evals++;
+    for (int i = 0; i < 4; ++i) {
+        const double *frhs = F0;
+        if (i > 0) {
+            // Y_i = y_n + h sum_{j<i} alpha_ij k_j; rhs = f(Y_i)
+            const double *kv[4];
+            double cf[4];
+            int cnt = 0;
+            for (int j = 0; j < i; ++j)
+                if (al[i][j] != 0.0) { kv[cnt] = c->K[j]; cf[cnt] = h * al[i][j]; cnt++; }
+            CU(c->ops->axpy_n(xi, y, kv, cf, cnt, N, nullptr, c->egrid, s));
+            c->launches++;
+            if ((r = stencil(c, io_plain(c, xi, rhs))) != ROK_OK) return r;
+            res_evals++;
+            // rhs += h J_n sum_{j<i} gamma_ij k_j
+            cnt = 0;
+            for (int j = 0; j < i; ++j)
+                if (ga[i][j] != 0.0) { kv[cnt] = c->K[j]; cf[cnt] = ga[i][j]; cnt++; }
+            if (cnt > 0) {
+                CU(c->ops->axpy_n(u, nullptr, kv, cf, cnt, N, nullptr, c->egrid, s));
+                c->launches++;
+                StencilIO io;
+                if (c->exact_jvp) {
+                    io = io_plain(c, y, rhs);
+                    io.dir = u;
+                } else {
+                    io = io_jvp(c, y, u, F0, rhs);
+                }
+                io.add_out = rhs;
+                io.s2 = h;
+                if ((r = stencil(c, io)) != ROK_OK) return r;
+                jvps++;
+                res_evals++;
+            }
+            frhs = rhs;
+        }
+        // (I - h g J_n) k_i = rhs by GMRES(m) from 0
+        int its = 0;
+        bool gconv = false;
+        if ((r = gmres_solve(c, y, F0, hg, frhs, c->K[i], op, &its, &gconv, &jvps, &res_evals)) != ROK_OK) return r;
+        gmres_total += its;
+        converged = converged && gconv;
+    }
+    const double *kv[4] = {c->K[0], c->K[1], c->K[2], c->K[3]};
+    double cb[4];
+    for (int j = 0; j < 4; ++j) cb[j] = h * bw[j];
+    CU(c->ops->axpy_n(converged ? y : c->t0, y, kv, cb, 4, N, st, c->egrid, s));
+    c->launches++;
+    c->last = rok_step_info{};
+    rok_status rs = sync_read(c, nullptr);
     c->last.gmres_iters = gmres_total;
     c->last.residual_evals = res_evals;
     c->last.jvps = jvps;

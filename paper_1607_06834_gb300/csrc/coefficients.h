@@ -50,4 +50,35 @@ inline constexpr double kDp5B[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 1
 inline constexpr double kDp5Bhat[7] = {5179.0 / 57600.0,    0.0,  7571.0 / 16695.0, 393.0 / 640.0,
                                        -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
 
+// ROS4: the L-stable 4-stage Rosenbrock method of order 4 of Hairer & Wanner
+// (Solving ODEs II, Sec. IV.7, g = 0.57282), published for the transformed
+// stages u_i (implementation form (1/(h g) I - J) u_i = f(y + sum a_ij u_j)
+// + sum (c_ij / h) u_j, y_1 = y_0 + sum m_j u_j); the driver converts it to
+// the form of Eq. ROS (Sec. 2.3).
+inline constexpr double kRos4Gamma = 0.57282;
+inline constexpr double kRos4A[4][4] = {{0.0, 0.0, 0.0, 0.0},
+                                        {2.000000000000000, 0.0, 0.0, 0.0},
+                                        {1.867943637803922, 0.2344449711399156, 0.0, 0.0},
+                                        {1.867943637803922, 0.2344449711399156, 0.0, 0.0}};
+inline constexpr double kRos4C[4][4] = {{0.0, 0.0, 0.0, 0.0},
+                                        {-7.137615036412310, 0.0, 0.0, 0.0},
+                                        {2.580708087951457, 0.6515950076447975, 0.0, 0.0},
+                                        {-2.137148994382534, -0.3214669691237626, -0.6949742501781779, 0.0}};
+inline constexpr double kRos4M[4] = {2.255570073418735, 0.2870493262186792, 0.4353179431840180, 1.093502252409163};
+
+// ROW: ROS34PW2 of Rang & Angermann (BIT 45, 2005), a 4-stage Rosenbrock-W
+// method of order 3, L-stable, published in the form of Eq. ROS
+// (g = 0.43586652150845900, the root of 6g^3 - 18g^2 + 9g - 1 in (0.4, 0.5)).
+inline constexpr double kRowGamma = 0.43586652150845900;
+inline constexpr double kRowAlpha[4][4] = {{0.0, 0.0, 0.0, 0.0},
+                                           {0.87173304301691801, 0.0, 0.0, 0.0},
+                                           {0.84457060015369423, -0.11299064236484185, 0.0, 0.0},
+                                           {0.0, 0.0, 1.0, 0.0}};
+inline constexpr double kRowGammaOff[4][4] = {{0.0, 0.0, 0.0, 0.0},
+                                              {-0.87173304301691801, 0.0, 0.0, 0.0},
+                                              {-0.90338057013044082, 0.054180672388095326, 0.0, 0.0},
+                                              {0.24212380706095346, -1.2232505839045147, 0.54526025533510214, 0.0}};
+inline constexpr double kRowB[4] = {0.24212380706095346, -1.2232505839045147, 1.5452602553351020,
+                                    0.43586652150845900};
+
 }  // namespace rok

@@ -916,7 +916,7 @@ __global__ void __launch_bounds__(RT) axpy_n_kernel(double *out, const double *b
 {
     if (guard && guard->status != 0) return;
     for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
-        double t = base[e];
+        double t = base ? base[e] : 0.0;
         for (int q = 0; q < count; ++q) t = t + a.c[q] * a.v[q][e];
         out[e] = t;
     }

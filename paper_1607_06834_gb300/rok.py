@@ -107,6 +107,8 @@ _sig = {
     'rok_step': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(StepInfo)]),
     'rk_step': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(StepInfo)]),
     'esdirk_step': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(EsdirkOpts), ctypes.POINTER(StepInfo)]),
+    'ros_step': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(EsdirkOpts),
+                                ctypes.POINTER(StepInfo)]),
     'rok_dt_from_cfl': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     'rok_sync': (ctypes.c_int, [_vp, ctypes.POINTER(StepInfo)]),
     'rok_set_graph': (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -284,6 +286,18 @@ def esdirk_step(ctx, y, h, gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, newton_
     o = EsdirkOpts(int(gmres_m), float(gmres_tol), int(gmres_restarts), float(newton_tol), int(newton_max))
     return _step_call(ctx, y, 'esdirk_step',
                       lambda yd, ip: _lib.esdirk_step(ctx.handle, _ptr(yd), float(h), ctypes.byref(o), ip), info)
+
+
+ROK_ROS_ROS4 = 0
+ROK_ROS_ROW = 1
+
+
+def ros_step(ctx, y, h, method=ROK_ROS_ROS4, gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, info=False):
+    """``ros_step``: one Rosenbrock (ROS4) or Rosenbrock-W (ROW) step, Eq. ROS."""
+    o = EsdirkOpts(int(gmres_m), float(gmres_tol), int(gmres_restarts), 1e-10, 10)
+    return _step_call(ctx, y, 'ros_step',
+                      lambda yd, ip: _lib.ros_step(ctx.handle, _ptr(yd), float(h), int(method), ctypes.byref(o), ip),
+                      info)
 
 
 def rok_dt_from_cfl(ctx, y, cfl):

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, 'include', 'rok.h')).read()
     src = re.sub(r'/\*.*?\*/', '', src, flags=re.S)
-    names = re.findall(r'^\s*(?:const\s+)?\w+\s*\*?\s*(rok_\w+|rk_step|esdirk_step|dopri5_integrate)\s*\(', src, flags=re.M)
+    names = re.findall(r'^\s*(?:const\s+)?\w+\s*\*?\s*(rok_\w+|rk_step|esdirk_step|ros_step|dopri5_integrate)\s*\(', src, flags=re.M)
     return sorted(set(names))
 
 

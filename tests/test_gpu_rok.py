@@ -273,6 +273,36 @@ def test_esdirk_step(rok, case):
     assert rel_l2(host(y), yo) <= 1e-8
 
 
+@pytest.mark.parametrize('method', ['ros4', 'row'])
+@pytest.mark.parametrize('case', ['vortex', 'tgv'])
+def test_ros_step(rok, case, method):
+    # the ROS4 / ROW comparators (Eq. ROS with GMRES stage solves) against the
+    # oracle's step: the same GMRES iterations, results within their rounding
+    if case == 'vortex':
+        prob, y0 = W.isentropic_vortex(32)
+        h = I.dt_from_cfl(prob, y0, 4.0)
+    else:
+        prob, y0 = W.taylor_green(32, reynolds=200.0)
+        h = I.dt_from_cfl(prob, y0, 6.0)
+    ctx = rok.rok_init(prob, krylov_max=30)
+    y = dev(y0)
+    info = rok.ros_step(ctx, y, h, method=getattr(rok, 'ROK_ROS_' + method.upper()), info=True)
+    oi = {}
+    yo = I.ros_step(core.System(prob), y0, h, method=method, info=oi)
+    assert oi['converged'] and info['gmres_iters'] >= 4
+    assert abs(info['gmres_iters'] - oi['gmres_iters']) <= 2
+    assert rel_l2(host(y), yo) <= 1e-8
+
+
+def test_ros_step_rejects_bad_arguments(rok):
+    prob, y0 = W.isentropic_vortex(16)
+    ctx = rok.rok_init(prob, krylov_max=8)
+    with pytest.raises(rok.RokError):
+        rok.ros_step(ctx, dev(y0), 0.01, method=7)
+    with pytest.raises(rok.RokError):
+        rok.ros_step(ctx, dev(y0), 0.01, gmres_m=30)   # beyond krylov_max
+
+
 # ---- mixed precision: binary32 Krylov basis and Gram-Schmidt (NEXT row f1) ----
 
 def test_mixed_arnoldi_strict_bitexact(rok):

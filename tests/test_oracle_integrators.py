@@ -479,3 +479,112 @@ def test_adaptive_integration_tolerance_proportionality(method):
         steps.append(st['accepted'])
     assert errs[0] > 10 * errs[1] and errs[1] > 10 * errs[2] and errs[2] < 1e-6, errs
     assert steps[0] < steps[1] < steps[2], steps
+
+
+# ---- Rosenbrock (ROS4) and Rosenbrock-W (ROW) comparators, Eq. ROS --------------
+
+def _ros_conditions(al, gm, b, g, order):
+    """Order conditions of Rosenbrock methods (Hairer & Wanner IV.7, exact
+    Jacobian) in the variables of Eq. ROS: beta = alpha + gamma (strictly lower),
+    a_i = sum_j alpha_ij, beta'_i = sum_j beta_ij."""
+    al, gm, b = np.array(al), np.array(gm), np.array(b)
+    be = al + gm
+    a, bp = al.sum(1), be.sum(1)
+    c = {'1': b.sum() - 1, '2': b @ bp - (0.5 - g)}
+    if order >= 3:
+        c['3'] = b @ a ** 2 - 1 / 3
+        c['4'] = b @ (be @ bp) - (1 / 6 - g + g * g)
+    if order >= 4:
+        c['5'] = b @ a ** 3 - 1 / 4
+        c['6'] = b @ (a * (al @ bp)) - (1 / 8 - g / 3)
+        c['7'] = b @ (be @ a ** 2) - (1 / 12 - g / 3)
+        c['8'] = b @ (be @ (be @ bp)) - (1 / 24 - g / 2 + 1.5 * g * g - g ** 3)
+    return c
+
+
+def _ros_R(method):
+    if method == 'ros4':
+        al, gm, b, g = C.ROS4_ALPHA, C.ROS4_GAMMA_OFFDIAG, C.ROS4_B, C.ROS4_GAMMA
+    else:
+        al, gm, b, g = C.ROW_ALPHA, C.ROW_GAMMA_OFFDIAG, C.ROW_B, C.ROW_GAMMA
+    B = np.array(al) + np.array(gm) + g * np.eye(4)
+    bb = np.array(b)
+    return lambda z: 1 + z * bb @ np.linalg.solve(np.eye(4) - z * B, np.ones(4))
+
+
+def test_ros4_order_conditions_and_L_stability():
+    c = _ros_conditions(C.ROS4_ALPHA, C.ROS4_GAMMA_OFFDIAG, C.ROS4_B, C.ROS4_GAMMA, 4)
+    for k, v in c.items():
+        assert abs(v) <= 1e-14, (k, v)
+    R = _ros_R('ros4')
+    for z in (1e-2, -1e-2, 2e-2j):
+        assert abs(R(z) - np.exp(z)) <= 3 * abs(z) ** 5
+    # L-stable: R(z) -> 0 like 1/z at infinity, |R| <= 1 on the imaginary axis
+    assert abs(R(-1e3)) < 1e-2 and abs(R(-1e5)) < abs(R(-1e3)) / 50
+    assert max(abs(R(1j * t)) for t in np.linspace(-200, 200, 4001)) <= 1 + 1e-12
+
+
+def test_row_order3_conditions_embedded_pair_and_L_stability():
+    c = _ros_conditions(C.ROW_ALPHA, C.ROW_GAMMA_OFFDIAG, C.ROW_B, C.ROW_GAMMA, 3)
+    for k, v in c.items():
+        assert abs(v) <= 1e-14, (k, v)
+    ch = _ros_conditions(C.ROW_ALPHA, C.ROW_GAMMA_OFFDIAG, C.ROW_BHAT, C.ROW_GAMMA, 3)
+    assert abs(ch['1']) <= 1e-14 and abs(ch['2']) <= 1e-14       # embedded weights: order 2
+    assert abs(ch['3']) > 1e-3                                   # ... and not 3
+    g = C.ROW_GAMMA
+    assert abs(6 * g ** 3 - 18 * g ** 2 + 9 * g - 1) < 1e-14
+    R = _ros_R('row')
+    for z in (1e-2, -1e-2, 2e-2j):
+        assert abs(R(z) - np.exp(z)) <= 3 * abs(z) ** 4
+    assert abs(R(-1e3)) < 1e-2 and abs(R(-1e5)) < abs(R(-1e3)) / 50
+    assert max(abs(R(1j * t)) for t in np.linspace(-200, 200, 4001)) <= 1 + 1e-12
+
+
+@pytest.mark.parametrize('method', ['ros4', 'row'])
+def test_ros_linear_is_R_of_hA(method):
+    # on y' = A y one step is y_1 = R(hA) y_0 (R of the tableau, textbook formula):
+    # pins the stage structure, including the J term of the right-hand sides
+    rng = np.random.default_rng(2)
+    Q = np.linalg.qr(rng.normal(size=(10, 10)))[0]
+    lam = -np.logspace(-1, 2, 10)
+    A = Q @ np.diag(lam) @ Q.T
+    y0 = rng.normal(size=10)
+    h = 0.1
+    y1 = I.ros_step(Linear(A), y0, h, method=method, gmres_tol=1e-14)
+    R = _ros_R(method)
+    Rz = np.array([R(z) for z in h * lam])
+    assert np.allclose(y1, Q @ (Rz * (Q.T @ y0)), rtol=1e-10, atol=1e-11)
+
+
+def test_ros4_order4_and_row_order3_lorenz96():
+    y0, ref = _l96_start()
+    sys = L96(exact=True)
+    sl, errs = _slopes(lambda y, h: I.ros_step(sys, y, h, method='ros4', gmres_tol=1e-13), y0, ref, 0.3,
+                       [16, 32, 64])
+    assert abs(sl[-1] - 4.0) < 0.25, (sl, errs)
+    sl, errs = _slopes(lambda y, h: I.ros_step(sys, y, h, method='row', gmres_tol=1e-13), y0, ref, 0.3,
+                       [16, 32, 64])
+    assert abs(sl[-1] - 3.0) < 0.25, (sl, errs)
+
+
+class L96WrongJacobian(L96):
+    """Lorenz-96 whose Jacobian-vector products use J + E, E a fixed matrix."""
+    def __init__(self):
+        super().__init__(exact=True)
+        self.E = 0.5 * np.random.default_rng(5).normal(size=(40, 40)) / np.sqrt(40)
+
+    def jvp(self, u, v, f0, eps):
+        return super().jvp(u, v, f0, eps) + self.E @ v
+
+
+def test_row_keeps_order3_with_a_wrong_jacobian_and_ros4_does_not():
+    # the W-property (Sec. 2.3.2): ROW keeps order 3 for any matrix in place of
+    # J; ROS4 drops to order 2 (its conditions assume the exact Jacobian)
+    y0, ref = _l96_start()
+    sys = L96WrongJacobian()
+    sl, errs = _slopes(lambda y, h: I.ros_step(sys, y, h, method='row', gmres_tol=1e-13), y0, ref, 0.3,
+                       [16, 32, 64])
+    assert abs(sl[-1] - 3.0) < 0.25, (sl, errs)
+    sl4, errs4 = _slopes(lambda y, h: I.ros_step(sys, y, h, method='ros4', gmres_tol=1e-13), y0, ref, 0.3,
+                         [16, 32, 64])
+    assert sl4[-1] < 2.5, (sl4, errs4)
