@@ -431,11 +431,33 @@ struct Tile {
         mu[SH::EH][SH::EW];
 };
 // differences of the four reconstructed primitives between a cell and its
-// lower neighbour along x (dx) and y (dy)
+// lower neighbour along x (dx, the tile's rows 2 .. TY+1 only: dx[k][ly - 2][lx])
+// and y (dy, the tile's columns 2 .. TX+1 only: dy[k][ly][lx - 2]) -- the ones
+// the faces read
 template <class S, class SH = Shape32x8>
 struct Diffs {
-    S dx[4][SH::EH][SH::EW], dy[4][SH::EH][SH::EW];
+    S dx[4][SH::TY][SH::EW], dy[4][SH::EH][SH::TX];
 };
+
+// FMA build, viscous faces: sums over the two cells beside a face of its
+// tangential neighbour rows / columns, shared by the faces above and below:
+// px[q][ly - 1][fx] = w[ly][fx + 1] + w[ly][fx + 2] (rows 1 .. TY+2),
+// qy[q][lx - 1][fy] = w[fy + 1][lx] + w[fy + 2][lx] (columns 1 .. TX+2), w = u, v
+template <class S, class SH = Shape32x8>
+struct PairSums {
+    S px[2][SH::TY + 2][SH::TX + 1], qy[2][SH::TX + 2][SH::TY + 1];
+};
+
+// shared-memory bytes of the pair sums (FMA build, viscous kernels only)
+template <bool VISC, class S, class SH>
+constexpr size_t pair_sums_bytes()
+{
+#ifdef ROK_STENCIL_FAST
+    return VISC ? sizeof(PairSums<S, SH>) : 0;
+#else
+    return 0;
+#endif
+}
 
 template <class S, class SH = Shape32x8>
 struct Faces {
@@ -566,6 +588,10 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     Tile<S, SH> &tl = *reinterpret_cast<Tile<S, SH> *>(smem_raw);
     Faces<S, SH> &fc = *reinterpret_cast<Faces<S, SH> *>(smem_raw + sizeof(Tile<S, SH>));
     Diffs<S, SH> &df = *reinterpret_cast<Diffs<S, SH> *>(smem_raw + sizeof(Tile<S, SH>) + sizeof(Faces<S, SH>));
+#ifdef ROK_STENCIL_FAST
+    PairSums<S, SH> &ps = *reinterpret_cast<PairSums<S, SH> *>(smem_raw + sizeof(Tile<S, SH>) +
+                                                               sizeof(Faces<S, SH>) + sizeof(Diffs<S, SH>));
+#endif
 
     const int nx = C.nx, ny = C.ny;
     const size_t nc = (size_t)nx * ny;
@@ -586,17 +612,33 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     // cell differences the faces read: along x in the tile's rows (lx >= 1),
     // along y in the tile's columns (ly >= 1)
     constexpr int NDX = (EW - 1) * TY, NDY = TX * (EH - 1);
-    for (int idx = tid; idx < NDX + NDY; idx += NT) {
+#ifdef ROK_STENCIL_FAST
+    constexpr int NPX = VISC ? 2 * (TY + 2) * (TX + 1) : 0, NQY = VISC ? 2 * (TX + 2) * (TY + 1) : 0;
+#else
+    constexpr int NPX = 0, NQY = 0;
+#endif
+    for (int idx = tid; idx < NDX + NDY + NPX + NQY; idx += NT) {
         if (idx < NDX) {
             const int ly = 2 + idx / (EW - 1), lx = 1 + idx % (EW - 1);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) df.dx[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
-        } else {
+            for (int k = 0; k < 4; ++k) df.dx[k][ly - 2][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
+        } else if (idx < NDX + NDY) {
             const int j = idx - NDX;
             const int ly = 1 + j / TX, lx = 2 + j % TX;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) df.dy[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
+            for (int k = 0; k < 4; ++k) df.dy[k][ly][lx - 2] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
         }
+#ifdef ROK_STENCIL_FAST
+        else if (idx < NDX + NDY + NPX) {
+            const int j = idx - NDX - NDY, q = j / ((TY + 2) * (TX + 1)), r = j % ((TY + 2) * (TX + 1));
+            const int row = r / (TX + 1), fx = r % (TX + 1);
+            ps.px[q][row][fx] = pick(tl, 1 + q, row + 1, fx + 1) + pick(tl, 1 + q, row + 1, fx + 2);
+        } else {
+            const int j = idx - NDX - NDY - NPX, q = j / ((TX + 2) * (TY + 1)), r = j % ((TX + 2) * (TY + 1));
+            const int col = r / (TY + 1), fy = r % (TY + 1);
+            ps.qy[q][col][fy] = pick(tl, 1 + q, fy + 1, col + 1) + pick(tl, 1 + q, fy + 2, col + 1);
+        }
+#endif
     }
     __syncthreads();
 
@@ -612,15 +654,14 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y][xl], df.dx[k][y][xr], df.dx[k][y][xr + 1],
+            muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y - 2][xl], df.dx[k][y - 2][xr], df.dx[k][y - 2][xr + 1],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
 #ifdef ROK_STENCIL_FAST
         roe2<0>(WL, WR, C, F);
         if (VISC)
             visc2<0, SUTH>(F, tl.u[y][xr] - tl.u[y][xl], tl.v[y][xr] - tl.v[y][xl], tl.T[y][xr] - tl.T[y][xl],
-                           (tl.u[y + 1][xl] + tl.u[y + 1][xr]) - (tl.u[y - 1][xl] + tl.u[y - 1][xr]),
-                           (tl.v[y + 1][xl] + tl.v[y + 1][xr]) - (tl.v[y - 1][xl] + tl.v[y - 1][xr]),
-                           tl.u[y][xl] + tl.u[y][xr], tl.v[y][xl] + tl.v[y][xr],
+                           ps.px[0][y][fx] - ps.px[0][y - 2][fx], ps.px[1][y][fx] - ps.px[1][y - 2][fx],
+                           ps.px[0][y - 1][fx], ps.px[1][y - 1][fx],
                            SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C.vk[0]);
 #else
         roe_x(WL, WR, C, F);
@@ -651,15 +692,14 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x], df.dy[k][yt][x], df.dy[k][yt + 1][x],
+            muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x - 2], df.dy[k][yt][x - 2], df.dy[k][yt + 1][x - 2],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
 #ifdef ROK_STENCIL_FAST
         roe2<1>(WL, WR, C, F);
         if (VISC)
             visc2<1, SUTH>(F, tl.v[yt][x] - tl.v[yb][x], tl.u[yt][x] - tl.u[yb][x], tl.T[yt][x] - tl.T[yb][x],
-                           (tl.v[yb][x + 1] + tl.v[yt][x + 1]) - (tl.v[yb][x - 1] + tl.v[yt][x - 1]),
-                           (tl.u[yb][x + 1] + tl.u[yt][x + 1]) - (tl.u[yb][x - 1] + tl.u[yt][x - 1]),
-                           tl.v[yb][x] + tl.v[yt][x], tl.u[yb][x] + tl.u[yt][x],
+                           ps.qy[1][x][fy] - ps.qy[1][x - 2][fy], ps.qy[0][x][fy] - ps.qy[0][x - 2][fy],
+                           ps.qy[1][x - 1][fy], ps.qy[0][x - 1][fy],
                            SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C.vk[1]);
 #else
         roe_y(WL, WR, C, F);
@@ -835,12 +875,12 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
         if (idx < NDX) {
             const int ly = 2 + idx / (EW - 1), lx = 1 + idx % (EW - 1);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) df.dx[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
+            for (int k = 0; k < 4; ++k) df.dx[k][ly - 2][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly, lx - 1);
         } else {
             const int j = idx - NDX;
             const int ly = 1 + j / TX, lx = 2 + j % TX;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) df.dy[k][ly][lx] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
+            for (int k = 0; k < 4; ++k) df.dy[k][ly][lx - 2] = pick(tl, k, ly, lx) - pick(tl, k, ly - 1, lx);
         }
     }
     __syncthreads();
@@ -857,7 +897,7 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y][xl], df.dx[k][y][xr], df.dx[k][y][xr + 1],
+            muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y - 2][xl], df.dx[k][y - 2][xr], df.dx[k][y - 2][xr + 1],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
         double nxf = G.in_x[fi], nyf = G.in_y[fi];
 #ifdef ROK_STENCIL_FAST
@@ -927,7 +967,7 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
         S WL[4], WR[4], F[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x], df.dy[k][yt][x], df.dy[k][yt + 1][x],
+            muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x - 2], df.dy[k][yt][x - 2], df.dy[k][yt + 1][x - 2],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
         double nxf = G.jn_x[fi], nyf = G.jn_y[fi];
 #ifdef ROK_STENCIL_FAST
@@ -1045,7 +1085,8 @@ template <bool V, bool SU, class S>
 static cudaError_t launch_cart_t(const StencilConsts &c, const StencilIO &io, cudaStream_t s)
 {
     constexpr int MINB = sizeof(S) == sizeof(double) ? 3 : 1;
-    const size_t smem = sizeof(Tile<S, CartShape>) + sizeof(Faces<S, CartShape>) + sizeof(Diffs<S, CartShape>);
+    const size_t smem = sizeof(Tile<S, CartShape>) + sizeof(Faces<S, CartShape>) + sizeof(Diffs<S, CartShape>) +
+                        pair_sums_bytes<V, S, CartShape>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(cart_kernel<V, SU, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1090,7 +1131,8 @@ template <bool V, bool SU, class SH>
 static cudaError_t launch_cart_batch_t(const StencilConsts &c, const StencilIO &io, const BatchTiles &bt, int ntiles,
                                        cudaStream_t s)
 {
-    const size_t smem = sizeof(Tile<double, SH>) + sizeof(Faces<double, SH>) + sizeof(Diffs<double, SH>);
+    const size_t smem = sizeof(Tile<double, SH>) + sizeof(Faces<double, SH>) + sizeof(Diffs<double, SH>) +
+                        pair_sums_bytes<V, double, SH>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(cart_batch_kernel<V, SU, SH, 3>,
