@@ -659,7 +659,7 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
 #ifdef ROK_STENCIL_FAST
         roe2<0>(WL, WR, C, F);
         if (VISC)
-            visc2<0, SUTH>(F, tl.u[y][xr] - tl.u[y][xl], tl.v[y][xr] - tl.v[y][xl], tl.T[y][xr] - tl.T[y][xl],
+            visc2<0, SUTH>(F, df.dx[1][y - 2][xr], df.dx[2][y - 2][xr], tl.T[y][xr] - tl.T[y][xl],
                            ps.px[0][y][fx] - ps.px[0][y - 2][fx], ps.px[1][y][fx] - ps.px[1][y - 2][fx],
                            ps.px[0][y - 1][fx], ps.px[1][y - 1][fx],
                            SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C.vk[0]);
@@ -697,7 +697,7 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
 #ifdef ROK_STENCIL_FAST
         roe2<1>(WL, WR, C, F);
         if (VISC)
-            visc2<1, SUTH>(F, tl.v[yt][x] - tl.v[yb][x], tl.u[yt][x] - tl.u[yb][x], tl.T[yt][x] - tl.T[yb][x],
+            visc2<1, SUTH>(F, df.dy[2][yt][x - 2], df.dy[1][yt][x - 2], tl.T[yt][x] - tl.T[yb][x],
                            ps.qy[1][x][fy] - ps.qy[1][x - 2][fy], ps.qy[0][x][fy] - ps.qy[0][x - 2][fy],
                            ps.qy[1][x - 1][fy], ps.qy[0][x - 1][fy],
                            SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C.vk[1]);
