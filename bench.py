@@ -429,7 +429,9 @@ def run_grad(args):
     """--mode grad: gradient of the final kinetic energy of the 256^2 Taylor-Green
     vortex (Re = 1000) after 100 ROK4 steps (M = 20, CFL 8) with respect to the
     initial state and the viscosity, through the reverse step with a checkpoint
-    every 10 steps.  Reports forward and backward times, the derivatives along
+    every 10 steps (segments re-run onto tapes of the step internals; the same
+    gradient recomputing every step inside its reverse is timed beside it and
+    compared bit for bit).  Reports forward and backward times, the derivatives along
     64 seeded random unit directions, the gradient over the first 2 steps against
     the oracle's complex-step derivative (one direction and mu), and central
     differences (h = 1e-6) of the GPU forward map along two directions."""
@@ -449,12 +451,12 @@ def run_grad(args):
     h = rok.rok_dt_from_cfl(ctx, yd0, CFL)
     stream = torch.cuda.current_stream()
 
-    def grad(nsteps):
+    def grad(nsteps, tapes=True):
         y = yd0.clone().requires_grad_(True)
         mu = torch.tensor(prob.mu, dtype=torch.float64, requires_grad=True)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
-        J = G.kinetic_energy(G.integrate(ctx, y, mu, h, M, nsteps, checkpoint_every=every))
+        J = G.kinetic_energy(G.integrate(ctx, y, mu, h, M, nsteps, checkpoint_every=every, tapes=tapes))
         e[1].record(stream)
         J.backward()
         e[2].record(stream)
@@ -462,7 +464,9 @@ def run_grad(args):
         return y.grad.detach(), float(mu.grad), float(J), e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
 
     grad(2)                                   # warm-up (allocations)
+    grad(2, tapes=False)
     g, gmu, J, ms_f, ms_b = grad(K)
+    gr, gmur, _, ms_fr, ms_br = grad(K, tapes=False)
     rng = np.random.default_rng(0)
     dirs = rng.standard_normal((64, y0.size))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
@@ -470,7 +474,11 @@ def run_grad(args):
     out = {'mode': 'grad', 'metric': METRIC, 'workload': 'ns2d-taylor-green-256x256-Re1000-rok4-M20-100steps',
            'steps': K, 'krylov_m': M, 'checkpoint_every': every, 'dt': h, 'J_final_ke': J,
            'forward_ms': round(ms_f, 2), 'backward_ms': round(ms_b, 2),
-           'backward_ms_per_step': round(ms_b / K, 3), 'dJ_dmu': gmu,
+           'backward_ms_per_step': round(ms_b / K, 3),
+           'tape_bytes_per_step': rok.rok_tape_bytes(ctx, M),
+           'without_tapes': {'forward_ms': round(ms_fr, 2), 'backward_ms': round(ms_br, 2),
+                             'gradient_bit_identical': bool(torch.equal(g, gr)) and gmu == gmur},
+           'dJ_dmu': gmu,
            'grad_norm': float(g.norm()), 'directional_derivatives_64': {
                'min': float(dd.min()), 'max': float(dd.max()), 'rms': float(np.sqrt(np.mean(dd ** 2)))},
            'dtype': 'f64', 'data': 'synthetic'}

@@ -26,6 +26,8 @@
 #ifndef ROK_H
 #define ROK_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -265,6 +267,29 @@ rok_status rok_vjp(rok_ctx *ctx, const double *y, const double *ubar, double *yb
  * vectors, allocated on the first call. */
 rok_status rok_step_vjp(rok_ctx *ctx, const double *y, double h, int M, const double *ybar_in, double *ybar_out,
                         double *mubar);
+
+/* Tapes: the reverse of a step without recomputing the step.  A tape holds
+ * what the reverse of one ROK4 step (Sec. 2.3.3, Eq. ROK; Arnoldi of
+ * Sec. 2.3.2 with the JVP of Eq. matvecFD) reads: y_n, the F_i and k_i, the
+ * Krylov basis, H with its LU, lambda_i and phi_i, and the last column's
+ * orthogonalised JVP, about (10 + M) state vectors.  The tape is plain device
+ * memory owned by the caller, 256-byte aligned, rok_tape_bytes bytes for
+ * Krylov dimension M, and is only read by the library after it was written.
+ *
+ * rok_tape_bytes: *bytes (HOST) = the size of a tape for Krylov dimension M.
+ * rok_step_record: rok_step(ctx, y, h, M, NULL) that also writes the tape
+ *   (y: device, N float64, in/out, y_{n+1} on return; tape: device, must not
+ *   overlap y); y_{n+1} is bit-identical to rok_step's.  Synchronises once.
+ *   Same support as rok_step_vjp; on an error status y is unchanged.
+ * rok_step_vjp_tape: rok_step_vjp(ctx, y_n, h, M, ybar_in, ybar_out, mubar)
+ *   from a tape that rok_step_record wrote on a context of the same problem;
+ *   bit-identical to it.  ybar_out must overlap neither the tape nor y_n.
+ *   ROK_ERR_INVALID_ARG for a tape whose header does not match this context.
+ *   Overwrites the context's step internals (as any step does). */
+rok_status rok_tape_bytes(rok_ctx *ctx, int M, size_t *bytes);
+rok_status rok_step_record(rok_ctx *ctx, double *y, double h, int M, void *tape);
+rok_status rok_step_vjp_tape(rok_ctx *ctx, const void *tape, const double *ybar_in, double *ybar_out,
+                             double *mubar);
 
 /* ---- Batches: many independent instances stepped together ---------------
  *

@@ -18,12 +18,14 @@
 // No atomics: the result is deterministic.
 //
 // ROK step reverse: the step is recomputed from y_n (its stage vectors, basis,
-// Hessenberg matrix and stage solutions stay in the context), then every
+// Hessenberg matrix and stage solutions stay in the context), or its internals
+// are copied back from a tape that a recording step wrote, then every
 // statement is reversed in the opposite order; eps is a constant of the step.
 // The reverse Gram-Schmidt passes of one Arnoldi column run as one cooperative
 // launch where the device allows it (pass by pass otherwise).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <vector>
@@ -839,41 +841,15 @@ void rok_free_adjoint(rok_ctx *c)
     }
 }
 
-extern "C" {
+// ---- the two halves of the reverse step ------------------------------------------
 
-rok_status rok_vjp(rok_ctx *c, const double *y, const double *ubar, double *ybar, double *mubar)
+// The step from y_n once more, keeping what its reverse reads: the basis V, H
+// and the LU of (I - h gamma H), lambda_i and phi_i (all in the StepState), the
+// F_i and k_i (in the context), and the last column's orthogonalised w, which
+// the step itself does not keep (in A->wlast).  y_{n+1} is left in A->y1;
+// *m_out = the Krylov dimension built.  Synchronises once (status, m).
+static rok_status step_internals(rok_ctx *c, const double *y, double h, int M, int *m_out)
 {
-    if (!c || !y || !ubar || !ybar || ybar == y || ybar == ubar) return ROK_ERR_INVALID_ARG;
-    rok_status r = vjp_supported(c);
-    if (r != ROK_OK) return r;
-    if ((r = ensure_work(c, false)) != ROK_OK) return r;
-    AdjWork *A = c->adj;
-    CU(cudaMemsetAsync(ybar, 0, c->N * sizeof(double), c->stream));
-    if (mubar) CU(cudaMemsetAsync(&A->as->mub, 0, sizeof(double), c->stream));
-    VjpOut o{ybar, 1.0, nullptr, nullptr, 0.0, nullptr};
-    if ((r = vjp(c, A, y, ubar, o, mubar ? &A->as->mub : nullptr, 1.0, nullptr)) != ROK_OK) return r;
-    if (mubar) {
-        if (!c->C.viscous) {
-            *mubar = 0.0;
-            return ROK_OK;
-        }
-        CU(cudaMemcpyAsync(A->h_mub, &A->as->mub, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        *mubar = *A->h_mub;
-    }
-    return ROK_OK;
-}
-
-rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const double *ybar_in, double *ybar_out,
-                        double *mubar)
-{
-    if (!c || !y || !ybar_in || !ybar_out || M < 0 || M > c->mmax || !(h > 0.0) || !isfinite(h))
-        return ROK_ERR_INVALID_ARG;
-    if (ybar_out == y) return ROK_ERR_INVALID_ARG;
-    rok_status r = vjp_supported(c);
-    if (r != ROK_OK) return r;
-    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
-    if ((r = ensure_work(c, true)) != ROK_OK) return r;
     AdjWork *A = c->adj;
     const size_t N = c->N;
     const int P = c->P;
@@ -881,10 +857,7 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
     AdjState *as = A->as;
     cudaStream_t s = c->stream;
     const LinalgOps &ops = *c->ops;
-    const int eg = egrid(c);
-
-    // 1. the step again from y_n, keeping its internals (V, H, LU, lambda_i,
-    //    phi_i, F_i, k_i stay in the context)
+    rok_status r;
     CU(cudaMemcpyAsync(A->y1, y, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CU(launch_begin(st, h, kRokGamma, M, s));
     CU(cudaMemsetAsync(&c->bar->count, 0, sizeof(unsigned), s));
@@ -896,6 +869,7 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
         return (A->h_st->status & kStatusTimeout) ? ROK_ERR_TIMEOUT : ROK_ERR_NONFINITE;
     }
     const int m = A->h_st->meff;
+    *m_out = m;
     // the last column's orthogonalised w (not kept by the step): its JVP and MGS
     // passes again, H entries to scratch
     if (m > 0) {
@@ -917,7 +891,24 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
         }
         c->launches += 2 + m;
     }
+    return ROK_OK;
+}
 
+// The reverse of the step from y_n, its internals in place (step_internals, or
+// a tape copied back): ybar_out = (dy_{n+1}/dy_n)^T ybar_in, mubar += the
+// step's viscosity part.
+static rok_status step_reverse(rok_ctx *c, const double *y, double h, int m, const double *ybar_in,
+                               double *ybar_out, double *mubar)
+{
+    AdjWork *A = c->adj;
+    const size_t N = c->N;
+    const int P = c->P;
+    StepState *st = c->st;
+    AdjState *as = A->as;
+    cudaStream_t s = c->stream;
+    const LinalgOps &ops = *c->ops;
+    const int eg = egrid(c);
+    rok_status r;
     // 2. stages in reverse: y_{n+1} = y_n + sum b_i k_i
     CU(cudaMemsetAsync(as, 0, sizeof(AdjState), s));
     CU(cudaMemcpyAsync(A->yb, ybar_in, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1042,6 +1033,165 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
     }
     CU(cudaGetLastError());
     return ROK_OK;
+}
+
+
+// ---- tapes: one step's internals kept for its reverse ----------------------------
+//
+// [0, 256)         TapeHeader
+// [256, ...)       the StepState after step_internals
+// then 10 + M vectors of N float64, each on a 256-byte boundary: y_n, F_1..F_4,
+// k_1..k_4, the last column's orthogonalised w, and the basis v_1..v_m (m <= M)
+constexpr unsigned long long kTapeMagic = 0x45504154344b4f52ull;   // bytes "ROK4TAPE"
+constexpr size_t kTapeAlign = 256;
+
+struct TapeHeader {
+    unsigned long long magic;
+    unsigned long long n;   // state entries
+    int M, m;               // Krylov dimension asked for / built
+    double h;
+};
+
+struct TapeLayout {
+    size_t st, vec, stride, bytes;
+};
+
+static size_t tape_round(size_t b) { return (b + kTapeAlign - 1) / kTapeAlign * kTapeAlign; }
+
+static TapeLayout tape_layout(size_t N, int M)
+{
+    TapeLayout L;
+    L.st = kTapeAlign;
+    L.vec = L.st + tape_round(sizeof(StepState));
+    L.stride = tape_round(N * sizeof(double));
+    L.bytes = L.vec + (size_t)(10 + M) * L.stride;
+    return L;
+}
+
+static bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+extern "C" {
+
+rok_status rok_vjp(rok_ctx *c, const double *y, const double *ubar, double *ybar, double *mubar)
+{
+    if (!c || !y || !ubar || !ybar || ybar == y || ybar == ubar) return ROK_ERR_INVALID_ARG;
+    rok_status r = vjp_supported(c);
+    if (r != ROK_OK) return r;
+    if ((r = ensure_work(c, false)) != ROK_OK) return r;
+    AdjWork *A = c->adj;
+    CU(cudaMemsetAsync(ybar, 0, c->N * sizeof(double), c->stream));
+    if (mubar) CU(cudaMemsetAsync(&A->as->mub, 0, sizeof(double), c->stream));
+    VjpOut o{ybar, 1.0, nullptr, nullptr, 0.0, nullptr};
+    if ((r = vjp(c, A, y, ubar, o, mubar ? &A->as->mub : nullptr, 1.0, nullptr)) != ROK_OK) return r;
+    if (mubar) {
+        if (!c->C.viscous) {
+            *mubar = 0.0;
+            return ROK_OK;
+        }
+        CU(cudaMemcpyAsync(A->h_mub, &A->as->mub, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        *mubar = *A->h_mub;
+    }
+    return ROK_OK;
+}
+
+rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const double *ybar_in, double *ybar_out,
+                        double *mubar)
+{
+    if (!c || !y || !ybar_in || !ybar_out || M < 0 || M > c->mmax || !(h > 0.0) || !isfinite(h))
+        return ROK_ERR_INVALID_ARG;
+    if (ybar_out == y) return ROK_ERR_INVALID_ARG;
+    rok_status r = vjp_supported(c);
+    if (r != ROK_OK) return r;
+    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
+    if ((r = ensure_work(c, true)) != ROK_OK) return r;
+    int m = 0;
+    if ((r = step_internals(c, y, h, M, &m)) != ROK_OK) return r;
+    return step_reverse(c, y, h, m, ybar_in, ybar_out, mubar);
+}
+
+rok_status rok_tape_bytes(rok_ctx *c, int M, size_t *bytes)
+{
+    if (!c || !bytes || M < 0 || M > c->mmax) return ROK_ERR_INVALID_ARG;
+    *bytes = tape_layout(c->N, M).bytes;
+    return ROK_OK;
+}
+
+rok_status rok_step_record(rok_ctx *c, double *y, double h, int M, void *tape)
+{
+    if (!c || !y || !tape || M < 0 || M > c->mmax || !(h > 0.0) || !isfinite(h)) return ROK_ERR_INVALID_ARG;
+    const size_t N = c->N, vb = N * sizeof(double);
+    const TapeLayout L = tape_layout(N, M);
+    if ((uintptr_t)tape % kTapeAlign || overlaps(y, vb, tape, L.bytes)) return ROK_ERR_INVALID_ARG;
+    rok_status r = vjp_supported(c);
+    if (r != ROK_OK) return r;
+    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
+    if ((r = ensure_work(c, true)) != ROK_OK) return r;
+    AdjWork *A = c->adj;
+    cudaStream_t s = c->stream;
+    int m = 0;
+    if ((r = step_internals(c, y, h, M, &m)) != ROK_OK) return r;
+    char *t = (char *)tape;
+    auto vec = [&](int k) { return t + L.vec + (size_t)k * L.stride; };
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    CU(cudaMemcpyAsync(t + L.st, c->st, sizeof(StepState), dd, s));
+    CU(cudaMemcpyAsync(vec(0), y, vb, dd, s));
+    for (int i = 0; i < 4; ++i) {
+        CU(cudaMemcpyAsync(vec(1 + i), c->F[i], vb, dd, s));
+        CU(cudaMemcpyAsync(vec(5 + i), c->K[i], vb, dd, s));
+    }
+    if (m > 0) {
+        CU(cudaMemcpyAsync(vec(9), A->wlast, vb, dd, s));
+        CU(cudaMemcpy2DAsync(vec(10), L.stride, c->V, vb, vb, m, dd, s));
+    }
+    // a pageable source: the call returns once the header has been staged
+    const TapeHeader hd{kTapeMagic, (unsigned long long)N, M, m, h};
+    CU(cudaMemcpyAsync(tape, &hd, sizeof hd, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(y, A->y1, vb, dd, s));
+    c->last = rok_step_info{};
+    c->last.residual_evals = 1 + M + 3;
+    c->last.jvps = M;
+    CU(cudaGetLastError());
+    return ROK_OK;
+}
+
+rok_status rok_step_vjp_tape(rok_ctx *c, const void *tape, const double *ybar_in, double *ybar_out, double *mubar)
+{
+    if (!c || !tape || !ybar_in || !ybar_out || (uintptr_t)tape % kTapeAlign) return ROK_ERR_INVALID_ARG;
+    rok_status r = vjp_supported(c);
+    if (r != ROK_OK) return r;
+    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
+    if ((r = ensure_work(c, true)) != ROK_OK) return r;
+    AdjWork *A = c->adj;
+    const size_t N = c->N, vb = N * sizeof(double);
+    cudaStream_t s = c->stream;
+    TapeHeader hd;
+    CU(cudaMemcpyAsync(&hd, tape, sizeof hd, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hd.magic != kTapeMagic || hd.n != (unsigned long long)N || hd.M < 0 || hd.M > c->mmax || hd.m < 0 ||
+        hd.m > hd.M || !(hd.h > 0.0) || !isfinite(hd.h))
+        return ROK_ERR_INVALID_ARG;
+    const TapeLayout L = tape_layout(N, hd.M);
+    if (overlaps(ybar_out, vb, tape, L.bytes)) return ROK_ERR_INVALID_ARG;
+    const char *t = (const char *)tape;
+    auto vec = [&](int k) { return t + L.vec + (size_t)k * L.stride; };
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    CU(cudaMemcpyAsync(c->st, t + L.st, sizeof(StepState), dd, s));
+    for (int i = 0; i < 4; ++i) {
+        CU(cudaMemcpyAsync(c->F[i], vec(1 + i), vb, dd, s));
+        CU(cudaMemcpyAsync(c->K[i], vec(5 + i), vb, dd, s));
+    }
+    if (hd.m > 0) {
+        CU(cudaMemcpyAsync(A->wlast, vec(9), vb, dd, s));
+        CU(cudaMemcpy2DAsync(c->V, vb, vec(10), L.stride, vb, hd.m, dd, s));
+    }
+    // a grid barrier that timed out leaves its arrival count behind: start clean
+    CU(cudaMemsetAsync(&c->bar->count, 0, sizeof(unsigned), s));
+    return step_reverse(c, (const double *)vec(0), hd.h, hd.m, ybar_in, ybar_out, mubar);
 }
 
 }  // extern "C"

@@ -123,6 +123,9 @@ _sig = {
                                         ctypes.POINTER(AdaptInfo)]),
     'rok_vjp': (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     'rok_step_vjp': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+    'rok_tape_bytes': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    'rok_step_record': (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_int, _vp]),
+    'rok_step_vjp_tape': (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     'rok_batch_init': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ProblemDesc), ctypes.c_int, _vp]),
     'rok_batch_destroy': (ctypes.c_int, [_vp]),
     'rok_batch_layout': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
@@ -373,6 +376,40 @@ def rok_step_vjp(ctx, y, h, M, ybar, out=None):
     mb = ctypes.c_double(0.0)
     _check(_lib.rok_step_vjp(ctx.handle, _ptr(y), float(h), int(M), _ptr(ybar), _ptr(out), ctypes.byref(mb)),
            'rok_step_vjp')
+    return out, mb.value
+
+
+def rok_tape_bytes(ctx, M):
+    """``rok_tape_bytes``: bytes of a tape for Krylov dimension M."""
+    n = ctypes.c_size_t(0)
+    _check(_lib.rok_tape_bytes(ctx.handle, int(M), ctypes.byref(n)), 'rok_tape_bytes')
+    return n.value
+
+
+def _tape_ptr(tape):
+    if not tape.is_contiguous() or tape.dtype != torch.uint8:
+        raise ValueError('expected a contiguous uint8 tape')
+    return ctypes.c_void_p(tape.data_ptr())
+
+
+def rok_step_record(ctx, y, h, M, tape=None):
+    """``rok_step_record``: one ROK4 step of y in place that also writes the
+    step's tape (a uint8 device tensor of ``rok_tape_bytes(ctx, M)`` bytes,
+    allocated when None); returns the tape."""
+    if tape is None:
+        tape = torch.empty(rok_tape_bytes(ctx, M), dtype=torch.uint8, device=y.device)
+    _check(_lib.rok_step_record(ctx.handle, _ptr(y), float(h), int(M), _tape_ptr(tape)), 'rok_step_record')
+    return tape
+
+
+def rok_step_vjp_tape(ctx, tape, ybar, out=None):
+    """``rok_step_vjp_tape``: reverse of the step a tape recorded; returns
+    (ybar_n, mubar of the step)."""
+    if out is None:
+        out = torch.empty_like(ybar)
+    mb = ctypes.c_double(0.0)
+    _check(_lib.rok_step_vjp_tape(ctx.handle, _tape_ptr(tape), _ptr(ybar), _ptr(out), ctypes.byref(mb)),
+           'rok_step_vjp_tape')
     return out, mb.value
 
 

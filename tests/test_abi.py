@@ -67,3 +67,15 @@ def test_batch_init_validates_descriptions_before_any_cuda_call():
     assert rok._lib.rok_batch_init(ctypes.byref(h), descs, 2, None) == rok.ROK_ERR_UNSUPPORTED
     assert rok._lib.rok_batch_init(ctypes.byref(h), descs, 0, None) == rok.ROK_ERR_INVALID_ARG
     assert rok._lib.rok_batch_init(None, descs, 2, None) == rok.ROK_ERR_INVALID_ARG
+
+
+def test_header_compiles_on_its_own_as_c_and_cxx():
+    import shutil
+    import subprocess
+
+    import pytest
+    hdr = os.path.join(ROOT, 'include', 'rok.h')
+    for cc, args in (('gcc', ['-std=c99', '-x', 'c']), ('g++', ['-std=c++17', '-x', 'c++'])):
+        if shutil.which(cc) is None:
+            pytest.skip('%s not found' % cc)
+        subprocess.run([cc, *args, '-Wall', '-Wextra', '-Werror', '-fsyntax-only', hdr], check=True)

@@ -172,3 +172,92 @@ def test_vjp_unsupported_cases(rok):
     with pytest.raises(rok.RokError) as e:
         rok.rok_vjp(ctx, dev(y4), dev(y4))
     assert e.value.status == rok.ROK_ERR_UNSUPPORTED
+
+
+def _ns_case():
+    prob, y = W.taylor_green(40, reynolds=300.0)
+    prob = W.FlowProblem(**{**prob.__dict__, 'ny': 36, 'ly': prob.ly * 36 / 40})
+    y = np.ascontiguousarray(y[:, :36, :] + 0.01 * W.random_smooth_state(prob, seed=9))
+    return prob, y
+
+
+@pytest.mark.parametrize('mode', ['strict', 'fast'])
+def test_recorded_step_and_its_reverse_are_bit_identical_to_the_recomputed_ones(rok, mode):
+    # two steps recorded on tapes, reversed in the opposite order: each y_{n+1}
+    # equals rok_step's and each reverse equals rok_step_vjp's, bit for bit (the
+    # same kernels on the same data; the tape only moves the internals)
+    import torch
+    prob, y = _ns_case()
+    h = I.dt_from_cfl(prob, y, 4.0)
+    M = 6
+    ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+    nbytes = rok.rok_tape_bytes(ctx, M)
+    assert nbytes >= (10 + M) * y.size * 8
+    ys = [dev(y)]
+    for _ in range(2):
+        ys.append(ys[-1].clone())
+        rok.rok_step(ctx, ys[-1], h, M)
+    yr = dev(y)
+    tapes = [rok.rok_step_record(ctx, yr, h, M)]
+    assert torch.equal(yr, ys[1])
+    tapes.append(rok.rok_step_record(ctx, yr, h, M))
+    assert torch.equal(yr, ys[2])
+    c = dev(np.random.default_rng(4).standard_normal(y.shape))
+    ref1, m1 = rok.rok_step_vjp(ctx, ys[1], h, M, c)
+    ref0, m0 = rok.rok_step_vjp(ctx, ys[0], h, M, ref1)
+    got1, g1 = rok.rok_step_vjp_tape(ctx, tapes[1], c)
+    got0, g0 = rok.rok_step_vjp_tape(ctx, tapes[0], got1, out=got1)
+    assert torch.equal(got0, ref0)
+    assert (g1, g0) == (m1, m0)
+    assert m0 != 0.0
+
+
+def test_tape_rejects_bad_arguments(rok):
+    import torch
+    prob, y = _ns_case()
+    h = I.dt_from_cfl(prob, y, 4.0)
+    ctx = rok.rok_init(prob, krylov_max=4)
+    tape = torch.empty(rok.rok_tape_bytes(ctx, 4) + 512, dtype=torch.uint8, device='cuda')
+    yd = dev(y)
+    c = dev(np.ones(y.shape))
+
+    def status(call):
+        with pytest.raises(rok.RokError) as e:
+            call()
+        return e.value.status
+
+    assert status(lambda: rok.rok_tape_bytes(ctx, 5)) == rok.ROK_ERR_INVALID_ARG      # M > krylov_max
+    assert status(lambda: rok.rok_step_record(ctx, yd, h, 4, tape[8:])) == rok.ROK_ERR_INVALID_ARG  # unaligned
+    assert status(lambda: rok.rok_step_record(ctx, yd, -h, 4, tape)) == rok.ROK_ERR_INVALID_ARG
+    assert torch.equal(yd, dev(y))
+    tape.zero_()
+    assert status(lambda: rok.rok_step_vjp_tape(ctx, tape, c)) == rok.ROK_ERR_INVALID_ARG  # no header
+    rok.rok_step_record(ctx, yd, h, 4, tape)
+    alias = tape[1024:1024 + y.size * 8].view(torch.float64)
+    assert status(lambda: rok.rok_step_vjp_tape(ctx, tape, c, out=alias)) == rok.ROK_ERR_INVALID_ARG
+    # a tape of another problem (other N)
+    p2, y2 = W.taylor_green(32, reynolds=300.0)
+    ctx2 = rok.rok_init(p2, krylov_max=4)
+    assert status(lambda: rok.rok_step_vjp_tape(ctx2, tape, dev(np.ones(y2.shape)))) == rok.ROK_ERR_INVALID_ARG
+    # the binary32 basis has no reverse
+    ctx3 = rok.rok_init(prob, krylov_max=4, basis=rok.ROK_BASIS_FP32)
+    assert status(lambda: rok.rok_step_record(ctx3, dev(y), h, 4, tape)) == rok.ROK_ERR_UNSUPPORTED
+
+
+def test_gradient_with_tapes_is_bit_identical_to_recomputation(rok):
+    # 7 steps, checkpoint every 3 (segments 3, 3, 1): the tape path records the
+    # ragged last segment in the forward and reuses its tapes for the others
+    import torch
+
+    from paper_1607_06834_gb300 import autograd as G
+    prob, y0 = _ns_case()
+    h = I.dt_from_cfl(prob, y0, 2.0)
+    ctx = rok.rok_init(prob, krylov_max=6)
+    grads = []
+    for tapes in (True, False):
+        y = dev(y0).requires_grad_(True)
+        mu = torch.tensor(prob.mu, dtype=torch.float64, requires_grad=True)
+        G.kinetic_energy(G.integrate(ctx, y, mu, h, 6, 7, checkpoint_every=3, tapes=tapes)).backward()
+        grads.append((y.grad.clone(), float(mu.grad)))
+    assert torch.equal(grads[0][0], grads[1][0])
+    assert grads[0][1] == grads[1][1]
