@@ -675,6 +675,7 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
                                                               const AdjState *as)
 {
     __shared__ double sh[16];
+    unsigned gen = grid_gen(bar);
     const unsigned G = gridDim.x;
     double b[kColChunks][EPL], w[kColChunks][EPL], v[kColChunks][EPL];
     size_t e0[kColChunks];
@@ -726,7 +727,7 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
         }
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
         if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
-        if (!grid_barrier(bar, G, &st->status)) return;
+        if (!grid_barrier(bar, G, &st->status, gen)) return;
         double *t = pin;
         pin = pout;
         pout = t;

@@ -228,14 +228,26 @@ __device__ __forceinline__ T warp_tree_partials(const T *__restrict__ p, int P)
     return lane_tree(leaf_tree(p, lane * C, C, P));
 }
 
-// The same tree by the whole CTA (thread t owns C = P2/256 leaves), result in
-// every thread.
+// The same tree by the CTA's first four warps, one per scheduler (thread
+// t < 128 owns C = P2/128 leaves; the four warp sums are added by one thread),
+// result in every thread; sh >= 5 values.  Half the FP64 instructions of a
+// tree spread over all eight warps, whose lane butterflies would repeat on
+// every warp.
 template <class T>
 __device__ __forceinline__ T tree_partials(const T *__restrict__ p, int P, T *sh)
 {
     const int P2 = pow2_ceil(P);
-    const int C = P2 > RT ? P2 / RT : 1;
-    return cta_tree(lane_tree(leaf_tree(p, threadIdx.x * C, C, P)), sh);
+    const int C = P2 > 128 ? P2 / 128 : 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (wid < 4) {
+        const T v = lane_tree(leaf_tree(p, threadIdx.x * C, C, P));
+        if (lane == 0) sh[wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh[4] = (sh[0] + sh[1]) + (sh[2] + sh[3]);
+    __syncthreads();
+    return sh[4];
 }
 
 __device__ __forceinline__ size_t lane_e0() { return ((size_t)blockIdx.x * RT + threadIdx.x) * EPL; }
@@ -267,25 +279,32 @@ __device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned x)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
 }
 
+// The barrier's generation when a persistent kernel starts (thread 0; read
+// before the CTA first arrives, so no barrier of this launch can have advanced
+// it yet).  The CTA then counts the generations itself.
+__device__ __forceinline__ unsigned grid_gen(GridBarrier *bar)
+{
+    return threadIdx.x == 0 ? ld_acquire_gpu(&bar->gen) : 0u;
+}
+
 // Bounded grid barrier: after the CTA barrier, thread 0 arrives on the counter
 // (acquire-release: it publishes the CTA's writes); the last CTA resets the
 // counter and advances the generation (release); the others poll the
-// generation (acquire) with a spin limit.  On expiry the status gets
-// kStatusTimeout and the CTA reports failure (the kernel then returns; nothing
-// waits forever).
-__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, int *status)
+// generation (acquire) until it leaves gen, with a spin limit.  gen (thread 0)
+// advances by one per barrier.  On expiry the status gets kStatusTimeout and
+// the CTA reports failure (the kernel then returns; nothing waits forever).
+__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, int *status, unsigned &gen)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        const unsigned g = ld_acquire_gpu(&bar->gen);
         if (atom_add_acq_rel_gpu(&bar->count, 1u) == nblocks - 1) {
             st_relaxed_gpu(&bar->count, 0u);
             red_add_release_gpu(&bar->gen, 1u);
         } else {
             long long spins = 0;
-            while (ld_acquire_gpu(&bar->gen) == g) {
+            while (ld_acquire_gpu(&bar->gen) == gen) {
                 if (++spins > kBarrierSpins) {
                     atomicOr(status, kStatusTimeout);
                     ok = 0;
@@ -294,6 +313,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks,
                 __nanosleep(32);
             }
         }
+        ++gen;
     }
     __syncthreads();
     return ok != 0;
@@ -511,6 +531,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
     if (threadIdx.x == 0) act = st->active;
     __syncthreads();
     if (act == 0) return;
+    unsigned gen = grid_gen(bar);
     const unsigned G = gridDim.x;
     T wv[kColChunks][EPL], vn[kColChunks][EPL];
     size_t e0[kColChunks];
@@ -555,7 +576,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
         }
     }
     T *pin = partA, *pout = partB;
-    if (!grid_barrier(bar, G, &st->status)) return;
+    if (!grid_barrier(bar, G, &st->status, gen)) return;
     T wnorm0 = T(0);
     for (int i = 0; i <= j; ++i) {
         const T h = tree_partials(pin, P, sh);
@@ -583,7 +604,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
         else sa = chunk_sumv(x[0], sh);
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
         if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
-        if (!grid_barrier(bar, G, &st->status)) return;
+        if (!grid_barrier(bar, G, &st->status, gen)) return;
         T *t = pin;
         pin = pout;
         pout = t;
