@@ -99,6 +99,7 @@ void free_ctx(rok_ctx *c)
     cudaFree(c->pA); cudaFree(c->pB); cudaFree(c->pM);
     cudaFree(c->st);
     cudaFree(c->bar);
+    cudaFree(c->colcnt);
     cudaFreeHost(c->h_st);
     cudaFreeHost(c->h_part);
     for (double *p : c->geo_bufs) cudaFree(p);
@@ -290,6 +291,8 @@ rok_status arnoldi_columns(rok_ctx *c, const double *y, int M)
     cudaStream_t s = c->stream;
     rok_status r;
     void *Vb = c->fp32 ? (void *)c->Vf : (void *)c->V;
+    if (c->col_ctas > 0 && c->persistent && M > 0)
+        CU(cudaMemsetAsync(c->colcnt, 0, column_counter_offset(M) * sizeof(unsigned), s));
     for (int j = 0; j < M; ++j) {
         StencilIO io;
         if (c->exact_jvp) {
@@ -311,7 +314,7 @@ rok_status arnoldi_columns(rok_ctx *c, const double *y, int M)
         cudaError_t e = cudaErrorNotSupported;
         if (c->col_ctas > 0 && c->persistent)
             e = c->ops->arnoldi_column(c->w, Vb, c->fp32 ? 1 : 0, N, N, j, j + 1 < M ? 1 : 0, P, c->pA, c->pB,
-                                       c->bar, st, c->col_ctas, s);
+                                       c->colcnt + column_counter_offset(j), st, c->col_ctas, s);
         if (e == cudaSuccess) {
             c->launches++;
             continue;
@@ -566,6 +569,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     if (ok && c->fp32) ok = cudaMalloc(&c->Vf, (size_t)(c->mmax + 1) * N * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->st, sizeof(StepState)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->bar, sizeof(GridBarrier)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->colcnt, column_counter_offset(kMaxKrylov) * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_st, sizeof(StepState)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_part, sizeof(double) * 2 * (kMaxKrylov + 2) * (size_t)c->P) == cudaSuccess;
     if (!ok) { free_ctx(c); return ROK_ERR_NOMEM; }

@@ -10,6 +10,11 @@
 namespace rok {
 
 
+// Arrival counters of the persistent Arnoldi column kernel: column j uses the
+// j + 2 counters from column_counter_offset(j); an Arnoldi process of M columns
+// zeroes the first column_counter_offset(M) before its first column.
+inline size_t column_counter_offset(int j) { return (size_t)j * (j + 3) / 2; }
+
 // Step state kept in device memory so that a whole step runs without host
 // synchronisation (and can be captured in a CUDA graph).
 struct StepState {
@@ -68,12 +73,14 @@ struct LinalgOps {
     // co-resident): h_ij = <v_i, w>, w -= h_ij v_i for i = 0..j (modified
     // Gram-Schmidt), then, when next != 0, h_{j+1,j} = ||w||, the breakdown test
     // and v_{j+1} = w * (1/h_{j+1,j}).  w and the next basis vector stay in
-    // registers between passes; partA/partB hold 2P partials each.  Same
-    // arithmetic as dot2 + mgs + normalize.  Returns cudaErrorNotSupported when
-    // the ctas cannot cover the P chunks (caller falls back).
+    // registers between passes; partA/partB hold 2P partials each; cnt[0 ..
+    // j + 2) are the arrival counters of the partial generations, zero on entry
+    // (column_counter_offset).  Same arithmetic as dot2 + mgs + normalize.
+    // Returns cudaErrorNotSupported when the ctas cannot cover the P chunks
+    // (caller falls back).
     // fp32: the basis V is binary32 and the Gram-Schmidt arithmetic binary32 (w rounded on load)
     cudaError_t (*arnoldi_column)(const double *w, void *V, int fp32, size_t ldv, size_t n, int j, int next, int P,
-                                  double *partA, double *partB, GridBarrier *bar, StepState *st, int ctas,
+                                  double *partA, double *partB, unsigned *cnt, StepState *st, int ctas,
                                   cudaStream_t s);
     // co-resident CTAs of arnoldi_column on this device (0 if cooperative launch is unavailable)
     int (*arnoldi_column_ctas)(int sms);

@@ -348,6 +348,38 @@ __device__ __forceinline__ void chunk_sum2v(const T a, const T b, T *sh, T &sa, 
     }
 }
 
+// Per-generation arrival counters (the persistent Arnoldi column): after
+// writing its partials of a generation, a CTA adds one to that generation's
+// counter (release, no reply awaited); a CTA that needs the generation waits
+// (thread 0, acquire, bounded) until the counter reaches the grid size.  Each
+// counter serves one generation and is zeroed before the launch, so the
+// arrivals neither wait for an atomic's reply nor need a release by the last
+// one.
+__device__ __forceinline__ void gen_arrive(unsigned *cnt)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) red_add_release_gpu(cnt, 1u);
+}
+
+__device__ __forceinline__ bool gen_wait(const unsigned *cnt, unsigned nblocks, int *status)
+{
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        long long spins = 0;
+        while (ld_acquire_gpu(cnt) < nblocks) {
+            if (++spins > kBarrierSpins) {
+                atomicOr(status, kStatusTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 // Hint: fetch the 128-byte line holding this thread's entries of p (from e0)
 // into L2; one thread per line issues it.
 template <class T>
@@ -522,7 +554,7 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double *__restrict__
 template <class T>
 __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__restrict__ w, T *__restrict__ V,
                                                                size_t ldv, size_t n, int j, int next, int P,
-                                                               T *partA, T *partB, GridBarrier *bar,
+                                                               T *partA, T *partB, unsigned *cnt,
                                                                StepState *st, double brk_tol)
 {
     static_assert(kColChunks == 2, "the CTA sums are formed for two chunks at once");
@@ -531,7 +563,6 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
     if (threadIdx.x == 0) act = st->active;
     __syncthreads();
     if (act == 0) return;
-    unsigned gen = grid_gen(bar);
     const unsigned G = gridDim.x;
     T wv[kColChunks][EPL], vn[kColChunks][EPL];
     size_t e0[kColChunks];
@@ -575,10 +606,13 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
             partA[P + blockIdx.x + G] = s1b;
         }
     }
+    gen_arrive(cnt);
     T *pin = partA, *pout = partB;
-    if (!grid_barrier(bar, G, &st->status, gen)) return;
     T wnorm0 = T(0);
     for (int i = 0; i <= j; ++i) {
+        // generation i complete; the buffer written next (i + 1) was last read
+        // for generation i - 1, which every CTA finished before its arrival at i
+        if (!gen_wait(cnt + i, G, &st->status)) return;
         const T h = tree_partials(pin, P, sh);
         if (i == 0) wnorm0 = sqrt(tree_partials(pin + P, P, sh));
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -604,12 +638,13 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
         else sa = chunk_sumv(x[0], sh);
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
         if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
-        if (!grid_barrier(bar, G, &st->status, gen)) return;
+        gen_arrive(cnt + i + 1);
         T *t = pin;
         pin = pout;
         pout = t;
     }
     if (!next) return;   // last column: the orthogonalised w is not needed further
+    if (!gen_wait(cnt + j + 1, G, &st->status)) return;
     const T hn = sqrt(tree_partials(pin, P, sh));
     const bool brk = !((double)hn > brk_tol * (double)wnorm0);
     if (brk) {
@@ -692,7 +727,7 @@ static int arnoldi_column_ctas(int sms)
 }
 
 static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv, size_t n, int j, int next, int P,
-                                  double *partA, double *partB, GridBarrier *bar, StepState *st, int ctas,
+                                  double *partA, double *partB, unsigned *cnt, StepState *st, int ctas,
                                   cudaStream_t s)
 {
     if (ctas <= 0) return cudaErrorNotSupported;
@@ -702,12 +737,12 @@ static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv
         float *Vf = static_cast<float *>(V);
         float *pa = reinterpret_cast<float *>(partA), *pb = reinterpret_cast<float *>(partB);
         double tol = 1e-5;
-        void *args[] = {&w, &Vf, &ldv, &n, &j, &next, &P, &pa, &pb, &bar, &st, &tol};
+        void *args[] = {&w, &Vf, &ldv, &n, &j, &next, &P, &pa, &pb, &cnt, &st, &tol};
         return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<float>, dim3(G), dim3(RT), args, 0, s);
     }
     double *Vd = static_cast<double *>(V);
     double tol = 1e-12;
-    void *args[] = {&w, &Vd, &ldv, &n, &j, &next, &P, &partA, &partB, &bar, &st, &tol};
+    void *args[] = {&w, &Vd, &ldv, &n, &j, &next, &P, &partA, &partB, &cnt, &st, &tol};
     return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<double>, dim3(G), dim3(RT), args, 0, s);
 }
 
