@@ -663,19 +663,19 @@ __global__ void __launch_bounds__(RT) mgsrev_kernel(double *__restrict__ wb, dou
 
 // The j+1 reverse passes of mgsrev_kernel for Arnoldi column j in one
 // cooperative launch (the mirror of arnoldi_column_kernel: the adjoint wbar and
-// w stay in registers, v_i is carried from one pass to the next, a bounded grid
-// barrier between passes).  On entry wb holds the adjoint of w_{j+1}, wcur =
+// w stay in registers, v_i is carried from one pass to the next, bounded waits
+// on per-pass arrival counters).  On entry wb holds the adjoint of w_{j+1}, wcur =
 // w_{j+1} and partA the chunk partials of <v_j, wbar> (dot2, as on the
 // pass-by-pass path); on exit wb holds the adjoint of w_0 = J v_j (wcur is not
-// updated).  The same arithmetic as the pass-by-pass kernels.
+// updated).  cnt[0 .. j) are the arrival counters of the passes' partials
+// (zero on entry).  The same arithmetic as the pass-by-pass kernels.
 __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict__ wb, const double *__restrict__ wcur,
                                                               double *__restrict__ Vb, const double *__restrict__ V,
                                                               size_t ldv, size_t n, int j, int P, double *partA,
-                                                              double *partB, GridBarrier *bar, StepState *st,
+                                                              double *partB, unsigned *cnt, StepState *st,
                                                               const AdjState *as)
 {
     __shared__ double sh[16];
-    unsigned gen = grid_gen(bar);
     const unsigned G = gridDim.x;
     double b[kColChunks][EPL], w[kColChunks][EPL], v[kColChunks][EPL];
     size_t e0[kColChunks];
@@ -695,6 +695,9 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
     double sa, sb;
     double *pin = partA, *pout = partB;
     for (int i = j; i >= 0; --i) {
+        // the partials of pass i + 1 (counter j - i - 1; those of pass j come
+        // from the preceding launch)
+        if (i < j && !gen_wait(cnt + (j - i - 1), G, &st->status)) return;
         const double d = tree_partials(pin, P, sh);
         const double hij = st->H[i * kMaxKrylov + j];
         const double hb = as->Hb[i * kMaxKrylov + j] - d;
@@ -727,7 +730,7 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
         }
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
         if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
-        if (!grid_barrier(bar, G, &st->status, gen)) return;
+        gen_arrive(cnt + (j - i));
         double *t = pin;
         pin = pout;
         pout = t;
@@ -861,7 +864,6 @@ static rok_status step_internals(rok_ctx *c, const double *y, double h, int M, i
     rok_status r;
     CU(cudaMemcpyAsync(A->y1, y, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CU(launch_begin(st, h, kRokGamma, M, s));
-    CU(cudaMemsetAsync(&c->bar->count, 0, sizeof(unsigned), s));
     if ((r = rok_host::enqueue_step_body(c, A->y1, M)) != ROK_OK) return r;
     CU(cudaMemcpyAsync(A->h_st, st, offsetof(StepState, H), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -967,6 +969,9 @@ static rok_status step_reverse(rok_ctx *c, const double *y, double h, int m, con
                                              c->F[2], c->F[3], st, as);
         CU(cudaMemsetAsync(A->F1acc, 0, N * sizeof(double), s));
         c->launches++;
+        // arrival counters of the cooperative reverse launches: column j takes j
+        CU(cudaMemsetAsync(c->colcnt, 0, column_counter_offset(m) * sizeof(unsigned), s));
+        unsigned *cnt = c->colcnt;
         for (int j = m - 1; j >= 0; --j) {
             const double *vj = c->V + (size_t)j * N;
             if (j + 1 < m) {
@@ -992,11 +997,12 @@ static rok_status step_reverse(rok_ctx *c, const double *y, double h, int m, con
                 double *Vbp = A->Vb;
                 size_t ldv = N, nn = N;
                 int jj = j, PP = P;
-                GridBarrier *barp = c->bar;
+                unsigned *cntp = cnt;
                 StepState *stp = st;
                 const AdjState *asp = as;
-                void *args[] = {&wbp, &wcp, &Vbp, &Vp, &ldv, &nn, &jj, &PP, &pa, &pb, &barp, &stp, &asp};
+                void *args[] = {&wbp, &wcp, &Vbp, &Vp, &ldv, &nn, &jj, &PP, &pa, &pb, &cntp, &stp, &asp};
                 CU(cudaLaunchCooperativeKernel((const void *)mgsrev_column_kernel, dim3(G), dim3(RT), args, 0, s));
+                cnt += j;
                 c->launches++;
             } else {
                 double *pin = A->pA, *pout = A->pB;
@@ -1190,8 +1196,6 @@ rok_status rok_step_vjp_tape(rok_ctx *c, const void *tape, const double *ybar_in
         CU(cudaMemcpyAsync(A->wlast, vec(9), vb, dd, s));
         CU(cudaMemcpy2DAsync(c->V, vb, vec(10), L.stride, vb, hd.m, dd, s));
     }
-    // a grid barrier that timed out leaves its arrival count behind: start clean
-    CU(cudaMemsetAsync(&c->bar->count, 0, sizeof(unsigned), s));
     return step_reverse(c, (const double *)vec(0), hd.h, hd.m, ybar_in, ybar_out, mubar);
 }
 

@@ -98,7 +98,6 @@ void free_ctx(rok_ctx *c)
     cudaFree(c->w); cudaFree(c->t0); cudaFree(c->t1); cudaFree(c->t2);
     cudaFree(c->pA); cudaFree(c->pB); cudaFree(c->pM);
     cudaFree(c->st);
-    cudaFree(c->bar);
     cudaFree(c->colcnt);
     cudaFreeHost(c->h_st);
     cudaFreeHost(c->h_part);
@@ -568,13 +567,11 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     for (int i = 0; i < 4 && ok; ++i) ok = al(&c->F[i], N) && al(&c->K[i], N);
     if (ok && c->fp32) ok = cudaMalloc(&c->Vf, (size_t)(c->mmax + 1) * N * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->st, sizeof(StepState)) == cudaSuccess;
-    ok = ok && cudaMalloc(&c->bar, sizeof(GridBarrier)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->colcnt, column_counter_offset(kMaxKrylov) * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_st, sizeof(StepState)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->h_part, sizeof(double) * 2 * (kMaxKrylov + 2) * (size_t)c->P) == cudaSuccess;
     if (!ok) { free_ctx(c); return ROK_ERR_NOMEM; }
     if (cudaMemset(c->st, 0, sizeof(StepState)) != cudaSuccess) { free_ctx(c); return ROK_ERR_CUDA; }
-    if (cudaMemset(c->bar, 0, sizeof(GridBarrier)) != cudaSuccess) { free_ctx(c); return ROK_ERR_CUDA; }
     c->col_ctas = c->ops->arnoldi_column_ctas(sms);
     if (c->fp32 && (c->col_ctas <= 0 || (c->P + c->col_ctas - 1) / c->col_ctas > 2)) {
         // the binary32 basis runs on the persistent column kernel only
@@ -694,8 +691,6 @@ rok_status rok_step(rok_ctx *c, double *y, double h, int M, rok_step_info *info)
     c->last.residual_evals = 1 + M + 3;
     c->last.jvps = M;
     CU(launch_begin(c->st, h, kRokGamma, M, c->stream));
-    // a grid barrier that timed out leaves its arrival count behind: start clean
-    CU(cudaMemsetAsync(&c->bar->count, 0, sizeof(unsigned), c->stream));
     c->launches++;
     if (c->use_graph && !c->time_stencil) {
         // graphs are captured and replayed on a private non-blocking stream fenced

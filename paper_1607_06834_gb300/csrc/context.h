@@ -37,8 +37,7 @@ struct rok_ctx {
     double *w = nullptr, *t0 = nullptr, *t1 = nullptr, *t2 = nullptr;
     double *pA = nullptr, *pB = nullptr, *pM = nullptr;   // partial sums
     StepState *st = nullptr;
-    GridBarrier *bar = nullptr; // grid barrier of the persistent reverse Gram-Schmidt kernel
-    unsigned *colcnt = nullptr; // arrival counters of the persistent Arnoldi column kernel
+    unsigned *colcnt = nullptr; // arrival counters of the persistent Gram-Schmidt column kernels
     int col_ctas = 0;           // co-resident CTAs of that kernel (0: multi-kernel path)
     bool persistent = true;     // use the persistent column kernels where they fit
     StepState *h_st = nullptr;  // pinned mirror

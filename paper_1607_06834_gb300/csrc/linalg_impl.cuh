@@ -252,71 +252,21 @@ __device__ __forceinline__ T tree_partials(const T *__restrict__ p, int P, T *sh
 
 __device__ __forceinline__ size_t lane_e0() { return ((size_t)blockIdx.x * RT + threadIdx.x) * EPL; }
 
-// ---- persistent kernels: grid barrier and paired chunk sums ---------------------
+// ---- persistent kernels: arrival counters and paired chunk sums -----------------
 
 constexpr int kColChunks = 2;                  // chunks of 2048 entries per CTA (max)
 constexpr long long kBarrierSpins = 1LL << 22; // 4M polls (~0.3 s or more), then give up
 
-// gpu-scope acquire / release accesses of the grid barrier's words
+// gpu-scope acquire / release accesses of the arrival counters
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned x)
-{
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(x) : "memory");
-    return old;
-}
-__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned x)
-{
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
-}
 __device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned x)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
-}
-
-// The barrier's generation when a persistent kernel starts (thread 0; read
-// before the CTA first arrives, so no barrier of this launch can have advanced
-// it yet).  The CTA then counts the generations itself.
-__device__ __forceinline__ unsigned grid_gen(GridBarrier *bar)
-{
-    return threadIdx.x == 0 ? ld_acquire_gpu(&bar->gen) : 0u;
-}
-
-// Bounded grid barrier: after the CTA barrier, thread 0 arrives on the counter
-// (acquire-release: it publishes the CTA's writes); the last CTA resets the
-// counter and advances the generation (release); the others poll the
-// generation (acquire) until it leaves gen, with a spin limit.  gen (thread 0)
-// advances by one per barrier.  On expiry the status gets kStatusTimeout and
-// the CTA reports failure (the kernel then returns; nothing waits forever).
-__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, int *status, unsigned &gen)
-{
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        if (atom_add_acq_rel_gpu(&bar->count, 1u) == nblocks - 1) {
-            st_relaxed_gpu(&bar->count, 0u);
-            red_add_release_gpu(&bar->gen, 1u);
-        } else {
-            long long spins = 0;
-            while (ld_acquire_gpu(&bar->gen) == gen) {
-                if (++spins > kBarrierSpins) {
-                    atomicOr(status, kStatusTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        ++gen;
-    }
-    __syncthreads();
-    return ok != 0;
 }
 
 // The sums of two 2048-entry chunks at once from the lanes' parts a and b
@@ -578,7 +528,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
 #pragma unroll
             for (int k = 0; k < EPL; ++k) wv[c][k] = (T)wd[k];
             load8(V, e0[c], n, vn[c]);     // v_0
-            if (j >= 1) prefetch_l2(V + ldv, e0[c], n);   // v_1, read after the first barrier
+            if (j >= 1) prefetch_l2(V + ldv, e0[c], n);   // v_1, read after the first wait
         }
     }
     // pass 0 partials: <v_0, w> and <w, w> (a missing second chunk sums zeros)

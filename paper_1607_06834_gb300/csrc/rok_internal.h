@@ -16,15 +16,9 @@ constexpr int kMaxAdd = 3;       // vectors added to the base state in one stenc
 enum : int {
     kStatusNonfinite = 1,
     kStatusSingular = 2,
-    kStatusTimeout = 4,    // a bounded device wait (grid barrier) gave up
+    kStatusTimeout = 4,    // a bounded device wait (arrival counter) gave up
 };
 
-// Grid barrier of the persistent kernels (device memory, zero-initialised):
-// arrival counter and generation.
-struct GridBarrier {
-    unsigned count;
-    unsigned gen;
-};
 
 // Constants of the finite-volume residual (Sec. 3.2).  Every derived constant is
 // computed on the host by the same expression the plain CPU evaluation uses, so the
