@@ -84,6 +84,12 @@ namespace {
     } while (0)
 
 constexpr int AT = 256;
+// Threads per CTA of the face pass: it needs about 140-160 registers a thread,
+// so only one 256-thread CTA fits an SM and 256^2 faces take two waves with
+// half the SMs idle in the second; 64-thread CTAs, 7 per SM (at most 144
+// registers), take one wave and split the faces over the SMs to within a
+// seventh of an SM's share.
+constexpr int FT = 64;
 constexpr int kFaceVals = 15;   // MUSCL left/right adjoints (8) + viscous input adjoints (7)
 
 __device__ __forceinline__ void prim_at(const StencilConsts &C, const double *__restrict__ y, size_t nc, size_t c,
@@ -303,14 +309,15 @@ __device__ __forceinline__ void roe_vjp(const double *L, const double *R, const 
 // 1: y-faces, face j of column i between (i, j-1) and (i, j)).  Stores
 // fa[q * nc + face] for q < 15 and one partial of ubar . df/dmu per CTA.
 template <bool VISC, int D>
-__global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, const double *__restrict__ pr,
+__global__ void __launch_bounds__(FT, 7) vjp_face_kernel(const StencilConsts C, const double *__restrict__ pr,
                                                       const double *__restrict__ ub, double *__restrict__ fa,
                                                       double *__restrict__ mupart)
 {
-    __shared__ double sh[10];
+    static_assert(FT == 64, "the CTA sum below adds two warp sums");
+    __shared__ double sh[2];
     const int nx = C.nx, ny = C.ny;
     const size_t nc = (size_t)nx * ny;
-    const size_t t = (size_t)blockIdx.x * AT + threadIdx.x;
+    const size_t t = (size_t)blockIdx.x * FT + threadIdx.x;
     double mu_c = 0.0;
     if (t < nc) {
         const int i = (int)(t % nx), j = (int)(t / nx);
@@ -388,8 +395,10 @@ __global__ void __launch_bounds__(AT) vjp_face_kernel(const StencilConsts C, con
             mu_c = -((Fb[1] * s1 + Fb[2] * s2) + Fb[3] * ((uf * s1 + vf * s2) + C.kfac * Tn));
         }
     }
-    const double s = cta_tree(lane_tree(mu_c), sh);
-    if (threadIdx.x == 0) mupart[blockIdx.x] = s;
+    const double s = lane_tree(mu_c);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) mupart[blockIdx.x] = sh[0] + sh[1];
 }
 
 struct VjpOut {
@@ -748,21 +757,22 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
     const StencilConsts &C = c->C;
     const size_t nc = (size_t)C.nx * C.ny;
     const int nb = (int)((nc + AT - 1) / AT);
+    const int nf = (int)((nc + FT - 1) / FT);
     double *fxa = A->faces, *fya = A->faces + kFaceVals * nc;
     cudaStream_t s = c->stream;
     prim_kernel<<<nb, AT, 0, s>>>(C, ystate, A->prims);
     if (C.viscous) {
-        vjp_face_kernel<true, 0><<<nb, AT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
-        vjp_face_kernel<true, 1><<<nb, AT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nb);
+        vjp_face_kernel<true, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
+        vjp_face_kernel<true, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
         vjp_cell_kernel<true><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
     } else {
-        vjp_face_kernel<false, 0><<<nb, AT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
-        vjp_face_kernel<false, 1><<<nb, AT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nb);
+        vjp_face_kernel<false, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
+        vjp_face_kernel<false, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
         vjp_cell_kernel<false><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
     }
     c->launches += 4;
     if (dst_mu && C.viscous) {
-        tree_add_kernel<<<1, AT, 0, s>>>(A->mupart, 2 * nb, mu_factor, mu_dev, dst_mu);
+        tree_add_kernel<<<1, AT, 0, s>>>(A->mupart, 2 * nf, mu_factor, mu_dev, dst_mu);
         c->launches++;
     }
     CU(cudaGetLastError());
@@ -801,7 +811,7 @@ rok_status ensure_work(rok_ctx *c, bool full)
     auto al = [&](double **p, size_t n) { return cudaMalloc(p, n * sizeof(double)) == cudaSuccess; };
     bool ok = true;
     if (!A->faces) {
-        A->nmu = 2 * (int)((nc + AT - 1) / AT);
+        A->nmu = 2 * (int)((nc + FT - 1) / FT);
         ok = al(&A->faces, 2 * kFaceVals * nc) && al(&A->prims, 5 * nc) && al(&A->mupart, A->nmu) &&
              cudaMalloc(&A->as, sizeof(AdjState)) == cudaSuccess &&
              cudaMallocHost(&A->h_mub, sizeof(double)) == cudaSuccess;
