@@ -402,6 +402,19 @@ rok_status rok_jvp_noalloc(const rok_problem_desc *desc, const double *y, const 
  * `repeats` timed launches of independent FMA chains.  Synchronises. */
 rok_status rok_fp64_fma_peak(double *tflops, int repeats);
 
+/* Self-test of the bounded waits (no counterpart in the paper).  The
+ * persistent Gram-Schmidt column kernels wait for the other CTAs of their
+ * launch on per-pass arrival counters, each wait bounded by a poll limit after
+ * which the kernel latches a timeout in the context's status and returns
+ * (ROK_ERR_TIMEOUT from the step).  This call runs that wait routine in one
+ * CTA on a counter that nothing advances, with a limit of `polls` (1 ..
+ * 4194304, the kernels' own limit), and reports in *expired (HOST) whether the
+ * wait gave up and latched the timeout (1) as designed; *ms (HOST, nullable)
+ * is its GPU time.  The context's status is put back as it was and the
+ * context stays usable.  Uses the context's counters (not while a step is in flight on its
+ * stream).  Synchronises. */
+rok_status rok_selftest_wait(rok_ctx *ctx, long long polls, int *expired, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ SOURCES = {
     'stencil_strict.cu': ['--fmad=false'],
     'peak.cu': [],
     'noalloc.cu': [],
+    'selftest.cu': [],
     'batch.cu': [],
     'adjoint.cu': [],
     'adaptive.cu': [],

@@ -311,14 +311,15 @@ __device__ __forceinline__ void gen_arrive(unsigned *cnt)
     if (threadIdx.x == 0) red_add_release_gpu(cnt, 1u);
 }
 
-__device__ __forceinline__ bool gen_wait(const unsigned *cnt, unsigned nblocks, int *status)
+__device__ __forceinline__ bool gen_wait(const unsigned *cnt, unsigned nblocks, int *status,
+                                         long long max_spins = kBarrierSpins)
 {
     __shared__ int ok;
     if (threadIdx.x == 0) {
         ok = 1;
         long long spins = 0;
         while (ld_acquire_gpu(cnt) < nblocks) {
-            if (++spins > kBarrierSpins) {
+            if (++spins > max_spins) {
                 atomicOr(status, kStatusTimeout);
                 ok = 0;
                 break;

@@ -137,6 +137,7 @@ _sig = {
     'rok_batch_set_graph': (ctypes.c_int, [_vp, ctypes.c_int]),
     'rok_batch_get_launches': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     'rok_jvp_noalloc': (ctypes.c_int, [ctypes.POINTER(ProblemDesc), _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp]),
+    'rok_selftest_wait': (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -559,6 +560,15 @@ def rok_fp64_fma_peak(repeats=20):
     t = ctypes.c_double(0.0)
     _check(_lib.rok_fp64_fma_peak(ctypes.byref(t), int(repeats)), 'rok_fp64_fma_peak')
     return t.value
+
+
+def rok_selftest_wait(ctx, polls=20000):
+    """``rok_selftest_wait``: run the bounded wait of the persistent kernels on
+    a counter nothing advances; returns (expired, GPU ms)."""
+    ex = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(_lib.rok_selftest_wait(ctx.handle, int(polls), ctypes.byref(ex), ctypes.byref(ms)), 'rok_selftest_wait')
+    return ex.value, ms.value
 
 
 def state_tensor(y, device='cuda'):

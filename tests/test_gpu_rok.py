@@ -435,3 +435,25 @@ def test_persistent_switch_refused_for_binary32_basis(rok):
         rok.rok_set_persistent(ctx, False)
     assert e.value.status == rok.ROK_ERR_UNSUPPORTED
     rok.rok_set_persistent(ctx, True)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(rok):
+    # the wait routine of the persistent Gram-Schmidt kernels, on a counter that
+    # nothing advances: it must end by its poll limit, latch the timeout, and
+    # leave the context able to step (bit-identically to a fresh context)
+    prob, y0 = W.isentropic_vortex(32)
+    h = I.dt_from_cfl(prob, y0, 5.0)
+    ctx = rok.rok_init(prob, krylov_max=8, rounding=rok.ROK_ROUND_STRICT)
+    expired, ms = rok.rok_selftest_wait(ctx, 20000)
+    assert expired == 1
+    assert 0.0 < ms < 2000.0, ms
+    y = dev(y0)
+    rok.rok_step(ctx, y, h, 8, info=True)   # raises if a status were left latched
+    fresh = rok.rok_init(prob, krylov_max=8, rounding=rok.ROK_ROUND_STRICT)
+    yf = dev(y0)
+    rok.rok_step(fresh, yf, h, 8)
+    assert np.array_equal(host(y), host(yf))
+    assert np.array_equal(host(y), I.rok_step(core.System(prob), y0, h, 8))
+    with pytest.raises(rok.RokError) as e:
+        rok.rok_selftest_wait(ctx, 0)
+    assert e.value.status == rok.ROK_ERR_INVALID_ARG
