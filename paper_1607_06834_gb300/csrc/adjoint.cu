@@ -677,21 +677,25 @@ __global__ void __launch_bounds__(RT) mgsrev_kernel(double *__restrict__ wb, dou
 // w_{j+1} and partA the chunk partials of <v_j, wbar> (dot2, as on the
 // pass-by-pass path); on exit wb holds the adjoint of w_0 = J v_j (wcur is not
 // updated).  cnt[0 .. j) are the arrival counters of the passes' partials
-// (zero on entry).  The same arithmetic as the pass-by-pass kernels.
+// (zero on entry).  The same arithmetic as the pass-by-pass kernels.  NC:
+// chunks per CTA (1 when the grid covers every chunk once, which keeps the
+// state of one chunk in registers without spilling, else 2).
+template <int NC>
 __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict__ wb, const double *__restrict__ wcur,
                                                               double *__restrict__ Vb, const double *__restrict__ V,
                                                               size_t ldv, size_t n, int j, int P, double *partA,
                                                               double *partB, unsigned *cnt, StepState *st,
                                                               const AdjState *as)
 {
+    static_assert(NC == 1 || NC == 2, "one or two chunks per CTA");
     __shared__ double sh[16];
     const unsigned G = gridDim.x;
-    double b[kColChunks][EPL], w[kColChunks][EPL], v[kColChunks][EPL];
-    size_t e0[kColChunks];
-    bool have[kColChunks];
-    double x[kColChunks];
+    double b[NC][EPL], w[NC][EPL], v[NC][EPL];
+    size_t e0[NC];
+    bool have[NC];
+    double x[NC];
 #pragma unroll
-    for (int c = 0; c < kColChunks; ++c) {
+    for (int c = 0; c < NC; ++c) {
         const int blk = blockIdx.x + c * G;
         have[c] = blk < P;
         e0[c] = ((size_t)blk * RT + threadIdx.x) * EPL;
@@ -712,7 +716,7 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
         const double hb = as->Hb[i * kMaxKrylov + j] - d;
         double *vbi = Vb + (size_t)i * ldv;
 #pragma unroll
-        for (int c = 0; c < kColChunks; ++c) {
+        for (int c = 0; c < NC; ++c) {
             x[c] = 0.0;
             if (!have[c]) continue;
             double g[EPL];
@@ -732,20 +736,20 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
             }
         }
         if (i == 0) break;
-        if (have[1]) {
-            chunk_sum2v(x[0], x[1], sh, sa, sb);
+        if (NC == 2 && have[NC - 1]) {
+            chunk_sum2v(x[0], x[NC - 1], sh, sa, sb);
         } else {
             sa = chunk_sumv(x[0], sh);
         }
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
-        if (threadIdx.x == 8 && have[1]) pout[blockIdx.x + G] = sb;
+        if (NC == 2 && threadIdx.x == 8 && have[NC - 1]) pout[blockIdx.x + G] = sb;
         gen_arrive(cnt + (j - i));
         double *t = pin;
         pin = pout;
         pout = t;
     }
 #pragma unroll
-    for (int c = 0; c < kColChunks; ++c)
+    for (int c = 0; c < NC; ++c)
         if (have[c]) store8(wb, e0[c], n, b[c]);
 }
 
@@ -841,7 +845,7 @@ int rev_column_ctas()
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgsrev_column_kernel, RT, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mgsrev_column_kernel<2>, RT, 0) != cudaSuccess) return 0;
     return per * sms;
 }
 
@@ -1011,7 +1015,11 @@ static rok_status step_reverse(rok_ctx *c, const double *y, double h, int m, con
                 StepState *stp = st;
                 const AdjState *asp = as;
                 void *args[] = {&wbp, &wcp, &Vbp, &Vp, &ldv, &nn, &jj, &PP, &pa, &pb, &cntp, &stp, &asp};
-                CU(cudaLaunchCooperativeKernel((const void *)mgsrev_column_kernel, dim3(G), dim3(RT), args, 0, s));
+                // one chunk per CTA when the grid covers them all (the one-chunk
+                // kernel needs fewer registers, so it is co-resident wherever
+                // the two-chunk one is)
+                const void *fn = G >= P ? (const void *)mgsrev_column_kernel<1> : (const void *)mgsrev_column_kernel<2>;
+                CU(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(RT), args, 0, s));
                 cnt += j;
                 c->launches++;
             } else {

@@ -457,3 +457,22 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(rok):
     with pytest.raises(rok.RokError) as e:
         rok.rok_selftest_wait(ctx, 0)
     assert e.value.status == rok.ROK_ERR_INVALID_ARG
+
+
+def test_reverse_gram_schmidt_two_chunks_per_cta_at_512(rok):
+    # 512^2: 512 chunks of 2048 entries, more than the co-resident CTAs, so the
+    # cooperative reverse Gram-Schmidt kernel takes two chunks per CTA; it must
+    # give the bits of the pass-by-pass launches
+    import torch
+    prob, y0 = W.taylor_green(512, reynolds=1600.0)
+    h = I.dt_from_cfl(prob, y0, 8.0)
+    M = 6
+    c = dev(np.random.default_rng(11).standard_normal(y0.shape))
+    res = []
+    for persistent in (True, False):
+        ctx = rok.rok_init(prob, krylov_max=M)
+        rok.rok_set_persistent(ctx, persistent)
+        yb, mub = rok.rok_step_vjp(ctx, dev(y0), h, M, c)
+        res.append((yb, mub))
+    assert torch.equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
