@@ -39,13 +39,14 @@ struct Shape {
     static_assert((TXv * TYv) % NTv == 0, "whole cells per thread");
 };
 using Shape32x8 = Shape<32, 8>;
+using CurvShape = Shape<16, 16>;
 
-// the curvilinear kernel uses 32 x 8 tiles (the uniform one: CartShape below)
-constexpr int TX = Shape32x8::TX;
-constexpr int TY = Shape32x8::TY;
-constexpr int NT = Shape32x8::NT;
-constexpr int EW = Shape32x8::EW;
-constexpr int EH = Shape32x8::EH;
+// the curvilinear kernel's tiles (the uniform one: CartShape below)
+constexpr int TX = CurvShape::TX;
+constexpr int TY = CurvShape::TY;
+constexpr int NT = CurvShape::NT;
+constexpr int EW = CurvShape::EW;
+constexpr int EH = CurvShape::EH;
 
 template <class S>
 __device__ __forceinline__ S harten(S lam, S delta)
@@ -425,7 +426,7 @@ __device__ __forceinline__ void visc_n2(S *G, double nx, double ny, double c0, d
 #endif  // ROK_STENCIL_FAST
 
 // shared-memory tile of primitive variables (halo included)
-template <class S, class SH = Shape32x8>
+template <class S, class SH = CurvShape>
 struct Tile {
     S r[SH::EH][SH::EW], u[SH::EH][SH::EW], v[SH::EH][SH::EW], p[SH::EH][SH::EW], T[SH::EH][SH::EW],
         mu[SH::EH][SH::EW];
@@ -434,7 +435,7 @@ struct Tile {
 // lower neighbour along x (dx, the tile's rows 2 .. TY+1 only: dx[k][ly - 2][lx])
 // and y (dy, the tile's columns 2 .. TX+1 only: dy[k][ly][lx - 2]) -- the ones
 // the faces read
-template <class S, class SH = Shape32x8>
+template <class S, class SH = CurvShape>
 struct Diffs {
     S dx[4][SH::TY][SH::EW], dy[4][SH::EH][SH::TX];
 };
@@ -443,7 +444,7 @@ struct Diffs {
 // tangential neighbour rows / columns, shared by the faces above and below:
 // px[q][ly - 1][fx] = w[ly][fx + 1] + w[ly][fx + 2] (rows 1 .. TY+2),
 // qy[q][lx - 1][fy] = w[fy + 1][lx] + w[fy + 2][lx] (columns 1 .. TX+2), w = u, v
-template <class S, class SH = Shape32x8>
+template <class S, class SH = CurvShape>
 struct PairSums {
     S px[2][SH::TY + 2][SH::TX + 1], qy[2][SH::TX + 2][SH::TY + 1];
 };
@@ -459,7 +460,7 @@ constexpr size_t pair_sums_bytes()
 #endif
 }
 
-template <class S, class SH = Shape32x8>
+template <class S, class SH = CurvShape>
 struct Faces {
     S fx[4][SH::TY][SH::TX + 1];
     S fy[4][SH::TY + 1][SH::TX];
