@@ -92,10 +92,10 @@ constexpr int AT = 256;
 constexpr int FT = 64;
 constexpr int kFaceVals = 15;   // MUSCL left/right adjoints (8) + viscous input adjoints (7)
 
-__device__ __forceinline__ void prim_at(const StencilConsts &C, const double *__restrict__ y, size_t nc, size_t c,
-                                        double *P, double &T)
+// primitives (rho, u, v, p) and T = p / rho of the conservative state (rho, mx, my, E)
+__device__ __forceinline__ void prim_of(const StencilConsts &C, double rho, double mx, double my, double E, double *P,
+                                        double &T)
 {
-    const double rho = y[c], mx = y[nc + c], my = y[2 * nc + c], E = y[3 * nc + c];
     const double rinv = 1.0 / rho;
     const double u = mx * rinv, v = my * rinv;
     const double p = C.gm1 * (E - 0.5 * (mx * u + my * v));
@@ -107,15 +107,26 @@ __device__ __forceinline__ void prim_at(const StencilConsts &C, const double *__
 }
 
 // Pass 0: the primitives of every cell, once (the face pass reads each cell's
-// from four faces and the viscous terms from four more)
+// from four faces and the viscous terms from four more).  The state is y, or
+// y + (*scale) dir formed on load (the perturbed state y + eps v_j of a JVP in
+// reverse; eps is a power of two, so the sum rounds as a separate pass would).
 __global__ void __launch_bounds__(AT) prim_kernel(const StencilConsts C, const double *__restrict__ y,
+                                                  const double *__restrict__ dir, const double *scale,
                                                   double *__restrict__ pr)
 {
     const size_t nc = (size_t)C.nx * C.ny;
     const size_t t = (size_t)blockIdx.x * AT + threadIdx.x;
     if (t >= nc) return;
+    double q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = y[k * nc + t];
+    if (dir) {
+        const double a = *scale;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = q[k] + a * dir[k * nc + t];
+    }
     double P[4], T;
-    prim_at(C, y, nc, t, P, T);
+    prim_of(C, q[0], q[1], q[2], q[3], P, T);
 #pragma unroll
     for (int k = 0; k < 4; ++k) pr[k * nc + t] = P[k];
     pr[4 * nc + t] = T;
@@ -756,7 +767,7 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
 // residual VJP launches: out1 += s1 g, out2 += s2 g with g = J(ystate)^T ubar;
 // dst_mu += mu_factor (* mu_dev) ubar . df/dmu(ystate)
 rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, const VjpOut &o, double *dst_mu,
-               double mu_factor, const double *mu_dev)
+               double mu_factor, const double *mu_dev, const double *dir = nullptr, const double *dir_scale = nullptr)
 {
     const StencilConsts &C = c->C;
     const size_t nc = (size_t)C.nx * C.ny;
@@ -764,7 +775,7 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
     const int nf = (int)((nc + FT - 1) / FT);
     double *fxa = A->faces, *fya = A->faces + kFaceVals * nc;
     cudaStream_t s = c->stream;
-    prim_kernel<<<nb, AT, 0, s>>>(C, ystate, A->prims);
+    prim_kernel<<<nb, AT, 0, s>>>(C, ystate, dir, dir_scale, A->prims);
     if (C.viscous) {
         vjp_face_kernel<true, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
         vjp_face_kernel<true, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
@@ -1033,11 +1044,9 @@ static rok_status step_reverse(rok_ctx *c, const double *y, double h, int m, con
                     double *t = pin; pin = pout; pout = t;
                 }
             }
-            // w_0 = (f(y + eps v_j) - F1) / eps
-            lin2_kernel<<<eg, AT, 0, s>>>(A->Yt, y, 1.0, vj, 1.0, &st->eps, N);
-            c->launches++;
+            // w_0 = (f(y + eps v_j) - F1) / eps (the state formed in the primitives pass)
             VjpOut o{A->Vb + (size_t)j * N, 1.0, nullptr, A->yb, 1.0, &st->inv_eps};
-            if ((r = vjp(c, A, A->Yt, A->wb, o, &as->mub, 1.0, &st->inv_eps)) != ROK_OK) return r;
+            if ((r = vjp(c, A, y, A->wb, o, &as->mub, 1.0, &st->inv_eps, vj, &st->eps)) != ROK_OK) return r;
             lin2_kernel<<<eg, AT, 0, s>>>(A->F1acc, A->F1acc, 1.0, A->wb, 1.0, nullptr, N);
             c->launches++;
         }
