@@ -630,17 +630,24 @@ __global__ void __launch_bounds__(AT) stage_rev_kernel(int stage, GamRowA gr, co
 }
 
 // Reverse of v = w / hn, hn = ||w|| (or of v_1 = F1 / beta):
-//   out = (base ? base : 0) + vb / hn + (extra - <v, vb> / hn) v, <v, vb> = tree(pin)
+//   out = (base ? base : 0) + vb / hn + (extra - <v, vb> / hn) v, <v, vb> = tree(pin);
+// wout (nullable) = hn v, the orthogonalised w that the pass before needs
 __global__ void __launch_bounds__(AT) normrev_kernel(double *out, const double *base, const double *vb,
                                                      const double *v, size_t n, const double *pin, int P,
-                                                     const double *hn_ptr, const double *extra_ptr)
+                                                     const double *hn_ptr, const double *extra_ptr, double *wout)
 {
     __shared__ double sh[10];
     const double d = tree_partials(pin, P, sh);
     const double hn = *hn_ptr;
-    const double cv = (extra_ptr ? *extra_ptr : 0.0) - d / hn;
-    for (size_t e = (size_t)blockIdx.x * AT + threadIdx.x; e < n; e += (size_t)gridDim.x * AT)
-        out[e] = (base ? base[e] : 0.0) + vb[e] / hn + cv * v[e];
+    // one division per thread; the entries are scaled by the reciprocal (an
+    // FP64 division costs about twenty FP64 instructions on this part)
+    const double rh = 1.0 / hn;
+    const double cv = (extra_ptr ? *extra_ptr : 0.0) - d * rh;
+    for (size_t e = (size_t)blockIdx.x * AT + threadIdx.x; e < n; e += (size_t)gridDim.x * AT) {
+        const double ve = v[e];
+        out[e] = (base ? base[e] : 0.0) + vb[e] * rh + cv * ve;
+        if (wout) wout[e] = hn * ve;   // w = h v (the normalised column scaled back)
+    }
 }
 
 // Reverse of one modified-Gram-Schmidt pass of column j: w_{i+1} = w_i - h_ij v_i,
@@ -1003,10 +1010,11 @@ static rok_status step_reverse(rok_ctx *c, const double *y, double h, int m, con
                 const double *v1 = c->V + (size_t)(j + 1) * N;
                 double *vb1 = A->Vb + (size_t)(j + 1) * N;
                 CU(ops.dot2(v1, vb1, nullptr, nullptr, N, A->pA, P, nullptr, s));
+                // wbar from the normalisation's reverse, and wcur = h_{j+1,j} v_{j+1}
                 normrev_kernel<<<eg, AT, 0, s>>>(A->wb, nullptr, vb1, v1, N, A->pA, P,
-                                                 &st->H[(j + 1) * kMaxKrylov + j], &as->Hb[(j + 1) * kMaxKrylov + j]);
-                lin2_kernel<<<eg, AT, 0, s>>>(A->wcur, nullptr, 0.0, v1, 1.0, &st->H[(j + 1) * kMaxKrylov + j], N);
-                c->launches += 3;
+                                                 &st->H[(j + 1) * kMaxKrylov + j], &as->Hb[(j + 1) * kMaxKrylov + j],
+                                                 A->wcur);
+                c->launches += 2;
             } else {
                 CU(cudaMemsetAsync(A->wb, 0, N * sizeof(double), s));
                 CU(cudaMemcpyAsync(A->wcur, A->wlast, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1052,7 +1060,7 @@ static rok_status step_reverse(rok_ctx *c, const double *y, double h, int m, con
         }
         // v_1 = F1 / beta
         CU(ops.dot2(c->V, A->Vb, nullptr, nullptr, N, A->pA, P, nullptr, s));
-        normrev_kernel<<<eg, AT, 0, s>>>(A->F1b, A->F1b, A->Vb, c->V, N, A->pA, P, &st->beta, nullptr);
+        normrev_kernel<<<eg, AT, 0, s>>>(A->F1b, A->F1b, A->Vb, c->V, N, A->pA, P, &st->beta, nullptr, nullptr);
         lin2_kernel<<<eg, AT, 0, s>>>(A->F1b, A->F1b, 1.0, A->F1acc, -1.0, &st->inv_eps, N);
         c->launches += 3;
     }
