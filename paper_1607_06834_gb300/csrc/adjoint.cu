@@ -156,7 +156,10 @@ __device__ __forceinline__ void roe_vjp(const double *L, const double *R, const 
     // forward (the order of roe_avg and roe_x / roe_y)
     const double kinL = 0.5 * (L[1] * L[1] + L[2] * L[2]), kinR = 0.5 * (R[1] * R[1] + R[2] * R[2]);
     const double eL = (pL * C.inv_gm1 + rL * kinL) + pL, eR = (pR * C.inv_gm1 + rR * kinR) + pR;
-    const double sL = sqrt(rL), sR = sqrt(rR);
+    // square roots from reciprocal square roots (the reverse needs 1/sqrt as well;
+    // an FP64 square root or division costs about twenty FP64 instructions)
+    const double qL = rsqrt(rL), qR = rsqrt(rR);
+    const double sL = rL * qL, sR = rR * qR;
     const double rt = sL * sR;
     const double Y = rt * (sL + sR), den = 1.0 / Y;
     const double rLsR = rL * sR, rRsL = rR * sL;
@@ -165,7 +168,8 @@ __device__ __forceinline__ void roe_vjp(const double *L, const double *R, const 
     const double X = eL * sR + eR * sL, Ht = X * den;
     const double kt = 0.5 * (nt * nt + tt * tt);
     const double ct2 = C.gm1 * (Ht - kt);
-    const double ct = sqrt(ct2), inv_c2 = 1.0 / ct2;
+    const double rc = rsqrt(ct2);
+    const double ct = ct2 * rc, inv_c2 = rc * rc;
     const double drho = rR - rL, dp = pR - pL, dn = nR - nL, dt = tR - tL;
     const double rtct = rt * ct, rcdq = rtct * dn;
     const double q1 = 0.5 * (dp - rcdq), q3 = 0.5 * (dp + rcdq);
@@ -262,7 +266,7 @@ __device__ __forceinline__ void roe_vjp(const double *L, const double *R, const 
     tRb += dtb;
     tLb -= dtb;
     // ct = sqrt(ct2), inv_c2 = 1 / ct2, ct2 = gm1 (Ht - kt)
-    const double ct2b = ctb * 0.5 / ct - inv_c2b * inv_c2 * inv_c2;
+    const double ct2b = (ctb * 0.5) * rc - inv_c2b * inv_c2 * inv_c2;
     Htb += C.gm1 * ct2b;
     ktb -= C.gm1 * ct2b;
     // kt = (nt^2 + tt^2) / 2
@@ -294,8 +298,8 @@ __device__ __forceinline__ void roe_vjp(const double *L, const double *R, const 
     // rt = sL sR, s = sqrt(rho)
     sLb += rtb * sR;
     sRb += rtb * sL;
-    rLb += sLb * 0.5 / sL;
-    rRb += sRb * 0.5 / sR;
+    rLb += (sLb * 0.5) * qL;
+    rRb += (sRb * 0.5) * qR;
     // e = p / (gamma - 1) + rho kin + p, kin = (u^2 + v^2) / 2
     pLb += eLb * (C.inv_gm1 + 1.0);
     pRb += eRb * (C.inv_gm1 + 1.0);
