@@ -107,6 +107,7 @@ extern "C" rok_status rok_jvp_noalloc(const rok_problem_desc *d, const double *y
     if (!d || !y || !fy || !v || !jv) return ROK_ERR_INVALID_ARG;
     if (jv == y || jv == v || jv == fy) return ROK_ERR_INVALID_ARG;
     if (d->rounding != ROK_ROUND_FAST && d->rounding != ROK_ROUND_STRICT) return ROK_ERR_INVALID_ARG;
+    if (d->jvp != ROK_JVP_FD) return ROK_ERR_UNSUPPORTED;   // the dual-number product is not offered here
     size_t N;
     if (d->kind == ROK_LORENZ96) {
         if (d->nx < 4) return ROK_ERR_INVALID_ARG;
