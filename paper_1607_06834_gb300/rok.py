@@ -138,6 +138,7 @@ _sig = {
     'rok_batch_get_launches': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     'rok_jvp_noalloc': (ctypes.c_int, [ctypes.POINTER(ProblemDesc), _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp]),
     'rok_selftest_wait': (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    'rok_selftest_rcp': (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -162,11 +163,23 @@ def _check(status, where):
         raise RokError(status, where)
 
 
-def _ptr(t):
+def _ptr(t, numel=None, dtype=torch.float64):
+    """Raw device pointer of a tensor after checking what the C ABI cannot:
+    a contiguous tensor of `dtype` on the current CUDA device, with `numel`
+    entries when given.  A CPU tensor or one of the wrong size would otherwise
+    reach the kernels as an out-of-bounds or host address."""
     if t is None:
         return None
-    if not t.is_contiguous() or t.dtype != torch.float64:
-        raise ValueError('expected a contiguous float64 tensor')
+    if not isinstance(t, torch.Tensor):
+        raise TypeError('expected a torch tensor, got %s' % type(t).__name__)
+    if not t.is_contiguous() or t.dtype != dtype:
+        raise ValueError('expected a contiguous %s tensor' % dtype)
+    if not t.is_cuda:
+        raise ValueError('expected a CUDA tensor (device memory), got one on %s' % t.device)
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError('tensor on %s but the current device is cuda:%d' % (t.device, torch.cuda.current_device()))
+    if numel is not None and t.numel() != numel:
+        raise ValueError('expected %d entries, got %d' % (numel, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -246,14 +259,17 @@ def rok_set_stream(ctx, stream):
 def rok_residual(ctx, y, f=None):
     if f is None:
         f = torch.empty_like(y)
-    _check(_lib.rok_residual(ctx.handle, _ptr(y), _ptr(f)), 'rok_residual')
+    n = ctx.problem.ndof
+    _check(_lib.rok_residual(ctx.handle, _ptr(y, n), _ptr(f, n)), 'rok_residual')
     return f
 
 
 def rok_jvp(ctx, y, v, fy=None, eps=0.0, mode=ROK_JVP_FD, out=None):
     if out is None:
         out = torch.empty_like(y)
-    _check(_lib.rok_jvp(ctx.handle, _ptr(y), _ptr(fy), _ptr(v), _ptr(out), float(eps), int(mode)), 'rok_jvp')
+    n = ctx.problem.ndof
+    _check(_lib.rok_jvp(ctx.handle, _ptr(y, n), _ptr(fy, n), _ptr(v, n), _ptr(out, n), float(eps), int(mode)),
+           'rok_jvp')
     return out
 
 
@@ -263,12 +279,14 @@ def rok_arnoldi(ctx, y, M):
     V = torch.zeros((M, N), dtype=torch.float64, device=y.device)
     H = torch.zeros((M, M), dtype=torch.float64, device=y.device)
     me = ctypes.c_int(0)
-    _check(_lib.rok_arnoldi(ctx.handle, _ptr(y), int(M), _ptr(V), _ptr(H), ctypes.byref(me)), 'rok_arnoldi')
+    _check(_lib.rok_arnoldi(ctx.handle, _ptr(y, ctx.problem.ndof), int(M), _ptr(V), _ptr(H), ctypes.byref(me)),
+           'rok_arnoldi')
     return V[:me.value], H, me.value
 
 
 def _step_call(ctx, y, where, call, info):
     yd, host = ctx._dev_state(y)
+    _ptr(yd, ctx.problem.ndof)
     si = StepInfo()
     st = call(yd, ctypes.byref(si) if (info or host is not None) else None)
     if host is not None:
@@ -306,7 +324,7 @@ def ros_step(ctx, y, h, method=ROK_ROS_ROS4, gmres_m=30, gmres_tol=1e-6, gmres_r
 
 def rok_dt_from_cfl(ctx, y, cfl):
     dt = ctypes.c_double(0.0)
-    _check(_lib.rok_dt_from_cfl(ctx.handle, _ptr(y), float(cfl), ctypes.byref(dt)), 'rok_dt_from_cfl')
+    _check(_lib.rok_dt_from_cfl(ctx.handle, _ptr(y, ctx.problem.ndof), float(cfl), ctypes.byref(dt)), 'rok_dt_from_cfl')
     return dt.value
 
 
@@ -345,7 +363,7 @@ def rok_integrate(ctx, y, T, M, atol, rtol, h0, safety=0.9, facmin=0.2, facmax=5
     """``rok_integrate``: adaptive ROK4 from 0 to T in place; returns the info dict."""
     o = _adapt(atol, rtol, h0, safety, facmin, facmax, max_steps)
     info = AdaptInfo()
-    _check(_lib.rok_integrate(ctx.handle, _ptr(y), float(T), int(M), ctypes.byref(o), ctypes.byref(info)),
+    _check(_lib.rok_integrate(ctx.handle, _ptr(y, ctx.problem.ndof), float(T), int(M), ctypes.byref(o), ctypes.byref(info)),
            'rok_integrate')
     return info.as_dict()
 
@@ -354,7 +372,7 @@ def dopri5_integrate(ctx, y, T, atol, rtol, h0, safety=0.9, facmin=0.2, facmax=5
     """``dopri5_integrate``: adaptive Dormand-Prince 5(4) from 0 to T in place."""
     o = _adapt(atol, rtol, h0, safety, facmin, facmax, max_steps)
     info = AdaptInfo()
-    _check(_lib.dopri5_integrate(ctx.handle, _ptr(y), float(T), ctypes.byref(o), ctypes.byref(info)),
+    _check(_lib.dopri5_integrate(ctx.handle, _ptr(y, ctx.problem.ndof), float(T), ctypes.byref(o), ctypes.byref(info)),
            'dopri5_integrate')
     return info.as_dict()
 
@@ -365,7 +383,9 @@ def rok_vjp(ctx, y, ubar, out=None, mubar=False):
     if out is None:
         out = torch.empty_like(y)
     mb = ctypes.c_double(0.0)
-    _check(_lib.rok_vjp(ctx.handle, _ptr(y), _ptr(ubar), _ptr(out), ctypes.byref(mb) if mubar else None), 'rok_vjp')
+    n = ctx.problem.ndof
+    _check(_lib.rok_vjp(ctx.handle, _ptr(y, n), _ptr(ubar, n), _ptr(out, n), ctypes.byref(mb) if mubar else None),
+           'rok_vjp')
     return (out, mb.value) if mubar else out
 
 
@@ -375,7 +395,8 @@ def rok_step_vjp(ctx, y, h, M, ybar, out=None):
     if out is None:
         out = torch.empty_like(y)
     mb = ctypes.c_double(0.0)
-    _check(_lib.rok_step_vjp(ctx.handle, _ptr(y), float(h), int(M), _ptr(ybar), _ptr(out), ctypes.byref(mb)),
+    n = ctx.problem.ndof
+    _check(_lib.rok_step_vjp(ctx.handle, _ptr(y, n), float(h), int(M), _ptr(ybar, n), _ptr(out, n), ctypes.byref(mb)),
            'rok_step_vjp')
     return out, mb.value
 
@@ -388,9 +409,7 @@ def rok_tape_bytes(ctx, M):
 
 
 def _tape_ptr(tape):
-    if not tape.is_contiguous() or tape.dtype != torch.uint8:
-        raise ValueError('expected a contiguous uint8 tape')
-    return ctypes.c_void_p(tape.data_ptr())
+    return _ptr(tape, None, torch.uint8)
 
 
 def rok_step_record(ctx, y, h, M, tape=None):
@@ -399,7 +418,8 @@ def rok_step_record(ctx, y, h, M, tape=None):
     allocated when None); returns the tape."""
     if tape is None:
         tape = torch.empty(rok_tape_bytes(ctx, M), dtype=torch.uint8, device=y.device)
-    _check(_lib.rok_step_record(ctx.handle, _ptr(y), float(h), int(M), _tape_ptr(tape)), 'rok_step_record')
+    _check(_lib.rok_step_record(ctx.handle, _ptr(y, ctx.problem.ndof), float(h), int(M), _tape_ptr(tape)),
+           'rok_step_record')
     return tape
 
 
@@ -409,7 +429,8 @@ def rok_step_vjp_tape(ctx, tape, ybar, out=None):
     if out is None:
         out = torch.empty_like(ybar)
     mb = ctypes.c_double(0.0)
-    _check(_lib.rok_step_vjp_tape(ctx.handle, _tape_ptr(tape), _ptr(ybar), _ptr(out), ctypes.byref(mb)),
+    n = ctx.problem.ndof
+    _check(_lib.rok_step_vjp_tape(ctx.handle, _tape_ptr(tape), _ptr(ybar, n), _ptr(out, n), ctypes.byref(mb)),
            'rok_step_vjp_tape')
     return out, mb.value
 
@@ -487,7 +508,7 @@ def rok_batch_destroy(b):
 def rok_batch_residual(b, y, f=None):
     if f is None:
         f = torch.zeros_like(y)
-    _check(_lib.rok_batch_residual(b.handle, _ptr(y), _ptr(f)), 'rok_batch_residual')
+    _check(_lib.rok_batch_residual(b.handle, _ptr(y, b.total), _ptr(f, b.total)), 'rok_batch_residual')
     return f
 
 
@@ -498,7 +519,7 @@ def rok_batch_step(b, y, h, M, nsteps=1, info=False):
     info=False raises only on argument or CUDA errors."""
     hv = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (len(b.problems),)))
     si = (StepInfo * len(b.problems))() if info else None
-    st = _lib.rok_batch_step(b.handle, _ptr(y), hv.ctypes.data_as(_dp), int(M), int(nsteps), si)
+    st = _lib.rok_batch_step(b.handle, _ptr(y, b.total), hv.ctypes.data_as(_dp), int(M), int(nsteps), si)
     if not info:
         _check(st, 'rok_batch_step')
         return None
@@ -510,7 +531,7 @@ def rok_batch_step(b, y, h, M, nsteps=1, info=False):
 
 def rok_batch_tune(b, y):
     t = BatchTuning()
-    _check(_lib.rok_batch_tune(b.handle, _ptr(y), ctypes.byref(t)), 'rok_batch_tune')
+    _check(_lib.rok_batch_tune(b.handle, _ptr(y, b.total), ctypes.byref(t)), 'rok_batch_tune')
     return t.as_dict()
 
 
@@ -544,12 +565,17 @@ ROK_NOALLOC_MAX_N = 4096 * 2048
 def rok_jvp_noalloc(problem, y, v, fy, out, eps=0.0, status=None, rounding=ROK_ROUND_FAST, stream=None):
     """``rok_jvp_noalloc``: FD Jacobian-vector product without any device
     allocation by the library (no context; scratch in a static device array).
-    ``out`` (and the optional int32 device tensor ``status``) are the caller's."""
+    ``y``, ``v``, ``fy`` and ``out`` are float64 CUDA tensors of
+    ``problem.ndof`` entries on the current device; ``out`` (and the optional
+    one-entry int32 CUDA tensor ``status``) are the caller's.  Every tensor is
+    checked here before the call: the C entry point has no context that could
+    catch a size or device mismatch."""
     if stream is None:
         stream = torch.cuda.current_stream()
     d, keep = _desc(problem, 0, rounding)
-    st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
-    _check(_lib.rok_jvp_noalloc(ctypes.byref(d), _ptr(y), _ptr(fy), _ptr(v), _ptr(out), float(eps), st,
+    n = problem.ndof
+    st = _ptr(status, 1, torch.int32) if status is not None else None
+    _check(_lib.rok_jvp_noalloc(ctypes.byref(d), _ptr(y, n), _ptr(fy, n), _ptr(v, n), _ptr(out, n), float(eps), st,
                                 ctypes.c_void_p(stream.cuda_stream)), 'rok_jvp_noalloc')
     del keep
     return out
@@ -574,3 +600,16 @@ def rok_selftest_wait(ctx, polls=20000):
 def state_tensor(y, device='cuda'):
     """float64 tensor of a NumPy state on the device (helper for callers)."""
     return torch.from_numpy(np.ascontiguousarray(y, dtype=np.float64)).to(device)
+
+
+def rok_selftest_rcp(x, out=None, stream=None):
+    """``rok_selftest_rcp``: the FMA-build stencil's reciprocal of every entry of
+    the float64 CUDA tensor x."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if out is None:
+        out = torch.empty_like(x)
+    n = x.numel()
+    _check(_lib.rok_selftest_rcp(_ptr(x, n), _ptr(out, n), int(n), ctypes.c_void_p(stream.cuda_stream)),
+           'rok_selftest_rcp')
+    return out
