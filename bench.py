@@ -39,6 +39,7 @@ WORKLOAD = 'ns2d-taylor-green-512x512-Re1600-M0.1-rok4-M20-cfl8'
 # balance 20; JVP state formation y + eps v 8 and quotient 8.
 FLOPS_RESIDUAL_NS = 390 + 10 + 20
 FLOPS_JVP_NS = FLOPS_RESIDUAL_NS + 8 + 8
+BYTES_RESIDUAL, BYTES_JVP = 64, 128
 
 # DRAM bytes (read + write) of one FD-JVP launch of the Navier-Stokes stencil at
 # 512 x 512, from an ncu capture of this workload (dram__bytes_read.sum +
@@ -127,7 +128,8 @@ def reduce_timing(ms_local, units_local, dist_ok):
     no data-path collective: only this scalar reduction and the barriers)."""
     import torch
     import torch.distributed as dist
-    t = torch.tensor([ms_local, units_local], dtype=torch.float64)
+    dev = 'cuda' if dist_ok and dist.get_backend() == 'nccl' else 'cpu'
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=dev)
     if dist_ok:
         mx = t[:1].clone()
         tot = t[1:].clone()
@@ -204,19 +206,19 @@ def run_ours(args):
         rok.rok_set_stencil_timing(ctx, False)
         cnt['stencil_ms'], cnt['stencil_timed'] = c2['stencil_ms'], c2['stencil_timed']
         rok.rok_set_graph(ctx, True)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device='cuda')
-    if ws > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    # whole job: the slowest rank's time, the cell-JVPs of all ranks
+    ms, units = reduce_timing(ms, float(cells * KRYLOV * args.steps), ws > 1)
     ms_per_step = ms / args.steps
-    jvps_per_step = KRYLOV
-    value = ws * cells * jvps_per_step * args.steps / (ms * 1e-3) / 1e6
+    value = units / (ms * 1e-3) / 1e6
 
     # dominant kernel: the residual / JVP stencil (1 + M + 3 launches per step)
     n_res, n_jvp = 4, KRYLOV
     flops_step = cells * (n_res * FLOPS_RESIDUAL_NS + n_jvp * FLOPS_JVP_NS)
     stencil_ms_per_launch = cnt['stencil_ms'] / max(cnt['stencil_timed'], 1)
     achieved = flops_step / (n_res + n_jvp) / (stencil_ms_per_launch * 1e-3) / 1e12
+    # algorithmic bytes of the average launch: a residual reads q and writes f
+    # (64 B per cell), an FD JVP reads y, v, f(y) and writes Jv (128 B per cell)
+    bytes_launch = cells * (n_res * BYTES_RESIDUAL + n_jvp * BYTES_JVP) / (n_res + n_jvp)
 
     # end to end through the public API with host buffers (pinned), copies inside
     yh = torch.from_numpy(y0.copy()).pin_memory()
@@ -306,6 +308,29 @@ def run_ours(args):
                               'rel_l2_vs_fd_after_steps': float((ye - yf).norm() / yf.norm()),
                               'steps_compared': args.steps}
         forms['batched'] = batch_form(10)
+        # the strict-rounding build (no contraction, IEEE division and square
+        # root, the oracle's operation order): the build whose ten-step
+        # trajectory equals the oracle's bit for bit
+        ctxs = rok.rok_init(prob, krylov_max=KRYLOV, rounding=rok.ROK_ROUND_STRICT, stream=stream)
+        if args.graph:
+            rok.rok_set_graph(ctxs, True)
+        ys = rok.state_tensor(y0)
+        for _ in range(args.warmup):
+            rok.rok_step(ctxs, ys, h, KRYLOV)
+        barrier()
+        evs = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rok.rok_step(ctxs, ys, h, KRYLOV)
+            b.record(stream)
+            evs.append((a, b))
+        barrier()
+        mss = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        forms['strict_rounding'] = {'ms_per_step': round(mss, 4), 'speedup_vs_fma': round(ms_per_step / mss, 3),
+                                    'value': round(ws * cells * KRYLOV / (mss * 1e-3) / 1e6, 3),
+                                    'parity': 'bit-exact against the oracle over 10 steps'}
     if rank != 0:
         return None
     peaks, src = _peaks()
@@ -326,13 +351,13 @@ def run_ours(args):
                      'achieved': round(achieved, 4), 'peak': round(fp64_roof, 4), 'unit': 'TFLOP/s',
                      'frac': round(achieved / fp64_roof, 4),
                      'traffic': STENCIL_JVP_DRAM_BYTES_512 if N_GRID == 512 else None,
-                     'traffic_unit': 'bytes per launch (ncu dram read+write)',
-                     'algorithmic_bytes_per_launch': cells * 128,
+                     'traffic_unit': 'bytes per FD-JVP launch (ncu dram read+write)',
+                     'algorithmic_bytes_per_launch': round(bytes_launch),
                      'peak_source': 'FP64 FMA roof = 152 SMs x 2 FMA/clk/SM x 2 flops x measured SM clock',
                      'fp64_fma_microbenchmark_tflops': round(fp64_peak, 4),
                      'flops_per_cell': {'residual': FLOPS_RESIDUAL_NS, 'jvp': FLOPS_JVP_NS},
                      'stencil_ms_per_launch': round(stencil_ms_per_launch, 5),
-                     'hbm_frac_of_' + src: round(cells * 96 / (stencil_ms_per_launch * 1e-3) / 1e9 / peaks['hbm_gbs'], 5)},
+                     'hbm_frac_of_' + src: round(bytes_launch / (stencil_ms_per_launch * 1e-3) / 1e9 / peaks['hbm_gbs'], 5)},
         'clocks': clocks,
         'e2e': {'value': round(e2e_value, 3), 'unit': UNIT, 'h2d_bytes_per_step': int(y0.nbytes),
                 'd2h_bytes_per_step': int(y0.nbytes)},
@@ -633,18 +658,35 @@ def run_configs(args):
 
 def cpu_baseline(prob, y0, h, steps=8):
     """The CPU oracle, as it stands, on a bounded sample: `steps` ROK4 steps of the
-    same workload, single-threaded."""
+    same workload, first single-threaded (the plain oracle), then with its
+    residual and FD-JVP loops on every host core (the OpenMP build of the same
+    C source, same bits; the NumPy parts of the integrator stay on one core)."""
     from oracle import core
     from oracle import integrators as I
-    sys_ = core.System(prob)
-    t0 = time.perf_counter()
-    y = y0
-    for _ in range(steps):
-        y = I.rok_step(sys_, y, h, KRYLOV)
-    dt = time.perf_counter() - t0
-    return {'value': round(prob.ncells * KRYLOV * steps / dt / 1e6, 5), 'unit': UNIT, 'cores': 1,
-            'kind': 'oracle', 'sample': '%d ROK4 step(s) of the 512x512 Taylor-Green workload (M=20), %.1f s'
-                                        % (steps, dt)}
+    cores = len(os.sched_getaffinity(0))
+
+    def run(n):
+        sys_ = core.System(prob)
+        t0 = time.perf_counter()
+        y = y0
+        for _ in range(n):
+            y = I.rok_step(sys_, y, h, KRYLOV)
+        return time.perf_counter() - t0
+
+    dt1 = run(steps)
+    try:
+        core.use_parallel_build(cores)
+        run(1)                                   # thread pool start-up
+        dtn = run(steps)
+    finally:
+        core.use_parallel_build(None)
+    v1 = prob.ncells * KRYLOV * steps / dt1 / 1e6
+    vn = prob.ncells * KRYLOV * steps / dtn / 1e6
+    return {'value': round(vn, 5), 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
+            'sample': '%d ROK4 step(s) of the 512x512 Taylor-Green workload (M=20), %.1f s on %d cores '
+                      '(OpenMP residual, NumPy integrator on one core)' % (steps, dtn, cores),
+            'single_thread': {'value': round(v1, 5), 'unit': UNIT, 'cores': 1,
+                              'sample': '%d ROK4 step(s), %.1f s' % (steps, dt1)}}
 
 
 def run_reference(args):
@@ -656,6 +698,8 @@ def run_reference(args):
     from oracle import integrators as I
     prob, y0 = W.taylor_green(N_GRID, mach=MACH, reynolds=RE)
     h = I.dt_from_cfl(prob, y0, CFL)
+    cores = len(os.sched_getaffinity(0))
+    core.use_parallel_build(cores)          # residual loops on every host core, same bits
     sys_ = core.System(prob)
     y = y0
     for _ in range(args.warmup):
@@ -669,8 +713,9 @@ def run_reference(args):
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': round(dt / args.steps * 1e3, 2),
             'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
             'config': {'workload': WORKLOAD, 'cells': prob.ncells, 'krylov_m': KRYLOV, 'cfl': CFL},
-            'cpu_baseline': {'value': round(value, 5), 'unit': UNIT, 'cores': 1, 'kind': 'oracle',
-                             'sample': '%d timed ROK4 steps of the same workload' % args.steps},
+            'cpu_baseline': {'value': round(value, 5), 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
+                             'sample': '%d timed ROK4 steps of the same workload (OpenMP residual on %d cores, '
+                                       'NumPy integrator on one)' % (args.steps, cores)},
             'e2e': {'value': round(value, 5), 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
 
 
@@ -726,7 +771,7 @@ def _interp_time(points, target):
 
 
 def run_wp(args):
-    """Work-precision with adaptive steps (the paper's comparison, Sec. 4.3):
+    """Work-precision with adaptive steps (the paper's comparison, Sec. 4.2):
     ROK4 with its embedded estimate vs DOPRI5 vs fixed-step RK4 at CFL 1 over
     the same horizon as the time-to-error study, tolerances 1e-4, 1e-6, 1e-8
     (atol = rtol = tol); GPU time by CUDA events, error against an RK4
@@ -780,7 +825,7 @@ def run_wp(args):
 
 
 def run_tte(args):
-    """Time to a fixed L2 error (the paper's work-precision measure, Sec. 4.3):
+    """Time to a fixed L2 error (the paper's work-precision measure, Sec. 4.2):
     ROK4 vs RK4 vs ESDIRK3 Newton-GMRES on one problem, fixed step sizes,
     error against an RK4 reference at a 16x finer step, GPU time of the whole
     integration by CUDA events."""

@@ -127,18 +127,18 @@ rok_status rok_residual(rok_ctx *ctx, const double *y, double *f);
  * keeps the quotient exact), eps <= 0 selects sqrt(2^-52 (1 + ||y||)) / ||v||
  * rounded to the nearest power of two.  mode ROK_JVP_EXACT: the exact
  * directional derivative of the discrete residual by forward-mode dual
- * numbers (the alternative the paper points to in Sec. 2.4); fy and eps are
+ * numbers (the alternative the paper points to in Sec. 2.3); fy and eps are
  * ignored.  All arrays device, N float64. */
 rok_status rok_jvp(rok_ctx *ctx, const double *y, const double *fy, const double *v, double *jv,
                    double eps, int mode);
 
-/* Arnoldi process of Sec. 2.3.3 alone (modified Gram-Schmidt, FD JVPs):
+/* Arnoldi process of Sec. 2.2.2 alone (modified Gram-Schmidt, FD JVPs):
  * builds V (rows v_1..v_Meff, each N float64, row-major M x N) and
  * H = V^T J V (M x M, row-major, zero beyond Meff) of K_M(J(y), f(y)).
  * V, H: device; m_eff: host (this call synchronises).  M <= krylov_max. */
 rok_status rok_arnoldi(rok_ctx *ctx, const double *y, int M, double *V, double *H, int *m_eff);
 
-/* One ROK4 step of size h with Krylov dimension M (Sec. 2.3.3, Eq. ROK),
+/* One ROK4 step of size h with Krylov dimension M (Sec. 2.2.2, Eq. ROK),
  * y in place (device, N float64).  0 <= M <= krylov_max; M = 0 is the
  * explicit RK limit.  info may be NULL (no synchronisation). */
 rok_status rok_step(rok_ctx *ctx, double *y, double h, int M, rok_step_info *info);
@@ -151,7 +151,7 @@ rok_status rk_step(rok_ctx *ctx, double *y, double h, rok_step_info *info);
  * 1e-10, 10).  Host-driven: synchronises the stream every GMRES iteration. */
 rok_status esdirk_step(rok_ctx *ctx, double *y, double h, const esdirk_opts *opts, rok_step_info *info);
 
-/* One Rosenbrock step (Sec. 2.3, Eq. ROS), the paper's ROS4 and ROW
+/* One Rosenbrock step (Sec. 2.2, Eq. ROS), the paper's ROS4 and ROW
  * comparators (table of methods, Sec. 3.1):
  *   Y_i = y_n + h sum_{j<i} alpha_ij k_j,
  *   (I - h g J_n) k_i = f(Y_i) + h J_n sum_{j<i} gamma_ij k_j   (Eq. ROS_stage_eq),
@@ -183,7 +183,7 @@ rok_status rok_sync(rok_ctx *ctx, rok_step_info *info);
  * kernel by kernel (0, default). */
 rok_status rok_set_graph(rok_ctx *ctx, int enable);
 
-/* Modified Gram-Schmidt of the Arnoldi process (Sec. 2.3.3) and its reverse in
+/* Modified Gram-Schmidt of the Arnoldi process (Sec. 2.2.2) and its reverse in
  * rok_step_vjp: one persistent cooperative launch per Krylov column where the
  * device holds the whole grid (1, default), or one launch per pass (0) -- the
  * path that grids beyond the persistent kernels' reach (more than 2 x 2048
@@ -210,7 +210,7 @@ const char *rok_status_string(rok_status s);
 /* ---- Adaptive time stepping ---------------------------------------------
  *
  * Integrate y' = f(y) from 0 to T with step sizes chosen by an embedded error
- * estimate (the paper compares its methods with adaptive steps, Sec. 4.3).
+ * estimate (the paper compares its methods with adaptive steps, Sec. 4.2).
  * err = sqrt(sum_i (e_i / sc_i)^2 / N), sc_i = atol + rtol max(|y_i|, |ynew_i|);
  * a step is accepted when err <= 1; the next step is
  * h min(facmax, max(facmin, safety err^(-1/(q+1)))), q the embedded order,
@@ -269,8 +269,8 @@ rok_status rok_step_vjp(rok_ctx *ctx, const double *y, double h, int M, const do
                         double *mubar);
 
 /* Tapes: the reverse of a step without recomputing the step.  A tape holds
- * what the reverse of one ROK4 step (Sec. 2.3.3, Eq. ROK; Arnoldi of
- * Sec. 2.3.2 with the JVP of Eq. matvecFD) reads: y_n, the F_i and k_i, the
+ * what the reverse of one ROK4 step (Sec. 2.2.2, Eq. ROK; Arnoldi of
+ * Sec. 2.2.1 with the JVP of Eq. matvecFD) reads: y_n, the F_i and k_i, the
  * Krylov basis, H with its LU, lambda_i and phi_i, and the last column's
  * orthogonalised JVP, about (10 + M) state vectors.  The tape is plain device
  * memory owned by the caller, 256-byte aligned, rok_tape_bytes bytes for
@@ -294,7 +294,7 @@ rok_status rok_step_vjp_tape(rok_ctx *ctx, const void *tape, const double *ybar_
 /* ---- Batches: many independent instances stepped together ---------------
  *
  * The paper integrates one problem at a time; a batch steps `count`
- * independent problems with the same ROK4 step (Sec. 2.3.3, Eq. ROK), every
+ * independent problems with the same ROK4 step (Sec. 2.2.2, Eq. ROK), every
  * kernel launch covering all of them, so that small grids fill the GPU.
  *
  * Instances: uniform periodic grids (xv == NULL, every bc ROK_BC_PERIODIC) of
@@ -380,7 +380,9 @@ rok_status rok_batch_get_launches(rok_batch *batch, long long *launches, int res
  * description and rounding mode (same kernels, same result bits).
  *   desc   uniform periodic Euler / Navier-Stokes grids (xv == NULL) or
  *          Lorenz-96; curvilinear grids return ROK_ERR_UNSUPPORTED (their
- *          metrics would need device memory).
+ *          metrics would need device memory), and so does desc->jvp other than
+ *          ROK_JVP_FD (this call computes the finite-difference product only);
+ *          desc->krylov_max and desc->basis are not used (no Krylov basis).
  *   y, fy, v, jv  device, N float64 (N = 4 nx ny, Lorenz-96: nx); fy = f(y)
  *          is required; jv must not overlap the inputs.
  *   eps    > 0 used as given; <= 0 selects the power-of-two increment of rok_jvp.
@@ -389,7 +391,10 @@ rok_status rok_batch_get_launches(rok_batch *batch, long long *launches, int res
  * N beyond ROK_NOALLOC_MAX_N returns ROK_ERR_INVALID_ARG without launching.
  * Calls no cudaMalloc, cudaFree or allocating routine.  The first call on a
  * device resolves the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture.  A cudaDeviceReset of a device discards the
+ * array and the kept address with it: do not call this entry point on that
+ * device again in the same process (reload the library).  All calls
  * share the one array: calls whose execution overlaps on the GPU (different
  * streams, or concurrent host threads) race on it and must be serialised by
  * the caller.  Asynchronous on cuda_stream. */
@@ -401,6 +406,18 @@ rok_status rok_jvp_noalloc(const rok_problem_desc *desc, const double *y, const 
  * throughput of the current device in TFLOP/s (2 flops per FMA), from
  * `repeats` timed launches of independent FMA chains.  Synchronises. */
 rok_status rok_fp64_fma_peak(double *tflops, int repeats);
+
+/* Self-test of the reciprocal of the FMA-build stencil (no counterpart in the
+ * paper).  r[k] = the stencil's 1/x[k]: the hardware estimate
+ * (rcp.approx.ftz.f64) refined by one third-order Newton step.  For
+ * 2^-1022 <= |x| <= 2^1022 it is within one unit in the last place of the
+ * IEEE quotient 1/x; the stencil applies it only to densities and sums of
+ * square roots of densities, which lie far inside that range.  Outside it the
+ * estimate's flush to zero decides: a subnormal, zero or infinite x gives NaN
+ * (the non-finite check of the residual then reports it), |x| > 2^1022 gives
+ * a signed zero.  x, r: DEVICE, n float64 each (n >= 0).  Asynchronous on
+ * cuda_stream. */
+rok_status rok_selftest_rcp(const double *x, double *r, long long n, void *cuda_stream);
 
 /* Self-test of the bounded waits (no counterpart in the paper).  The
  * persistent Gram-Schmidt column kernels wait for the other CTAs of their

@@ -1,6 +1,6 @@
 """Discrete adjoints for gradients of a final-time functional: the transposed
 Jacobian of the residual, the viscosity derivative of the residual, and the
-reverse of one ROK4 step (Sec. 2.3.3, Eq. ROK) with finite-difference
+reverse of one ROK4 step (Sec. 2.2.2, Eq. ROK) with finite-difference
 Jacobian-vector products (Eq. matvecFD).
 
 TEST INFRASTRUCTURE ONLY.  Plain NumPy, binary64, written out step by step.

@@ -3,6 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Lorenz-96 (appendix) is written in NumPy here.
 """
 import ctypes
+import ctypes.util
 
 import numpy as np
 
@@ -25,10 +26,27 @@ class _Problem(ctypes.Structure):
     ]
 
 
+_parallel = False
+
+
+def use_parallel_build(threads):
+    """Switch the residual to the OpenMP build of the same source (identical
+    bits) with `threads` threads, or back to the plain build (threads=None).
+    Only the CPU-baseline timing uses this."""
+    global _lib, _parallel
+    want = threads is not None
+    if want != _parallel:
+        _lib = None
+        _parallel = want
+    lib()
+    if want:
+        ctypes.CDLL(ctypes.util.find_library('gomp') or 'libgomp.so.1').omp_set_num_threads(int(threads))
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build_parallel() if _parallel else _build.build()
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         L.oracle_residual.argtypes = [ctypes.POINTER(_Problem), dp, dp]

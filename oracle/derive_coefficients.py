@@ -3,14 +3,14 @@
 TEST INFRASTRUCTURE ONLY (writes the oracle's own table; the CUDA library
 carries its own literal copy and never imports this file).
 
-The paper defines the ROK step (Sec. 2.3.3, Eq. ROK) but prints no
+The paper defines the ROK step (Sec. 2.2.2, Eq. ROK) but prints no
 coefficients, and the ESDIRK comparator has none either.  Both tables are
 therefore solved here from their order conditions, in 40-digit arithmetic,
 and rounded once to binary64.
 
 ROK4 (4 stages, order 4 for Krylov dimension M >= 4)
 ----------------------------------------------------
-Eq. ROK is algebraically a W-method (Sec. 2.3.2 form, h-scaled stages) with
+Eq. ROK is algebraically a W-method (Sec. 2.2.1 form, h-scaled stages) with
 the Jacobian replaced by A = V H V^T = P J P, P the orthogonal projector on
 K_M(J, f(y_n)).  For M >= 4 every elementary differential of order <= 4 in
 which A multiplies a chain J^k f (k <= 2) equals its exact-Jacobian twin,
@@ -29,7 +29,7 @@ tree [[tau, tau]] splits into an alpha-part (= 1/12) and a gamma-part
 with beta = alpha + gamma (strictly lower), a_i = sum_j alpha_ij,
 beta'_i = sum_j beta_ij.  Choices made here:
   * (alpha, b) = classical RK4, so (1), (3), (5), (7a) hold and the M = 0
-    limit of the method is the classical RK4 step (Sec. 2.3.3 notes that
+    limit of the method is the classical RK4 step (Sec. 2.2.2 notes that
     M = 0 reduces ROK to an explicit Runge-Kutta method);
   * g = 0.5728160624821349, the root in the A-stability interval of
     g^4 - 4g^3 + 3g^2 - 2g/3 + 1/24 = 0, which makes the stability function
@@ -62,7 +62,7 @@ The Dormand-Prince 5(4) pair (Dormand & Prince, J. Comput. Appl. Math. 6,
 1980), 7 stages, first-same-as-last, written here as exact rationals; the
 order conditions it satisfies are checked in the oracle's tests.
 
-ROS4 and ROW (Rosenbrock comparators, Sec. 2.3, Eq. ROS)
+ROS4 and ROW (Rosenbrock comparators, Sec. 2.2, Eq. ROS)
 ---------------------------------------------------------
 The paper's ROS4 is a 4-stage, order-4, L-stable Rosenbrock method and its
 ROW a 4-stage, order-3, L-stable Rosenbrock-W method (table of methods,

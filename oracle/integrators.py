@@ -81,7 +81,7 @@ def fd_eps(ynorm, vnorm=1.0):
 
 
 def arnoldi(sys, y, F1, M, eps, breakdown_tol=None, basis=np.float64):
-    """Modified-Gram-Schmidt Arnoldi (Sec. 2.3.3): V (M_eff x N, rows orthonormal)
+    """Modified-Gram-Schmidt Arnoldi (Sec. 2.2.2): V (M_eff x N, rows orthonormal)
     and H = V^T J V (M_eff x M_eff, upper Hessenberg) of K_M(J, f(y_n)), with the
     Jacobian applied by Eq. matvecFD.  Returns (V, H, M_eff).
 
@@ -172,7 +172,7 @@ def lu_solve(LU, piv, b):
 
 def rok_step(sys, y, h, M, gamma=None, alpha=None, gamma_off=None, b=None, info=None, basis=np.float64,
              stages=None):
-    """One step of the Rosenbrock-Krylov method, Eq. ROK (Sec. 2.3.3):
+    """One step of the Rosenbrock-Krylov method, Eq. ROK (Sec. 2.2.2):
 
         F_i      = f(y_n + sum_{j<i} alpha_ij k_j)
         phi_i    = V^T F_i
@@ -454,7 +454,7 @@ def esdirk_step(sys, y, h, gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, newton_
 
 
 def ros_step(sys, y, h, method='ros4', gmres_m=30, gmres_tol=1e-6, gmres_restarts=5, info=None):
-    """Rosenbrock step, Sec. 2.3, Eq. ROS (method 'ros4') or Rosenbrock-W step
+    """Rosenbrock step, Sec. 2.2, Eq. ROS (method 'ros4') or Rosenbrock-W step
     of the same form (method 'row'):
         Y_i = y_n + h sum_{j<i} alpha_ij k_j,
         (I - h g J_n) k_i = f(Y_i) + h J_n sum_{j<i} gamma_ij k_j   (Eq. ROS_stage_eq),

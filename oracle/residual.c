@@ -1,7 +1,7 @@
 /*
  * FP64 CPU oracle for the semi-discrete compressible Euler / Navier-Stokes
  * right-hand side f(y) of the IVP y' = f(y) (Sec. 2, Eq. ode) and for the
- * finite-difference Jacobian-vector product (Sec. 2.4, Eq. matvecFD).
+ * finite-difference Jacobian-vector product (Sec. 2.3, Eq. matvecFD).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
  * or calls this file; only the test-suite, the smoke check and the CPU
@@ -82,6 +82,13 @@ typedef struct { real_t r, u, v, p, T, mu; } prim;
 
 #define NG 2
 
+/* Every loop marked with this macro writes each entry from its own inputs
+ * only (grid rows, faces or vector entries are independent).  The CPU
+ * baseline build (-fopenmp) runs such loops over threads; the test build
+ * ignores the pragma.  Either way every entry is the same sequence of
+ * operations, so both builds give the same bits. */
+#define ROWS_IN_PARALLEL _Pragma("omp parallel for schedule(static)")
+
 static real_t sutherland(const oracle_problem *P, real_t T)
 {
     if (P->suth_s <= 0.0) return P->mu_ref;
@@ -112,6 +119,7 @@ static void fill_prims(const oracle_problem *P, const real_t *q, prim *W)
     const int nx = P->nx, ny = P->ny;
     const size_t nc = (size_t)nx * ny;
     prim inf = to_prim(P, P->q_inf[0], P->q_inf[1], P->q_inf[2], P->q_inf[3]);
+    ROWS_IN_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = (size_t)j * nx + i;
@@ -414,6 +422,7 @@ static int residual_impl(const oracle_problem *P, const real_t *q, real_t *f)
     const double q_rdx = 0.25 * rdx, q_rdy = 0.25 * rdy;
 
     /* i-faces: between cells (i-1, j) and (i, j) */
+    ROWS_IN_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i <= nx; ++i) {
             size_t fidx = (size_t)j * (nx + 1) + i;
@@ -449,6 +458,7 @@ static int residual_impl(const oracle_problem *P, const real_t *q, real_t *f)
             for (int k = 0; k < 4; ++k) FX[k * nfi + fidx] = F[k];
         }
     /* j-faces: between cells (i, j-1) and (i, j) */
+    ROWS_IN_PARALLEL
     for (int j = 0; j <= ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t fidx = (size_t)j * nx + i;
@@ -484,6 +494,7 @@ static int residual_impl(const oracle_problem *P, const real_t *q, real_t *f)
             for (int k = 0; k < 4; ++k) FY[k * nfj + fidx] = F[k];
         }
     /* cell balance, faces summed west/east then south/north */
+    ROWS_IN_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = (size_t)j * nx + i;
@@ -528,8 +539,10 @@ int oracle_jvp_fd(const oracle_problem *P, const double *y, const double *v, con
     const size_t n = (size_t)4 * P->nx * P->ny;
     double *yp = malloc(n * sizeof(double));
     if (!yp) return -1;
+    ROWS_IN_PARALLEL
     for (size_t k = 0; k < n; ++k) yp[k] = y[k] + eps * v[k];
     int rc = oracle_residual(P, yp, w);
+    ROWS_IN_PARALLEL
     for (size_t k = 0; k < n; ++k) w[k] = (w[k] - f0[k]) / eps;
     free(yp);
     return rc;

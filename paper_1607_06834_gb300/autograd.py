@@ -1,6 +1,6 @@
 """Gradients of a functional of the state after K ROK4 steps, through
 ``torch.autograd``: forward K steps with ``rok_step``, backward with
-``rok_step_vjp`` (the discrete adjoint of each step, Sec. 2.3.3 / Eq. ROK with
+``rok_step_vjp`` (the discrete adjoint of each step, Sec. 2.2.2 / Eq. ROK with
 the finite-difference JVP of Eq. matvecFD, eps held constant).
 
 Memory: the forward keeps the state every ``checkpoint_every`` steps; the

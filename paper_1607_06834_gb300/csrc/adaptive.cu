@@ -1,6 +1,6 @@
 // Adaptive time stepping with embedded error estimates: ROK4 with its embedded
 // order-2 weights and the DOPRI5 comparator (the paper compares methods with
-// adaptive steps, Sec. 4.3; Table of Sec. 3.1 lists DOPRI5).
+// adaptive steps, Sec. 4.2; Table of Sec. 3.1 lists DOPRI5).
 //
 // Controller (Hairer, Norsett & Wanner I, Sec. II.4): err = weighted RMS norm
 // of the estimate, sqrt(sum_i (e_i / sc_i)^2 / N), sc_i = atol + rtol

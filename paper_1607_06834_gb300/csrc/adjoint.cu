@@ -1,6 +1,6 @@
 // Reverse mode (vector-Jacobian products) of the residual and of one ROK4 step
-// with finite-difference Jacobian-vector products (Sec. 2.3.3, Eq. ROK;
-// Sec. 2.4, Eq. matvecFD), for gradients of a final-time functional with
+// with finite-difference Jacobian-vector products (Sec. 2.2.2, Eq. ROK;
+// Sec. 2.3, Eq. matvecFD), for gradients of a final-time functional with
 // respect to the state and the (constant) viscosity.
 //
 // Residual VJP, uniform periodic grids: f_c = -(F_{c+1/2} - F_{c-1/2}) / dx

@@ -1,5 +1,5 @@
 // C ABI of librok (include/rok.h): context, workspace, and the host drivers of
-// the ROK4 step (Sec. 2.3.3, Eq. ROK), classical RK4 (Sec. 2.1, Eq. RK) and
+// the ROK4 step (Sec. 2.2.2, Eq. ROK), classical RK4 (Sec. 2.1, Eq. RK) and
 // ESDIRK3 with matrix-free Newton-GMRES (Sec. 2.1, Eqs. Newton, SDIRK_Newton,
 // Newton_Jac_Matrix).  Every arithmetic step runs in the CUDA kernels of
 // stencil_*.cu and linalg.cu; the host only enqueues launches (and, for the
@@ -278,7 +278,7 @@ rok_status sync_read(rok_ctx *c, rok_step_info *info)
     return s;
 }
 
-// Columns 0..M-1 of the Arnoldi process of Sec. 2.3.3 (v_1 already in V[0]):
+// Columns 0..M-1 of the Arnoldi process of Sec. 2.2.2 (v_1 already in V[0]):
 // JVP of v_j, then the modified-Gram-Schmidt column, either in one persistent
 // cooperative launch or as dot2 + (j+1) mgs passes + normalize.  Both forms
 // perform the same arithmetic.

@@ -1,5 +1,5 @@
 // Batches of independent problems (include/rok.h, rok_batch_*): the ROK4 step of
-// Sec. 2.3.3 (Eq. ROK) applied to many uniform periodic grids at once.  Every
+// Sec. 2.2.2 (Eq. ROK) applied to many uniform periodic grids at once.  Every
 // kernel launch covers all instances: the residual stencil walks a tile table
 // that spans the grids of one physics group, the vector kernels walk 2048-entry
 // chunks that each belong to one instance, and the small per-instance solves

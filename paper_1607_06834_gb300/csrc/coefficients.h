@@ -54,7 +54,7 @@ inline constexpr double kDp5Bhat[7] = {5179.0 / 57600.0,    0.0,  7571.0 / 16695
 // (Solving ODEs II, Sec. IV.7, g = 0.57282), published for the transformed
 // stages u_i (implementation form (1/(h g) I - J) u_i = f(y + sum a_ij u_j)
 // + sum (c_ij / h) u_j, y_1 = y_0 + sum m_j u_j); the driver converts it to
-// the form of Eq. ROS (Sec. 2.3).
+// the form of Eq. ROS (Sec. 2.2).
 inline constexpr double kRos4Gamma = 0.57282;
 inline constexpr double kRos4A[4][4] = {{0.0, 0.0, 0.0, 0.0},
                                         {2.000000000000000, 0.0, 0.0, 0.0},

@@ -1,5 +1,5 @@
 // Forward-mode dual numbers (value, tangent) for the exact Jacobian-vector
-// product J(y) v = d/dt f(y + t v) at t = 0 (Sec. 2.4 mentions exact products
+// product J(y) v = d/dt f(y + t v) at t = 0 (Sec. 2.3 mentions exact products
 // as the alternative to Eq. matvecFD).  Each operation carries the tangent by
 // the chain rule; branches (|x|, the entropy-fix switch) follow the value.
 #pragma once

@@ -1,5 +1,5 @@
 // Vector kernels of the ROK step on GB300: deterministic reductions, the
-// modified-Gram-Schmidt Arnoldi passes (Sec. 2.3.3), the projected stage
+// modified-Gram-Schmidt Arnoldi passes (Sec. 2.2.2), the projected stage
 // solves of Eq. ROK, stage vectors and combines.  Declarations shared by
 // linalg.cu (definitions) and api.cu (host drivers).
 #pragma once

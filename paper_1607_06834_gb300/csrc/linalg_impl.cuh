@@ -1,4 +1,4 @@
-// Vector kernels of the ROK step (Sec. 2.3.3): inner products, the
+// Vector kernels of the ROK step (Sec. 2.2.2): inner products, the
 // modified-Gram-Schmidt passes of the Arnoldi process, the projected stage
 // solves of Eq. ROK, stage vectors and combines.
 //

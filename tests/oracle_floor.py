@@ -1,0 +1,49 @@
+"""Oracle trajectories for the multi-step parity tests, and the oracle's own
+rounding floor.
+
+The FD Jacobian-vector product (Eq. matvecFD) divides a difference of two
+residuals by eps ~ sqrt(u ||y||), so a last-bit change of f becomes a change
+of ~u/eps in the Krylov vectors; over several ROK4 steps (Eq. ROK) the
+trajectory is fixed by the binary64 arithmetic only to that level.  The
+rounding floor of a configuration is measured on the oracle itself: the
+relative L2 distance after `steps` steps between its trajectory from y0 and
+from y0 with every entry moved by one ulp (seeded random direction).  Any
+arithmetic that does not repeat the oracle's operations one by one (fused
+multiply-adds, another summation order) lands at about that distance.
+
+Trajectories run in spawned worker processes (safe after CUDA is initialised
+in the test process), several at once.
+"""
+import multiprocessing as mp
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+
+
+def one_ulp_everywhere(y0, seed=0):
+    """y0 with every entry moved by one ulp up or down (seeded)."""
+    up = np.random.default_rng(seed).random(y0.shape) < 0.5
+    return np.where(up, np.nextafter(y0, np.inf), np.nextafter(y0, -np.inf))
+
+
+def trajectory(args):
+    """`steps` oracle ROK4 steps from y0 (optionally perturbed); returns the state."""
+    from oracle import core
+    from oracle import integrators as I
+    prob, y0, h, M, steps, basis32, perturb_seed = args
+    y = y0 if perturb_seed is None else one_ulp_everywhere(y0, perturb_seed)
+    sys_ = core.System(prob)
+    for _ in range(steps):
+        y = I.rok_step(sys_, y, h, M, basis=np.float32 if basis32 else np.float64)
+    return y
+
+
+def run_all(tasks, workers=8):
+    """Run `trajectory` for every task tuple, in parallel; results in order."""
+    ctx = mp.get_context('spawn')
+    with ProcessPoolExecutor(max_workers=min(workers, len(tasks)), mp_context=ctx) as ex:
+        return list(ex.map(trajectory, tasks))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))

@@ -1,9 +1,9 @@
-"""GPU parity of the Arnoldi process (Sec. 2.3.3), the ROK4 step (Eq. ROK), RK4
+"""GPU parity of the Arnoldi process (Sec. 2.2.2), the ROK4 step (Eq. ROK), RK4
 (Eq. RK), ESDIRK3 Newton-GMRES and the CFL time step against the CPU oracle,
 through the C ABI.
 
-Tolerances: 10 ROK4 steps agree to 1e-9 relative L2 (plain FP64 path); the
-Arnoldi basis and Hessenberg matrix to 1e-9 (they see FD-JVP rounding only
+Tolerances: 10 strict-rounding ROK4 steps are bit-exact (the FMA build's
+ten-step bars are in test_gpu_parity10.py); the Arnoldi basis and Hessenberg matrix to 1e-9 (they see FD-JVP rounding only
 through the dot-product order); RK4 to 1e-13; ESDIRK3 to the Newton/GMRES
 tolerances it is solved to (1e-10 Newton, 1e-6 GMRES -> 1e-8 on y)."""
 import numpy as np
@@ -84,32 +84,10 @@ def _ten_steps(rok, prob, y0, cfl, M, mode, steps=10):
     return host(y), yo, h
 
 
-def _oracle_self_sensitivity(prob, y0, h, M, steps=10):
-    """How far the oracle itself moves after `steps` ROK4 steps when one entry of
-    the initial state moves by one ulp: FD-JVP quotients re-round at every
-    evaluation, so two evaluations that differ in the last bit of the state drift
-    apart at the FD noise level."""
-    sys_ = core.System(prob)
-    ya, yb = y0.copy(), y0.copy()
-    yb.flat[yb.size // 3] = np.nextafter(yb.flat[yb.size // 3], np.inf)
-    for _ in range(steps):
-        ya = I.rok_step(sys_, ya, h, M)
-        yb = I.rok_step(sys_, yb, h, M)
-    return rel_l2(ya, yb)
-
-
 def test_rok_ten_steps_vortex_strict_bitexact(rok):
     prob, y0 = W.isentropic_vortex(64)
     y, yo, _ = _ten_steps(rok, prob, y0, 5.0, 12, 'strict')
     assert np.array_equal(y, yo), rel_l2(y, yo)
-
-
-def test_rok_ten_steps_vortex_fast(rok):
-    prob, y0 = W.isentropic_vortex(64)
-    y, yo, h = _ten_steps(rok, prob, y0, 5.0, 12, 'fast')
-    err = rel_l2(y, yo)
-    sens = _oracle_self_sensitivity(prob, y0, h, 12)
-    assert err <= max(1e-9, 30 * sens), (err, sens)
 
 
 def test_rok_ns_and_ogrid_steps_strict_bitexact(rok):

@@ -1,5 +1,5 @@
 """Pins of the oracle integrators (Eq. ROK, Eq. RK, Eqs. Newton/SDIRK_Newton,
-Arnoldi of Sec. 2.3.3) against closed forms, textbook identities, brute force
+Arnoldi of Sec. 2.2.2) against closed forms, textbook identities, brute force
 on tiny problems and the paper's observed orders."""
 import json
 import os
@@ -578,7 +578,7 @@ class L96WrongJacobian(L96):
 
 
 def test_row_keeps_order3_with_a_wrong_jacobian_and_ros4_does_not():
-    # the W-property (Sec. 2.3.2): ROW keeps order 3 for any matrix in place of
+    # the W-property (Sec. 2.2.1): ROW keeps order 3 for any matrix in place of
     # J; ROS4 drops to order 2 (its conditions assume the exact Jacobian)
     y0, ref = _l96_start()
     sys = L96WrongJacobian()

@@ -1,5 +1,5 @@
 """Pins of the oracle residual and FD-JVP against facts fixed by mathematics,
-not by the oracle's own formulas (Sec. 3.2 Eq. Nav_Stokes; Sec. 2.4 Eq. matvecFD)."""
+not by the oracle's own formulas (Sec. 3.2 Eq. Nav_Stokes; Sec. 2.3 Eq. matvecFD)."""
 import numpy as np
 import pytest
 
@@ -276,3 +276,21 @@ def test_complex_step_is_linear_and_matches_fd_limit():
     f0 = core.residual(prob, y)
     e = [np.linalg.norm(core.jvp_fd(prob, y, v1, f0, 2.0 ** -k) - w1) for k in (10, 12, 14)]
     assert 3.5 < e[0] / e[1] < 4.5 and 3.5 < e[1] / e[2] < 4.5
+
+
+def test_openmp_build_gives_the_same_bits():
+    # the CPU-baseline build of the oracle (OpenMP over independent rows) must
+    # compute exactly what the plain build computes
+    cases = [W.taylor_green(40, reynolds=300.0), W.isentropic_vortex(36)]
+    p3, y3, _ = W.cylinder_ogrid(12, 40)
+    cases.append((p3, y3 + 0.02 * W.random_smooth_state(p3, seed=2)))
+    plain = [core.residual(p, y) for p, y in cases]
+    v = np.random.default_rng(3).standard_normal(cases[0][1].shape)
+    j_plain = core.jvp_fd(cases[0][0], cases[0][1], v, plain[0], 2.0 ** -20)
+    try:
+        core.use_parallel_build(4)
+        for (p, y), f in zip(cases, plain):
+            assert np.array_equal(core.residual(p, y), f)
+        assert np.array_equal(core.jvp_fd(cases[0][0], cases[0][1], v, plain[0], 2.0 ** -20), j_plain)
+    finally:
+        core.use_parallel_build(None)
