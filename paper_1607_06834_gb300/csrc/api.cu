@@ -393,46 +393,6 @@ rok_status enqueue_rok_body(rok_ctx *c, double *y, int M)
     return ROK_OK;
 }
 
-// Givens-rotation least squares of GMRES on the host (tiny)
-struct Givens {
-    std::vector<double> cs, sn, g, R;  // R: column-major (m+1) x m upper triangle
-    int m;
-    void reset(int m_, double beta)
-    {
-        m = m_;
-        cs.assign(m, 0.0); sn.assign(m, 0.0); g.assign(m + 1, 0.0); R.assign((size_t)(m + 1) * m, 0.0);
-        g[0] = beta;
-    }
-    // add column j (h[0..j+1]) and return the new residual estimate |g[j+1]|
-    double add(int j, const double *h)
-    {
-        double *col = &R[(size_t)j * (m + 1)];
-        for (int i = 0; i <= j + 1; ++i) col[i] = h[i];
-        for (int i = 0; i < j; ++i) {
-            double t = cs[i] * col[i] + sn[i] * col[i + 1];
-            col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-            col[i] = t;
-        }
-        double a = col[j], b = col[j + 1];
-        double r = hypot(a, b);
-        cs[j] = r > 0.0 ? a / r : 1.0;
-        sn[j] = r > 0.0 ? b / r : 0.0;
-        col[j] = r;
-        col[j + 1] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        return fabs(g[j + 1]);
-    }
-    void solve(int k, double *y) const
-    {
-        for (int i = k - 1; i >= 0; --i) {
-            double t = g[i];
-            for (int j = i + 1; j < k; ++j) t -= R[(size_t)j * (m + 1) + i] * y[j];
-            y[i] = t / R[(size_t)i * (m + 1) + i];
-        }
-    }
-};
-
 // pairwise (aligned binary tree) sum of p[0..n), zero-padded to a power of two
 double host_tree(const double *p, int n)
 {
@@ -764,23 +724,29 @@ rok_status rk_step(rok_ctx *c, double *y, double h, rok_step_info *info)
     return ROK_OK;
 }
 
-// x = (I - hg J_n)^{-1} rhs by restarted GMRES(m) from x0 = 0 (modified
-// Gram-Schmidt Arnoldi on the device, Givens rotations of the small
-// Hessenberg system on the host, stop at ||rhs - op(x)|| <= tol ||rhs||);
-// J_n at y applied by the FD product with base F0 = f(y) (or exactly).  Uses
-// c->V, c->H, c->w and c->F[1] as workspace; rhs and x must be other buffers.
+// x = (I - hg J_n)^{-1} rhs by restarted GMRES(m) from x0 = 0, on the device:
+// the Arnoldi columns of (I - hg J_n) by modified Gram-Schmidt (the persistent
+// column kernel where it fits, else one launch per pass), the Givens rotations
+// of the Hessenberg columns, the residual estimate and the stop decision in the
+// step state.  The host enqueues one whole restart cycle (m columns; the
+// columns after a stop are skipped on the device: the JVP and the column kernel
+// check the Arnoldi flag) and reads the GMRES state once per cycle.  Stops at
+// ||rhs - op(x)|| <= tol ||rhs|| (the least-squares estimate).  J_n at y is
+// applied by the FD product with base F0 = f(y) (or exactly).  Uses c->V, the
+// step state's H, c->w and c->F[1] as workspace; rhs and x must be other buffers.
 static rok_status gmres_solve(rok_ctx *c, const double *y, const double *F0, double hg, const double *rhs,
                               double *x, const esdirk_opts &op, int *its_out, bool *conv_out, int *jvps,
                               int *res_evals)
 {
     const size_t N = c->N;
     const int P = c->P;
+    const int m = op.gmres_m;
     StepState *st = c->st;
     cudaStream_t s = c->stream;
     double *wv = c->w;
-    rok_status r, err = ROK_OK;
-    // op(v) = v - h g J_n v into out
-    auto apply_op = [&](const double *v, double *out) -> rok_status {
+    rok_status r;
+    // op(v) = v - h g J_n v into out; skipped on the device when *active == 0
+    auto apply_op = [&](const double *v, double *out, const int *active) -> rok_status {
         StencilIO io;
         if (c->exact_jvp) {
             io = io_plain(c, y, out);
@@ -790,77 +756,78 @@ static rok_status gmres_solve(rok_ctx *c, const double *y, const double *F0, dou
         }
         io.add_out = v;
         io.s2 = -hg;
-        (*jvps)++;
-        (*res_evals)++;
+        io.active = active;
         return stencil(c, io);
     };
+    const bool persistent = c->col_ctas > 0 && c->persistent;
     CU(cudaMemsetAsync(x, 0, N * sizeof(double), s));
-    double bnorm = host_norm(c, rhs, &err);
-    if (err) return err;
-    int its = 0;
-    bool conv = bnorm == 0.0;
-    if (bnorm > 0.0) {
-        for (int cycle = 0; cycle <= op.gmres_restarts; ++cycle) {
+    CU(c->ops->dot2(rhs, rhs, nullptr, nullptr, N, c->pA, P, nullptr, s));
+    CU(c->ops->gmres_start(c->pA, P, op.gmres_tol, m, st, s));
+    c->launches += 2;
+    int restarts_applied = 0;
+    bool conv = false;
+    const GmresState &hgm = c->h_st->gm;
+    for (int cycle = 0; cycle <= op.gmres_restarts; ++cycle) {
+        const double *r0 = rhs;
+        if (cycle > 0) {
             // r0 = rhs - op(x)
-            const double *r0 = rhs;
-            if (its > 0) {
-                if ((r = apply_op(x, wv)) != ROK_OK) return r;
-                const double *vv[1] = {wv};
-                double cc[1] = {-1.0};
-                CU(c->ops->axpy_n(c->F[1], rhs, vv, cc, 1, N, nullptr, c->egrid, s));
+            if ((r = apply_op(x, wv, nullptr)) != ROK_OK) return r;
+            restarts_applied++;
+            const double *vv[1] = {wv};
+            double cc[1] = {-1.0};
+            CU(c->ops->axpy_n(c->F[1], rhs, vv, cc, 1, N, nullptr, c->egrid, s));
+            c->launches++;
+            r0 = c->F[1];
+        }
+        // beta = ||r0||, stop test, g = beta e_1; v_0 = r0 / beta
+        CU(c->ops->dot2(r0, r0, nullptr, nullptr, N, c->pA, P, nullptr, s));
+        CU(c->ops->gmres_cycle(c->pA, P, st, s));
+        CU(c->ops->first_vector(r0, c->V, 0, N, c->pB, P, st, s));
+        c->launches += 4;
+        if (persistent) CU(cudaMemsetAsync(c->colcnt, 0, column_counter_offset(m) * sizeof(unsigned), s));
+        for (int j = 0; j < m; ++j) {
+            if ((r = apply_op(c->V + (size_t)j * N, wv, &st->active)) != ROK_OK) return r;
+            cudaError_t e = cudaErrorNotSupported;
+            if (persistent)
+                e = c->ops->arnoldi_column(wv, c->V, 0, N, N, j, 1, P, c->pA, c->pB,
+                                           c->colcnt + column_counter_offset(j), st, c->col_ctas, s);
+            if (e == cudaSuccess) {
                 c->launches++;
-                r0 = c->F[1];
-            }
-            double beta = host_norm(c, r0, &err);
-            if (err) return err;
-            if (beta <= op.gmres_tol * bnorm) { conv = true; break; }
-            // v_0 = r0 / beta
-            CU(launch_set_int(&st->active, 1, s));
-            CU(c->ops->dot2(r0, r0, nullptr, nullptr, N, c->pA, P, nullptr, s));
-            CU(c->ops->normalize(r0, c->V, N, c->pA, P, nullptr, 0, st, s));
-            c->launches += 3;
-            Givens gv;
-            gv.reset(op.gmres_m, beta);
-            int k_used = 0;
-            bool done = false;
-            for (int j = 0; j < op.gmres_m; ++j) {
-                if ((r = apply_op(c->V + (size_t)j * N, wv)) != ROK_OK) return r;
-                CU(c->ops->dot2(c->V, wv, wv, wv, N, c->pA, P, nullptr, s));
+            } else {
+                if (e != cudaErrorNotSupported) return ROK_ERR_CUDA;
+                (void)cudaGetLastError();
+                CU(c->ops->dot2(c->V, wv, wv, wv, N, c->pA, P, &st->active, s));
                 double *pin = c->pA, *pout = c->pB;
                 for (int q = 1; q <= j + 1; ++q) {
                     const double *vnext = q <= j ? c->V + (size_t)q * N : nullptr;
                     CU(c->ops->mgs(wv, c->V + (size_t)(q - 1) * N, vnext, N, pin, P,
-                                  &st->H[(q - 1) * kMaxKrylov + j], pout, q == 1, st, s));
-                    double *t = pin; pin = pout; pout = t;
+                                   &st->H[(q - 1) * kMaxKrylov + j], pout, q == 1, st, s));
+                    double *t = pin;
+                    pin = pout;
+                    pout = t;
                 }
-                c->launches += 2 + j;
-                // h_{j+1,j} = ||w||; v_{j+1} = w / h_{j+1,j}
-                CU(cudaMemcpyAsync(c->h_part, pin, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
                 CU(c->ops->normalize(wv, c->V + (size_t)(j + 1) * N, N, pin, P,
-                                    &st->H[(j + 1) * kMaxKrylov + j], j + 1, st, s));
-                CU(cudaMemcpyAsync(&c->h_st->active, &st->active, sizeof(int), cudaMemcpyDeviceToHost, s));
-                c->launches++;
-                double hc[kMaxKrylov + 1];
-                CU(cudaMemcpy2DAsync(hc, sizeof(double), &st->H[j], kMaxKrylov * sizeof(double), sizeof(double),
-                                     j + 1, cudaMemcpyDeviceToHost, s));
-                CU(cudaStreamSynchronize(s));
-                hc[j + 1] = sqrt(host_tree(c->h_part, P));
-                its++;
-                double res = gv.add(j, hc);
-                k_used = j + 1;
-                if (res <= op.gmres_tol * bnorm || c->h_st->active == 0) { done = true; break; }
+                                     &st->H[(j + 1) * kMaxKrylov + j], j + 1, st, s));
+                c->launches += 3 + j;
             }
-            std::vector<double> yv(k_used);
-            gv.solve(k_used, yv.data());
-            CU(cudaMemcpyAsync(st->gcoef, yv.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
-            CU(c->ops->basis_combine(x, x, c->V, N, N, k_used, st->gcoef, c->egrid, s));
-            CU(cudaStreamSynchronize(s));
+            CU(c->ops->gmres_givens(j, st, s));
             c->launches++;
-            if (done) { conv = true; break; }
+        }
+        // x += V y with R y = g (no-op when the cycle started converged)
+        CU(c->ops->gmres_lsq(st, s));
+        CU(c->ops->basis_combine(x, x, c->V, N, N, m, st->gcoef, &st->gm.k, c->egrid, s));
+        CU(cudaMemcpyAsync(&c->h_st->gm, &st->gm, sizeof(GmresState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        c->launches += 2;
+        if (hgm.conv) {
+            conv = true;
+            break;
         }
     }
-    *its_out = its;
+    *its_out = hgm.its;
     *conv_out = conv;
+    *jvps += hgm.its + restarts_applied;
+    *res_evals += hgm.its + restarts_applied;
     return ROK_OK;
 }
 

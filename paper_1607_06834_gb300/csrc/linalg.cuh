@@ -17,6 +17,23 @@ inline size_t column_counter_offset(int j) { return (size_t)j * (j + 3) / 2; }
 
 // Step state kept in device memory so that a whole step runs without host
 // synchronisation (and can be captured in a CUDA graph).
+// Restarted GMRES(m) of the comparators' stage solves, kept on the device so
+// that a restart cycle runs without host round trips: Givens rotations of the
+// Hessenberg columns (rotated in place in StepState::H), the rotated
+// right-hand side g, the residual estimate and the stop flags.
+struct GmresState {
+    double cs[kMaxKrylov], sn[kMaxKrylov];
+    double g[kMaxKrylov + 1];
+    double bnorm, tol_abs;   // ||rhs||, tol ||rhs||
+    double res;              // |g_{k}|: residual estimate of the current iterate
+    int m;                   // restart length
+    int k;                   // columns in the current cycle's least-squares system
+    int its;                 // Arnoldi columns processed in this solve
+    int live;                // the current cycle is still extending its basis
+    int conv;                // converged (residual estimate <= tol ||rhs||)
+    int pad;
+};
+
 struct StepState {
     double h, hg;             // step size, h * gamma
     double eps, inv_eps;      // finite-difference increment (Eq. matvecFD)
@@ -34,7 +51,8 @@ struct StepState {
     double cvec[4][kMaxKrylov];
     double phi[kMaxKrylov];
     double phis[4][kMaxKrylov];    // phi of every stage (kept for the reverse step)
-    double gcoef[kMaxKrylov + 1];  // host-provided coefficients (GMRES update)
+    double gcoef[kMaxKrylov + 1];  // coefficients of the GMRES update x += V gcoef
+    GmresState gm;
 };
 
 // ---- rounding-mode dependent vector kernels (linalg_impl.cuh, compiled twice) ----
@@ -63,9 +81,10 @@ struct LinalgOps {
     // out = base + sum_q c_q v_q (count <= 8, host coefficients); skipped when guard->status != 0
     cudaError_t (*axpy_n)(double *out, const double *base, const double *const *v, const double *c, int count,
                           size_t n, const StepState *guard, int grid, cudaStream_t s);
-    // out = base + sum_{m<count} gcoef[m] V_m (device coefficients)
+    // out = base + sum_{m<count} gcoef[m] V_m (device coefficients; count_dev, when
+    // not null, lowers count to *count_dev on the device)
     cudaError_t (*basis_combine)(double *out, const double *base, const double *V, size_t ldv, size_t n, int count,
-                                 const double *gcoef, int grid, cudaStream_t s);
+                                 const double *gcoef, const int *count_dev, int grid, cudaStream_t s);
     // eps from tree(pin) = ||y||^2 and tree(pin + P) = ||v||^2 (or ||v|| = 1)
     cudaError_t (*eps)(const double *pin, int P, bool v_unit, double eps_given, StepState *st, cudaStream_t s);
     cudaError_t (*sum_sqrt)(const double *pin, int P, double *dst, cudaStream_t s);
@@ -91,6 +110,19 @@ struct LinalgOps {
     // sc_i = atol + rtol max(|y_i|, |ynew_i|): the weighted RMS norm of an error estimate
     cudaError_t (*err_sum)(const double *y, const double *ynew, const double *const *kv, const double *d, int count,
                            double atol, double rtol, size_t n, double *partials, int P, cudaStream_t s);
+    // Restarted GMRES on the device.  gmres_start: ||rhs|| = sqrt(tree(pin)),
+    // tol_abs = tol ||rhs||, counters reset (||rhs|| = 0: converged at x = 0).
+    cudaError_t (*gmres_start)(const double *pin, int P, double tol, int m, StepState *st, cudaStream_t s);
+    // gmres_cycle: beta = sqrt(tree(pin)), the norm of the cycle's starting
+    // residual; converged when beta <= tol_abs, otherwise g = beta e_1, the
+    // subdiagonal of H cleared and the Arnoldi flag set for the cycle.
+    cudaError_t (*gmres_cycle)(const double *pin, int P, StepState *st, cudaStream_t s);
+    // gmres_givens: column j of H (written by the Arnoldi column) rotated by the
+    // earlier rotations, the new rotation, g updated, residual estimate; stops
+    // the cycle (Arnoldi flag cleared) at convergence, breakdown or column m-1.
+    cudaError_t (*gmres_givens)(int j, StepState *st, cudaStream_t s);
+    // gmres_lsq: R y = g by back substitution into gcoef[0 .. k)
+    cudaError_t (*gmres_lsq)(StepState *st, cudaStream_t s);
 };
 
 // Segment table of a batch (device arrays): chunk c of a flat vector belongs to

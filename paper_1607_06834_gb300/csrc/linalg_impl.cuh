@@ -930,9 +930,11 @@ __global__ void __launch_bounds__(RT) axpy_n_kernel(double *out, const double *b
 }
 
 __global__ void __launch_bounds__(RT) basis_combine_kernel(double *out, const double *base, const double *V,
-                                                           size_t ldv, size_t n, int count, const double *gcoef)
+                                                           size_t ldv, size_t n, int count, const double *gcoef,
+                                                           const int *count_dev)
 {
     __shared__ double c[kMaxKrylov + 1];
+    if (count_dev && *count_dev < count) count = *count_dev;
     for (int i = threadIdx.x; i < count; i += blockDim.x) c[i] = gcoef[i];
     __syncthreads();
     for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
@@ -968,6 +970,99 @@ __global__ void sum_sqrt_kernel(const double *pin, int P, double *dst)
     __shared__ double sh[10];
     double s = tree_partials(pin, P, sh);
     if (threadIdx.x == 0) *dst = sqrt(s);
+}
+
+// ---- restarted GMRES(m) on the device (stage solves of the comparators) ----------
+// The Arnoldi columns of a cycle are the Gram-Schmidt column kernels above
+// applied to w = (I - h g J) v_j; these small kernels keep the least-squares
+// problem min ||beta e_1 - H y|| (Givens rotations, as in Saad & Schultz) and the
+// stop decision on the device, so the host reads the state once per cycle.
+
+__global__ void __launch_bounds__(RT) gmres_start_kernel(const double *pin, int P, double tol, int m, StepState *st)
+{
+    __shared__ double sh[10];
+    const double bn = sqrt(tree_partials(pin, P, sh));
+    if (threadIdx.x == 0) {
+        GmresState &g = st->gm;
+        g.bnorm = bn;
+        g.tol_abs = tol * bn;
+        g.res = bn;
+        g.m = m;
+        g.k = 0;
+        g.its = 0;
+        g.live = 0;
+        g.conv = bn == 0.0 ? 1 : 0;
+        st->active = 0;
+    }
+}
+
+__global__ void __launch_bounds__(RT) gmres_cycle_kernel(const double *pin, int P, StepState *st)
+{
+    __shared__ double sh[10];
+    const double beta = sqrt(tree_partials(pin, P, sh));
+    if (threadIdx.x == 0) {
+        GmresState &g = st->gm;
+        g.k = 0;
+        if (g.conv || beta <= g.tol_abs) {
+            g.conv = 1;
+            g.live = 0;
+            st->active = 0;
+        } else {
+            g.live = 1;
+            g.res = beta;
+            st->active = 1;
+            g.g[0] = beta;
+            for (int i = 1; i <= g.m; ++i) g.g[i] = 0.0;
+            for (int j = 0; j < g.m; ++j) st->H[(j + 1) * kMaxKrylov + j] = 0.0;
+        }
+    }
+}
+
+// one thread: the rotations of column j (their count is the restart length at most)
+__global__ void gmres_givens_kernel(int j, StepState *st)
+{
+    GmresState &g = st->gm;
+    if (!g.live) return;
+    const bool brk = st->active == 0;   // the Arnoldi column stopped at a breakdown
+    double *H = st->H;
+    constexpr int L = kMaxKrylov;
+    for (int i = 0; i < j; ++i) {
+        const double a = H[i * L + j], b = H[(i + 1) * L + j];
+        H[i * L + j] = g.cs[i] * a + g.sn[i] * b;
+        H[(i + 1) * L + j] = -g.sn[i] * a + g.cs[i] * b;
+    }
+    const double a = H[j * L + j], b = brk ? 0.0 : H[(j + 1) * L + j];
+    const double r = hypot(a, b);
+    const double cs = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? b / r : 0.0;
+    g.cs[j] = cs;
+    g.sn[j] = sn;
+    H[j * L + j] = r;
+    g.g[j + 1] = -sn * g.g[j];
+    g.g[j] = cs * g.g[j];
+    g.its += 1;
+    g.k = j + 1;
+    g.res = fabs(g.g[j + 1]);
+    if (g.res <= g.tol_abs || brk) {
+        g.conv = 1;
+        g.live = 0;
+        st->active = 0;
+    } else if (j + 1 >= g.m) {
+        g.live = 0;
+        st->active = 0;
+    }
+}
+
+// one thread: R y = g[0 .. k) by back substitution (R the rotated upper triangle of H)
+__global__ void gmres_lsq_kernel(StepState *st)
+{
+    const GmresState &g = st->gm;
+    constexpr int L = kMaxKrylov;
+    const int k = g.k;
+    for (int i = k - 1; i >= 0; --i) {
+        double t = g.g[i];
+        for (int q = i + 1; q < k; ++q) t -= st->H[i * L + q] * st->gcoef[q];
+        st->gcoef[i] = t / st->H[i * L + i];
+    }
 }
 
 // ---- batches of independent instances --------------------------------------------
@@ -1431,9 +1526,33 @@ static cudaError_t axpy_n(double *out, const double *base, const double *const *
 }
 
 static cudaError_t basis_combine(double *out, const double *base, const double *V, size_t ldv, size_t n, int count,
-                                 const double *gcoef, int grid, cudaStream_t s)
+                                 const double *gcoef, const int *count_dev, int grid, cudaStream_t s)
 {
-    basis_combine_kernel<<<grid, RT, 0, s>>>(out, base, V, ldv, n, count, gcoef);
+    basis_combine_kernel<<<grid, RT, 0, s>>>(out, base, V, ldv, n, count, gcoef, count_dev);
+    return cudaGetLastError();
+}
+
+static cudaError_t gmres_start(const double *pin, int P, double tol, int m, StepState *st, cudaStream_t s)
+{
+    gmres_start_kernel<<<1, RT, 0, s>>>(pin, P, tol, m, st);
+    return cudaGetLastError();
+}
+
+static cudaError_t gmres_cycle(const double *pin, int P, StepState *st, cudaStream_t s)
+{
+    gmres_cycle_kernel<<<1, RT, 0, s>>>(pin, P, st);
+    return cudaGetLastError();
+}
+
+static cudaError_t gmres_givens(int j, StepState *st, cudaStream_t s)
+{
+    gmres_givens_kernel<<<1, 1, 0, s>>>(j, st);
+    return cudaGetLastError();
+}
+
+static cudaError_t gmres_lsq(StepState *st, cudaStream_t s)
+{
+    gmres_lsq_kernel<<<1, 1, 0, s>>>(st);
     return cudaGetLastError();
 }
 
@@ -1462,8 +1581,10 @@ static cudaError_t err_sum(const double *y, const double *ynew, const double *co
     return cudaGetLastError();
 }
 
-const LinalgOps ops = {dot2, mgs, normalize, multidot, stage_solve, lu, stage_vec, axpy_n, basis_combine, eps,
-                       sum_sqrt, arnoldi_column, arnoldi_column_ctas, first_vector, err_sum};
+const LinalgOps ops = {dot2,          mgs,         normalize,  multidot,    stage_solve,  lu,
+                       stage_vec,     axpy_n,      basis_combine, eps,      sum_sqrt,     arnoldi_column,
+                       arnoldi_column_ctas, first_vector, err_sum, gmres_start, gmres_cycle, gmres_givens,
+                       gmres_lsq};
 
 #endif  // ROK_LINALG_DEVICE_ONLY
 

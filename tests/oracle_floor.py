@@ -1,4 +1,5 @@
-"""Oracle trajectories for the multi-step parity tests, and the oracle's own
+"""Oracle trajectories for the multi-step parity tests (and one ESDIRK3 step of
+the comparator test), and the oracle's own
 rounding floor.
 
 The FD Jacobian-vector product (Eq. matvecFD) divides a difference of two
@@ -47,3 +48,13 @@ def run_all(tasks, workers=8):
 
 def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def esdirk_task(args):
+    """One oracle ESDIRK3 Newton-GMRES(30) step; returns (state, info)."""
+    from oracle import core
+    from oracle import integrators as I
+    prob, y0, h = args
+    info = {}
+    y = I.esdirk_step(core.System(prob), y0, h, info=info)
+    return y, info

@@ -454,3 +454,55 @@ def test_reverse_gram_schmidt_two_chunks_per_cta_at_512(rok):
         res.append((yb, mub))
     assert torch.equal(res[0][0], res[1][0])
     assert res[0][1] == res[1][1]
+
+
+@pytest.mark.parametrize('method', ['esdirk', 'ros4'])
+def test_device_gmres_persistent_and_pass_by_pass_agree(rok, method):
+    # the GMRES Arnoldi columns in one cooperative launch each and in one launch
+    # per Gram-Schmidt pass: the same sums in the same order, so the same bits
+    prob, y0 = W.taylor_green(48, reynolds=300.0)
+    y0 = np.ascontiguousarray(y0 + 0.01 * W.random_smooth_state(prob, seed=5))
+    h = I.dt_from_cfl(prob, y0, 6.0)
+    res = []
+    for persistent in (True, False):
+        ctx = rok.rok_init(prob, krylov_max=30)
+        rok.rok_set_persistent(ctx, persistent)
+        y = dev(y0)
+        if method == 'esdirk':
+            info = rok.esdirk_step(ctx, y, h, info=True)
+        else:
+            info = rok.ros_step(ctx, y, h, method=rok.ROK_ROS_ROS4, info=True)
+        res.append((host(y), info['gmres_iters']))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1] and res[0][1] >= 4
+
+
+def test_esdirk_step_full_size_taylor_green(rok):
+    # the comparator on the benchmark workload (512^2 Taylor-Green, CFL 8): the
+    # device-resident Newton-GMRES(30) against the oracle's step, with the
+    # oracle running in a spawned worker while the GPU steps
+    import time
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+    import torch
+    from tests.oracle_floor import esdirk_task
+    prob, y0 = W.taylor_green(512, reynolds=1600.0)
+    h = I.dt_from_cfl(prob, y0, 8.0)
+    with ProcessPoolExecutor(max_workers=1, mp_context=mp.get_context('spawn')) as ex:
+        fut = ex.submit(esdirk_task, (prob, y0, h))
+        ctx = rok.rok_init(prob, krylov_max=30)
+        y = dev(y0)
+        rok.esdirk_step(ctx, dev(y0), h)           # warm-up (kernel loading)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = rok.esdirk_step(ctx, y, h, info=True)
+        ms = (time.perf_counter() - t0) * 1e3
+        yo, oi = fut.result()
+    err = rel_l2(host(y), yo)
+    print('\n[esdirk] 512^2 Taylor-Green CFL 8: %.1f ms, %d Newton, %d GMRES iterations (%.3f ms each); '
+          'oracle %d / %d; rel L2 vs oracle %.2e' % (ms, info['newton_iters'], info['gmres_iters'],
+                                                      ms / max(info['gmres_iters'], 1), oi['newton_iters'],
+                                                      oi['gmres_iters'], err))
+    assert oi['converged']
+    assert abs(info['gmres_iters'] - oi['gmres_iters']) <= 0.05 * oi['gmres_iters'] + 2
+    assert err <= 1e-8
