@@ -312,7 +312,8 @@ rok_status arnoldi_columns(rok_ctx *c, const double *y, int M)
         if ((r = stencil(c, io)) != ROK_OK) return r;
         cudaError_t e = cudaErrorNotSupported;
         if (c->col_ctas > 0 && c->persistent)
-            e = c->ops->arnoldi_column(c->w, Vb, c->fp32 ? 1 : 0, N, N, j, j + 1 < M ? 1 : 0, P, c->pA, c->pB,
+            e = c->ops->arnoldi_column(c->w, Vb, c->fp32 ? 1 : 0, N, N, j, j + 1 < M ? 1 : 0, P,
+                                       c->fp32 ? c->pM : c->pA, c->pB,
                                        c->colcnt + column_counter_offset(j), st, c->col_ctas, s);
         if (e == cudaSuccess) {
             c->launches++;
@@ -523,7 +524,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     auto al = [&](double **p, size_t n) { return cudaMalloc(p, n * sizeof(double)) == cudaSuccess; };
     bool ok = al(&c->V, (size_t)(c->mmax + 1) * N) && al(&c->w, N) && al(&c->t0, N) && al(&c->t1, N) &&
               al(&c->t2, N) && al(&c->pA, 2 * (size_t)c->P) && al(&c->pB, 2 * (size_t)c->P) &&
-              al(&c->pM, (size_t)kMaxKrylov * c->P);
+              al(&c->pM, (size_t)(kMaxKrylov + 2) * c->P);
     for (int i = 0; i < 4 && ok; ++i) ok = al(&c->F[i], N) && al(&c->K[i], N);
     if (ok && c->fp32) ok = cudaMalloc(&c->Vf, (size_t)(c->mmax + 1) * N * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->st, sizeof(StepState)) == cudaSuccess;

@@ -97,7 +97,9 @@ struct LinalgOps {
     // (column_counter_offset).  Same arithmetic as dot2 + mgs + normalize.
     // Returns cudaErrorNotSupported when the ctas cannot cover the P chunks
     // (caller falls back).
-    // fp32: the basis V is binary32 and the Gram-Schmidt arithmetic binary32 (w rounded on load)
+    // fp32: the basis V is binary32 and the Gram-Schmidt arithmetic binary32 (w rounded on load);
+    // the FMA build orthogonalises by CGS2 then (two waits per column) and takes
+    // partA as 2 (kMaxKrylov + 1) P binary32 partials (partB unused)
     cudaError_t (*arnoldi_column)(const double *w, void *V, int fp32, size_t ldv, size_t n, int j, int next, int P,
                                   double *partA, double *partB, unsigned *cnt, StepState *st, int ctas,
                                   cudaStream_t s);

@@ -618,6 +618,196 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_column_kernel(const double *__r
     }
 }
 
+#ifdef ROK_LINALG_FAST
+// ---- mixed-precision Arnoldi column by classical Gram-Schmidt, twice (CGS2) -----
+// The binary32 Gram-Schmidt of the mixed-precision form is cheap arithmetic but
+// pays one grid-wide wait per modified-Gram-Schmidt pass (j + 2 per column).
+// CGS2 forms all j + 1 projections of a pass at once: h1 = V^T w, w' = w - V h1,
+// h2 = V^T w' (the second projection restores orthogonality to binary32
+// rounding), ||w'||^2 in the same reduction, h_{j+1,j}^2 = ||w'||^2 - ||h2||^2
+// (w'' = w' - V h2 is orthogonal to V), H[:, j] = h1 + h2, v_{j+1} = w'' / h.
+// Two waits per column.  It spans the same Krylov space and equals MGS up to
+// rounding (classical Gram-Schmidt twice is as stable as MGS here); the strict
+// build keeps MGS, whose every rounding the oracle repeats.
+constexpr int kCgsVals = kMaxKrylov + 1;   // j + 1 projections and one squared norm
+
+// out[i * G + blockIdx.x] = the CTA's part of <v_i, w> for i <= j and of
+// ||w||^2 for i = j + 1 (nv = j + 2 values).  Per slot the thread loads eight
+// basis vectors at once (one L2 latency per eight vectors), forms their dots
+// with its entries, and the values go 16 at a time through lane_tree16.
+__device__ __forceinline__ void cgs_values(const float (&wv)[kColChunks][EPL], const bool (&have)[kColChunks],
+                                           const size_t (&e0)[kColChunks], const float *__restrict__ V,
+                                           size_t ldv, size_t n, int j, float (*ws)[8], float *out, unsigned G)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nv = j + 2;
+    for (int g = 0; g < nv; g += 16) {
+        float t[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) t[q] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kColChunks; ++c) {
+            if (!have[c]) continue;
+#pragma unroll
+            for (int q0 = 0; q0 < 16; q0 += 8) {
+                float v[8][EPL];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = g + q0 + q;
+                    if (i <= j) {
+                        load8(V + (size_t)i * ldv, e0[c], n, v[q]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < EPL; ++k) v[q][k] = i == j + 1 ? wv[c][k] : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) t[q0 + q] += lane_dot(v[q], wv[c]);
+            }
+        }
+        const float sum = lane_tree16(t, lane);
+        const int q = lane_tree16_value(lane);
+        if (lane < 16 && g + q < nv) ws[g + q][wid] = sum;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += RT) {
+        const float *w8 = ws[i];
+        out[(size_t)i * G + blockIdx.x] = ((w8[0] + w8[1]) + (w8[2] + w8[3])) + ((w8[4] + w8[5]) + (w8[6] + w8[7]));
+    }
+}
+
+// hs[i] = sum over the G CTA partials of value i, i < nv (one warp per value;
+// a lane issues all its loads of a value before adding: one L2 latency per
+// value instead of one per load)
+constexpr int kCgsMaxCtasPerLane = 32;   // G <= 1024
+__device__ __forceinline__ void grid_values(int nv, const float *part, unsigned G, float *hs)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i < nv; i += RT / 32) {
+        const float *p = part + (size_t)i * G;
+        float x[kCgsMaxCtasPerLane];
+#pragma unroll
+        for (int q = 0; q < kCgsMaxCtasPerLane; ++q) {
+            const unsigned b = lane + 32u * q;
+            x[q] = b < G ? p[b] : 0.0f;
+        }
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kCgsMaxCtasPerLane; ++q) s += x[q];
+        s = lane_tree(s);
+        if (lane == 0) hs[i] = s;
+    }
+    __syncthreads();
+}
+
+// w -= sum_{i <= j} h[i] v_i over the thread's entries, four basis vectors at a
+// time with their loads issued together
+__device__ __forceinline__ void cgs_update(float (&wv)[kColChunks][EPL], const bool (&have)[kColChunks],
+                                           const size_t (&e0)[kColChunks], const float *__restrict__ V, size_t ldv,
+                                           size_t n, int j, const float *h)
+{
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c) {
+        if (!have[c]) continue;
+        int i = 0;
+        for (; i + 4 <= j + 1; i += 4) {
+            float v[4][EPL];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) load8(V + (size_t)(i + q) * ldv, e0[c], n, v[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float hq = h[i + q];
+#pragma unroll
+                for (int k = 0; k < EPL; ++k) wv[c][k] = wv[c][k] - hq * v[q][k];
+            }
+        }
+        for (; i <= j; ++i) {
+            float v[EPL];
+            load8(V + (size_t)i * ldv, e0[c], n, v);
+            const float hi = h[i];
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) wv[c][k] = wv[c][k] - hi * v[k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RT, 2) cgs2_column_kernel(const double *__restrict__ w, float *__restrict__ V,
+                                                            size_t ldv, size_t n, int j, int next, int P,
+                                                            float *part, unsigned *cnt, StepState *st,
+                                                            double brk_tol)
+{
+    __shared__ float ws[kCgsVals][8];
+    __shared__ float h1[kCgsVals], h2[kCgsVals];
+    __shared__ int act;
+    if (threadIdx.x == 0) act = st->active;
+    __syncthreads();
+    if (act == 0) return;
+    const unsigned G = gridDim.x;
+    float wv[kColChunks][EPL];
+    size_t e0[kColChunks];
+    bool have[kColChunks];
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c) {
+        const int b = blockIdx.x + c * G;
+        have[c] = b < P;
+        e0[c] = ((size_t)b * RT + threadIdx.x) * EPL;
+        if (have[c]) {
+            double wd[EPL];
+            load8(w, e0[c], n, wd);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) wv[c][k] = (float)wd[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) wv[c][k] = 0.0f;
+        }
+    }
+    const int nv = j + 2;
+    float *partA = part, *partB = part + (size_t)kCgsVals * G;
+    // first projection h1 = V^T w and ||w||^2
+    cgs_values(wv, have, e0, V, ldv, n, j, ws, partA, G);
+    gen_arrive(cnt);
+    if (!gen_wait(cnt, G, &st->status)) return;
+    grid_values(nv, partA, G, h1);
+    const float wnorm0 = sqrt(h1[j + 1]);
+    // w' = w - V h1, then h2 = V^T w' and ||w'||^2
+    cgs_update(wv, have, e0, V, ldv, n, j, h1);
+    __syncthreads();   // ws is reused
+    cgs_values(wv, have, e0, V, ldv, n, j, ws, partB, G);
+    gen_arrive(cnt + 1);
+    if (!gen_wait(cnt + 1, G, &st->status)) return;
+    grid_values(nv, partB, G, h2);
+    float hn2 = h2[j + 1];
+    for (int i = 0; i <= j; ++i) hn2 -= h2[i] * h2[i];
+    const float hn = hn2 > 0.0f ? sqrt(hn2) : 0.0f;
+    const bool brk = !((double)hn > brk_tol * (double)wnorm0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i <= j; ++i) st->H[i * kMaxKrylov + j] = (double)h1[i] + (double)h2[i];
+        st->wnorm0 = (double)wnorm0;
+        if (next) {
+            if (brk) {
+                st->active = 0;
+                st->meff = j + 1;
+            } else {
+                st->H[(j + 1) * kMaxKrylov + j] = (double)hn;
+            }
+        }
+    }
+    if (!next || brk) return;
+    // v_{j+1} = (w' - V h2) / h_{j+1,j}
+    cgs_update(wv, have, e0, V, ldv, n, j, h2);
+    const float r = 1.0f / hn;
+    float *vout = V + (size_t)(j + 1) * ldv;
+#pragma unroll
+    for (int c = 0; c < kColChunks; ++c) {
+        if (!have[c]) continue;
+        float x[EPL];
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) x[k] = wv[c][k] * r;
+        store8(vout, e0[c], n, x);
+    }
+}
+#endif  // ROK_LINALG_FAST
+
 // First basis vector: partials of ||(T)F1||^2 ...
 template <class T>
 __global__ void __launch_bounds__(RT) first_partials_kernel(const double *__restrict__ F, size_t n, T *partials)
@@ -674,6 +864,11 @@ static int arnoldi_column_ctas(int sms)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, arnoldi_column_kernel<float>, RT, 0) != cudaSuccess)
         return 0;
+#ifdef ROK_LINALG_FAST
+    int pc = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, cgs2_column_kernel, RT, 0) != cudaSuccess) return 0;
+    if (pc < p32) p32 = pc;
+#endif
     return (p64 < p32 ? p64 : p32) * sms;
 }
 
@@ -688,8 +883,16 @@ static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv
         float *Vf = static_cast<float *>(V);
         float *pa = reinterpret_cast<float *>(partA), *pb = reinterpret_cast<float *>(partB);
         double tol = 1e-5;
+#ifdef ROK_LINALG_FAST
+        // CGS2: partA holds 2 (kMaxKrylov + 1) G binary32 partials
+        (void)pb;
+        if (G > 32 * kCgsMaxCtasPerLane) return cudaErrorNotSupported;
+        void *cargs[] = {&w, &Vf, &ldv, &n, &j, &next, &P, &pa, &cnt, &st, &tol};
+        return cudaLaunchCooperativeKernel((const void *)cgs2_column_kernel, dim3(G), dim3(RT), cargs, 0, s);
+#else
         void *args[] = {&w, &Vf, &ldv, &n, &j, &next, &P, &pa, &pb, &cnt, &st, &tol};
         return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<float>, dim3(G), dim3(RT), args, 0, s);
+#endif
     }
     double *Vd = static_cast<double *>(V);
     double tol = 1e-12;
