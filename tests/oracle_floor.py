@@ -58,3 +58,30 @@ def esdirk_task(args):
     info = {}
     y = I.esdirk_step(core.System(prob), y0, h, info=info)
     return y, info
+
+
+def ke_complex_step_task(args):
+    """d/dt KE(y_K) at t = 0 by the complex step through the oracle's K ROK4
+    steps: along the state direction d (y0 + i t d), or along the viscosity
+    (mu + i t, f affine in mu) when d is None."""
+    from oracle import adjoint as A
+    from oracle import core
+    from oracle import integrators as I
+    prob, y0, h, M, K, d = args
+    hc = 1e-30
+    if d is not None:
+        sys_ = core.System(prob)
+        y = y0 + 1j * hc * d
+    else:
+        class MuStep(core.System):
+            def f(self, yy):
+                return core.residual(prob, yy) + 1j * hc * A.residual_dmu(prob, yy)
+
+            def jvp(self, yy, v, f0, eps):
+                return (self.f(np.asarray(yy) + eps * np.asarray(v)) - f0) / eps
+        sys_ = MuStep(prob)
+        y = y0.astype(complex)
+    for _ in range(K):
+        y = I.rok_step(sys_, y, h, M)
+    ke = 0.5 * np.sum((y[1] ** 2 + y[2] ** 2) / y[0])
+    return float(np.imag(ke) / hc)

@@ -261,3 +261,94 @@ def test_gradient_with_tapes_is_bit_identical_to_recomputation(rok):
         grads.append((y.grad.clone(), float(mu.grad)))
     assert torch.equal(grads[0][0], grads[1][0])
     assert grads[0][1] == grads[1][1]
+
+
+def _full_length_case(viscous):
+    prob, y0 = W.isentropic_vortex(64)
+    if viscous:
+        prob = W.FlowProblem(**{**prob.__dict__, 'kind': W.NAVIER_STOKES, 'mu': 0.01})
+    return prob, y0, I.dt_from_cfl(prob, y0, 0.5)
+
+
+def _cell_ke(t):
+    a = host(t)
+    return 0.5 * (a[1] * a[1] + a[2] * a[2]) / a[0]
+
+
+@pytest.mark.parametrize('viscous', [False, True], ids=['euler', 'navier-stokes'])
+def test_gradient_full_length_well_conditioned(rok, viscous):
+    # The gradient workload's shape (100 ROK4 steps, checkpoint every 10) on a
+    # map whose derivative is well conditioned: the isentropic vortex 64^2,
+    # M = 12, CFL 0.5 (Euler; Navier-Stokes with mu = 0.01 for dJ/dmu), J the
+    # final kinetic energy.  Checks, strict and FMA builds:
+    #  - 100 steps: dJ/dy0 . d and dJ/dmu against the complex-step derivative of
+    #    the oracle's own 100-step map, 1e-5;
+    #  - 10 steps: dJ/dy0 . d against central differences (h = 1e-6) of the
+    #    GPU's forward map, 1e-5 (their spread under one-ulp changes of y0 is
+    #    ~1e-6 there; after 100 steps it grows to ~2e-5 and the differences
+    #    are only reported);
+    #  - 100 steps: dJ/dmu against central differences in mu (relative step
+    #    1e-4; the map is smooth in mu), 1e-5.
+    # (At CFL >= 2, or on the low-Mach Taylor-Green state, complex step and
+    # central differences of the same map disagree by O(1): the FD-JVP
+    # Krylov map is not smooth at that scale.)
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import torch
+
+    from paper_1607_06834_gb300 import autograd as G
+    from tests.oracle_floor import ke_complex_step_task
+    prob, y0, h = _full_length_case(viscous)
+    M, every = 12, 10
+    d = np.random.default_rng(0).standard_normal(y0.shape)
+    d /= np.linalg.norm(d)
+
+    def grad(ctx, K):
+        y = dev(y0).requires_grad_(True)
+        mu = torch.tensor(prob.mu, dtype=torch.float64, requires_grad=True)
+        G.kinetic_energy(G.integrate(ctx, y, mu, h, M, K, checkpoint_every=every)).backward()
+        return float(np.sum(host(y.grad) * d)), float(mu.grad)
+
+    def forward(ctx, start, K):
+        yy = dev(start)
+        for _ in range(K):
+            rok.rok_step(ctx, yy, h, M)
+        return _cell_ke(yy)
+
+    with ProcessPoolExecutor(max_workers=2, mp_context=mp.get_context('spawn')) as ex:
+        f_cs = ex.submit(ke_complex_step_task, (prob, y0, h, M, 100, d))
+        f_csm = ex.submit(ke_complex_step_task, (prob, y0, h, M, 100, None)) if viscous else None
+        res = {}
+        for mode in ('strict', 'fast'):
+            rounding = getattr(rok, 'ROK_ROUND_' + mode.upper())
+            ctx = rok.rok_init(prob, krylov_max=M, rounding=rounding)
+            gd100, gmu100 = grad(ctx, 100)
+            gd10, _ = grad(ctx, 10)
+            fd10 = float(np.sum(forward(ctx, y0 + 1e-6 * d, 10) - forward(ctx, y0 - 1e-6 * d, 10))) / 2e-6
+            fd100 = float(np.sum(forward(ctx, y0 + 1e-6 * d, 100) - forward(ctx, y0 - 1e-6 * d, 100))) / 2e-6
+            fdm = None
+            if viscous:
+                vm = []
+                for sgn in (1.0, -1.0):
+                    pm = W.FlowProblem(**{**prob.__dict__, 'mu': prob.mu * (1.0 + sgn * 1e-4)})
+                    vm.append(forward(rok.rok_init(pm, krylov_max=M, rounding=rounding), y0, 100))
+                fdm = float(np.sum(vm[0] - vm[1])) / (2e-4 * prob.mu)
+            res[mode] = (gd100, gmu100, gd10, fd10, fd100, fdm)
+        cs = f_cs.result()
+        csm = f_csm.result() if viscous else None
+    for mode, (gd100, gmu100, gd10, fd10, fd100, fdm) in res.items():
+        tag = 'NS' if viscous else 'Euler'
+        print('\n[grad] vortex 64^2 %s, %s build: 100 steps dJ/dy0.d %.10g vs complex step %.10g (rel %.2e), '
+              'central FD %.10g (rel %.2e, reported); 10 steps %.10g vs central FD %.10g (rel %.2e)'
+              % (tag, mode, gd100, cs, abs(gd100 - cs) / abs(cs), fd100, abs(gd100 - fd100) / abs(gd100),
+                 gd10, fd10, abs(gd10 - fd10) / abs(gd10)))
+        assert abs(gd100 - cs) <= 1e-5 * abs(cs)
+        assert abs(gd10 - fd10) <= 1e-5 * abs(gd10)
+        if viscous:
+            print('[grad]   100 steps dJ/dmu %.10g vs complex step %.10g (rel %.2e), central FD %.10g (rel %.2e)'
+                  % (gmu100, csm, abs(gmu100 - csm) / abs(csm), fdm, abs(gmu100 - fdm) / abs(gmu100)))
+            assert abs(gmu100 - csm) <= 1e-5 * abs(csm)
+            assert abs(gmu100 - fdm) <= 1e-5 * abs(gmu100)
+        else:
+            assert gmu100 == 0.0
