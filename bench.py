@@ -923,9 +923,68 @@ def run_tte(args):
     print(json.dumps(out))
 
 
+def run_stability(args):
+    """Largest stable CFL of ROK4 on the cylinder O-grid for several Krylov
+    dimensions (the paper: ROK is conditionally stable, Sec. 3.1 table of
+    methods; its Krylov size study, Sec. 4.4).  For each M, CFL numbers are
+    tried in increasing order over the same physical time T = horizon x the
+    CFL-1 step; a CFL counts as stable when every step stays finite and the
+    state norm stays within 2x its start.  The scan per M stops at the first
+    unstable CFL.  Start: the impulsive free stream, or with --developed K a
+    state after K RK4 steps at CFL 1 from it (the start-up transient past)."""
+    import torch
+
+    from paper_1607_06834_gb300 import rok
+    from paper_1607_06834_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    prob, y0, _ = W.cylinder_ogrid(256, 512)
+    ms = [int(x) for x in args.krylov_list.split(',')]
+    cfls = [float(x) for x in (args.cfls or '1,2,3,5,7,10,15,20,30,50,100,300,1000').split(',')]
+    ctx = rok.rok_init(prob, krylov_max=max(ms))
+    y = rok.state_tensor(y0)
+    dt1 = rok.rok_dt_from_cfl(ctx, y, 1.0)
+    start = 'impulsive'
+    if args.developed > 0:
+        for _ in range(args.developed):
+            rok.rk_step(ctx, y, dt1)
+        torch.cuda.synchronize()
+        start = 'after %d RK4 steps at CFL 1 (t = %.4g)' % (args.developed, args.developed * dt1)
+    ys = y.clone()
+    n0 = float(ys.norm())
+    T = args.horizon * dt1
+    out = {'study': 'stable-cfl-vs-krylov-dimension', 'case': prob.name, 'start': start, 'T': T, 'dt_cfl1': dt1,
+           'scan': {}}
+    for M in ms:
+        rows, largest = [], None
+        for c in cfls:
+            n = max(1, int(round(T / (c * dt1))))
+            h = T / n
+            yy = ys.clone()
+            ok, why = True, ''
+            t0 = time.perf_counter()
+            for k in range(n):
+                try:
+                    rok.rok_step(ctx, yy, h, M, info=(k % 10 == 9 or k == n - 1))
+                except rok.RokError as e:
+                    ok, why = False, 'step %d: %s' % (k + 1, rok.rok_status_string(e.status))
+                    break
+            if ok:
+                nr = float(yy.norm())
+                if not (nr <= 2.0 * n0):
+                    ok, why = False, 'norm grew %.3g x' % (nr / n0)
+            rows.append({'cfl': c, 'steps': n, 'stable': ok, 'why': why, 'wall_s': round(time.perf_counter() - t0, 2)})
+            if not ok:
+                break
+            largest = c
+        out['scan'][str(M)] = {'largest_stable_cfl': largest, 'runs': rows}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument('--study', default=None, choices=[None, 'tte', 'wp'])
+    ap.add_argument('--study', default=None, choices=[None, 'tte', 'wp', 'stability'])
+    ap.add_argument('--krylov-list', default='4,8,12,20,30', help='Krylov dimensions (stability study)')
+    ap.add_argument('--developed', type=int, default=0, help='RK4 steps before the stability scan')
     ap.add_argument('--case', default='tgv', choices=['tgv', 'cylinder'])
     ap.add_argument('--horizon', type=float, default=50.0, help='T in units of the base-CFL step')
     ap.add_argument('--ref-factor', type=float, default=16.0)
@@ -960,6 +1019,9 @@ def main():
         return
     if args.study == 'wp':
         run_wp(args)
+        return
+    if args.study == 'stability':
+        run_stability(args)
         return
     out = run_reference(args) if args.impl == 'reference' else run_ours(args)
     if out is not None:
