@@ -12,9 +12,7 @@ impulsive start) the linearised step y' = J y shows it: the smallest Krylov
 dimension that keeps ROK4 from outgrowing the exact solution rises with the
 CFL number, 2 at CFL 10 (48 decaying modes outside the RK4 region), 8 at
 CFL 30 (96) and 32 at CFL 100 (112 modes, max |R| ~ 3e6); one step below
-each, the iteration blows up or grows well beyond the exact solution.  The
-256 x 512 grid has about a thousand times as many wall-normal stiff modes,
-which M = 30 cannot cover beyond CFL ~10.
+each, the iteration blows up or grows well beyond the exact solution.
 These tests run the oracle's ROK4 step on that linear system."""
 import numpy as np
 import pytest
