@@ -806,6 +806,119 @@ __global__ void __launch_bounds__(RT, 2) cgs2_column_kernel(const double *__rest
         store8(vout, e0[c], n, x);
     }
 }
+
+// ---- binary64 Arnoldi column, FMA build: the entries split evenly --------------
+// The strict build's pairwise tree fixes 2048-entry chunks, and 512 of them
+// (512^2) do not divide over 152 SMs: some SMs hold 4, the others 3, and the
+// FP64 phase of every pass runs at the pace of the 4-chunk SMs.  The FMA build
+// is free in its summation order, so this variant gives CTA b the contiguous
+// range [b L, (b + 1) L) of L = ceil(n / G) entries (at most kEvenPerThread per
+// thread, strided by the CTA width so that loads stay coalesced) and one
+// partial per CTA; the modified Gram-Schmidt passes, the waits, the breakdown
+// test and the normalisation are those of arnoldi_column_kernel.
+constexpr int kEvenPerThread = 2 * EPL;   // 4096 entries per CTA at most (E <= 16)
+
+// the first kmax terms (kmax uniform over the CTA: the slots no thread of the
+// CTA holds are skipped, not multiplied by zero)
+template <int E>
+__device__ __forceinline__ double even_dot(const double (&a)[E], const double (&b)[E], int kmax)
+{
+    double s = a[0] * b[0];
+#pragma unroll
+    for (int k = 1; k < E; ++k)
+        if (k < kmax) s = a[k] * b[k] + s;
+    return s;
+}
+
+// this thread's entries of a range are base[k RT], k < kv (a prefix of the k);
+// slots kv <= k < kmax hold zeros
+template <int E>
+__device__ __forceinline__ void even_load(double (&x)[E], const double *__restrict__ base, int kv, int kmax)
+{
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+        if (k < kmax) x[k] = k < kv ? base[k * RT] : 0.0;
+}
+
+template <int E>
+__device__ __forceinline__ void even_prefetch(const double *base, int kv)
+{
+    if ((threadIdx.x & 15) != 0) return;   // one thread per 128-byte line
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+        if (k < kv) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + k * RT));
+}
+
+template <int E>
+__global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__restrict__ w, double *__restrict__ V,
+                                                             size_t ldv, size_t n, int j, int next, size_t L,
+                                                             double *partA, double *partB, unsigned *cnt,
+                                                             StepState *st, double brk_tol)
+{
+    __shared__ double sh[16];
+    __shared__ int act;
+    if (threadIdx.x == 0) act = st->active;
+    __syncthreads();
+    if (act == 0) return;
+    const unsigned G = gridDim.x;
+    const size_t lo = (size_t)blockIdx.x * L;
+    const size_t hi = lo + L < n ? lo + L : n;
+    const size_t my = lo + threadIdx.x;   // this thread's first entry
+    const int kv = my < hi ? (int)((hi - my + RT - 1) / RT) : 0;
+    const int kmax = (int)((hi - lo + RT - 1) / RT);   // uniform over the CTA
+    double wv[E], vn[E];
+    even_load(wv, w + my, kv, kmax);
+    even_load(vn, V + my, kv, kmax);   // v_0
+    if (j >= 1) even_prefetch<E>(V + ldv + my, kv);   // v_1, read after the first wait
+    // pass 0 partials: <v_0, w> and <w, w>
+    {
+        double s0, s1;
+        chunk_sum2v(even_dot(vn, wv, kmax), even_dot(wv, wv, kmax), sh, s0, s1);
+        if (threadIdx.x == 0) partA[blockIdx.x] = s0;
+        if (threadIdx.x == 8) partA[G + blockIdx.x] = s1;
+    }
+    gen_arrive(cnt);
+    double *pin = partA, *pout = partB;
+    double wnorm0 = 0.0;
+    for (int i = 0; i <= j; ++i) {
+        if (!gen_wait(cnt + i, G, &st->status)) return;
+        const double h = tree_partials(pin, (int)G, sh);
+        if (i == 0) wnorm0 = sqrt(tree_partials(pin + G, (int)G, sh));
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->H[i * kMaxKrylov + j] = h;
+            if (i == 0) st->wnorm0 = wnorm0;
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k)
+            if (k < kmax) wv[k] = wv[k] - h * vn[k];
+        const bool more = i < j;
+        if (more) even_load(vn, V + (size_t)(i + 1) * ldv + my, kv, kmax);
+        if (i + 2 <= j) even_prefetch<E>(V + (size_t)(i + 2) * ldv + my, kv);   // the next pass's vector
+        const double x = more ? even_dot(vn, wv, kmax) : even_dot(wv, wv, kmax);
+        const double sa = chunk_sumv(x, sh);
+        if (threadIdx.x == 0) pout[blockIdx.x] = sa;
+        gen_arrive(cnt + i + 1);
+        double *t = pin;
+        pin = pout;
+        pout = t;
+    }
+    if (!next) return;
+    if (!gen_wait(cnt + j + 1, G, &st->status)) return;
+    const double hn = sqrt(tree_partials(pin, (int)G, sh));
+    if (!(hn > brk_tol * wnorm0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->active = 0;
+            st->meff = j + 1;
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->H[(j + 1) * kMaxKrylov + j] = hn;
+    const double r = 1.0 / hn;
+    double *vout = V + (size_t)(j + 1) * ldv + my;
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+        if (k < kv) vout[k * RT] = wv[k] * r;
+}
 #endif  // ROK_LINALG_FAST
 
 // First basis vector: partials of ||(T)F1||^2 ...
@@ -865,9 +978,13 @@ static int arnoldi_column_ctas(int sms)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, arnoldi_column_kernel<float>, RT, 0) != cudaSuccess)
         return 0;
 #ifdef ROK_LINALG_FAST
-    int pc = 0;
+    int pc = 0, pe = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, cgs2_column_kernel, RT, 0) != cudaSuccess) return 0;
     if (pc < p32) p32 = pc;
+    for (auto kern : {arnoldi_even_kernel<8>, arnoldi_even_kernel<14>, arnoldi_even_kernel<16>}) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pe, kern, RT, 0) != cudaSuccess) return 0;
+        if (pe < p64) p64 = pe;
+    }
 #endif
     return (p64 < p32 ? p64 : p32) * sms;
 }
@@ -896,8 +1013,21 @@ static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv
     }
     double *Vd = static_cast<double *>(V);
     double tol = 1e-12;
+#ifdef ROK_LINALG_FAST
+    // even split: G CTAs of L entries each
+    size_t L = (n + G - 1) / G;
+    L += L & 1;
+    if (L > (size_t)RT * kEvenPerThread) return cudaErrorNotSupported;
+    void *eargs[] = {&w, &Vd, &ldv, &n, &j, &next, &L, &partA, &partB, &cnt, &st, &tol};
+    // entries per thread: the smallest instantiation that holds L / RT
+    const void *kern = L <= (size_t)RT * 8 ? (const void *)arnoldi_even_kernel<8>
+                       : L <= (size_t)RT * 14 ? (const void *)arnoldi_even_kernel<14>
+                                              : (const void *)arnoldi_even_kernel<16>;
+    return cudaLaunchCooperativeKernel(kern, dim3(G), dim3(RT), eargs, 0, s);
+#else
     void *args[] = {&w, &Vd, &ldv, &n, &j, &next, &P, &partA, &partB, &cnt, &st, &tol};
     return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<double>, dim3(G), dim3(RT), args, 0, s);
+#endif
 }
 
 static cudaError_t first_vector(const double *F, void *V0, int fp32, size_t n, double *partials, int P,

@@ -420,8 +420,12 @@ def test_cylinder_full_size_one_step_strict_bitexact(rok):
 def test_persistent_and_pass_by_pass_gram_schmidt_agree(rok, mode):
     # one ROK4 step and its reverse, with the Gram-Schmidt passes of each Krylov
     # column in one cooperative launch and with one launch per pass (the path of
-    # grids beyond the cooperative kernels' reach): the same sums in the same
-    # order, so the same bits; strict rounding also equals the oracle's step
+    # grids beyond the cooperative kernels' reach).  Strict rounding: the same
+    # sums in the same order, so the same bits, and the oracle's step.  FMA
+    # build: the cooperative binary64 column splits the entries evenly over its
+    # CTAs (another summation order than the 2048-entry chunks of the
+    # pass-by-pass kernels), so the two agree to the rounding the FD quotients
+    # amplify (the oracle's one-ulp floor of this step)
     prob, y0 = W.taylor_green(48, reynolds=300.0)
     y0 = np.ascontiguousarray(y0 + 0.01 * W.random_smooth_state(prob, seed=7))
     h = I.dt_from_cfl(prob, y0, 4.0)
@@ -436,11 +440,20 @@ def test_persistent_and_pass_by_pass_gram_schmidt_agree(rok, mode):
         yb, mub = rok.rok_step_vjp(ctx, dev(y0), h, M, dev(c))
         res.append((host(y), host(yb), mub))
     (ya, yba, ma), (yp, ybp, mp) = res
-    assert np.array_equal(ya, yp)
-    assert np.array_equal(yba, ybp)
-    assert ma == mp
     if mode == 'strict':
+        assert np.array_equal(ya, yp)
+        assert np.array_equal(yba, ybp)
+        assert ma == mp
         assert np.array_equal(ya, I.rok_step(core.System(prob), y0, h, M))
+    else:
+        from tests.oracle_floor import one_ulp_everywhere
+        sys_ = core.System(prob)
+        yo = I.rok_step(sys_, y0, h, M)
+        floor = rel_l2(I.rok_step(sys_, one_ulp_everywhere(y0, 1), h, M), yo)
+        d, db = rel_l2(ya, yp), rel_l2(yba, ybp)
+        print('\n[persistent] FMA build, one step: y %.2e, reverse %.2e, oracle floor %.2e' % (d, db, floor))
+        assert d <= max(1e-12, 10 * floor)
+        assert db <= 1e-6 and abs(ma - mp) <= 1e-6 * abs(mp)
 
 
 def test_persistent_switch_refused_for_binary32_basis(rok):
@@ -477,7 +490,8 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(rok):
 def test_reverse_gram_schmidt_two_chunks_per_cta_at_512(rok):
     # 512^2: 512 chunks of 2048 entries, more than the co-resident CTAs, so the
     # cooperative reverse Gram-Schmidt kernel takes two chunks per CTA; it must
-    # give the bits of the pass-by-pass launches
+    # give the bits of the pass-by-pass launches (strict rounding, where the
+    # recomputed forward steps of the two paths agree bit for bit too)
     import torch
     prob, y0 = W.taylor_green(512, reynolds=1600.0)
     h = I.dt_from_cfl(prob, y0, 8.0)
@@ -485,7 +499,7 @@ def test_reverse_gram_schmidt_two_chunks_per_cta_at_512(rok):
     c = dev(np.random.default_rng(11).standard_normal(y0.shape))
     res = []
     for persistent in (True, False):
-        ctx = rok.rok_init(prob, krylov_max=M)
+        ctx = rok.rok_init(prob, krylov_max=M, rounding=rok.ROK_ROUND_STRICT)
         rok.rok_set_persistent(ctx, persistent)
         yb, mub = rok.rok_step_vjp(ctx, dev(y0), h, M, c)
         res.append((yb, mub))
@@ -496,13 +510,14 @@ def test_reverse_gram_schmidt_two_chunks_per_cta_at_512(rok):
 @pytest.mark.parametrize('method', ['esdirk', 'ros4'])
 def test_device_gmres_persistent_and_pass_by_pass_agree(rok, method):
     # the GMRES Arnoldi columns in one cooperative launch each and in one launch
-    # per Gram-Schmidt pass: the same sums in the same order, so the same bits
+    # per Gram-Schmidt pass, strict rounding: the same sums in the same order,
+    # so the same bits
     prob, y0 = W.taylor_green(48, reynolds=300.0)
     y0 = np.ascontiguousarray(y0 + 0.01 * W.random_smooth_state(prob, seed=5))
     h = I.dt_from_cfl(prob, y0, 6.0)
     res = []
     for persistent in (True, False):
-        ctx = rok.rok_init(prob, krylov_max=30)
+        ctx = rok.rok_init(prob, krylov_max=30, rounding=rok.ROK_ROUND_STRICT)
         rok.rok_set_persistent(ctx, persistent)
         y = dev(y0)
         if method == 'esdirk':
