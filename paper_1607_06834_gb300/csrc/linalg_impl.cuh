@@ -840,6 +840,63 @@ __device__ __forceinline__ void even_load(double (&x)[E], const double *__restri
         if (k < kmax) x[k] = k < kv ? base[k * RT] : 0.0;
 }
 
+// Reductions of the even split with fewer FP64 warp instructions: on this
+// part every warp-wide FP64 instruction costs the SM's FP64 pipe as much as a
+// full one, so a butterfly in each of the 8 warps (40 instructions a CTA)
+// gives way to one warp that adds the 256 values (7 + 5 instructions).
+// The CTA sum of x (one value per thread), valid in warp 0; s256 holds 256 values.
+__device__ __forceinline__ double cta_sum_w0(double x, double *s256)
+{
+    s256[threadIdx.x] = x;
+    __syncthreads();
+    double v = 0.0;
+    if (threadIdx.x < 32) {
+        const double *q = s256 + threadIdx.x * 8;
+        v = lane_tree(((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7])));
+    }
+    return v;
+}
+
+// the CTA sums of x (in warp 0) and y (in warp 1); s512 holds 512 values
+__device__ __forceinline__ void cta_sum2_w01(double x, double y, double *s512, double &sx, double &sy)
+{
+    s512[threadIdx.x] = x;
+    s512[RT + threadIdx.x] = y;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const double *q = s512 + (threadIdx.x >> 5) * RT + (threadIdx.x & 31) * 8;
+        const double v = lane_tree(((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7])));
+        sx = v;
+        sy = v;
+    }
+}
+
+// sum of the G CTA partials p[0 .. G) (G <= 512) by warp 0, broadcast through sh
+__device__ __forceinline__ double grid_sum(const double *__restrict__ p, int G, double *sh)
+{
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int qmax = (G + 31) >> 5;   // uniform
+        double x[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int b = threadIdx.x + 32 * q;
+            x[q] = q < qmax && b < G ? p[b] : 0.0;
+        }
+        double a = x[0], c = 0.0;
+#pragma unroll
+        for (int q = 1; q < 16; ++q)
+            if (q < qmax) {
+                if (q & 1) c = c + x[q];
+                else a = a + x[q];
+            }
+        const double v = lane_tree(a + c);
+        if (threadIdx.x == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
 template <int E>
 __device__ __forceinline__ void even_prefetch(const double *base, int kv)
 {
@@ -856,6 +913,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
                                                              StepState *st, double brk_tol)
 {
     __shared__ double sh[16];
+    __shared__ double sred[2 * RT];
     __shared__ int act;
     if (threadIdx.x == 0) act = st->active;
     __syncthreads();
@@ -872,18 +930,18 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
     if (j >= 1) even_prefetch<E>(V + ldv + my, kv);   // v_1, read after the first wait
     // pass 0 partials: <v_0, w> and <w, w>
     {
-        double s0, s1;
-        chunk_sum2v(even_dot(vn, wv, kmax), even_dot(wv, wv, kmax), sh, s0, s1);
+        double s0 = 0.0, s1 = 0.0;
+        cta_sum2_w01(even_dot(vn, wv, kmax), even_dot(wv, wv, kmax), sred, s0, s1);
         if (threadIdx.x == 0) partA[blockIdx.x] = s0;
-        if (threadIdx.x == 8) partA[G + blockIdx.x] = s1;
+        if (threadIdx.x == 32) partA[G + blockIdx.x] = s1;
     }
     gen_arrive(cnt);
     double *pin = partA, *pout = partB;
     double wnorm0 = 0.0;
     for (int i = 0; i <= j; ++i) {
         if (!gen_wait(cnt + i, G, &st->status)) return;
-        const double h = tree_partials(pin, (int)G, sh);
-        if (i == 0) wnorm0 = sqrt(tree_partials(pin + G, (int)G, sh));
+        const double h = grid_sum(pin, (int)G, sh);
+        if (i == 0) wnorm0 = sqrt(grid_sum(pin + G, (int)G, sh));
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->H[i * kMaxKrylov + j] = h;
             if (i == 0) st->wnorm0 = wnorm0;
@@ -895,7 +953,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
         if (more) even_load(vn, V + (size_t)(i + 1) * ldv + my, kv, kmax);
         if (i + 2 <= j) even_prefetch<E>(V + (size_t)(i + 2) * ldv + my, kv);   // the next pass's vector
         const double x = more ? even_dot(vn, wv, kmax) : even_dot(wv, wv, kmax);
-        const double sa = chunk_sumv(x, sh);
+        const double sa = cta_sum_w0(x, sred);
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
         gen_arrive(cnt + i + 1);
         double *t = pin;
@@ -904,7 +962,7 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
     }
     if (!next) return;
     if (!gen_wait(cnt + j + 1, G, &st->status)) return;
-    const double hn = sqrt(tree_partials(pin, (int)G, sh));
+    const double hn = sqrt(grid_sum(pin, (int)G, sh));
     if (!(hn > brk_tol * wnorm0)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->active = 0;
@@ -1017,7 +1075,7 @@ static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv
     // even split: G CTAs of L entries each
     size_t L = (n + G - 1) / G;
     L += L & 1;
-    if (L > (size_t)RT * kEvenPerThread) return cudaErrorNotSupported;
+    if (L > (size_t)RT * kEvenPerThread || G > 512) return cudaErrorNotSupported;
     void *eargs[] = {&w, &Vd, &ldv, &n, &j, &next, &L, &partA, &partB, &cnt, &st, &tol};
     // entries per thread: the smallest instantiation that holds L / RT
     const void *kern = L <= (size_t)RT * 8 ? (const void *)arnoldi_even_kernel<8>
