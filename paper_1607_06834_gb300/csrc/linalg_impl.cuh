@@ -927,7 +927,6 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
     double wv[E], vn[E];
     even_load(wv, w + my, kv, kmax);
     even_load(vn, V + my, kv, kmax);   // v_0
-    if (j >= 1) even_prefetch<E>(V + ldv + my, kv);   // v_1, read after the first wait
     // pass 0 partials: <v_0, w> and <w, w>
     {
         double s0 = 0.0, s1 = 0.0;
@@ -938,6 +937,8 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
     gen_arrive(cnt);
     double *pin = partA, *pout = partB;
     double wnorm0 = 0.0;
+    double vq[E];   // v_{i+1}, loaded before the wait of pass i
+    if (j >= 1) even_load(vq, V + ldv + my, kv, kmax);
     for (int i = 0; i <= j; ++i) {
         if (!gen_wait(cnt + i, G, &st->status)) return;
         const double h = grid_sum(pin, (int)G, sh);
@@ -950,8 +951,11 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
         for (int k = 0; k < E; ++k)
             if (k < kmax) wv[k] = wv[k] - h * vn[k];
         const bool more = i < j;
-        if (more) even_load(vn, V + (size_t)(i + 1) * ldv + my, kv, kmax);
-        if (i + 2 <= j) even_prefetch<E>(V + (size_t)(i + 2) * ldv + my, kv);   // the next pass's vector
+        if (more) {
+#pragma unroll
+            for (int k = 0; k < E; ++k) vn[k] = vq[k];
+            if (i + 2 <= j) even_load(vq, V + (size_t)(i + 2) * ldv + my, kv, kmax);   // lands during the next wait
+        }
         const double x = more ? even_dot(vn, wv, kmax) : even_dot(wv, wv, kmax);
         const double sa = cta_sum_w0(x, sred);
         if (threadIdx.x == 0) pout[blockIdx.x] = sa;
