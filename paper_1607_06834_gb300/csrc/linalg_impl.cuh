@@ -816,7 +816,27 @@ __global__ void __launch_bounds__(RT, 2) cgs2_column_kernel(const double *__rest
 // thread, strided by the CTA width so that loads stay coalesced) and one
 // partial per CTA; the modified Gram-Schmidt passes, the waits, the breakdown
 // test and the normalisation are those of arnoldi_column_kernel.
-constexpr int kEvenPerThread = 2 * EPL;   // 4096 entries per CTA at most (E <= 16)
+//
+// One CTA of kEvenThreads threads per SM (the register file holds 512 threads
+// of this kernel): one set of reductions and one arrival per SM and pass, and
+// every reduction spread over four warps, one per SM sub-partition.  On this
+// part a warp-wide FP64 instruction occupies a sub-partition's FP64 unit for
+// many cycles whatever its active lanes, so a reduction's latency is the
+// number of dependent FP64 instructions on the busiest sub-partition: a CTA
+// sum of 512 values by one warp takes 20, by four warps 8; a grid sum of 152
+// partials by one warp 10, by four warps 8.  The basis vector of the pass
+// after next is loaded after the arrival, so the release of the arrival does
+// not wait for those loads.
+constexpr int kEvenThreads = 512;
+constexpr int kEvenPerThread = 16;    // 8192 entries per CTA at most (E <= 16)
+constexpr int kEvenMaxGrid = 256;     // grid sums: 4 warps, 2 partials a lane
+
+// named barrier ID of NT threads (immediate operands)
+template <int ID, int NT>
+__device__ __forceinline__ void bar_named()
+{
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NT) : "memory");
+}
 
 // the first kmax terms (kmax uniform over the CTA: the slots no thread of the
 // CTA holds are skipped, not multiplied by zero)
@@ -830,122 +850,133 @@ __device__ __forceinline__ double even_dot(const double (&a)[E], const double (&
     return s;
 }
 
-// this thread's entries of a range are base[k RT], k < kv (a prefix of the k);
-// slots kv <= k < kmax hold zeros
+// this thread's entries of a range are base[k kEvenThreads], k < kv (a prefix
+// of the k); slots kv <= k < kmax hold zeros
 template <int E>
 __device__ __forceinline__ void even_load(double (&x)[E], const double *__restrict__ base, int kv, int kmax)
 {
 #pragma unroll
     for (int k = 0; k < E; ++k)
-        if (k < kmax) x[k] = k < kv ? base[k * RT] : 0.0;
+        if (k < kmax) x[k] = k < kv ? base[k * kEvenThreads] : 0.0;
 }
 
-// Reductions of the even split with fewer FP64 warp instructions: on this
-// part every warp-wide FP64 instruction costs the SM's FP64 pipe as much as a
-// full one, so a butterfly in each of the 8 warps (40 instructions a CTA)
-// gives way to one warp that adds the 256 values (7 + 5 instructions).
-// The CTA sum of x (one value per thread), valid in warp 0; s256 holds 256 values.
-__device__ __forceinline__ double cta_sum_w0(double x, double *s256)
+// The sum of s[0 .. 512) by the four warps of quad q (warps 4q .. 4q + 3,
+// named barrier 1 + q): warp k adds s[128 k .. 128 k + 128), four consecutive
+// values a lane, then the lane butterfly; the quad's first thread adds the
+// four warp sums.  The result is valid in thread 128 q; sh4 holds 8 values.
+template <int q>
+__device__ __forceinline__ double quad_cta_sum(const double *s, double *sh4)
 {
-    s256[threadIdx.x] = x;
-    __syncthreads();
-    double v = 0.0;
-    if (threadIdx.x < 32) {
-        const double *q = s256 + threadIdx.x * 8;
-        v = lane_tree(((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7])));
-    }
-    return v;
+    const int k = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+    const double *v = s + k * 128 + lane * 4;
+    const double a = lane_tree((v[0] + v[1]) + (v[2] + v[3]));
+    if (lane == 0) sh4[4 * q + k] = a;
+    bar_named<1 + q, 128>();
+    double r = 0.0;
+    if ((threadIdx.x & 127) == 0) r = (sh4[4 * q] + sh4[4 * q + 1]) + (sh4[4 * q + 2] + sh4[4 * q + 3]);
+    return r;
 }
 
-// the CTA sums of x (in warp 0) and y (in warp 1); s512 holds 512 values
-__device__ __forceinline__ void cta_sum2_w01(double x, double y, double *s512, double &sx, double &sy)
+// The sum of the G CTA partials p[0 .. G) (G <= kEvenMaxGrid) by quad q: warp
+// k adds the k-th quarter (two partials a lane, then the butterfly), the
+// quad's first thread the four quarter sums.  Every CTA forms the same sum in
+// the same order.  Valid in thread 128 q.
+template <int q>
+__device__ __forceinline__ double quad_grid_sum(const double *p, int G, double *sh4)
 {
-    s512[threadIdx.x] = x;
-    s512[RT + threadIdx.x] = y;
-    __syncthreads();
-    if (threadIdx.x < 64) {
-        const double *q = s512 + (threadIdx.x >> 5) * RT + (threadIdx.x & 31) * 8;
-        const double v = lane_tree(((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7])));
-        sx = v;
-        sy = v;
-    }
+    const int k = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+    const int Q = (G + 3) >> 2;
+    const int b0 = k * Q + lane, e = min(G, (k + 1) * Q);
+    const double x0 = b0 < e ? p[b0] : 0.0;
+    const double x1 = b0 + 32 < e ? p[b0 + 32] : 0.0;
+    const double a = lane_tree(x0 + x1);
+    if (lane == 0) sh4[4 * q + k] = a;
+    bar_named<1 + q, 128>();
+    double r = 0.0;
+    if ((threadIdx.x & 127) == 0) r = (sh4[4 * q] + sh4[4 * q + 1]) + (sh4[4 * q + 2] + sh4[4 * q + 3]);
+    return r;
 }
 
-// sum of the G CTA partials p[0 .. G) (G <= 512) by warp 0, broadcast through sh
-__device__ __forceinline__ double grid_sum(const double *__restrict__ p, int G, double *sh)
+// Wait (thread 0, bounded) until generation counter *cnt reaches G, then the
+// grid sums of the nsum (1 or 2) partial arrays p + q G by quads q < nsum;
+// every thread finds them in sh[0 .. nsum).  False (status set) on timeout.
+template <int nsum>
+__device__ __forceinline__ bool even_wait_sums(const unsigned *cnt, unsigned G, int *status, const double *p,
+                                               double *sh, double *sh4)
 {
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int qmax = (G + 31) >> 5;   // uniform
-        double x[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int b = threadIdx.x + 32 * q;
-            x[q] = q < qmax && b < G ? p[b] : 0.0;
-        }
-        double a = x[0], c = 0.0;
-#pragma unroll
-        for (int q = 1; q < 16; ++q)
-            if (q < qmax) {
-                if (q & 1) c = c + x[q];
-                else a = a + x[q];
+    __shared__ int ok;
+    const int q = threadIdx.x >> 7;
+    if (q < nsum) {
+        if (threadIdx.x == 0) {
+            ok = 1;
+            long long spins = 0;
+            while (ld_acquire_gpu(cnt) < G) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
-        const double v = lane_tree(a + c);
-        if (threadIdx.x == 0) sh[0] = v;
+        }
+        bar_named<3, 128 * nsum>();
+        if (ok) {
+            const double s = q == 0 ? quad_grid_sum<0>(p, (int)G, sh4) : quad_grid_sum<1>(p + G, (int)G, sh4);
+            if ((threadIdx.x & 127) == 0) sh[q] = s;
+        }
     }
     __syncthreads();
-    return sh[0];
+    return ok != 0;
 }
 
 template <int E>
-__device__ __forceinline__ void even_prefetch(const double *base, int kv)
+__global__ void __launch_bounds__(kEvenThreads, 1)
+    arnoldi_even_kernel(const double *__restrict__ w, double *__restrict__ V, size_t ldv, size_t n, int j, int next,
+                        size_t L, double *partA, double *partB, unsigned *cnt, StepState *st, double brk_tol)
 {
-    if ((threadIdx.x & 15) != 0) return;   // one thread per 128-byte line
-#pragma unroll
-    for (int k = 0; k < E; ++k)
-        if (k < kv) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + k * RT));
-}
-
-template <int E>
-__global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__restrict__ w, double *__restrict__ V,
-                                                             size_t ldv, size_t n, int j, int next, size_t L,
-                                                             double *partA, double *partB, unsigned *cnt,
-                                                             StepState *st, double brk_tol)
-{
-    __shared__ double sh[16];
-    __shared__ double sred[2 * RT];
+    constexpr int T = kEvenThreads;
+    __shared__ double sh[2];
+    __shared__ double sh4[8];
+    __shared__ double sred[2 * T];
     __shared__ int act;
     if (threadIdx.x == 0) act = st->active;
     __syncthreads();
     if (act == 0) return;
     const unsigned G = gridDim.x;
+    const int quad = threadIdx.x >> 7;
     const size_t lo = (size_t)blockIdx.x * L;
     const size_t hi = lo + L < n ? lo + L : n;
     const size_t my = lo + threadIdx.x;   // this thread's first entry
-    const int kv = my < hi ? (int)((hi - my + RT - 1) / RT) : 0;
-    const int kmax = (int)((hi - lo + RT - 1) / RT);   // uniform over the CTA
+    const int kv = my < hi ? (int)((hi - my + T - 1) / T) : 0;
+    const int kmax = (int)((hi - lo + T - 1) / T);   // uniform over the CTA
     double wv[E], vn[E];
     even_load(wv, w + my, kv, kmax);
     even_load(vn, V + my, kv, kmax);   // v_0
-    // pass 0 partials: <v_0, w> and <w, w>
-    {
-        double s0 = 0.0, s1 = 0.0;
-        cta_sum2_w01(even_dot(vn, wv, kmax), even_dot(wv, wv, kmax), sred, s0, s1);
-        if (threadIdx.x == 0) partA[blockIdx.x] = s0;
-        if (threadIdx.x == 32) partA[G + blockIdx.x] = s1;
+    // pass 0 partials: <v_0, w> by quad 0 and <w, w> by quad 1
+    sred[threadIdx.x] = even_dot(vn, wv, kmax);
+    sred[T + threadIdx.x] = even_dot(wv, wv, kmax);
+    __syncthreads();
+    if (quad < 2) {
+        const double s = quad == 0 ? quad_cta_sum<0>(sred, sh4) : quad_cta_sum<1>(sred + T, sh4);
+        if ((threadIdx.x & 127) == 0) partA[quad * G + blockIdx.x] = s;
     }
-    gen_arrive(cnt);
-    double *pin = partA, *pout = partB;
-    double wnorm0 = 0.0;
-    double vq[E];   // v_{i+1}, loaded before the wait of pass i
+    __syncthreads();   // both partials stored before the arrival
+    if (threadIdx.x == 0) red_add_release_gpu(cnt, 1u);
+    double vq[E];   // v_{i+1} during pass i
     if (j >= 1) even_load(vq, V + ldv + my, kv, kmax);
+    double *pin = partA, *pout = partB;
+    double wnorm0 = 0.0;   // thread 0 only
     for (int i = 0; i <= j; ++i) {
-        if (!gen_wait(cnt + i, G, &st->status)) return;
-        const double h = grid_sum(pin, (int)G, sh);
-        if (i == 0) wnorm0 = sqrt(grid_sum(pin + G, (int)G, sh));
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            st->H[i * kMaxKrylov + j] = h;
-            if (i == 0) st->wnorm0 = wnorm0;
+        if (!(i == 0 ? even_wait_sums<2>(cnt, G, &st->status, pin, sh, sh4)
+                     : even_wait_sums<1>(cnt + i, G, &st->status, pin, sh, sh4)))
+            return;
+        const double h = sh[0];
+        if (threadIdx.x == 0) {
+            if (i == 0) wnorm0 = sqrt(sh[1]);
+            if (blockIdx.x == 0) {
+                st->H[i * kMaxKrylov + j] = h;
+                if (i == 0) st->wnorm0 = wnorm0;
+            }
         }
 #pragma unroll
         for (int k = 0; k < E; ++k)
@@ -954,32 +985,47 @@ __global__ void __launch_bounds__(RT, 2) arnoldi_even_kernel(const double *__res
         if (more) {
 #pragma unroll
             for (int k = 0; k < E; ++k) vn[k] = vq[k];
-            if (i + 2 <= j) even_load(vq, V + (size_t)(i + 2) * ldv + my, kv, kmax);   // lands during the next wait
         }
-        const double x = more ? even_dot(vn, wv, kmax) : even_dot(wv, wv, kmax);
-        const double sa = cta_sum_w0(x, sred);
-        if (threadIdx.x == 0) pout[blockIdx.x] = sa;
-        gen_arrive(cnt + i + 1);
+        sred[threadIdx.x] = more ? even_dot(vn, wv, kmax) : even_dot(wv, wv, kmax);
+        __syncthreads();
+        if (quad == 0) {
+            const double s = quad_cta_sum<0>(sred, sh4);
+            if (threadIdx.x == 0) {
+                pout[blockIdx.x] = s;   // the same thread releases it
+                red_add_release_gpu(cnt + i + 1, 1u);
+            }
+        }
+        if (more && i + 2 <= j) even_load(vq, V + (size_t)(i + 2) * ldv + my, kv, kmax);   // lands during the wait
         double *t = pin;
         pin = pout;
         pout = t;
     }
     if (!next) return;
-    if (!gen_wait(cnt + j + 1, G, &st->status)) return;
-    const double hn = sqrt(grid_sum(pin, (int)G, sh));
-    if (!(hn > brk_tol * wnorm0)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            st->active = 0;
-            st->meff = j + 1;
+    if (!even_wait_sums<1>(cnt + j + 1, G, &st->status, pin, sh, sh4)) return;
+    // the norm, the breakdown test and the reciprocal by thread 0 (FP64
+    // square roots and divisions in every warp would cost each sub-partition)
+    __shared__ double rs;
+    __shared__ int brk;
+    if (threadIdx.x == 0) {
+        const double hn = sqrt(sh[0]);
+        brk = !(hn > brk_tol * wnorm0);
+        rs = 1.0 / hn;
+        if (blockIdx.x == 0) {
+            if (brk) {
+                st->active = 0;
+                st->meff = j + 1;
+            } else {
+                st->H[(j + 1) * kMaxKrylov + j] = hn;
+            }
         }
-        return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->H[(j + 1) * kMaxKrylov + j] = hn;
-    const double r = 1.0 / hn;
+    __syncthreads();
+    if (brk) return;
+    const double r = rs;
     double *vout = V + (size_t)(j + 1) * ldv + my;
 #pragma unroll
     for (int k = 0; k < E; ++k)
-        if (k < kv) vout[k * RT] = wv[k] * r;
+        if (k < kv) vout[k * T] = wv[k] * r;
 }
 #endif  // ROK_LINALG_FAST
 
@@ -1043,9 +1089,11 @@ static int arnoldi_column_ctas(int sms)
     int pc = 0, pe = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, cgs2_column_kernel, RT, 0) != cudaSuccess) return 0;
     if (pc < p32) p32 = pc;
+    // the binary64 column runs as arnoldi_even_kernel, kEvenThreads threads a CTA:
+    // its grid is ctas RT / kEvenThreads, which must be co-resident too
     for (auto kern : {arnoldi_even_kernel<8>, arnoldi_even_kernel<14>, arnoldi_even_kernel<16>}) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pe, kern, RT, 0) != cudaSuccess) return 0;
-        if (pe < p64) p64 = pe;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pe, kern, kEvenThreads, 0) != cudaSuccess) return 0;
+        if (pe * kEvenThreads < p64 * RT) p64 = pe * kEvenThreads / RT;
     }
 #endif
     return (p64 < p32 ? p64 : p32) * sms;
@@ -1076,16 +1124,18 @@ static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv
     double *Vd = static_cast<double *>(V);
     double tol = 1e-12;
 #ifdef ROK_LINALG_FAST
-    // even split: G CTAs of L entries each
-    size_t L = (n + G - 1) / G;
+    // even split: Ge CTAs of kEvenThreads threads and L entries each
+    const int Gmax = ctas * RT / kEvenThreads;
+    const int Ge = P < Gmax ? P : Gmax;
+    size_t L = (n + Ge - 1) / Ge;
     L += L & 1;
-    if (L > (size_t)RT * kEvenPerThread || G > 512) return cudaErrorNotSupported;
+    if (Ge < 1 || L > (size_t)kEvenThreads * kEvenPerThread || Ge > kEvenMaxGrid) return cudaErrorNotSupported;
     void *eargs[] = {&w, &Vd, &ldv, &n, &j, &next, &L, &partA, &partB, &cnt, &st, &tol};
-    // entries per thread: the smallest instantiation that holds L / RT
-    const void *kern = L <= (size_t)RT * 8 ? (const void *)arnoldi_even_kernel<8>
-                       : L <= (size_t)RT * 14 ? (const void *)arnoldi_even_kernel<14>
-                                              : (const void *)arnoldi_even_kernel<16>;
-    return cudaLaunchCooperativeKernel(kern, dim3(G), dim3(RT), eargs, 0, s);
+    // entries per thread: the smallest instantiation that holds L / kEvenThreads
+    const void *kern = L <= (size_t)kEvenThreads * 8 ? (const void *)arnoldi_even_kernel<8>
+                       : L <= (size_t)kEvenThreads * 14 ? (const void *)arnoldi_even_kernel<14>
+                                                        : (const void *)arnoldi_even_kernel<16>;
+    return cudaLaunchCooperativeKernel(kern, dim3(Ge), dim3(kEvenThreads), eargs, 0, s);
 #else
     void *args[] = {&w, &Vd, &ldv, &n, &j, &next, &P, &partA, &partB, &cnt, &st, &tol};
     return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<double>, dim3(G), dim3(RT), args, 0, s);
