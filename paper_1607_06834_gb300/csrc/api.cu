@@ -523,7 +523,7 @@ rok_status rok_init(rok_ctx **out, const rok_problem_desc *d, void *stream)
     const size_t N = c->N;
     auto al = [&](double **p, size_t n) { return cudaMalloc(p, n * sizeof(double)) == cudaSuccess; };
     bool ok = al(&c->V, (size_t)(c->mmax + 1) * N) && al(&c->w, N) && al(&c->t0, N) && al(&c->t1, N) &&
-              al(&c->t2, N) && al(&c->pA, 2 * (size_t)c->P) && al(&c->pB, 2 * (size_t)c->P) &&
+              al(&c->t2, N) && al(&c->pA, 4 * (size_t)c->P) && al(&c->pB, 2 * (size_t)c->P) &&
               al(&c->pM, (size_t)(kMaxKrylov + 2) * c->P);
     for (int i = 0; i < 4 && ok; ++i) ok = al(&c->F[i], N) && al(&c->K[i], N);
     if (ok && c->fp32) ok = cudaMalloc(&c->Vf, (size_t)(c->mmax + 1) * N * sizeof(float)) == cudaSuccess;

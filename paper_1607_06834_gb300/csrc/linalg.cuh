@@ -53,6 +53,7 @@ struct StepState {
     double phis[4][kMaxKrylov];    // phi of every stage (kept for the reverse step)
     double gcoef[kMaxKrylov + 1];  // coefficients of the GMRES update x += V gcoef
     GmresState gm;
+    double gram[kMaxKrylov];       // <v_{i+1}, v_i> of the basis (FMA-build two-vector passes)
 };
 
 // ---- rounding-mode dependent vector kernels (linalg_impl.cuh, compiled twice) ----
@@ -92,9 +93,12 @@ struct LinalgOps {
     // co-resident): h_ij = <v_i, w>, w -= h_ij v_i for i = 0..j (modified
     // Gram-Schmidt), then, when next != 0, h_{j+1,j} = ||w||, the breakdown test
     // and v_{j+1} = w * (1/h_{j+1,j}).  w and the next basis vector stay in
-    // registers between passes; partA/partB hold 2P partials each; cnt[0 ..
+    // registers between passes; partA holds 4P partials, partB 2P; cnt[0 ..
     // j + 2) are the arrival counters of the partial generations, zero on entry
-    // (column_counter_offset).  Same arithmetic as dot2 + mgs + normalize.
+    // (column_counter_offset).  Strict build: the same arithmetic as dot2 + mgs
+    // + normalize.  FMA build: two basis vectors a pass (MGS to rounding); the
+    // columns of one basis run in order, and partA[3G, 4G) (G <= P its grid)
+    // carries the partials of <v_{j+1}, v_j> from column j to column j + 1.
     // Returns cudaErrorNotSupported when the ctas cannot cover the P chunks
     // (caller falls back).
     // fp32: the basis V is binary32 and the Gram-Schmidt arithmetic binary32 (w rounded on load);

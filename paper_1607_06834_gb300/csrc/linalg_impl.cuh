@@ -807,35 +807,92 @@ __global__ void __launch_bounds__(RT, 2) cgs2_column_kernel(const double *__rest
     }
 }
 
-// ---- binary64 Arnoldi column, FMA build: the entries split evenly --------------
+// ---- binary64 Arnoldi column, FMA build: even split, two basis vectors a pass ----
 // The strict build's pairwise tree fixes 2048-entry chunks, and 512 of them
-// (512^2) do not divide over 152 SMs: some SMs hold 4, the others 3, and the
-// FP64 phase of every pass runs at the pace of the 4-chunk SMs.  The FMA build
-// is free in its summation order, so this variant gives CTA b the contiguous
-// range [b L, (b + 1) L) of L = ceil(n / G) entries (at most kEvenPerThread per
-// thread, strided by the CTA width so that loads stay coalesced) and one
-// partial per CTA; the modified Gram-Schmidt passes, the waits, the breakdown
-// test and the normalisation are those of arnoldi_column_kernel.
+// (512^2) do not divide over 152 SMs: some SMs would hold 4, the others 3.
+// The FMA build is free in its summation order, so this kernel gives CTA b the
+// contiguous range [b L, (b + 1) L) of L = ceil(n / G) entries (at most
+// kEvenPerThread per thread, strided by the CTA width so that loads stay
+// coalesced) and one partial per CTA and value.
+//
+// Orthogonalisation (Sec. 2.3.3, Arnoldi; the modified Gram-Schmidt
+// projections taken two basis vectors at a time).  For the pair (a, b) =
+// (v_{2p}, v_{2p+1}) and the current w, one grid-wide reduction gives
+// alpha = <a, w> and beta = <b, w>; then h_{2p} = alpha and
+// h_{2p+1} = beta - g alpha with g = <b, a>, and w -= h_{2p} a + h_{2p+1} b.
+// This is exactly the product (I - b b^T)(I - a a^T) w of the two MGS
+// projections, for any a and b: the term g alpha is what the second
+// projection sees of the first.  g is reduced once, when b is formed (its
+// partials at the end of the column that made b, its sum in the next
+// column's first reduction), and kept in StepState::gram.  So a pair costs
+// the same 2 FMAs per entry and vector as two MGS passes but one grid-wide
+// wait instead of two; the results agree with one-vector MGS to rounding (the
+// two differ only in where the dot product of b is rounded).
 //
 // One CTA of kEvenThreads threads per SM (the register file holds 512 threads
-// of this kernel): one set of reductions and one arrival per SM and pass, and
-// every reduction spread over four warps, one per SM sub-partition.  On this
-// part a warp-wide FP64 instruction occupies a sub-partition's FP64 unit for
-// many cycles whatever its active lanes, so a reduction's latency is the
-// number of dependent FP64 instructions on the busiest sub-partition: a CTA
-// sum of 512 values by one warp takes 20, by four warps 8; a grid sum of 152
-// partials by one warp 10, by four warps 8.  The basis vector of the pass
-// after next is loaded after the arrival, so the release of the arrival does
-// not wait for those loads.
+// of this kernel): one set of reductions and one arrival per SM and pass,
+// each reduction spread over quads of four warps, one warp per SM
+// sub-partition (a warp-wide FP64 instruction occupies a sub-partition's FP64
+// unit for many cycles whatever its active lanes, so a reduction's latency
+// is its dependent FP64 instructions on the busiest sub-partition).  The
+// pair after next is staged into shared memory by asynchronous copies while
+// the current pair is in registers; each thread copies and later reads only
+// its own slots, so the staging needs no CTA barrier.
 constexpr int kEvenThreads = 512;
 constexpr int kEvenPerThread = 16;    // 8192 entries per CTA at most (E <= 16)
 constexpr int kEvenMaxGrid = 256;     // grid sums: 4 warps, 2 partials a lane
+
+template <int E>
+constexpr size_t pair_stage_bytes() { return 2 * (size_t)E * kEvenThreads * sizeof(double); }
 
 // named barrier ID of NT threads (immediate operands)
 template <int ID, int NT>
 __device__ __forceinline__ void bar_named()
 {
     asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NT) : "memory");
+}
+
+// bulk copies global -> shared completing on an mbarrier (one phase a stage)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bytes (a multiple of 16) from global src to shared dst, both 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// the stage's reads of the buffer (generic proxy) before the bulk copy that overwrites it
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// bounded wait of every thread for the phase of the stage buffer; false after
+// kStageSpins polls (the caller then gives up together, see pair_stage_wait)
+constexpr long long kStageSpins = 1LL << 20;
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+{
+    for (long long s = 0; s < kStageSpins; ++s)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // the first kmax terms (kmax uniform over the CTA: the slots no thread of the
@@ -860,156 +917,234 @@ __device__ __forceinline__ void even_load(double (&x)[E], const double *__restri
         if (k < kmax) x[k] = k < kv ? base[k * kEvenThreads] : 0.0;
 }
 
-// The sum of s[0 .. 512) by the four warps of quad q (warps 4q .. 4q + 3,
-// named barrier 1 + q): warp k adds s[128 k .. 128 k + 128), four consecutive
-// values a lane, then the lane butterfly; the quad's first thread adds the
-// four warp sums.  The result is valid in thread 128 q; sh4 holds 8 values.
-template <int q>
-__device__ __forceinline__ double quad_cta_sum(const double *s, double *sh4)
+// Stage the CTA's ranges of a (and b, if not null), cnt entries each, into
+// sa (sb) by bulk copies completing on bar; by one thread, after the CTA's
+// reads of the previous contents (a barrier) and the proxy fence.  The slots
+// past cnt keep the zeros written at the start.
+__device__ __forceinline__ void pair_stage_issue(double *sa, double *sb, const double *a, const double *b, size_t cnt,
+                                                 unsigned long long *bar)
 {
-    const int k = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
-    const double *v = s + k * 128 + lane * 4;
-    const double a = lane_tree((v[0] + v[1]) + (v[2] + v[3]));
-    if (lane == 0) sh4[4 * q + k] = a;
-    bar_named<1 + q, 128>();
-    double r = 0.0;
-    if ((threadIdx.x & 127) == 0) r = (sh4[4 * q] + sh4[4 * q + 1]) + (sh4[4 * q + 2] + sh4[4 * q + 3]);
-    return r;
+    const unsigned bytes = (unsigned)(cnt * sizeof(double));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, b ? 2 * bytes : bytes);
+    if (bytes) {
+        bulk_g2s(sa, a, bytes, bar);
+        if (b) bulk_g2s(sb, b, bytes, bar);
+    }
 }
 
-// The sum of the G CTA partials p[0 .. G) (G <= kEvenMaxGrid) by quad q: warp
-// k adds the k-th quarter (two partials a lane, then the butterfly), the
-// quad's first thread the four quarter sums.  Every CTA forms the same sum in
-// the same order.  Valid in thread 128 q.
-template <int q>
-__device__ __forceinline__ double quad_grid_sum(const double *p, int G, double *sh4)
+template <int E>
+__device__ __forceinline__ void pair_unstage(double (&x)[E], const double *s, int kmax)
 {
-    const int k = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
-    const int Q = (G + 3) >> 2;
-    const int b0 = k * Q + lane, e = min(G, (k + 1) * Q);
-    const double x0 = b0 < e ? p[b0] : 0.0;
-    const double x1 = b0 + 32 < e ? p[b0 + 32] : 0.0;
-    const double a = lane_tree(x0 + x1);
-    if (lane == 0) sh4[4 * q + k] = a;
-    bar_named<1 + q, 128>();
-    double r = 0.0;
-    if ((threadIdx.x & 127) == 0) r = (sh4[4 * q] + sh4[4 * q + 1]) + (sh4[4 * q + 2] + sh4[4 * q + 3]);
-    return r;
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+        if (k < kmax) x[k] = s[k * kEvenThreads + threadIdx.x];
+}
+
+// CTA sums of the nsum arrays s + q kEvenThreads by quads q < nsum (warps
+// 4q .. 4q + 3): warp k of a quad adds 128 consecutive values, four a lane,
+// then the lane butterfly, into sh4[4q + k]; then a barrier of the quads.
+// quad_total gives a sum from its four warp sums.
+template <int nsum>
+__device__ __forceinline__ void quads_cta(const double *s, double *sh4)
+{
+    const int q = threadIdx.x >> 7;
+    if (q < nsum) {
+        const int k = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+        const double *v = s + q * kEvenThreads + k * 128 + lane * 4;
+        const double a = lane_tree((v[0] + v[1]) + (v[2] + v[3]));
+        if (lane == 0) sh4[4 * q + k] = a;
+        bar_named<1, 128 * nsum>();
+    }
+}
+
+__device__ __forceinline__ double quad_total(const double *sh4, int q)
+{
+    return (sh4[4 * q] + sh4[4 * q + 1]) + (sh4[4 * q + 2] + sh4[4 * q + 3]);
 }
 
 // Wait (thread 0, bounded) until generation counter *cnt reaches G, then the
-// grid sums of the nsum (1 or 2) partial arrays p + q G by quads q < nsum;
-// every thread finds them in sh[0 .. nsum).  False (status set) on timeout.
+// grid sums of the nsum partial arrays p + q G (G <= kEvenMaxGrid) by quads
+// q < nsum: warp k of a quad adds the k-th quarter (two partials a lane, then
+// the butterfly) into sh4[4q + k].  Every CTA forms the same sums in the same
+// order.  After it, thread 0 reads the sums with quad_total.  False (status
+// set) on timeout, in every thread of the quads (the others learn it from
+// the caller's barrier).
 template <int nsum>
-__device__ __forceinline__ bool even_wait_sums(const unsigned *cnt, unsigned G, int *status, const double *p,
-                                               double *sh, double *sh4)
+__device__ __forceinline__ bool pair_wait(const unsigned *cnt, unsigned G, int *status, const double *p, double *sh4,
+                                          int *ok)
 {
-    __shared__ int ok;
     const int q = threadIdx.x >> 7;
     if (q < nsum) {
         if (threadIdx.x == 0) {
-            ok = 1;
+            int good = 1;
             long long spins = 0;
             while (ld_acquire_gpu(cnt) < G) {
                 if (++spins > kBarrierSpins) {
                     atomicOr(status, kStatusTimeout);
-                    ok = 0;
+                    good = 0;
                     break;
                 }
                 __nanosleep(32);
             }
+            *ok = good;
         }
-        bar_named<3, 128 * nsum>();
-        if (ok) {
-            const double s = q == 0 ? quad_grid_sum<0>(p, (int)G, sh4) : quad_grid_sum<1>(p + G, (int)G, sh4);
-            if ((threadIdx.x & 127) == 0) sh[q] = s;
-        }
+        bar_named<2, 128 * nsum>();
+        if (!*ok) return false;
+        const int k = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+        const int Q = ((int)G + 3) >> 2;
+        const int b0 = k * Q + lane, e = min((int)G, (k + 1) * Q);
+        const double *pq = p + (size_t)q * G;
+        const double x0 = b0 < e ? pq[b0] : 0.0;
+        const double x1 = b0 + 32 < e ? pq[b0 + 32] : 0.0;
+        const double a = lane_tree(x0 + x1);
+        if (lane == 0) sh4[4 * q + k] = a;
+        bar_named<1, 128 * nsum>();
     }
-    __syncthreads();
-    return ok != 0;
+    return true;
 }
-
 template <int E>
 __global__ void __launch_bounds__(kEvenThreads, 1)
-    arnoldi_even_kernel(const double *__restrict__ w, double *__restrict__ V, size_t ldv, size_t n, int j, int next,
+    arnoldi_pair_kernel(const double *__restrict__ w, double *__restrict__ V, size_t ldv, size_t n, int j, int next,
                         size_t L, double *partA, double *partB, unsigned *cnt, StepState *st, double brk_tol)
 {
     constexpr int T = kEvenThreads;
+    extern __shared__ __align__(16) double stage_buf[];   // 2 E T: the staged pair
+    double *sa = stage_buf, *sb = stage_buf + E * T;
+    __shared__ double sred[4 * T];
+    __shared__ double sh4[16];
     __shared__ double sh[2];
-    __shared__ double sh4[8];
-    __shared__ double sred[2 * T];
-    __shared__ int act;
-    if (threadIdx.x == 0) act = st->active;
+    __shared__ double sgram[kMaxKrylov];
+    __shared__ __align__(8) unsigned long long stage_bar;   // one phase per staged pair
+    __shared__ int act, ok, brk;
+    if (threadIdx.x == 0) {
+        act = st->active;
+        mbar_init(&stage_bar);
+    }
+    if (threadIdx.x + 1 < (unsigned)j) sgram[threadIdx.x] = st->gram[threadIdx.x];   // <v_{i+1}, v_i>, i < j - 1
     __syncthreads();
     if (act == 0) return;
     const unsigned G = gridDim.x;
-    const int quad = threadIdx.x >> 7;
     const size_t lo = (size_t)blockIdx.x * L;
     const size_t hi = lo + L < n ? lo + L : n;
     const size_t my = lo + threadIdx.x;   // this thread's first entry
     const int kv = my < hi ? (int)((hi - my + T - 1) / T) : 0;
     const int kmax = (int)((hi - lo + T - 1) / T);   // uniform over the CTA
-    double wv[E], vn[E];
+    const int P = (j + 2) >> 1;   // passes: pairs (v_{2p}, v_{2p+1}); the last is v_j alone when j is even
+    double *gpart = partA + 3 * (size_t)G;   // partials of <v_{j+1}, v_j> for the next column
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+        if (k >= kv && k < kmax) sa[k * T + threadIdx.x] = sb[k * T + threadIdx.x] = 0.0;
+    double wv[E], va[E], vb[E];
     even_load(wv, w + my, kv, kmax);
-    even_load(vn, V + my, kv, kmax);   // v_0
-    // pass 0 partials: <v_0, w> by quad 0 and <w, w> by quad 1
-    sred[threadIdx.x] = even_dot(vn, wv, kmax);
-    sred[T + threadIdx.x] = even_dot(wv, wv, kmax);
+    even_load(va, V + my, kv, kmax);   // v_0
+    if (j >= 1) even_load(vb, V + ldv + my, kv, kmax);   // v_1
+    if (P >= 2 && threadIdx.x == 0)   // pair 1 (the zeros above lie past its bytes)
+        pair_stage_issue(sa, sb, V + 2 * ldv + lo, j >= 3 ? V + 3 * ldv + lo : nullptr, hi - lo, &stage_bar);
+    // first partials: <v_0, w>, <v_1, w> and <w, w>
+    sred[threadIdx.x] = even_dot(va, wv, kmax);
+    sred[T + threadIdx.x] = j >= 1 ? even_dot(vb, wv, kmax) : 0.0;
+    sred[2 * T + threadIdx.x] = even_dot(wv, wv, kmax);
     __syncthreads();
-    if (quad < 2) {
-        const double s = quad == 0 ? quad_cta_sum<0>(sred, sh4) : quad_cta_sum<1>(sred + T, sh4);
-        if ((threadIdx.x & 127) == 0) partA[quad * G + blockIdx.x] = s;
+    quads_cta<3>(sred, sh4);
+    if (threadIdx.x == 0) {
+        partA[blockIdx.x] = quad_total(sh4, 0);
+        partA[G + blockIdx.x] = quad_total(sh4, 1);
+        partA[2 * G + blockIdx.x] = quad_total(sh4, 2);
+        red_add_release_gpu(cnt, 1u);   // the same thread stored the partials
     }
-    __syncthreads();   // both partials stored before the arrival
-    if (threadIdx.x == 0) red_add_release_gpu(cnt, 1u);
-    double vq[E];   // v_{i+1} during pass i
-    if (j >= 1) even_load(vq, V + ldv + my, kv, kmax);
     double *pin = partA, *pout = partB;
-    double wnorm0 = 0.0;   // thread 0 only
-    for (int i = 0; i <= j; ++i) {
-        if (!(i == 0 ? even_wait_sums<2>(cnt, G, &st->status, pin, sh, sh4)
-                     : even_wait_sums<1>(cnt + i, G, &st->status, pin, sh, sh4)))
-            return;
-        const double h = sh[0];
-        if (threadIdx.x == 0) {
-            if (i == 0) wnorm0 = sqrt(sh[1]);
+    double wnorm0 = 0.0, gfresh = 0.0;   // thread 0 only
+    for (int p = 0; p < P; ++p) {
+        const bool pair = 2 * p + 1 <= j;
+        bool good;
+        if (p == 0)   // with j >= 1 also <v_j, v_{j-1}> from the previous column's partials
+            good = j >= 1 ? pair_wait<4>(cnt, G, &st->status, pin, sh4, &ok)
+                          : pair_wait<3>(cnt, G, &st->status, pin, sh4, &ok);
+        else
+            good = pair ? pair_wait<2>(cnt + p, G, &st->status, pin, sh4, &ok)
+                        : pair_wait<1>(cnt + p, G, &st->status, pin, sh4, &ok);
+        if (threadIdx.x == 0 && good) {
+            const double alpha = quad_total(sh4, 0);
+            if (p == 0) {
+                wnorm0 = sqrt(quad_total(sh4, 2));
+                if (j >= 1) gfresh = quad_total(sh4, 3);
+            }
+            double h1 = 0.0;
+            if (pair) {
+                const double g = 2 * p + 1 == j ? gfresh : sgram[2 * p];
+                h1 = fma(-g, alpha, quad_total(sh4, 1));
+            }
+            sh[0] = alpha;
+            sh[1] = h1;
             if (blockIdx.x == 0) {
-                st->H[i * kMaxKrylov + j] = h;
-                if (i == 0) st->wnorm0 = wnorm0;
+                st->H[2 * p * kMaxKrylov + j] = alpha;
+                if (pair) st->H[(2 * p + 1) * kMaxKrylov + j] = h1;
+                if (p == 0) {
+                    st->wnorm0 = wnorm0;
+                    if (j >= 1) st->gram[j - 1] = gfresh;
+                }
             }
         }
-#pragma unroll
-        for (int k = 0; k < E; ++k)
-            if (k < kmax) wv[k] = wv[k] - h * vn[k];
-        const bool more = i < j;
-        if (more) {
-#pragma unroll
-            for (int k = 0; k < E; ++k) vn[k] = vq[k];
-        }
-        sred[threadIdx.x] = more ? even_dot(vn, wv, kmax) : even_dot(wv, wv, kmax);
         __syncthreads();
-        if (quad == 0) {
-            const double s = quad_cta_sum<0>(sred, sh4);
+        if (!ok) {
+            if (p + 1 < P) mbar_wait_bounded(&stage_bar, p & 1);   // the staged pair in flight
+            return;
+        }
+        const double h0 = sh[0], h1 = sh[1];
+        if (pair) {
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+                if (k < kmax) wv[k] = wv[k] - h0 * va[k] - h1 * vb[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+                if (k < kmax) wv[k] = wv[k] - h0 * va[k];
+        }
+        if (p + 1 < P) {
+            const bool npair = 2 * p + 3 <= j;
+            const bool late = !mbar_wait_bounded(&stage_bar, p & 1);   // pair p + 1 staged
+            pair_unstage(va, sa, kmax);
+            if (npair) pair_unstage(vb, sb, kmax);
+            sred[threadIdx.x] = even_dot(va, wv, kmax);
+            if (npair) sred[T + threadIdx.x] = even_dot(vb, wv, kmax);
+            if (__syncthreads_or(late)) {   // every thread gives up together
+                if (threadIdx.x == 0) atomicOr(&st->status, kStatusTimeout);
+                mbar_wait_bounded(&stage_bar, p & 1);
+                return;
+            }
+            if (p + 2 < P && threadIdx.x == 0)   // the buffer is read: stage pair p + 2
+                pair_stage_issue(sa, sb, V + (size_t)(2 * p + 4) * ldv + lo,
+                                 2 * p + 5 <= j ? V + (size_t)(2 * p + 5) * ldv + lo : nullptr, hi - lo,
+                                 &stage_bar);
+            if (npair) quads_cta<2>(sred, sh4);
+            else quads_cta<1>(sred, sh4);
             if (threadIdx.x == 0) {
-                pout[blockIdx.x] = s;   // the same thread releases it
-                red_add_release_gpu(cnt + i + 1, 1u);
+                pout[blockIdx.x] = quad_total(sh4, 0);
+                if (npair) pout[G + blockIdx.x] = quad_total(sh4, 1);
+                red_add_release_gpu(cnt + p + 1, 1u);
+            }
+        } else {
+            sred[threadIdx.x] = even_dot(wv, wv, kmax);
+            __syncthreads();
+            quads_cta<1>(sred, sh4);
+            if (threadIdx.x == 0) {
+                pout[blockIdx.x] = quad_total(sh4, 0);
+                red_add_release_gpu(cnt + p + 1, 1u);
             }
         }
-        if (more && i + 2 <= j) even_load(vq, V + (size_t)(i + 2) * ldv + my, kv, kmax);   // lands during the wait
         double *t = pin;
         pin = pout;
         pout = t;
     }
     if (!next) return;
-    if (!even_wait_sums<1>(cnt + j + 1, G, &st->status, pin, sh, sh4)) return;
+    const bool good = pair_wait<1>(cnt + P, G, &st->status, pin, sh4, &ok);
     // the norm, the breakdown test and the reciprocal by thread 0 (FP64
     // square roots and divisions in every warp would cost each sub-partition)
-    __shared__ double rs;
-    __shared__ int brk;
-    if (threadIdx.x == 0) {
-        const double hn = sqrt(sh[0]);
+    if (threadIdx.x == 0 && good) {
+        const double hn = sqrt(quad_total(sh4, 0));
         brk = !(hn > brk_tol * wnorm0);
-        rs = 1.0 / hn;
+        sh[0] = 1.0 / hn;
         if (blockIdx.x == 0) {
             if (brk) {
                 st->active = 0;
@@ -1020,12 +1155,23 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
         }
     }
     __syncthreads();
-    if (brk) return;
-    const double r = rs;
+    if (!ok || brk) return;
+    const double r = sh[0];
+    // v_{j+1}, and the partials of <v_{j+1}, v_j> (v_j: the last vector used)
+    const bool last_pair = (j & 1) != 0;
     double *vout = V + (size_t)(j + 1) * ldv + my;
+    double g = 0.0;
 #pragma unroll
     for (int k = 0; k < E; ++k)
-        if (k < kv) vout[k * T] = wv[k] * r;
+        if (k < kmax) {
+            const double x = wv[k] * r;
+            if (k < kv) vout[k * T] = x;
+            g = x * (last_pair ? vb[k] : va[k]) + g;
+        }
+    sred[threadIdx.x] = g;
+    __syncthreads();
+    quads_cta<1>(sred, sh4);
+    if (threadIdx.x == 0) gpart[blockIdx.x] = quad_total(sh4, 0);   // read by the next launch
 }
 #endif  // ROK_LINALG_FAST
 
@@ -1089,10 +1235,16 @@ static int arnoldi_column_ctas(int sms)
     int pc = 0, pe = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, cgs2_column_kernel, RT, 0) != cudaSuccess) return 0;
     if (pc < p32) p32 = pc;
-    // the binary64 column runs as arnoldi_even_kernel, kEvenThreads threads a CTA:
-    // its grid is ctas RT / kEvenThreads, which must be co-resident too
-    for (auto kern : {arnoldi_even_kernel<8>, arnoldi_even_kernel<14>, arnoldi_even_kernel<16>}) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pe, kern, kEvenThreads, 0) != cudaSuccess) return 0;
+    // the binary64 column runs as arnoldi_pair_kernel, kEvenThreads threads a CTA
+    // and a dynamic staging buffer: its grid is ctas RT / kEvenThreads, which must
+    // be co-resident too
+    const void *pk[3] = {(const void *)arnoldi_pair_kernel<8>, (const void *)arnoldi_pair_kernel<14>,
+                         (const void *)arnoldi_pair_kernel<16>};
+    const size_t pb[3] = {pair_stage_bytes<8>(), pair_stage_bytes<14>(), pair_stage_bytes<16>()};
+    for (int i = 0; i < 3; ++i) {
+        if (cudaFuncSetAttribute(pk[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb[i]) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pe, pk[i], kEvenThreads, pb[i]) != cudaSuccess) return 0;
         if (pe * kEvenThreads < p64 * RT) p64 = pe * kEvenThreads / RT;
     }
 #endif
@@ -1130,12 +1282,23 @@ static cudaError_t arnoldi_column(const double *w, void *V, int fp32, size_t ldv
     size_t L = (n + Ge - 1) / Ge;
     L += L & 1;
     if (Ge < 1 || L > (size_t)kEvenThreads * kEvenPerThread || Ge > kEvenMaxGrid) return cudaErrorNotSupported;
+    // the bulk copies of the CTA ranges want 16-byte aligned starts and lengths
+    if ((n & 1) || (ldv & 1) || ((uintptr_t)Vd & 15)) return cudaErrorNotSupported;
     void *eargs[] = {&w, &Vd, &ldv, &n, &j, &next, &L, &partA, &partB, &cnt, &st, &tol};
     // entries per thread: the smallest instantiation that holds L / kEvenThreads
-    const void *kern = L <= (size_t)kEvenThreads * 8 ? (const void *)arnoldi_even_kernel<8>
-                       : L <= (size_t)kEvenThreads * 14 ? (const void *)arnoldi_even_kernel<14>
-                                                        : (const void *)arnoldi_even_kernel<16>;
-    return cudaLaunchCooperativeKernel(kern, dim3(Ge), dim3(kEvenThreads), eargs, 0, s);
+    const void *kern;
+    size_t smem;
+    if (L <= (size_t)kEvenThreads * 8) {
+        kern = (const void *)arnoldi_pair_kernel<8>;
+        smem = pair_stage_bytes<8>();
+    } else if (L <= (size_t)kEvenThreads * 14) {
+        kern = (const void *)arnoldi_pair_kernel<14>;
+        smem = pair_stage_bytes<14>();
+    } else {
+        kern = (const void *)arnoldi_pair_kernel<16>;
+        smem = pair_stage_bytes<16>();
+    }
+    return cudaLaunchCooperativeKernel(kern, dim3(Ge), dim3(kEvenThreads), eargs, smem, s);
 #else
     void *args[] = {&w, &Vd, &ldv, &n, &j, &next, &P, &partA, &partB, &cnt, &st, &tol};
     return cudaLaunchCooperativeKernel((const void *)arnoldi_column_kernel<double>, dim3(G), dim3(RT), args, 0, s);

@@ -424,8 +424,9 @@ def test_persistent_and_pass_by_pass_gram_schmidt_agree(rok, mode):
     # sums in the same order, so the same bits, and the oracle's step.  FMA
     # build: the cooperative binary64 column splits the entries evenly over its
     # CTAs (another summation order than the 2048-entry chunks of the
-    # pass-by-pass kernels), so the two agree to the rounding the FD quotients
-    # amplify (the oracle's one-ulp floor of this step)
+    # pass-by-pass kernels) and projects two basis vectors a pass (the pair's
+    # Gram correction makes it MGS to rounding), so the two agree to the
+    # rounding the FD quotients amplify (the oracle's one-ulp floor of this step)
     prob, y0 = W.taylor_green(48, reynolds=300.0)
     y0 = np.ascontiguousarray(y0 + 0.01 * W.random_smooth_state(prob, seed=7))
     h = I.dt_from_cfl(prob, y0, 4.0)
