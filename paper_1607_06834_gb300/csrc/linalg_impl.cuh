@@ -1003,6 +1003,74 @@ __device__ __forceinline__ bool pair_wait(const unsigned *cnt, unsigned G, int *
     }
     return true;
 }
+// Two sums in one warp butterfly: lanes < 16 keep a and send b to lane ^ 16,
+// lanes >= 16 the reverse, so after one exchange the low half carries a and
+// the high half b, each summed over two lanes; four more levels finish both.
+// Lane 0 ends with the warp sum of a, lane 16 with that of b (one FP64
+// instruction a level for both sums).
+__device__ __forceinline__ double lane_tree2(double a, double b)
+{
+    const bool low = (threadIdx.x & 16) == 0;
+    double v = (low ? a : b) + __shfl_xor_sync(0xffffffffu, low ? b : a, 16);
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The CTA sums of s[0 .. T) and s[T .. 2T) together by quad 0: warp k adds
+// the values of threads 128 k .. 128 k + 127 of both arrays (four a lane,
+// then lane_tree2) into sh4[k] and sh4[4 + k]; then the quad's barrier.
+__device__ __forceinline__ void quad0_cta2(const double *s, double *sh4)
+{
+    if (threadIdx.x < 128) {
+        const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const double *u = s + k * 128 + lane * 4, *v = u + kEvenThreads;
+        const double x = lane_tree2((u[0] + u[1]) + (u[2] + u[3]), (v[0] + v[1]) + (v[2] + v[3]));
+        if (lane == 0) sh4[k] = x;
+        if (lane == 16) sh4[4 + k] = x;
+        bar_named<1, 128>();
+    }
+}
+
+// pair_wait for the two partial arrays p and p + G, both by quad 0 (warp k:
+// the k-th quarter of each, two partials a lane, then lane_tree2).
+__device__ __forceinline__ bool pair_wait2(const unsigned *cnt, unsigned G, int *status, const double *p,
+                                           double *sh4, int *ok)
+{
+    if (threadIdx.x < 128) {
+        if (threadIdx.x == 0) {
+            int good = 1;
+            long long spins = 0;
+            while (ld_acquire_gpu(cnt) < G) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(status, kStatusTimeout);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            *ok = good;
+        }
+        bar_named<2, 128>();
+        if (!*ok) return false;
+        const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int Q = ((int)G + 3) >> 2;
+        const int b0 = k * Q + lane, e = min((int)G, (k + 1) * Q);
+        const double *pb = p + G;
+        const double a = (b0 < e ? p[b0] : 0.0) + (b0 + 32 < e ? p[b0 + 32] : 0.0);
+        const double b = (b0 < e ? pb[b0] : 0.0) + (b0 + 32 < e ? pb[b0 + 32] : 0.0);
+        const double x = lane_tree2(a, b);
+        if (lane == 0) sh4[k] = x;
+        if (lane == 16) sh4[4 + k] = x;
+        bar_named<1, 128>();
+    }
+    return true;
+}
+
+// In warp 0, lane q (q < 4) forms total q from sh4[4q .. 4q + 4): all the
+// totals of a pass in one set of three FP64 instructions.
+__device__ __forceinline__ double warp0_totals(const double *sh4) { return quad_total(sh4, threadIdx.x & 3); }
+
 template <int E>
 __global__ void __launch_bounds__(kEvenThreads, 1)
     arnoldi_pair_kernel(const double *__restrict__ w, double *__restrict__ V, size_t ldv, size_t n, int j, int next,
@@ -1047,14 +1115,18 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
     sred[2 * T + threadIdx.x] = even_dot(wv, wv, kmax);
     __syncthreads();
     quads_cta<3>(sred, sh4);
-    if (threadIdx.x == 0) {
-        partA[blockIdx.x] = quad_total(sh4, 0);
-        partA[G + blockIdx.x] = quad_total(sh4, 1);
-        partA[2 * G + blockIdx.x] = quad_total(sh4, 2);
-        red_add_release_gpu(cnt, 1u);   // the same thread stored the partials
+    if (threadIdx.x < 32) {
+        const double t = warp0_totals(sh4);
+        const double t1 = __shfl_sync(0xffffffffu, t, 1), t2 = __shfl_sync(0xffffffffu, t, 2);
+        if (threadIdx.x == 0) {
+            partA[blockIdx.x] = t;
+            partA[G + blockIdx.x] = t1;
+            partA[2 * G + blockIdx.x] = t2;
+            red_add_release_gpu(cnt, 1u);   // the same thread stored the partials
+        }
     }
     double *pin = partA, *pout = partB;
-    double wnorm0 = 0.0, gfresh = 0.0;   // thread 0 only
+    double wnorm0 = 0.0, gfresh = 0.0;   // warp 0 only (wnorm0: lane 0)
     for (int p = 0; p < P; ++p) {
         const bool pair = 2 * p + 1 <= j;
         bool good;
@@ -1062,22 +1134,26 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
             good = j >= 1 ? pair_wait<4>(cnt, G, &st->status, pin, sh4, &ok)
                           : pair_wait<3>(cnt, G, &st->status, pin, sh4, &ok);
         else
-            good = pair ? pair_wait<2>(cnt + p, G, &st->status, pin, sh4, &ok)
+            good = pair ? pair_wait2(cnt + p, G, &st->status, pin, sh4, &ok)
                         : pair_wait<1>(cnt + p, G, &st->status, pin, sh4, &ok);
-        if (threadIdx.x == 0 && good) {
-            const double alpha = quad_total(sh4, 0);
+        if (threadIdx.x < 32 && good) {   // warp 0: the totals in lanes 0 .. 3 at once
+            const double t = warp0_totals(sh4);
+            const double alpha = __shfl_sync(0xffffffffu, t, 0), beta = __shfl_sync(0xffffffffu, t, 1);
             if (p == 0) {
-                wnorm0 = sqrt(quad_total(sh4, 2));
-                if (j >= 1) gfresh = quad_total(sh4, 3);
+                const double ww = __shfl_sync(0xffffffffu, t, 2);
+                gfresh = __shfl_sync(0xffffffffu, t, 3);
+                if (threadIdx.x == 0) wnorm0 = sqrt(ww);
             }
             double h1 = 0.0;
             if (pair) {
                 const double g = 2 * p + 1 == j ? gfresh : sgram[2 * p];
-                h1 = fma(-g, alpha, quad_total(sh4, 1));
+                h1 = fma(-g, alpha, beta);
             }
-            sh[0] = alpha;
-            sh[1] = h1;
-            if (blockIdx.x == 0) {
+            if (threadIdx.x == 0) {
+                sh[0] = alpha;
+                sh[1] = h1;
+            }
+            if (threadIdx.x == 0 && blockIdx.x == 0) {
                 st->H[2 * p * kMaxKrylov + j] = alpha;
                 if (pair) st->H[(2 * p + 1) * kMaxKrylov + j] = h1;
                 if (p == 0) {
@@ -1117,12 +1193,16 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
                 pair_stage_issue(sa, sb, V + (size_t)(2 * p + 4) * ldv + lo,
                                  2 * p + 5 <= j ? V + (size_t)(2 * p + 5) * ldv + lo : nullptr, hi - lo,
                                  &stage_bar);
-            if (npair) quads_cta<2>(sred, sh4);
+            if (npair) quad0_cta2(sred, sh4);
             else quads_cta<1>(sred, sh4);
-            if (threadIdx.x == 0) {
-                pout[blockIdx.x] = quad_total(sh4, 0);
-                if (npair) pout[G + blockIdx.x] = quad_total(sh4, 1);
-                red_add_release_gpu(cnt + p + 1, 1u);
+            if (threadIdx.x < 32) {
+                const double t = warp0_totals(sh4);
+                const double tb = __shfl_sync(0xffffffffu, t, 1);
+                if (threadIdx.x == 0) {
+                    pout[blockIdx.x] = t;
+                    if (npair) pout[G + blockIdx.x] = tb;
+                    red_add_release_gpu(cnt + p + 1, 1u);
+                }
             }
         } else {
             sred[threadIdx.x] = even_dot(wv, wv, kmax);
