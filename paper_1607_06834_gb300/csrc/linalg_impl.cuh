@@ -832,12 +832,12 @@ __global__ void __launch_bounds__(RT, 2) cgs2_column_kernel(const double *__rest
 // One CTA of kEvenThreads threads per SM (the register file holds 512 threads
 // of this kernel): one set of reductions and one arrival per SM and pass,
 // each reduction spread over quads of four warps, one warp per SM
-// sub-partition (a warp-wide FP64 instruction occupies a sub-partition's FP64
-// unit for many cycles whatever its active lanes, so a reduction's latency
-// is its dependent FP64 instructions on the busiest sub-partition).  The
-// pair after next is staged into shared memory by asynchronous copies while
-// the current pair is in registers; each thread copies and later reads only
-// its own slots, so the staging needs no CTA barrier.
+// sub-partition (a warp-wide FP64 instruction keeps a sub-partition's FP64
+// unit busy for 64 cycles, so a reduction's latency is its dependent FP64
+// instructions on the busiest sub-partition).  The next pair is staged into
+// shared memory by two bulk copies (the CTA's contiguous ranges, completing
+// on an mbarrier) while the current pair is in registers; the copy is issued
+// after a CTA barrier has ordered every thread's reads of the buffer.
 constexpr int kEvenThreads = 512;
 constexpr int kEvenPerThread = 16;    // 8192 entries per CTA at most (E <= 16)
 constexpr int kEvenMaxGrid = 256;     // grid sums: 4 warps, 2 partials a lane
