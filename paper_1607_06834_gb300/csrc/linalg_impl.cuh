@@ -1253,6 +1253,124 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
     quads_cta<1>(sred, sh4);
     if (threadIdx.x == 0) gpart[blockIdx.x] = quad_total(sh4, 0);   // read by the next launch
 }
+
+// ---- projections <V_i, F>, FMA build: the entries split evenly ------------------
+// The chunked multidot gives the 2048-entry chunks to 512 CTAs, so on 152 SMs
+// some SMs hold 4 chunks and the others 3; the FP64 work (m FMAs per entry)
+// runs at the pace of the 4-chunk SMs.  Here CTA b of G = one per SM owns the
+// contiguous range [b L, (b + 1) L), each thread E slots strided by the CTA
+// width, and the m values of a group are summed across the lanes by recursive
+// halving sized to the group (R = 16, 8 or 4 values: R - 1 + 5 - log2 R
+// additions a lane, not 16 for every group).  The partials keep the layout of
+// the chunked kernel, pout[i P + b], with zeros for G <= b < P, so the stage
+// solve reads them unchanged.
+
+// lane sums of R values at once (R = 16, 8, 4): LV halving levels, then the
+// plain butterfly; lane l ends with the sum of value lane_treeR_value<R>(l)
+template <int R>
+__device__ __forceinline__ double lane_treeR(double (&t)[16], int lane)
+{
+    constexpr int LV = R == 16 ? 4 : R == 8 ? 3 : 2;
+#pragma unroll
+    for (int lev = 0; lev < LV; ++lev) {
+        const int half = (R / 2) >> lev;
+        const bool upper = (lane >> lev) & 1;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const double recv = __shfl_xor_sync(0xffffffffu, upper ? t[k] : t[k + half], 1 << lev);
+            t[k] = upper ? recv + t[k + half] : t[k] + recv;
+        }
+    }
+    double v = t[0];
+#pragma unroll
+    for (int o = 1 << LV; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int R>
+__device__ __forceinline__ int lane_treeR_value(int lane)
+{
+    constexpr int LV = R == 16 ? 4 : R == 8 ? 3 : 2;
+    int v = 0;
+#pragma unroll
+    for (int lev = 0; lev < LV; ++lev)
+        if ((lane >> lev) & 1) v += (R / 2) >> lev;
+    return v;
+}
+
+template <int R>
+__device__ __forceinline__ void multidot_group(double (&t)[16], int g, int m, double (*ws)[kEvenThreads / 32])
+{
+    const int lane = threadIdx.x & 31;
+    const double s = lane_treeR<R>(t, lane);
+    const int q = lane_treeR_value<R>(lane);
+    if (lane < R && g + q < m) ws[g + q][threadIdx.x >> 5] = s;
+}
+
+// four consecutive binary64 values (one 32-byte load; p 32-byte aligned)
+struct Quad {
+    double x, y, z, w;
+};
+__device__ __forceinline__ Quad ld_quad(const double *p)
+{
+    Quad q;
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(q.x), "=d"(q.y), "=d"(q.z), "=d"(q.w) : "l"(p));
+    return q;
+}
+
+template <int E>
+__global__ void __launch_bounds__(kEvenThreads, 1)
+    multidot_even_kernel(const double *__restrict__ F, const double *__restrict__ V, size_t ldv, size_t n, size_t L,
+                         double *__restrict__ pout, int P, const StepState *st)
+{
+    // quads of consecutive entries (32-byte loads): thread t holds quads t + k T, k < E / 4
+    constexpr int T = kEvenThreads, NW = kEvenThreads / 32, E4 = E / 4;
+    static_assert(NW == 16, "the CTA sum below adds 16 warp sums");
+    __shared__ double ws[kMaxKrylov][NW];
+    const int m = st->meff;
+    const size_t lo = (size_t)blockIdx.x * L;
+    const size_t hi = lo + L < n ? lo + L : n;
+    const size_t nq = (hi - lo) / 4;   // quads of this CTA (L, n multiples of 4)
+    const int kv = threadIdx.x < nq ? (int)((nq - threadIdx.x + T - 1) / T) : 0;
+    const double *F4 = F + lo + 4 * (size_t)threadIdx.x;
+    Quad f[E4];
+#pragma unroll
+    for (int k = 0; k < E4; ++k) f[k] = k < kv ? ld_quad(F4 + (size_t)4 * k * T) : Quad{0.0, 0.0, 0.0, 0.0};
+    for (int g = 0; g < m; g += 16) {
+        const int cnt = m - g < 16 ? m - g : 16;   // uniform
+        double t[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            double s = 0.0;
+            if (q < cnt) {
+                const double *v = V + (size_t)(g + q) * ldv + lo + 4 * (size_t)threadIdx.x;
+#pragma unroll
+                for (int k = 0; k < E4; ++k)
+                    if (k < kv) {
+                        const Quad x = ld_quad(v + (size_t)4 * k * T);
+                        s = x.x * f[k].x + s;
+                        s = x.y * f[k].y + s;
+                        s = x.z * f[k].z + s;
+                        s = x.w * f[k].w + s;
+                    }
+            }
+            t[q] = s;
+        }
+        if (cnt > 8) multidot_group<16>(t, g, m, ws);
+        else if (cnt > 4) multidot_group<8>(t, g, m, ws);
+        else multidot_group<4>(t, g, m, ws);
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        const double *w = ws[threadIdx.x];
+        const double s = (((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]))) +
+                         (((w[8] + w[9]) + (w[10] + w[11])) + ((w[12] + w[13]) + (w[14] + w[15])));
+        pout[(size_t)threadIdx.x * P + blockIdx.x] = s;
+    }
+    if (blockIdx.x == 0)   // the chunk slots past the grid
+        for (int i = threadIdx.x; i < m * (P - (int)gridDim.x); i += T)
+            pout[(size_t)(i / (P - (int)gridDim.x)) * P + gridDim.x + i % (P - (int)gridDim.x)] = 0.0;
+}
 #endif  // ROK_LINALG_FAST
 
 // First basis vector: partials of ||(T)F1||^2 ...
@@ -2172,6 +2290,30 @@ static cudaError_t normalize(const double *w, double *v, size_t n, const double 
 static cudaError_t multidot(const double *F, const void *V, int fp32, size_t ldv, size_t n, double *pout, int P,
                             const StepState *st, cudaStream_t s)
 {
+#ifdef ROK_LINALG_FAST
+    if (!fp32) {   // even split, one CTA per SM (the strict build keeps the oracle's chunks)
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                sms = -1;
+        }
+        const int G = sms > 0 && P > sms ? sms : P;
+        size_t L = (n + G - 1) / G;
+        L = (L + 3) & ~(size_t)3;
+        // 32-byte loads of entry quads: lengths multiples of 4, aligned starts
+        if (sms > 0 && L <= (size_t)kEvenThreads * kEvenPerThread && !(n & 3) && !(ldv & 3) &&
+            !((uintptr_t)F & 31) && !((uintptr_t)V & 31)) {
+            const double *Vd = static_cast<const double *>(V);
+            if (L <= (size_t)kEvenThreads * 8)
+                multidot_even_kernel<8><<<G, kEvenThreads, 0, s>>>(F, Vd, ldv, n, L, pout, P, st);
+            else
+                multidot_even_kernel<16><<<G, kEvenThreads, 0, s>>>(F, Vd, ldv, n, L, pout, P, st);
+            return cudaGetLastError();
+        }
+    }
+#endif
     if (fp32) multidot_kernel<float><<<P, RT, 0, s>>>(F, static_cast<const float *>(V), ldv, n, pout, P, st);
     else multidot_kernel<double><<<P, RT, 0, s>>>(F, static_cast<const double *>(V), ldv, n, pout, P, st);
     return cudaGetLastError();
