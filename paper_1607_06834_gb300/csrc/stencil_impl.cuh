@@ -222,9 +222,9 @@ __device__ __forceinline__ void roe_n(const S *L, const S *R, double nx, double 
 //     dropped and the cell balance uses 0.5/dx, 0.5/dy;
 //   * the viscous coefficients carry mu, the grid spacing and the factor 2
 //     (face_coefs);
-//   * rho H = p gamma/(gamma-1) + rho k, and the Roe weights from
-//     1/(sqrt(rho_L) + sqrt(rho_R)) and the reciprocal square roots, the
-//     averaged velocity as q_R - w_L (q_R - q_L);
+//   * rho H = p gamma/(gamma-1) + rho k; the Roe averages from one
+//     reciprocal square root z = 1/sqrt(rho_L rho_R) and one reciprocal
+//     (w_L = 1/(1 + rho_R z)), the averaged velocity as q_R - w_L (q_R - q_L);
 //   * halving and the comparison of non-negative numbers on the integer pipe;
 //   * reciprocals from the hardware estimate and one Newton step.
 
@@ -298,17 +298,20 @@ __device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts
     constexpr int N = 1 + DIR, T = 2 - DIR;
     const S rL = L[0], nL = L[N], tL = L[T], pL = L[3];
     const S rR = R[0], nR = R[N], tR = R[T], pR = R[3];
-    // Roe average; qX = 1/sqrt(rho_X), sX = sqrt(rho_X)
+    // Roe average from one reciprocal square root z = 1/sqrt(rho_L rho_R)
+    // (sX = sqrt(rho_X)): rho~ = rho_L rho_R z = sL sR; a = rho_R z = sR / sL;
+    // the left weight sL / (sL + sR) = 1 / (1 + a); and
+    // H~ = (eL / sL + eR / sR) / (sL + sR) = wl z (eL a + eR)
     const S eL = pL * C.gg + rL * half(nL * nL + tL * tL);   // rho H = E + p
     const S eR = pR * C.gg + rR * half(nR * nR + tR * tR);
-    const S qL = rsqrt(rL), qR = rsqrt(rR);
-    const S sL = rL * qL, sR = rR * qR;
-    const S rt = sL * sR;
-    const S inv = rcp(sL + sR);
+    const S prr = rL * rR;
+    const S z = rsqrt(prr);
+    const S rt = prr * z;
+    const S a = rR * z;
+    const S wl = rcp(a + 1.0);   // the right weight is 1 - wl
     const S drho = rR - rL, dp = pR - pL, dn = nR - nL, dt = tR - tL;
-    const S wl = sL * inv;   // the right weight is 1 - wl
     const S nt = nR - wl * dn, tt = tR - wl * dt;
-    const S Ht = (eL * qL + eR * qR) * inv;
+    const S Ht = (wl * z) * (eL * a + eR);
     const S kt = half(nt * nt + tt * tt);
     const S ct2 = C.gm1 * (Ht - kt);
     const S rc = rsqrt(ct2);
@@ -363,14 +366,15 @@ __device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double
     const S qnL = uL * nx + vL * ny, qnR = uR * nx + vR * ny;
     const S eL = pL * C.gg + rL * half(uL * uL + vL * vL);
     const S eR = pR * C.gg + rR * half(uR * uR + vR * vR);
-    const S qL = rsqrt(rL), qR = rsqrt(rR);
-    const S sL = rL * qL, sR = rR * qR;
-    const S rt = sL * sR;
-    const S inv = rcp(sL + sR);
+    // Roe average from one reciprocal square root, as in roe2
+    const S prr = rL * rR;
+    const S z = rsqrt(prr);
+    const S rt = prr * z;
+    const S a = rR * z;
+    const S wl = rcp(a + 1.0);   // the right weight is 1 - wl
     const S drho = rR - rL, dp = pR - pL, du = uR - uL, dv = vR - vL, dqn = qnR - qnL;
-    const S wl = sL * inv;   // the right weight is 1 - wl
     const S ut = uR - wl * du, vt = vR - wl * dv;
-    const S Ht = (eL * qL + eR * qR) * inv;
+    const S Ht = (wl * z) * (eL * a + eR);
     const S kt = half(ut * ut + vt * vt);
     const S ct2 = C.gm1 * (Ht - kt);
     const S rc = rsqrt(ct2);
