@@ -291,9 +291,12 @@ __device__ __forceinline__ S harten2(S lam, S delta)
 
 // Doubled Roe flux G = 2F through a face of a uniform grid with unit normal
 // e_DIR (DIR 0: x, 1: y): the same flux as roe_x / roe_y, component N the
-// normal and T the tangential momentum.
-template <int DIR, class S>
-__device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts &C, S *G)
+// normal and T the tangential momentum.  With VX the doubled viscous flux
+// (vn, vt, ve: normal momentum, tangential momentum, energy; visc2_terms) is
+// subtracted too, vn and ve inside the dissipation sums where a product
+// becomes a fused multiply-add (one FP64 instruction fewer each).
+template <int DIR, bool VX, class S>
+__device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts &C, S *G, S vn, S vt, S ve)
 {
     constexpr int N = 1 + DIR, T = 2 - DIR;
     const S rL = L[0], nL = L[N], tL = L[T], pL = L[3];
@@ -326,9 +329,9 @@ __device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts
     const S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
     const S sA = A1 + A3, dA = A3 - A1, D0 = sA + A2;
     const S Asdt = As * dt;
-    const S Dn = nt * D0 + ct * dA;
-    const S Dt = tt * D0 + Asdt;
-    const S D3 = Ht * sA + (kt * A2 + ((ct * nt) * dA + tt * Asdt));
+    const S Dn = nt * D0 + (VX ? ct * dA + vn : ct * dA);
+    const S Dt = VX ? tt * D0 + Asdt + vt : tt * D0 + Asdt;
+    const S D3 = Ht * sA + (kt * A2 + ((ct * nt) * dA + (VX ? tt * Asdt + ve : tt * Asdt)));
     const S mL = rL * nL, mR = rR * nR;
     G[0] = (mL + mR) - D0;
     G[N] = mL * nL + (mR * nR + ((pL + pR) - Dn));
@@ -336,14 +339,15 @@ __device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts
     G[3] = nL * eL + (nR * eR - D3);
 }
 
-// Doubled viscous flux subtracted from G (coefficients of face_coefs): dnn,
-// dtn, dTn differences across the face, dnt, dtt four-cell differences along
-// it, sn, st the sums of the two cells' normal and tangential velocities, mus
-// the sum of their viscosities (Sutherland's law only).
-template <int DIR, bool SUTH, class S>
-__device__ __forceinline__ void visc2(S *G, S dnn, S dtn, S dTn, S dnt, S dtt, S sn, S st, S mus, const double *vk)
+// Doubled viscous flux terms of a uniform-grid face (coefficients of
+// face_coefs), for roe2 to subtract: dnn, dtn, dTn differences across the
+// face, dnt, dtt four-cell differences along it, sn, st the sums of the two
+// cells' normal and tangential velocities, mus the sum of their viscosities
+// (Sutherland's law only); vn, vt the momentum and ve the energy terms.
+template <bool SUTH, class S>
+__device__ __forceinline__ void visc2_terms(S dnn, S dtn, S dTn, S dnt, S dtt, S sn, S st, S mus, const double *vk,
+                                            S &vn, S &vt, S &ve)
 {
-    constexpr int N = 1 + DIR, T = 2 - DIR;
     S tnn = dnn * vk[0] + dtt * vk[1];
     S tnt = dnt * vk[2] + dtn * vk[3];
     S q = dTn * vk[4];
@@ -352,14 +356,15 @@ __device__ __forceinline__ void visc2(S *G, S dnn, S dtn, S dTn, S dnt, S dtt, S
         tnt = tnt * mus;
         q = q * mus;
     }
-    G[N] = G[N] - tnn;
-    G[T] = G[T] - tnt;
-    G[3] = G[3] - (half(sn) * tnn + (half(st) * tnt + q));
+    vn = tnn;
+    vt = tnt;
+    ve = half(sn) * tnn + (half(st) * tnt + q);
 }
 // Doubled Roe flux G = 2F through a face with unit normal (nx, ny) (curvilinear
 // grids): the flux of roe_n.
-template <class S>
-__device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double ny, const StencilConsts &C, S *G)
+template <bool VX, class S>
+__device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double ny, const StencilConsts &C, S *G,
+                                       S v1, S v2, S v3)
 {
     const S rL = L[0], uL = L[1], vL = L[2], pL = L[3];
     const S rR = R[0], uR = R[1], vR = R[2], pR = R[3];
@@ -389,9 +394,11 @@ __device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double
     const S A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3, As = l2 * rt;
     const S sA = A1 + A3, dA = A3 - A1, D0 = sA + A2;
     const S cdA = ct * dA;
-    const S D1 = ut * D0 + (cdA * nx + As * (du - dqn * nx));
-    const S D2 = vt * D0 + (cdA * ny + As * (dv - dqn * ny));
-    const S D3 = Ht * sA + (kt * A2 + (qnt * cdA + As * ((ut * du + vt * dv) - qnt * dqn)));
+    // with VX the viscous terms v1, v2, v3 (visc_n2_terms) join the products by As
+    const S sx = du - dqn * nx, sy = dv - dqn * ny, s3 = (ut * du + vt * dv) - qnt * dqn;
+    const S D1 = ut * D0 + (cdA * nx + (VX ? As * sx + v1 : As * sx));
+    const S D2 = vt * D0 + (cdA * ny + (VX ? As * sy + v2 : As * sy));
+    const S D3 = Ht * sA + (kt * A2 + (qnt * cdA + (VX ? As * s3 + v3 : As * s3)));
     const S mL = rL * qnL, mR = rR * qnR, pLR = pL + pR;
     G[0] = (mL + mR) - D0;
     G[1] = mL * uL + (mR * uR + (pLR * nx - D1));
@@ -399,15 +406,16 @@ __device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double
     G[3] = qnL * eL + (qnR * eR - D3);
 }
 
-// Doubled viscous flux of a curvilinear face subtracted from G.  The gradients
+// Doubled viscous flux terms of a curvilinear face, for roe_n2 to subtract
+// (v1, v2 the momentum and v3 the energy terms).  The gradients
 // come from the difference across the face (dC*) and four times the difference
 // of the two vertex averages along it (dV*: the middle pair of cells cancels),
 // with the metric terms c0, c1q = c1 / 4, c2, c3q = c3 / 4; su, sv the sums of
 // the two cells' velocities, mus of their viscosities (Sutherland's law only).
 template <bool SUTH, class S>
-__device__ __forceinline__ void visc_n2(S *G, double nx, double ny, double c0, double c1q, double c2, double c3q,
-                                        S dCu, S dCv, S dCT, S dVu, S dVv, S dVT, S su, S sv, S mus,
-                                        const StencilConsts &C)
+__device__ __forceinline__ void visc_n2_terms(double nx, double ny, double c0, double c1q, double c2, double c3q,
+                                              S dCu, S dCv, S dCT, S dVu, S dVv, S dVT, S su, S sv, S mus,
+                                              const StencilConsts &C, S &v1, S &v2, S &v3)
 {
     const S ux = dCu * c0 + dVu * c1q, uy = dCu * c2 + dVu * c3q;
     const S vx = dCv * c0 + dVv * c1q, vy = dCv * c2 + dVv * c3q;
@@ -423,9 +431,9 @@ __device__ __forceinline__ void visc_n2(S *G, double nx, double ny, double c0, d
         q = q * mus;
     }
     const S tnx = txx * nx + txy * ny, tny = txy * nx + tyy * ny;
-    G[1] = G[1] - tnx;
-    G[2] = G[2] - tny;
-    G[3] = G[3] - (half(su) * tnx + (half(sv) * tny + q));
+    v1 = tnx;
+    v2 = tny;
+    v3 = half(su) * tnx + (half(sv) * tny + q);
 }
 #endif  // ROK_STENCIL_FAST
 
@@ -662,12 +670,13 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
             muscl_d(pick(tl, k, y, xl), pick(tl, k, y, xr), df.dx[k][y - 2][xl], df.dx[k][y - 2][xr], df.dx[k][y - 2][xr + 1],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
 #ifdef ROK_STENCIL_FAST
-        roe2<0>(WL, WR, C, F);
+        S vn = lift<S>(0.0), vt = lift<S>(0.0), ve = lift<S>(0.0);
         if (VISC)
-            visc2<0, SUTH>(F, df.dx[1][y - 2][xr], df.dx[2][y - 2][xr], tl.T[y][xr] - tl.T[y][xl],
-                           ps.px[0][y][fx] - ps.px[0][y - 2][fx], ps.px[1][y][fx] - ps.px[1][y - 2][fx],
-                           ps.px[0][y - 1][fx], ps.px[1][y - 1][fx],
-                           SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C.vk[0]);
+            visc2_terms<SUTH>(df.dx[1][y - 2][xr], df.dx[2][y - 2][xr], tl.T[y][xr] - tl.T[y][xl],
+                              ps.px[0][y][fx] - ps.px[0][y - 2][fx], ps.px[1][y][fx] - ps.px[1][y - 2][fx],
+                              ps.px[0][y - 1][fx], ps.px[1][y - 1][fx],
+                              SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C.vk[0], vn, vt, ve);
+        roe2<0, VISC>(WL, WR, C, F, vn, vt, ve);
 #else
         roe_x(WL, WR, C, F);
         if (VISC) {
@@ -700,12 +709,13 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
             muscl_d(pick(tl, k, yb, x), pick(tl, k, yt, x), df.dy[k][yb][x - 2], df.dy[k][yt][x - 2], df.dy[k][yt + 1][x - 2],
                     C.c_lo, C.c_hi, WL[k], WR[k]);
 #ifdef ROK_STENCIL_FAST
-        roe2<1>(WL, WR, C, F);
+        S vn = lift<S>(0.0), vt = lift<S>(0.0), ve = lift<S>(0.0);
         if (VISC)
-            visc2<1, SUTH>(F, df.dy[2][yt][x - 2], df.dy[1][yt][x - 2], tl.T[yt][x] - tl.T[yb][x],
-                           ps.qy[1][x][fy] - ps.qy[1][x - 2][fy], ps.qy[0][x][fy] - ps.qy[0][x - 2][fy],
-                           ps.qy[1][x - 1][fy], ps.qy[0][x - 1][fy],
-                           SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C.vk[1]);
+            visc2_terms<SUTH>(df.dy[2][yt][x - 2], df.dy[1][yt][x - 2], tl.T[yt][x] - tl.T[yb][x],
+                              ps.qy[1][x][fy] - ps.qy[1][x - 2][fy], ps.qy[0][x][fy] - ps.qy[0][x - 2][fy],
+                              ps.qy[1][x - 1][fy], ps.qy[0][x - 1][fy],
+                              SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C.vk[1], vn, vt, ve);
+        roe2<1, VISC>(WL, WR, C, F, vn, vt, ve);
 #else
         roe_y(WL, WR, C, F);
         if (VISC) {
@@ -906,15 +916,16 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
                     C.c_lo, C.c_hi, WL[k], WR[k]);
         double nxf = G.in_x[fi], nyf = G.in_y[fi];
 #ifdef ROK_STENCIL_FAST
-        roe_n2(WL, WR, nxf, nyf, C, F);
+        S v1 = lift<S>(0.0), v2 = lift<S>(0.0), v3 = lift<S>(0.0);
         if (VISC)
-            visc_n2<SUTH>(F, nxf, nyf, G.ic0[fi], quarter(G.ic1[fi]), G.ic2[fi], quarter(G.ic3[fi]),
+            visc_n2_terms<SUTH>(nxf, nyf, G.ic0[fi], quarter(G.ic1[fi]), G.ic2[fi], quarter(G.ic3[fi]),
                           tl.u[y][xr] - tl.u[y][xl], tl.v[y][xr] - tl.v[y][xl], tl.T[y][xr] - tl.T[y][xl],
                           (tl.u[y + 1][xl] + tl.u[y + 1][xr]) - (tl.u[y - 1][xl] + tl.u[y - 1][xr]),
                           (tl.v[y + 1][xl] + tl.v[y + 1][xr]) - (tl.v[y - 1][xl] + tl.v[y - 1][xr]),
                           (tl.T[y + 1][xl] + tl.T[y + 1][xr]) - (tl.T[y - 1][xl] + tl.T[y - 1][xr]),
                           tl.u[y][xl] + tl.u[y][xr], tl.v[y][xl] + tl.v[y][xr],
-                          SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C);
+                          SUTH ? tl.mu[y][xl] + tl.mu[y][xr] : lift<S>(0.0), C, v1, v2, v3);
+        roe_n2<VISC>(WL, WR, nxf, nyf, C, F, v1, v2, v3);
         const double len = half(G.il[fi]);   // the face holds 2F
 #else
         roe_n(WL, WR, nxf, nyf, C, F);
@@ -976,15 +987,16 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
                     C.c_lo, C.c_hi, WL[k], WR[k]);
         double nxf = G.jn_x[fi], nyf = G.jn_y[fi];
 #ifdef ROK_STENCIL_FAST
-        roe_n2(WL, WR, nxf, nyf, C, F);
+        S v1 = lift<S>(0.0), v2 = lift<S>(0.0), v3 = lift<S>(0.0);
         if (VISC)
-            visc_n2<SUTH>(F, nxf, nyf, G.jc0[fi], quarter(G.jc1[fi]), G.jc2[fi], quarter(G.jc3[fi]),
+            visc_n2_terms<SUTH>(nxf, nyf, G.jc0[fi], quarter(G.jc1[fi]), G.jc2[fi], quarter(G.jc3[fi]),
                           tl.u[yt][x] - tl.u[yb][x], tl.v[yt][x] - tl.v[yb][x], tl.T[yt][x] - tl.T[yb][x],
                           (tl.u[yb][x - 1] + tl.u[yt][x - 1]) - (tl.u[yb][x + 1] + tl.u[yt][x + 1]),
                           (tl.v[yb][x - 1] + tl.v[yt][x - 1]) - (tl.v[yb][x + 1] + tl.v[yt][x + 1]),
                           (tl.T[yb][x - 1] + tl.T[yt][x - 1]) - (tl.T[yb][x + 1] + tl.T[yt][x + 1]),
                           tl.u[yb][x] + tl.u[yt][x], tl.v[yb][x] + tl.v[yt][x],
-                          SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C);
+                          SUTH ? tl.mu[yb][x] + tl.mu[yt][x] : lift<S>(0.0), C, v1, v2, v3);
+        roe_n2<VISC>(WL, WR, nxf, nyf, C, F, v1, v2, v3);
         const double len = half(G.jl[fi]);   // the face holds 2F
 #else
         roe_n(WL, WR, nxf, nyf, C, F);
