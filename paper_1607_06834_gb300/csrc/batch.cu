@@ -123,6 +123,7 @@ void group_consts(const rok_problem_desc &d, StencilConsts &C)
     C.suth_s = d.sutherland_s;
     C.gg = C.inv_gm1 + 1.0;
     C.gm1h = 0.5 * C.gm1;
+    C.efix_k = (1.0 - C.efix) / (1.0 + C.efix);
 }
 
 // instances of one group share the gas model and scheme constants

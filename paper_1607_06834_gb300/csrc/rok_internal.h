@@ -42,6 +42,7 @@ struct StencilConsts {
     double gg, gm1h, hrdx, hrdy;
     double vk[2][5];
     double vc[4];
+    double efix_k;             // (1 - efix) / (1 + efix): c~ efix_k >= |u~| <=> c~ - |u~| >= efix (|u~| + c~)
 };
 
 // Viscous coefficients of the doubled face flux G = 2F of a uniform grid, per
@@ -72,6 +73,7 @@ inline void set_fast_consts(StencilConsts &C)
 {
     C.gg = C.inv_gm1 + 1.0;
     C.gm1h = 0.5 * C.gm1;
+    C.efix_k = (1.0 - C.efix) / (1.0 + C.efix);
     C.hrdx = 0.5 * C.rdx;
     C.hrdy = 0.5 * C.rdy;
     face_coefs(C.mu, C.sutherland != 0, C.kfac, C.rdx, C.rdy, C.vk);

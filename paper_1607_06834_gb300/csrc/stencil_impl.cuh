@@ -292,22 +292,23 @@ __device__ __forceinline__ S harten2(S lam, S delta)
 // The sum and difference of the two acoustic wave terms of the Roe
 // dissipation, sA = l1 a1 + l3 a3 and dA = l3 a3 - l1 a1, with
 // a1,3 = (dp -+ rho~ c~ dn) / (2 c~^2) and l1,3 = |u~ -+ c~| after Harten's
-// fix.  Where the face is subsonic and the fix idle (c~ - |u~| >= delta),
-// l1,3 = c~ -+ u~, and with c~ / c~^2 = 1 / c~ the two reduce to
-// sA = (dp + u~ rho~ dn) / c~ and dA = rho~ dn + u~ dp / c~^2 (7 FP64
-// instructions instead of 12).  The choice is made face by face (a warp
-// whose faces differ runs both forms), so a face's arithmetic does not depend
-// on the faces sharing its warp; rc = 1 / c~.
+// fix (delta = efix (|u~| + c~)).  Where the face is subsonic and the fix idle
+// (c~ - |u~| >= delta, i.e. c~ efix_k >= |u~|), l1,3 = c~ -+ u~, and with
+// c~ / c~^2 = 1 / c~ the two reduce to sA = (dp + u~ rho~ dn) / c~ and
+// dA = rho~ dn + u~ dp / c~^2 (7 FP64 instructions instead of 15).  The
+// choice is made face by face (a warp whose faces differ runs both forms), so
+// a face's arithmetic does not depend on the faces sharing its warp; rc = 1/c~.
 template <class S>
-__device__ __forceinline__ void acoustic_sums(S un, S ct, S rc, S inv_c2, S rt, S dn, S dp, S l2, S delta, S &sA,
-                                              S &dA)
+__device__ __forceinline__ void acoustic_sums(S un, S ct, S rc, S inv_c2, S rt, S dn, S dp, S l2,
+                                              const StencilConsts &C, S &sA, S &dA)
 {
-    // c~ - |u~| >= delta (the bit-pattern order of less_nonneg also puts a
-    // negative difference, a supersonic face, below delta >= 0)
-    if (!less_nonneg(val(ct - l2), val(delta))) {
+    // both sides non-negative for efix <= 1 (a negative product, efix > 1,
+    // orders below by its sign bit: the general form)
+    if (!less_nonneg(val(ct * C.efix_k), val(l2))) {
         sA = rc * ((un * rt) * dn + dp);
         dA = (inv_c2 * un) * dp + rt * dn;
     } else {
+        const S delta = C.efix * (l2 + ct);
         const S hc = half(inv_c2);
         const S rcdq = (rt * ct) * dn;
         const S a1 = (dp - rcdq) * hc, a3 = (dp + rcdq) * hc;
@@ -351,9 +352,8 @@ __device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts
     // wave strengths and speeds (Harten's fix on the acoustic waves)
     const S a2 = drho - dp * inv_c2;
     const S l2 = fabs(nt);
-    const S delta = C.efix * (l2 + ct);
     S sA, dA;
-    acoustic_sums(nt, ct, rc, inv_c2, rt, dn, dp, l2, delta, sA, dA);
+    acoustic_sums(nt, ct, rc, inv_c2, rt, dn, dp, l2, C, sA, dA);
     const S A2 = l2 * a2, As = l2 * rt;
     const S D0 = sA + A2;
     const S Asdt = As * dt;
@@ -415,9 +415,8 @@ __device__ __forceinline__ void roe_n2(const S *L, const S *R, double nx, double
     const S qnt = ut * nx + vt * ny;
     const S a2 = drho - dp * inv_c2;
     const S l2 = fabs(qnt);
-    const S delta = C.efix * (l2 + ct);
     S sA, dA;
-    acoustic_sums(qnt, ct, rc, inv_c2, rt, dqn, dp, l2, delta, sA, dA);
+    acoustic_sums(qnt, ct, rc, inv_c2, rt, dqn, dp, l2, C, sA, dA);
     const S A2 = l2 * a2, As = l2 * rt;
     const S D0 = sA + A2;
     const S cdA = ct * dA;
