@@ -97,8 +97,9 @@ struct LinalgOps {
     // j + 2) are the arrival counters of the partial generations, zero on entry
     // (column_counter_offset).  Strict build: the same arithmetic as dot2 + mgs
     // + normalize.  FMA build: two basis vectors a pass (MGS to rounding); the
-    // columns of one basis run in order, and partA[3G, 4G) (G <= P its grid)
-    // carries the partials of <v_{j+1}, v_j> from column j to column j + 1.
+    // columns of one basis run in order, and partA[2G, 3G) (G <= P its grid)
+    // carries the partials of <v_{j+1}, v_j> from column j to column j + 1;
+    // the breakdown test's scale ||J v_j|| is (sum_i h_ij^2 + h_{j+1,j}^2)^(1/2).
     // Returns cudaErrorNotSupported when the ctas cannot cover the P chunks
     // (caller falls back).
     // fp32: the basis V is binary32 and the Gram-Schmidt arithmetic binary32 (w rounded on load);

@@ -827,7 +827,10 @@ __global__ void __launch_bounds__(RT, 2) cgs2_column_kernel(const double *__rest
 // column's first reduction), and kept in StepState::gram.  So a pair costs
 // the same 2 FMAs per entry and vector as two MGS passes but one grid-wide
 // wait instead of two; the results agree with one-vector MGS to rounding (the
-// two differ only in where the dot product of b is rounded).
+// two differ only in where the dot product of b is rounded).  The scale of
+// the breakdown test, ||w|| before the projections, is taken as
+// (sum_i h_ij^2 + h_{j+1,j}^2)^(1/2) (Pythagoras for the orthonormal basis)
+// instead of a dot product of its own.
 //
 // One CTA of kEvenThreads threads per SM (the register file holds 512 threads
 // of this kernel): one set of reductions and one arrival per SM and pass,
@@ -1099,7 +1102,7 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
     const int kv = my < hi ? (int)((hi - my + T - 1) / T) : 0;
     const int kmax = (int)((hi - lo + T - 1) / T);   // uniform over the CTA
     const int P = (j + 2) >> 1;   // passes: pairs (v_{2p}, v_{2p+1}); the last is v_j alone when j is even
-    double *gpart = partA + 3 * (size_t)G;   // partials of <v_{j+1}, v_j> for the next column
+    double *gpart = partA + 2 * (size_t)G;   // partials of <v_{j+1}, v_j> for the next column
 #pragma unroll
     for (int k = 0; k < E; ++k)
         if (k >= kv && k < kmax) sa[k * T + threadIdx.x] = sb[k * T + threadIdx.x] = 0.0;
@@ -1109,46 +1112,46 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
     if (j >= 1) even_load(vb, V + ldv + my, kv, kmax);   // v_1
     if (P >= 2 && threadIdx.x == 0)   // pair 1 (the zeros above lie past its bytes)
         pair_stage_issue(sa, sb, V + 2 * ldv + lo, j >= 3 ? V + 3 * ldv + lo : nullptr, hi - lo, &stage_bar);
-    // first partials: <v_0, w>, <v_1, w> and <w, w>
+    // first partials: <v_0, w> and (j >= 1) <v_1, w>
     sred[threadIdx.x] = even_dot(va, wv, kmax);
-    sred[T + threadIdx.x] = j >= 1 ? even_dot(vb, wv, kmax) : 0.0;
-    sred[2 * T + threadIdx.x] = even_dot(wv, wv, kmax);
+    if (j >= 1) sred[T + threadIdx.x] = even_dot(vb, wv, kmax);
     __syncthreads();
-    quads_cta<3>(sred, sh4);
+    if (j >= 1) quad0_cta2(sred, sh4);
+    else quads_cta<1>(sred, sh4);
     if (threadIdx.x < 32) {
         const double t = warp0_totals(sh4);
-        const double t1 = __shfl_sync(0xffffffffu, t, 1), t2 = __shfl_sync(0xffffffffu, t, 2);
+        const double t1 = __shfl_sync(0xffffffffu, t, 1);
         if (threadIdx.x == 0) {
             partA[blockIdx.x] = t;
-            partA[G + blockIdx.x] = t1;
-            partA[2 * G + blockIdx.x] = t2;
+            if (j >= 1) partA[G + blockIdx.x] = t1;
             red_add_release_gpu(cnt, 1u);   // the same thread stored the partials
         }
     }
     double *pin = partA, *pout = partB;
-    double wnorm0 = 0.0, gfresh = 0.0;   // warp 0 only (wnorm0: lane 0)
+    // warp 0: sum of the squares of the column's projections so far; with the
+    // final h_{j+1,j}^2 it is ||w||^2 of the JVP result for an orthonormal
+    // basis (Pythagoras), the scale of the breakdown test
+    double ssq = 0.0, gfresh = 0.0;
     for (int p = 0; p < P; ++p) {
         const bool pair = 2 * p + 1 <= j;
         bool good;
         if (p == 0)   // with j >= 1 also <v_j, v_{j-1}> from the previous column's partials
-            good = j >= 1 ? pair_wait<4>(cnt, G, &st->status, pin, sh4, &ok)
-                          : pair_wait<3>(cnt, G, &st->status, pin, sh4, &ok);
+            good = j >= 1 ? pair_wait<3>(cnt, G, &st->status, pin, sh4, &ok)
+                          : pair_wait<1>(cnt, G, &st->status, pin, sh4, &ok);
         else
             good = pair ? pair_wait2(cnt + p, G, &st->status, pin, sh4, &ok)
                         : pair_wait<1>(cnt + p, G, &st->status, pin, sh4, &ok);
         if (threadIdx.x < 32 && good) {   // warp 0: the totals in lanes 0 .. 3 at once
             const double t = warp0_totals(sh4);
             const double alpha = __shfl_sync(0xffffffffu, t, 0), beta = __shfl_sync(0xffffffffu, t, 1);
-            if (p == 0) {
-                const double ww = __shfl_sync(0xffffffffu, t, 2);
-                gfresh = __shfl_sync(0xffffffffu, t, 3);
-                if (threadIdx.x == 0) wnorm0 = sqrt(ww);
-            }
+            if (p == 0) gfresh = __shfl_sync(0xffffffffu, t, 2);
             double h1 = 0.0;
             if (pair) {
                 const double g = 2 * p + 1 == j ? gfresh : sgram[2 * p];
                 h1 = fma(-g, alpha, beta);
             }
+            ssq = fma(alpha, alpha, ssq);
+            if (pair) ssq = fma(h1, h1, ssq);
             if (threadIdx.x == 0) {
                 sh[0] = alpha;
                 sh[1] = h1;
@@ -1156,10 +1159,7 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
             if (threadIdx.x == 0 && blockIdx.x == 0) {
                 st->H[2 * p * kMaxKrylov + j] = alpha;
                 if (pair) st->H[(2 * p + 1) * kMaxKrylov + j] = h1;
-                if (p == 0) {
-                    st->wnorm0 = wnorm0;
-                    if (j >= 1) st->gram[j - 1] = gfresh;
-                }
+                if (p == 0 && j >= 1) st->gram[j - 1] = gfresh;
             }
         }
         __syncthreads();
@@ -1222,10 +1222,13 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
     // the norm, the breakdown test and the reciprocal by thread 0 (FP64
     // square roots and divisions in every warp would cost each sub-partition)
     if (threadIdx.x == 0 && good) {
-        const double hn = sqrt(quad_total(sh4, 0));
+        const double hn2 = quad_total(sh4, 0);
+        const double hn = sqrt(hn2);
+        const double wnorm0 = sqrt(ssq + hn2);   // ||J v_j||
         brk = !(hn > brk_tol * wnorm0);
         sh[0] = 1.0 / hn;
         if (blockIdx.x == 0) {
+            st->wnorm0 = wnorm0;
             if (brk) {
                 st->active = 0;
                 st->meff = j + 1;
