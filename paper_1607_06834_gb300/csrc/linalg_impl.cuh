@@ -1374,6 +1374,41 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
         for (int i = threadIdx.x; i < m * (P - (int)gridDim.x); i += T)
             pout[(size_t)(i / (P - (int)gridDim.x)) * P + gridDim.x + i % (P - (int)gridDim.x)] = 0.0;
 }
+
+// ---- stage vectors k = sum_i c_i V_i + h F, FMA build: quads of entries ---------
+// Each thread forms four consecutive entries (32-byte loads, four independent
+// FMA chains in the basis order of stage_vec_kernel, so the same values), one
+// quad per thread and no grid-stride remainder.
+__device__ __forceinline__ void st_quad(double *p, const Quad &q)
+{
+    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(q.x), "d"(q.y), "d"(q.z), "d"(q.w)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(RT) stage_vec_quad_kernel(double *__restrict__ k, const double *__restrict__ F,
+                                                            const double *__restrict__ V, size_t ldv, size_t nq,
+                                                            int stage, const StepState *st)
+{
+    __shared__ double c[kMaxKrylov];
+    const int m = st->meff;
+    const double h = st->h;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) c[i] = st->cvec[stage][i];
+    __syncthreads();
+    const size_t q = (size_t)blockIdx.x * RT + threadIdx.x;
+    if (q >= nq) return;
+    Quad a{0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) {
+        const Quad v = ld_quad(V + (size_t)i * ldv + 4 * q);
+        const double ci = c[i];
+        a.x = a.x + ci * v.x;
+        a.y = a.y + ci * v.y;
+        a.z = a.z + ci * v.z;
+        a.w = a.w + ci * v.w;
+    }
+    const Quad f = ld_quad(F + 4 * q);
+    st_quad(k + 4 * q, Quad{a.x + h * f.x, a.y + h * f.y, a.z + h * f.z, a.w + h * f.w});
+}
 #endif  // ROK_LINALG_FAST
 
 // First basis vector: partials of ||(T)F1||^2 ...
@@ -2340,6 +2375,14 @@ static cudaError_t lu(StepState *st, cudaStream_t s)
 static cudaError_t stage_vec(double *k, const double *F, const void *V, int fp32, size_t ldv, size_t n, int stage,
                              const StepState *st, int grid, cudaStream_t s)
 {
+#ifdef ROK_LINALG_FAST
+    if (!fp32 && !(n & 3) && !(ldv & 3) && !((uintptr_t)F & 31) && !((uintptr_t)V & 31) && !((uintptr_t)k & 31)) {
+        const size_t nq = n / 4;
+        stage_vec_quad_kernel<<<(unsigned)((nq + RT - 1) / RT), RT, 0, s>>>(k, F, static_cast<const double *>(V), ldv,
+                                                                            nq, stage, st);
+        return cudaGetLastError();
+    }
+#endif
     if (fp32) stage_vec_kernel<float><<<grid, RT, 0, s>>>(k, F, static_cast<const float *>(V), ldv, n, stage, st);
     else stage_vec_kernel<double><<<grid, RT, 0, s>>>(k, F, static_cast<const double *>(V), ldv, n, stage, st);
     return cudaGetLastError();
