@@ -1320,25 +1320,32 @@ __device__ __forceinline__ Quad ld_quad(const double *p)
     asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(q.x), "=d"(q.y), "=d"(q.z), "=d"(q.w) : "l"(p));
     return q;
 }
+// four consecutive binary32 basis values (one 16-byte load), exactly as binary64
+__device__ __forceinline__ Quad ld_quad(const float *p)
+{
+    const float4 f = __ldg(reinterpret_cast<const float4 *>(p));
+    return Quad{(double)f.x, (double)f.y, (double)f.z, (double)f.w};
+}
 
-template <int E>
+template <int E, class T>
 __global__ void __launch_bounds__(kEvenThreads, 1)
-    multidot_even_kernel(const double *__restrict__ F, const double *__restrict__ V, size_t ldv, size_t n, size_t L,
+    multidot_even_kernel(const double *__restrict__ F, const T *__restrict__ V, size_t ldv, size_t n, size_t L,
                          double *__restrict__ pout, int P, const StepState *st)
 {
-    // quads of consecutive entries (32-byte loads): thread t holds quads t + k T, k < E / 4
-    constexpr int T = kEvenThreads, NW = kEvenThreads / 32, E4 = E / 4;
+    // quads of consecutive entries (32-byte loads of binary64, 16-byte of a
+    // binary32 basis): thread t holds quads t + k TH, k < E / 4
+    constexpr int TH = kEvenThreads, NW = kEvenThreads / 32, E4 = E / 4;
     static_assert(NW == 16, "the CTA sum below adds 16 warp sums");
     __shared__ double ws[kMaxKrylov][NW];
     const int m = st->meff;
     const size_t lo = (size_t)blockIdx.x * L;
     const size_t hi = lo + L < n ? lo + L : n;
     const size_t nq = (hi - lo) / 4;   // quads of this CTA (L, n multiples of 4)
-    const int kv = threadIdx.x < nq ? (int)((nq - threadIdx.x + T - 1) / T) : 0;
+    const int kv = threadIdx.x < nq ? (int)((nq - threadIdx.x + TH - 1) / TH) : 0;
     const double *F4 = F + lo + 4 * (size_t)threadIdx.x;
     Quad f[E4];
 #pragma unroll
-    for (int k = 0; k < E4; ++k) f[k] = k < kv ? ld_quad(F4 + (size_t)4 * k * T) : Quad{0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < E4; ++k) f[k] = k < kv ? ld_quad(F4 + (size_t)4 * k * TH) : Quad{0.0, 0.0, 0.0, 0.0};
     for (int g = 0; g < m; g += 16) {
         const int cnt = m - g < 16 ? m - g : 16;   // uniform
         double t[16];
@@ -1346,11 +1353,11 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
         for (int q = 0; q < 16; ++q) {
             double s = 0.0;
             if (q < cnt) {
-                const double *v = V + (size_t)(g + q) * ldv + lo + 4 * (size_t)threadIdx.x;
+                const T *v = V + (size_t)(g + q) * ldv + lo + 4 * (size_t)threadIdx.x;
 #pragma unroll
                 for (int k = 0; k < E4; ++k)
                     if (k < kv) {
-                        const Quad x = ld_quad(v + (size_t)4 * k * T);
+                        const Quad x = ld_quad(v + (size_t)4 * k * TH);
                         s = x.x * f[k].x + s;
                         s = x.y * f[k].y + s;
                         s = x.z * f[k].z + s;
@@ -1371,7 +1378,7 @@ __global__ void __launch_bounds__(kEvenThreads, 1)
         pout[(size_t)threadIdx.x * P + blockIdx.x] = s;
     }
     if (blockIdx.x == 0)   // the chunk slots past the grid
-        for (int i = threadIdx.x; i < m * (P - (int)gridDim.x); i += T)
+        for (int i = threadIdx.x; i < m * (P - (int)gridDim.x); i += TH)
             pout[(size_t)(i / (P - (int)gridDim.x)) * P + gridDim.x + i % (P - (int)gridDim.x)] = 0.0;
 }
 
@@ -1385,8 +1392,9 @@ __device__ __forceinline__ void st_quad(double *p, const Quad &q)
                  : "memory");
 }
 
+template <class T>
 __global__ void __launch_bounds__(RT) stage_vec_quad_kernel(double *__restrict__ k, const double *__restrict__ F,
-                                                            const double *__restrict__ V, size_t ldv, size_t nq,
+                                                            const T *__restrict__ V, size_t ldv, size_t nq,
                                                             int stage, const StepState *st)
 {
     __shared__ double c[kMaxKrylov];
@@ -2329,7 +2337,7 @@ static cudaError_t multidot(const double *F, const void *V, int fp32, size_t ldv
                             const StepState *st, cudaStream_t s)
 {
 #ifdef ROK_LINALG_FAST
-    if (!fp32) {   // even split, one CTA per SM (the strict build keeps the oracle's chunks)
+    {   // even split, one CTA per SM (the strict build keeps the oracle's chunks)
         static int sms = 0;
         if (sms == 0) {
             int dev = 0;
@@ -2340,14 +2348,20 @@ static cudaError_t multidot(const double *F, const void *V, int fp32, size_t ldv
         const int G = sms > 0 && P > sms ? sms : P;
         size_t L = (n + G - 1) / G;
         L = (L + 3) & ~(size_t)3;
-        // 32-byte loads of entry quads: lengths multiples of 4, aligned starts
+        // loads of entry quads: lengths multiples of 4, aligned starts
+        const uintptr_t va = fp32 ? 15 : 31;
         if (sms > 0 && L <= (size_t)kEvenThreads * kEvenPerThread && !(n & 3) && !(ldv & 3) &&
-            !((uintptr_t)F & 31) && !((uintptr_t)V & 31)) {
-            const double *Vd = static_cast<const double *>(V);
-            if (L <= (size_t)kEvenThreads * 8)
-                multidot_even_kernel<8><<<G, kEvenThreads, 0, s>>>(F, Vd, ldv, n, L, pout, P, st);
-            else
-                multidot_even_kernel<16><<<G, kEvenThreads, 0, s>>>(F, Vd, ldv, n, L, pout, P, st);
+            !((uintptr_t)F & 31) && !((uintptr_t)V & va)) {
+            const bool e8 = L <= (size_t)kEvenThreads * 8;
+            if (fp32) {
+                const float *Vf = static_cast<const float *>(V);
+                if (e8) multidot_even_kernel<8, float><<<G, kEvenThreads, 0, s>>>(F, Vf, ldv, n, L, pout, P, st);
+                else multidot_even_kernel<16, float><<<G, kEvenThreads, 0, s>>>(F, Vf, ldv, n, L, pout, P, st);
+            } else {
+                const double *Vd = static_cast<const double *>(V);
+                if (e8) multidot_even_kernel<8, double><<<G, kEvenThreads, 0, s>>>(F, Vd, ldv, n, L, pout, P, st);
+                else multidot_even_kernel<16, double><<<G, kEvenThreads, 0, s>>>(F, Vd, ldv, n, L, pout, P, st);
+            }
             return cudaGetLastError();
         }
     }
@@ -2376,10 +2390,14 @@ static cudaError_t stage_vec(double *k, const double *F, const void *V, int fp32
                              const StepState *st, int grid, cudaStream_t s)
 {
 #ifdef ROK_LINALG_FAST
-    if (!fp32 && !(n & 3) && !(ldv & 3) && !((uintptr_t)F & 31) && !((uintptr_t)V & 31) && !((uintptr_t)k & 31)) {
+    if (!(n & 3) && !(ldv & 3) && !((uintptr_t)F & 31) && !((uintptr_t)V & (fp32 ? 15 : 31)) &&
+        !((uintptr_t)k & 31)) {
         const size_t nq = n / 4;
-        stage_vec_quad_kernel<<<(unsigned)((nq + RT - 1) / RT), RT, 0, s>>>(k, F, static_cast<const double *>(V), ldv,
-                                                                            nq, stage, st);
+        const unsigned grid = (unsigned)((nq + RT - 1) / RT);
+        if (fp32)
+            stage_vec_quad_kernel<float><<<grid, RT, 0, s>>>(k, F, static_cast<const float *>(V), ldv, nq, stage, st);
+        else
+            stage_vec_quad_kernel<double><<<grid, RT, 0, s>>>(k, F, static_cast<const double *>(V), ldv, nq, stage, st);
         return cudaGetLastError();
     }
 #endif
