@@ -75,3 +75,4 @@ def test_rok_step_with_breakdown(rok, period, mode):
         assert np.abs(y - yo).max() <= 1e-9 * np.abs(yo).max()
     # the step stays in the invariant subspace
     assert np.array_equal(y, np.tile(y[:period], 20 // period))
+

@@ -559,3 +559,25 @@ def test_esdirk_step_full_size_taylor_green(rok):
     assert oi['converged']
     assert abs(info['gmres_iters'] - oi['gmres_iters']) <= 0.05 * oi['gmres_iters'] + 2
     assert err <= 1e-8
+
+
+@pytest.mark.parametrize('n', [41, 42, 44])
+@pytest.mark.parametrize('mode', ['strict', 'fast'])
+def test_sizes_outside_the_fast_kernels_preconditions(rok, n, mode):
+    # n = 41: odd, so the FMA build's two-vector column kernel and the quad
+    # projection / stage-vector kernels decline and the launchers fall back to
+    # the pass-by-pass and chunked kernels; n = 42: the column kernel runs, the
+    # quad kernels (n % 4 != 0) fall back; n = 44: all fast kernels run
+    prob, y0 = W.lorenz96(n, seed=5)
+    h = 0.01
+    M = 8
+    yo = I.rok_step(core.System(prob), y0, h, M)
+    ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+    y = dev(y0)
+    info = rok.rok_step(ctx, y, h, M, info=True)
+    assert info['m_eff'] == M
+    y = host(y)
+    if mode == 'strict':
+        assert np.array_equal(y, yo)
+    else:
+        assert np.abs(y - yo).max() <= 1e-9 * np.abs(yo).max()
