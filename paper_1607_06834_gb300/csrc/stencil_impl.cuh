@@ -325,12 +325,10 @@ __device__ __forceinline__ void acoustic_sums(S un, S ct, S rc, S inv_c2, S rt, 
 // (vn, vt, ve: normal momentum, tangential momentum, energy; visc2_terms) is
 // subtracted too, vn and ve inside the dissipation sums where a product
 // becomes a fused multiply-add (one FP64 instruction fewer each).
-template <int DIR, bool VX, class S>
-__device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts &C, S *G, S vn, S vt, S ve)
+template <bool VX, class S>
+__device__ __forceinline__ void roe2_nt(S rL, S nL, S tL, S pL, S rR, S nR, S tR, S pR, const StencilConsts &C,
+                                        S &g0, S &gn, S &gt, S &g3, S vn, S vt, S ve)
 {
-    constexpr int N = 1 + DIR, T = 2 - DIR;
-    const S rL = L[0], nL = L[N], tL = L[T], pL = L[3];
-    const S rR = R[0], nR = R[N], tR = R[T], pR = R[3];
     // Roe average from one reciprocal square root z = 1/sqrt(rho_L rho_R)
     // (sX = sqrt(rho_X)): rho~ = rho_L rho_R z = sL sR; a = rho_R z = sR / sL;
     // the left weight sL / (sL + sR) = 1 / (1 + a); and
@@ -361,10 +359,17 @@ __device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts
     const S Dt = VX ? tt * D0 + Asdt + vt : tt * D0 + Asdt;
     const S D3 = Ht * sA + (kt * A2 + ((ct * nt) * dA + (VX ? tt * Asdt + ve : tt * Asdt)));
     const S mL = rL * nL, mR = rR * nR;
-    G[0] = (mL + mR) - D0;
-    G[N] = mL * nL + (mR * nR + ((pL + pR) - Dn));
-    G[T] = mL * tL + (mR * tR - Dt);
-    G[3] = nL * eL + (nR * eR - D3);
+    g0 = (mL + mR) - D0;
+    gn = mL * nL + (mR * nR + ((pL + pR) - Dn));
+    gt = mL * tL + (mR * tR - Dt);
+    g3 = nL * eL + (nR * eR - D3);
+}
+
+template <int DIR, bool VX, class S>
+__device__ __forceinline__ void roe2(const S *L, const S *R, const StencilConsts &C, S *G, S vn, S vt, S ve)
+{
+    constexpr int N = 1 + DIR, T = 2 - DIR;
+    roe2_nt<VX>(L[0], L[N], L[T], L[3], R[0], R[N], R[T], R[3], C, G[0], G[N], G[T], G[3], vn, vt, ve);
 }
 
 // Doubled viscous flux terms of a uniform-grid face (coefficients of
@@ -681,6 +686,61 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
     }
     __syncthreads();
 
+#ifdef ROK_STENCIL_FAST
+    // One face per thread, x- and y-faces in one sequence of full warp batches
+    // ((TX+1) TY + TX (TY+1) faces: 17 x 32 for 16 x 16 tiles, where batches of
+    // one orientation each need 18, two of them half full: an FP64 warp
+    // instruction costs the same with 16 lanes as with 32).  The orientation
+    // is a per-lane value: it selects the cells, the shared-memory rows of the
+    // differences and pair sums, the normal and tangential velocity and the
+    // output array; the arithmetic is the same for both.
+    {
+        constexpr int NFX_ = (TX + 1) * TY, NF = NFX_ + TX * (TY + 1);
+        auto face = [&](int f) {
+            const bool yd = f >= NFX_;
+            const int g = yd ? f - NFX_ : f;
+            const int fx = yd ? g % TX : g % (TX + 1), fy = yd ? g / TX : g / (TX + 1);
+            // the cells on the minus and plus side (tile coordinates)
+            const int ym = yd ? fy + 1 : fy + 2, xm = yd ? fx + 2 : fx + 1;
+            const int yp = fy + 2, xp = fx + 2;
+            // differences along the face normal: dl, dc, dr at d[0], d[ds], d[2 ds]
+            const int ds = yd ? TX : 1;
+            S WL[4], WR[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const S *d = yd ? &df.dy[k][ym][xm - 2] : &df.dx[k][ym - 2][xm];
+                muscl_d(pick(tl, k, ym, xm), pick(tl, k, yp, xp), d[0], d[ds], d[2 * ds], C.c_lo, C.c_hi, WL[k],
+                        WR[k]);
+            }
+            S vn = lift<S>(0.0), vt = lift<S>(0.0), ve = lift<S>(0.0);
+            if (VISC) {
+                // normal / tangential velocity: u / v on x-faces, v / u on y-faces
+                const S *dn = yd ? &df.dy[2][ym][xm - 2] : &df.dx[1][ym - 2][xm];
+                const S *dt = yd ? &df.dy[1][ym][xm - 2] : &df.dx[2][ym - 2][xm];
+                const int ps_stride = yd ? TY + 1 : TX + 1;
+                const S *pn = yd ? &ps.qy[1][xm][fy] : &ps.px[0][ym][fx];
+                const S *pt = yd ? &ps.qy[0][xm][fy] : &ps.px[1][ym][fx];
+                visc2_terms<SUTH>(dn[ds], dt[ds], tl.T[yp][xp] - tl.T[ym][xm], pn[0] - pn[-2 * ps_stride],
+                                  pt[0] - pt[-2 * ps_stride], pn[-ps_stride], pt[-ps_stride],
+                                  SUTH ? tl.mu[ym][xm] + tl.mu[yp][xp] : lift<S>(0.0), C.vk[yd ? 1 : 0], vn, vt,
+                                  ve);
+            }
+            S g0, gn, gt, g3;
+            roe2_nt<VISC>(WL[0], yd ? WL[2] : WL[1], yd ? WL[1] : WL[2], WL[3], WR[0], yd ? WR[2] : WR[1],
+                          yd ? WR[1] : WR[2], WR[3], C, g0, gn, gt, g3, vn, vt, ve);
+            S *out = yd ? &fc.fy[0][fy][fx] : &fc.fx[0][fy][fx];
+            const int ks = yd ? (TY + 1) * TX : TY * (TX + 1);
+            out[0] = g0;
+            out[ks] = yd ? gt : gn;
+            out[2 * ks] = yd ? gn : gt;
+            out[3 * ks] = g3;
+        };
+        for (int bt = tid >> 5; bt < (NF + 31) / 32; bt += NT / 32) {
+            const int f = bt * 32 + (tid & 31);
+            if (f < NF) face(f);
+        }
+    }
+#else
     // one face per thread, in warp-sized batches with the x-face batches first:
     // warp w takes batches w, w + NT/32, ...  Every batch has one orientation
     // (a warp-uniform branch), and the partial x batch and the last y batch
@@ -775,6 +835,7 @@ __device__ __forceinline__ void cart_tile(const StencilConsts &C, const StencilI
             if (f < NFY) yface(f);
         }
     }
+#endif
     __syncthreads();
 
 #ifdef ROK_STENCIL_FAST
