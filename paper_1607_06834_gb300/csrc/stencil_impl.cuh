@@ -987,6 +987,57 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
     }
     __syncthreads();
 
+#ifdef ROK_STENCIL_FAST
+    // i- and j-faces in one sequence of full warp batches, the orientation a
+    // per-lane value (as in cart_tile): it selects the cells, the difference
+    // rows, the tangential neighbours (+1 row on i-faces, -1 column on j-faces,
+    // the sign convention of the metric terms), the metric arrays and the output
+    {
+        constexpr int NFX_ = (TX + 1) * TY, NF = NFX_ + TX * (TY + 1);
+        auto face = [&](int f) {
+            const bool yd = f >= NFX_;
+            const int g = yd ? f - NFX_ : f;
+            const int fx = yd ? g % TX : g % (TX + 1), fy = yd ? g / TX : g / (TX + 1);
+            const int gi = i0 + fx, gj = j0 + fy;
+            if (yd ? (gi >= nx || gj > ny) : (gi > nx || gj >= ny)) return;
+            const size_t fi = yd ? (size_t)gj * nx + gi : (size_t)gj * (nx + 1) + gi;
+            const int ym = yd ? fy + 1 : fy + 2, xm = yd ? fx + 2 : fx + 1;
+            const int yp = fy + 2, xp = fx + 2;
+            const int ds = yd ? TX : 1;
+            const int ty = yd ? 0 : 1, txo = yd ? -1 : 0;   // tangential step
+            S WL[4], WR[4], F[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const S *d = yd ? &df.dy[k][ym][xm - 2] : &df.dx[k][ym - 2][xm];
+                muscl_d(pick(tl, k, ym, xm), pick(tl, k, yp, xp), d[0], d[ds], d[2 * ds], C.c_lo, C.c_hi, WL[k],
+                        WR[k]);
+            }
+            const double nxf = yd ? G.jn_x[fi] : G.in_x[fi], nyf = yd ? G.jn_y[fi] : G.in_y[fi];
+            S v1 = lift<S>(0.0), v2 = lift<S>(0.0), v3 = lift<S>(0.0);
+            if (VISC) {
+                auto across = [&](const S (&w)[EH][EW]) { return w[yp][xp] - w[ym][xm]; };
+                auto along = [&](const S (&w)[EH][EW]) {
+                    return (w[ym + ty][xm + txo] + w[yp + ty][xp + txo]) - (w[ym - ty][xm - txo] + w[yp - ty][xp - txo]);
+                };
+                visc_n2_terms<SUTH>(nxf, nyf, yd ? G.jc0[fi] : G.ic0[fi], quarter(yd ? G.jc1[fi] : G.ic1[fi]),
+                                    yd ? G.jc2[fi] : G.ic2[fi], quarter(yd ? G.jc3[fi] : G.ic3[fi]), across(tl.u),
+                                    across(tl.v), across(tl.T), along(tl.u), along(tl.v), along(tl.T),
+                                    tl.u[ym][xm] + tl.u[yp][xp], tl.v[ym][xm] + tl.v[yp][xp],
+                                    SUTH ? tl.mu[ym][xm] + tl.mu[yp][xp] : lift<S>(0.0), C, v1, v2, v3);
+            }
+            roe_n2<VISC>(WL, WR, nxf, nyf, C, F, v1, v2, v3);
+            const double len = half(yd ? G.jl[fi] : G.il[fi]);   // the face holds 2F
+            S *out = yd ? &fc.fy[0][fy][fx] : &fc.fx[0][fy][fx];
+            const int ks = yd ? (TY + 1) * TX : TY * (TX + 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out[k * ks] = F[k] * len;
+        };
+        for (int bt = tid >> 5; bt < (NF + 31) / 32; bt += NT / 32) {
+            const int f = bt * 32 + (tid & 31);
+            if (f < NF) face(f);
+        }
+    }
+#else
     // faces in warp-sized batches spread over the warps (as in cart_tile)
     constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
     constexpr int BX = (NFX + 31) / 32, BY = (NFY + 31) / 32;
@@ -1142,6 +1193,7 @@ __global__ void __launch_bounds__(NT, MINB) curv_kernel(const StencilConsts C, c
             if (f < NFY) yface(f);
         }
     }
+#endif
     __syncthreads();
 
     const int tx = tid % TX, ty = tid / TX;
