@@ -45,7 +45,7 @@ BYTES_RESIDUAL, BYTES_JVP = 64, 128
 # 512 x 512, from an ncu capture of this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum, cold L2): the three inputs y, v, f(y) are read once
 # (25.17 MB algorithmic); the 8.4 MB output stays in L2 within the launch.
-STENCIL_JVP_DRAM_BYTES_512 = 25252352 + 256
+STENCIL_JVP_DRAM_BYTES_512 = 25243136 + 0
 
 
 def _peaks():
