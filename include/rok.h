@@ -250,8 +250,10 @@ rok_status dopri5_integrate(rok_ctx *ctx, double *y, double T, const rok_adapt_o
  * viscosity part.  The derivative is that of the discrete step map (the
  * discrete adjoint), with the finite-difference increment eps of
  * Eq. matvecFD held constant.  Supported: uniform periodic grids (Euler, or
- * Navier-Stokes with constant viscosity), binary64 basis, finite-difference
- * JVPs; ROK_ERR_UNSUPPORTED otherwise. */
+ * Navier-Stokes with constant viscosity or Sutherland's law), binary64 basis,
+ * finite-difference JVPs; ROK_ERR_UNSUPPORTED otherwise.  "The viscosity" mu
+ * is desc->mu: the constant viscosity, or the viscosity at t_ref under
+ * Sutherland's law (mu(T) = mu g(T); the residual is affine in mu either way). */
 
 /* ybar = J(y)^T ubar (the transposed Jacobian of the residual of
  * rok_residual) and, if mubar is non-NULL (HOST), mubar = ubar . df/dmu(y)

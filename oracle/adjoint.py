@@ -72,13 +72,13 @@ def residual_vjp(prob, y, u):
 
 
 def residual_dmu(prob, y):
-    """d f / d mu for a constant viscosity: f is affine in mu (the viscous flux is
-    linear in mu, the heat flux through k = mu gamma / ((gamma - 1) Pr)), so the
-    derivative is f(y; mu = 1) - f(y; mu = 0)."""
+    """d f / d mu, mu the constant viscosity or, under Sutherland's law
+    (Sec. 3.2), the viscosity at t_ref: every cell's viscosity is mu times a
+    function of its temperature, the viscous flux is linear in the face
+    viscosity and the heat flux goes through k = mu_face gamma / ((gamma - 1) Pr),
+    so f is affine in mu and the derivative is f(y; mu = 1) - f(y; mu = 0)."""
     if prob.kind != 1:
         return np.zeros(prob.shape)
-    if prob.sutherland_s > 0.0:
-        raise ValueError('constant viscosity only')
     p1 = type(prob)(**{**prob.__dict__, 'mu': 1.0})
     p0 = type(prob)(**{**prob.__dict__, 'mu': 0.0})
     return core.residual(p1, y) - core.residual(p0, y)

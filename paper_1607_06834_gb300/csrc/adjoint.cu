@@ -65,7 +65,7 @@ struct AdjWork {
     double *yb = nullptr, *Fb = nullptr, *F1b = nullptr, *F1acc = nullptr;
     double *wb = nullptr, *wcur = nullptr, *wlast = nullptr, *Yt = nullptr, *y1 = nullptr;
     double *pA = nullptr, *pB = nullptr, *pM = nullptr;
-    double *faces = nullptr;   // 15 x (nx ny) per direction
+    double *faces = nullptr;   // 16 x (nx ny) per direction
     double *prims = nullptr;   // rho, u, v, p, T of every cell (5 x nx ny)
     double *mupart = nullptr;  // CTA partials of the viscosity adjoint
     int nmu = 0;
@@ -90,7 +90,9 @@ constexpr int AT = 256;
 // registers), take one wave and split the faces over the SMs to within a
 // seventh of an SM's share.
 constexpr int FT = 64;
-constexpr int kFaceVals = 15;   // MUSCL left/right adjoints (8) + viscous input adjoints (7)
+// MUSCL left/right adjoints (8) + viscous input adjoints (7) + the adjoint of
+// each neighbour's Sutherland viscosity (1; Sutherland's law only)
+constexpr int kFaceVals = 16;
 
 // primitives (rho, u, v, p) and T = p / rho of the conservative state (rho, mx, my, E)
 __device__ __forceinline__ void prim_of(const StencilConsts &C, double rho, double mx, double my, double E, double *P,
@@ -130,6 +132,17 @@ __global__ void __launch_bounds__(AT) prim_kernel(const StencilConsts C, const d
 #pragma unroll
     for (int k = 0; k < 4; ++k) pr[k * nc + t] = P[k];
     pr[4 * nc + t] = T;
+}
+
+// Sutherland's law (Sec. 3.2) written mu(T) = mu_ref g(T) with
+// g = t^{3/2} (1 + S) / (t + S), t = T / T_ref; also dg/dT = g (t + 3 S) / (2 T (t + S)).
+__device__ __forceinline__ double suth_g(const StencilConsts &C, double T, double &dgdT)
+{
+    const double t = T * C.inv_tref, S = C.suth_s;
+    const double r = 1.0 / (t + S);
+    const double g = (t * sqrt(t)) * ((1.0 + S) * r);
+    dgdT = (0.5 * g) * ((t + 3.0 * S) * r) / T;
+    return g;
 }
 
 __device__ __forceinline__ void prim_load(const double *__restrict__ pr, size_t nc, size_t c, double *P, double &T)
@@ -322,8 +335,9 @@ __device__ __forceinline__ void roe_vjp(const double *L, const double *R, const 
 
 // Pass 1: face D (0: x-faces, face i of row j between cells (i-1, j) and (i, j);
 // 1: y-faces, face j of column i between (i, j-1) and (i, j)).  Stores
-// fa[q * nc + face] for q < 15 and one partial of ubar . df/dmu per CTA.
-template <bool VISC, int D>
+// fa[q * nc + face] for q < 15 (q = 15 too with Sutherland's law) and one
+// partial of ubar . df/dmu per CTA (mu: the viscosity at T_ref with Sutherland's law).
+template <bool VISC, bool SUTH, int D>
 __global__ void __launch_bounds__(FT, 7) vjp_face_kernel(const StencilConsts C, const double *__restrict__ pr,
                                                       const double *__restrict__ ub, double *__restrict__ fa,
                                                       double *__restrict__ mupart)
@@ -377,7 +391,14 @@ __global__ void __launch_bounds__(FT, 7) vjp_face_kernel(const StencilConsts C, 
             const double vt = ((uv(cross(cm1, 1), 1) + uv(cross(cp1, 1), 1)) -
                                (uv(cross(cm1, -1), 1) + uv(cross(cp1, -1), 1))) * q_rt;
             const double uf = 0.5 * (Pm1[1] + Pp1[1]), vf = 0.5 * (Pm1[2] + Pp1[2]);
-            const double mu = C.mu, kf = mu * C.kfac;
+            // face viscosity mu_f: mu, or with Sutherland's law the mean of the two
+            // cells' mu(T) = mu_ref gf (gf = 1 for a constant viscosity)
+            double gf = 1.0;
+            if (SUTH) {
+                double dg_m, dg_p;
+                gf = 0.5 * (suth_g(C, Tm1, dg_m) + suth_g(C, Tp1, dg_p));
+            }
+            const double mu = SUTH ? C.mu * gf : C.mu, kf = mu * C.kfac;
             // x-face: ux = un, uy = ut, vx = vn, vy = vt; y-face: uy = un, ux = ut, vy = vn, vx = vt
             const double ux = D == 0 ? un : ut, uy = D == 0 ? ut : un, vx = D == 0 ? vn : vt, vy = D == 0 ? vt : vn;
             const double div = ux + vy;
@@ -407,7 +428,10 @@ __global__ void __launch_bounds__(FT, 7) vjp_face_kernel(const StencilConsts C, 
             fa[12 * nc + t] = Tnb;
             fa[13 * nc + t] = ufb;
             fa[14 * nc + t] = vfb;
-            mu_c = -((Fb[1] * s1 + Fb[2] * s2) + Fb[3] * ((uf * s1 + vf * s2) + C.kfac * Tn));
+            // adjoint of mu_f; each neighbour's mu(T) enters mu_f with weight 1/2
+            const double mufb = -((Fb[1] * s1 + Fb[2] * s2) + Fb[3] * ((uf * s1 + vf * s2) + C.kfac * Tn));
+            if (SUTH) fa[15 * nc + t] = 0.5 * mufb;
+            mu_c = SUTH ? mufb * gf : mufb;   // d mu_f / d mu_ref = gf
         }
     }
     const double s = lane_tree(mu_c);
@@ -426,7 +450,7 @@ struct VjpOut {
 };
 
 // Pass 2: g = J^T ubar at each cell from the face adjoints
-template <bool VISC>
+template <bool VISC, bool SUTH>
 __global__ void __launch_bounds__(AT) vjp_cell_kernel(const StencilConsts C, const double *__restrict__ pr,
                                                       const double *__restrict__ fx, const double *__restrict__ fy,
                                                       const VjpOut o)
@@ -480,6 +504,14 @@ __global__ void __launch_bounds__(AT) vjp_cell_kernel(const StencilConsts C, con
     }
     double P[4], T;
     prim_load(pr, nc, t, P, T);
+    if (SUTH) {
+        // the cell's mu(T) enters the viscosity of the four faces around it
+        const double mub = (fx[15 * nc + xf(i, j)] + fx[15 * nc + xf(i + 1, j)]) +
+                           (fy[15 * nc + xf(i, j)] + fy[15 * nc + xf(i, j + 1)]);
+        double dg;
+        suth_g(C, T, dg);
+        Tb += mub * (C.mu * dg);
+    }
     const double rho = P[0], u = P[1], v = P[2];
     const double rinv = 1.0 / rho;
     // T = p / rho
@@ -787,14 +819,18 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
     double *fxa = A->faces, *fya = A->faces + kFaceVals * nc;
     cudaStream_t s = c->stream;
     prim_kernel<<<nb, AT, 0, s>>>(C, ystate, dir, dir_scale, A->prims);
-    if (C.viscous) {
-        vjp_face_kernel<true, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
-        vjp_face_kernel<true, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
-        vjp_cell_kernel<true><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
+    if (C.viscous && C.sutherland) {
+        vjp_face_kernel<true, true, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
+        vjp_face_kernel<true, true, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
+        vjp_cell_kernel<true, true><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
+    } else if (C.viscous) {
+        vjp_face_kernel<true, false, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
+        vjp_face_kernel<true, false, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
+        vjp_cell_kernel<true, false><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
     } else {
-        vjp_face_kernel<false, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
-        vjp_face_kernel<false, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
-        vjp_cell_kernel<false><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
+        vjp_face_kernel<false, false, 0><<<nf, FT, 0, s>>>(C, A->prims, ub, fxa, A->mupart);
+        vjp_face_kernel<false, false, 1><<<nf, FT, 0, s>>>(C, A->prims, ub, fya, A->mupart + nf);
+        vjp_cell_kernel<false, false><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
     }
     c->launches += 4;
     if (dst_mu && C.viscous) {
@@ -808,7 +844,6 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
 rok_status vjp_supported(const rok_ctx *c)
 {
     if (c->kind == ROK_LORENZ96 || c->curv) return ROK_ERR_UNSUPPORTED;
-    if (c->C.sutherland) return ROK_ERR_UNSUPPORTED;
     return ROK_OK;
 }
 

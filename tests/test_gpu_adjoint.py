@@ -32,6 +32,9 @@ def _cases():
     p = W.FlowProblem(**{**p.__dict__, 'ny': 36, 'ly': p.ly * 36 / 40})
     y = np.ascontiguousarray(y[:, :36, :] + 0.01 * W.random_smooth_state(p, seed=3))
     out = [('ns-40x36', p, y)]
+    # Sutherland's law, temperatures away from t_ref (g(T) = mu(T) / mu_ref != 1)
+    ps = W.FlowProblem(**{**p.__dict__, 'sutherland_s': 0.4, 't_ref': 0.5})
+    out.append(('ns-sutherland-40x36', ps, y))
     p, y = W.isentropic_vortex(33)
     out.append(('euler-33', p, y))
     return out
@@ -63,9 +66,11 @@ def test_residual_vjp_adjoint_identity_full_size(rok):
     assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
 
 
-@pytest.mark.parametrize('M', [0, 4, 10])
-def test_step_vjp_matches_oracle_adjoint(rok, M):
+@pytest.mark.parametrize('M,sutherland', [(0, False), (4, False), (10, False), (4, True)])
+def test_step_vjp_matches_oracle_adjoint(rok, M, sutherland):
     prob, y = W.taylor_green(24, reynolds=400.0)
+    if sutherland:
+        prob = W.FlowProblem(**{**prob.__dict__, 'sutherland_s': 0.4, 't_ref': 0.5})
     y = np.ascontiguousarray(y + 0.01 * W.random_smooth_state(prob, seed=5))
     h = I.dt_from_cfl(prob, y, 5.0)
     c = np.random.default_rng(M + 1).standard_normal(y.shape)

@@ -61,14 +61,23 @@ def test_residual_vjp_adjoint_identity_larger_grids():
         assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(u * core.jvp_exact(prob, yy, np.abs(v)))), (lhs, rhs)
 
 
-def test_residual_is_affine_in_the_viscosity():
+@pytest.mark.parametrize('sutherland', [False, True])
+def test_residual_is_affine_in_the_viscosity(sutherland):
+    # constant viscosity, and Sutherland's law with mu the viscosity at t_ref
+    # (a temperature field away from t_ref, so that g(T) != 1 matters)
     p, y = W.taylor_green(16, reynolds=200.0)
+    if sutherland:
+        p = W.FlowProblem(**{**p.__dict__, 'sutherland_s': 0.4, 't_ref': 0.5})
     d = A.residual_dmu(p, y)
     pa = W.FlowProblem(**{**p.__dict__, 'mu': 0.05})
     pb = W.FlowProblem(**{**p.__dict__, 'mu': 0.01})
     diff = core.residual(pa, y) - core.residual(pb, y)
     assert np.abs(diff - 0.04 * d).max() <= 1e-11 * np.abs(core.residual(pa, y)).max()
     assert np.abs(d).max() > 0.0
+    if sutherland:
+        # the derivative differs from the constant-viscosity one (g(T) enters)
+        pc = W.FlowProblem(**{**p.__dict__, 'sutherland_s': 0.0})
+        assert np.abs(d - A.residual_dmu(pc, y)).max() > 1e-3 * np.abs(d).max()
 
 
 def _step_derivative_cs(prob, y, h, M, d, c):
@@ -78,10 +87,12 @@ def _step_derivative_cs(prob, y, h, M, d, c):
 
 
 @pytest.mark.parametrize('M', [0, 3, 8])
-@pytest.mark.parametrize('case', ['tgv', 'vortex'])
+@pytest.mark.parametrize('case', ['tgv', 'tgv-sutherland', 'vortex'])
 def test_rok_step_vjp_matches_complex_step(case, M):
-    if case == 'tgv':
+    if case.startswith('tgv'):
         prob, y = W.taylor_green(16, reynolds=400.0)
+        if case == 'tgv-sutherland':
+            prob = W.FlowProblem(**{**prob.__dict__, 'sutherland_s': 0.4, 't_ref': 0.5})
         y = np.ascontiguousarray(y + 0.01 * W.random_smooth_state(prob, seed=5))
     else:
         prob, y = W.isentropic_vortex(16)
@@ -109,13 +120,15 @@ def test_rok_step_vjp_state_adjoint_reproduces_the_step_for_M0():
     assert abs(np.sum(yb * d) - fd) <= 1e-7 * abs(fd)
 
 
-@pytest.mark.parametrize('M', [0, 2, 6])
-def test_rok_step_vjp_viscosity_matches_complex_step(M):
+@pytest.mark.parametrize('M,sutherland', [(0, False), (2, False), (6, False), (2, True)])
+def test_rok_step_vjp_viscosity_matches_complex_step(M, sutherland):
     # f is affine in mu (pinned above), so f(y; mu + i d) = f(y; mu) + i d df/dmu(y)
     # continues the residual analytically in mu; the complex step through the
     # oracle's ROK4 step then gives dPhi/dmu exactly.  (Central differences in mu
     # do not converge here: the FD-JVP quotients re-round at every evaluation.)
     prob, y = W.taylor_green(16, reynolds=100.0)
+    if sutherland:
+        prob = W.FlowProblem(**{**prob.__dict__, 'sutherland_s': 0.4, 't_ref': 0.5})
     y = np.ascontiguousarray(y + 0.01 * W.random_smooth_state(prob, seed=6))
     h = I.dt_from_cfl(prob, y, 2.0)
     c = np.random.default_rng(2).standard_normal(y.shape)
