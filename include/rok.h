@@ -249,11 +249,17 @@ rok_status dopri5_integrate(rok_ctx *ctx, double *y, double T, const rok_adapt_o
  * by step: ybar_n = (d y_{n+1} / d y_n)^T ybar_{n+1}, plus each step's
  * viscosity part.  The derivative is that of the discrete step map (the
  * discrete adjoint), with the finite-difference increment eps of
- * Eq. matvecFD held constant.  Supported: uniform periodic grids (Euler, or
- * Navier-Stokes with constant viscosity or Sutherland's law), binary64 basis,
- * finite-difference JVPs; ROK_ERR_UNSUPPORTED otherwise.  "The viscosity" mu
- * is desc->mu: the constant viscosity, or the viscosity at t_ref under
- * Sutherland's law (mu(T) = mu g(T); the residual is affine in mu either way). */
+ * Eq. matvecFD held constant.  Supported: every problem and grid of
+ * rok_init with the binary64 basis and finite-difference JVPs (the reverse
+ * step of the binary32 basis or of the exact-JVP step returns
+ * ROK_ERR_UNSUPPORTED).  Uniform periodic grids take a hand-written reverse of
+ * the face fluxes (about the cost of two residuals); curvilinear grids and
+ * Lorenz-96 take J^T u from a compressed Jacobian: 4 px py exact JVPs (px for
+ * Lorenz-96), px and py the smallest divisors >= 5 of a periodic extent (the
+ * extent itself if none; 5 across walls and far fields), e.g. 160 JVPs per
+ * product on a 512 x 256 O-grid.  "The viscosity" mu is desc->mu: the
+ * constant viscosity, or the viscosity at t_ref under Sutherland's law
+ * (mu(T) = mu g(T); the residual is affine in mu either way). */
 
 /* ybar = J(y)^T ubar (the transposed Jacobian of the residual of
  * rok_residual) and, if mubar is non-NULL (HOST), mubar = ubar . df/dmu(y)

@@ -68,6 +68,9 @@ struct AdjWork {
     double *faces = nullptr;   // 16 x (nx ny) per direction
     double *prims = nullptr;   // rho, u, v, p, T of every cell (5 x nx ny)
     double *mupart = nullptr;  // CTA partials of the viscosity adjoint
+    // compressed-Jacobian products (curvilinear grids, Lorenz-96): class
+    // direction, its JVP, g = J^T u, reduction partials
+    double *cseed = nullptr, *cD = nullptr, *cg = nullptr, *cpart = nullptr;
     int nmu = 0;
     int rev_ctas = -1;         // CTAs of the cooperative reverse-MGS launch (0: pass by pass)
     AdjState *as = nullptr;
@@ -807,11 +810,176 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
         if (have[c]) store8(wb, e0[c], n, b[c]);
 }
 
+// ---- residual VJP by a compressed Jacobian (curvilinear grids, Lorenz-96) ----
+//
+// The residual of a cell depends only on cells at most two away along each
+// grid direction: MUSCL reaches two cells along a face normal, the viscous
+// gradients one cell across (the diamond's vertex values), the wall ghosts
+// mirror cells within two of the wall, and Lorenz-96 reads u_{i-2} .. u_{i+1}.
+// Cells whose indices agree modulo (px, py), both periods >= 5 (or the whole
+// periodic extent), therefore never enter the same residual row.  One exact
+// (dual-number) JVP along the direction that is 1 in variable q at every cell
+// of such a class gives, in each row within two cells of a class member, the
+// derivative of that row with respect to that member alone (the column
+// grouping of Curtis, Powell and Reid).  g = J^T u at the member is the sum
+// over those rows of D_r . u_r.  4 px py exact JVPs per product (px for
+// Lorenz-96), each g entry written once with a fixed summation order.
+
+// class period along a direction of n cells
+int class_period(int n, bool periodic)
+{
+    if (!periodic) return 5;
+    for (int p = 5; p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+// e = 1 in variable q at the cells i = ci (mod px), j = cj (mod py), else 0
+__global__ void __launch_bounds__(AT) seed_kernel(double *__restrict__ e, int nx, int ny, int ncomp, int q, int ci,
+                                                  int cj, int px, int py)
+{
+    const size_t nc = (size_t)nx * ny, n = nc * (size_t)ncomp;
+    for (size_t t = (size_t)blockIdx.x * AT + threadIdx.x; t < n; t += (size_t)gridDim.x * AT) {
+        const size_t cell = t % nc;
+        const int k = (int)(t / nc), i = (int)(cell % nx), j = (int)(cell / nx);
+        e[t] = (k == q && i % px == ci && j % py == cj) ? 1.0 : 0.0;
+    }
+}
+
+// the rows along one direction that a member at index m reaches: m - 2 .. m + 2
+// (wrapped when periodic, clipped otherwise), or all n rows of a periodic
+// direction shorter than 5 (each row once)
+__device__ __forceinline__ int row_of(int m, int o, int n, bool periodic, bool all)
+{
+    if (all) return o;
+    int r = m + o;
+    if (periodic) return ((r % n) + n) % n;
+    return (r < 0 || r >= n) ? -1 : r;
+}
+
+// g[q][c] = sum over the rows r that member c of class (ci, cj) reaches of
+// sum_k D[k][r] u[k][r]
+__global__ void __launch_bounds__(AT) gather_kernel(double *__restrict__ g, const double *__restrict__ D,
+                                                    const double *__restrict__ u, int nx, int ny, int ncomp, int q,
+                                                    int ci, int cj, int px, int py, int perx, int pery)
+{
+    const size_t nc = (size_t)nx * ny;
+    const int mx = (nx - ci + px - 1) / px, my = (ny - cj + py - 1) / py;
+    const bool allx = perx && nx < 5, ally = pery && ny < 5;
+    const int ox0 = allx ? 0 : -2, ox1 = allx ? nx - 1 : 2;
+    const int oy0 = ally ? 0 : -2, oy1 = ally ? ny - 1 : 2;
+    for (long long t = (long long)blockIdx.x * AT + threadIdx.x; t < (long long)mx * my;
+         t += (long long)gridDim.x * AT) {
+        const int i = ci + (int)(t % mx) * px, j = cj + (int)(t / mx) * py;
+        double sum = 0.0;
+        for (int oy = oy0; oy <= oy1; ++oy) {
+            const int rj = row_of(j, oy, ny, pery != 0, ally);
+            if (rj < 0) continue;
+            for (int ox = ox0; ox <= ox1; ++ox) {
+                const int ri = row_of(i, ox, nx, perx != 0, allx);
+                if (ri < 0) continue;
+                const size_t r = (size_t)rj * nx + ri;
+                for (int k = 0; k < ncomp; ++k) sum += D[(size_t)k * nc + r] * u[(size_t)k * nc + r];
+            }
+        }
+        g[(size_t)q * nc + (size_t)j * nx + i] = sum;
+    }
+}
+
+// out1 += s1 (* s1dev) g, out2 += s2 (* s2dev) g
+__global__ void __launch_bounds__(AT) vjp_apply_kernel(const VjpOut o, const double *__restrict__ g, size_t n)
+{
+    const double s1 = o.s1dev ? o.s1 * *o.s1dev : o.s1;
+    const double s2 = o.s2dev ? o.s2 * *o.s2dev : o.s2;
+    for (size_t e = (size_t)blockIdx.x * AT + threadIdx.x; e < n; e += (size_t)gridDim.x * AT) {
+        if (o.out1) o.out1[e] = o.out1[e] + s1 * g[e];
+        if (o.out2) o.out2[e] = o.out2[e] + s2 * g[e];
+    }
+}
+
+// the curvilinear residual launch with other constants (the viscosity derivative)
+rok_status curv_stencil_with(rok_ctx *c, const StencilConsts &Cx, const StencilIO &io)
+{
+    const cudaError_t e = c->strict ? strict::launch_curv(Cx, c->G, io, c->stream)
+                                    : fast::launch_curv(Cx, c->G, io, c->stream);
+    c->launches++;
+    return e == cudaSuccess ? ROK_OK : ROK_ERR_CUDA;
+}
+
+// the constants with the viscosity (at T_ref under Sutherland's law) set to mu
+StencilConsts with_mu(const StencilConsts &C0, double mu)
+{
+    StencilConsts C = C0;
+    C.mu = mu;
+    double g = 1.0;
+    if (C.sutherland) {
+        const double t = C.prim_inf[4] * C.inv_tref;
+        g = (t * sqrt(t)) * ((1.0 + C.suth_s) / (t + C.suth_s));
+    }
+    C.prim_inf[5] = mu * g;
+    set_fast_consts(C);
+    return C;
+}
+
+rok_status vjp_colored(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, const VjpOut &o,
+                       double *dst_mu, double mu_factor, const double *mu_dev, const double *dir,
+                       const double *dir_scale)
+{
+    const StencilConsts &C = c->C;
+    const bool lor = c->kind == ROK_LORENZ96;
+    const int nx = C.nx, ny = lor ? 1 : C.ny, ncomp = lor ? 1 : 4;
+    const bool perx = lor || C.bc[0] == ROK_BC_PERIODIC, pery = lor || C.bc[2] == ROK_BC_PERIODIC;
+    const int px = class_period(nx, perx), py = class_period(ny, pery);
+    const size_t N = c->N;
+    const int eg = c->egrid;
+    cudaStream_t s = c->stream;
+    rok_status r;
+    StencilIO io = rok_host::plain_io(c, ystate, A->cD);
+    if (dir) {   // the state y + (*dir_scale) dir, formed in the stencil's load stage
+        io.add[0] = dir;
+        io.coef[0] = 1.0;
+        io.coef_dev[0] = dir_scale;
+        io.nadd = 1;
+    }
+    for (int cj = 0; cj < py && cj < ny; ++cj)
+        for (int ci = 0; ci < px && ci < nx; ++ci) {
+            const int members = ((nx - ci + px - 1) / px) * ((ny - cj + py - 1) / py);
+            const int gb = (members + AT - 1) / AT;
+            for (int q = 0; q < ncomp; ++q) {
+                seed_kernel<<<eg, AT, 0, s>>>(A->cseed, nx, ny, ncomp, q, ci, cj, px, py);
+                StencilIO jo = io;
+                jo.dir = A->cseed;
+                if ((r = rok_host::launch_stencil(c, jo)) != ROK_OK) return r;
+                gather_kernel<<<gb, AT, 0, s>>>(A->cg, A->cD, ub, nx, ny, ncomp, q, ci, cj, px, py, perx, pery);
+                c->launches += 2;
+            }
+        }
+    vjp_apply_kernel<<<eg, AT, 0, s>>>(o, A->cg, N);
+    c->launches++;
+    if (dst_mu && !lor && C.viscous) {
+        // d f / d mu = f(y; mu = 1) - f(y; mu = 0): the residual is affine in mu
+        StencilIO fo = io;
+        fo.out = A->cD;
+        if ((r = curv_stencil_with(c, with_mu(C, 1.0), fo)) != ROK_OK) return r;
+        fo.out = A->cseed;
+        fo.sub = A->cD;
+        fo.s1 = -1.0;
+        if ((r = curv_stencil_with(c, with_mu(C, 0.0), fo)) != ROK_OK) return r;
+        CU(c->ops->dot2(ub, A->cseed, nullptr, nullptr, N, A->cpart, c->P, nullptr, s));
+        tree_add_kernel<<<1, AT, 0, s>>>(A->cpart, c->P, mu_factor, mu_dev, dst_mu);
+        c->launches += 2;
+    }
+    CU(cudaGetLastError());
+    return ROK_OK;
+}
+
 // residual VJP launches: out1 += s1 g, out2 += s2 g with g = J(ystate)^T ubar;
 // dst_mu += mu_factor (* mu_dev) ubar . df/dmu(ystate)
 rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, const VjpOut &o, double *dst_mu,
                double mu_factor, const double *mu_dev, const double *dir = nullptr, const double *dir_scale = nullptr)
 {
+    if (c->curv || c->kind == ROK_LORENZ96)
+        return vjp_colored(c, A, ystate, ub, o, dst_mu, mu_factor, mu_dev, dir, dir_scale);
     const StencilConsts &C = c->C;
     const size_t nc = (size_t)C.nx * C.ny;
     const int nb = (int)((nc + AT - 1) / AT);
@@ -843,7 +1011,7 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
 
 rok_status vjp_supported(const rok_ctx *c)
 {
-    if (c->kind == ROK_LORENZ96 || c->curv) return ROK_ERR_UNSUPPORTED;
+    (void)c;   // every grid and problem kind (compressed Jacobian off uniform grids)
     return ROK_OK;
 }
 
@@ -856,6 +1024,7 @@ void free_work(AdjWork *A)
     cudaFree(A->wb); cudaFree(A->wcur); cudaFree(A->wlast); cudaFree(A->Yt); cudaFree(A->y1);
     cudaFree(A->pA); cudaFree(A->pB); cudaFree(A->pM);
     cudaFree(A->faces); cudaFree(A->prims); cudaFree(A->mupart); cudaFree(A->as);
+    cudaFree(A->cseed); cudaFree(A->cD); cudaFree(A->cg); cudaFree(A->cpart);
     cudaFreeHost(A->h_st); cudaFreeHost(A->h_mub);
     delete A;
 }
@@ -877,6 +1046,8 @@ rok_status ensure_work(rok_ctx *c, bool full)
              cudaMalloc(&A->as, sizeof(AdjState)) == cudaSuccess &&
              cudaMallocHost(&A->h_mub, sizeof(double)) == cudaSuccess;
     }
+    if (ok && (c->curv || c->kind == ROK_LORENZ96) && !A->cseed)
+        ok = al(&A->cseed, N) && al(&A->cD, N) && al(&A->cg, N) && al(&A->cpart, (size_t)c->P);
     if (ok && full) {
         ok = al(&A->Vb, (size_t)(c->mmax > 0 ? c->mmax : 1) * N) && al(&A->yb, N) && al(&A->Fb, N) &&
              al(&A->F1b, N) && al(&A->F1acc, N) && al(&A->wb, N) && al(&A->wcur, N) && al(&A->wlast, N) &&

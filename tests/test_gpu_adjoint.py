@@ -37,6 +37,20 @@ def _cases():
     out.append(('ns-sutherland-40x36', ps, y))
     p, y = W.isentropic_vortex(33)
     out.append(('euler-33', p, y))
+    # off uniform periodic grids: the compressed-Jacobian product
+    out.extend(_off_uniform_cases())
+    return out
+
+
+def _off_uniform_cases():
+    xv, yv = W.perturbed_box_grid(40, 36, 2.0, 1.8, amp=0.3, seed=4)
+    p3 = W.FlowProblem(kind=W.NAVIER_STOKES, nx=40, ny=36, xv=xv, yv=yv, mu=0.02)
+    out = [('curv-40x36', p3, W.random_smooth_state(p3, seed=7, amp=0.08))]
+    # O-grid 32 x 16 (periodic in theta, wall and far field), Sutherland's law
+    p4, y4, _ = W.cylinder_ogrid(16, 32)
+    out.append(('ogrid-32x16', p4, np.ascontiguousarray(y4 + 0.02 * W.random_smooth_state(p4, seed=2))))
+    p5, y5 = W.lorenz96(40)
+    out.append(('lorenz-40', p5, y5))
     return out
 
 
@@ -171,12 +185,35 @@ def test_gradient_wrt_viscosity_with_checkpoints_matches_oracle_complex_step(rok
     assert abs(gmu - csm) <= 1e-5 * abs(csm), (gmu, csm)
 
 
+@pytest.mark.parametrize('name', ['ogrid-32x16', 'lorenz-40'])
+@pytest.mark.parametrize('mode', ['strict', 'fast'])
+def test_step_vjp_off_uniform_grids_matches_oracle_adjoint(rok, name, mode):
+    prob, y = {c[0]: (c[1], c[2]) for c in _off_uniform_cases()}[name]
+    M = 4
+    h = I.dt_from_cfl(prob, y, 2.0) if prob.kind != 2 else 0.01
+    c = np.random.default_rng(11).standard_normal(y.shape)
+    ctx = rok.rok_init(prob, krylov_max=M, rounding=getattr(rok, 'ROK_ROUND_' + mode.upper()))
+    yb, mub = rok.rok_step_vjp(ctx, dev(y), h, M, dev(c))
+    ref, mref = A.rok_step_vjp(prob, y, h, M, c)
+    yb = host(yb)
+    err = np.linalg.norm(yb - ref) / np.linalg.norm(ref)
+    print(name, mode, 'relative L2 of ybar', err, 'mubar', mub, mref)
+    assert err <= 1e-5, err
+    if prob.kind == 2:
+        assert mub == 0.0 and mref == 0.0
+    else:
+        assert abs(mub - mref) <= 1e-5 * abs(mref), (mub, mref)
+
+
 def test_vjp_unsupported_cases(rok):
-    p4, y4, _ = W.cylinder_ogrid(16, 32)
-    ctx = rok.rok_init(p4, krylov_max=4)
-    with pytest.raises(rok.RokError) as e:
-        rok.rok_vjp(ctx, dev(y4), dev(y4))
-    assert e.value.status == rok.ROK_ERR_UNSUPPORTED
+    # the reverse step of the binary32 basis and of the exact-JVP step
+    prob, y = W.taylor_green(24, reynolds=400.0)
+    h = I.dt_from_cfl(prob, y, 2.0)
+    for kw in ({'basis': rok.ROK_BASIS_FP32}, {'jvp': rok.ROK_JVP_EXACT}):
+        ctx = rok.rok_init(prob, krylov_max=4, **kw)
+        with pytest.raises(rok.RokError) as e:
+            rok.rok_step_vjp(ctx, dev(y), h, 4, dev(y))
+        assert e.value.status == rok.ROK_ERR_UNSUPPORTED
 
 
 def _ns_case():

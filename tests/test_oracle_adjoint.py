@@ -87,16 +87,23 @@ def _step_derivative_cs(prob, y, h, M, d, c):
 
 
 @pytest.mark.parametrize('M', [0, 3, 8])
-@pytest.mark.parametrize('case', ['tgv', 'tgv-sutherland', 'vortex'])
+@pytest.mark.parametrize('case', ['tgv', 'tgv-sutherland', 'vortex', 'ogrid', 'lorenz'])
 def test_rok_step_vjp_matches_complex_step(case, M):
     if case.startswith('tgv'):
         prob, y = W.taylor_green(16, reynolds=400.0)
         if case == 'tgv-sutherland':
             prob = W.FlowProblem(**{**prob.__dict__, 'sutherland_s': 0.4, 't_ref': 0.5})
         y = np.ascontiguousarray(y + 0.01 * W.random_smooth_state(prob, seed=5))
+    elif case == 'ogrid':
+        # curvilinear, wall and far field, Sutherland's law
+        prob, y, _ = W.cylinder_ogrid(6, 16)
+        y = np.ascontiguousarray(y + 0.02 * W.random_smooth_state(prob, seed=2))
+    elif case == 'lorenz':
+        prob, y = W.lorenz96(12)
     else:
         prob, y = W.isentropic_vortex(16)
-    h = I.dt_from_cfl(prob, y, 5.0)
+    # (CFL 1 on the O-grid: the M = 0 step is explicit RK4 there)
+    h = 0.01 if case == 'lorenz' else I.dt_from_cfl(prob, y, 1.0 if case == 'ogrid' else 5.0)
     rng = np.random.default_rng(M)
     d = rng.standard_normal(y.shape)
     c = rng.standard_normal(y.shape)
