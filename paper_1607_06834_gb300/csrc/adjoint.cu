@@ -69,7 +69,7 @@ struct AdjWork {
     double *prims = nullptr;   // rho, u, v, p, T of every cell (5 x nx ny)
     double *mupart = nullptr;  // CTA partials of the viscosity adjoint
     // compressed-Jacobian products (curvilinear grids, Lorenz-96): class
-    // direction, its JVP, g = J^T u, reduction partials
+    // direction, its JVP, g = J^T u, reduction partials (2P: dot2 writes both sets)
     double *cseed = nullptr, *cD = nullptr, *cg = nullptr, *cpart = nullptr;
     int nmu = 0;
     int rev_ctas = -1;         // CTAs of the cooperative reverse-MGS launch (0: pass by pass)
@@ -1047,7 +1047,7 @@ rok_status ensure_work(rok_ctx *c, bool full)
              cudaMallocHost(&A->h_mub, sizeof(double)) == cudaSuccess;
     }
     if (ok && (c->curv || c->kind == ROK_LORENZ96) && !A->cseed)
-        ok = al(&A->cseed, N) && al(&A->cD, N) && al(&A->cg, N) && al(&A->cpart, (size_t)c->P);
+        ok = al(&A->cseed, N) && al(&A->cD, N) && al(&A->cg, N) && al(&A->cpart, 2 * (size_t)c->P);
     if (ok && full) {
         ok = al(&A->Vb, (size_t)(c->mmax > 0 ? c->mmax : 1) * N) && al(&A->yb, N) && al(&A->Fb, N) &&
              al(&A->F1b, N) && al(&A->F1acc, N) && al(&A->wb, N) && al(&A->wcur, N) && al(&A->wlast, N) &&
