@@ -252,12 +252,13 @@ rok_status dopri5_integrate(rok_ctx *ctx, double *y, double T, const rok_adapt_o
  * Eq. matvecFD held constant.  Supported: every problem and grid of
  * rok_init with the binary64 basis and finite-difference JVPs (the reverse
  * step of the binary32 basis or of the exact-JVP step returns
- * ROK_ERR_UNSUPPORTED).  Uniform periodic grids take a hand-written reverse of
- * the face fluxes (about the cost of two residuals); curvilinear grids and
- * Lorenz-96 take J^T u from a compressed Jacobian: 4 px py exact JVPs (px for
- * Lorenz-96), px and py the smallest divisors >= 5 of a periodic extent (the
- * extent itself if none; 5 across walls and far fields), e.g. 160 JVPs per
- * product on a 512 x 256 O-grid.  "The viscosity" mu is desc->mu: the
+ * ROK_ERR_UNSUPPORTED).  Euler / Navier-Stokes grids take a hand-written
+ * reverse sweep of the face fluxes (uniform and curvilinear, every boundary
+ * condition; a few residuals' cost per product); Lorenz-96 and curvilinear
+ * grids of fewer than 2 cells in a direction take J^T u from a compressed
+ * Jacobian: 4 px py exact JVPs (px for Lorenz-96), px and py the smallest
+ * divisors >= 5 of a periodic extent (the extent itself if none; 5 across
+ * walls and far fields).  "The viscosity" mu is desc->mu: the
  * constant viscosity, or the viscosity at t_ref under Sutherland's law
  * (mu(T) = mu g(T); the residual is affine in mu either way). */
 

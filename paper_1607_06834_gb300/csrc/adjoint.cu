@@ -68,9 +68,11 @@ struct AdjWork {
     double *faces = nullptr;   // 16 x (nx ny) per direction
     double *prims = nullptr;   // rho, u, v, p, T of every cell (5 x nx ny)
     double *mupart = nullptr;  // CTA partials of the viscosity adjoint
-    // compressed-Jacobian products (curvilinear grids, Lorenz-96): class
-    // direction, its JVP, g = J^T u, reduction partials (2P: dot2 writes both sets)
+    // compressed-Jacobian products (Lorenz-96, curvilinear grids below 2 x 2):
+    // class direction, its JVP, g = J^T u, reduction partials (2P: dot2 writes both sets)
     double *cseed = nullptr, *cD = nullptr, *cg = nullptr, *cpart = nullptr;
+    // curvilinear reverse sweep: 17 values per face, CTA partials of the viscosity adjoint
+    double *cfaces = nullptr, *cmupart = nullptr;
     int nmu = 0;
     int rev_ctas = -1;         // CTAs of the cooperative reverse-MGS launch (0: pass by pass)
     AdjState *as = nullptr;
@@ -810,7 +812,7 @@ __global__ void __launch_bounds__(RT, 2) mgsrev_column_kernel(double *__restrict
         if (have[c]) store8(wb, e0[c], n, b[c]);
 }
 
-// ---- residual VJP by a compressed Jacobian (curvilinear grids, Lorenz-96) ----
+// ---- residual VJP by a compressed Jacobian (Lorenz-96, tiny curvilinear grids) ----
 //
 // The residual of a cell depends only on cells at most two away along each
 // grid direction: MUSCL reaches two cells along a face normal, the viscous
@@ -973,13 +975,378 @@ rok_status vjp_colored(rok_ctx *c, AdjWork *A, const double *ystate, const doubl
     return ROK_OK;
 }
 
+// ---- residual VJP on curvilinear grids: hand-written reverse sweep ----------
+//
+// The residual of a curvilinear grid (Sec. 3.2) is f_c = -(sum of the outward
+// face fluxes F_f l_f) / V_c, each face flux the Roe flux of the MUSCL states
+// through the face normal minus the viscous flux, whose gradients come from
+// the diamond around the face (the two cells and the two vertices, a vertex
+// value the mean of its four cells).  Boundary cells read ghosts: a periodic
+// image, a wall mirror (velocity negated) or the free stream; a corner ghost
+// applies the rule of the i-direction first, then that of the j-direction.
+// Pass 1 (one thread per face) takes Fbar = l_f (ubar_R / V_R - ubar_L / V_L)
+// back through one face: the Roe flux in the face's (normal, tangential)
+// frame by the reverse sweep of the uniform grids, rotated back, and the
+// viscous flux by hand; it stores 17 values a face: the adjoints of the two
+// MUSCL states (8), of the cell differences and the vertex differences of
+// u, v, T (6), of the face velocity (2) and of the face viscosity (1).
+// Pass 2 (one thread per cell) gathers, in a fixed order, what every face
+// gave to the cell and to each ghost that images it (mirrored adjoints
+// negate u and v), and maps primitive adjoints to conserved ones.
+constexpr int kCurvFaceVals = 17;
+
+// source of an extended index e of a direction of n cells with boundary
+// conditions lo / hi: the interior index, whether a wall mirrors it, or the
+// free stream
+struct ExtSrc {
+    int i;
+    bool flip, inf;
+};
+__device__ __forceinline__ ExtSrc ext_src1(int e, int n, int lo, int hi)
+{
+    if (e < 0) {
+        if (lo == ROK_BC_PERIODIC) return {e + n, false, false};
+        if (lo == ROK_BC_WALL) return {-1 - e, true, false};
+        return {0, false, true};
+    }
+    if (e >= n) {
+        if (hi == ROK_BC_PERIODIC) return {e - n, false, false};
+        if (hi == ROK_BC_WALL) return {2 * n - 1 - e, true, false};
+        return {0, false, true};
+    }
+    return {e, false, false};
+}
+
+// primitives (rho, u, v, p, T) of extended cell (ei, ej), ghosts included
+__device__ __forceinline__ void ext_prim(const StencilConsts &C, const double *__restrict__ pr, size_t nc, int ei,
+                                         int ej, double *w)
+{
+    const ExtSrc si = ext_src1(ei, C.nx, C.bc[0], C.bc[1]);
+    bool flip = si.flip, inf = si.inf;
+    int sj = 0;
+    if (!inf) {
+        const ExtSrc s2 = ext_src1(ej, C.ny, C.bc[2], C.bc[3]);
+        flip = flip != s2.flip;
+        inf = s2.inf;
+        sj = s2.i;
+    }
+    if (inf) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[k] = C.prim_inf[k];
+    } else {
+        const size_t c = (size_t)sj * C.nx + si.i;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[k] = pr[k * nc + c];
+    }
+    if (flip) {
+        w[1] = -w[1];
+        w[2] = -w[2];
+    }
+}
+
+// u, v, T at vertex (vi, vj): the mean of its four cells, in the oracle's order
+__device__ __forceinline__ void vertex_uvT(const StencilConsts &C, const double *__restrict__ pr, size_t nc, int vi,
+                                           int vj, double *o)
+{
+    double a[5], b[5], c[5], d[5];
+    ext_prim(C, pr, nc, vi - 1, vj - 1, a);
+    ext_prim(C, pr, nc, vi, vj - 1, b);
+    ext_prim(C, pr, nc, vi - 1, vj, c);
+    ext_prim(C, pr, nc, vi, vj, d);
+    o[0] = 0.25 * (((a[1] + b[1]) + c[1]) + d[1]);
+    o[1] = 0.25 * (((a[2] + b[2]) + c[2]) + d[2]);
+    o[2] = 0.25 * (((a[4] + b[4]) + c[4]) + d[4]);
+}
+
+// Pass 1 of a curvilinear grid: faces of direction D (0: i-faces, face (i, j)
+// between cells (i-1, j) and (i, j), (nx+1) ny of them; 1: j-faces, face (i, j)
+// between (i, j-1) and (i, j), nx (ny+1) of them).  fa[q * nf + f], q < 17
+// (q < 8 without viscosity); one partial of ubar . df/dmu per CTA.
+template <bool VISC, bool SUTH, int D>
+__global__ void __launch_bounds__(FT, 7)
+    curv_vjp_face_kernel(const StencilConsts C, const CurvGeom G, const double *__restrict__ pr,
+                         const double *__restrict__ ub, double *__restrict__ fa, double *__restrict__ mupart)
+{
+    static_assert(FT == 64, "the CTA sum below adds two warp sums");
+    __shared__ double sh[2];
+    const int nx = C.nx, ny = C.ny;
+    const size_t nc = (size_t)nx * ny;
+    const int fw = D == 0 ? nx + 1 : nx;   // faces per row
+    const size_t nf = D == 0 ? (size_t)(nx + 1) * ny : (size_t)nx * (ny + 1);
+    const size_t t = (size_t)blockIdx.x * FT + threadIdx.x;
+    double mu_c = 0.0;
+    if (t < nf) {
+        const int i = (int)(t % fw), j = (int)(t / fw);
+        // the four cells along the grid line, the face between the middle two
+        double m2[5], m1[5], p1[5], p2[5];
+        if (D == 0) {
+            ext_prim(C, pr, nc, i - 2, j, m2);
+            ext_prim(C, pr, nc, i - 1, j, m1);
+            ext_prim(C, pr, nc, i, j, p1);
+            ext_prim(C, pr, nc, i + 1, j, p2);
+        } else {
+            ext_prim(C, pr, nc, i, j - 2, m2);
+            ext_prim(C, pr, nc, i, j - 1, m1);
+            ext_prim(C, pr, nc, i, j, p1);
+            ext_prim(C, pr, nc, i, j + 1, p2);
+        }
+        const double nxf = D == 0 ? G.in_x[t] : G.jn_x[t], nyf = D == 0 ? G.in_y[t] : G.jn_y[t];
+        const double len = D == 0 ? G.il[t] : G.jl[t];
+        // Fbar = l (ubar_R / V_R - ubar_L / V_L) over the interior neighbours
+        const int li = D == 0 ? i - 1 : i, lj = D == 0 ? j : j - 1;
+        const bool lin = li >= 0 && lj >= 0, rin = i < nx && j < ny;
+        const size_t lc = lin ? (size_t)lj * nx + li : 0, rc = rin ? (size_t)j * nx + i : 0;
+        double Fb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double r = rin ? ub[k * nc + rc] * G.inv_vol[rc] : 0.0;
+            const double l = lin ? ub[k * nc + lc] * G.inv_vol[lc] : 0.0;
+            Fb[k] = len * (r - l);
+        }
+        double WL[4], WR[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) muscl(m2[k], m1[k], p1[k], p2[k], C.c_lo, C.c_hi, WL[k], WR[k]);
+        // Roe flux in the frame (n, t), t = (-ny, nx): the x-direction flux of the
+        // rotated states, rotated back (the flux is invariant under rotation)
+        {
+            const double Lr[4] = {WL[0], WL[1] * nxf + WL[2] * nyf, -WL[1] * nyf + WL[2] * nxf, WL[3]};
+            const double Rr[4] = {WR[0], WR[1] * nxf + WR[2] * nyf, -WR[1] * nyf + WR[2] * nxf, WR[3]};
+            const double Fbr[4] = {Fb[0], Fb[1] * nxf + Fb[2] * nyf, -Fb[1] * nyf + Fb[2] * nxf, Fb[3]};
+            double Lb[4], Rb[4];
+            roe_vjp<0>(Lr, Rr, C, Fbr, Lb, Rb);
+            fa[0 * nf + t] = Lb[0];
+            fa[1 * nf + t] = Lb[1] * nxf - Lb[2] * nyf;
+            fa[2 * nf + t] = Lb[1] * nyf + Lb[2] * nxf;
+            fa[3 * nf + t] = Lb[3];
+            fa[4 * nf + t] = Rb[0];
+            fa[5 * nf + t] = Rb[1] * nxf - Rb[2] * nyf;
+            fa[6 * nf + t] = Rb[1] * nyf + Rb[2] * nxf;
+            fa[7 * nf + t] = Rb[3];
+        }
+        if (VISC) {
+            // diamond gradients: g = dC (c0, c2) + dV (c1, c3) for u, v, T; dC
+            // across the face (cells), dV along it (vertex P3 minus vertex P1)
+            double va[3], vb[3];
+            if (D == 0) {
+                vertex_uvT(C, pr, nc, i, j, va);
+                vertex_uvT(C, pr, nc, i, j + 1, vb);
+            } else {
+                vertex_uvT(C, pr, nc, i + 1, j, va);
+                vertex_uvT(C, pr, nc, i, j, vb);
+            }
+            const double c0 = D == 0 ? G.ic0[t] : G.jc0[t], c1 = D == 0 ? G.ic1[t] : G.jc1[t];
+            const double c2 = D == 0 ? G.ic2[t] : G.jc2[t], c3 = D == 0 ? G.ic3[t] : G.jc3[t];
+            const double dC[3] = {p1[1] - m1[1], p1[2] - m1[2], p1[4] - m1[4]};
+            const double dV[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
+            const double ux = dC[0] * c0 + dV[0] * c1, uy = dC[0] * c2 + dV[0] * c3;
+            const double vx = dC[1] * c0 + dV[1] * c1, vy = dC[1] * c2 + dV[1] * c3;
+            const double Tx = dC[2] * c0 + dV[2] * c1, Ty = dC[2] * c2 + dV[2] * c3;
+            // face viscosity mu_ref gf (gf = 1 for a constant viscosity)
+            double gf = 1.0;
+            if (SUTH) {
+                double dgl, dgr;
+                gf = 0.5 * (suth_g(C, m1[4], dgl) + suth_g(C, p1[4], dgr));
+            }
+            const double mu = SUTH ? C.mu * gf : C.mu;
+            const double div = ux + vy;
+            const double sxx = 2.0 * ux - C.c23 * div, syy = 2.0 * vy - C.c23 * div, sxy = uy + vx;
+            const double snx = sxx * nxf + sxy * nyf, sny = sxy * nxf + syy * nyf;
+            const double dTn = Tx * nxf + Ty * nyf;
+            const double uf = 0.5 * (m1[1] + p1[1]), vf = 0.5 * (m1[2] + p1[2]);
+            // F -= Fv: Fv = mu (0, snx, sny, uf snx + vf sny + kfac dTn)
+            const double Fv1b = -Fb[1], Fv2b = -Fb[2], Fv3b = -Fb[3];
+            const double snxb = mu * (Fv1b + uf * Fv3b), snyb = mu * (Fv2b + vf * Fv3b);
+            const double dTnb = (mu * C.kfac) * Fv3b;
+            const double mufb = (Fv1b * snx + Fv2b * sny) + Fv3b * ((uf * snx + vf * sny) + C.kfac * dTn);
+            const double sxxb = snxb * nxf, syyb = snyb * nyf, sxyb = snxb * nyf + snyb * nxf;
+            const double uxb = 2.0 * sxxb - C.c23 * (sxxb + syyb), vyb = 2.0 * syyb - C.c23 * (sxxb + syyb);
+            const double uyb = sxyb, vxb = sxyb, Txb = dTnb * nxf, Tyb = dTnb * nyf;
+            fa[8 * nf + t] = uxb * c0 + uyb * c2;    // dC of u
+            fa[9 * nf + t] = vxb * c0 + vyb * c2;    // dC of v
+            fa[10 * nf + t] = Txb * c0 + Tyb * c2;   // dC of T
+            fa[11 * nf + t] = uxb * c1 + uyb * c3;   // dV of u
+            fa[12 * nf + t] = vxb * c1 + vyb * c3;   // dV of v
+            fa[13 * nf + t] = Txb * c1 + Tyb * c3;   // dV of T
+            fa[14 * nf + t] = mu * snx * Fv3b;       // face u
+            fa[15 * nf + t] = mu * sny * Fv3b;       // face v
+            fa[16 * nf + t] = mufb;                  // face viscosity
+            mu_c = SUTH ? mufb * gf : mufb;          // d mu_f / d mu_ref = gf
+        }
+    }
+    const double s = lane_tree(mu_c);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) mupart[blockIdx.x] = sh[0] + sh[1];
+}
+
+// the extended indices of a direction (n >= 2 cells, boundary conditions
+// lo / hi) that image interior index i: itself and the ghosts copied or
+// mirrored from it (at most one on each side: the two ghost layers of a side
+// come from different interior indices)
+__device__ __forceinline__ int ext_images(int i, int n, int lo, int hi, int *e, bool *flip)
+{
+    int k = 0;
+    e[k] = i;
+    flip[k++] = false;
+#pragma unroll
+    for (int g = 1; g <= 2; ++g) {
+        if (lo == ROK_BC_PERIODIC && i == n - g) { e[k] = -g; flip[k++] = false; }
+        if (lo == ROK_BC_WALL && i == g - 1) { e[k] = -g; flip[k++] = true; }
+        if (hi == ROK_BC_PERIODIC && i == g - 1) { e[k] = n - 1 + g; flip[k++] = false; }
+        if (hi == ROK_BC_WALL && i == n - g) { e[k] = n - 1 + g; flip[k++] = true; }
+    }
+    return k;
+}
+
+// Pass 2 of a curvilinear grid: g = J^T ubar at each cell from the face values
+// (fx: i-faces, fy: j-faces); out1 += s1 g, out2 += s2 g
+template <bool VISC, bool SUTH>
+__global__ void __launch_bounds__(AT) curv_vjp_cell_kernel(const StencilConsts C, const double *__restrict__ pr,
+                                                           const double *__restrict__ fx,
+                                                           const double *__restrict__ fy, const VjpOut o)
+{
+    const int nx = C.nx, ny = C.ny;
+    const size_t nc = (size_t)nx * ny;
+    const size_t nfx = (size_t)(nx + 1) * ny, nfy = (size_t)nx * (ny + 1);
+    const size_t t = (size_t)blockIdx.x * AT + threadIdx.x;
+    if (t >= nc) return;
+    const int i = (int)(t % nx), j = (int)(t / nx);
+    // face values, 0 where the face does not exist
+    auto FX = [&](int q, int a, int b) -> double {
+        return (a >= 0 && a <= nx && b >= 0 && b < ny) ? fx[q * nfx + (size_t)b * (nx + 1) + a] : 0.0;
+    };
+    auto FY = [&](int q, int a, int b) -> double {
+        return (a >= 0 && a < nx && b >= 0 && b <= ny) ? fy[q * nfy + (size_t)b * nx + a] : 0.0;
+    };
+    const double a1 = (1.0 + C.c_lo) - C.c_hi;
+    int ex[3], ey[3];
+    bool flx[3], fly[3];
+    const int nix = ext_images(i, nx, C.bc[0], C.bc[1], ex, flx);
+    const int niy = ext_images(j, ny, C.bc[2], C.bc[3], ey, fly);
+    double Pb[4] = {0.0, 0.0, 0.0, 0.0}, Tb = 0.0, mub = 0.0;
+    for (int a = 0; a < nix; ++a)
+        for (int b = 0; b < niy; ++b) {
+            const int ei = ex[a], ej = ey[b];
+            double pb[4] = {0.0, 0.0, 0.0, 0.0}, tb = 0.0;
+            // MUSCL: the cell is m2 of face e+2, m1 of face e+1, p1 of face e, p2 of face e-1
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double s = -C.c_lo * FX(k, ei + 2, ej);
+                s = s + (a1 * FX(k, ei + 1, ej) + C.c_hi * FX(k + 4, ei + 1, ej));
+                s = s + (C.c_hi * FX(k, ei, ej) + a1 * FX(k + 4, ei, ej));
+                s = s - C.c_lo * FX(k + 4, ei - 1, ej);
+                s = s - C.c_lo * FY(k, ei, ej + 2);
+                s = s + (a1 * FY(k, ei, ej + 1) + C.c_hi * FY(k + 4, ei, ej + 1));
+                s = s + (C.c_hi * FY(k, ei, ej) + a1 * FY(k + 4, ei, ej));
+                s = s - C.c_lo * FY(k + 4, ei, ej - 1);
+                pb[k] = s;
+            }
+            if (VISC) {
+                // right cell of faces (ei, ej) [i] and (ei, ej) [j], left cell of
+                // faces (ei + 1, ej) [i] and (ei, ej + 1) [j]
+                pb[1] += ((FX(8, ei, ej) - FX(8, ei + 1, ej)) + 0.5 * (FX(14, ei, ej) + FX(14, ei + 1, ej))) +
+                         ((FY(8, ei, ej) - FY(8, ei, ej + 1)) + 0.5 * (FY(14, ei, ej) + FY(14, ei, ej + 1)));
+                pb[2] += ((FX(9, ei, ej) - FX(9, ei + 1, ej)) + 0.5 * (FX(15, ei, ej) + FX(15, ei + 1, ej))) +
+                         ((FY(9, ei, ej) - FY(9, ei, ej + 1)) + 0.5 * (FY(15, ei, ej) + FY(15, ei, ej + 1)));
+                tb += (FX(10, ei, ej) - FX(10, ei + 1, ej)) + (FY(10, ei, ej) - FY(10, ei, ej + 1));
+                if (SUTH)
+                    mub += 0.5 * ((FX(16, ei, ej) + FX(16, ei + 1, ej)) + (FY(16, ei, ej) + FY(16, ei, ej + 1)));
+                // vertex (vi, vj) is P1 of i-face (vi, vj) and of j-face (vi - 1, vj),
+                // P3 of i-face (vi, vj - 1) and of j-face (vi, vj); the cell is one
+                // of the four around vertices (ei, ej), (ei+1, ej), (ei, ej+1), (ei+1, ej+1)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int vi = ei + (v & 1), vj = ej + (v >> 1);
+                        s += ((FX(11 + q, vi, vj - 1) - FX(11 + q, vi, vj)) +
+                              (FY(11 + q, vi, vj) - FY(11 + q, vi - 1, vj)));
+                    }
+                    if (q < 2) pb[1 + q] += 0.25 * s;
+                    else tb += 0.25 * s;
+                }
+            }
+            const double sg = (flx[a] != fly[b]) ? -1.0 : 1.0;   // a mirror image negates u and v
+            Pb[0] += pb[0];
+            Pb[1] += sg * pb[1];
+            Pb[2] += sg * pb[2];
+            Pb[3] += pb[3];
+            Tb += tb;
+        }
+    double P[4], T;
+    prim_load(pr, nc, t, P, T);
+    if (SUTH) {
+        double dg;
+        suth_g(C, T, dg);
+        Tb += mub * (C.mu * dg);
+    }
+    const double rho = P[0], u = P[1], v = P[2];
+    const double rinv = 1.0 / rho;
+    // T = p / rho
+    Pb[3] += Tb * rinv;
+    Pb[0] -= Tb * T * rinv;
+    double qb[4];
+    qb[0] = (Pb[0] - (u * Pb[1] + v * Pb[2]) * rinv) + C.gm1 * 0.5 * (u * u + v * v) * Pb[3];
+    qb[1] = Pb[1] * rinv - C.gm1 * u * Pb[3];
+    qb[2] = Pb[2] * rinv - C.gm1 * v * Pb[3];
+    qb[3] = C.gm1 * Pb[3];
+    const double s1 = o.s1dev ? o.s1 * *o.s1dev : o.s1;
+    const double s2 = o.s2dev ? o.s2 * *o.s2dev : o.s2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const size_t e = (size_t)k * nc + t;
+        if (o.out1) o.out1[e] = o.out1[e] + s1 * qb[k];
+        if (o.out2) o.out2[e] = o.out2[e] + s2 * qb[k];
+    }
+}
+
+// the reverse sweep covers curvilinear grids of at least 2 x 2 cells; smaller
+// ones and Lorenz-96 take the compressed Jacobian
+bool curv_sweep(const rok_ctx *c) { return c->curv && c->C.nx >= 2 && c->C.ny >= 2; }
+bool colored(const rok_ctx *c) { return c->kind == ROK_LORENZ96 || (c->curv && !curv_sweep(c)); }
+
+rok_status vjp_curv(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, const VjpOut &o,
+                    double *dst_mu, double mu_factor, const double *mu_dev, const double *dir,
+                    const double *dir_scale)
+{
+    const StencilConsts &C = c->C;
+    const size_t nc = c->nc;
+    const size_t nfx = (size_t)(C.nx + 1) * C.ny, nfy = (size_t)C.nx * (C.ny + 1);
+    const int nb = (int)((nc + AT - 1) / AT);
+    const int gx = (int)((nfx + FT - 1) / FT), gy = (int)((nfy + FT - 1) / FT);
+    double *fxa = A->cfaces, *fya = A->cfaces + kCurvFaceVals * nfx;
+    cudaStream_t s = c->stream;
+    prim_kernel<<<nb, AT, 0, s>>>(C, ystate, dir, dir_scale, A->prims);
+    if (C.viscous && C.sutherland) {
+        curv_vjp_face_kernel<true, true, 0><<<gx, FT, 0, s>>>(C, c->G, A->prims, ub, fxa, A->cmupart);
+        curv_vjp_face_kernel<true, true, 1><<<gy, FT, 0, s>>>(C, c->G, A->prims, ub, fya, A->cmupart + gx);
+        curv_vjp_cell_kernel<true, true><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
+    } else if (C.viscous) {
+        curv_vjp_face_kernel<true, false, 0><<<gx, FT, 0, s>>>(C, c->G, A->prims, ub, fxa, A->cmupart);
+        curv_vjp_face_kernel<true, false, 1><<<gy, FT, 0, s>>>(C, c->G, A->prims, ub, fya, A->cmupart + gx);
+        curv_vjp_cell_kernel<true, false><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
+    } else {
+        curv_vjp_face_kernel<false, false, 0><<<gx, FT, 0, s>>>(C, c->G, A->prims, ub, fxa, A->cmupart);
+        curv_vjp_face_kernel<false, false, 1><<<gy, FT, 0, s>>>(C, c->G, A->prims, ub, fya, A->cmupart + gx);
+        curv_vjp_cell_kernel<false, false><<<nb, AT, 0, s>>>(C, A->prims, fxa, fya, o);
+    }
+    c->launches += 4;
+    if (dst_mu && C.viscous) {
+        tree_add_kernel<<<1, AT, 0, s>>>(A->cmupart, gx + gy, mu_factor, mu_dev, dst_mu);
+        c->launches++;
+    }
+    CU(cudaGetLastError());
+    return ROK_OK;
+}
+
 // residual VJP launches: out1 += s1 g, out2 += s2 g with g = J(ystate)^T ubar;
 // dst_mu += mu_factor (* mu_dev) ubar . df/dmu(ystate)
 rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, const VjpOut &o, double *dst_mu,
                double mu_factor, const double *mu_dev, const double *dir = nullptr, const double *dir_scale = nullptr)
 {
-    if (c->curv || c->kind == ROK_LORENZ96)
-        return vjp_colored(c, A, ystate, ub, o, dst_mu, mu_factor, mu_dev, dir, dir_scale);
+    if (curv_sweep(c)) return vjp_curv(c, A, ystate, ub, o, dst_mu, mu_factor, mu_dev, dir, dir_scale);
+    if (colored(c)) return vjp_colored(c, A, ystate, ub, o, dst_mu, mu_factor, mu_dev, dir, dir_scale);
     const StencilConsts &C = c->C;
     const size_t nc = (size_t)C.nx * C.ny;
     const int nb = (int)((nc + AT - 1) / AT);
@@ -1011,7 +1378,7 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
 
 rok_status vjp_supported(const rok_ctx *c)
 {
-    (void)c;   // every grid and problem kind (compressed Jacobian off uniform grids)
+    (void)c;   // every grid and problem kind
     return ROK_OK;
 }
 
@@ -1025,6 +1392,7 @@ void free_work(AdjWork *A)
     cudaFree(A->pA); cudaFree(A->pB); cudaFree(A->pM);
     cudaFree(A->faces); cudaFree(A->prims); cudaFree(A->mupart); cudaFree(A->as);
     cudaFree(A->cseed); cudaFree(A->cD); cudaFree(A->cg); cudaFree(A->cpart);
+    cudaFree(A->cfaces); cudaFree(A->cmupart);
     cudaFreeHost(A->h_st); cudaFreeHost(A->h_mub);
     delete A;
 }
@@ -1040,14 +1408,21 @@ rok_status ensure_work(rok_ctx *c, bool full)
     A->M = c->mmax;
     auto al = [&](double **p, size_t n) { return cudaMalloc(p, n * sizeof(double)) == cudaSuccess; };
     bool ok = true;
-    if (!A->faces) {
+    if (!A->prims) {
+        // face values of the uniform-grid sweep (curvilinear grids keep theirs in cfaces)
+        const bool uniform = !c->curv && c->kind != ROK_LORENZ96;
         A->nmu = 2 * (int)((nc + FT - 1) / FT);
-        ok = al(&A->faces, 2 * kFaceVals * nc) && al(&A->prims, 5 * nc) && al(&A->mupart, A->nmu) &&
+        ok = al(&A->prims, 5 * nc) && al(&A->mupart, A->nmu) && (!uniform || al(&A->faces, 2 * kFaceVals * nc)) &&
              cudaMalloc(&A->as, sizeof(AdjState)) == cudaSuccess &&
              cudaMallocHost(&A->h_mub, sizeof(double)) == cudaSuccess;
     }
-    if (ok && (c->curv || c->kind == ROK_LORENZ96) && !A->cseed)
+    if (ok && colored(c) && !A->cseed)
         ok = al(&A->cseed, N) && al(&A->cD, N) && al(&A->cg, N) && al(&A->cpart, 2 * (size_t)c->P);
+    if (ok && curv_sweep(c) && !A->cfaces) {
+        const size_t nfx = (size_t)(c->C.nx + 1) * c->C.ny, nfy = (size_t)c->C.nx * (c->C.ny + 1);
+        ok = al(&A->cfaces, kCurvFaceVals * (nfx + nfy)) &&
+             al(&A->cmupart, (nfx + FT - 1) / FT + (nfy + FT - 1) / FT);
+    }
     if (ok && full) {
         ok = al(&A->Vb, (size_t)(c->mmax > 0 ? c->mmax : 1) * N) && al(&A->yb, N) && al(&A->Fb, N) &&
              al(&A->F1b, N) && al(&A->F1acc, N) && al(&A->wb, N) && al(&A->wcur, N) && al(&A->wlast, N) &&

@@ -49,6 +49,14 @@ def _off_uniform_cases():
     # O-grid 32 x 16 (periodic in theta, wall and far field), Sutherland's law
     p4, y4, _ = W.cylinder_ogrid(16, 32)
     out.append(('ogrid-32x16', p4, np.ascontiguousarray(y4 + 0.02 * W.random_smooth_state(p4, seed=2))))
+    # walls on three sides and a far field (i-walls: corner ghosts mirrored twice)
+    q_inf = (1.0, 0.3, 0.1, 2.5)
+    xw, yw = W.perturbed_box_grid(20, 18, 2.0, 1.8, amp=0.3, seed=5)
+    p6 = W.FlowProblem(kind=W.NAVIER_STOKES, nx=20, ny=18, xv=xw, yv=yw, mu=0.02, q_inf=q_inf,
+                       bc=(W.WALL, W.FARFIELD, W.WALL, W.WALL), sutherland_s=0.4, t_ref=0.5)
+    out.append(('box-walls-20x18', p6, W.random_smooth_state(p6, seed=8, amp=0.08)))
+    p7 = W.FlowProblem(**{**p3.__dict__, 'kind': W.EULER, 'mu': 0.0})
+    out.append(('curv-euler-40x36', p7, W.random_smooth_state(p7, seed=9, amp=0.08)))
     p5, y5 = W.lorenz96(40)
     out.append(('lorenz-40', p5, y5))
     return out
