@@ -78,7 +78,8 @@ class _Integrate(torch.autograd.Function):
 def integrate(rctx, y0, mu, h, M, nsteps, checkpoint_every=10, tapes=True):
     """y_K after ``nsteps`` ROK4 steps of size h (Krylov dimension M) from y0,
     differentiable with respect to y0 and mu (a 0-d float64 tensor equal to
-    the context problem's constant viscosity).  ``tapes``: keep each re-run
+    the context problem's viscosity: the constant one, or under Sutherland's
+    law the viscosity at t_ref).  ``tapes``: keep each re-run
     step's internals for its reverse (faster, about (10 + M) state vectors per
     step of a segment) instead of recomputing them."""
     return _Integrate.apply(y0, mu, rctx, float(h), int(M), int(nsteps), int(checkpoint_every), bool(tapes))

@@ -150,6 +150,37 @@ def _gpu_gradient(rok, prob, y0, h, M, K, every):
     return host(y.grad), float(mu.grad)
 
 
+def test_gradient_on_the_cylinder_ogrid_matches_oracle_complex_step(rok):
+    # curvilinear reverse sweep inside the differentiable integration: J =
+    # kinetic energy after 4 ROK4 steps (M = 4, CFL 2) on a 32 x 16 O-grid
+    # (wall, far field, Sutherland's law), checkpoints every 2 steps; dJ/dy0 . d
+    # and dJ/dmu_ref against the complex step through the oracle's 4 steps (in
+    # the state, and in mu_ref through the affine continuation f + i d df/dmu)
+    prob, y0, _ = W.cylinder_ogrid(16, 32)
+    y0 = np.ascontiguousarray(y0 + 0.02 * W.random_smooth_state(prob, seed=2))
+    h = I.dt_from_cfl(prob, y0, 2.0)
+    M, K = 4, 4
+    g, gmu = _gpu_gradient(rok, prob, y0, h, M, K, 2)
+    d = np.random.default_rng(11).standard_normal(y0.shape)
+    yc = y0 + 1e-30j * d
+    for _ in range(K):
+        yc = I.rok_step(core.System(prob), yc, h, M)
+    cs = float(np.imag(_ke(yc)) / 1e-30)
+    assert abs(np.sum(g * d) - cs) <= 1e-5 * abs(cs), (np.sum(g * d), cs)
+
+    class MuStep(core.System):
+        def f(self, yy):
+            return core.residual(prob, yy) + 1e-30j * A.residual_dmu(prob, yy)
+
+        def jvp(self, yy, v, f0, eps):
+            return (self.f(np.asarray(yy) + eps * np.asarray(v)) - f0) / eps
+    yc = y0.astype(complex)
+    for _ in range(K):
+        yc = I.rok_step(MuStep(prob), yc, h, M)
+    csm = float(np.imag(_ke(yc)) / 1e-30)
+    assert abs(gmu - csm) <= 1e-5 * abs(csm), (gmu, csm)
+
+
 def test_gradient_wrt_state_with_checkpoints_matches_oracle_complex_step(rok):
     # J = kinetic energy after 6 ROK4 steps (M = 8, CFL 1) of the Euler vortex,
     # checkpoint every 2 steps: dJ/dy0 . d against the complex-step derivative of
