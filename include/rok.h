@@ -250,9 +250,12 @@ rok_status dopri5_integrate(rok_ctx *ctx, double *y, double T, const rok_adapt_o
  * viscosity part.  The derivative is that of the discrete step map (the
  * discrete adjoint), with the finite-difference increment eps of
  * Eq. matvecFD held constant.  Supported: every problem and grid of
- * rok_init with the binary64 basis and finite-difference JVPs (the reverse
- * step of the binary32 basis or of the exact-JVP step returns
- * ROK_ERR_UNSUPPORTED).  Euler / Navier-Stokes grids take a hand-written
+ * rok_init with finite-difference JVPs (the reverse step of the exact-JVP
+ * step returns ROK_ERR_UNSUPPORTED: it would need second derivatives of f).
+ * With the binary32 basis the reverse runs in binary64 on the basis the
+ * step built, widened exactly: the derivative of the exact-arithmetic
+ * Arnoldi process (MGS and classical Gram-Schmidt twice coincide there) at
+ * the rounded basis.  Euler / Navier-Stokes grids take a hand-written
  * reverse sweep of the face fluxes (uniform and curvilinear, every boundary
  * condition; a few residuals' cost per product); Lorenz-96 and curvilinear
  * grids of fewer than 2 cells in a direction take J^T u from a compressed

@@ -1490,6 +1490,12 @@ static rok_status step_internals(rok_ctx *c, const double *y, double h, int M, i
     }
     const int m = A->h_st->meff;
     *m_out = m;
+    // binary32 basis: widened exactly into the binary64 basis array, on which
+    // the recomputed last column below and the reverse run.  The classical
+    // Gram-Schmidt of the FMA build and MGS give the same V and H in exact
+    // arithmetic, so the reverse of MGS is the derivative of either (at the
+    // rounded basis).
+    if (c->fp32 && m > 0) CU(launch_f2d(c->Vf, c->V, (size_t)m * N, s));
     // the last column's orthogonalised w (not kept by the step): its JVP and MGS
     // passes again, H entries to scratch
     if (m > 0) {
@@ -1734,7 +1740,7 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
     if (ybar_out == y) return ROK_ERR_INVALID_ARG;
     rok_status r = vjp_supported(c);
     if (r != ROK_OK) return r;
-    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
+    if (c->exact_jvp) return ROK_ERR_UNSUPPORTED;
     if ((r = ensure_work(c, true)) != ROK_OK) return r;
     int m = 0;
     if ((r = step_internals(c, y, h, M, &m)) != ROK_OK) return r;
@@ -1756,7 +1762,7 @@ rok_status rok_step_record(rok_ctx *c, double *y, double h, int M, void *tape)
     if ((uintptr_t)tape % kTapeAlign || overlaps(y, vb, tape, L.bytes)) return ROK_ERR_INVALID_ARG;
     rok_status r = vjp_supported(c);
     if (r != ROK_OK) return r;
-    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
+    if (c->exact_jvp) return ROK_ERR_UNSUPPORTED;
     if ((r = ensure_work(c, true)) != ROK_OK) return r;
     AdjWork *A = c->adj;
     cudaStream_t s = c->stream;
@@ -1791,7 +1797,7 @@ rok_status rok_step_vjp_tape(rok_ctx *c, const void *tape, const double *ybar_in
     if (!c || !tape || !ybar_in || !ybar_out || (uintptr_t)tape % kTapeAlign) return ROK_ERR_INVALID_ARG;
     rok_status r = vjp_supported(c);
     if (r != ROK_OK) return r;
-    if (c->fp32 || c->exact_jvp) return ROK_ERR_UNSUPPORTED;
+    if (c->exact_jvp) return ROK_ERR_UNSUPPORTED;
     if ((r = ensure_work(c, true)) != ROK_OK) return r;
     AdjWork *A = c->adj;
     const size_t N = c->N, vb = N * sizeof(double);
