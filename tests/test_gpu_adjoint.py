@@ -250,7 +250,9 @@ def test_step_vjp_binary32_basis_matches_oracle_adjoint(rok, name, mode):
     # the reverse on the widened binary32 basis: the derivative of the exact
     # Arnoldi process at the rounded basis, against the oracle's binary64
     # adjoint (the basis rounding, relative 2^-24, enters the JVP directions,
-    # not the FD increment, so no 1/eps amplification)
+    # not the FD increment, so no 1/eps amplification).  FMA build: the bar of
+    # test_step_vjp_euler_vortex, the recomputed step's FD noise (the oracle's
+    # own reverse moves by 1.3e-5 under one-ulp state changes on Taylor-Green)
     if name == 'tgv-24':
         prob, y = W.taylor_green(24, reynolds=400.0)
         y = np.ascontiguousarray(y + 0.01 * W.random_smooth_state(prob, seed=5))
@@ -265,8 +267,9 @@ def test_step_vjp_binary32_basis_matches_oracle_adjoint(rok, name, mode):
     ref, mref = A.rok_step_vjp(prob, y, h, M, c)
     err = np.linalg.norm(host(yb) - ref) / np.linalg.norm(ref)
     print(name, mode, 'binary32 basis: relative L2 of ybar', err, 'mubar', mub, mref)
-    assert err <= 1e-5, err
-    assert abs(mub - mref) <= 1e-5 * abs(mref), (mub, mref)
+    bar = 1e-5 if mode == 'strict' else max(1e-5, 4 * _adjoint_self_sensitivity(prob, y, h, M, c))
+    assert err <= bar, (err, bar)
+    assert abs(mub - mref) <= bar * abs(mref), (mub, mref)
 
 
 def test_vjp_unsupported_cases(rok):
@@ -344,8 +347,8 @@ def test_tape_rejects_bad_arguments(rok):
     p2, y2 = W.taylor_green(32, reynolds=300.0)
     ctx2 = rok.rok_init(p2, krylov_max=4)
     assert status(lambda: rok.rok_step_vjp_tape(ctx2, tape, dev(np.ones(y2.shape)))) == rok.ROK_ERR_INVALID_ARG
-    # the binary32 basis has no reverse
-    ctx3 = rok.rok_init(prob, krylov_max=4, basis=rok.ROK_BASIS_FP32)
+    # the exact-JVP step has no reverse
+    ctx3 = rok.rok_init(prob, krylov_max=4, jvp=rok.ROK_JVP_EXACT)
     assert status(lambda: rok.rok_step_record(ctx3, dev(y), h, 4, tape)) == rok.ROK_ERR_UNSUPPORTED
 
 
