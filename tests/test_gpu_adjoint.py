@@ -37,7 +37,7 @@ def _cases():
     out.append(('ns-sutherland-40x36', ps, y))
     p, y = W.isentropic_vortex(33)
     out.append(('euler-33', p, y))
-    # off uniform periodic grids: the compressed-Jacobian product
+    # curvilinear grids (reverse sweep) and Lorenz-96 (compressed Jacobian)
     out.extend(_off_uniform_cases())
     return out
 
