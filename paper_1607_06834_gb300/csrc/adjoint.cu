@@ -1,7 +1,10 @@
 // Reverse mode (vector-Jacobian products) of the residual and of one ROK4 step
 // with finite-difference Jacobian-vector products (Sec. 2.2.2, Eq. ROK;
 // Sec. 2.3, Eq. matvecFD), for gradients of a final-time functional with
-// respect to the state and the (constant) viscosity.
+// respect to the state and the viscosity (the constant one, or the reference
+// viscosity of Sutherland's law).  Uniform periodic grids (below) and
+// curvilinear grids (their own two passes, further down) take hand-written
+// reverse sweeps; Lorenz-96 takes a compressed Jacobian of exact JVPs.
 //
 // Residual VJP, uniform periodic grids: f_c = -(F_{c+1/2} - F_{c-1/2}) / dx
 // - (G_{c+1/2} - G_{c-1/2}) / dy, so a face flux's adjoint is
