@@ -1379,11 +1379,9 @@ rok_status vjp(rok_ctx *c, AdjWork *A, const double *ystate, const double *ub, c
     return ROK_OK;
 }
 
-rok_status vjp_supported(const rok_ctx *c)
-{
-    (void)c;   // every grid and problem kind
-    return ROK_OK;
-}
+// the reverse of a step: every grid, problem kind and basis, but not the
+// exact-JVP step (the derivative of J(y) v in y is a second derivative of f)
+rok_status step_reverse_supported(const rok_ctx *c) { return c->exact_jvp ? ROK_ERR_UNSUPPORTED : ROK_OK; }
 
 void free_work(AdjWork *A)
 {
@@ -1715,8 +1713,7 @@ extern "C" {
 rok_status rok_vjp(rok_ctx *c, const double *y, const double *ubar, double *ybar, double *mubar)
 {
     if (!c || !y || !ubar || !ybar || ybar == y || ybar == ubar) return ROK_ERR_INVALID_ARG;
-    rok_status r = vjp_supported(c);
-    if (r != ROK_OK) return r;
+    rok_status r;
     if ((r = ensure_work(c, false)) != ROK_OK) return r;
     AdjWork *A = c->adj;
     CU(cudaMemsetAsync(ybar, 0, c->N * sizeof(double), c->stream));
@@ -1741,9 +1738,8 @@ rok_status rok_step_vjp(rok_ctx *c, const double *y, double h, int M, const doub
     if (!c || !y || !ybar_in || !ybar_out || M < 0 || M > c->mmax || !(h > 0.0) || !isfinite(h))
         return ROK_ERR_INVALID_ARG;
     if (ybar_out == y) return ROK_ERR_INVALID_ARG;
-    rok_status r = vjp_supported(c);
+    rok_status r = step_reverse_supported(c);
     if (r != ROK_OK) return r;
-    if (c->exact_jvp) return ROK_ERR_UNSUPPORTED;
     if ((r = ensure_work(c, true)) != ROK_OK) return r;
     int m = 0;
     if ((r = step_internals(c, y, h, M, &m)) != ROK_OK) return r;
@@ -1763,9 +1759,8 @@ rok_status rok_step_record(rok_ctx *c, double *y, double h, int M, void *tape)
     const size_t N = c->N, vb = N * sizeof(double);
     const TapeLayout L = tape_layout(N, M);
     if ((uintptr_t)tape % kTapeAlign || overlaps(y, vb, tape, L.bytes)) return ROK_ERR_INVALID_ARG;
-    rok_status r = vjp_supported(c);
+    rok_status r = step_reverse_supported(c);
     if (r != ROK_OK) return r;
-    if (c->exact_jvp) return ROK_ERR_UNSUPPORTED;
     if ((r = ensure_work(c, true)) != ROK_OK) return r;
     AdjWork *A = c->adj;
     cudaStream_t s = c->stream;
@@ -1798,9 +1793,8 @@ rok_status rok_step_record(rok_ctx *c, double *y, double h, int M, void *tape)
 rok_status rok_step_vjp_tape(rok_ctx *c, const void *tape, const double *ybar_in, double *ybar_out, double *mubar)
 {
     if (!c || !tape || !ybar_in || !ybar_out || (uintptr_t)tape % kTapeAlign) return ROK_ERR_INVALID_ARG;
-    rok_status r = vjp_supported(c);
+    rok_status r = step_reverse_supported(c);
     if (r != ROK_OK) return r;
-    if (c->exact_jvp) return ROK_ERR_UNSUPPORTED;
     if ((r = ensure_work(c, true)) != ROK_OK) return r;
     AdjWork *A = c->adj;
     const size_t N = c->N, vb = N * sizeof(double);
