@@ -1047,7 +1047,7 @@ __device__ __forceinline__ void ext_prim(const StencilConsts &C, const double *_
     }
 }
 
-// u, v, T at vertex (vi, vj): the mean of its four cells, in the oracle's order
+// u, v, T at vertex (vi, vj): the mean of its four cells, summed ((a + b) + c) + d
 __device__ __forceinline__ void vertex_uvT(const StencilConsts &C, const double *__restrict__ pr, size_t nc, int vi,
                                            int vj, double *o)
 {
