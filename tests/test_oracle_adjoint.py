@@ -21,6 +21,12 @@ def _cases():
     out.append(('euler-8x8', p, y))
     p4, y4, _ = W.cylinder_ogrid(6, 16)
     out.append(('ogrid-6x16', p4, np.ascontiguousarray(y4 + 0.02 * W.random_smooth_state(p4, seed=2))))
+    # walls on three sides and a far field, Sutherland's law (corner ghosts
+    # mirrored across two walls)
+    xw, yw = W.perturbed_box_grid(7, 6, 2.0, 1.8, amp=0.3, seed=5)
+    p6 = W.FlowProblem(kind=W.NAVIER_STOKES, nx=7, ny=6, xv=xw, yv=yw, mu=0.02, q_inf=(1.0, 0.3, 0.1, 2.5),
+                       bc=(W.WALL, W.FARFIELD, W.WALL, W.WALL), sutherland_s=0.4, t_ref=0.5)
+    out.append(('box-walls-7x6', p6, W.random_smooth_state(p6, seed=8, amp=0.08)))
     p5, y5 = W.lorenz96(12)
     out.append(('lorenz12', p5, y5))
     return out
